@@ -1,0 +1,174 @@
+/*
+ * fe_ks.h -- C interface of the GB300 matrix-free finite-element Kohn-Sham
+ * operator Y = H X (Panigrahi & Motamarri, "Matrix-free algorithms for fast
+ * ab initio calculations on distributed CPU architectures using
+ * finite-element discretization").
+ *
+ * H = H_loc + H_nloc is the FE-discretised Kohn-Sham Hamiltonian of a periodic
+ * cell (Sec. 2.2, eq. FEeigen):
+ *   H_loc = T + L + G - iK                                   (eq. Hloc)
+ *     T_IJ = 1/2 int grad N_I . grad N_J
+ *     L_IJ = int V^L N_I N_J,   V^L = V_loc + |k|^2/2         (eq. Vloc)
+ *     G_IJ = int V^G . (grad N_I N_J + N_I grad N_J)
+ *     K_IJ = int k . (N_I grad N_J)
+ *   H_nloc,IJ = sum_a sum_b F^a_{b,I} h^a_b conj(F^a_{b,J})  (eq. Vnonloc)
+ *     F^a_{b,I} = int sum_r exp(-ik.(x - L_r)) chi^a_b(x - R_a - L_r) N_I(x) dx
+ * N_I are degree-p Lagrange functions on Gauss-Lobatto-Legendre nodes; the
+ * integrals use the tensor Gauss rule with n_q points per direction
+ * (eq. cellIntegrals).  The action is evaluated matrix-free: cell gather
+ * Q C P X, sum-factorised contractions with N^1D and the collocation
+ * derivative D~^1D, quadrature-point coefficients, transposed contractions and
+ * scatter-add (eq. HX, eq. ggaReal / eq. ggaCmplx, Algorithms 1 and 2).
+ *
+ * Conventions (all entry points):
+ *  - Multivectors are row-major [m][n_v] with the vector index fastest.
+ *    Complex operators (k != 0) use interleaved complex numbers (re, im),
+ *    i.e. [m][n_v] complex = [m][2 n_v] reals.  Pointers must be 16-byte
+ *    aligned device pointers unless stated otherwise.
+ *  - Calls are asynchronous on the context's CUDA stream.  Argument errors are
+ *    reported synchronously; device-side errors (watchdog timeouts) are
+ *    reported by the next call that synchronises, or by fe_ks_check_status.
+ *  - No call after fe_ks_setup allocates device memory except where stated.
+ *  - On error the call returns a negative fe_ks_status and fe_ks_last_error()
+ *    returns a message (thread-local).  No C++ exception crosses the ABI.
+ */
+#ifndef FE_KS_H
+#define FE_KS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fe_ks_ctx fe_ks_ctx;   /* opaque; owns the device copies of all tables */
+
+typedef enum {
+  FE_KS_OK = 0,
+  FE_KS_ERR_ARG = -1,          /* invalid argument (null pointer, bad size, misalignment)   */
+  FE_KS_ERR_MESH = -2,         /* invalid mesh: DoF index out of range, det J <= 0         */
+  FE_KS_ERR_CUDA = -3,         /* a CUDA runtime call failed                                */
+  FE_KS_ERR_OOM = -4,          /* device allocation failed during setup                     */
+  FE_KS_ERR_TIMEOUT = -5,      /* a device-side bounded wait gave up (batched persistent)   */
+  FE_KS_ERR_UNSUPPORTED = -6   /* valid request this build does not implement               */
+} fe_ks_status;
+
+/* Arithmetic of one application. */
+typedef enum {
+  FE_KS_F64 = 0,               /* FP64 storage and FP64 arithmetic (DFMA)                  */
+  FE_KS_F32 = 1                /* FP32 storage and FP32 arithmetic (FFMA)                  */
+} fe_ks_precision;
+
+/* Terms of H that an application includes (terms_mask of fe_ks_setup). */
+enum {
+  FE_KS_TERM_T = 1,            /* kinetic 1/2 grad.grad                                     */
+  FE_KS_TERM_L = 2,            /* local potential V_loc + |k|^2/2                          */
+  FE_KS_TERM_G = 4,            /* GGA gradient term (needs v_gga_q)                        */
+  FE_KS_TERM_K = 8,            /* Bloch -iK term (k != 0)                                   */
+  FE_KS_TERM_NL = 16,          /* separable nonlocal pseudopotential                       */
+  FE_KS_TERM_ALL = 31
+};
+
+/*
+ * Problem description.  All pointers are HOST pointers, read during
+ * fe_ks_setup only; the caller keeps ownership.
+ *
+ *  n_cells, n_dofs : E hexahedral cells, m global DoFs (after periodic
+ *                    identification; the constraint map C is folded into
+ *                    cell_dofs, Sec. 3.1 eq. HX).
+ *  degree          : FE degree p, n_p = p + 1 GLL nodes per direction (2..8).
+ *  n_q             : Gauss points per direction; this build supports n_q = n_p.
+ *  cell_vertices   : [E][8][3] physical vertex coordinates; vertex slot
+ *                    a + 2b + 4c sits at reference corner (2a-1, 2b-1, 2c-1);
+ *                    the cell map is trilinear; coordinates are unwrapped per
+ *                    cell (periodic images are not folded back).
+ *  cell_dofs       : [E][n_p^3] global DoF of local node i + n_p (j + n_p k).
+ *  v_loc_q         : [E][n_q^3] V_loc at the quadrature points returned by
+ *                    fe_ks_quadrature_points, WITHOUT |k|^2/2 (setup adds it).
+ *  v_gga_q         : [E][n_q^3][3] physical V^G at the quadrature points, or NULL.
+ *  kpt             : Bloch vector k (bohr^-1).  Nonzero k makes the operator
+ *                    complex; force_complex = 1 makes it complex at k = 0 too.
+ *  n_atoms, n_proj : atoms carrying separable projectors, projectors per atom.
+ *  atom_cell_ptr   : [n_atoms + 1] CSR offsets into atom_cells / image_shift.
+ *  atom_cells      : [nnz] cells meeting the support of atom a (E(a) of Sec. 3);
+ *                    a cell may appear twice with different lattice images.
+ *  image_shift     : [nnz][3] lattice vector L_r of the atom image for that entry.
+ *  chi_q           : [nnz][n_q^3][n_proj] projector values chi_b(x_Q - R_a - L_r)
+ *                    at that cell's quadrature points (real).
+ *  h_coef          : [n_atoms][n_proj] diagonal coefficients Delta^a (Ha).
+ */
+typedef struct {
+  int64_t n_cells;
+  int64_t n_dofs;
+  int32_t degree;
+  int32_t n_q;
+  const double* cell_vertices;
+  const int32_t* cell_dofs;
+  const double* v_loc_q;
+  const double* v_gga_q;
+  double kpt[3];
+  int32_t force_complex;
+  int32_t n_atoms;
+  int32_t n_proj;
+  const int32_t* atom_cell_ptr;
+  const int32_t* atom_cells;
+  const double* image_shift;
+  const double* chi_q;
+  const double* h_coef;
+} fe_ks_problem;
+
+/*
+ * Physical coordinates of all quadrature points, so the caller can evaluate
+ * its fields there (Sec. 3.1, eq. cellIntegrals: tensor Gauss points mapped by
+ * the trilinear cell map).  xq_out is a HOST buffer [E][n_q^3][3], point index
+ * qx + n_q (qy + n_q qz).  Only n_cells, degree, n_q and cell_vertices are read.
+ */
+fe_ks_status fe_ks_quadrature_points(const fe_ks_problem* prob, double* xq_out);
+
+/*
+ * Build a context: 1D tables (Gauss / GLL by Newton iteration), per-point
+ * coefficients (Sec. 3.1 eq. reformcellmat with the Jacobian scaling folded
+ * in), cell-level projector matrices F^(a,e) (eq. Vnonloc), a conflict-free
+ * colouring of the cells for the scatter-add, the GLL-lumped mass D, and all
+ * device workspace for n_v_max vectors.  terms_mask selects the terms of H.
+ * cuda_stream (cudaStream_t, may be NULL = legacy default stream) orders all
+ * later calls.  Returns FE_KS_ERR_MESH for out-of-range DoFs or det J <= 0.
+ */
+fe_ks_status fe_ks_setup(const fe_ks_problem* prob, int terms_mask, int64_t n_v_max,
+                         void* cuda_stream, fe_ks_ctx** out);
+
+/*
+ * Y = H X for n_v vectors (eq. HX).  X, Y: device [m][n_v] (complex:
+ * interleaved) in the precision's storage type (double or float).  Y is
+ * overwritten.  X and Y must not overlap.  1 <= n_v <= n_v_max.
+ */
+fe_ks_status fe_ks_apply(fe_ks_ctx* ctx, const void* X, void* Y, int64_t n_v, int precision);
+
+/*
+ * Y = Hs X with Hs = D^{-1/2} H D^{-1/2}, D the GLL-lumped mass (the diagonal
+ * approximation of M used by Algorithm 4).  Same layout rules as fe_ks_apply.
+ */
+fe_ks_status fe_ks_apply_scaled(fe_ks_ctx* ctx, const void* X, void* Y, int64_t n_v,
+                                int precision);
+
+/* Length-m device copy of D^{-1/2} in FP64 (owned by the context). */
+const double* fe_ks_dinv_sqrt(const fe_ks_ctx* ctx);
+
+/* Problem sizes as seen by the context. */
+fe_ks_status fe_ks_info(const fe_ks_ctx* ctx, int64_t* n_dofs, int64_t* n_cells, int32_t* degree,
+                        int32_t* is_complex, int32_t* n_colours, int64_t* n_pairs);
+
+/* Change the stream used by later calls. */
+fe_ks_status fe_ks_set_stream(fe_ks_ctx* ctx, void* cuda_stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* fe_ks_last_error(void);
+
+/* Free the context and all device memory it owns (NULL is ignored). */
+void fe_ks_destroy(fe_ks_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FE_KS_H */

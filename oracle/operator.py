@@ -78,10 +78,11 @@ class Problem:
             J += X[v][None, :, None] * dphi[:, None, :]
         return x, J
 
-    def cell(self, e):
+    def cell(self, e, grads=True):
         """Quadrature data of cell e (cached): points, weights*detJ, N and physical grad N."""
-        if e in self._cell_cache:
-            return self._cell_cache[e]
+        hit = self._cell_cache.get(e)
+        if hit is not None and (not grads or "g" in hit):
+            return hit
         t, nq, npn = self.t, self.nq, self.np_
         q = np.arange(nq)
         qz, qy, qx = np.meshgrid(q, q, q, indexing="ij")
@@ -90,51 +91,52 @@ class Problem:
         w = t["w_q"][qx] * t["w_q"][qy] * t["w_q"][qz]
         x, J = self.trilinear(e, xi)
         detJ = np.linalg.det(J)
-        Jinv = np.linalg.inv(J)
         li = np.arange(npn)
         kk, jj, ii = np.meshgrid(li, li, li, indexing="ij")
         ii, jj, kk = ii.ravel(), jj.ravel(), kk.ravel()        # I = i + np(j + np k)
         N, dN = t["N1D"], t["dN1D"]
         Bx, By, Bz = N[qx][:, ii], N[qy][:, jj], N[qz][:, kk]
         B = Bx * By * Bz                                       # [Q, I]
-        gref = np.stack([dN[qx][:, ii] * By * Bz,
-                         Bx * dN[qy][:, jj] * Bz,
-                         Bx * By * dN[qz][:, kk]], axis=0)     # [3, Q, I]  d/dxi_d
-        # grad_x N = J^{-T} grad_xi N : component c = sum_d Jinv[d, c] d/dxi_d
-        gphys = np.einsum("qdc,dqi->cqi", Jinv, gref)
-        out = dict(x=x, wdet=w * detJ, detJ=detJ, B=B, g=gphys)
-        if len(self._cell_cache) < 4096:
+        out = dict(x=x, wdet=w * detJ, detJ=detJ, B=B)
+        if grads:
+            Jinv = np.linalg.inv(J)
+            gref = np.stack([dN[qx][:, ii] * By * Bz,
+                             Bx * dN[qy][:, jj] * Bz,
+                             Bx * By * dN[qz][:, kk]], axis=0)     # [3, Q, I]  d/dxi_d
+            # grad_x N = J^{-T} grad_xi N : component c = sum_d Jinv[d, c] d/dxi_d
+            out["g"] = np.einsum("qdc,dqi->cqi", Jinv, gref)
+        if len(self._cell_cache) < 512:
             self._cell_cache[e] = out
         return out
 
     # ------------------------------------------------------- cell matrices
-    def cell_matrix(self, e, terms=("T", "L", "G", "K")):
-        """H^(e) = T + L + G - iK (eq. Hloccell), real when k = 0."""
+    def cell_matrix(self, e, terms=("T", "L", "G", "K"), rows=None):
+        """H^(e) = T + L + G - iK (eq. Hloccell), real when k = 0; optionally only rows `rows`."""
         c = self.cell(e)
         wd, B, g = c["wdet"], c["B"], c["g"]
+        sel = slice(None) if rows is None else np.asarray(rows)
         k = self.kpt
-        H = np.zeros((B.shape[1], B.shape[1]))
+        H = np.zeros((B[:, sel].shape[1], B.shape[1]))
         if "T" in terms:
             for d in range(3):
-                H += 0.5 * g[d].T @ (wd[:, None] * g[d])
+                H += 0.5 * g[d][:, sel].T @ (wd[:, None] * g[d])
         if "L" in terms:
             VL = self.vloc(c["x"]) + 0.5 * float(k @ k)
-            H += B.T @ ((wd * VL)[:, None] * B)
+            H += B[:, sel].T @ ((wd * VL)[:, None] * B)
         if "G" in terms and self.vgga is not None:
             VG = self.vgga(c["x"])                              # [Q,3]
             gv = np.einsum("qc,cqi->qi", VG, g)                 # V^G . grad N_I at Q
-            Gm = gv.T @ (wd[:, None] * B)                       # int (V^G.grad N_I) N_J
-            H += Gm + Gm.T
+            H += gv[:, sel].T @ (wd[:, None] * B)               # int (V^G.grad N_I) N_J
+            H += B[:, sel].T @ (wd[:, None] * gv)               # int N_I (V^G.grad N_J)
         if self.complex:
             H = H.astype(np.complex128)
             if "K" in terms:
                 kg = np.einsum("c,cqi->qi", k, g)               # k . grad N_J at Q
-                Km = B.T @ (wd[:, None] * kg)                   # int N_I (k . grad N_J)
-                H -= 1j * Km
+                H -= 1j * (B[:, sel].T @ (wd[:, None] * kg))    # int N_I (k . grad N_J)
         return H
 
     def mass_matrix(self, e):
-        c = self.cell(e)
+        c = self.cell(e, grads=False)
         return c["B"].T @ (c["wdet"][:, None] * c["B"])
 
     # ------------------------------------------------------------ nonlocal
@@ -148,7 +150,7 @@ class Problem:
 
     def projector_matrix(self, a, e):
         """F^(a,e)[I, b] = int_e sum_r exp(-ik.(x-L_r)) chi_b(x - R_a - L_r) N_I dx."""
-        c = self.cell(e)
+        c = self.cell(e, grads=False)
         x = c["x"]
         acc = np.zeros((x.shape[0], 9), dtype=np.complex128 if self.complex else np.float64)
         for Lr in lattice_images(self.wl.L):
@@ -162,14 +164,18 @@ class Problem:
                 acc += chi
         return c["B"].T @ (c["wdet"][:, None] * acc)            # [I, 9]
 
-    def projector_blocks(self):
-        """[(a, cells, [F^(a,e) for e in cells])] for all atoms (cached)."""
+    def projector_block(self, a):
+        """(a, cells, [F^(a,e) for e in cells]) for atom a (cached)."""
         if not hasattr(self, "_proj"):
-            self._proj = []
-            for a in range(self.R.shape[0]):
-                cells = self.atom_cells(a)
-                self._proj.append((a, cells, [self.projector_matrix(a, e) for e in cells]))
-        return self._proj
+            self._proj = {}
+        if a not in self._proj:
+            cells = self.atom_cells(a)
+            self._proj[a] = (a, cells, [self.projector_matrix(a, e) for e in cells])
+        return self._proj[a]
+
+    def projector_blocks(self):
+        """[(a, cells, [F^(a,e)])] for all atoms."""
+        return [self.projector_block(a) for a in range(self.R.shape[0])]
 
     # -------------------------------------------------------------- action
     def apply(self, X, local=True, nonlocal_=True, cells=None):
@@ -199,15 +205,16 @@ class Problem:
         hit = np.isin(self.dofs, rows)
         for e in np.nonzero(hit.any(axis=1))[0]:
             loc = np.nonzero(hit[e])[0]
-            He = self.cell_matrix(e)
-            contrib = He[loc] @ X[self.dofs[e]]
+            contrib = self.cell_matrix(e, rows=loc) @ X[self.dofs[e]]
             for li, row in zip(loc, contrib):
                 out[pos[int(self.dofs[e][li])]] += row
         if self.R.shape[0] > 0:
-            for a, cl, Fs in self.projector_blocks():
-                touch = [i for i, e in enumerate(cl) if hit[e].any()]
-                if not touch:
+            hit_cells = np.nonzero(hit.any(axis=1))[0]
+            for a in range(self.R.shape[0]):
+                if not np.isin(self.atom_cells(a), hit_cells).any():
                     continue
+                _, cl, Fs = self.projector_block(a)
+                touch = [i for i, e in enumerate(cl) if hit[e].any()]
                 P = sum(F.conj().T @ X[self.dofs[e]] for e, F in zip(cl, Fs))
                 P = self.h[a][:, None] * P
                 for i in touch:

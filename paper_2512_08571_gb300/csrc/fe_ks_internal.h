@@ -1,0 +1,136 @@
+// Internal declarations shared by the translation units of libfe_ks.so.
+// Paper: Panigrahi & Motamarri, matrix-free FE Kohn-Sham operator (Sec. 3-4).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/fe_ks.h"
+
+namespace feks {
+
+constexpr int kMaxN = 10;      // n_p, n_q <= 10
+constexpr int kMaxH = kMaxN / 2;
+
+// Even-odd split of a centro-(anti)symmetric 1D matrix M (NO x NI) with
+// M[NO-1-o][NI-1-i] = S * M[o][i]  (S = +1 for N^1D, -1 for D~^1D; Sec. 5.4,
+// "even-odd decomposition").  For o < NO/2, i < NI/2:
+//   E[o][i] = (M[o][i] + M[o][NI-1-i]) / 2,  E[o][NI/2] = M[o][NI/2] (NI odd)
+//   O[o][i] = (M[o][i] - M[o][NI-1-i]) / 2
+// and the middle row (NO odd) MID[i] = M[NO/2][i].
+template <typename T>
+struct EOMat {
+  T E[kMaxH][kMaxH + 1];
+  T O[kMaxH][kMaxH];
+  T MID[kMaxH + 1];
+};
+
+// The four 1D operators of Algorithm 2: N^1D, (N^1D)^T, D~^1D, (D~^1D)^T.
+template <typename T>
+struct EOTables {
+  EOMat<T> N, Nt, D, Dt;
+};
+
+// Coefficient slots per quadrature point (Sec. 3.1, eq. reformcellmat, with
+// det J w_Q and J^{-1} folded in):
+//   0..5  G_sd = 1/2 (J^-1 J^-T)_sd det J w      (00 01 02 11 12 22)
+//   6     V^L  = (V_loc + |k|^2/2) det J w
+//   7..9  V^G_s = (J^-1 V^G)_s det J w
+//   10..12 V^K_s = (J^-1 k)_s det J w           (complex operators only)
+constexpr int kCoefReal = 10;
+constexpr int kCoefCplx = 13;
+
+template <typename T>
+struct OpData {
+  T* coef = nullptr;       // [E][ncoef][n_q^3]
+  T* F = nullptr;          // [n_pairs][n_proj][n_p^3] (complex: x2 interleaved)
+  T* dscale = nullptr;     // [m] D^{-1/2}
+  T* Q = nullptr;          // workspace [n_atoms][n_proj][ncols_max]
+  EOTables<T> tab;
+};
+
+// Kernel parameters of the fused local kernel (one colour of cells).
+template <typename T>
+struct LocalParams {
+  const T* X;
+  T* Y;
+  int64_t ld;              // row pitch of X and Y in scalars (= ncols)
+  int ncols;               // real columns (complex: 2 n_v)
+  const int* cell_dofs;    // [E][n_p^3]
+  const int* cells;        // cells of this colour
+  int n_cells;
+  const T* coef;
+  int ncoef;
+  int gga;                 // V^G coefficients present
+  const T* dscale;         // D^{-1/2} or nullptr
+  // nonlocal expansion fused into the scatter (Algorithm 1, F Delta T3)
+  const int* cell_pair_ptr;  // [E+1] or nullptr
+  const int* cell_pairs;
+  const int* pair_atom;
+  const T* F;
+  const T* Q;              // [n_atoms][n_proj][ld], already scaled by Delta
+  int n_proj;
+  EOTables<T> tab;
+};
+
+// Projection kernel parameters: Q[a][b][col] = h[a][b] sum conj(F) X.
+template <typename T>
+struct ProjParams {
+  const T* X;
+  int64_t ld;
+  int ncols;
+  const int* cell_dofs;
+  const int* atom_pair_ptr;  // [n_atoms+1]
+  const int* pair_cell;
+  const T* F;
+  const T* h;              // [n_atoms][n_proj]
+  const T* dscale;
+  T* Q;
+  int n_proj;
+  int np3;
+};
+
+struct Ctx {
+  int p = 0, nq = 0, np = 0, np3 = 0, nq3 = 0;
+  int cplx = 0, terms = 0, gga = 0, ncoef = 0;
+  int64_t E = 0, m = 0, n_v_max = 0;
+  int n_atoms = 0, n_proj = 0;
+  int64_t n_pairs = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  // device tables
+  int* cell_dofs = nullptr;
+  int* colour_cells = nullptr;
+  std::vector<int> colour_ptr;
+  int* pair_atom = nullptr;
+  int* pair_cell = nullptr;
+  int* atom_pair_ptr = nullptr;
+  int* cell_pair_ptr = nullptr;
+  int* cell_pairs = nullptr;
+  double* h64 = nullptr;
+  float* h32 = nullptr;
+  OpData<double> f64;
+  OpData<float> f32;
+  std::vector<void*> allocations;
+};
+
+// error reporting (thread-local message)
+void set_error(const std::string& msg);
+fe_ks_status fail(fe_ks_status code, const std::string& msg);
+
+// host 1D tables (fe_ks_tables.cpp)
+void gauss_legendre(int n, double* x, double* w);
+void gauss_lobatto(int n, double* x, double* w);
+void lagrange_eval(int n, const double* nodes, double x, double* val, double* der);
+template <typename T>
+void build_eo_tables(int p, int nq, EOTables<T>* out);
+
+// kernel launchers (fe_ks_local_pN.cu)
+template <typename T>
+cudaError_t launch_local(const Ctx& c, const LocalParams<T>& prm, cudaStream_t s);
+template <typename T>
+cudaError_t launch_proj(const Ctx& c, const ProjParams<T>& prm, int n_atoms, cudaStream_t s);
+
+}  // namespace feks

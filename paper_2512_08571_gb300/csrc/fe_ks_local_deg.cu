@@ -1,0 +1,12 @@
+// One FE degree of the fused local kernel (compiled once per degree with
+// -DFEKS_P=<p> so the degrees build in parallel).
+#include "fe_ks_local.cuh"
+
+#ifndef FEKS_P
+#error "FEKS_P must be defined"
+#endif
+
+namespace feks {
+template cudaError_t launch_local_deg<double, FEKS_P>(const Ctx&, const LocalParams<double>&, cudaStream_t);
+template cudaError_t launch_local_deg<float, FEKS_P>(const Ctx&, const LocalParams<float>&, cudaStream_t);
+}  // namespace feks

@@ -1,0 +1,134 @@
+// Host 1D tables: Gauss-Legendre rule, GLL nodes, Lagrange basis, and the
+// even-odd split of N^1D, (N^1D)^T, D~^1D, (D~^1D)^T (Sec. 3.2; Sec. 5.4).
+// Nodes come from Newton's method on Legendre polynomials (three-term
+// recurrence), written here independently of any other component.
+#include <cmath>
+
+#include "fe_ks_internal.h"
+
+namespace feks {
+
+// P_n(x) and P_n'(x) by the Bonnet recurrence.
+static void legendre(int n, double x, double* P, double* dP) {
+  double p0 = 1.0, p1 = x;
+  if (n == 0) {
+    *P = 1.0;
+    *dP = 0.0;
+    return;
+  }
+  for (int k = 2; k <= n; ++k) {
+    double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+    p0 = p1;
+    p1 = p2;
+  }
+  *P = p1;
+  if (std::fabs(std::fabs(x) - 1.0) < 1e-300) {
+    *dP = (x > 0 ? 1.0 : ((n - 1) % 2 ? -1.0 : 1.0)) * n * (n + 1) / 2.0;
+  } else {
+    *dP = n * (p0 - x * p1) / (1.0 - x * x);
+  }
+}
+
+void gauss_legendre(int n, double* x, double* w) {
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < n; ++i) {
+    double z = -std::cos(pi * (i + 0.75) / (n + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double P, dP;
+      legendre(n, z, &P, &dP);
+      double dz = P / dP;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    double P, dP;
+    legendre(n, z, &P, &dP);
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dP * dP);
+  }
+}
+
+void gauss_lobatto(int n, double* x, double* w) {
+  const double pi = 3.14159265358979323846;
+  const int p = n - 1;
+  x[0] = -1.0;
+  x[n - 1] = 1.0;
+  for (int i = 1; i < n - 1; ++i) {
+    double z = -std::cos(pi * i / p);
+    for (int it = 0; it < 100; ++it) {
+      double P, dP;
+      legendre(p, z, &P, &dP);
+      // Legendre's equation gives P'' = (2 z P' - p(p+1) P) / (1 - z^2)
+      double d2 = (2.0 * z * dP - p * (p + 1.0) * P) / (1.0 - z * z);
+      double dz = dP / d2;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[i] = z;
+  }
+  for (int i = 0; i < n; ++i) {
+    double P, dP;
+    legendre(p, x[i], &P, &dP);
+    w[i] = 2.0 / (p * (p + 1.0) * P * P);
+  }
+}
+
+// Lagrange basis on `nodes`: val[i] = L_i(x), der[i] = L_i'(x) (product rule).
+void lagrange_eval(int n, const double* nodes, double x, double* val, double* der) {
+  for (int i = 0; i < n; ++i) {
+    double v = 1.0, d = 0.0;
+    for (int j = 0; j < n; ++j) {
+      if (j == i) continue;
+      double f = 1.0 / (nodes[i] - nodes[j]);
+      d = d * (x - nodes[j]) * f + v * f;
+      v *= (x - nodes[j]) * f;
+    }
+    val[i] = v;
+    der[i] = d;
+  }
+}
+
+template <typename T>
+static void split(const double* M, int NO, int NI, EOMat<T>* out) {
+  *out = EOMat<T>{};
+  const int HO = NO / 2, HI = NI / 2;
+  for (int o = 0; o < HO; ++o) {
+    for (int i = 0; i < HI; ++i) {
+      out->E[o][i] = (T)(0.5 * (M[o * NI + i] + M[o * NI + NI - 1 - i]));
+      out->O[o][i] = (T)(0.5 * (M[o * NI + i] - M[o * NI + NI - 1 - i]));
+    }
+    if (NI % 2) out->E[o][HI] = (T)M[o * NI + HI];
+  }
+  if (NO % 2)
+    for (int i = 0; i <= HI && i < NI; ++i) out->MID[i] = (T)M[HO * NI + i];
+}
+
+template <typename T>
+void build_eo_tables(int p, int nq, EOTables<T>* out) {
+  const int np = p + 1;
+  double xg[kMaxN], wg[kMaxN], xq[kMaxN], wq[kMaxN];
+  gauss_lobatto(np, xg, wg);
+  gauss_legendre(nq, xq, wq);
+  double N[kMaxN * kMaxN], Nt[kMaxN * kMaxN], D[kMaxN * kMaxN], Dt[kMaxN * kMaxN];
+  double val[kMaxN], der[kMaxN];
+  for (int q = 0; q < nq; ++q) {
+    lagrange_eval(np, xg, xq[q], val, der);
+    for (int i = 0; i < np; ++i) {
+      N[q * np + i] = val[i];
+      Nt[i * nq + q] = val[i];
+    }
+    lagrange_eval(nq, xq, xq[q], val, der);
+    for (int r = 0; r < nq; ++r) {
+      D[q * nq + r] = der[r];
+      Dt[r * nq + q] = der[r];
+    }
+  }
+  split<T>(N, nq, np, &out->N);
+  split<T>(Nt, np, nq, &out->Nt);
+  split<T>(D, nq, nq, &out->D);
+  split<T>(Dt, nq, nq, &out->Dt);
+}
+
+template void build_eo_tables<double>(int, int, EOTables<double>*);
+template void build_eo_tables<float>(int, int, EOTables<float>*);
+
+}  // namespace feks

@@ -1,0 +1,131 @@
+"""ctypes binding of libfe_ks.so (argument marshalling only).
+
+Every function mirrors an entry point of ``include/fe_ks.h`` under the same
+name; all work happens in the library's CUDA kernels.  There is no fallback:
+if the shared library is missing or fails to load, importing the binding
+raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfe_ks.so")
+
+FE_KS_OK = 0
+STATUS_NAMES = {0: "FE_KS_OK", -1: "FE_KS_ERR_ARG", -2: "FE_KS_ERR_MESH", -3: "FE_KS_ERR_CUDA",
+                -4: "FE_KS_ERR_OOM", -5: "FE_KS_ERR_TIMEOUT", -6: "FE_KS_ERR_UNSUPPORTED"}
+FE_KS_F64, FE_KS_F32 = 0, 1
+TERM_T, TERM_L, TERM_G, TERM_K, TERM_NL, TERM_ALL = 1, 2, 4, 8, 16, 31
+
+EXPORTED = ("fe_ks_quadrature_points", "fe_ks_setup", "fe_ks_apply", "fe_ks_apply_scaled",
+            "fe_ks_dinv_sqrt", "fe_ks_info", "fe_ks_set_stream", "fe_ks_last_error", "fe_ks_destroy")
+
+
+class FeKsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class fe_ks_problem(ctypes.Structure):
+    _fields_ = [
+        ("n_cells", ctypes.c_int64), ("n_dofs", ctypes.c_int64),
+        ("degree", ctypes.c_int32), ("n_q", ctypes.c_int32),
+        ("cell_vertices", ctypes.c_void_p), ("cell_dofs", ctypes.c_void_p),
+        ("v_loc_q", ctypes.c_void_p), ("v_gga_q", ctypes.c_void_p),
+        ("kpt", ctypes.c_double * 3), ("force_complex", ctypes.c_int32),
+        ("n_atoms", ctypes.c_int32), ("n_proj", ctypes.c_int32),
+        ("atom_cell_ptr", ctypes.c_void_p), ("atom_cells", ctypes.c_void_p),
+        ("image_shift", ctypes.c_void_p), ("chi_q", ctypes.c_void_p), ("h_coef", ctypes.c_void_p),
+    ]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libfe_ks.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    lib.fe_ks_quadrature_points.argtypes = [P(fe_ks_problem), vp]
+    lib.fe_ks_setup.argtypes = [P(fe_ks_problem), ctypes.c_int, i64, vp, P(vp)]
+    lib.fe_ks_apply.argtypes = [vp, vp, vp, i64, ctypes.c_int]
+    lib.fe_ks_apply_scaled.argtypes = [vp, vp, vp, i64, ctypes.c_int]
+    lib.fe_ks_dinv_sqrt.argtypes = [vp]
+    lib.fe_ks_dinv_sqrt.restype = vp
+    lib.fe_ks_info.argtypes = [vp, P(i64), P(i64), P(i32), P(i32), P(i32), P(i64)]
+    lib.fe_ks_set_stream.argtypes = [vp, vp]
+    lib.fe_ks_last_error.restype = ctypes.c_char_p
+    lib.fe_ks_destroy.argtypes = [vp]
+    lib.fe_ks_destroy.restype = None
+    for name in ("fe_ks_quadrature_points", "fe_ks_setup", "fe_ks_apply", "fe_ks_apply_scaled",
+                 "fe_ks_info", "fe_ks_set_stream"):
+        getattr(lib, name).restype = ctypes.c_int
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def _check(status):
+    if status != FE_KS_OK:
+        raise FeKsError(status, _lib.fe_ks_last_error().decode())
+
+
+def _ptr(a):
+    """Data pointer of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def fe_ks_quadrature_points(prob):
+    xq = np.empty((prob.n_cells, prob.n_q ** 3, 3), dtype=np.float64)
+    _check(_lib.fe_ks_quadrature_points(ctypes.byref(prob), xq.ctypes.data))
+    return xq
+
+
+def fe_ks_setup(prob, terms_mask=TERM_ALL, n_v_max=1, stream=None):
+    ctx = ctypes.c_void_p()
+    _check(_lib.fe_ks_setup(ctypes.byref(prob), terms_mask, n_v_max, stream, ctypes.byref(ctx)))
+    return ctx
+
+
+def fe_ks_apply(ctx, X, Y, n_v, precision):
+    _check(_lib.fe_ks_apply(ctx, _ptr(X), _ptr(Y), n_v, precision))
+
+
+def fe_ks_apply_scaled(ctx, X, Y, n_v, precision):
+    _check(_lib.fe_ks_apply_scaled(ctx, _ptr(X), _ptr(Y), n_v, precision))
+
+
+def fe_ks_dinv_sqrt(ctx):
+    return _lib.fe_ks_dinv_sqrt(ctx)
+
+
+def fe_ks_info(ctx):
+    m, E, npairs = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    p, cplx, ncol = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib.fe_ks_info(ctx, ctypes.byref(m), ctypes.byref(E), ctypes.byref(p), ctypes.byref(cplx),
+                           ctypes.byref(ncol), ctypes.byref(npairs)))
+    return dict(n_dofs=m.value, n_cells=E.value, degree=p.value, complex=bool(cplx.value),
+                n_colours=ncol.value, n_pairs=npairs.value)
+
+
+def fe_ks_set_stream(ctx, stream):
+    _check(_lib.fe_ks_set_stream(ctx, stream))
+
+
+def fe_ks_last_error():
+    return _lib.fe_ks_last_error().decode()
+
+
+def fe_ks_destroy(ctx):
+    _lib.fe_ks_destroy(ctx)

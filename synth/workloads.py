@@ -22,7 +22,7 @@ import numpy as np
 __all__ = [
     "Workload", "CONFIGS", "batched_systems", "make_mesh", "vloc_fn", "vgga_fn",
     "atoms", "projector_values", "atom_cell_pairs", "trial_vectors", "N_PROJ",
-    "PROJ_L", "PROJ_RC", "PROJ_SIGMA", "lattice_images",
+    "PROJ_L", "PROJ_RC", "PROJ_SIGMA", "lattice_images", "trial_chunk", "TRIAL_CHUNK",
 ]
 
 N_PROJ = 9                     # l = 0, 1, 2 -> 1 + 3 + 5 real projectors
@@ -241,12 +241,38 @@ def atom_cell_pairs(wl, verts, R):
             np.array(shifts, dtype=np.float64).reshape(-1, 3))
 
 
-def trial_vectors(wl, n_v=None, seed_purpose=5):
-    """X [m, n_v], entries uniform in [-1, 1] (complex: re and im independent)."""
-    rng = _rng(wl, seed_purpose)
+TRIAL_CHUNK = 1 << 16
+
+
+def trial_vectors(wl, n_v=None, seed_purpose=5, rows=None, dtype=np.float64):
+    """X [m, n_v], entries uniform in [-1, 1] (complex: re and im independent).
+
+    Rows are drawn in fixed chunks of 65536 rows, chunk c from
+    default_rng(seed + purpose + 7919 c), so any subset of rows (``rows``) or
+    any chunk can be regenerated without drawing the whole matrix.
+    """
     n_v = wl.n_v if n_v is None else n_v
     m = wl.n_dofs
-    X = rng.uniform(-1.0, 1.0, (m, n_v))
+    if rows is None:
+        out = np.empty((m, n_v), dtype=np.complex128 if wl.complex else dtype)
+        for c0 in range(0, m, TRIAL_CHUNK):
+            out[c0:c0 + TRIAL_CHUNK] = trial_chunk(wl, n_v, c0 // TRIAL_CHUNK, seed_purpose)
+        return out
+    rows = np.asarray(rows)
+    out = np.empty((rows.size, n_v), dtype=np.complex128 if wl.complex else np.float64)
+    chunks = rows // TRIAL_CHUNK
+    for c in np.unique(chunks):
+        blk = trial_chunk(wl, n_v, int(c), seed_purpose)
+        sel = chunks == c
+        out[sel] = blk[rows[sel] - int(c) * TRIAL_CHUNK]
+    return out
+
+
+def trial_chunk(wl, n_v, c, seed_purpose=5):
+    """Rows [c*65536, min(m, (c+1)*65536)) of the trial block X."""
+    rng = np.random.default_rng(wl.seed + seed_purpose + 7919 * c)
+    r = min(wl.n_dofs, (c + 1) * TRIAL_CHUNK) - c * TRIAL_CHUNK
+    X = rng.uniform(-1.0, 1.0, (r, n_v))
     if wl.complex:
-        X = X + 1j * rng.uniform(-1.0, 1.0, (m, n_v))
+        X = X + 1j * rng.uniform(-1.0, 1.0, (r, n_v))
     return X

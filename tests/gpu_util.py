@@ -1,0 +1,45 @@
+"""Helpers shared by the GPU parity tests (test-side glue, no method arithmetic)."""
+import numpy as np
+
+from paper_2512_08571_gb300 import fe_ks as fk
+from paper_2512_08571_gb300.problem import HostProblem
+
+
+def rel_err_cols(Y, Yref):
+    """max over columns of ||Y_v - Yref_v||_2 / ||Yref_v||_2."""
+    num = np.linalg.norm(Y - Yref, axis=0)
+    den = np.linalg.norm(Yref, axis=0)
+    return float(np.max(num / np.maximum(den, 1e-300)))
+
+
+def torch_dtype(precision, cplx):
+    import torch
+    if precision == fk.FE_KS_F64:
+        return torch.complex128 if cplx else torch.float64
+    return torch.complex64 if cplx else torch.float32
+
+
+def round_input(X, precision):
+    """The input the GPU actually sees, promoted back to FP64 for the oracle."""
+    if precision == fk.FE_KS_F32:
+        return X.astype(np.complex64 if np.iscomplexobj(X) else np.float32).astype(
+            np.complex128 if np.iscomplexobj(X) else np.float64)
+    return X
+
+
+def gpu_apply(hp, X, precision, scaled=False, terms=fk.TERM_ALL, repeat=1):
+    import torch
+    n_v = X.shape[1]
+    ctx = fk.fe_ks_setup(hp.struct, terms, n_v, torch.cuda.current_stream().cuda_stream)
+    try:
+        dt = torch_dtype(precision, hp.complex)
+        Xd = torch.from_numpy(np.ascontiguousarray(X)).to("cuda").to(dt)
+        outs = []
+        for _ in range(repeat):
+            Yd = torch.full_like(Xd, float("nan"))
+            (fk.fe_ks_apply_scaled if scaled else fk.fe_ks_apply)(ctx, Xd, Yd, n_v, precision)
+            torch.cuda.synchronize()
+            outs.append(Yd.cpu().numpy())
+        return outs if repeat > 1 else outs[0]
+    finally:
+        fk.fe_ks_destroy(ctx)

@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Benchmark of the matrix-free FE Kohn-Sham operator Y = H X on GB300.
+
+Workload (default): the p = 8 configuration -- periodic cube L = 30 bohr,
+24^3 hexahedral cells, degree 8 with 9 Gauss points per direction, full real
+operator (kinetic + V_loc + GGA + 64 atoms of l <= 2 projectors), N_v = 256,
+m = 7,077,888 DoFs.  One step = one application Y = H X of the whole operator
+(all cells, all vectors) in FP64; X (14.5 GB) is far larger than L2, so no
+flush is needed between steps.  The line also carries the FP32 ("mixed")
+application on the same workload.
+
+Metric: DoF x vectors per second (m * N_v / time of one application).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+N > 1 runs under torchrun as independent replicas (one per GPU, weak
+scaling; the operator has no data-path exchange on one GPU per system).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "H.X DoF*vectors/s (FP64; mixed FP32 beside) at p=8"
+UNIT = "DoF*vec/s"
+# Nominal FP64 rate of GB300 (recipe table: 1.25 TFLOP/s) and the FP32 CUDA-core rate
+# 152 SMs x 128 lanes x 2 flop x 2.07 GHz.
+PEAK_FP64_NOMINAL = 1.25e12
+PEAK_FP32_NOMINAL = 152 * 128 * 2 * 2.07e9
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--workload", default="C4")
+    ap.add_argument("--cells", type=int, default=None,
+                    help="cells per direction (same recipe on a smaller grid, for profiling)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle sample")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- helpers
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def alg_flops(wl, n_pairs, n_v):
+    """Paper's operation count (eq. flopRealMF / flopComplexMF) with n_s read as the
+    number of (projector, cell) incidences, split into the fused local kernel's
+    share (cell terms + expansion F Delta T3) and the projection kernel's share."""
+    n_p = n_q = wl.p + 1
+    npo, nqo = n_p // 2, n_q // 2
+    s = n_p * n_p + n_p * n_q + n_q * n_q
+    if wl.complex:
+        per_cell = (2 * n_v * (npo * (n_q + 2) + nqo * (n_p + 2)) * s + 6 * n_v * nqo * n_q ** 2 * (2 * n_q + 5)
+                    + 2 * n_q ** 3 + 40 * n_v * n_q ** 3)
+        nl = n_v * (8 * n_p ** 3 + 3) * 9 * n_pairs
+    else:
+        per_cell = (2 * n_v * (npo * (n_q + 2) + nqo * (n_p + 2)) * s + 6 * n_v * nqo * n_q ** 2 * (2 * n_q + 5)
+                    + 2 * n_q ** 3 + 34 * n_v * n_q ** 3)
+        nl = n_v * (4 * n_p ** 3 + 1) * 9 * n_pairs
+    return per_cell * wl.n_cells + nl / 2.0, nl / 2.0
+
+
+def load_traffic(key):
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            return json.load(f).get(key)
+    except (OSError, ValueError):
+        return None
+
+
+def fill_trial(wl, n_v, X_dev, dtype_np):
+    """Copy the seeded trial block into a device tensor chunk by chunk."""
+    import torch
+    from synth import trial_chunk, TRIAL_CHUNK
+    nch = (wl.n_dofs + TRIAL_CHUNK - 1) // TRIAL_CHUNK
+    for c in range(nch):
+        blk = trial_chunk(wl, n_v, c)
+        r0 = c * TRIAL_CHUNK
+        X_dev[r0:r0 + blk.shape[0]].copy_(torch.from_numpy(blk.astype(dtype_np)))
+
+
+# ------------------------------------------------------------- native arm
+def run_native(args, wl, rank, world):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2512_08571_gb300 import fe_ks as fk
+    from paper_2512_08571_gb300.problem import HostProblem
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    t0 = time.time()
+    hp = HostProblem(wl)
+    ctx = fk.fe_ks_setup(hp.struct, fk.TERM_ALL, wl.n_v, stream.cuda_stream)
+    info = fk.fe_ks_info(ctx)
+    setup_s = time.time() - t0
+    cplx = hp.complex
+    m, n_v = hp.m, wl.n_v
+    units = m * n_v
+    local_flops, proj_flops = alg_flops(wl, info["n_pairs"], n_v)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def measure(precision, steps, warmup):
+        dt = {fk.FE_KS_F64: (torch.complex128 if cplx else torch.float64, np.float64),
+              fk.FE_KS_F32: (torch.complex64 if cplx else torch.float32, np.float32)}[precision]
+        X = torch.empty((m, n_v), dtype=dt[0], device=dev)
+        fill_trial(wl, n_v, X, np.complex128 if cplx else dt[1])
+        Y = torch.empty_like(X)
+        for _ in range(warmup):
+            fk.fe_ks_apply(ctx, X, Y, n_v, precision)
+        torch.cuda.synchronize()
+        fk.fe_ks_read_profile(ctx)
+        fk.fe_ks_set_profiling(ctx, True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(dev.index) as clk:
+            e0.record(stream)
+            for _ in range(steps):
+                fk.fe_ks_apply(ctx, X, Y, n_v, precision)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        barrier()
+        fk.fe_ks_set_profiling(ctx, False)
+        prof = fk.fe_ks_read_profile(ctx)
+        ms = e0.elapsed_time(e1) / steps
+        if world > 1:
+            t = torch.tensor([ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        local_ms, local_n = prof["local"]
+        achieved = local_flops * steps / (local_ms * 1e-3) if local_ms > 0 else None
+        out = dict(ms=ms, value=units * world / (ms * 1e-3), prof=prof, clocks=clk.summary(),
+                   achieved=achieved, local_launch_ms=local_ms / max(local_n, 1),
+                   launches=int(prof["proj"][1] + prof["local"][1]))
+        del X, Y
+        torch.cuda.empty_cache()
+        return out
+
+    f64 = measure(fk.FE_KS_F64, args.steps, args.warmup)
+    mixed = None
+    if not args.no_mixed:
+        mixed = measure(fk.FE_KS_F32, max(args.steps, 20), max(args.warmup, 3))
+
+    peak64_live = fk.fe_ks_measure_fma_peak(fk.FE_KS_F64) * 1e12
+    peak32_live = fk.fe_ks_measure_fma_peak(fk.FE_KS_F32) * 1e12
+
+    # end to end through the C ABI from pinned host memory: H2D(X), apply, D2H(Y)
+    e2e = None
+    if not args.no_e2e:
+        tdt = torch.complex128 if cplx else torch.float64
+        Xh = torch.empty((m, n_v), dtype=tdt, pin_memory=True)
+        fill_trial(wl, n_v, Xh, np.complex128 if cplx else np.float64)
+        Yh = torch.empty_like(Xh, pin_memory=True)
+        Xd = torch.empty((m, n_v), dtype=tdt, device=dev)
+        Yd = torch.empty_like(Xd)
+        ksteps = max(1, min(args.steps, 3))
+        for _ in range(1):
+            Xd.copy_(Xh, non_blocking=True)
+            fk.fe_ks_apply(ctx, Xd, Yd, n_v, fk.FE_KS_F64)
+            Yh.copy_(Yd, non_blocking=True)
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(ksteps):
+            Xd.copy_(Xh, non_blocking=True)
+            fk.fe_ks_apply(ctx, Xd, Yd, n_v, fk.FE_KS_F64)
+            Yh.copy_(Yd, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_e2e = e0.elapsed_time(e1) / ksteps
+        if world > 1:
+            t = torch.tensor([ms_e2e], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_e2e = float(t.item())
+        nbytes = Xh.numel() * Xh.element_size()
+        e2e = {"value": units * world / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "ms_per_step": ms_e2e}
+        del Xh, Yh, Xd, Yd
+    fk.fe_ks_destroy(ctx)
+    return dict(f64=f64, mixed=mixed, e2e=e2e, setup_s=setup_s, info=info, local_flops=local_flops,
+                peak64_live=peak64_live, peak32_live=peak32_live)
+
+
+# ----------------------------------------------------------- oracle timing
+_ORACLE = {}
+
+
+def oracle_sample(wl, budget_s, max_cells=None):
+    """Time the FP64 oracle (cell-matrix method: per-cell H^(e) by quadrature, then
+    H^(e) X^(e)) on host cores over a sample of cells until the budget is spent.
+    Returns (DoF*vec/s, cells done, seconds)."""
+    import numpy as np
+    from oracle.operator import Problem
+    from synth import trial_vectors
+    if wl.name not in _ORACLE:
+        _ORACLE[wl.name] = Problem(wl, with_atoms=False)
+    P = _ORACLE[wl.name]
+    rng = np.random.default_rng(12345)
+    order = rng.permutation(P.E)
+    done, t0 = 0, time.perf_counter()
+    for e in order:
+        Xe = trial_vectors(wl, rows=P.dofs[e])
+        Ye = P.cell_matrix(e) @ Xe
+        assert Ye.shape == Xe.shape
+        done += 1
+        if time.perf_counter() - t0 > budget_s or (max_cells and done >= max_cells):
+            break
+    el = time.perf_counter() - t0
+    units = done / P.E * wl.n_dofs * wl.n_v
+    return units / el, done, el
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+# ------------------------------------------------------------------- main
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    from synth import CONFIGS
+    wl = CONFIGS[args.workload]
+    if args.cells:
+        wl = wl.scaled(n=args.cells)
+    config = {"workload": f"{wl.name}: L={wl.L:g} bohr, {wl.n}^3 cells, p={wl.p}, n_q={wl.nq}, "
+                          f"N_v={wl.n_v}, {'complex' if wl.complex else 'real'}, GGA={wl.gga}, "
+                          f"atoms={wl.n_atoms}",
+              "n_dofs": wl.n_dofs, "n_v": wl.n_v, "degree": wl.p, "n_q": wl.nq,
+              "l2": "inputs larger than L2 (X = %.1f GB), no flush" % (wl.n_dofs * wl.n_v * 8 / 1e9),
+              "parallelism": f"replicas x{args.gpus}"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        for _ in range(args.warmup):
+            oracle_sample(wl, 1e9, max_cells=2)
+        vals, secs = [], []
+        for _ in range(args.steps):
+            v, n, el = oracle_sample(wl, 1e9, max_cells=4)
+            vals.append(v)
+            secs.append(el)
+        value = len(vals) / sum(1.0 / v for v in vals)
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": config,
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                                 "sample": f"4 cells of {wl.n_cells} per step (cell-matrix method, local "
+                                           f"terms, all {wl.n_v} vectors), scaled to the whole operator"},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    res = run_native(args, wl, rank, world)
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    f64 = res["f64"]
+    traffic = load_traffic(f"fe_local_kernel f64 {wl.name}")
+    achieved = f64["achieved"]
+    roofline = {"bound": "alu", "achieved": achieved / 1e12 if achieved else None,
+                "peak": PEAK_FP64_NOMINAL / 1e12, "unit": "TFLOP/s",
+                "frac": (achieved / PEAK_FP64_NOMINAL) if achieved else None, "traffic": traffic,
+                "kernel": "fe_local_kernel (FP64 DFMA pipe)",
+                "peak_source": "nominal FP64 1.25 TFLOP/s; live DFMA probe %.3f TFLOP/s" % (res["peak64_live"] / 1e12),
+                "frac_of_live_probe": (achieved / res["peak64_live"]) if achieved else None,
+                "avg_launch_ms": f64["local_launch_ms"]}
+    line = {"metric": METRIC, "value": f64["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": f64["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded mesh, fields, atoms, X)",
+            "config": config, "roofline": roofline, "clocks": f64["clocks"],
+            "gpu_launches": f64["launches"], "setup_s": res["setup_s"]}
+    mixed = res["mixed"]
+    if mixed:
+        ach = mixed["achieved"]
+        line["mixed"] = {"dtype": "f32", "value": mixed["value"], "unit": UNIT, "ms_per_step": mixed["ms"],
+                         "speedup_vs_f64": f64["ms"] / mixed["ms"],
+                         "roofline": {"bound": "alu", "achieved": ach / 1e12 if ach else None,
+                                      "peak": PEAK_FP32_NOMINAL / 1e12, "unit": "TFLOP/s",
+                                      "frac": ach / PEAK_FP32_NOMINAL if ach else None,
+                                      "live_probe": res["peak32_live"] / 1e12,
+                                      "avg_launch_ms": mixed["local_launch_ms"]},
+                         "clocks": mixed["clocks"], "gpu_launches": mixed["launches"]}
+    if res["e2e"]:
+        line["e2e"] = res["e2e"]
+    if world == 1 and not args.no_cpu_baseline:
+        v, n, el = oracle_sample(wl, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                                "sample": f"{n} of {wl.n_cells} cells in {el:.1f} s (cell-matrix method: "
+                                          f"H^(e) by quadrature then H^(e) X^(e), local terms, all "
+                                          f"{wl.n_v} vectors), scaled to the whole operator"}
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -159,6 +159,26 @@ const double* fe_ks_dinv_sqrt(const fe_ks_ctx* ctx);
 fe_ks_status fe_ks_info(const fe_ks_ctx* ctx, int64_t* n_dofs, int64_t* n_cells, int32_t* degree,
                         int32_t* is_complex, int32_t* n_colours, int64_t* n_pairs);
 
+/*
+ * Per-phase timing of later applications (CUDA events on the context's
+ * stream, recorded around the zero-fill, the projection kernel and the fused
+ * local kernels).  fe_ks_set_profiling(ctx, 1) starts recording (events are
+ * created lazily, no device memory is allocated), 0 stops.
+ * fe_ks_read_profile synchronises the recorded events and returns, for
+ * phases 0 = zero-fill, 1 = nonlocal projection, 2 = fused local kernel, the
+ * total milliseconds ms[3] and the number of kernel launches launches[3] since
+ * the last read, then clears them.
+ */
+fe_ks_status fe_ks_set_profiling(fe_ks_ctx* ctx, int on);
+fe_ks_status fe_ks_read_profile(fe_ks_ctx* ctx, double ms[3], int64_t launches[3]);
+
+/*
+ * Diagnostic: FP64 (precision = FE_KS_F64) or FP32 FMA throughput of the
+ * current device in TFLOP/s (2 flops per FMA), from a bounded register-only
+ * FMA loop on 4 CTAs per SM.  Allocates and frees a small device buffer.
+ */
+fe_ks_status fe_ks_measure_fma_peak(int precision, double* tflops);
+
 /* Change the stream used by later calls. */
 fe_ks_status fe_ks_set_stream(fe_ks_ctx* ctx, void* cuda_stream);
 

@@ -196,10 +196,14 @@ class Problem:
         return Y
 
     def apply_rows(self, X, rows):
-        """Rows Y[rows, :] of Y = H X, computed only from the cells touching them."""
-        X = np.asarray(X)
+        """Rows Y[rows, :] of Y = H X, computed only from the cells touching them.
+
+        X may be any object with ``shape``, ``dtype`` and row indexing ``X[idx]``.
+        """
+        if not hasattr(X, "dtype"):
+            X = np.asarray(X)
         rows = np.asarray(rows)
-        dt = np.complex128 if (self.complex or np.iscomplexobj(X)) else np.float64
+        dt = np.complex128 if (self.complex or np.issubdtype(X.dtype, np.complexfloating)) else np.float64
         out = np.zeros((rows.size, X.shape[1]), dtype=dt)
         pos = {int(r): i for i, r in enumerate(rows)}
         hit = np.isin(self.dofs, rows)

@@ -460,7 +460,39 @@ fe_ks_status fe_ks_setup(const fe_ks_problem* prob, int terms_mask, int64_t n_v_
 void fe_ks_destroy(fe_ks_ctx* ctx) {
   if (!ctx) return;
   for (void* p : ctx->c.allocations) cudaFree(p);
+  for (cudaEvent_t e : ctx->c.ev_pool) cudaEventDestroy(e);
+  for (auto& r : ctx->c.ev_rec)
+    for (cudaEvent_t e : r) cudaEventDestroy(e);
   delete ctx;
+}
+
+fe_ks_status fe_ks_set_profiling(fe_ks_ctx* ctx, int on) {
+  if (!ctx) return fail(FE_KS_ERR_ARG, "ctx is NULL");
+  ctx->c.profiling = on != 0;
+  return FE_KS_OK;
+}
+
+fe_ks_status fe_ks_read_profile(fe_ks_ctx* ctx, double ms[3], int64_t launches[3]) {
+  if (!ctx || !ms || !launches) return fail(FE_KS_ERR_ARG, "NULL argument");
+  Ctx& c = ctx->c;
+  for (int i = 0; i < 3; ++i) {
+    ms[i] = 0.0;
+    launches[i] = 0;
+  }
+  for (size_t r = 0; r < c.ev_rec.size(); ++r) {
+    auto& ev = c.ev_rec[r];
+    if (cudaEventSynchronize(ev[3]) != cudaSuccess) return fail(FE_KS_ERR_CUDA, "event synchronize failed");
+    for (int i = 0; i < 3; ++i) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
+      ms[i] += t;
+      launches[i] += c.ev_launches[r][i];
+    }
+    for (cudaEvent_t e : ev) c.ev_pool.push_back(e);
+  }
+  c.ev_rec.clear();
+  c.ev_launches.clear();
+  return FE_KS_OK;
 }
 
 fe_ks_status fe_ks_set_stream(fe_ks_ctx* ctx, void* cuda_stream) {
@@ -507,7 +539,22 @@ static fe_ks_status apply_impl(fe_ks_ctx* ctx, const void* Xv, void* Yv, int64_t
   OpData<T>& od = *reinterpret_cast<OpData<T>*>(sizeof(T) == 8 ? (void*)&c.f64 : (void*)&c.f32);
   const T* hcoef = reinterpret_cast<const T*>(sizeof(T) == 8 ? (const void*)c.h64 : (const void*)c.h32);
   cudaStream_t s = c.stream;
+  std::array<cudaEvent_t, 4> ev{};
+  std::array<int, 3> nlaunch{1, 0, 0};
+  auto mark = [&](int i) {
+    if (!c.profiling) return;
+    if (c.ev_pool.empty()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      c.ev_pool.push_back(e);
+    }
+    ev[i] = c.ev_pool.back();
+    c.ev_pool.pop_back();
+    cudaEventRecord(ev[i], s);
+  };
+  mark(0);
   if (cudaMemsetAsync(Y, 0, bytes, s) != cudaSuccess) return fail(FE_KS_ERR_CUDA, "cudaMemsetAsync failed");
+  mark(1);
   const bool nl = (c.terms & FE_KS_TERM_NL) && c.n_pairs > 0;
   if (nl) {
     ProjParams<T> pp{};
@@ -525,7 +572,9 @@ static fe_ks_status apply_impl(fe_ks_ctx* ctx, const void* Xv, void* Yv, int64_t
     pp.np3 = c.np3;
     cudaError_t err = launch_proj<T>(c, pp, c.n_atoms, s);
     if (err != cudaSuccess) return fail(FE_KS_ERR_CUDA, std::string("projection kernel: ") + cudaGetErrorString(err));
+    nlaunch[1] = 1;
   }
+  mark(2);
   LocalParams<T> lp{};
   lp.X = X;
   lp.Y = Y;
@@ -548,6 +597,12 @@ static fe_ks_status apply_impl(fe_ks_ctx* ctx, const void* Xv, void* Yv, int64_t
     lp.n_cells = c.colour_ptr[col + 1] - c.colour_ptr[col];
     cudaError_t err = launch_local<T>(c, lp, s);
     if (err != cudaSuccess) return fail(FE_KS_ERR_CUDA, std::string("local kernel: ") + cudaGetErrorString(err));
+    if (lp.n_cells > 0) nlaunch[2]++;
+  }
+  mark(3);
+  if (c.profiling) {
+    c.ev_rec.push_back(ev);
+    c.ev_launches.push_back(nlaunch);
   }
   return FE_KS_OK;
 }

@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <array>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -114,6 +115,11 @@ struct Ctx {
   OpData<double> f64;
   OpData<float> f32;
   std::vector<void*> allocations;
+  // profiling: events recorded per application (start, after fill, after projection, after local)
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::array<cudaEvent_t, 4>> ev_rec;
+  std::vector<std::array<int, 3>> ev_launches;
 };
 
 // error reporting (thread-local message)

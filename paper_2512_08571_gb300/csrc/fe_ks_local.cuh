@@ -84,6 +84,10 @@ fe_local_kernel(const __grid_constant__ LocalParams<T> p) {
   const int col = blockIdx.x * VT + v;
   const bool act = col < p.ncols;
   const EOTables<T>& tb = p.tab;
+  // this thread's column inside the [point][VT] tiles
+  T* Av = A + v;
+  T* Bv = B + v;
+  T* Cv = C + v;
 
   for (int ci = blockIdx.y; ci < p.n_cells; ci += gridDim.y) {
     const int e = p.cells[ci];
@@ -104,7 +108,7 @@ fe_local_kernel(const __grid_constant__ LocalParams<T> p) {
       }
       eo_apply<NP, NQ, 1>(x, t, tb.N);
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) A[i * SX + j * SY + q * SZ] = t[q];
+      for (int q = 0; q < NQ; ++q) Av[i * SX + j * SY + q * SZ] = t[q];
     }
     __syncthreads();
     // (2) N^1D along y
@@ -112,10 +116,10 @@ fe_local_kernel(const __grid_constant__ LocalParams<T> p) {
       const int i = ln % NP, qz = ln / NP;
       T x[NP], t[NQ];
 #pragma unroll
-      for (int j = 0; j < NP; ++j) x[j] = A[i * SX + j * SY + qz * SZ];
+      for (int j = 0; j < NP; ++j) x[j] = Av[i * SX + j * SY + qz * SZ];
       eo_apply<NP, NQ, 1>(x, t, tb.N);
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) A[i * SX + q * SY + qz * SZ] = t[q];
+      for (int q = 0; q < NQ; ++q) Av[i * SX + q * SY + qz * SZ] = t[q];
     }
     __syncthreads();
     // (3) N^1D along x  ->  A = Y~0 (values at quadrature points)
@@ -123,10 +127,10 @@ fe_local_kernel(const __grid_constant__ LocalParams<T> p) {
       const int qy = ln % NQ, qz = ln / NQ;
       T x[NP], t[NQ];
 #pragma unroll
-      for (int i = 0; i < NP; ++i) x[i] = A[i * SX + qy * SY + qz * SZ];
+      for (int i = 0; i < NP; ++i) x[i] = Av[i * SX + qy * SY + qz * SZ];
       eo_apply<NP, NQ, 1>(x, t, tb.N);
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) A[q * SX + qy * SY + qz * SZ] = t[q];
+      for (int q = 0; q < NQ; ++q) Av[q * SX + qy * SY + qz * SZ] = t[q];
     }
     __syncthreads();
     // (4) Y~1: D~ along x (A -> B) and along y (A -> C)
@@ -134,15 +138,15 @@ fe_local_kernel(const __grid_constant__ LocalParams<T> p) {
       const int a0 = ln % NQ, qz = ln / NQ;
       T x[NQ], t[NQ];
 #pragma unroll
-      for (int r = 0; r < NQ; ++r) x[r] = A[r * SX + a0 * SY + qz * SZ];
+      for (int r = 0; r < NQ; ++r) x[r] = Av[r * SX + a0 * SY + qz * SZ];
       eo_apply<NQ, NQ, -1>(x, t, tb.D);
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) B[q * SX + a0 * SY + qz * SZ] = t[q];
+      for (int q = 0; q < NQ; ++q) Bv[q * SX + a0 * SY + qz * SZ] = t[q];
 #pragma unroll
-      for (int r = 0; r < NQ; ++r) x[r] = A[a0 * SX + r * SY + qz * SZ];
+      for (int r = 0; r < NQ; ++r) x[r] = Av[a0 * SX + r * SY + qz * SZ];
       eo_apply<NQ, NQ, -1>(x, t, tb.D);
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) C[a0 * SX + q * SY + qz * SZ] = t[q];
+      for (int q = 0; q < NQ; ++q) Cv[a0 * SX + q * SY + qz * SZ] = t[q];
     }
     __syncthreads();
     // (5) D~ along z in registers, then the quadrature-point step of
@@ -154,14 +158,14 @@ fe_local_kernel(const __grid_constant__ LocalParams<T> p) {
       const int qx = ln % NQ, qy = ln / NQ;
       T u[NQ], g[NQ];
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) u[q] = A[qx * SX + qy * SY + q * SZ];
+      for (int q = 0; q < NQ; ++q) u[q] = Av[qx * SX + qy * SY + q * SZ];
       eo_apply<NQ, NQ, -1>(u, g, tb.D);
       const T* cf = p.coef + (int64_t)e * p.ncoef * NQ3 + qx + NQ * qy;
 #pragma unroll
       for (int qz = 0; qz < NQ; ++qz) {
         const int o = qz * NQ * NQ;
         const int s = qx * SX + qy * SY + qz * SZ;
-        const T gx = B[s], gy = C[s], gz = g[qz], uu = u[qz];
+        const T gx = Bv[s], gy = Cv[s], gz = g[qz], uu = u[qz];
         const T G00 = cf[0 * NQ3 + o], G01 = cf[1 * NQ3 + o], G02 = cf[2 * NQ3 + o];
         const T G11 = cf[3 * NQ3 + o], G12 = cf[4 * NQ3 + o], G22 = cf[5 * NQ3 + o];
         const T VL = cf[6 * NQ3 + o];
@@ -183,8 +187,8 @@ fe_local_kernel(const __grid_constant__ LocalParams<T> p) {
           // -i (a + i b) = b - i a : real column adds Im, imaginary column subtracts Re
           z += (v & 1) ? -kp : kp;
         }
-        B[s] = w0;
-        C[s] = w1;
+        Bv[s] = w0;
+        Cv[s] = w1;
         u[qz] = w2;
         zc[qz] = z;
       }
@@ -199,15 +203,15 @@ fe_local_kernel(const __grid_constant__ LocalParams<T> p) {
       const int a0 = ln % NQ, qz = ln / NQ;
       T x[NQ], t[NQ];
 #pragma unroll
-      for (int r = 0; r < NQ; ++r) x[r] = B[r * SX + a0 * SY + qz * SZ];
+      for (int r = 0; r < NQ; ++r) x[r] = Bv[r * SX + a0 * SY + qz * SZ];
       eo_apply<NQ, NQ, -1>(x, t, tb.Dt);
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) B[q * SX + a0 * SY + qz * SZ] = t[q];
+      for (int q = 0; q < NQ; ++q) Bv[q * SX + a0 * SY + qz * SZ] = t[q];
 #pragma unroll
-      for (int r = 0; r < NQ; ++r) x[r] = C[a0 * SX + r * SY + qz * SZ];
+      for (int r = 0; r < NQ; ++r) x[r] = Cv[a0 * SX + r * SY + qz * SZ];
       eo_apply<NQ, NQ, -1>(x, t, tb.Dt);
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) C[a0 * SX + q * SY + qz * SZ] = t[q];
+      for (int q = 0; q < NQ; ++q) Cv[a0 * SX + q * SY + qz * SZ] = t[q];
     }
     __syncthreads();
     // (7) Z += D~x^T W_x + D~y^T W_y, then N^T along z -> A
@@ -216,12 +220,12 @@ fe_local_kernel(const __grid_constant__ LocalParams<T> p) {
 #pragma unroll
       for (int q = 0; q < NQ; ++q) {
         const int s = qx * SX + qy * SY + q * SZ;
-        zc[q] += B[s] + C[s];
+        zc[q] += Bv[s] + Cv[s];
       }
       T t[NP];
       eo_apply<NQ, NP, 1>(zc, t, tb.Nt);
 #pragma unroll
-      for (int k = 0; k < NP; ++k) A[qx * SX + qy * SY + k * SZ] = t[k];
+      for (int k = 0; k < NP; ++k) Av[qx * SX + qy * SY + k * SZ] = t[k];
     }
     __syncthreads();
     // (8) N^T along y
@@ -229,10 +233,10 @@ fe_local_kernel(const __grid_constant__ LocalParams<T> p) {
       const int qx = ln % NQ, k = ln / NQ;
       T x[NQ], t[NP];
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) x[q] = A[qx * SX + q * SY + k * SZ];
+      for (int q = 0; q < NQ; ++q) x[q] = Av[qx * SX + q * SY + k * SZ];
       eo_apply<NQ, NP, 1>(x, t, tb.Nt);
 #pragma unroll
-      for (int j = 0; j < NP; ++j) A[qx * SX + j * SY + k * SZ] = t[j];
+      for (int j = 0; j < NP; ++j) Av[qx * SX + j * SY + k * SZ] = t[j];
     }
     __syncthreads();
     // (9) N^T along x, + sum_a F Delta P (nonlocal), assembly Y += Q^T T0
@@ -240,7 +244,7 @@ fe_local_kernel(const __grid_constant__ LocalParams<T> p) {
       const int j = ln % NP, k = ln / NP;
       T x[NQ], y[NP];
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) x[q] = A[q * SX + j * SY + k * SZ];
+      for (int q = 0; q < NQ; ++q) x[q] = Av[q * SX + j * SY + k * SZ];
       eo_apply<NQ, NP, 1>(x, y, tb.Nt);
       if (act) {
         if (p.cell_pair_ptr) {

@@ -19,8 +19,7 @@ STATUS_NAMES = {0: "FE_KS_OK", -1: "FE_KS_ERR_ARG", -2: "FE_KS_ERR_MESH", -3: "F
 FE_KS_F64, FE_KS_F32 = 0, 1
 TERM_T, TERM_L, TERM_G, TERM_K, TERM_NL, TERM_ALL = 1, 2, 4, 8, 16, 31
 
-EXPORTED = ("fe_ks_quadrature_points", "fe_ks_setup", "fe_ks_apply", "fe_ks_apply_scaled",
-            "fe_ks_dinv_sqrt", "fe_ks_info", "fe_ks_set_stream", "fe_ks_last_error", "fe_ks_destroy")
+
 
 
 class FeKsError(RuntimeError):
@@ -57,10 +56,14 @@ def _load():
     lib.fe_ks_info.argtypes = [vp, P(i64), P(i64), P(i32), P(i32), P(i32), P(i64)]
     lib.fe_ks_set_stream.argtypes = [vp, vp]
     lib.fe_ks_last_error.restype = ctypes.c_char_p
+    lib.fe_ks_set_profiling.argtypes = [vp, ctypes.c_int]
+    lib.fe_ks_read_profile.argtypes = [vp, P(ctypes.c_double), P(i64)]
+    lib.fe_ks_measure_fma_peak.argtypes = [ctypes.c_int, P(ctypes.c_double)]
     lib.fe_ks_destroy.argtypes = [vp]
     lib.fe_ks_destroy.restype = None
     for name in ("fe_ks_quadrature_points", "fe_ks_setup", "fe_ks_apply", "fe_ks_apply_scaled",
-                 "fe_ks_info", "fe_ks_set_stream"):
+                 "fe_ks_info", "fe_ks_set_stream", "fe_ks_set_profiling", "fe_ks_read_profile",
+                 "fe_ks_measure_fma_peak"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -117,6 +120,24 @@ def fe_ks_info(ctx):
                            ctypes.byref(ncol), ctypes.byref(npairs)))
     return dict(n_dofs=m.value, n_cells=E.value, degree=p.value, complex=bool(cplx.value),
                 n_colours=ncol.value, n_pairs=npairs.value)
+
+
+def fe_ks_set_profiling(ctx, on):
+    _check(_lib.fe_ks_set_profiling(ctx, int(bool(on))))
+
+
+def fe_ks_read_profile(ctx):
+    """{phase: (ms, launches)} for phases 'fill', 'proj', 'local' since the last read."""
+    ms = (ctypes.c_double * 3)()
+    n = (ctypes.c_int64 * 3)()
+    _check(_lib.fe_ks_read_profile(ctx, ms, n))
+    return {k: (ms[i], n[i]) for i, k in enumerate(("fill", "proj", "local"))}
+
+
+def fe_ks_measure_fma_peak(precision):
+    out = ctypes.c_double()
+    _check(_lib.fe_ks_measure_fma_peak(precision, ctypes.byref(out)))
+    return out.value
 
 
 def fe_ks_set_stream(ctx, stream):

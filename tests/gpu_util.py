@@ -43,3 +43,47 @@ def gpu_apply(hp, X, precision, scaled=False, terms=fk.TERM_ALL, repeat=1):
         return outs if repeat > 1 else outs[0]
     finally:
         fk.fe_ks_destroy(ctx)
+
+
+class RowCache:
+    """Rows of the seeded trial block X, generated once for a known row set.
+
+    Supports ``X[idx]`` for global row indices inside the set, so the oracle's
+    sampled-row evaluation can run at full size without materialising X.
+    """
+
+    def __init__(self, wl, rows, n_v=None, round_to=None):
+        from synth import trial_vectors
+        self.rows = np.unique(np.asarray(rows))
+        vals = trial_vectors(wl, n_v=n_v, rows=self.rows)
+        if round_to is not None:
+            vals = vals.astype(round_to).astype(vals.dtype)
+        self.vals = vals
+        self.dtype = vals.dtype
+        self.shape = (wl.n_dofs, vals.shape[1])
+
+    def __getitem__(self, idx):
+        pos = np.searchsorted(self.rows, np.asarray(idx))
+        return self.vals[pos]
+
+
+def needed_rows(P, rows):
+    """Global rows the oracle reads to evaluate Y[rows] (touched cells and atom supports)."""
+    rows = np.asarray(rows)
+    hit = np.isin(P.dofs, rows).any(axis=1)
+    cells = set(np.nonzero(hit)[0].tolist())
+    for a in range(P.R.shape[0]):
+        ac = P.atom_cells(a)
+        if np.any(hit[ac]):
+            cells |= set(ac.tolist())
+    return np.unique(P.dofs[sorted(cells)])
+
+
+def fill_device(wl, n_v, X_dev, dtype_np):
+    """Copy the seeded trial block into a device tensor chunk by chunk."""
+    import torch
+    from synth import trial_chunk, TRIAL_CHUNK
+    for c in range((wl.n_dofs + TRIAL_CHUNK - 1) // TRIAL_CHUNK):
+        blk = trial_chunk(wl, n_v, c)
+        r0 = c * TRIAL_CHUNK
+        X_dev[r0:r0 + blk.shape[0]].copy_(torch.from_numpy(blk.astype(dtype_np)))

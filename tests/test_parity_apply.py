@@ -44,7 +44,8 @@ def test_apply_matches_oracle(cases, key, precision):
     Xin = round_input(X, precision)
     Y = gpu_apply(hp, Xin, precision)
     Yref = P.apply(Xin)
-    assert rel_err_cols(Y, Yref) <= TOL[precision]
+    err = rel_err_cols(Y, Yref)
+    assert err <= TOL[precision], err
 
 
 @pytest.mark.parametrize("precision", PREC)
@@ -54,7 +55,8 @@ def test_apply_scaled_matches_oracle(cases, precision):
     s = 1.0 / np.sqrt(P.lumped_mass())
     Y = gpu_apply(hp, Xin, precision, scaled=True)
     Yref = s[:, None] * P.apply(s[:, None] * Xin)
-    assert rel_err_cols(Y, Yref) <= TOL[precision]
+    err = rel_err_cols(Y, Yref)
+    assert err <= TOL[precision], err
 
 
 @pytest.mark.parametrize("p", range(1, 9))
@@ -64,7 +66,8 @@ def test_every_degree_kinetic_and_local(p):
     P = Problem(wl)
     X = trial_vectors(wl)
     Y = gpu_apply(hp, X, fk.FE_KS_F64)
-    assert rel_err_cols(Y, P.apply(X)) <= 1e-12
+    err = rel_err_cols(Y, P.apply(X))
+    assert err <= 1e-12, err
 
 
 def test_term_subsets(cases):

@@ -26,8 +26,8 @@
  *    i.e. [m][n_v] complex = [m][2 n_v] reals.  Pointers must be 16-byte
  *    aligned device pointers unless stated otherwise.
  *  - Calls are asynchronous on the context's CUDA stream.  Argument errors are
- *    reported synchronously; device-side errors (watchdog timeouts) are
- *    reported by the next call that synchronises, or by fe_ks_check_status.
+ *    reported synchronously; errors of kernels already in flight surface at
+ *    the caller's next synchronisation, as for any CUDA launch.
  *  - No call after fe_ks_setup allocates device memory except where stated.
  *  - On error the call returns a negative fe_ks_status and fe_ks_last_error()
  *    returns a message (thread-local).  No C++ exception crosses the ABI.
@@ -151,6 +151,33 @@ fe_ks_status fe_ks_apply(fe_ks_ctx* ctx, const void* X, void* Y, int64_t n_v, in
  */
 fe_ks_status fe_ks_apply_scaled(fe_ks_ctx* ctx, const void* X, void* Y, int64_t n_v,
                                 int precision);
+
+/*
+ * Residual-based Chebyshev filter (R-ChFSI, Algorithm 4) of degree `degree`
+ * on the standard form Hs = D^{-1/2} H D^{-1/2}: D is the GLL-lumped mass
+ * (Algorithm 4's diagonal approximation of M), so in scaled variables M and
+ * D become the identity and the filter reads
+ *   Y = Hs X - X Lam ;  R_Y = (s1/e) Y ;  R_X = 0 ;
+ *   R_X <- (2 s2/e) [(Hs - c) R_Y + Y Lam_Y] - s s2 R_X   (k = 2..degree)
+ *   X  <- R_Y + X Lam_Y
+ * with e = (lam_max - lam_T)/2, c = (lam_max + lam_T)/2 and the scalar
+ * recurrence of Algorithm 4.  The residual Y and the final combination are
+ * FP64; the degree - 1 applications inside the recurrence run in `precision`
+ * (FE_KS_F64 or FE_KS_F32), which is where the paper's R-ChFSI tolerates
+ * inexact products.
+ *  X     : device FP64 [m][n_v] (complex: interleaved), overwritten by the
+ *          filtered block.
+ *  ritz  : device FP64 [n_v] current Ritz values Lam (real).
+ *  bounds: lam_min < lam_T < lam_max (spectrum lower bound, upper end of the
+ *          wanted part, spectrum upper bound).
+ *  work  : device workspace of at least fe_ks_cheb_filter_workspace bytes,
+ *          256-byte aligned; owned by the caller, not retained.
+ * Stream-ordered, allocates nothing, so it can be captured in a CUDA graph.
+ */
+fe_ks_status fe_ks_cheb_filter_workspace(const fe_ks_ctx* ctx, int64_t n_v, int precision, size_t* bytes);
+fe_ks_status fe_ks_cheb_filter(fe_ks_ctx* ctx, double* X, const double* ritz, int64_t n_v, int degree,
+                               double lam_min, double lam_T, double lam_max, int precision, void* work,
+                               size_t work_bytes);
 
 /* Length-m device copy of D^{-1/2} in FP64 (owned by the context). */
 const double* fe_ks_dinv_sqrt(const fe_ks_ctx* ctx);

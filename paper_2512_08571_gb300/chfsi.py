@@ -1,0 +1,102 @@
+"""R-ChFSI eigensolver driver on the GPU (Algorithm 3 around Algorithm 4).
+
+The caller's side of ``fe_ks_cheb_filter``: the outer subspace iteration of
+Algorithm 3 in the standard form Hs = D^{-1/2} H D^{-1/2} (D the GLL-lumped
+mass).  Each iteration filters the block with the library's residual-based
+Chebyshev filter and then performs the Rayleigh-Ritz step in FP64
+(orthonormalisation and the projected N_v x N_v eigenproblem as dense library
+GEMM / QR / symmetric eigensolver calls on the device).  Spectral bounds: the
+upper bound from k Lanczos steps (theta_max + |beta_k|, the standard safe
+bound), the lower bound and the wanted-spectrum edge from the current Ritz
+values.
+"""
+import torch
+
+from . import fe_ks as fk
+
+
+class RChFSI:
+    def __init__(self, ctx, m, n_v, cplx, degree=20, precision=fk.FE_KS_F32, lanczos_steps=10):
+        self.ctx, self.m, self.n_v, self.cplx = ctx, m, n_v, cplx
+        self.degree, self.precision, self.lanczos_steps = degree, precision, lanczos_steps
+        self.dt = torch.complex128 if cplx else torch.float64
+        self.dev = torch.device("cuda", torch.cuda.current_device())
+        nb = fk.fe_ks_cheb_filter_workspace(ctx, n_v, precision)
+        self.work = torch.empty(nb + 256, dtype=torch.uint8, device=self.dev)
+        off = (-self.work.data_ptr()) % 256
+        self.work_view = self.work[off:off + nb]
+        self.work_bytes = nb
+        self.tmp = torch.empty((m, n_v), dtype=self.dt, device=self.dev)
+        self.lmax = None
+
+    def apply_scaled(self, V, out=None):
+        out = torch.empty_like(V) if out is None else out
+        fk.fe_ks_apply_scaled(self.ctx, V, out, V.shape[1], fk.FE_KS_F64)
+        return out
+
+    def lanczos_upper_bound(self, seed=0):
+        g = torch.Generator(device=self.dev)
+        g.manual_seed(seed)
+        v = torch.randn((self.m, 1), generator=g, device=self.dev, dtype=torch.float64).to(self.dt)
+        v /= torch.linalg.vector_norm(v)
+        v_prev = torch.zeros_like(v)
+        w = torch.empty_like(v)
+        alphas, betas, beta = [], [], 0.0
+        for _ in range(self.lanczos_steps):
+            self.apply_scaled(v, w)
+            alpha = torch.real(torch.vdot(v[:, 0], w[:, 0])).item()
+            w = w - alpha * v - beta * v_prev
+            beta = torch.linalg.vector_norm(w).item()
+            alphas.append(alpha)
+            betas.append(beta)
+            if beta == 0.0:
+                break
+            v_prev, v = v, w / beta
+            w = torch.empty_like(v)
+        k = len(alphas)
+        T = torch.zeros((k, k), dtype=torch.float64)
+        for i in range(k):
+            T[i, i] = alphas[i]
+            if i + 1 < k:
+                T[i, i + 1] = T[i + 1, i] = betas[i]
+        self.lmax = float(torch.linalg.eigvalsh(T).max().item() + abs(betas[-1]))
+        return self.lmax
+
+    def rayleigh_ritz(self, Y):
+        """Orthonormalise Y (QR) and solve the projected problem: returns (lam, X)."""
+        Q, _ = torch.linalg.qr(Y)
+        HQ = self.apply_scaled(Q, self.tmp)
+        A = Q.conj().T @ HQ
+        A = 0.5 * (A + A.conj().T)
+        lam, W = torch.linalg.eigh(A)
+        return lam.to(torch.float64).contiguous(), (Q @ W).contiguous()
+
+    def residual_norms(self, X, lam):
+        R = self.apply_scaled(X, self.tmp) - X * lam[None, :].to(X.dtype)
+        return torch.linalg.vector_norm(R, dim=0)
+
+    def filter(self, X, lam):
+        lmin, lT = float(lam[0].item()), float(lam[-1].item())
+        if not lmin < lT < self.lmax:
+            raise RuntimeError("spectral bounds out of order")
+        fk.fe_ks_cheb_filter(self.ctx, X, lam, self.n_v, self.degree, lmin, lT, self.lmax, self.precision,
+                             self.work_view, self.work_bytes)
+        return X
+
+    def run(self, X0, n_iter, tol=None, n_check=None):
+        """Algorithm 3: Rayleigh-Ritz on X0, then (filter, Rayleigh-Ritz) n_iter times."""
+        if self.lmax is None:
+            self.lanczos_upper_bound()
+        lam, X = self.rayleigh_ritz(X0)
+        res = None
+        n_check = self.n_v if n_check is None else n_check
+        for it in range(n_iter):
+            X = self.filter(X, lam)
+            lam, X = self.rayleigh_ritz(X)
+            if tol is not None:
+                res = self.residual_norms(X, lam)
+                if float(res[:n_check].max()) < tol:
+                    return lam, X, res, it + 1
+        if res is None:
+            res = self.residual_norms(X, lam)
+        return lam, X, res, n_iter

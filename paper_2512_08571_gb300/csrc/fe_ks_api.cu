@@ -125,10 +125,6 @@ static fe_ks_status check_geometry_args(const fe_ks_problem* prob) {
 
 using namespace feks;
 
-struct fe_ks_ctx {
-  Ctx c;
-};
-
 extern "C" {
 
 const char* fe_ks_last_error(void) { return g_last_error.c_str(); }
@@ -521,26 +517,13 @@ fe_ks_status fe_ks_info(const fe_ks_ctx* ctx, int64_t* n_dofs, int64_t* n_cells,
 namespace feks {
 
 template <typename T>
-static fe_ks_status apply_impl(fe_ks_ctx* ctx, const void* Xv, void* Yv, int64_t n_v, bool scaled) {
-  g_last_error.clear();
-  if (!ctx) return fail(FE_KS_ERR_ARG, "ctx is NULL");
-  Ctx& c = ctx->c;
-  if (!Xv || !Yv) return fail(FE_KS_ERR_ARG, "X or Y is NULL");
-  if (n_v < 1 || n_v > c.n_v_max) return fail(FE_KS_ERR_ARG, "n_v must be in 1..n_v_max");
-  if (((uintptr_t)Xv % sizeof(T)) || ((uintptr_t)Yv % sizeof(T)))
-    return fail(FE_KS_ERR_ARG, "X and Y must be aligned to the scalar size");
-  const int64_t ncols = n_v * (c.cplx ? 2 : 1);
-  const size_t bytes = (size_t)c.m * ncols * sizeof(T);
-  const char* xb = static_cast<const char*>(Xv);
-  const char* yb = static_cast<const char*>(Yv);
-  if (xb < yb + bytes && yb < xb + bytes) return fail(FE_KS_ERR_ARG, "X and Y overlap");
-  const T* X = static_cast<const T*>(Xv);
-  T* Y = static_cast<T*>(Yv);
+fe_ks_status apply_core(Ctx& c, const T* X, T* Y, int64_t ncols, bool scaled, T alpha, bool zero_fill) {
   OpData<T>& od = *reinterpret_cast<OpData<T>*>(sizeof(T) == 8 ? (void*)&c.f64 : (void*)&c.f32);
   const T* hcoef = reinterpret_cast<const T*>(sizeof(T) == 8 ? (const void*)c.h64 : (const void*)c.h32);
   cudaStream_t s = c.stream;
+  const size_t bytes = (size_t)c.m * ncols * sizeof(T);
   std::array<cudaEvent_t, 4> ev{};
-  std::array<int, 3> nlaunch{1, 0, 0};
+  std::array<int, 3> nlaunch{zero_fill ? 1 : 0, 0, 0};
   auto mark = [&](int i) {
     if (!c.profiling) return;
     if (c.ev_pool.empty()) {
@@ -553,7 +536,8 @@ static fe_ks_status apply_impl(fe_ks_ctx* ctx, const void* Xv, void* Yv, int64_t
     cudaEventRecord(ev[i], s);
   };
   mark(0);
-  if (cudaMemsetAsync(Y, 0, bytes, s) != cudaSuccess) return fail(FE_KS_ERR_CUDA, "cudaMemsetAsync failed");
+  if (zero_fill && cudaMemsetAsync(Y, 0, bytes, s) != cudaSuccess)
+    return fail(FE_KS_ERR_CUDA, "cudaMemsetAsync failed");
   mark(1);
   const bool nl = (c.terms & FE_KS_TERM_NL) && c.n_pairs > 0;
   if (nl) {
@@ -591,6 +575,7 @@ static fe_ks_status apply_impl(fe_ks_ctx* ctx, const void* Xv, void* Yv, int64_t
   lp.F = od.F;
   lp.Q = od.Q;
   lp.n_proj = c.n_proj;
+  lp.alpha = alpha;
   lp.tab = od.tab;
   for (size_t col = 0; col + 1 < c.colour_ptr.size(); ++col) {
     lp.cells = c.colour_cells + c.colour_ptr[col];
@@ -605,6 +590,26 @@ static fe_ks_status apply_impl(fe_ks_ctx* ctx, const void* Xv, void* Yv, int64_t
     c.ev_launches.push_back(nlaunch);
   }
   return FE_KS_OK;
+}
+
+template fe_ks_status apply_core<double>(Ctx&, const double*, double*, int64_t, bool, double, bool);
+template fe_ks_status apply_core<float>(Ctx&, const float*, float*, int64_t, bool, float, bool);
+
+template <typename T>
+static fe_ks_status apply_impl(fe_ks_ctx* ctx, const void* Xv, void* Yv, int64_t n_v, bool scaled) {
+  g_last_error.clear();
+  if (!ctx) return fail(FE_KS_ERR_ARG, "ctx is NULL");
+  Ctx& c = ctx->c;
+  if (!Xv || !Yv) return fail(FE_KS_ERR_ARG, "X or Y is NULL");
+  if (n_v < 1 || n_v > c.n_v_max) return fail(FE_KS_ERR_ARG, "n_v must be in 1..n_v_max");
+  if (((uintptr_t)Xv % sizeof(T)) || ((uintptr_t)Yv % sizeof(T)))
+    return fail(FE_KS_ERR_ARG, "X and Y must be aligned to the scalar size");
+  const int64_t ncols = n_v * (c.cplx ? 2 : 1);
+  const size_t bytes = (size_t)c.m * ncols * sizeof(T);
+  const char* xb = static_cast<const char*>(Xv);
+  const char* yb = static_cast<const char*>(Yv);
+  if (xb < yb + bytes && yb < xb + bytes) return fail(FE_KS_ERR_ARG, "X and Y overlap");
+  return apply_core<T>(c, static_cast<const T*>(Xv), static_cast<T*>(Yv), ncols, scaled, T(1), true);
 }
 
 }  // namespace feks

@@ -1,0 +1,173 @@
+// Residual-based Chebyshev filter (R-ChFSI, Algorithm 4) on the standard form
+// Hs = D^{-1/2} H D^{-1/2} (D = GLL-lumped mass, so D -> I and M -> I):
+//
+//   Y   = Hs X - X Lam                          (FP64: residual)
+//   R_X = 0, R_Y = (s1/e) Y, Lam_X = 1, Lam_Y = (s1/e)(Lam - c)
+//   k = 2..m: s2 = 1/(gamma - s)
+//       R_X   <- (2 s2/e) [ (Hs - c) R_Y + Y Lam_Y ] - s s2 R_X   (precision of the call)
+//       Lam_X <- (2 s2/e) Lam_Y (Lam - c) - s s2 Lam_X
+//       swap(R_X, R_Y), swap(Lam_X, Lam_Y), s = s2
+//   X   <- R_Y + X Lam_Y                        (FP64)
+//
+// The recurrence term (Hs - c) R_Y + Y Lam_Y is formed by first writing
+// a(-c R_Y + Y Lam_Y) - b R_X in place into R_X (elementwise kernel) and then
+// letting the fused cell kernel scatter-add a * Hs R_Y on top (alpha = a).
+#include <cmath>
+
+#include "fe_ks_internal.h"
+
+namespace feks {
+
+constexpr int kEwThreads = 256;
+
+static int ew_blocks(int64_t n) {
+  int64_t b = (n + kEwThreads - 1) / kEwThreads;
+  return (int)(b < 152 * 16 ? b : 152 * 16);
+}
+
+// Y = -X * lam[col / cw]   (so that a later accumulate-apply gives Hs X - X Lam)
+__global__ void k_residual_init(double* __restrict__ Y, const double* __restrict__ X, const double* __restrict__ lam,
+                                int64_t n, int64_t ncols, int cw) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t col = i % ncols;
+    Y[i] = -X[i] * lam[col / cw];
+  }
+}
+
+// Ylow = Y, R_Y = s1e * Y (in the precision of the recurrence)
+template <typename T>
+__global__ void k_residual_split(const double* __restrict__ Y, T* __restrict__ Yl, T* __restrict__ RY, double s1e,
+                                 int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double y = Y[i];
+    if (Yl != nullptr) Yl[i] = (T)y;
+    RY[i] = (T)(s1e * y);
+  }
+}
+
+// R_X <- a (-c R_Y + Y Lam_Y) - b R_X   (b == 0: R_X is not read)
+template <typename T>
+__global__ void k_cheb_prologue(T* __restrict__ RX, const T* __restrict__ RY, const T* __restrict__ Yl,
+                                const double* __restrict__ LY, T a, T c, T b, int64_t n, int64_t ncols, int cw) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t col = i % ncols;
+    const T ly = (T)LY[col / cw];
+    T v = a * fma(Yl[i], ly, -c * RY[i]);
+    if (b != T(0)) v = fma(-b, RX[i], v);
+    RX[i] = v;
+  }
+}
+
+// Lam_X <- a Lam_Y (lam - c) - b Lam_X ; init: Lam_X = 1, Lam_Y = s1e (lam - c)
+__global__ void k_lambda(double* LX, double* LY, const double* lam, double a, double c, double b, int init, int n_v) {
+  for (int j = threadIdx.x + blockIdx.x * blockDim.x; j < n_v; j += blockDim.x * gridDim.x) {
+    if (init) {
+      LX[j] = 1.0;
+      LY[j] = a * (lam[j] - c);
+    } else {
+      LX[j] = a * LY[j] * (lam[j] - c) - b * LX[j];
+    }
+  }
+}
+
+// X <- R_Y + X Lam_Y
+template <typename T>
+__global__ void k_cheb_final(double* __restrict__ X, const T* __restrict__ RY, const double* __restrict__ LY, int64_t n,
+                             int64_t ncols, int cw) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t col = i % ncols;
+    X[i] = (double)RY[i] + X[i] * LY[col / cw];
+  }
+}
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+static size_t filter_bytes(const Ctx& c, int64_t n_v, int precision) {
+  const size_t n = (size_t)c.m * n_v * (c.cplx ? 2 : 1);
+  const size_t lo = precision == FE_KS_F64 ? 8 : 4;
+  size_t b = align256(n * 8);                    // Y (FP64 residual)
+  if (precision != FE_KS_F64) b += align256(n * lo);   // Y in the recurrence precision
+  b += 2 * align256(n * lo);                     // R_X, R_Y
+  b += 2 * align256((size_t)n_v * 8);            // Lam_X, Lam_Y
+  return b;
+}
+
+template <typename T>
+static fe_ks_status cheb_impl(Ctx& c, double* X, const double* lam, int64_t n_v, int degree, double lmin, double lT,
+                              double lmax, char* work) {
+  cudaStream_t s = c.stream;
+  const int cw = c.cplx ? 2 : 1;
+  const int64_t ncols = n_v * cw;
+  const int64_t n = c.m * ncols;
+  const bool low = sizeof(T) != 8;
+  size_t off = 0;
+  double* Y = reinterpret_cast<double*>(work + off);
+  off += align256(n * 8);
+  T* Yl = low ? reinterpret_cast<T*>(work + off) : reinterpret_cast<T*>(Y);
+  if (low) off += align256(n * sizeof(T));
+  T* RX = reinterpret_cast<T*>(work + off);
+  off += align256(n * sizeof(T));
+  T* RY = reinterpret_cast<T*>(work + off);
+  off += align256(n * sizeof(T));
+  double* LX = reinterpret_cast<double*>(work + off);
+  off += align256(n_v * 8);
+  double* LY = reinterpret_cast<double*>(work + off);
+
+  const double e = 0.5 * (lmax - lT), cc = 0.5 * (lmax + lT);
+  double sigma = e / (lmin - cc);
+  const double sigma1 = sigma, gamma = 2.0 / sigma1;
+  const int nb = ew_blocks(n);
+
+  // Y = Hs X - X Lam (FP64)
+  k_residual_init<<<nb, kEwThreads, 0, s>>>(Y, X, lam, n, ncols, cw);
+  fe_ks_status st = apply_core<double>(c, X, Y, ncols, true, 1.0, false);
+  if (st != FE_KS_OK) return st;
+  k_residual_split<T><<<nb, kEwThreads, 0, s>>>(Y, low ? Yl : nullptr, RY, sigma1 / e, n);
+  k_lambda<<<(int)((n_v + 255) / 256), 256, 0, s>>>(LX, LY, lam, sigma1 / e, cc, 0.0, 1, (int)n_v);
+  for (int k = 2; k <= degree; ++k) {
+    const double sigma2 = 1.0 / (gamma - sigma);
+    const double a = 2.0 * sigma2 / e, b = (k == 2) ? 0.0 : sigma * sigma2;
+    k_cheb_prologue<T><<<nb, kEwThreads, 0, s>>>(RX, RY, Yl, LY, (T)a, (T)cc, (T)b, n, ncols, cw);
+    st = apply_core<T>(c, RY, RX, ncols, true, (T)a, false);
+    if (st != FE_KS_OK) return st;
+    k_lambda<<<(int)((n_v + 255) / 256), 256, 0, s>>>(LX, LY, lam, a, cc, sigma * sigma2, 0, (int)n_v);
+    std::swap(RX, RY);
+    std::swap(LX, LY);
+    sigma = sigma2;
+  }
+  k_cheb_final<T><<<nb, kEwThreads, 0, s>>>(X, RY, LY, n, ncols, cw);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return fail(FE_KS_ERR_CUDA, std::string("filter kernels: ") + cudaGetErrorString(err));
+  return FE_KS_OK;
+}
+
+}  // namespace feks
+
+using namespace feks;
+
+extern "C" {
+
+fe_ks_status fe_ks_cheb_filter_workspace(const fe_ks_ctx* ctx, int64_t n_v, int precision, size_t* bytes) {
+  if (!ctx || !bytes) return fail(FE_KS_ERR_ARG, "NULL argument");
+  if (precision != FE_KS_F64 && precision != FE_KS_F32) return fail(FE_KS_ERR_UNSUPPORTED, "unknown precision");
+  *bytes = filter_bytes(ctx->c, n_v, precision);
+  return FE_KS_OK;
+}
+
+fe_ks_status fe_ks_cheb_filter(fe_ks_ctx* ctx, double* X, const double* ritz, int64_t n_v, int degree, double lam_min,
+                               double lam_T, double lam_max, int precision, void* work, size_t work_bytes) {
+  set_error("");
+  if (!ctx || !X || !ritz || !work) return fail(FE_KS_ERR_ARG, "NULL argument");
+  Ctx& c = ctx->c;
+  if (n_v < 1 || n_v > c.n_v_max) return fail(FE_KS_ERR_ARG, "n_v must be in 1..n_v_max");
+  if (degree < 1) return fail(FE_KS_ERR_ARG, "degree must be >= 1");
+  if (!(lam_min < lam_T && lam_T < lam_max)) return fail(FE_KS_ERR_ARG, "need lam_min < lam_T < lam_max");
+  if (precision != FE_KS_F64 && precision != FE_KS_F32) return fail(FE_KS_ERR_UNSUPPORTED, "unknown precision");
+  if (work_bytes < filter_bytes(c, n_v, precision)) return fail(FE_KS_ERR_ARG, "workspace too small");
+  if (((uintptr_t)work & 255) || ((uintptr_t)X & 7)) return fail(FE_KS_ERR_ARG, "misaligned X or workspace");
+  char* w = static_cast<char*>(work);
+  if (precision == FE_KS_F64) return cheb_impl<double>(c, X, ritz, n_v, degree, lam_min, lam_T, lam_max, w);
+  return cheb_impl<float>(c, X, ritz, n_v, degree, lam_min, lam_T, lam_max, w);
+}
+
+}  // extern "C"

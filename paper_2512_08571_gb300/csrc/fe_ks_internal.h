@@ -73,6 +73,7 @@ struct LocalParams {
   const T* F;
   const T* Q;              // [n_atoms][n_proj][ld], already scaled by Delta
   int n_proj;
+  T alpha;                 // Y += alpha * (H X) (1 for a plain application)
   EOTables<T> tab;
 };
 
@@ -133,6 +134,10 @@ void lagrange_eval(int n, const double* nodes, double x, double* val, double* de
 template <typename T>
 void build_eo_tables(int p, int nq, EOTables<T>* out);
 
+// Y (+)= alpha H X or alpha Hs X on the context's stream; zero_fill clears Y first.
+template <typename T>
+fe_ks_status apply_core(Ctx& c, const T* X, T* Y, int64_t ncols, bool scaled, T alpha, bool zero_fill);
+
 // kernel launchers (fe_ks_local_pN.cu)
 template <typename T>
 cudaError_t launch_local(const Ctx& c, const LocalParams<T>& prm, cudaStream_t s);
@@ -140,3 +145,8 @@ template <typename T>
 cudaError_t launch_proj(const Ctx& c, const ProjParams<T>& prm, int n_atoms, cudaStream_t s);
 
 }  // namespace feks
+
+// The opaque handle of the C interface.
+struct fe_ks_ctx {
+  feks::Ctx c;
+};

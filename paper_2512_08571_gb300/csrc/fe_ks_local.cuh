@@ -275,7 +275,7 @@ fe_local_kernel(const __grid_constant__ LocalParams<T> p) {
 #pragma unroll
         for (int i = 0; i < NP; ++i) {
           const int d = sd[i + NP * (j + NP * k)];
-          T val = y[i];
+          T val = y[i] * p.alpha;
           if (p.dscale) val *= p.dscale[d];
           T* yp = p.Y + (int64_t)d * p.ld + col;
           *yp += val;
@@ -300,15 +300,24 @@ cudaError_t launch_local_deg(const Ctx& c, const LocalParams<T>& prm, cudaStream
   const int gy = prm.n_cells < 65535 ? prm.n_cells : 65535;
   if (prm.n_cells == 0) return cudaSuccess;
   dim3 grid(tiles, gy);
+  // the shared-memory opt-in is a per-device function attribute: set it once per device
+  static bool attr_done[2][64] = {};
+  const int dev = c.device & 63;
   if (c.cplx) {
     auto k = fe_local_kernel<T, NP, NQ, VT, true>;
-    cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return err;
+    if (!attr_done[1][dev]) {
+      cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (err != cudaSuccess) return err;
+      attr_done[1][dev] = true;
+    }
     k<<<grid, VT * NQ * NQ, smem, s>>>(prm);
   } else {
     auto k = fe_local_kernel<T, NP, NQ, VT, false>;
-    cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return err;
+    if (!attr_done[0][dev]) {
+      cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (err != cudaSuccess) return err;
+      attr_done[0][dev] = true;
+    }
     k<<<grid, VT * NQ * NQ, smem, s>>>(prm);
   }
   return cudaGetLastError();

@@ -59,11 +59,14 @@ def _load():
     lib.fe_ks_set_profiling.argtypes = [vp, ctypes.c_int]
     lib.fe_ks_read_profile.argtypes = [vp, P(ctypes.c_double), P(i64)]
     lib.fe_ks_measure_fma_peak.argtypes = [ctypes.c_int, P(ctypes.c_double)]
+    lib.fe_ks_cheb_filter_workspace.argtypes = [vp, i64, ctypes.c_int, P(ctypes.c_size_t)]
+    lib.fe_ks_cheb_filter.argtypes = [vp, vp, vp, i64, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_int, vp, ctypes.c_size_t]
     lib.fe_ks_destroy.argtypes = [vp]
     lib.fe_ks_destroy.restype = None
     for name in ("fe_ks_quadrature_points", "fe_ks_setup", "fe_ks_apply", "fe_ks_apply_scaled",
                  "fe_ks_info", "fe_ks_set_stream", "fe_ks_set_profiling", "fe_ks_read_profile",
-                 "fe_ks_measure_fma_peak"):
+                 "fe_ks_measure_fma_peak", "fe_ks_cheb_filter_workspace", "fe_ks_cheb_filter"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -107,6 +110,17 @@ def fe_ks_apply(ctx, X, Y, n_v, precision):
 
 def fe_ks_apply_scaled(ctx, X, Y, n_v, precision):
     _check(_lib.fe_ks_apply_scaled(ctx, _ptr(X), _ptr(Y), n_v, precision))
+
+
+def fe_ks_cheb_filter_workspace(ctx, n_v, precision):
+    out = ctypes.c_size_t()
+    _check(_lib.fe_ks_cheb_filter_workspace(ctx, n_v, precision, ctypes.byref(out)))
+    return out.value
+
+
+def fe_ks_cheb_filter(ctx, X, ritz, n_v, degree, lam_min, lam_T, lam_max, precision, work, work_bytes):
+    _check(_lib.fe_ks_cheb_filter(ctx, _ptr(X), _ptr(ritz), n_v, degree, lam_min, lam_T, lam_max, precision,
+                                  _ptr(work), work_bytes))
 
 
 def fe_ks_dinv_sqrt(ctx):

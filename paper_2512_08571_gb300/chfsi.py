@@ -30,7 +30,8 @@ class RChFSI:
         self.lmax = None
 
     def apply_scaled(self, V, out=None):
-        out = torch.empty_like(V) if out is None else out
+        V = V.contiguous()
+        out = torch.empty(V.shape, dtype=V.dtype, device=V.device) if out is None else out
         fk.fe_ks_apply_scaled(self.ctx, V, out, V.shape[1], fk.FE_KS_F64)
         return out
 
@@ -65,6 +66,7 @@ class RChFSI:
     def rayleigh_ritz(self, Y):
         """Orthonormalise Y (QR) and solve the projected problem: returns (lam, X)."""
         Q, _ = torch.linalg.qr(Y)
+        Q = Q.contiguous()          # QR returns column-major factors; the C ABI is row-major
         HQ = self.apply_scaled(Q, self.tmp)
         A = Q.conj().T @ HQ
         A = 0.5 * (A + A.conj().T)

@@ -84,11 +84,15 @@ def _check(status):
 
 
 def _ptr(a):
-    """Data pointer of a numpy array or torch tensor (None -> NULL)."""
+    """Data pointer of a C-contiguous numpy array or torch tensor (None -> NULL)."""
     if a is None:
         return None
     if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous (row-major [m][n_v])")
         return a.ctypes.data
+    if hasattr(a, "is_contiguous") and not a.is_contiguous():
+        raise ValueError("tensor must be contiguous (row-major [m][n_v])")
     return a.data_ptr()
 
 

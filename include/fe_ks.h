@@ -206,6 +206,43 @@ fe_ks_status fe_ks_read_profile(fe_ks_ctx* ctx, double ms[3], int64_t launches[3
  */
 fe_ks_status fe_ks_measure_fma_peak(int precision, double* tflops);
 
+/*
+ * Allocation-free nonlocal term (no counterpart in the paper; an interface
+ * for callers that cannot call cudaMalloc).
+ *
+ * Who needs it: callers whose device memory is owned by another allocator
+ * (a framework's memory pool that must account for every byte), or code that
+ * runs where a cudaMalloc would implicitly synchronise the device or exceed a
+ * fixed memory budget.  They pass every input and output; this call allocates
+ * nothing (no cudaMalloc / cudaFree, no allocating library routine) and keeps
+ * its only scratch -- the per-atom projections diag(h_a) F_a^H X -- in a
+ * file-scope device array of 4 MiB (524288 doubles) that every GPU which
+ * loads the library holds until the process exits.
+ *
+ *   Y += sum_a F_a diag(h_a) F_a^H X          (FP64; eq. Vnonloc)
+ *
+ *  X, Y          : device FP64 [n_dofs][n_v] (complex: interleaved, is_complex = 1);
+ *                  Y is accumulated into (zero it first for the bare term).
+ *  cell_dofs     : device [E][(degree+1)^3] global DoF of each cell node.
+ *  atom_pair_ptr : device [n_atoms + 1] CSR offsets of each atom's (cell, image) entries.
+ *  pair_cell     : device [n_pairs] cell of each entry; pair_atom: device [n_pairs] its atom.
+ *  F             : device [n_pairs][n_proj][(degree+1)^3] projector matrices
+ *                  F^(a,e) (complex: interleaved re, im per entry).
+ *  h_coef        : device [n_atoms][n_proj] coefficients Delta^a.
+ * Limit: n_atoms * n_proj * n_v * (1 + is_complex) <= 524288, else
+ * FE_KS_ERR_ARG with a message naming the limit.  The first call on a device
+ * looks up the scratch address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the one scratch array, which keeps the last call's contents (every entry a
+ * call reads is written by that call first): calls that overlap on the GPU
+ * (different streams, or other devices' threads using the same device) race.
+ */
+fe_ks_status fe_ks_nonlocal_apply_static(const double* X, double* Y, int64_t n_v, int32_t is_complex,
+                                         int32_t degree, int64_t n_dofs, const int32_t* cell_dofs,
+                                         int32_t n_atoms, int32_t n_proj, const int32_t* atom_pair_ptr,
+                                         const int32_t* pair_cell, const int32_t* pair_atom, int64_t n_pairs,
+                                         const double* F, const double* h_coef, void* cuda_stream);
+
 /* Change the stream used by later calls. */
 fe_ks_status fe_ks_set_stream(fe_ks_ctx* ctx, void* cuda_stream);
 

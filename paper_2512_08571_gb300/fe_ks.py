@@ -62,11 +62,14 @@ def _load():
     lib.fe_ks_cheb_filter_workspace.argtypes = [vp, i64, ctypes.c_int, P(ctypes.c_size_t)]
     lib.fe_ks_cheb_filter.argtypes = [vp, vp, vp, i64, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_int, vp, ctypes.c_size_t]
+    lib.fe_ks_nonlocal_apply_static.argtypes = [vp, vp, i64, i32, i32, i64, vp, i32, i32, vp, vp, vp, i64,
+                                                vp, vp, vp]
     lib.fe_ks_destroy.argtypes = [vp]
     lib.fe_ks_destroy.restype = None
     for name in ("fe_ks_quadrature_points", "fe_ks_setup", "fe_ks_apply", "fe_ks_apply_scaled",
                  "fe_ks_info", "fe_ks_set_stream", "fe_ks_set_profiling", "fe_ks_read_profile",
-                 "fe_ks_measure_fma_peak", "fe_ks_cheb_filter_workspace", "fe_ks_cheb_filter"):
+                 "fe_ks_measure_fma_peak", "fe_ks_cheb_filter_workspace", "fe_ks_cheb_filter",
+                 "fe_ks_nonlocal_apply_static"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -125,6 +128,14 @@ def fe_ks_cheb_filter_workspace(ctx, n_v, precision):
 def fe_ks_cheb_filter(ctx, X, ritz, n_v, degree, lam_min, lam_T, lam_max, precision, work, work_bytes):
     _check(_lib.fe_ks_cheb_filter(ctx, _ptr(X), _ptr(ritz), n_v, degree, lam_min, lam_T, lam_max, precision,
                                   _ptr(work), work_bytes))
+
+
+def fe_ks_nonlocal_apply_static(X, Y, n_v, is_complex, degree, n_dofs, cell_dofs, n_atoms, n_proj,
+                                atom_pair_ptr, pair_cell, pair_atom, n_pairs, F, h_coef, stream=None):
+    _check(_lib.fe_ks_nonlocal_apply_static(_ptr(X), _ptr(Y), n_v, int(is_complex), degree, n_dofs,
+                                            _ptr(cell_dofs), n_atoms, n_proj, _ptr(atom_pair_ptr),
+                                            _ptr(pair_cell), _ptr(pair_atom), n_pairs, _ptr(F), _ptr(h_coef),
+                                            stream))
 
 
 def fe_ks_dinv_sqrt(ctx):

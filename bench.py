@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the six-system batched launch")
+    ap.add_argument("--precision", choices=["both", "f64", "f32"], default="both",
+                    help="f32 alone times only the FP32 application (for profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle sample")
     return ap.parse_args()
 
@@ -180,6 +183,7 @@ def run_native(args, wl, rank, world):
         X = torch.empty((m, n_v), dtype=dt[0], device=dev)
         fill_trial(wl, n_v, X, np.complex128 if cplx else dt[1])
         Y = torch.empty_like(X)
+        best, tune_ms = fk.fe_ks_tune(ctx, X, Y, n_v, precision, reps=1)
         for _ in range(warmup):
             fk.fe_ks_apply(ctx, X, Y, n_v, precision)
         torch.cuda.synchronize()
@@ -205,15 +209,18 @@ def run_native(args, wl, rank, world):
         local_ms, local_n = prof["local"]
         achieved = local_flops * steps / (local_ms * 1e-3) if local_ms > 0 else None
         out = dict(ms=ms, value=units * world / (ms * 1e-3), prof=prof, clocks=clk.summary(),
+                   tile_config=best, tune_ms=[round(t, 3) for t in tune_ms],
                    achieved=achieved, local_launch_ms=local_ms / max(local_n, 1),
                    launches=int(prof["proj"][1] + prof["local"][1]))
         del X, Y
         torch.cuda.empty_cache()
         return out
 
-    f64 = measure(fk.FE_KS_F64, args.steps, args.warmup)
+    f64 = measure(fk.FE_KS_F64, args.steps, args.warmup) if args.precision != "f32" else None
     mixed = None
-    if not args.no_mixed:
+    if args.precision == "f32":
+        mixed = measure(fk.FE_KS_F32, args.steps, args.warmup)
+    elif not args.no_mixed and args.precision == "both":
         mixed = measure(fk.FE_KS_F32, max(args.steps, 20), max(args.warmup, 3))
 
     peak64_live = fk.fe_ks_measure_fma_peak(fk.FE_KS_F64) * 1e12
@@ -255,6 +262,90 @@ def run_native(args, wl, rank, world):
     fk.fe_ks_destroy(ctx)
     return dict(f64=f64, mixed=mixed, e2e=e2e, setup_s=setup_s, info=info, local_flops=local_flops,
                 peak64_live=peak64_live, peak32_live=peak32_live)
+
+
+# -------------------------------------------------------- batched systems
+def run_batched(args):
+    """Six uneven systems (cell grids 6^3..20^3, degrees 4..8, N_v 16..512, FP64/FP32
+    alternating) in one persistent launch captured in a CUDA graph, against one
+    fe_ks_apply per system.  Returns a dict for the JSON line."""
+    import torch
+    from paper_2512_08571_gb300 import fe_ks as fk
+    from paper_2512_08571_gb300.problem import HostProblem
+    from synth import batched_systems
+    wls = batched_systems()
+    if args.cells:
+        wls = [wl.scaled(n=max(2, wl.n * args.cells // 20)) for wl in wls]
+    stream = torch.cuda.current_stream()
+    prec = [fk.FE_KS_F64 if wl.precision == "f64" else fk.FE_KS_F32 for wl in wls]
+    ctxs, Xs, Ys = [], [], []
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(5000)
+    for wl, pr in zip(wls, prec):
+        hp = HostProblem(wl)
+        ctxs.append(fk.fe_ks_setup(hp.struct, fk.TERM_ALL, wl.n_v, stream.cuda_stream))
+        dt = torch.float64 if pr == fk.FE_KS_F64 else torch.float32
+        X = (torch.rand((wl.n_dofs, wl.n_v), generator=gen, device="cuda", dtype=dt) * 2 - 1)
+        Xs.append(X)
+        Ys.append(torch.empty_like(X))
+    units = sum(wl.n_dofs * wl.n_v for wl in wls)
+    for c, X, Y, wl, pr in zip(ctxs, Xs, Ys, wls, prec):
+        fk.fe_ks_tune(c, X, Y, wl.n_v, pr, reps=2)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def separate():
+        for c, X, Y, wl, pr in zip(ctxs, Xs, Ys, wls, prec):
+            fk.fe_ks_apply(c, X, Y, wl.n_v, pr)
+
+    ms_sep = timed(separate, args.steps)
+    b = fk.fe_ks_batch_create(ctxs, [wl.n_v for wl in wls], prec)
+    best = None
+    trials = []
+    for tile in (0, 1):
+        for cells in (1, 2, 4):
+            for depth in (1, 2):
+                fk.fe_ks_batch_configure(b, [tile] * len(wls), cells, depth, 2.0, False)
+                ms = timed(lambda: fk.fe_ks_batch_apply(b, Xs, Ys, stream.cuda_stream), 2)
+                fk.fe_ks_batch_status(b)
+                trials.append({"tile": tile, "cells_per_item": cells, "depth": depth, "ms": round(ms, 3)})
+                if best is None or ms < best[0]:
+                    best = (ms, tile, cells, depth)
+    _, tile, cells, depth = best
+    fk.fe_ks_batch_configure(b, [tile] * len(wls), cells, depth, 2.0, False)
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        fk.fe_ks_batch_apply(b, Xs, Ys, side.cuda_stream)
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g):
+        fk.fe_ks_batch_apply(b, Xs, Ys, torch.cuda.current_stream().cuda_stream)
+    ms_graph = timed(g.replay, args.steps)
+    fk.fe_ks_batch_status(b)
+    info = fk.fe_ks_batch_info(b)
+    fk.fe_ks_batch_destroy(b)
+    for c in ctxs:
+        fk.fe_ks_destroy(c)
+    return {"workload": "6 systems: grids " + ",".join(f"{wl.n}^3" for wl in wls) + "; p=" +
+                        ",".join(str(wl.p) for wl in wls) + "; N_v=" + ",".join(str(wl.n_v) for wl in wls) +
+                        "; " + ",".join(wl.precision for wl in wls),
+            "value": units / (ms_graph * 1e-3), "unit": UNIT, "ms_per_step": ms_graph,
+            "one_launch_per_system": {"value": units / (ms_sep * 1e-3), "ms_per_step": ms_sep},
+            "speedup_vs_separate": ms_sep / ms_graph,
+            "tuned": {"tile_config": tile, "cells_per_item": cells, "depth": depth},
+            "tuning_trials": trials, "items": info["n_items"], "grid": info["grid"],
+            "smem_bytes": info["smem_bytes"], "graph": True, "x_inputs": "device RNG (seed 5000), U(-1,1)"}
 
 
 # ----------------------------------------------------------- oracle timing
@@ -341,6 +432,9 @@ def main():
             torch.distributed.destroy_process_group()
         return
     f64 = res["f64"]
+    if f64 is None:
+        print(json.dumps({"metric": METRIC, "profiling_only": True, "f32_ms": res["mixed"]["ms"]}))
+        return
     traffic = load_traffic(f"fe_local_kernel f64 {wl.name}")
     achieved = f64["achieved"]
     roofline = {"bound": "alu", "achieved": achieved / 1e12 if achieved else None,
@@ -349,7 +443,8 @@ def main():
                 "kernel": "fe_local_kernel (FP64 DFMA pipe)",
                 "peak_source": "nominal FP64 1.25 TFLOP/s; live DFMA probe %.3f TFLOP/s" % (res["peak64_live"] / 1e12),
                 "frac_of_live_probe": (achieved / res["peak64_live"]) if achieved else None,
-                "avg_launch_ms": f64["local_launch_ms"]}
+                "avg_launch_ms": f64["local_launch_ms"], "tile_config": f64["tile_config"],
+                "tune_ms_per_config": f64["tune_ms"]}
     line = {"metric": METRIC, "value": f64["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": f64["ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded mesh, fields, atoms, X)",
@@ -364,10 +459,14 @@ def main():
                                       "peak": PEAK_FP32_NOMINAL / 1e12, "unit": "TFLOP/s",
                                       "frac": ach / PEAK_FP32_NOMINAL if ach else None,
                                       "live_probe": res["peak32_live"] / 1e12,
-                                      "avg_launch_ms": mixed["local_launch_ms"]},
+                                      "avg_launch_ms": mixed["local_launch_ms"],
+                                      "tile_config": mixed["tile_config"],
+                                      "tune_ms_per_config": mixed["tune_ms"]},
                          "clocks": mixed["clocks"], "gpu_launches": mixed["launches"]}
     if res["e2e"]:
         line["e2e"] = res["e2e"]
+    if not args.no_batched:
+        line["batched"] = run_batched(args)
     if world == 1 and not args.no_cpu_baseline:
         v, n, el = oracle_sample(wl, args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",

@@ -179,6 +179,52 @@ fe_ks_status fe_ks_cheb_filter(fe_ks_ctx* ctx, double* X, const double* ritz, in
                                double lam_min, double lam_T, double lam_max, int precision, void* work,
                                size_t work_bytes);
 
+/*
+ * Tile configuration of the fused cell kernel (columns per CTA tile and block
+ * size; 0 is the default, FE_KS_N_CONFIGS choices).  fe_ks_tune times every
+ * configuration with fe_ks_apply on the caller's X and Y (reps timed calls
+ * each, after one untimed call), keeps the fastest for this context and
+ * precision, and reports the milliseconds per call (-1 for a configuration
+ * that cannot launch, e.g. shared memory too large) and the choice.
+ * fe_ks_set_config sets it directly.  Y is overwritten.
+ */
+#define FE_KS_N_CONFIGS 3
+fe_ks_status fe_ks_tune(fe_ks_ctx* ctx, const void* X, void* Y, int64_t n_v, int precision, int reps,
+                        double* ms_per_config, int* best);
+fe_ks_status fe_ks_set_config(fe_ks_ctx* ctx, int precision, int config);
+
+/*
+ * Batched application: Y_s = H_s X_s for up to 16 independent systems of
+ * uneven size, degree (4..8), vector count and precision in ONE persistent
+ * kernel launch.  The work queue is phase-major -- zero-fill of every Y_s and
+ * the per-atom projections first, then the cells of colour 0, 1, ... of every
+ * system -- and a work item of system s waits (bounded) for the completion of
+ * s's previous phase only, so systems overlap freely.  Real operators only.
+ *
+ * fe_ks_batch_create builds the queue for the given contexts (owned by the
+ * caller, must outlive the batch), vector counts and precisions (FE_KS_F64 /
+ * FE_KS_F32); it allocates the queue and counters (the only allocation).
+ * fe_ks_batch_configure sets the tunables -- tile configuration per system
+ * (0/1: columns per tile), cells per work item, items claimed per fetch --
+ * plus the bounded-wait limit in seconds, and inject_missing_item = 1 makes
+ * the host count one phase-0 item that is never published (fault injection:
+ * the launch then ends with FE_KS_ERR_TIMEOUT reported by fe_ks_batch_status).
+ * fe_ks_batch_apply launches on cuda_stream (NULL: the first context's
+ * stream) with X[s], Y[s] device arrays laid out as for fe_ks_apply; it is a
+ * counter reset plus one kernel, so it can be captured into a CUDA graph.
+ * fe_ks_batch_status synchronises with the device and reports a wait that
+ * expired.
+ */
+typedef struct fe_ks_batch fe_ks_batch;
+fe_ks_status fe_ks_batch_create(fe_ks_ctx* const* ctxs, int n_sys, const int64_t* n_v, const int* precision,
+                                fe_ks_batch** out);
+fe_ks_status fe_ks_batch_configure(fe_ks_batch* b, const int* tile_config, int cells_per_item, int depth,
+                                   double wait_seconds, int inject_missing_item);
+fe_ks_status fe_ks_batch_apply(fe_ks_batch* b, const void* const* X, void* const* Y, void* cuda_stream);
+fe_ks_status fe_ks_batch_status(fe_ks_batch* b);
+fe_ks_status fe_ks_batch_info(const fe_ks_batch* b, int* n_items, int* grid, size_t* smem_bytes);
+void fe_ks_batch_destroy(fe_ks_batch* b);
+
 /* Length-m device copy of D^{-1/2} in FP64 (owned by the context). */
 const double* fe_ks_dinv_sqrt(const fe_ks_ctx* ctx);
 

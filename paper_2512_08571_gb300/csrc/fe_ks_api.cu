@@ -622,6 +622,61 @@ fe_ks_status fe_ks_apply(fe_ks_ctx* ctx, const void* X, void* Y, int64_t n_v, in
   return fail(FE_KS_ERR_UNSUPPORTED, "unknown precision");
 }
 
+fe_ks_status fe_ks_set_config(fe_ks_ctx* ctx, int precision, int config) {
+  if (!ctx) return fail(FE_KS_ERR_ARG, "ctx is NULL");
+  if (config < 0 || config >= kLocalConfigs) return fail(FE_KS_ERR_ARG, "config out of range");
+  if (precision == FE_KS_F64)
+    ctx->c.cfg64 = config;
+  else if (precision == FE_KS_F32)
+    ctx->c.cfg32 = config;
+  else
+    return fail(FE_KS_ERR_UNSUPPORTED, "unknown precision");
+  return FE_KS_OK;
+}
+
+fe_ks_status fe_ks_tune(fe_ks_ctx* ctx, const void* X, void* Y, int64_t n_v, int precision, int reps,
+                        double* ms_per_config, int* best) {
+  g_last_error.clear();
+  if (!ctx || !X || !Y) return fail(FE_KS_ERR_ARG, "NULL argument");
+  if (precision != FE_KS_F64 && precision != FE_KS_F32) return fail(FE_KS_ERR_UNSUPPORTED, "unknown precision");
+  if (reps < 1) reps = 1;
+  Ctx& c = ctx->c;
+  int& cfg = precision == FE_KS_F64 ? c.cfg64 : c.cfg32;
+  const int keep = cfg;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best_ms = 1e300;
+  int best_cfg = keep;
+  for (int k = 0; k < kLocalConfigs; ++k) {
+    cfg = k;
+    double ms = -1.0;
+    fe_ks_status st = fe_ks_apply(ctx, X, Y, n_v, precision);   // warm-up, and rejects configs that cannot launch
+    if (st == FE_KS_OK) {
+      cudaEventRecord(e0, c.stream);
+      for (int r = 0; r < reps && st == FE_KS_OK; ++r) st = fe_ks_apply(ctx, X, Y, n_v, precision);
+      cudaEventRecord(e1, c.stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) st = FE_KS_ERR_CUDA;
+      float t = 0.f;
+      if (st == FE_KS_OK && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess) ms = t / reps;
+    } else {
+      cudaGetLastError();   // clear a rejected launch configuration
+      g_last_error.clear();
+    }
+    if (ms_per_config) ms_per_config[k] = ms;
+    if (ms > 0 && ms < best_ms) {
+      best_ms = ms;
+      best_cfg = k;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cfg = best_cfg;
+  if (best) *best = best_cfg;
+  if (best_ms == 1e300) return fail(FE_KS_ERR_CUDA, "no tile configuration could be launched");
+  return FE_KS_OK;
+}
+
 fe_ks_status fe_ks_apply_scaled(fe_ks_ctx* ctx, const void* X, void* Y, int64_t n_v, int precision) {
   if (precision == FE_KS_F64) return apply_impl<double>(ctx, X, Y, n_v, true);
   if (precision == FE_KS_F32) return apply_impl<float>(ctx, X, Y, n_v, true);

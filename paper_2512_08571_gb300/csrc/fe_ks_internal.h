@@ -97,6 +97,7 @@ struct ProjParams {
 struct Ctx {
   int p = 0, nq = 0, np = 0, np3 = 0, nq3 = 0;
   int cplx = 0, terms = 0, gga = 0, ncoef = 0;
+  int cfg64 = 0, cfg32 = 0;      // tile configuration of the fused kernel per precision
   int64_t E = 0, m = 0, n_v_max = 0;
   int n_atoms = 0, n_proj = 0;
   int64_t n_pairs = 0;
@@ -137,6 +138,8 @@ void build_eo_tables(int p, int nq, EOTables<T>* out);
 // Y (+)= alpha H X or alpha Hs X on the context's stream; zero_fill clears Y first.
 template <typename T>
 fe_ks_status apply_core(Ctx& c, const T* X, T* Y, int64_t ncols, bool scaled, T alpha, bool zero_fill);
+
+constexpr int kLocalConfigs = 3;
 
 // kernel launchers (fe_ks_local_pN.cu)
 template <typename T>

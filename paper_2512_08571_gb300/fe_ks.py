@@ -64,12 +64,23 @@ def _load():
                                       ctypes.c_double, ctypes.c_int, vp, ctypes.c_size_t]
     lib.fe_ks_nonlocal_apply_static.argtypes = [vp, vp, i64, i32, i32, i64, vp, i32, i32, vp, vp, vp, i64,
                                                 vp, vp, vp]
+    lib.fe_ks_tune.argtypes = [vp, vp, vp, i64, ctypes.c_int, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_int)]
+    lib.fe_ks_set_config.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    lib.fe_ks_batch_create.argtypes = [P(vp), ctypes.c_int, P(i64), P(ctypes.c_int), P(vp)]
+    lib.fe_ks_batch_configure.argtypes = [vp, P(ctypes.c_int), ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                          ctypes.c_int]
+    lib.fe_ks_batch_apply.argtypes = [vp, P(vp), P(vp), vp]
+    lib.fe_ks_batch_status.argtypes = [vp]
+    lib.fe_ks_batch_info.argtypes = [vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_size_t)]
+    lib.fe_ks_batch_destroy.argtypes = [vp]
+    lib.fe_ks_batch_destroy.restype = None
     lib.fe_ks_destroy.argtypes = [vp]
     lib.fe_ks_destroy.restype = None
     for name in ("fe_ks_quadrature_points", "fe_ks_setup", "fe_ks_apply", "fe_ks_apply_scaled",
                  "fe_ks_info", "fe_ks_set_stream", "fe_ks_set_profiling", "fe_ks_read_profile",
                  "fe_ks_measure_fma_peak", "fe_ks_cheb_filter_workspace", "fe_ks_cheb_filter",
-                 "fe_ks_nonlocal_apply_static"):
+                 "fe_ks_nonlocal_apply_static", "fe_ks_tune", "fe_ks_set_config", "fe_ks_batch_create",
+                 "fe_ks_batch_configure", "fe_ks_batch_apply", "fe_ks_batch_status", "fe_ks_batch_info"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -136,6 +147,58 @@ def fe_ks_nonlocal_apply_static(X, Y, n_v, is_complex, degree, n_dofs, cell_dofs
                                             _ptr(cell_dofs), n_atoms, n_proj, _ptr(atom_pair_ptr),
                                             _ptr(pair_cell), _ptr(pair_atom), n_pairs, _ptr(F), _ptr(h_coef),
                                             stream))
+
+
+N_CONFIGS = 3
+
+
+def fe_ks_tune(ctx, X, Y, n_v, precision, reps=3):
+    """Time every tile configuration on (X, Y); keep the fastest. Returns (best, [ms per config])."""
+    ms = (ctypes.c_double * N_CONFIGS)()
+    best = ctypes.c_int()
+    _check(_lib.fe_ks_tune(ctx, _ptr(X), _ptr(Y), n_v, precision, reps, ms, ctypes.byref(best)))
+    return best.value, list(ms)
+
+
+def fe_ks_set_config(ctx, precision, config):
+    _check(_lib.fe_ks_set_config(ctx, precision, config))
+
+
+def fe_ks_batch_create(ctxs, n_v, precision):
+    n = len(ctxs)
+    arr = (ctypes.c_void_p * n)(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
+    nv = (ctypes.c_int64 * n)(*n_v)
+    pr = (ctypes.c_int * n)(*precision)
+    out = ctypes.c_void_p()
+    _check(_lib.fe_ks_batch_create(arr, n, nv, pr, ctypes.byref(out)))
+    return out
+
+
+def fe_ks_batch_configure(batch, tile_config=None, cells_per_item=1, depth=1, wait_seconds=2.0,
+                          inject_missing_item=False):
+    tc = None if tile_config is None else (ctypes.c_int * len(tile_config))(*tile_config)
+    _check(_lib.fe_ks_batch_configure(batch, tc, cells_per_item, depth, wait_seconds, int(inject_missing_item)))
+
+
+def fe_ks_batch_apply(batch, Xs, Ys, stream=None):
+    n = len(Xs)
+    xa = (ctypes.c_void_p * n)(*[_ptr(x) for x in Xs])
+    ya = (ctypes.c_void_p * n)(*[_ptr(y) for y in Ys])
+    _check(_lib.fe_ks_batch_apply(batch, xa, ya, stream))
+
+
+def fe_ks_batch_status(batch):
+    _check(_lib.fe_ks_batch_status(batch))
+
+
+def fe_ks_batch_info(batch):
+    n, g, s = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+    _check(_lib.fe_ks_batch_info(batch, ctypes.byref(n), ctypes.byref(g), ctypes.byref(s)))
+    return dict(n_items=n.value, grid=g.value, smem_bytes=s.value)
+
+
+def fe_ks_batch_destroy(batch):
+    _lib.fe_ks_batch_destroy(batch)
 
 
 def fe_ks_dinv_sqrt(ctx):

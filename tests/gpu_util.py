@@ -27,11 +27,13 @@ def round_input(X, precision):
     return X
 
 
-def gpu_apply(hp, X, precision, scaled=False, terms=fk.TERM_ALL, repeat=1):
+def gpu_apply(hp, X, precision, scaled=False, terms=fk.TERM_ALL, repeat=1, config=None):
     import torch
     n_v = X.shape[1]
     ctx = fk.fe_ks_setup(hp.struct, terms, n_v, torch.cuda.current_stream().cuda_stream)
     try:
+        if config is not None:
+            fk.fe_ks_set_config(ctx, precision, config)
         dt = torch_dtype(precision, hp.complex)
         Xd = torch.from_numpy(np.ascontiguousarray(X)).to("cuda").to(dt)
         outs = []

@@ -1,0 +1,125 @@
+"""Batched persistent launch (many uneven systems in one kernel) on the GPU.
+
+Systems follow the C5 recipe (degrees 4..8, uneven grids and vector counts,
+FP64 / FP32 alternating, GGA + projectors) on parity-sized grids.  Each
+system's result must equal its own fe_ks_apply (and, for FP64, the oracle),
+for every tunable setting, when captured in a CUDA graph and replayed, and
+the bounded waits must turn a never-published work item into
+FE_KS_ERR_TIMEOUT without losing the context.
+"""
+import numpy as np
+import pytest
+
+from paper_2512_08571_gb300 import fe_ks as fk
+from paper_2512_08571_gb300.problem import HostProblem
+from oracle.operator import Problem
+from synth import Workload, trial_vectors
+from gpu_util import rel_err_cols, torch_dtype
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GRIDS = (2, 3, 2, 3, 2, 2)
+DEGS = (4, 5, 6, 6, 7, 8)
+NVS = (3, 5, 8, 6, 4, 7)
+PREC = (fk.FE_KS_F64, fk.FE_KS_F32, fk.FE_KS_F64, fk.FE_KS_F32, fk.FE_KS_F64, fk.FE_KS_F32)
+TOL = {fk.FE_KS_F64: 1e-12, fk.FE_KS_F32: 1e-5}
+
+
+def _systems():
+    return [Workload(f"b{s}", L=3.0 * GRIDS[s], n=GRIDS[s], p=DEGS[s], nq=DEGS[s] + 1, n_v=NVS[s], gga=True,
+                     n_atoms=1 + s % 3, jitter=0.05 * (s % 2), seed=7000 + 10 * s) for s in range(6)]
+
+
+@pytest.fixture(scope="module")
+def batch_setup():
+    stream = torch.cuda.current_stream().cuda_stream
+    wls = _systems()
+    hps = [HostProblem(wl) for wl in wls]
+    ctxs = [fk.fe_ks_setup(hp.struct, fk.TERM_ALL, wl.n_v, stream) for hp, wl in zip(hps, wls)]
+    Xs, Ys, refs = [], [], []
+    for s, (wl, hp, ctx) in enumerate(zip(wls, hps, ctxs)):
+        dt = torch_dtype(PREC[s], False)
+        X = torch.from_numpy(trial_vectors(wl)).cuda().to(dt)
+        Y = torch.empty_like(X)
+        fk.fe_ks_apply(ctx, X, Y, wl.n_v, PREC[s])
+        Xs.append(X)
+        Ys.append(torch.empty_like(X))
+        refs.append(Y.clone())
+    torch.cuda.synchronize()
+    b = fk.fe_ks_batch_create(ctxs, [wl.n_v for wl in wls], list(PREC))
+    yield wls, hps, ctxs, Xs, Ys, refs, b
+    fk.fe_ks_batch_destroy(b)
+    for c in ctxs:
+        fk.fe_ks_destroy(c)
+
+
+def _check(Ys, refs):
+    for s, (Y, R) in enumerate(zip(Ys, refs)):
+        err = rel_err_cols(Y.double().cpu().numpy(), R.double().cpu().numpy())
+        assert err <= TOL[PREC[s]], (s, err)
+
+
+@pytest.mark.parametrize("tile,cells,depth", [(0, 1, 1), (1, 1, 1), (0, 3, 2), (1, 2, 4)])
+def test_batched_equals_individual_applications(batch_setup, tile, cells, depth):
+    wls, hps, ctxs, Xs, Ys, refs, b = batch_setup
+    fk.fe_ks_batch_configure(b, [tile] * 6, cells, depth, 2.0, False)
+    for Y in Ys:
+        Y.fill_(float("nan"))
+    fk.fe_ks_batch_apply(b, Xs, Ys, torch.cuda.current_stream().cuda_stream)
+    fk.fe_ks_batch_status(b)
+    _check(Ys, refs)
+
+
+def test_batched_fp64_systems_match_oracle(batch_setup):
+    wls, hps, ctxs, Xs, Ys, refs, b = batch_setup
+    fk.fe_ks_batch_configure(b, [0] * 6, 1, 1, 2.0, False)
+    fk.fe_ks_batch_apply(b, Xs, Ys, torch.cuda.current_stream().cuda_stream)
+    fk.fe_ks_batch_status(b)
+    for s in (0, 2, 4):
+        Yref = Problem(wls[s]).apply(Xs[s].cpu().numpy())
+        assert rel_err_cols(Ys[s].cpu().numpy(), Yref) <= 1e-12
+
+
+def test_batched_launch_in_cuda_graph(batch_setup):
+    wls, hps, ctxs, Xs, Ys, refs, b = batch_setup
+    fk.fe_ks_batch_configure(b, [1] * 6, 2, 2, 2.0, False)
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        fk.fe_ks_batch_apply(b, Xs, Ys, side.cuda_stream)      # warm-up outside capture
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g):
+        fk.fe_ks_batch_apply(b, Xs, Ys, torch.cuda.current_stream().cuda_stream)
+    for _ in range(2):
+        for Y in Ys:
+            Y.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        fk.fe_ks_batch_status(b)
+        _check(Ys, refs)
+
+
+def test_bounded_wait_reports_timeout_and_recovers(batch_setup):
+    wls, hps, ctxs, Xs, Ys, refs, b = batch_setup
+    fk.fe_ks_batch_configure(b, [0] * 6, 1, 1, 0.02, True)   # one phase-0 item never arrives
+    fk.fe_ks_batch_apply(b, Xs, Ys, torch.cuda.current_stream().cuda_stream)
+    with pytest.raises(fk.FeKsError, match="TIMEOUT"):
+        fk.fe_ks_batch_status(b)
+    fk.fe_ks_batch_configure(b, [0] * 6, 1, 1, 2.0, False)
+    fk.fe_ks_batch_apply(b, Xs, Ys, torch.cuda.current_stream().cuda_stream)
+    fk.fe_ks_batch_status(b)
+    _check(Ys, refs)
+
+
+def test_batched_rejects_complex_and_bad_arguments():
+    wl = Workload("cx", L=6.0, n=2, p=4, nq=5, n_v=2, kfrac=(0.2, 0, 0), complex=True, seed=1)
+    hp = HostProblem(wl)
+    ctx = fk.fe_ks_setup(hp.struct, fk.TERM_ALL, 2, torch.cuda.current_stream().cuda_stream)
+    try:
+        with pytest.raises(fk.FeKsError, match="real"):
+            fk.fe_ks_batch_create([ctx], [2], [fk.FE_KS_F64])
+    finally:
+        fk.fe_ks_destroy(ctx)

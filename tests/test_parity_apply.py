@@ -48,6 +48,22 @@ def test_apply_matches_oracle(cases, key, precision):
     assert err <= TOL[precision], err
 
 
+@pytest.mark.parametrize("config", range(fk.N_CONFIGS))
+@pytest.mark.parametrize("key", ["C2s", "C3s", "C4s"])
+def test_every_tile_configuration(cases, key, config):
+    """Every tile configuration the tuner may pick gives the same answer."""
+    wl, hp, P, X = cases[key]
+    for precision in PREC:
+        Xin = round_input(X, precision)
+        try:
+            Y = gpu_apply(hp, Xin, precision, config=config)
+        except fk.FeKsError as exc:          # configuration too large for this degree/precision
+            assert "configuration" in str(exc) or "invalid" in str(exc), exc
+            continue
+        err = rel_err_cols(Y, P.apply(Xin))
+        assert err <= TOL[precision], (config, precision, err)
+
+
 @pytest.mark.parametrize("precision", PREC)
 def test_apply_scaled_matches_oracle(cases, precision):
     wl, hp, P, X = cases["C2s"]

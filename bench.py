@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the six-system batched launch")
+    ap.add_argument("--no-filter", action="store_true", help="skip the R-ChFSI filter timing")
     ap.add_argument("--precision", choices=["both", "f64", "f32"], default="both",
                     help="f32 alone times only the FP32 application (for profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle sample")
@@ -177,11 +178,15 @@ def run_native(args, wl, rank, world):
         if world > 1:
             dist.barrier()
 
+    # the seeded trial block, generated once on the host and kept on the device
+    X64 = torch.empty((m, n_v), dtype=torch.complex128 if cplx else torch.float64, device=dev)
+    fill_trial(wl, n_v, X64, np.complex128 if cplx else np.float64)
+
     def measure(precision, steps, warmup):
-        dt = {fk.FE_KS_F64: (torch.complex128 if cplx else torch.float64, np.float64),
-              fk.FE_KS_F32: (torch.complex64 if cplx else torch.float32, np.float32)}[precision]
-        X = torch.empty((m, n_v), dtype=dt[0], device=dev)
-        fill_trial(wl, n_v, X, np.complex128 if cplx else dt[1])
+        dt = {fk.FE_KS_F64: torch.complex128 if cplx else torch.float64,
+              fk.FE_KS_F64E: torch.complex128 if cplx else torch.float64,
+              fk.FE_KS_F32: torch.complex64 if cplx else torch.float32}[precision]
+        X = X64 if dt == X64.dtype else X64.to(dt)
         Y = torch.empty_like(X)
         best, tune_ms = fk.fe_ks_tune(ctx, X, Y, n_v, precision, reps=1)
         for _ in range(warmup):
@@ -217,6 +222,7 @@ def run_native(args, wl, rank, world):
         return out
 
     f64 = measure(fk.FE_KS_F64, args.steps, args.warmup) if args.precision != "f32" else None
+    f64e = measure(fk.FE_KS_F64E, args.steps, args.warmup) if args.precision == "both" else None
     mixed = None
     if args.precision == "f32":
         mixed = measure(fk.FE_KS_F32, args.steps, args.warmup)
@@ -231,7 +237,7 @@ def run_native(args, wl, rank, world):
     if not args.no_e2e:
         tdt = torch.complex128 if cplx else torch.float64
         Xh = torch.empty((m, n_v), dtype=tdt, pin_memory=True)
-        fill_trial(wl, n_v, Xh, np.complex128 if cplx else np.float64)
+        Xh.copy_(X64)
         Yh = torch.empty_like(Xh, pin_memory=True)
         Xd = torch.empty((m, n_v), dtype=tdt, device=dev)
         Yd = torch.empty_like(Xd)
@@ -259,9 +265,92 @@ def run_native(args, wl, rank, world):
         e2e = {"value": units * world / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "ms_per_step": ms_e2e}
         del Xh, Yh, Xd, Yd
+        torch.cuda.empty_cache()
+    filt = None
+    if not args.no_filter and rank == 0 and not cplx:
+        filt = run_filter(args, wl, ctx, hp, X64)
+    del X64
+    torch.cuda.empty_cache()
     fk.fe_ks_destroy(ctx)
-    return dict(f64=f64, mixed=mixed, e2e=e2e, setup_s=setup_s, info=info, local_flops=local_flops,
+    return dict(filter=filt, f64e=f64e, f64=f64, mixed=mixed, e2e=e2e, setup_s=setup_s, info=info, local_flops=local_flops,
                 peak64_live=peak64_live, peak32_live=peak32_live)
+
+
+# ------------------------------------------------------------ R-ChFSI filter
+def run_filter(args, wl, ctx, hp, X64):
+    """One R-ChFSI pass on the workload (Lanczos bound, degree-20 filter,
+    Rayleigh-Ritz), all-FP64 against the mixed filter (FP32 recurrence), plus a
+    convergence run on the same recipe at 8^3 cells (N_v = 64) to residual
+    1e-9 with both filters, reporting iterations and the eigenvalue gap."""
+    import numpy as np
+    import torch
+    from paper_2512_08571_gb300 import fe_ks as fk
+    from paper_2512_08571_gb300.chfsi import RChFSI
+    from paper_2512_08571_gb300.problem import HostProblem
+    stream = torch.cuda.current_stream()
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    def ev_ms(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), out
+
+    out = {"degree": 20, "lanczos_steps": 10}
+    # cost of one application against the number of vectors (Lanczos uses n_v = 1)
+    nv_ms = {}
+    for nv in (1, 8, 64):
+        Xa = X64[:, :nv].contiguous()
+        Ya = torch.empty_like(Xa)
+        fk.fe_ks_apply(ctx, Xa, Ya, nv, fk.FE_KS_F64)
+        nv_ms[nv], _ = ev_ms(lambda: fk.fe_ks_apply(ctx, Xa, Ya, nv, fk.FE_KS_F64))
+        del Xa, Ya
+    out["f64_apply_ms_by_n_v"] = nv_ms
+    m, n_v = hp.m, wl.n_v
+    X0 = X64.clone()
+    s64 = RChFSI(ctx, m, n_v, False, degree=20, precision=fk.FE_KS_F64)
+    out["lanczos_ms"], lmax = ev_ms(s64.lanczos_upper_bound)
+    out["rayleigh_ritz_ms"], (lam, X) = ev_ms(lambda: s64.rayleigh_ritz(X0))
+    del X0
+    X1 = X.clone()
+    out["filter_f64_ms"], _ = ev_ms(lambda: s64.filter(X1, lam))
+    del X1, s64
+    torch.cuda.empty_cache()
+    s32 = RChFSI(ctx, m, n_v, False, degree=20, precision=fk.FE_KS_F32)
+    s32.lmax = lmax
+    X2 = X.clone()
+    s32.filter(X2, lam)                       # warm-up
+    X2 = X.clone()
+    out["filter_mixed_ms"], _ = ev_ms(lambda: s32.filter(X2, lam))
+    del X2, s32, X
+    torch.cuda.empty_cache()
+    p64 = out["lanczos_ms"] + out["filter_f64_ms"] + out["rayleigh_ritz_ms"]
+    pmx = out["lanczos_ms"] + out["filter_mixed_ms"] + out["rayleigh_ritz_ms"]
+    out.update(pass_f64_ms=p64, pass_mixed_ms=pmx, speedup_pass=p64 / pmx,
+               speedup_filter=out["filter_f64_ms"] / out["filter_mixed_ms"])
+    # convergence at 6^3 cells
+    wls = wl.scaled(n=6, n_v=32)
+    hps = HostProblem(wls)
+    cs = fk.fe_ks_setup(hps.struct, fk.TERM_ALL, wls.n_v, stream.cuda_stream)
+    Xs0 = torch.empty((hps.m, wls.n_v), dtype=torch.float64, device=dev)
+    fill_trial(wls, wls.n_v, Xs0, np.float64)
+    n_chk = wls.n_v // 2
+    conv = {"workload": f"same recipe, 6^3 cells, N_v={wls.n_v}, residual < 1e-9 on the lowest {n_chk}"}
+    lams = {}
+    for name, prec in (("f64", fk.FE_KS_F64), ("mixed", fk.FE_KS_F32)):
+        sol = RChFSI(cs, hps.m, wls.n_v, False, degree=20, precision=prec)
+        t, (lam_c, _, res, its) = ev_ms(lambda: sol.run(Xs0.clone(), n_iter=60, tol=1e-9, n_check=n_chk))
+        lams[name] = lam_c.cpu().numpy()
+        conv[name] = {"iterations": its, "ms": t, "max_residual": float(res[:n_chk].max())}
+        del sol
+    conv["max_eig_diff_mixed_vs_f64_Ha"] = float(np.max(np.abs(lams["mixed"][:n_chk] - lams["f64"][:n_chk])))
+    conv["speedup"] = conv["f64"]["ms"] / conv["mixed"]["ms"]
+    out["converged_6cubed"] = conv
+    fk.fe_ks_destroy(cs)
+    return out
 
 
 # -------------------------------------------------------- batched systems
@@ -311,17 +400,19 @@ def run_batched(args):
     b = fk.fe_ks_batch_create(ctxs, [wl.n_v for wl in wls], prec)
     best = None
     trials = []
-    for tile in (0, 1):
-        for cells in (1, 2, 4):
-            for depth in (1, 2):
-                fk.fe_ks_batch_configure(b, [tile] * len(wls), cells, depth, 2.0, False)
-                ms = timed(lambda: fk.fe_ks_batch_apply(b, Xs, Ys, stream.cuda_stream), 2)
-                fk.fe_ks_batch_status(b)
-                trials.append({"tile": tile, "cells_per_item": cells, "depth": depth, "ms": round(ms, 3)})
-                if best is None or ms < best[0]:
-                    best = (ms, tile, cells, depth)
-    _, tile, cells, depth = best
-    fk.fe_ks_batch_configure(b, [tile] * len(wls), cells, depth, 2.0, False)
+    for occ in (1, 2):
+        for tile in (0, 1):
+            for cells in (1, 2, 4):
+                for depth in (1, 2):
+                    fk.fe_ks_batch_configure(b, [tile] * len(wls), cells, depth, 2.0, False, blocks_per_sm=occ)
+                    ms = timed(lambda: fk.fe_ks_batch_apply(b, Xs, Ys, stream.cuda_stream), 2)
+                    fk.fe_ks_batch_status(b)
+                    trials.append({"blocks_per_sm": occ, "tile": tile, "cells_per_item": cells, "depth": depth,
+                                   "ms": round(ms, 3)})
+                    if best is None or ms < best[0]:
+                        best = (ms, tile, cells, depth, occ)
+    _, tile, cells, depth, occ = best
+    fk.fe_ks_batch_configure(b, [tile] * len(wls), cells, depth, 2.0, False, blocks_per_sm=occ)
     g = torch.cuda.CUDAGraph()
     side = torch.cuda.Stream()
     side.wait_stream(stream)
@@ -343,7 +434,7 @@ def run_batched(args):
             "value": units / (ms_graph * 1e-3), "unit": UNIT, "ms_per_step": ms_graph,
             "one_launch_per_system": {"value": units / (ms_sep * 1e-3), "ms_per_step": ms_sep},
             "speedup_vs_separate": ms_sep / ms_graph,
-            "tuned": {"tile_config": tile, "cells_per_item": cells, "depth": depth},
+            "tuned": {"tile_config": tile, "cells_per_item": cells, "depth": depth, "blocks_per_sm": occ},
             "tuning_trials": trials, "items": info["n_items"], "grid": info["grid"],
             "smem_bytes": info["smem_bytes"], "graph": True, "x_inputs": "device RNG (seed 5000), U(-1,1)"}
 
@@ -450,6 +541,17 @@ def main():
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded mesh, fields, atoms, X)",
             "config": config, "roofline": roofline, "clocks": f64["clocks"],
             "gpu_launches": f64["launches"], "setup_s": res["setup_s"]}
+    if res.get("f64e"):
+        e = res["f64e"]
+        ach = e["achieved"]
+        line["f64_pairs_of_fp32"] = {
+            "dtype": "f32x2 (FP64 in/out, FP64-accurate: parity <= 1e-12 vs the oracle)", "value": e["value"],
+            "unit": UNIT, "ms_per_step": e["ms"], "speedup_vs_f64": f64["ms"] / e["ms"],
+            "roofline": {"bound": "alu", "achieved_alg_fp64_equiv": ach / 1e12 if ach else None, "unit": "TFLOP/s",
+                         "frac_of_nominal_fp64": ach / PEAK_FP64_NOMINAL if ach else None,
+                         "avg_launch_ms": e["local_launch_ms"], "tile_config": e["tile_config"],
+                         "tune_ms_per_config": e["tune_ms"]},
+            "clocks": e["clocks"], "gpu_launches": e["launches"]}
     mixed = res["mixed"]
     if mixed:
         ach = mixed["achieved"]
@@ -465,6 +567,8 @@ def main():
                          "clocks": mixed["clocks"], "gpu_launches": mixed["launches"]}
     if res["e2e"]:
         line["e2e"] = res["e2e"]
+    if res["filter"]:
+        line["filter"] = res["filter"]
     if not args.no_batched:
         line["batched"] = run_batched(args)
     if world == 1 and not args.no_cpu_baseline:

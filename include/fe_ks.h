@@ -57,7 +57,10 @@ typedef enum {
 /* Arithmetic of one application. */
 typedef enum {
   FE_KS_F64 = 0,               /* FP64 storage and FP64 arithmetic (DFMA)                  */
-  FE_KS_F32 = 1                /* FP32 storage and FP32 arithmetic (FFMA)                  */
+  FE_KS_F32 = 1,               /* FP32 storage and FP32 arithmetic (FFMA)                  */
+  FE_KS_F64E = 2               /* FP64 storage, FP64-accurate result; the cell kernel works
+                                  in pairs of floats (hi + lo, ~48 bits) on the FP32 pipe,
+                                  the projections in FP64 (apply / apply_scaled / tune only) */
 } fe_ks_precision;
 
 /* Terms of H that an application includes (terms_mask of fe_ks_setup). */
@@ -180,15 +183,17 @@ fe_ks_status fe_ks_cheb_filter(fe_ks_ctx* ctx, double* X, const double* ritz, in
                                size_t work_bytes);
 
 /*
- * Tile configuration of the fused cell kernel (columns per CTA tile and block
- * size; 0 is the default, FE_KS_N_CONFIGS choices).  fe_ks_tune times every
+ * Tile configuration of the fused cell kernel: 0..2 run one CTA per (cell,
+ * column tile) with 3 tile widths; 3..4 run one CTA per cell walking all
+ * column tiles with the next tile's rows of X staged by cp.async and a
+ * reduction-based scatter.  0 is the default, FE_KS_N_CONFIGS choices.  fe_ks_tune times every
  * configuration with fe_ks_apply on the caller's X and Y (reps timed calls
  * each, after one untimed call), keeps the fastest for this context and
  * precision, and reports the milliseconds per call (-1 for a configuration
  * that cannot launch, e.g. shared memory too large) and the choice.
  * fe_ks_set_config sets it directly.  Y is overwritten.
  */
-#define FE_KS_N_CONFIGS 3
+#define FE_KS_N_CONFIGS 5
 fe_ks_status fe_ks_tune(fe_ks_ctx* ctx, const void* X, void* Y, int64_t n_v, int precision, int reps,
                         double* ms_per_config, int* best);
 fe_ks_status fe_ks_set_config(fe_ks_ctx* ctx, int precision, int config);
@@ -205,7 +210,8 @@ fe_ks_status fe_ks_set_config(fe_ks_ctx* ctx, int precision, int config);
  * caller, must outlive the batch), vector counts and precisions (FE_KS_F64 /
  * FE_KS_F32); it allocates the queue and counters (the only allocation).
  * fe_ks_batch_configure sets the tunables -- tile configuration per system
- * (0/1: columns per tile), cells per work item, items claimed per fetch --
+ * (0/1: columns per tile), cells per work item, items claimed per fetch,
+ * resident CTAs per SM (1, or 2 with a tighter register budget) --
  * plus the bounded-wait limit in seconds, and inject_missing_item = 1 makes
  * the host count one phase-0 item that is never published (fault injection:
  * the launch then ends with FE_KS_ERR_TIMEOUT reported by fe_ks_batch_status).
@@ -219,7 +225,7 @@ typedef struct fe_ks_batch fe_ks_batch;
 fe_ks_status fe_ks_batch_create(fe_ks_ctx* const* ctxs, int n_sys, const int64_t* n_v, const int* precision,
                                 fe_ks_batch** out);
 fe_ks_status fe_ks_batch_configure(fe_ks_batch* b, const int* tile_config, int cells_per_item, int depth,
-                                   double wait_seconds, int inject_missing_item);
+                                   int blocks_per_sm, double wait_seconds, int inject_missing_item);
 fe_ks_status fe_ks_batch_apply(fe_ks_batch* b, const void* const* X, void* const* Y, void* cuda_stream);
 fe_ks_status fe_ks_batch_status(fe_ks_batch* b);
 fe_ks_status fe_ks_batch_info(const fe_ks_batch* b, int* n_items, int* grid, size_t* smem_bytes);

@@ -7,13 +7,14 @@
 #include <cstring>
 #include <functional>
 #include <thread>
+#include <type_traits>
 
 #include "fe_ks_internal.h"
 
 namespace feks {
 
-template <typename T, int P>
-cudaError_t launch_local_deg(const Ctx&, const LocalParams<T>&, cudaStream_t);
+template <typename T, typename TS, int P>
+cudaError_t launch_local_deg(const Ctx&, const LocalParams<T, TS>&, cudaStream_t);
 
 static thread_local std::string g_last_error;
 
@@ -24,17 +25,17 @@ fe_ks_status fail(fe_ks_status code, const std::string& msg) {
   return code;
 }
 
-template <typename T>
-cudaError_t launch_local(const Ctx& c, const LocalParams<T>& prm, cudaStream_t s) {
+template <typename T, typename TS>
+cudaError_t launch_local(const Ctx& c, const LocalParams<T, TS>& prm, cudaStream_t s) {
   switch (c.p) {
-    case 1: return launch_local_deg<T, 1>(c, prm, s);
-    case 2: return launch_local_deg<T, 2>(c, prm, s);
-    case 3: return launch_local_deg<T, 3>(c, prm, s);
-    case 4: return launch_local_deg<T, 4>(c, prm, s);
-    case 5: return launch_local_deg<T, 5>(c, prm, s);
-    case 6: return launch_local_deg<T, 6>(c, prm, s);
-    case 7: return launch_local_deg<T, 7>(c, prm, s);
-    case 8: return launch_local_deg<T, 8>(c, prm, s);
+    case 1: return launch_local_deg<T, TS, 1>(c, prm, s);
+    case 2: return launch_local_deg<T, TS, 2>(c, prm, s);
+    case 3: return launch_local_deg<T, TS, 3>(c, prm, s);
+    case 4: return launch_local_deg<T, TS, 4>(c, prm, s);
+    case 5: return launch_local_deg<T, TS, 5>(c, prm, s);
+    case 6: return launch_local_deg<T, TS, 6>(c, prm, s);
+    case 7: return launch_local_deg<T, TS, 7>(c, prm, s);
+    case 8: return launch_local_deg<T, TS, 8>(c, prm, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -215,6 +216,7 @@ fe_ks_status fe_ks_setup(const fe_ks_problem* prob, int terms_mask, int64_t n_v_
   gauss_lobatto(np, xl, wl);
   build_eo_tables<double>(c->p, nq, &c->f64.tab);
   build_eo_tables<float>(c->p, nq, &c->f32.tab);
+  build_eo_tables<ff2>(c->p, nq, &c->emu.tab);
 
   // ---- per-point coefficients (eq. reformcellmat with det J w_Q and J^-1 folded in)
   const int ncoef = c->ncoef;
@@ -425,16 +427,25 @@ fe_ks_status fe_ks_setup(const fe_ks_problem* prob, int terms_mask, int64_t n_v_
   };
   std::vector<double> ds(m);
   for (int64_t i = 0; i < m; ++i) ds[i] = 1.0 / std::sqrt(D[i]);
+  std::vector<ff2> tmpff;
+  auto toff = [&](const std::vector<double>& v) {
+    tmpff.resize(v.size());
+    for (size_t i = 0; i < v.size(); ++i) tmpff[i] = ff_from_double_host(v[i]);
+    return tmpff.data();
+  };
   bool ok = chk(upload(c, &c->cell_dofs, prob->cell_dofs, (size_t)E * np3)) &&
             chk(upload(c, &c->colour_cells, colour_cells.data(), colour_cells.size())) &&
             chk(upload(c, &c->f64.coef, coef.data(), coef.size())) &&
             chk(upload(c, &c->f32.coef, to32(coef), coef.size())) &&
             chk(upload(c, &c->f64.dscale, ds.data(), ds.size())) &&
-            chk(upload(c, &c->f32.dscale, to32(ds), ds.size()));
+            chk(upload(c, &c->f32.dscale, to32(ds), ds.size())) &&
+            chk(upload(c, reinterpret_cast<ff2**>(&c->emu.coef), toff(coef), coef.size())) &&
+            chk(upload(c, reinterpret_cast<ff2**>(&c->emu.dscale), toff(ds), ds.size()));
   if (ok && want_nl) {
     std::vector<double> hh(prob->h_coef, prob->h_coef + (size_t)prob->n_atoms * prob->n_proj);
     const size_t qn = (size_t)prob->n_atoms * prob->n_proj * n_v_max * (c->cplx ? 2 : 1);
     ok = chk(upload(c, &c->f64.F, F.data(), F.size())) && chk(upload(c, &c->f32.F, to32(F), F.size())) &&
+         chk(upload(c, reinterpret_cast<ff2**>(&c->emu.F), toff(F), F.size())) &&
          chk(upload(c, &c->h64, hh.data(), hh.size())) && chk(upload(c, &c->h32, to32(hh), hh.size())) &&
          chk(upload(c, &c->pair_atom, pair_atom.data(), pair_atom.size())) &&
          chk(upload(c, &c->pair_cell, pair_cell.data(), pair_cell.size())) &&
@@ -580,7 +591,7 @@ fe_ks_status apply_core(Ctx& c, const T* X, T* Y, int64_t ncols, bool scaled, T 
   for (size_t col = 0; col + 1 < c.colour_ptr.size(); ++col) {
     lp.cells = c.colour_cells + c.colour_ptr[col];
     lp.n_cells = c.colour_ptr[col + 1] - c.colour_ptr[col];
-    cudaError_t err = launch_local<T>(c, lp, s);
+    cudaError_t err = launch_local<T, T>(c, lp, s);
     if (err != cudaSuccess) return fail(FE_KS_ERR_CUDA, std::string("local kernel: ") + cudaGetErrorString(err));
     if (lp.n_cells > 0) nlaunch[2]++;
   }
@@ -595,21 +606,101 @@ fe_ks_status apply_core(Ctx& c, const T* X, T* Y, int64_t ncols, bool scaled, T 
 template fe_ks_status apply_core<double>(Ctx&, const double*, double*, int64_t, bool, double, bool);
 template fe_ks_status apply_core<float>(Ctx&, const float*, float*, int64_t, bool, float, bool);
 
+// FP64-accurate application computed in pairs of floats: FP64 projections,
+// pair-of-floats cell kernel with FP64 gather / scatter (alpha is applied in
+// the pair arithmetic).
+fe_ks_status apply_core_emu(Ctx& c, const double* X, double* Y, int64_t ncols, bool scaled, double alpha,
+                            bool zero_fill) {
+  cudaStream_t s = c.stream;
+  const size_t bytes = (size_t)c.m * ncols * sizeof(double);
+  std::array<cudaEvent_t, 4> ev{};
+  std::array<int, 3> nlaunch{zero_fill ? 1 : 0, 0, 0};
+  auto mark = [&](int i) {
+    if (!c.profiling) return;
+    if (c.ev_pool.empty()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      c.ev_pool.push_back(e);
+    }
+    ev[i] = c.ev_pool.back();
+    c.ev_pool.pop_back();
+    cudaEventRecord(ev[i], s);
+  };
+  mark(0);
+  if (zero_fill && cudaMemsetAsync(Y, 0, bytes, s) != cudaSuccess) return fail(FE_KS_ERR_CUDA, "cudaMemsetAsync failed");
+  mark(1);
+  const bool nl = (c.terms & FE_KS_TERM_NL) && c.n_pairs > 0;
+  if (nl) {
+    ProjParams<double> pp{};
+    pp.X = X;
+    pp.ld = ncols;
+    pp.ncols = (int)ncols;
+    pp.cell_dofs = c.cell_dofs;
+    pp.atom_pair_ptr = c.atom_pair_ptr;
+    pp.pair_cell = c.pair_cell;
+    pp.F = c.f64.F;
+    pp.h = c.h64;
+    pp.dscale = scaled ? c.f64.dscale : nullptr;
+    pp.Q = c.f64.Q;
+    pp.n_proj = c.n_proj;
+    pp.np3 = c.np3;
+    cudaError_t err = launch_proj<double>(c, pp, c.n_atoms, s);
+    if (err != cudaSuccess) return fail(FE_KS_ERR_CUDA, std::string("projection kernel: ") + cudaGetErrorString(err));
+    nlaunch[1] = 1;
+  }
+  mark(2);
+  LocalParams<ff2, double> lp{};
+  lp.X = X;
+  lp.Y = Y;
+  lp.ld = ncols;
+  lp.ncols = (int)ncols;
+  lp.cell_dofs = c.cell_dofs;
+  lp.coef = static_cast<const ff2*>(c.emu.coef);
+  lp.ncoef = c.ncoef;
+  lp.gga = c.gga;
+  lp.dscale = scaled ? static_cast<const ff2*>(c.emu.dscale) : nullptr;
+  lp.cell_pair_ptr = nl ? c.cell_pair_ptr : nullptr;
+  lp.cell_pairs = c.cell_pairs;
+  lp.pair_atom = c.pair_atom;
+  lp.F = static_cast<const ff2*>(c.emu.F);
+  lp.Q = c.f64.Q;
+  lp.n_proj = c.n_proj;
+  lp.alpha = ff_from_double_host(alpha);
+  lp.tab = c.emu.tab;
+  for (size_t col = 0; col + 1 < c.colour_ptr.size(); ++col) {
+    lp.cells = c.colour_cells + c.colour_ptr[col];
+    lp.n_cells = c.colour_ptr[col + 1] - c.colour_ptr[col];
+    cudaError_t err = launch_local<ff2, double>(c, lp, s);
+    if (err != cudaSuccess) return fail(FE_KS_ERR_CUDA, std::string("local kernel: ") + cudaGetErrorString(err));
+    if (lp.n_cells > 0) nlaunch[2]++;
+  }
+  mark(3);
+  if (c.profiling) {
+    c.ev_rec.push_back(ev);
+    c.ev_launches.push_back(nlaunch);
+  }
+  return FE_KS_OK;
+}
+
 template <typename T>
 static fe_ks_status apply_impl(fe_ks_ctx* ctx, const void* Xv, void* Yv, int64_t n_v, bool scaled) {
+  using TS = typename std::conditional<std::is_same<T, ff2>::value, double, T>::type;
   g_last_error.clear();
   if (!ctx) return fail(FE_KS_ERR_ARG, "ctx is NULL");
   Ctx& c = ctx->c;
   if (!Xv || !Yv) return fail(FE_KS_ERR_ARG, "X or Y is NULL");
   if (n_v < 1 || n_v > c.n_v_max) return fail(FE_KS_ERR_ARG, "n_v must be in 1..n_v_max");
-  if (((uintptr_t)Xv % sizeof(T)) || ((uintptr_t)Yv % sizeof(T)))
+  if (((uintptr_t)Xv % sizeof(TS)) || ((uintptr_t)Yv % sizeof(TS)))
     return fail(FE_KS_ERR_ARG, "X and Y must be aligned to the scalar size");
   const int64_t ncols = n_v * (c.cplx ? 2 : 1);
-  const size_t bytes = (size_t)c.m * ncols * sizeof(T);
+  const size_t bytes = (size_t)c.m * ncols * sizeof(TS);
   const char* xb = static_cast<const char*>(Xv);
   const char* yb = static_cast<const char*>(Yv);
   if (xb < yb + bytes && yb < xb + bytes) return fail(FE_KS_ERR_ARG, "X and Y overlap");
-  return apply_core<T>(c, static_cast<const T*>(Xv), static_cast<T*>(Yv), ncols, scaled, T(1), true);
+  if constexpr (std::is_same<T, ff2>::value)
+    return apply_core_emu(c, static_cast<const double*>(Xv), static_cast<double*>(Yv), ncols, scaled, 1.0, true);
+  else
+    return apply_core<T>(c, static_cast<const T*>(Xv), static_cast<T*>(Yv), ncols, scaled, T(1), true);
 }
 
 }  // namespace feks
@@ -618,6 +709,7 @@ extern "C" {
 
 fe_ks_status fe_ks_apply(fe_ks_ctx* ctx, const void* X, void* Y, int64_t n_v, int precision) {
   if (precision == FE_KS_F64) return apply_impl<double>(ctx, X, Y, n_v, false);
+  if (precision == FE_KS_F64E) return apply_impl<ff2>(ctx, X, Y, n_v, false);
   if (precision == FE_KS_F32) return apply_impl<float>(ctx, X, Y, n_v, false);
   return fail(FE_KS_ERR_UNSUPPORTED, "unknown precision");
 }
@@ -629,6 +721,8 @@ fe_ks_status fe_ks_set_config(fe_ks_ctx* ctx, int precision, int config) {
     ctx->c.cfg64 = config;
   else if (precision == FE_KS_F32)
     ctx->c.cfg32 = config;
+  else if (precision == FE_KS_F64E)
+    ctx->c.cfgE = config;
   else
     return fail(FE_KS_ERR_UNSUPPORTED, "unknown precision");
   return FE_KS_OK;
@@ -638,10 +732,11 @@ fe_ks_status fe_ks_tune(fe_ks_ctx* ctx, const void* X, void* Y, int64_t n_v, int
                         double* ms_per_config, int* best) {
   g_last_error.clear();
   if (!ctx || !X || !Y) return fail(FE_KS_ERR_ARG, "NULL argument");
-  if (precision != FE_KS_F64 && precision != FE_KS_F32) return fail(FE_KS_ERR_UNSUPPORTED, "unknown precision");
+  if (precision != FE_KS_F64 && precision != FE_KS_F32 && precision != FE_KS_F64E)
+    return fail(FE_KS_ERR_UNSUPPORTED, "unknown precision");
   if (reps < 1) reps = 1;
   Ctx& c = ctx->c;
-  int& cfg = precision == FE_KS_F64 ? c.cfg64 : c.cfg32;
+  int& cfg = precision == FE_KS_F64 ? c.cfg64 : (precision == FE_KS_F32 ? c.cfg32 : c.cfgE);
   const int keep = cfg;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -679,6 +774,7 @@ fe_ks_status fe_ks_tune(fe_ks_ctx* ctx, const void* X, void* Y, int64_t n_v, int
 
 fe_ks_status fe_ks_apply_scaled(fe_ks_ctx* ctx, const void* X, void* Y, int64_t n_v, int precision) {
   if (precision == FE_KS_F64) return apply_impl<double>(ctx, X, Y, n_v, true);
+  if (precision == FE_KS_F64E) return apply_impl<ff2>(ctx, X, Y, n_v, true);
   if (precision == FE_KS_F32) return apply_impl<float>(ctx, X, Y, n_v, true);
   return fail(FE_KS_ERR_UNSUPPORTED, "unknown precision");
 }

@@ -199,7 +199,8 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
   return v;
 }
 
-__global__ void __launch_bounds__(kBatchNT, 1) fe_batched_kernel(const __grid_constant__ BatchParams bp) {
+template <int MINB>
+__global__ void __launch_bounds__(kBatchNT, MINB) fe_batched_kernel(const __grid_constant__ BatchParams bp) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_base, s_stop;
   for (;;) {
@@ -286,6 +287,7 @@ struct fe_ks_batch {
   std::vector<int> cfg;
   int cells_per_item = 1;
   int depth = 1;
+  int blocks_per_sm = 1;     // 1: registers for every variant; 2: two CTAs per SM, some spills
   double wait_seconds = 2.0;
   int inject_missing = 0;
   int device = 0;
@@ -351,10 +353,14 @@ static fe_ks_status batch_build(fe_ks_batch* b) {
   cudaMemcpy(b->d_need, need.data(), need.size() * sizeof(int), cudaMemcpyHostToDevice);
   b->n_items = (int)items.size();
   b->smem = smem;
-  if (cudaFuncSetAttribute(fe_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  if (cudaFuncSetAttribute(fe_batched_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaFuncSetAttribute(fe_batched_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return fail(FE_KS_ERR_CUDA, "batched kernel shared memory");
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fe_batched_kernel, kBatchNT, smem);
+  if (b->blocks_per_sm == 2)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fe_batched_kernel<2>, kBatchNT, smem);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fe_batched_kernel<1>, kBatchNT, smem);
   b->grid = std::max(1, per_sm) * b->sms;
   // kernel parameters
   BatchParams& P = b->host;
@@ -446,8 +452,10 @@ fe_ks_status fe_ks_batch_create(fe_ks_ctx* const* ctxs, int n_sys, const int64_t
 }
 
 fe_ks_status fe_ks_batch_configure(fe_ks_batch* b, const int* tile_config, int cells_per_item, int depth,
-                                   double wait_seconds, int inject_missing_item) {
+                                   int blocks_per_sm, double wait_seconds, int inject_missing_item) {
   if (!b) return fail(FE_KS_ERR_ARG, "batch is NULL");
+  if (blocks_per_sm != 1 && blocks_per_sm != 2) return fail(FE_KS_ERR_ARG, "blocks_per_sm must be 1 or 2");
+  b->blocks_per_sm = blocks_per_sm;
   if (cells_per_item < 1 || cells_per_item > 64 || depth < 1 || depth > 16 || !(wait_seconds > 0))
     return fail(FE_KS_ERR_ARG, "cells_per_item in 1..64, depth in 1..16, wait_seconds > 0");
   if (tile_config)
@@ -473,7 +481,10 @@ fe_ks_status fe_ks_batch_apply(fe_ks_batch* b, const void* const* X, void* const
   }
   if (cudaMemsetAsync(b->d_state, 0, sizeof(int) * (2 + kMaxSys * kMaxPhase), s) != cudaSuccess)
     return fail(FE_KS_ERR_CUDA, "reset of the batch counters failed");
-  fe_batched_kernel<<<b->grid, kBatchNT, b->smem, s>>>(P);
+  if (b->blocks_per_sm == 2)
+    fe_batched_kernel<2><<<b->grid, kBatchNT, b->smem, s>>>(P);
+  else
+    fe_batched_kernel<1><<<b->grid, kBatchNT, b->smem, s>>>(P);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return fail(FE_KS_ERR_CUDA, std::string("batched kernel: ") + cudaGetErrorString(err));
   return FE_KS_OK;

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/fe_ks.h"
+#include "fe_ks_ff.cuh"
 
 namespace feks {
 
@@ -52,11 +53,13 @@ struct OpData {
   EOTables<T> tab;
 };
 
-// Kernel parameters of the fused local kernel (one colour of cells).
-template <typename T>
+// Kernel parameters of the fused local kernel (one colour of cells).  T is
+// the arithmetic type, TS the storage type of X, Y and the projections Q
+// (they differ only for the pair-of-floats FP64 variant).
+template <typename T, typename TS = T>
 struct LocalParams {
-  const T* X;
-  T* Y;
+  const TS* X;
+  TS* Y;
   int64_t ld;              // row pitch of X and Y in scalars (= ncols)
   int ncols;               // real columns (complex: 2 n_v)
   const int* cell_dofs;    // [E][n_p^3]
@@ -71,7 +74,7 @@ struct LocalParams {
   const int* cell_pairs;
   const int* pair_atom;
   const T* F;
-  const T* Q;              // [n_atoms][n_proj][ld], already scaled by Delta
+  const TS* Q;             // [n_atoms][n_proj][ld], already scaled by Delta
   int n_proj;
   T alpha;                 // Y += alpha * (H X) (1 for a plain application)
   EOTables<T> tab;
@@ -97,7 +100,7 @@ struct ProjParams {
 struct Ctx {
   int p = 0, nq = 0, np = 0, np3 = 0, nq3 = 0;
   int cplx = 0, terms = 0, gga = 0, ncoef = 0;
-  int cfg64 = 0, cfg32 = 0;      // tile configuration of the fused kernel per precision
+  int cfg64 = 0, cfg32 = 0, cfgE = 0;   // tile configuration of the fused kernel per precision
   int64_t E = 0, m = 0, n_v_max = 0;
   int n_atoms = 0, n_proj = 0;
   int64_t n_pairs = 0;
@@ -116,6 +119,14 @@ struct Ctx {
   float* h32 = nullptr;
   OpData<double> f64;
   OpData<float> f32;
+  // pair-of-floats copies of the coefficients, projector matrices, D^{-1/2}
+  // and 1D tables for the FP64-accurate FP32-pipe variant
+  struct {
+    void* coef = nullptr;
+    void* F = nullptr;
+    void* dscale = nullptr;
+    EOTables<ff2> tab;
+  } emu;
   std::vector<void*> allocations;
   // profiling: events recorded per application (start, after fill, after projection, after local)
   bool profiling = false;
@@ -134,16 +145,20 @@ void gauss_lobatto(int n, double* x, double* w);
 void lagrange_eval(int n, const double* nodes, double x, double* val, double* der);
 template <typename T>
 void build_eo_tables(int p, int nq, EOTables<T>* out);
+template <>
+void build_eo_tables<ff2>(int p, int nq, EOTables<ff2>* out);
 
 // Y (+)= alpha H X or alpha Hs X on the context's stream; zero_fill clears Y first.
 template <typename T>
 fe_ks_status apply_core(Ctx& c, const T* X, T* Y, int64_t ncols, bool scaled, T alpha, bool zero_fill);
+fe_ks_status apply_core_emu(Ctx& c, const double* X, double* Y, int64_t ncols, bool scaled, double alpha,
+                            bool zero_fill);
 
-constexpr int kLocalConfigs = 3;
+constexpr int kLocalConfigs = 5;
 
 // kernel launchers (fe_ks_local_pN.cu)
-template <typename T>
-cudaError_t launch_local(const Ctx& c, const LocalParams<T>& prm, cudaStream_t s);
+template <typename T, typename TS>
+cudaError_t launch_local(const Ctx& c, const LocalParams<T, TS>& prm, cudaStream_t s);
 template <typename T>
 cudaError_t launch_proj(const Ctx& c, const ProjParams<T>& prm, int n_atoms, cudaStream_t s);
 

@@ -14,9 +14,34 @@
 // (fixed NT).  No register state survives a barrier: the pointwise phase
 // writes its partial sum back into tile A, which is free at that point.
 #pragma once
+#include <type_traits>
+
 #include "fe_ks_internal.h"
 
 namespace feks {
+
+// Arithmetic-type traits: zero, conversion from the storage type, the
+// scatter-add into the storage type, and the re/im partner shuffle.
+template <typename T>
+struct Num {
+  static __device__ __forceinline__ T zero() { return T(0); }
+  static __device__ __forceinline__ T one() { return T(1); }
+  template <typename TS>
+  static __device__ __forceinline__ T in(TS x) { return (T)x; }
+  template <typename TS>
+  static __device__ __forceinline__ void add_to(TS* y, T v) { *y += v; }
+  static __device__ __forceinline__ T shfl1(T v) { return __shfl_xor_sync(0xffffffffu, v, 1); }
+};
+template <>
+struct Num<ff2> {
+  static __device__ __forceinline__ ff2 zero() { return ff_make(0.f, 0.f); }
+  static __device__ __forceinline__ ff2 one() { return ff_make(1.f, 0.f); }
+  static __device__ __forceinline__ ff2 in(double x) { return ff_from_double(x); }
+  static __device__ __forceinline__ void add_to(double* y, ff2 v) { *y += ff_to_double(v); }
+  static __device__ __forceinline__ ff2 shfl1(ff2 v) {
+    return ff_make(__shfl_xor_sync(0xffffffffu, v.hi, 1), __shfl_xor_sync(0xffffffffu, v.lo, 1));
+  }
+};
 
 // y = M x for an NO x NI matrix with M[NO-1-o][NI-1-i] = S M[o][i], given its
 // even-odd split (see EOMat).  All indices are compile-time constants, so the
@@ -67,11 +92,14 @@ struct CellShape {
   static constexpr int SX = VT, SY = PY * VT, SZ = NQ * SY, BUF = NQ * SZ;
   static constexpr int NQ3 = NQ * NQ * NQ, NP3 = NP * NP * NP;
   static constexpr int NCOEF = CPLX ? kCoefCplx : kCoefReal;
+  // coefficient block padded to a multiple of 16 bytes, so that what follows
+  // it stays 16-byte aligned (cp.async of 16 bytes needs aligned targets)
+  static constexpr int CF_ELEMS = ((NCOEF * NQ3 * (int)sizeof(T) + 15) / 16) * 16 / (int)sizeof(T);
   // FP32 stages the cell's coefficients in shared memory (its loads are latency
   // bound); FP64 is bound by the FP64 pipe and keeps the occupancy instead.
   static constexpr bool STAGE_COEF = sizeof(T) == 4;
   static constexpr size_t bytes =
-      (size_t)(3 * BUF + (STAGE_COEF ? NCOEF * NQ3 : 0)) * sizeof(T) + (size_t)NP3 * sizeof(int);
+      (size_t)(3 * BUF + (STAGE_COEF ? CF_ELEMS : 0)) * sizeof(T) + (size_t)NP3 * sizeof(int);
   static constexpr bool fits = bytes <= 227 * 1024;
 };
 
@@ -84,39 +112,16 @@ __device__ __forceinline__ void cp_async_8(void* smem, const void* gmem) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 
-// One cell e, columns [col0, col0 + VT).  All NT threads of the block call it.
-// Prm is any struct with the operand fields of LocalParams (X, Y, ld, ncols,
-// cell_dofs, coef, ncoef, gga, dscale, cell_pair_ptr, cell_pairs, pair_atom,
-// F, Q, n_proj, alpha); the 1D tables come separately so that they stay in
-// the kernel parameter bank.
-template <typename T, int NP, int NQ, int VT, bool CPLX, int NT, class Prm>
-__device__ __forceinline__ void cell_tile(const Prm& p, const EOTables<T>& tb, int e, int col0, unsigned char* smem) {
+// Phases (1)-(9) of one cell tile.  xs: staged gather [n_p^3][VT] in shared
+// memory, or nullptr to gather from global memory; cfs: the cell's
+// coefficients (shared or global); ATOMIC: scatter with fire-and-forget
+// reductions instead of read-modify-write.
+template <typename T, int NP, int NQ, int VT, bool CPLX, int NT, bool ATOMIC, class Prm>
+__device__ __forceinline__ void tile_body(const Prm& p, const EOTables<T>& tb, int e, int col0, T* A, T* B, T* C,
+                                          const T* cfs, const int* sd, const T* xs, bool wait_coef) {
   using S = CellShape<T, NP, NQ, VT, CPLX>;
-  constexpr int SX = S::SX, SY = S::SY, SZ = S::SZ, BUF = S::BUF, NQ3 = S::NQ3, NP3 = S::NP3;
-  constexpr int NCOEF = S::NCOEF;
-  T* A = reinterpret_cast<T*>(smem);
-  T* B = A + BUF;
-  T* C = B + BUF;
-  T* CF = C + BUF;
-  int* sd = reinterpret_cast<int*>(CF + (S::STAGE_COEF ? NCOEF * NQ3 : 0));
+  constexpr int SX = S::SX, SY = S::SY, SZ = S::SZ, NQ3 = S::NQ3, NP3 = S::NP3;
   const int tid = threadIdx.x;
-
-  __syncthreads();   // the previous tile's readers of the shared tiles are done
-  // cell coefficients: asynchronous copy, overlapped with phases (1)-(4)
-  if (S::STAGE_COEF) {
-    const T* g = p.coef + (int64_t)e * p.ncoef * NQ3;
-    const int n = p.ncoef * NQ3;
-    for (int i = tid; i < n; i += NT) {
-      if (sizeof(T) == 8)
-        cp_async_8(CF + i, g + i);
-      else
-        cp_async_4(CF + i, g + i);
-    }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-  }
-  for (int i = tid; i < NP3; i += NT) sd[i] = p.cell_dofs[(int64_t)e * NP3 + i];
-  __syncthreads();
-
   // (1) extraction T0 = Q X (Algorithm 1) fused with N^1D along z
 #pragma unroll 1
   for (int w = tid; w < NP * NP * VT; w += NT) {
@@ -127,8 +132,9 @@ __device__ __forceinline__ void cell_tile(const Prm& p, const EOTables<T>& tb, i
     T x[NP], t[NQ];
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
-      const int d = sd[i + NP * (j + NP * k)];
-      T val = act ? p.X[(int64_t)d * p.ld + col] : T(0);
+      const int node = i + NP * (j + NP * k);
+      const int d = sd[node];
+      T val = xs ? xs[node * VT + v] : (act ? Num<T>::in(p.X[(int64_t)d * p.ld + col]) : Num<T>::zero());
       if (p.dscale) val *= p.dscale[d];
       x[k] = val;
     }
@@ -186,7 +192,7 @@ __device__ __forceinline__ void cell_tile(const Prm& p, const EOTables<T>& tb, i
 #pragma unroll
     for (int q = 0; q < NQ; ++q) Cv[a0 * SX + q * SY + qz * SZ] = t[q];
   }
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  if (wait_coef) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
   // (5) D~ along z in registers, then the quadrature-point step of
   //     Algorithm 2:  Z = V^L Y0 + V^G.Y1 - i V^K.Y1,
@@ -207,7 +213,7 @@ __device__ __forceinline__ void cell_tile(const Prm& p, const EOTables<T>& tb, i
 #pragma unroll
     for (int q = 0; q < NQ; ++q) u[q] = Av[qx * SX + qy * SY + q * SZ];
     eo_apply<NQ, NQ, -1>(u, g, tb.D);
-    const T* cf = (S::STAGE_COEF ? CF : p.coef + (int64_t)e * p.ncoef * NQ3) + qx + NQ * qy;
+    const T* cf = cfs + qx + NQ * qy;
 #pragma unroll
     for (int qz = 0; qz < NQ; ++qz) {
       const int o = qz * NQ * NQ;
@@ -230,7 +236,7 @@ __device__ __forceinline__ void cell_tile(const Prm& p, const EOTables<T>& tb, i
       if (CPLX) {
         const T K0 = cf[10 * NQ3 + o], K1 = cf[11 * NQ3 + o], K2 = cf[12 * NQ3 + o];
         const T kk = fma(K0, gx, fma(K1, gy, K2 * gz));
-        const T kp = __shfl_xor_sync(0xffffffffu, kk, 1);
+        const T kp = Num<T>::shfl1(kk);
         // -i (a + i b) = b - i a : real column adds Im, imaginary column subtracts Re
         z += (v & 1) ? -kp : kp;
       }
@@ -320,16 +326,16 @@ __device__ __forceinline__ void cell_tile(const Prm& p, const EOTables<T>& tb, i
         const int pr = p.cell_pairs[pi];
         const int a = p.pair_atom[pr];
         for (int b = 0; b < p.n_proj; ++b) {
-          const T* Qa = p.Q + ((int64_t)a * p.n_proj + b) * p.ld;
+          const auto* Qa = p.Q + ((int64_t)a * p.n_proj + b) * p.ld;
           if (!CPLX) {
             const T* Fr = p.F + ((int64_t)pr * p.n_proj + b) * NP3 + NP * (j + NP * k);
-            const T q = Qa[col];
+            const T q = Num<T>::in(Qa[col]);
 #pragma unroll
             for (int i = 0; i < NP; ++i) y[i] = fma(Fr[i], q, y[i]);
           } else {
             const T* Fr = p.F + (((int64_t)pr * p.n_proj + b) * NP3 + NP * (j + NP * k)) * 2;
             const int cb = col & ~1;
-            const T qr = Qa[cb], qi = Qa[cb + 1];
+            const T qr = Num<T>::in(Qa[cb]), qi = Num<T>::in(Qa[cb + 1]);
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
               const T fr = Fr[2 * i], fi = Fr[2 * i + 1];
@@ -344,19 +350,166 @@ __device__ __forceinline__ void cell_tile(const Prm& p, const EOTables<T>& tb, i
       const int d = sd[i + NP * (j + NP * k)];
       T val = y[i] * p.alpha;
       if (p.dscale) val *= p.dscale[d];
-      T* yp = p.Y + (int64_t)d * p.ld + col;
-      *yp += val;
+      auto* yp = p.Y + (int64_t)d * p.ld + col;
+      if constexpr (ATOMIC)
+        atomicAdd(yp, val);   // fire-and-forget reduction; the colouring keeps it race-free anyway
+      else
+        Num<T>::add_to(yp, val);
     }
   }
 }
 
+// One cell e, columns [col0, col0 + VT).  All NT threads of the block call it.
+// Prm is any struct with the operand fields of LocalParams (X, Y, ld, ncols,
+// cell_dofs, coef, ncoef, gga, dscale, cell_pair_ptr, cell_pairs, pair_atom,
+// F, Q, n_proj, alpha); the 1D tables come separately so that they stay in
+// the kernel parameter bank.
+template <typename T, int NP, int NQ, int VT, bool CPLX, int NT, class Prm>
+__device__ __forceinline__ void cell_tile(const Prm& p, const EOTables<T>& tb, int e, int col0, unsigned char* smem) {
+  using S = CellShape<T, NP, NQ, VT, CPLX>;
+  constexpr int BUF = S::BUF, NQ3 = S::NQ3, NP3 = S::NP3;
+  T* A = reinterpret_cast<T*>(smem);
+  T* B = A + BUF;
+  T* C = B + BUF;
+  T* CF = C + BUF;
+  int* sd = reinterpret_cast<int*>(CF + (S::STAGE_COEF ? S::CF_ELEMS : 0));
+  const int tid = threadIdx.x;
+
+  __syncthreads();   // the previous tile's readers of the shared tiles are done
+  // cell coefficients: asynchronous copy, overlapped with phases (1)-(4)
+  if (S::STAGE_COEF) {
+    const T* g = p.coef + (int64_t)e * p.ncoef * NQ3;
+    const int n = p.ncoef * NQ3;
+    for (int i = tid; i < n; i += NT) {
+      if (sizeof(T) == 8)
+        cp_async_8(CF + i, g + i);
+      else
+        cp_async_4(CF + i, g + i);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
+  for (int i = tid; i < NP3; i += NT) sd[i] = p.cell_dofs[(int64_t)e * NP3 + i];
+  __syncthreads();
+  tile_body<T, NP, NQ, VT, CPLX, NT, false>(p, tb, e, col0, A, B, C,
+                                           S::STAGE_COEF ? CF : p.coef + (int64_t)e * p.ncoef * NQ3, sd, nullptr,
+                                           S::STAGE_COEF);
+}
+
 // One CTA per (cell of the colour, VT-column tile); loops over cells when the
 // colour has more cells than gridDim.y.
-template <typename T, int NP, int NQ, int VT, bool CPLX, int NT>
-__global__ void __launch_bounds__(NT) fe_local_kernel(const __grid_constant__ LocalParams<T> p) {
+template <typename T, typename TS, int NP, int NQ, int VT, bool CPLX, int NT>
+__global__ void __launch_bounds__(NT) fe_local_kernel(const __grid_constant__ LocalParams<T, TS> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   for (int ci = blockIdx.y; ci < p.n_cells; ci += gridDim.y)
     cell_tile<T, NP, NQ, VT, CPLX, NT>(p, p.tab, p.cells[ci], blockIdx.x * VT, smem_raw);
+}
+
+// Cell-major variant: one CTA per cell of the colour.  It stages the cell's
+// coefficients and DoF list once, then walks all column tiles of the cell,
+// gathering the next tile's rows of X into a second shared buffer with
+// cp.async while the current tile is computed; the scatter uses
+// fire-and-forget reductions, so no thread waits on a read of Y.
+template <typename T, int NP, int NQ, int VT, bool CPLX>
+struct StagedShape {
+  using S = CellShape<T, NP, NQ, VT, CPLX>;
+  static constexpr size_t xs_elems = (size_t)S::NP3 * VT;
+  static constexpr size_t bytes = (size_t)(3 * S::BUF + S::CF_ELEMS + 2 * xs_elems) * sizeof(T) +
+                                  (size_t)S::NP3 * sizeof(int);
+  static_assert((3 * S::BUF * sizeof(T)) % 16 == 0 && (S::CF_ELEMS * sizeof(T)) % 16 == 0 &&
+                    (xs_elems * sizeof(T)) % 16 == 0,
+                "staged gather buffers must start on 16-byte boundaries");
+  static constexpr bool fits = bytes <= 227 * 1024;
+};
+
+__device__ __forceinline__ void cp_async_16z(void* smem, const void* gmem, int src_bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_4z(void* smem, const void* gmem, int src_bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_8z(void* smem, const void* gmem, int src_bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes) : "memory");
+}
+
+// Issue the gather of columns [col0, col0 + VT) of the cell's rows into xs.
+template <typename T, int NP3, int VT, int NT>
+__device__ __forceinline__ void stage_rows(const T* __restrict__ X, int64_t ld, int ncols, const int* sd, int col0,
+                                           T* xs, bool vec_ok) {
+  constexpr int EPC = 16 / sizeof(T);   // elements per 16-byte chunk
+  if (vec_ok) {
+    constexpr int CH = VT / EPC;
+    for (int idx = threadIdx.x; idx < NP3 * CH; idx += NT) {
+      const int node = idx / CH, ch = idx % CH;
+      const int col = col0 + ch * EPC;
+      int nb = (ncols - col) * (int)sizeof(T);
+      nb = nb < 0 ? 0 : (nb > 16 ? 16 : nb);
+      const T* src = nb > 0 ? X + (int64_t)sd[node] * ld + col : X;
+      cp_async_16z(xs + node * VT + ch * EPC, src, nb);
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < NP3 * VT; idx += NT) {
+      const int node = idx / VT, v = idx % VT;
+      const int col = col0 + v;
+      const bool in = col < ncols;
+      const T* src = in ? X + (int64_t)sd[node] * ld + col : X;
+      if (sizeof(T) == 8)
+        cp_async_8z(xs + idx, src, in ? 8 : 0);
+      else
+        cp_async_4z(xs + idx, src, in ? 4 : 0);
+    }
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+template <typename T, int NP, int NQ, int VT, bool CPLX, int NT>
+__global__ void __launch_bounds__(NT) fe_local_staged_kernel(const __grid_constant__ LocalParams<T, T> p) {
+  using S = CellShape<T, NP, NQ, VT, CPLX>;
+  using SS = StagedShape<T, NP, NQ, VT, CPLX>;
+  constexpr int BUF = S::BUF, NQ3 = S::NQ3, NP3 = S::NP3;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* A = reinterpret_cast<T*>(smem_raw);
+  T* B = A + BUF;
+  T* C = B + BUF;
+  T* CF = C + BUF;
+  T* XS0 = CF + S::CF_ELEMS;
+  T* XS1 = XS0 + SS::xs_elems;
+  int* sd = reinterpret_cast<int*>(XS1 + SS::xs_elems);
+  const int ntiles = (p.ncols + VT - 1) / VT;
+  const bool vec_ok = (VT * sizeof(T)) % 16 == 0 && ((uintptr_t)p.X % 16) == 0 && ((p.ld * sizeof(T)) % 16) == 0;
+  for (int ci = blockIdx.x; ci < p.n_cells; ci += gridDim.x) {
+    const int e = p.cells[ci];
+    __syncthreads();   // previous cell's readers are done with the shared buffers
+    {
+      const T* g = p.coef + (int64_t)e * p.ncoef * NQ3;
+      const int n = p.ncoef * NQ3;
+      for (int i = threadIdx.x; i < n; i += NT) {
+        if (sizeof(T) == 8)
+          cp_async_8(CF + i, g + i);
+        else
+          cp_async_4(CF + i, g + i);
+      }
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+    for (int i = threadIdx.x; i < NP3; i += NT) sd[i] = p.cell_dofs[(int64_t)e * NP3 + i];
+    __syncthreads();
+    stage_rows<T, NP3, VT, NT>(p.X, p.ld, p.ncols, sd, 0, XS0, vec_ok);
+    for (int t = 0; t < ntiles; ++t) {
+      T* cur = (t & 1) ? XS1 : XS0;
+      T* nxt = (t & 1) ? XS0 : XS1;
+      if (t + 1 < ntiles) {
+        stage_rows<T, NP3, VT, NT>(p.X, p.ld, p.ncols, sd, (t + 1) * VT, nxt, vec_ok);
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+      } else {
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+      }
+      __syncthreads();
+      tile_body<T, NP, NQ, VT, CPLX, NT, true>(p, p.tab, e, t * VT, A, B, C, CF, sd, cur, false);
+      __syncthreads();
+    }
+  }
 }
 
 // Tile configurations the launcher may pick from (chosen per context by
@@ -369,8 +522,8 @@ __host__ __device__ constexpr int cfg_nt(int vt, int nq) {
   return vt * nq * nq > 1024 ? 512 : ((vt * nq * nq + 31) / 32) * 32;
 }
 
-template <typename T, int NP, int NQ, int VT, int NT>
-cudaError_t launch_local_cfg(const Ctx& c, const LocalParams<T>& prm, cudaStream_t s) {
+template <typename T, typename TS, int NP, int NQ, int VT, int NT>
+cudaError_t launch_local_cfg(const Ctx& c, const LocalParams<T, TS>& prm, cudaStream_t s) {
   const int tiles = (prm.ncols + VT - 1) / VT;
   const int gy = prm.n_cells < 65535 ? prm.n_cells : 65535;
   if (prm.n_cells == 0) return cudaSuccess;
@@ -383,7 +536,7 @@ cudaError_t launch_local_cfg(const Ctx& c, const LocalParams<T>& prm, cudaStream
     if constexpr (!S::fits) {
       return cudaErrorInvalidConfiguration;
     } else {
-      auto k = fe_local_kernel<T, NP, NQ, VT, true, NT>;
+      auto k = fe_local_kernel<T, TS, NP, NQ, VT, true, NT>;
       if (!attr_done[1][dev]) {
         cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
         if (err != cudaSuccess) return err;
@@ -396,7 +549,7 @@ cudaError_t launch_local_cfg(const Ctx& c, const LocalParams<T>& prm, cudaStream
     if constexpr (!S::fits) {
       return cudaErrorInvalidConfiguration;
     } else {
-      auto k = fe_local_kernel<T, NP, NQ, VT, false, NT>;
+      auto k = fe_local_kernel<T, TS, NP, NQ, VT, false, NT>;
       if (!attr_done[0][dev]) {
         cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
         if (err != cudaSuccess) return err;
@@ -408,15 +561,63 @@ cudaError_t launch_local_cfg(const Ctx& c, const LocalParams<T>& prm, cudaStream
   return cudaGetLastError();
 }
 
-template <typename T, int P>
-cudaError_t launch_local_deg(const Ctx& c, const LocalParams<T>& prm, cudaStream_t s) {
+template <typename T, typename TS, int NP, int NQ, int VT, int NT>
+cudaError_t launch_staged_cfg(const Ctx& c, const LocalParams<T, TS>& prm, cudaStream_t s) {
+  if constexpr (!std::is_same<T, TS>::value) {
+    return cudaErrorInvalidConfiguration;   // the reduction scatter needs T == storage type
+  } else {
+    if (prm.n_cells == 0) return cudaSuccess;
+    const int gx = prm.n_cells < (1 << 30) ? prm.n_cells : (1 << 30);
+    static bool attr_done[2][64] = {};
+    const int dev = c.device & 63;
+    if (c.cplx) {
+      using SS = StagedShape<T, NP, NQ, VT, true>;
+      if constexpr (!SS::fits) {
+        return cudaErrorInvalidConfiguration;
+      } else {
+        auto k = fe_local_staged_kernel<T, NP, NQ, VT, true, NT>;
+        if (!attr_done[1][dev]) {
+          cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SS::bytes);
+          if (err != cudaSuccess) return err;
+          attr_done[1][dev] = true;
+        }
+        k<<<gx, NT, SS::bytes, s>>>(prm);
+      }
+    } else {
+      using SS = StagedShape<T, NP, NQ, VT, false>;
+      if constexpr (!SS::fits) {
+        return cudaErrorInvalidConfiguration;
+      } else {
+        auto k = fe_local_staged_kernel<T, NP, NQ, VT, false, NT>;
+        if (!attr_done[0][dev]) {
+          cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SS::bytes);
+          if (err != cudaSuccess) return err;
+          attr_done[0][dev] = true;
+        }
+        k<<<gx, NT, SS::bytes, s>>>(prm);
+      }
+    }
+    return cudaGetLastError();
+  }
+}
+
+template <typename T, typename TS>
+__host__ __forceinline__ int cfg_for(const Ctx& c) {
+  if (std::is_same<T, double>::value) return c.cfg64;
+  if (std::is_same<T, float>::value) return c.cfg32;
+  return c.cfgE;
+}
+
+template <typename T, typename TS, int P>
+cudaError_t launch_local_deg(const Ctx& c, const LocalParams<T, TS>& prm, cudaStream_t s) {
   constexpr int NP = P + 1, NQ = P + 1;
   constexpr int V0 = cfg_vt<NQ>(0), V1 = cfg_vt<NQ>(1), V2 = cfg_vt<NQ>(2);
-  const int cfg = sizeof(T) == 8 ? c.cfg64 : c.cfg32;
-  switch (cfg) {
-    case 1: return launch_local_cfg<T, NP, NQ, V1, cfg_nt(V1, NQ)>(c, prm, s);
-    case 2: return launch_local_cfg<T, NP, NQ, V2, cfg_nt(V2, NQ)>(c, prm, s);
-    default: return launch_local_cfg<T, NP, NQ, V0, cfg_nt(V0, NQ)>(c, prm, s);
+  switch (cfg_for<T, TS>(c)) {
+    case 1: return launch_local_cfg<T, TS, NP, NQ, V1, cfg_nt(V1, NQ)>(c, prm, s);
+    case 2: return launch_local_cfg<T, TS, NP, NQ, V2, cfg_nt(V2, NQ)>(c, prm, s);
+    case 3: return launch_staged_cfg<T, TS, NP, NQ, V0, cfg_nt(V0, NQ)>(c, prm, s);
+    case 4: return launch_staged_cfg<T, TS, NP, NQ, V1, cfg_nt(V1, NQ)>(c, prm, s);
+    default: return launch_local_cfg<T, TS, NP, NQ, V0, cfg_nt(V0, NQ)>(c, prm, s);
   }
 }
 

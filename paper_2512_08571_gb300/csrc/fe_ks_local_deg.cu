@@ -7,6 +7,10 @@
 #endif
 
 namespace feks {
-template cudaError_t launch_local_deg<double, FEKS_P>(const Ctx&, const LocalParams<double>&, cudaStream_t);
-template cudaError_t launch_local_deg<float, FEKS_P>(const Ctx&, const LocalParams<float>&, cudaStream_t);
+template cudaError_t launch_local_deg<double, double, FEKS_P>(const Ctx&, const LocalParams<double, double>&,
+                                                              cudaStream_t);
+template cudaError_t launch_local_deg<float, float, FEKS_P>(const Ctx&, const LocalParams<float, float>&,
+                                                            cudaStream_t);
+template cudaError_t launch_local_deg<ff2, double, FEKS_P>(const Ctx&, const LocalParams<ff2, double>&,
+                                                           cudaStream_t);
 }  // namespace feks

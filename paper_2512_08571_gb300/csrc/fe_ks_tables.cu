@@ -128,6 +128,16 @@ void build_eo_tables(int p, int nq, EOTables<T>* out) {
   split<T>(Dt, nq, nq, &out->Dt);
 }
 
+template <>
+void build_eo_tables<ff2>(int p, int nq, EOTables<ff2>* out) {
+  EOTables<double> d;
+  build_eo_tables<double>(p, nq, &d);
+  const double* src = reinterpret_cast<const double*>(&d);
+  ff2* dst = reinterpret_cast<ff2*>(out);
+  static_assert(sizeof(EOTables<double>) == sizeof(EOTables<ff2>), "table layouts differ");
+  for (size_t i = 0; i < sizeof(EOTables<double>) / sizeof(double); ++i) dst[i] = ff_from_double_host(src[i]);
+}
+
 template void build_eo_tables<double>(int, int, EOTables<double>*);
 template void build_eo_tables<float>(int, int, EOTables<float>*);
 

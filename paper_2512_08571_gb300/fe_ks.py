@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libfe_ks.so")
 FE_KS_OK = 0
 STATUS_NAMES = {0: "FE_KS_OK", -1: "FE_KS_ERR_ARG", -2: "FE_KS_ERR_MESH", -3: "FE_KS_ERR_CUDA",
                 -4: "FE_KS_ERR_OOM", -5: "FE_KS_ERR_TIMEOUT", -6: "FE_KS_ERR_UNSUPPORTED"}
-FE_KS_F64, FE_KS_F32 = 0, 1
+FE_KS_F64, FE_KS_F32, FE_KS_F64E = 0, 1, 2
 TERM_T, TERM_L, TERM_G, TERM_K, TERM_NL, TERM_ALL = 1, 2, 4, 8, 16, 31
 
 
@@ -67,8 +67,8 @@ def _load():
     lib.fe_ks_tune.argtypes = [vp, vp, vp, i64, ctypes.c_int, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_int)]
     lib.fe_ks_set_config.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     lib.fe_ks_batch_create.argtypes = [P(vp), ctypes.c_int, P(i64), P(ctypes.c_int), P(vp)]
-    lib.fe_ks_batch_configure.argtypes = [vp, P(ctypes.c_int), ctypes.c_int, ctypes.c_int, ctypes.c_double,
-                                          ctypes.c_int]
+    lib.fe_ks_batch_configure.argtypes = [vp, P(ctypes.c_int), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_double, ctypes.c_int]
     lib.fe_ks_batch_apply.argtypes = [vp, P(vp), P(vp), vp]
     lib.fe_ks_batch_status.argtypes = [vp]
     lib.fe_ks_batch_info.argtypes = [vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_size_t)]
@@ -149,7 +149,7 @@ def fe_ks_nonlocal_apply_static(X, Y, n_v, is_complex, degree, n_dofs, cell_dofs
                                             stream))
 
 
-N_CONFIGS = 3
+N_CONFIGS = 5
 
 
 def fe_ks_tune(ctx, X, Y, n_v, precision, reps=3):
@@ -175,9 +175,10 @@ def fe_ks_batch_create(ctxs, n_v, precision):
 
 
 def fe_ks_batch_configure(batch, tile_config=None, cells_per_item=1, depth=1, wait_seconds=2.0,
-                          inject_missing_item=False):
+                          inject_missing_item=False, blocks_per_sm=1):
     tc = None if tile_config is None else (ctypes.c_int * len(tile_config))(*tile_config)
-    _check(_lib.fe_ks_batch_configure(batch, tc, cells_per_item, depth, wait_seconds, int(inject_missing_item)))
+    _check(_lib.fe_ks_batch_configure(batch, tc, cells_per_item, depth, blocks_per_sm, wait_seconds,
+                                      int(inject_missing_item)))
 
 
 def fe_ks_batch_apply(batch, Xs, Ys, stream=None):

@@ -14,7 +14,7 @@ def rel_err_cols(Y, Yref):
 
 def torch_dtype(precision, cplx):
     import torch
-    if precision == fk.FE_KS_F64:
+    if precision in (fk.FE_KS_F64, fk.FE_KS_F64E):
         return torch.complex128 if cplx else torch.float64
     return torch.complex64 if cplx else torch.float32
 

@@ -60,10 +60,10 @@ def _check(Ys, refs):
         assert err <= TOL[PREC[s]], (s, err)
 
 
-@pytest.mark.parametrize("tile,cells,depth", [(0, 1, 1), (1, 1, 1), (0, 3, 2), (1, 2, 4)])
-def test_batched_equals_individual_applications(batch_setup, tile, cells, depth):
+@pytest.mark.parametrize("tile,cells,depth,occ", [(0, 1, 1, 1), (1, 1, 1, 2), (0, 3, 2, 2), (1, 2, 4, 1)])
+def test_batched_equals_individual_applications(batch_setup, tile, cells, depth, occ):
     wls, hps, ctxs, Xs, Ys, refs, b = batch_setup
-    fk.fe_ks_batch_configure(b, [tile] * 6, cells, depth, 2.0, False)
+    fk.fe_ks_batch_configure(b, [tile] * 6, cells, depth, 2.0, False, blocks_per_sm=occ)
     for Y in Ys:
         Y.fill_(float("nan"))
     fk.fe_ks_batch_apply(b, Xs, Ys, torch.cuda.current_stream().cuda_stream)

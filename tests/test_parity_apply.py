@@ -1,9 +1,9 @@
 """GPU parity of fe_ks_apply against the FP64 oracle (eq. HX, Algorithms 1-2).
 
 Tolerances: relative error per column (max over columns of
-||Y_v - Y_v^ref|| / ||Y_v^ref||) <= 1e-12 for FP64 and <= 1e-5 for FP32; the
-FP32 case feeds the oracle the FP32-rounded input, so only the arithmetic
-differs.
+||Y_v - Y_v^ref|| / ||Y_v^ref||) <= 1e-12 for FP64 and for the FP64-accurate
+pair-of-floats variant (FE_KS_F64E), <= 1e-5 for FP32; the FP32 case feeds the
+oracle the FP32-rounded input, so only the arithmetic differs.
 """
 import numpy as np
 import pytest
@@ -17,8 +17,8 @@ from gpu_util import gpu_apply, rel_err_cols, round_input
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {fk.FE_KS_F64: 1e-12, fk.FE_KS_F32: 1e-5}
-PREC = [fk.FE_KS_F64, fk.FE_KS_F32]
+TOL = {fk.FE_KS_F64: 1e-12, fk.FE_KS_F32: 1e-5, fk.FE_KS_F64E: 1e-12}
+PREC = [fk.FE_KS_F64, fk.FE_KS_F32, fk.FE_KS_F64E]
 
 # parity-sized versions of the four operator workloads (several tiles, ragged column tails)
 SMALL = {
@@ -26,6 +26,9 @@ SMALL = {
     "C2s": CONFIGS["C2"].scaled(n=6, n_v=7),
     "C3s": CONFIGS["C3"].scaled(n=4, n_v=3, n_atoms=4),
     "C4s": CONFIGS["C4"].scaled(n=4, n_v=5, n_atoms=6),
+    # column counts whose rows are 16-byte aligned (vectorised staging path)
+    "C4v": CONFIGS["C4"].scaled(n=4, n_v=16, n_atoms=6),
+    "C3v": CONFIGS["C3"].scaled(n=4, n_v=4, n_atoms=4),
 }
 
 
@@ -49,7 +52,7 @@ def test_apply_matches_oracle(cases, key, precision):
 
 
 @pytest.mark.parametrize("config", range(fk.N_CONFIGS))
-@pytest.mark.parametrize("key", ["C2s", "C3s", "C4s"])
+@pytest.mark.parametrize("key", ["C2s", "C3s", "C4s", "C4v", "C3v"])
 def test_every_tile_configuration(cases, key, config):
     """Every tile configuration the tuner may pick gives the same answer."""
     wl, hp, P, X = cases[key]

@@ -16,7 +16,7 @@ from gpu_util import RowCache, needed_rows, fill_device, rel_err_cols, torch_dty
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {fk.FE_KS_F64: 1e-12, fk.FE_KS_F32: 1e-5}
+TOL = {fk.FE_KS_F64: 1e-12, fk.FE_KS_F32: 1e-5, fk.FE_KS_F64E: 1e-12}
 
 
 def _rows(P, wl, seed):
@@ -36,7 +36,7 @@ def test_full_size_sampled_rows(key):
     need = needed_rows(P, rows)
     ctx = fk.fe_ks_setup(hp.struct, fk.TERM_ALL, wl.n_v, torch.cuda.current_stream().cuda_stream)
     try:
-        for precision in (fk.FE_KS_F64, fk.FE_KS_F32):
+        for precision in (fk.FE_KS_F64, fk.FE_KS_F32, fk.FE_KS_F64E):
             dt = torch_dtype(precision, hp.complex)
             X = torch.empty((hp.m, wl.n_v), dtype=dt, device="cuda")
             npdt = {torch.float64: np.float64, torch.float32: np.float32,

@@ -279,9 +279,11 @@ def run_native(args, wl, rank, world):
 # ------------------------------------------------------------ R-ChFSI filter
 def run_filter(args, wl, ctx, hp, X64):
     """One R-ChFSI pass on the workload (Lanczos bound, degree-20 filter,
-    Rayleigh-Ritz), all-FP64 against the mixed filter (FP32 recurrence), plus a
-    convergence run on the same recipe at 8^3 cells (N_v = 64) to residual
-    1e-9 with both filters, reporting iterations and the eigenvalue gap."""
+    Rayleigh-Ritz) three ways: all native FP64; FP64-accurate pairs of floats;
+    mixed (FP32 recurrence, FP64-accurate residual / Lanczos / Rayleigh-Ritz
+    through the pair-of-floats kernel).  Plus a convergence run on the same
+    recipe at 6^3 cells (N_v = 32) to residual 1e-9 on the lowest 8, all-FP64
+    against mixed, reporting iterations and the eigenvalue gap."""
     import numpy as np
     import torch
     from paper_2512_08571_gb300 import fe_ks as fk
@@ -310,39 +312,47 @@ def run_filter(args, wl, ctx, hp, X64):
         del Xa, Ya
     out["f64_apply_ms_by_n_v"] = nv_ms
     m, n_v = hp.m, wl.n_v
-    X0 = X64.clone()
-    s64 = RChFSI(ctx, m, n_v, False, degree=20, precision=fk.FE_KS_F64)
-    out["lanczos_ms"], lmax = ev_ms(s64.lanczos_upper_bound)
-    out["rayleigh_ritz_ms"], (lam, X) = ev_ms(lambda: s64.rayleigh_ritz(X0))
-    del X0
-    X1 = X.clone()
-    out["filter_f64_ms"], _ = ev_ms(lambda: s64.filter(X1, lam))
-    del X1, s64
-    torch.cuda.empty_cache()
-    s32 = RChFSI(ctx, m, n_v, False, degree=20, precision=fk.FE_KS_F32)
-    s32.lmax = lmax
-    X2 = X.clone()
-    s32.filter(X2, lam)                       # warm-up
-    X2 = X.clone()
-    out["filter_mixed_ms"], _ = ev_ms(lambda: s32.filter(X2, lam))
-    del X2, s32, X
-    torch.cuda.empty_cache()
-    p64 = out["lanczos_ms"] + out["filter_f64_ms"] + out["rayleigh_ritz_ms"]
-    pmx = out["lanczos_ms"] + out["filter_mixed_ms"] + out["rayleigh_ritz_ms"]
-    out.update(pass_f64_ms=p64, pass_mixed_ms=pmx, speedup_pass=p64 / pmx,
-               speedup_filter=out["filter_f64_ms"] / out["filter_mixed_ms"])
+    # (recurrence, FP64-accurate parts, Rayleigh-Ritz GEMMs in cuBLAS FP64 emulation)
+    plans = {"f64": (fk.FE_KS_F64, fk.FE_KS_F64, False),
+             "f64_pairs": (fk.FE_KS_F64E, fk.FE_KS_F64E, False),
+             "mixed": (fk.FE_KS_F32, fk.FE_KS_F64E, False),
+             "mixed_emulated_gemm": (fk.FE_KS_F32, fk.FE_KS_F64E, True)}
+    lam = X = lmax = None
+    for name, (prec, exact, emu_gemm) in plans.items():
+        sol = RChFSI(ctx, m, n_v, False, degree=20, precision=prec, exact=exact, gemm_emulated=emu_gemm)
+        t_l, lm = ev_ms(sol.lanczos_upper_bound)
+        if lmax is None:
+            lmax = lm
+            lam, X = sol.rayleigh_ritz(X64.clone())
+        sol.lmax = lmax
+        try:
+            t_rr, _ = ev_ms(lambda: sol.rayleigh_ritz(X.clone()))
+        except fk.FeKsError as exc:          # FP64 emulation unavailable
+            out[name] = {"unavailable": str(exc)}
+            del sol
+            continue
+        Xf = X.clone()
+        t_f, _ = ev_ms(lambda: sol.filter(Xf, lam))
+        out[name] = {"lanczos_ms": t_l, "rayleigh_ritz_ms": t_rr, "filter_ms": t_f, "pass_ms": t_l + t_rr + t_f}
+        del sol, Xf
+        torch.cuda.empty_cache()
+    out["speedup_filter_mixed_vs_f64"] = out["f64"]["filter_ms"] / out["mixed"]["filter_ms"]
+    out["speedup_pass_mixed_vs_f64"] = out["f64"]["pass_ms"] / out["mixed"]["pass_ms"]
+    if "pass_ms" in out["mixed_emulated_gemm"]:
+        out["speedup_pass_mixed_emulated_gemm_vs_f64"] = out["f64"]["pass_ms"] / out["mixed_emulated_gemm"]["pass_ms"]
+    del X
     # convergence at 6^3 cells
     wls = wl.scaled(n=6, n_v=32)
     hps = HostProblem(wls)
     cs = fk.fe_ks_setup(hps.struct, fk.TERM_ALL, wls.n_v, stream.cuda_stream)
     Xs0 = torch.empty((hps.m, wls.n_v), dtype=torch.float64, device=dev)
     fill_trial(wls, wls.n_v, Xs0, np.float64)
-    n_chk = wls.n_v // 2
+    n_chk = wls.n_v // 4
     conv = {"workload": f"same recipe, 6^3 cells, N_v={wls.n_v}, residual < 1e-9 on the lowest {n_chk}"}
     lams = {}
-    for name, prec in (("f64", fk.FE_KS_F64), ("mixed", fk.FE_KS_F32)):
-        sol = RChFSI(cs, hps.m, wls.n_v, False, degree=20, precision=prec)
-        t, (lam_c, _, res, its) = ev_ms(lambda: sol.run(Xs0.clone(), n_iter=60, tol=1e-9, n_check=n_chk))
+    for name, prec, exact in (("f64", fk.FE_KS_F64, fk.FE_KS_F64), ("mixed", fk.FE_KS_F32, fk.FE_KS_F64E)):
+        sol = RChFSI(cs, hps.m, wls.n_v, False, degree=20, precision=prec, exact=exact)
+        t, (lam_c, _, res, its) = ev_ms(lambda: sol.run(Xs0.clone(), n_iter=80, tol=1e-9, n_check=n_chk))
         lams[name] = lam_c.cpu().numpy()
         conv[name] = {"iterations": its, "ms": t, "max_residual": float(res[:n_chk].max())}
         del sol

@@ -165,9 +165,11 @@ fe_ks_status fe_ks_apply_scaled(fe_ks_ctx* ctx, const void* X, void* Y, int64_t 
  *   X  <- R_Y + X Lam_Y
  * with e = (lam_max - lam_T)/2, c = (lam_max + lam_T)/2 and the scalar
  * recurrence of Algorithm 4.  The residual Y and the final combination are
- * FP64; the degree - 1 applications inside the recurrence run in `precision`
- * (FE_KS_F64 or FE_KS_F32), which is where the paper's R-ChFSI tolerates
- * inexact products.
+ * FP64-accurate: residual_precision selects native FP64 (FE_KS_F64) or the
+ * pair-of-floats kernel (FE_KS_F64E) for the residual's application.  The
+ * degree - 1 applications inside the recurrence run in `precision`
+ * (FE_KS_F64, FE_KS_F64E or FE_KS_F32), which is where the paper's R-ChFSI
+ * tolerates inexact products.
  *  X     : device FP64 [m][n_v] (complex: interleaved), overwritten by the
  *          filtered block.
  *  ritz  : device FP64 [n_v] current Ritz values Lam (real).
@@ -179,8 +181,8 @@ fe_ks_status fe_ks_apply_scaled(fe_ks_ctx* ctx, const void* X, void* Y, int64_t 
  */
 fe_ks_status fe_ks_cheb_filter_workspace(const fe_ks_ctx* ctx, int64_t n_v, int precision, size_t* bytes);
 fe_ks_status fe_ks_cheb_filter(fe_ks_ctx* ctx, double* X, const double* ritz, int64_t n_v, int degree,
-                               double lam_min, double lam_T, double lam_max, int precision, void* work,
-                               size_t work_bytes);
+                               double lam_min, double lam_T, double lam_max, int precision,
+                               int residual_precision, void* work, size_t work_bytes);
 
 /*
  * Tile configuration of the fused cell kernel: 0..2 run one CTA per (cell,
@@ -294,6 +296,18 @@ fe_ks_status fe_ks_nonlocal_apply_static(const double* X, double* Y, int64_t n_v
                                          int32_t n_atoms, int32_t n_proj, const int32_t* atom_pair_ptr,
                                          const int32_t* pair_cell, const int32_t* pair_atom, int64_t n_pairs,
                                          const double* F, const double* h_coef, void* cuda_stream);
+
+/*
+ * Column-major FP64 GEMM C = alpha op(A) op(B) + beta C through cuBLAS, for
+ * the Rayleigh-Ritz step of Algorithm 3 (Gram matrices and the rotation of
+ * the filtered block).  emulated = 1 asks cuBLAS for its FP64 emulation on
+ * integer tensor cores (fixed-point slices); FE_KS_ERR_UNSUPPORTED if
+ * unavailable.  trans_* = 1 transposes.  The first call on a device creates
+ * a cuBLAS handle (which allocates); stream-ordered on cuda_stream.
+ */
+fe_ks_status fe_ks_gemm_f64(int trans_a, int trans_b, int64_t m, int64_t n, int64_t k, double alpha,
+                            const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
+                            int64_t ldc, int emulated, void* cuda_stream);
 
 /* Change the stream used by later calls. */
 fe_ks_status fe_ks_set_stream(fe_ks_ctx* ctx, void* cuda_stream);

@@ -16,9 +16,16 @@ from . import fe_ks as fk
 
 
 class RChFSI:
-    def __init__(self, ctx, m, n_v, cplx, degree=20, precision=fk.FE_KS_F32, lanczos_steps=10):
+    """precision: arithmetic of the filter's recurrence (FE_KS_F32, FE_KS_F64 or FE_KS_F64E);
+    exact: the FP64-accurate path used for the filter's residual, Lanczos, Rayleigh-Ritz and
+    residual norms (FE_KS_F64 native, or FE_KS_F64E pairs of floats)."""
+
+    def __init__(self, ctx, m, n_v, cplx, degree=20, precision=fk.FE_KS_F32, lanczos_steps=10,
+                 exact=fk.FE_KS_F64, gemm_emulated=False):
         self.ctx, self.m, self.n_v, self.cplx = ctx, m, n_v, cplx
         self.degree, self.precision, self.lanczos_steps = degree, precision, lanczos_steps
+        self.exact = exact
+        self.gemm_emulated = gemm_emulated and not cplx
         self.dt = torch.complex128 if cplx else torch.float64
         self.dev = torch.device("cuda", torch.cuda.current_device())
         nb = fk.fe_ks_cheb_filter_workspace(ctx, n_v, precision)
@@ -32,7 +39,7 @@ class RChFSI:
     def apply_scaled(self, V, out=None):
         V = V.contiguous()
         out = torch.empty(V.shape, dtype=V.dtype, device=V.device) if out is None else out
-        fk.fe_ks_apply_scaled(self.ctx, V, out, V.shape[1], fk.FE_KS_F64)
+        fk.fe_ks_apply_scaled(self.ctx, V, out, V.shape[1], self.exact)
         return out
 
     def lanczos_upper_bound(self, seed=0):
@@ -64,7 +71,39 @@ class RChFSI:
         return self.lmax
 
     def rayleigh_ritz(self, Y):
-        """Orthonormalise Y (QR) and solve the projected problem: returns (lam, X)."""
+        """Rayleigh-Ritz on span(Y): (Y^H Hs Y) E = (Y^H Y) E Lam, returns (Lam, Y E).
+
+        Cholesky of the Gram matrix S = Y^H Y = L L^H reduces it to the standard
+        problem L^-1 (Y^H Hs Y) L^-H W = W Lam with E = L^-H W (three FP64 GEMMs).
+        A Householder QR is used instead when S is too ill-conditioned for Cholesky.
+        """
+        Y = Y.contiguous()
+        S = self._gram(Y, Y)
+        S = 0.5 * (S + S.conj().T)
+        L, info = torch.linalg.cholesky_ex(S)
+        d = torch.real(torch.diagonal(L)) if int(info.item()) == 0 else None
+        if d is None or float(d.min()) <= 1e-6 * float(d.max()):
+            return self._rayleigh_ritz_qr(Y)
+        HY = self.apply_scaled(Y, self.tmp)
+        A = self._gram(Y, HY)
+        T1 = torch.linalg.solve_triangular(L, A, upper=False)
+        B = torch.linalg.solve_triangular(L, T1.conj().T, upper=False).conj().T
+        B = 0.5 * (B + B.conj().T)
+        lam, W = torch.linalg.eigh(B)
+        E = torch.linalg.solve_triangular(L.conj().T, W, upper=True)
+        return lam.to(torch.float64).contiguous(), self._rotate(Y, E)
+
+    def _gram(self, Y, Z):
+        if self.gemm_emulated:
+            return fk.row_gram(Y, Z, emulated=True, stream=torch.cuda.current_stream().cuda_stream)
+        return Y.conj().T @ Z
+
+    def _rotate(self, Y, E):
+        if self.gemm_emulated:
+            return fk.row_rotate(Y, E.contiguous(), emulated=True, stream=torch.cuda.current_stream().cuda_stream)
+        return (Y @ E).contiguous()
+
+    def _rayleigh_ritz_qr(self, Y):
         Q, _ = torch.linalg.qr(Y)
         Q = Q.contiguous()          # QR returns column-major factors; the C ABI is row-major
         HQ = self.apply_scaled(Q, self.tmp)
@@ -82,7 +121,7 @@ class RChFSI:
         if not lmin < lT < self.lmax:
             raise RuntimeError("spectral bounds out of order")
         fk.fe_ks_cheb_filter(self.ctx, X, lam, self.n_v, self.degree, lmin, lT, self.lmax, self.precision,
-                             self.work_view, self.work_bytes)
+                             self.work_view, self.work_bytes, residual_precision=self.exact)
         return X
 
     def run(self, X0, n_iter, tol=None, n_check=None):

@@ -13,6 +13,7 @@
 // a(-c R_Y + Y Lam_Y) - b R_X in place into R_X (elementwise kernel) and then
 // letting the fused cell kernel scatter-add a * Hs R_Y on top (alpha = a).
 #include <cmath>
+#include <type_traits>
 
 #include "fe_ks_internal.h"
 
@@ -84,17 +85,27 @@ static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 static size_t filter_bytes(const Ctx& c, int64_t n_v, int precision) {
   const size_t n = (size_t)c.m * n_v * (c.cplx ? 2 : 1);
-  const size_t lo = precision == FE_KS_F64 ? 8 : 4;
+  const bool low = precision == FE_KS_F32;
+  const size_t lo = low ? 4 : 8;
   size_t b = align256(n * 8);                    // Y (FP64 residual)
-  if (precision != FE_KS_F64) b += align256(n * lo);   // Y in the recurrence precision
+  if (low) b += align256(n * lo);                // Y in the recurrence precision
   b += 2 * align256(n * lo);                     // R_X, R_Y
   b += 2 * align256((size_t)n_v * 8);            // Lam_X, Lam_Y
   return b;
 }
 
+// Recurrence application a * Hs R_Y accumulated into R_X, in the recurrence's arithmetic.
+template <typename T>
+static fe_ks_status recurrence_apply(Ctx& c, const T* RY, T* RX, int64_t ncols, double a, bool emu) {
+  if constexpr (std::is_same<T, double>::value) {
+    if (emu) return apply_core_emu(c, RY, RX, ncols, true, a, false);
+  }
+  return apply_core<T>(c, RY, RX, ncols, true, (T)a, false);
+}
+
 template <typename T>
 static fe_ks_status cheb_impl(Ctx& c, double* X, const double* lam, int64_t n_v, int degree, double lmin, double lT,
-                              double lmax, char* work) {
+                              double lmax, char* work, bool rec_emu, bool res_emu) {
   cudaStream_t s = c.stream;
   const int cw = c.cplx ? 2 : 1;
   const int64_t ncols = n_v * cw;
@@ -120,7 +131,8 @@ static fe_ks_status cheb_impl(Ctx& c, double* X, const double* lam, int64_t n_v,
 
   // Y = Hs X - X Lam (FP64)
   k_residual_init<<<nb, kEwThreads, 0, s>>>(Y, X, lam, n, ncols, cw);
-  fe_ks_status st = apply_core<double>(c, X, Y, ncols, true, 1.0, false);
+  fe_ks_status st = res_emu ? apply_core_emu(c, X, Y, ncols, true, 1.0, false)
+                            : apply_core<double>(c, X, Y, ncols, true, 1.0, false);
   if (st != FE_KS_OK) return st;
   k_residual_split<T><<<nb, kEwThreads, 0, s>>>(Y, low ? Yl : nullptr, RY, sigma1 / e, n);
   k_lambda<<<(int)((n_v + 255) / 256), 256, 0, s>>>(LX, LY, lam, sigma1 / e, cc, 0.0, 1, (int)n_v);
@@ -128,7 +140,7 @@ static fe_ks_status cheb_impl(Ctx& c, double* X, const double* lam, int64_t n_v,
     const double sigma2 = 1.0 / (gamma - sigma);
     const double a = 2.0 * sigma2 / e, b = (k == 2) ? 0.0 : sigma * sigma2;
     k_cheb_prologue<T><<<nb, kEwThreads, 0, s>>>(RX, RY, Yl, LY, (T)a, (T)cc, (T)b, n, ncols, cw);
-    st = apply_core<T>(c, RY, RX, ncols, true, (T)a, false);
+    st = recurrence_apply<T>(c, RY, RX, ncols, a, rec_emu);
     if (st != FE_KS_OK) return st;
     k_lambda<<<(int)((n_v + 255) / 256), 256, 0, s>>>(LX, LY, lam, a, cc, sigma * sigma2, 0, (int)n_v);
     std::swap(RX, RY);
@@ -149,25 +161,32 @@ extern "C" {
 
 fe_ks_status fe_ks_cheb_filter_workspace(const fe_ks_ctx* ctx, int64_t n_v, int precision, size_t* bytes) {
   if (!ctx || !bytes) return fail(FE_KS_ERR_ARG, "NULL argument");
-  if (precision != FE_KS_F64 && precision != FE_KS_F32) return fail(FE_KS_ERR_UNSUPPORTED, "unknown precision");
+  if (precision != FE_KS_F64 && precision != FE_KS_F32 && precision != FE_KS_F64E)
+    return fail(FE_KS_ERR_UNSUPPORTED, "unknown precision");
   *bytes = filter_bytes(ctx->c, n_v, precision);
   return FE_KS_OK;
 }
 
 fe_ks_status fe_ks_cheb_filter(fe_ks_ctx* ctx, double* X, const double* ritz, int64_t n_v, int degree, double lam_min,
-                               double lam_T, double lam_max, int precision, void* work, size_t work_bytes) {
+                               double lam_T, double lam_max, int precision, int residual_precision, void* work,
+                               size_t work_bytes) {
   set_error("");
   if (!ctx || !X || !ritz || !work) return fail(FE_KS_ERR_ARG, "NULL argument");
   Ctx& c = ctx->c;
   if (n_v < 1 || n_v > c.n_v_max) return fail(FE_KS_ERR_ARG, "n_v must be in 1..n_v_max");
   if (degree < 1) return fail(FE_KS_ERR_ARG, "degree must be >= 1");
   if (!(lam_min < lam_T && lam_T < lam_max)) return fail(FE_KS_ERR_ARG, "need lam_min < lam_T < lam_max");
-  if (precision != FE_KS_F64 && precision != FE_KS_F32) return fail(FE_KS_ERR_UNSUPPORTED, "unknown precision");
+  if (precision != FE_KS_F64 && precision != FE_KS_F32 && precision != FE_KS_F64E)
+    return fail(FE_KS_ERR_UNSUPPORTED, "unknown precision");
+  if (residual_precision != FE_KS_F64 && residual_precision != FE_KS_F64E)
+    return fail(FE_KS_ERR_ARG, "residual_precision must be FE_KS_F64 or FE_KS_F64E");
   if (work_bytes < filter_bytes(c, n_v, precision)) return fail(FE_KS_ERR_ARG, "workspace too small");
   if (((uintptr_t)work & 255) || ((uintptr_t)X & 7)) return fail(FE_KS_ERR_ARG, "misaligned X or workspace");
   char* w = static_cast<char*>(work);
-  if (precision == FE_KS_F64) return cheb_impl<double>(c, X, ritz, n_v, degree, lam_min, lam_T, lam_max, w);
-  return cheb_impl<float>(c, X, ritz, n_v, degree, lam_min, lam_T, lam_max, w);
+  const bool res_emu = residual_precision == FE_KS_F64E;
+  if (precision == FE_KS_F32)
+    return cheb_impl<float>(c, X, ritz, n_v, degree, lam_min, lam_T, lam_max, w, false, res_emu);
+  return cheb_impl<double>(c, X, ritz, n_v, degree, lam_min, lam_T, lam_max, w, precision == FE_KS_F64E, res_emu);
 }
 
 }  // extern "C"

@@ -61,7 +61,7 @@ def _load():
     lib.fe_ks_measure_fma_peak.argtypes = [ctypes.c_int, P(ctypes.c_double)]
     lib.fe_ks_cheb_filter_workspace.argtypes = [vp, i64, ctypes.c_int, P(ctypes.c_size_t)]
     lib.fe_ks_cheb_filter.argtypes = [vp, vp, vp, i64, ctypes.c_int, ctypes.c_double, ctypes.c_double,
-                                      ctypes.c_double, ctypes.c_int, vp, ctypes.c_size_t]
+                                      ctypes.c_double, ctypes.c_int, ctypes.c_int, vp, ctypes.c_size_t]
     lib.fe_ks_nonlocal_apply_static.argtypes = [vp, vp, i64, i32, i32, i64, vp, i32, i32, vp, vp, vp, i64,
                                                 vp, vp, vp]
     lib.fe_ks_tune.argtypes = [vp, vp, vp, i64, ctypes.c_int, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_int)]
@@ -74,13 +74,16 @@ def _load():
     lib.fe_ks_batch_info.argtypes = [vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_size_t)]
     lib.fe_ks_batch_destroy.argtypes = [vp]
     lib.fe_ks_batch_destroy.restype = None
+    lib.fe_ks_gemm_f64.argtypes = [ctypes.c_int, ctypes.c_int, i64, i64, i64, ctypes.c_double, vp, i64, vp, i64,
+                                   ctypes.c_double, vp, i64, ctypes.c_int, vp]
     lib.fe_ks_destroy.argtypes = [vp]
     lib.fe_ks_destroy.restype = None
     for name in ("fe_ks_quadrature_points", "fe_ks_setup", "fe_ks_apply", "fe_ks_apply_scaled",
                  "fe_ks_info", "fe_ks_set_stream", "fe_ks_set_profiling", "fe_ks_read_profile",
                  "fe_ks_measure_fma_peak", "fe_ks_cheb_filter_workspace", "fe_ks_cheb_filter",
                  "fe_ks_nonlocal_apply_static", "fe_ks_tune", "fe_ks_set_config", "fe_ks_batch_create",
-                 "fe_ks_batch_configure", "fe_ks_batch_apply", "fe_ks_batch_status", "fe_ks_batch_info"):
+                 "fe_ks_batch_configure", "fe_ks_batch_apply", "fe_ks_batch_status", "fe_ks_batch_info",
+                 "fe_ks_gemm_f64"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -136,9 +139,10 @@ def fe_ks_cheb_filter_workspace(ctx, n_v, precision):
     return out.value
 
 
-def fe_ks_cheb_filter(ctx, X, ritz, n_v, degree, lam_min, lam_T, lam_max, precision, work, work_bytes):
+def fe_ks_cheb_filter(ctx, X, ritz, n_v, degree, lam_min, lam_T, lam_max, precision, work, work_bytes,
+                      residual_precision=FE_KS_F64):
     _check(_lib.fe_ks_cheb_filter(ctx, _ptr(X), _ptr(ritz), n_v, degree, lam_min, lam_T, lam_max, precision,
-                                  _ptr(work), work_bytes))
+                                  residual_precision, _ptr(work), work_bytes))
 
 
 def fe_ks_nonlocal_apply_static(X, Y, n_v, is_complex, degree, n_dofs, cell_dofs, n_atoms, n_proj,
@@ -200,6 +204,34 @@ def fe_ks_batch_info(batch):
 
 def fe_ks_batch_destroy(batch):
     _lib.fe_ks_batch_destroy(batch)
+
+
+def fe_ks_gemm_f64(trans_a, trans_b, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, emulated=False, stream=None):
+    _check(_lib.fe_ks_gemm_f64(int(trans_a), int(trans_b), m, n, k, alpha, _ptr(A), lda, _ptr(B), ldb, beta,
+                               _ptr(C), ldc, int(emulated), stream))
+
+
+def row_gram(Y, Z, emulated=False, stream=None):
+    """Y^T Z for row-major real FP64 Y [m][n1], Z [m][n2] (contiguous device tensors) -> [n1][n2]."""
+    import torch
+    m, n1 = Y.shape
+    n2 = Z.shape[1]
+    C = torch.empty((n2, n1), dtype=torch.float64, device=Y.device)     # column-major (n1 x n2)
+    # column-major views: Yc (n1 x m, ld n1), Zc (n2 x m, ld n2); C = Yc Zc^T
+    fe_ks_gemm_f64(0, 1, n1, n2, m, 1.0, Y, n1, Z, n2, 0.0, C, n1, emulated, stream)
+    return C.T
+
+
+def row_rotate(Y, E, emulated=False, stream=None):
+    """Y E for row-major real FP64 Y [m][n], E [n][k] (contiguous device tensors) -> [m][k] row-major."""
+    import torch
+    m, n = Y.shape
+    k = E.shape[1]
+    Ec = E.contiguous()
+    X = torch.empty((m, k), dtype=torch.float64, device=Y.device)
+    # row-major X = Y E  <=>  column-major Xc (k x m) = Ec (k x n) Yc (n x m)
+    fe_ks_gemm_f64(0, 0, k, m, n, 1.0, Ec, k, Y, n, 0.0, X, k, emulated, stream)
+    return X
 
 
 def fe_ks_dinv_sqrt(ctx):

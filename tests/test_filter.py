@@ -41,8 +41,11 @@ def gpu():
     fk.fe_ks_destroy(ctx)
 
 
-@pytest.mark.parametrize("precision,tol", [(fk.FE_KS_F64, 1e-10), (fk.FE_KS_F32, 2e-4)])
-def test_one_filter_pass_matches_oracle(dense, gpu, precision, tol):
+@pytest.mark.parametrize("precision,tol,resid", [(fk.FE_KS_F64, 1e-10, fk.FE_KS_F64),
+                                                (fk.FE_KS_F64E, 1e-10, fk.FE_KS_F64E),
+                                                (fk.FE_KS_F32, 2e-4, fk.FE_KS_F64),
+                                                (fk.FE_KS_F32, 2e-4, fk.FE_KS_F64E)])
+def test_one_filter_pass_matches_oracle(dense, gpu, precision, tol, resid):
     P, Hs, ev = dense
     hp, ctx = gpu
     X = np.linalg.qr(trial_vectors(WL))[0]
@@ -53,20 +56,21 @@ def test_one_filter_pass_matches_oracle(dense, gpu, precision, tol):
     lamd = torch.from_numpy(lam).cuda()
     nb = fk.fe_ks_cheb_filter_workspace(ctx, WL.n_v, precision)
     work = torch.empty(nb, dtype=torch.uint8, device="cuda")
-    fk.fe_ks_cheb_filter(ctx, Xd, lamd, WL.n_v, 12, lmin, lT, lmax, precision, work, nb)
+    fk.fe_ks_cheb_filter(ctx, Xd, lamd, WL.n_v, 12, lmin, lT, lmax, precision, work, nb, residual_precision=resid)
     torch.cuda.synchronize()
     got = Xd.cpu().numpy()
     err = np.max(np.linalg.norm(got - want, axis=0) / np.linalg.norm(want, axis=0))
     assert err < tol, err
 
 
-@pytest.mark.parametrize("precision", [fk.FE_KS_F64, fk.FE_KS_F32])
-def test_eigensolver_converges_to_oracle_eigenvalues(dense, gpu, precision):
+@pytest.mark.parametrize("precision,exact", [(fk.FE_KS_F64, fk.FE_KS_F64), (fk.FE_KS_F32, fk.FE_KS_F64),
+                                             (fk.FE_KS_F32, fk.FE_KS_F64E)])
+def test_eigensolver_converges_to_oracle_eigenvalues(dense, gpu, precision, exact):
     from paper_2512_08571_gb300.chfsi import RChFSI
     P, Hs, ev = dense
     hp, ctx = gpu
     n_conv = WL.n_v - 6
-    solver = RChFSI(ctx, hp.m, WL.n_v, False, degree=20, precision=precision)
+    solver = RChFSI(ctx, hp.m, WL.n_v, False, degree=20, precision=precision, exact=exact)
     lmax = solver.lanczos_upper_bound()
     assert lmax >= ev[-1] - 1e-9
     X0 = torch.from_numpy(trial_vectors(WL)).cuda()

@@ -195,7 +195,7 @@ fe_ks_status fe_ks_cheb_filter(fe_ks_ctx* ctx, double* X, const double* ritz, in
  * that cannot launch, e.g. shared memory too large) and the choice.
  * fe_ks_set_config sets it directly.  Y is overwritten.
  */
-#define FE_KS_N_CONFIGS 5
+#define FE_KS_N_CONFIGS 7
 fe_ks_status fe_ks_tune(fe_ks_ctx* ctx, const void* X, void* Y, int64_t n_v, int precision, int reps,
                         double* ms_per_config, int* best);
 fe_ks_status fe_ks_set_config(fe_ks_ctx* ctx, int precision, int config);

@@ -644,7 +644,7 @@ fe_ks_status apply_core_emu(Ctx& c, const double* X, double* Y, int64_t ncols, b
     pp.Q = c.f64.Q;
     pp.n_proj = c.n_proj;
     pp.np3 = c.np3;
-    cudaError_t err = launch_proj<double>(c, pp, c.n_atoms, s);
+    cudaError_t err = launch_proj_emu(c, pp, static_cast<const ff2*>(c.emu.F), c.n_atoms, s);
     if (err != cudaSuccess) return fail(FE_KS_ERR_CUDA, std::string("projection kernel: ") + cudaGetErrorString(err));
     nlaunch[1] = 1;
   }

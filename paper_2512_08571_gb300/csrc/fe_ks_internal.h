@@ -154,13 +154,14 @@ fe_ks_status apply_core(Ctx& c, const T* X, T* Y, int64_t ncols, bool scaled, T 
 fe_ks_status apply_core_emu(Ctx& c, const double* X, double* Y, int64_t ncols, bool scaled, double alpha,
                             bool zero_fill);
 
-constexpr int kLocalConfigs = 5;
+constexpr int kLocalConfigs = 7;
 
 // kernel launchers (fe_ks_local_pN.cu)
 template <typename T, typename TS>
 cudaError_t launch_local(const Ctx& c, const LocalParams<T, TS>& prm, cudaStream_t s);
 template <typename T>
 cudaError_t launch_proj(const Ctx& c, const ProjParams<T>& prm, int n_atoms, cudaStream_t s);
+cudaError_t launch_proj_emu(const Ctx& c, const ProjParams<double>& prm, const ff2* F, int n_atoms, cudaStream_t s);
 
 }  // namespace feks
 

@@ -404,6 +404,394 @@ __global__ void __launch_bounds__(NT) fe_local_kernel(const __grid_constant__ Lo
     cell_tile<T, NP, NQ, VT, CPLX, NT>(p, p.tab, p.cells[ci], blockIdx.x * VT, smem_raw);
 }
 
+// Column-group loads / stores: VPT consecutive columns of one point, as one
+// shared-memory access when VPT * sizeof(T) is 8 or 16 bytes.
+template <typename T, int VPT>
+__device__ __forceinline__ void ld_cols(const T* p, T* out) {
+  if constexpr (VPT * sizeof(T) == 16) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    const T* t = reinterpret_cast<const T*>(&v);
+#pragma unroll
+    for (int u = 0; u < VPT; ++u) out[u] = t[u];
+  } else if constexpr (VPT * sizeof(T) == 8) {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    const T* t = reinterpret_cast<const T*>(&v);
+#pragma unroll
+    for (int u = 0; u < VPT; ++u) out[u] = t[u];
+  } else {
+#pragma unroll
+    for (int u = 0; u < VPT; ++u) out[u] = p[u];
+  }
+}
+template <typename T, int VPT>
+__device__ __forceinline__ void st_cols(T* p, const T* in) {
+  if constexpr (VPT * sizeof(T) == 16) {
+    float4 v;
+    T* t = reinterpret_cast<T*>(&v);
+#pragma unroll
+    for (int u = 0; u < VPT; ++u) t[u] = in[u];
+    *reinterpret_cast<float4*>(p) = v;
+  } else if constexpr (VPT * sizeof(T) == 8) {
+    float2 v;
+    T* t = reinterpret_cast<T*>(&v);
+#pragma unroll
+    for (int u = 0; u < VPT; ++u) t[u] = in[u];
+    *reinterpret_cast<float2*>(p) = v;
+  } else {
+#pragma unroll
+    for (int u = 0; u < VPT; ++u) p[u] = in[u];
+  }
+}
+
+// Phases (1)-(9) of one cell tile with VPT consecutive columns per thread
+// (vector shared-memory accesses; the coefficients of a point are read once
+// for its VPT columns; for complex operators the re/im partner column sits in
+// the same thread).  Gathers from the staged buffer xs only; scatters with
+// reductions.  Same arithmetic, in the same order per column, as tile_body.
+template <typename T, int NP, int NQ, int VT, int VPT, bool CPLX, int NT, class Prm>
+__device__ __forceinline__ void tile_body_v(const Prm& p, const EOTables<T>& tb, int e, int col0, T* A, T* B, T* C,
+                                            const T* cfs, const int* sd, const T* xs) {
+  using S = CellShape<T, NP, NQ, VT, CPLX>;
+  constexpr int SX = S::SX, SY = S::SY, SZ = S::SZ, NQ3 = S::NQ3, NP3 = S::NP3;
+  constexpr int VG = VT / VPT;
+  static_assert(VT % VPT == 0 && (!CPLX || VPT % 2 == 0), "column groups must hold whole complex pairs");
+  const int tid = threadIdx.x;
+
+  // (1) N^1D along z from the staged gather
+#pragma unroll 1
+  for (int w = tid; w < NP * NP * VG; w += NT) {
+    const int v0 = (w % VG) * VPT, ln = w / VG;
+    const int i = ln % NP, j = ln / NP;
+    T x[VPT][NP], t[NQ];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      const int node = i + NP * (j + NP * k);
+      T c[VPT];
+      ld_cols<T, VPT>(xs + node * VT + v0, c);
+      if (p.dscale) {
+        const T ds = p.dscale[sd[node]];
+#pragma unroll
+        for (int u = 0; u < VPT; ++u) c[u] *= ds;
+      }
+#pragma unroll
+      for (int u = 0; u < VPT; ++u) x[u][k] = c[u];
+    }
+    T o[NQ][VPT];
+#pragma unroll
+    for (int u = 0; u < VPT; ++u) {
+      eo_apply<NP, NQ, 1>(x[u], t, tb.N);
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) o[q][u] = t[q];
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) st_cols<T, VPT>(A + i * SX + j * SY + q * SZ + v0, o[q]);
+  }
+  __syncthreads();
+  // (2) N^1D along y
+#pragma unroll 1
+  for (int w = tid; w < NP * NQ * VG; w += NT) {
+    const int v0 = (w % VG) * VPT, ln = w / VG;
+    const int i = ln % NP, qz = ln / NP;
+    T x[VPT][NP], t[NQ], o[NQ][VPT];
+#pragma unroll
+    for (int jj = 0; jj < NP; ++jj) {
+      T c[VPT];
+      ld_cols<T, VPT>(A + i * SX + jj * SY + qz * SZ + v0, c);
+#pragma unroll
+      for (int u = 0; u < VPT; ++u) x[u][jj] = c[u];
+    }
+#pragma unroll
+    for (int u = 0; u < VPT; ++u) {
+      eo_apply<NP, NQ, 1>(x[u], t, tb.N);
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) o[q][u] = t[q];
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) st_cols<T, VPT>(A + i * SX + q * SY + qz * SZ + v0, o[q]);
+  }
+  __syncthreads();
+  // (3) N^1D along x
+#pragma unroll 1
+  for (int w = tid; w < NQ * NQ * VG; w += NT) {
+    const int v0 = (w % VG) * VPT, ln = w / VG;
+    const int qy = ln % NQ, qz = ln / NQ;
+    T x[VPT][NP], t[NQ], o[NQ][VPT];
+#pragma unroll
+    for (int ii = 0; ii < NP; ++ii) {
+      T c[VPT];
+      ld_cols<T, VPT>(A + ii * SX + qy * SY + qz * SZ + v0, c);
+#pragma unroll
+      for (int u = 0; u < VPT; ++u) x[u][ii] = c[u];
+    }
+#pragma unroll
+    for (int u = 0; u < VPT; ++u) {
+      eo_apply<NP, NQ, 1>(x[u], t, tb.N);
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) o[q][u] = t[q];
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) st_cols<T, VPT>(A + q * SX + qy * SY + qz * SZ + v0, o[q]);
+  }
+  __syncthreads();
+  // (4) D~ along x (A -> B) and along y (A -> C)
+#pragma unroll 1
+  for (int w = tid; w < NQ * NQ * VG; w += NT) {
+    const int v0 = (w % VG) * VPT, ln = w / VG;
+    const int a0 = ln % NQ, qz = ln / NQ;
+    T x[VPT][NQ], t[NQ], o[NQ][VPT];
+#pragma unroll
+    for (int r = 0; r < NQ; ++r) {
+      T c[VPT];
+      ld_cols<T, VPT>(A + r * SX + a0 * SY + qz * SZ + v0, c);
+#pragma unroll
+      for (int u = 0; u < VPT; ++u) x[u][r] = c[u];
+    }
+#pragma unroll
+    for (int u = 0; u < VPT; ++u) {
+      eo_apply<NQ, NQ, -1>(x[u], t, tb.D);
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) o[q][u] = t[q];
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) st_cols<T, VPT>(B + q * SX + a0 * SY + qz * SZ + v0, o[q]);
+#pragma unroll
+    for (int r = 0; r < NQ; ++r) {
+      T c[VPT];
+      ld_cols<T, VPT>(A + a0 * SX + r * SY + qz * SZ + v0, c);
+#pragma unroll
+      for (int u = 0; u < VPT; ++u) x[u][r] = c[u];
+    }
+#pragma unroll
+    for (int u = 0; u < VPT; ++u) {
+      eo_apply<NQ, NQ, -1>(x[u], t, tb.D);
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) o[q][u] = t[q];
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) st_cols<T, VPT>(C + a0 * SX + q * SY + qz * SZ + v0, o[q]);
+  }
+  __syncthreads();
+  // (5) D~ along z, quadrature-point step, D~z^T; W_x -> B, W_y -> C, Z -> A
+#pragma unroll 1
+  for (int w = tid; w < NQ * NQ * VG; w += NT) {
+    const int v0 = (w % VG) * VPT, ln = w / VG;
+    const int qx = ln % NQ, qy = ln / NQ;
+    T u_[VPT][NQ], g_[VPT][NQ], z_[VPT][NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      T c[VPT];
+      ld_cols<T, VPT>(A + qx * SX + qy * SY + q * SZ + v0, c);
+#pragma unroll
+      for (int u = 0; u < VPT; ++u) u_[u][q] = c[u];
+    }
+#pragma unroll
+    for (int u = 0; u < VPT; ++u) eo_apply<NQ, NQ, -1>(u_[u], g_[u], tb.D);
+    const T* cf = cfs + qx + NQ * qy;
+#pragma unroll
+    for (int qz = 0; qz < NQ; ++qz) {
+      const int o = qz * NQ * NQ;
+      const int s = qx * SX + qy * SY + qz * SZ + v0;
+      T gx[VPT], gy[VPT], w0[VPT], w1[VPT], kk[VPT];
+      ld_cols<T, VPT>(B + s, gx);
+      ld_cols<T, VPT>(C + s, gy);
+      const T G00 = cf[0 * NQ3 + o], G01 = cf[1 * NQ3 + o], G02 = cf[2 * NQ3 + o];
+      const T G11 = cf[3 * NQ3 + o], G12 = cf[4 * NQ3 + o], G22 = cf[5 * NQ3 + o];
+      const T VL = cf[6 * NQ3 + o];
+      T V0 = Num<T>::zero(), V1 = V0, V2 = V0;
+      if (p.gga) {
+        V0 = cf[7 * NQ3 + o];
+        V1 = cf[8 * NQ3 + o];
+        V2 = cf[9 * NQ3 + o];
+      }
+#pragma unroll
+      for (int u = 0; u < VPT; ++u) {
+        const T gz = g_[u][qz], uu = u_[u][qz];
+        T z = VL * uu;
+        T a0v = fma(G00, gx[u], fma(G01, gy[u], G02 * gz));
+        T a1v = fma(G01, gx[u], fma(G11, gy[u], G12 * gz));
+        T a2v = fma(G02, gx[u], fma(G12, gy[u], G22 * gz));
+        if (p.gga) {
+          z = fma(V0, gx[u], fma(V1, gy[u], fma(V2, gz, z)));
+          a0v = fma(V0, uu, a0v);
+          a1v = fma(V1, uu, a1v);
+          a2v = fma(V2, uu, a2v);
+        }
+        if (CPLX) {
+          const T K0 = cf[10 * NQ3 + o], K1 = cf[11 * NQ3 + o], K2 = cf[12 * NQ3 + o];
+          kk[u] = fma(K0, gx[u], fma(K1, gy[u], K2 * gz));
+        }
+        w0[u] = a0v;
+        w1[u] = a1v;
+        u_[u][qz] = a2v;
+        z_[u][qz] = z;
+      }
+      if (CPLX) {
+        // -i (a + i b) = b - i a : the partner column of u is u ^ 1 in this thread
+#pragma unroll
+        for (int u = 0; u < VPT; ++u) z_[u][qz] += (u & 1) ? -kk[u ^ 1] : kk[u ^ 1];
+      }
+      st_cols<T, VPT>(B + s, w0);
+      st_cols<T, VPT>(C + s, w1);
+    }
+    T t[NQ], o[NQ][VPT];
+#pragma unroll
+    for (int u = 0; u < VPT; ++u) {
+      eo_apply<NQ, NQ, -1>(u_[u], t, tb.Dt);
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) o[q][u] = z_[u][q] + t[q];
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) st_cols<T, VPT>(A + qx * SX + qy * SY + q * SZ + v0, o[q]);
+  }
+  __syncthreads();
+  // (6) D~^T along x on B and along y on C (in place)
+#pragma unroll 1
+  for (int w = tid; w < NQ * NQ * VG; w += NT) {
+    const int v0 = (w % VG) * VPT, ln = w / VG;
+    const int a0 = ln % NQ, qz = ln / NQ;
+    T x[VPT][NQ], t[NQ], o[NQ][VPT];
+#pragma unroll
+    for (int r = 0; r < NQ; ++r) {
+      T c[VPT];
+      ld_cols<T, VPT>(B + r * SX + a0 * SY + qz * SZ + v0, c);
+#pragma unroll
+      for (int u = 0; u < VPT; ++u) x[u][r] = c[u];
+    }
+#pragma unroll
+    for (int u = 0; u < VPT; ++u) {
+      eo_apply<NQ, NQ, -1>(x[u], t, tb.Dt);
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) o[q][u] = t[q];
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) st_cols<T, VPT>(B + q * SX + a0 * SY + qz * SZ + v0, o[q]);
+#pragma unroll
+    for (int r = 0; r < NQ; ++r) {
+      T c[VPT];
+      ld_cols<T, VPT>(C + a0 * SX + r * SY + qz * SZ + v0, c);
+#pragma unroll
+      for (int u = 0; u < VPT; ++u) x[u][r] = c[u];
+    }
+#pragma unroll
+    for (int u = 0; u < VPT; ++u) {
+      eo_apply<NQ, NQ, -1>(x[u], t, tb.Dt);
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) o[q][u] = t[q];
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) st_cols<T, VPT>(C + a0 * SX + q * SY + qz * SZ + v0, o[q]);
+  }
+  __syncthreads();
+  // (7) Z += D~x^T W_x + D~y^T W_y, then N^T along z -> A
+#pragma unroll 1
+  for (int w = tid; w < NQ * NQ * VG; w += NT) {
+    const int v0 = (w % VG) * VPT, ln = w / VG;
+    const int qx = ln % NQ, qy = ln / NQ;
+    T zc[VPT][NQ], t[NP], o[NP][VPT];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const int s = qx * SX + qy * SY + q * SZ + v0;
+      T a[VPT], b[VPT], c[VPT];
+      ld_cols<T, VPT>(A + s, a);
+      ld_cols<T, VPT>(B + s, b);
+      ld_cols<T, VPT>(C + s, c);
+#pragma unroll
+      for (int u = 0; u < VPT; ++u) zc[u][q] = a[u] + (b[u] + c[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < VPT; ++u) {
+      eo_apply<NQ, NP, 1>(zc[u], t, tb.Nt);
+#pragma unroll
+      for (int k = 0; k < NP; ++k) o[k][u] = t[k];
+    }
+#pragma unroll
+    for (int k = 0; k < NP; ++k) st_cols<T, VPT>(A + qx * SX + qy * SY + k * SZ + v0, o[k]);
+  }
+  __syncthreads();
+  // (8) N^T along y
+#pragma unroll 1
+  for (int w = tid; w < NQ * NP * VG; w += NT) {
+    const int v0 = (w % VG) * VPT, ln = w / VG;
+    const int qx = ln % NQ, k = ln / NQ;
+    T x[VPT][NQ], t[NP], o[NP][VPT];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      T c[VPT];
+      ld_cols<T, VPT>(A + qx * SX + q * SY + k * SZ + v0, c);
+#pragma unroll
+      for (int u = 0; u < VPT; ++u) x[u][q] = c[u];
+    }
+#pragma unroll
+    for (int u = 0; u < VPT; ++u) {
+      eo_apply<NQ, NP, 1>(x[u], t, tb.Nt);
+#pragma unroll
+      for (int jj = 0; jj < NP; ++jj) o[jj][u] = t[jj];
+    }
+#pragma unroll
+    for (int jj = 0; jj < NP; ++jj) st_cols<T, VPT>(A + qx * SX + jj * SY + k * SZ + v0, o[jj]);
+  }
+  __syncthreads();
+  // (9) N^T along x, + sum_a F Delta P, assembly by reductions
+#pragma unroll 1
+  for (int w = tid; w < NP * NP * VG; w += NT) {
+    const int v0 = (w % VG) * VPT, ln = w / VG;
+    const int j = ln % NP, k = ln / NP;
+    T x[VPT][NQ], y[VPT][NP];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      T c[VPT];
+      ld_cols<T, VPT>(A + q * SX + j * SY + k * SZ + v0, c);
+#pragma unroll
+      for (int u = 0; u < VPT; ++u) x[u][q] = c[u];
+    }
+#pragma unroll
+    for (int u = 0; u < VPT; ++u) eo_apply<NQ, NP, 1>(x[u], y[u], tb.Nt);
+    if (p.cell_pair_ptr) {
+      const int pb = p.cell_pair_ptr[e], pe = p.cell_pair_ptr[e + 1];
+      for (int pi = pb; pi < pe; ++pi) {
+        const int pr = p.cell_pairs[pi];
+        const int a = p.pair_atom[pr];
+        for (int b = 0; b < p.n_proj; ++b) {
+          const auto* Qa = p.Q + ((int64_t)a * p.n_proj + b) * p.ld + col0 + v0;
+          T q[VPT];
+#pragma unroll
+          for (int u = 0; u < VPT; ++u) q[u] = (col0 + v0 + u < p.ncols) ? Num<T>::in(Qa[u]) : Num<T>::zero();
+          if (!CPLX) {
+            const T* Fr = p.F + ((int64_t)pr * p.n_proj + b) * NP3 + NP * (j + NP * k);
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+              const T f = Fr[i];
+#pragma unroll
+              for (int u = 0; u < VPT; ++u) y[u][i] = fma(f, q[u], y[u][i]);
+            }
+          } else {
+            const T* Fr = p.F + (((int64_t)pr * p.n_proj + b) * NP3 + NP * (j + NP * k)) * 2;
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+              const T fr = Fr[2 * i], fi = Fr[2 * i + 1];
+#pragma unroll
+              for (int u = 0; u < VPT; u += 2) {
+                const T qr = q[u], qi = q[u + 1];
+                y[u][i] += fma(fr, qr, -fi * qi);
+                y[u + 1][i] += fma(fr, qi, fi * qr);
+              }
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      const int d = sd[i + NP * (j + NP * k)];
+      const T ds = p.dscale ? p.dscale[d] : Num<T>::one();
+      auto* yp = p.Y + (int64_t)d * p.ld + col0 + v0;
+#pragma unroll
+      for (int u = 0; u < VPT; ++u)
+        if (col0 + v0 + u < p.ncols) atomicAdd(yp + u, y[u][i] * p.alpha * ds);
+    }
+  }
+}
+
 // Cell-major variant: one CTA per cell of the colour.  It stages the cell's
 // coefficients and DoF list once, then walks all column tiles of the cell,
 // gathering the next tile's rows of X into a second shared buffer with
@@ -464,7 +852,7 @@ __device__ __forceinline__ void stage_rows(const T* __restrict__ X, int64_t ld, 
   asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 
-template <typename T, int NP, int NQ, int VT, bool CPLX, int NT>
+template <typename T, int NP, int NQ, int VT, bool CPLX, int NT, int VPT>
 __global__ void __launch_bounds__(NT) fe_local_staged_kernel(const __grid_constant__ LocalParams<T, T> p) {
   using S = CellShape<T, NP, NQ, VT, CPLX>;
   using SS = StagedShape<T, NP, NQ, VT, CPLX>;
@@ -506,7 +894,10 @@ __global__ void __launch_bounds__(NT) fe_local_staged_kernel(const __grid_consta
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");
       }
       __syncthreads();
-      tile_body<T, NP, NQ, VT, CPLX, NT, true>(p, p.tab, e, t * VT, A, B, C, CF, sd, cur, false);
+      if constexpr (VPT == 1)
+        tile_body<T, NP, NQ, VT, CPLX, NT, true>(p, p.tab, e, t * VT, A, B, C, CF, sd, cur, false);
+      else
+        tile_body_v<T, NP, NQ, VT, VPT, CPLX, NT>(p, p.tab, e, t * VT, A, B, C, CF, sd, cur);
       __syncthreads();
     }
   }
@@ -561,7 +952,7 @@ cudaError_t launch_local_cfg(const Ctx& c, const LocalParams<T, TS>& prm, cudaSt
   return cudaGetLastError();
 }
 
-template <typename T, typename TS, int NP, int NQ, int VT, int NT>
+template <typename T, typename TS, int NP, int NQ, int VT, int NT, int VPT = 1>
 cudaError_t launch_staged_cfg(const Ctx& c, const LocalParams<T, TS>& prm, cudaStream_t s) {
   if constexpr (!std::is_same<T, TS>::value) {
     return cudaErrorInvalidConfiguration;   // the reduction scatter needs T == storage type
@@ -575,7 +966,7 @@ cudaError_t launch_staged_cfg(const Ctx& c, const LocalParams<T, TS>& prm, cudaS
       if constexpr (!SS::fits) {
         return cudaErrorInvalidConfiguration;
       } else {
-        auto k = fe_local_staged_kernel<T, NP, NQ, VT, true, NT>;
+        auto k = fe_local_staged_kernel<T, NP, NQ, VT, true, NT, VPT>;
         if (!attr_done[1][dev]) {
           cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SS::bytes);
           if (err != cudaSuccess) return err;
@@ -588,7 +979,7 @@ cudaError_t launch_staged_cfg(const Ctx& c, const LocalParams<T, TS>& prm, cudaS
       if constexpr (!SS::fits) {
         return cudaErrorInvalidConfiguration;
       } else {
-        auto k = fe_local_staged_kernel<T, NP, NQ, VT, false, NT>;
+        auto k = fe_local_staged_kernel<T, NP, NQ, VT, false, NT, VPT>;
         if (!attr_done[0][dev]) {
           cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SS::bytes);
           if (err != cudaSuccess) return err;
@@ -617,6 +1008,8 @@ cudaError_t launch_local_deg(const Ctx& c, const LocalParams<T, TS>& prm, cudaSt
     case 2: return launch_local_cfg<T, TS, NP, NQ, V2, cfg_nt(V2, NQ)>(c, prm, s);
     case 3: return launch_staged_cfg<T, TS, NP, NQ, V0, cfg_nt(V0, NQ)>(c, prm, s);
     case 4: return launch_staged_cfg<T, TS, NP, NQ, V1, cfg_nt(V1, NQ)>(c, prm, s);
+    case 5: return launch_staged_cfg<T, TS, NP, NQ, V1, cfg_nt(V1 / 2, NQ), 2>(c, prm, s);
+    case 6: return launch_staged_cfg<T, TS, NP, NQ, V1, cfg_nt(V1 / 4, NQ), 4>(c, prm, s);
     default: return launch_local_cfg<T, TS, NP, NQ, V0, cfg_nt(V0, NQ)>(c, prm, s);
   }
 }

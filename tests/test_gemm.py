@@ -9,6 +9,18 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
+def _time(fn, reps=3):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fn()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
 @pytest.mark.parametrize("emulated", [False, True])
 def test_row_gram_and_rotate(emulated):
     g = torch.Generator(device="cuda")
@@ -28,3 +40,14 @@ def test_row_gram_and_rotate(emulated):
     X = fk.row_rotate(Y, E, emulated=emulated)
     refx = Y @ E
     assert (X - refx).abs().max().item() <= 1e-13 * (Y.abs() @ E.abs()).max().item()
+
+
+def test_report_gram_speed():
+    """Not a pass/fail check of speed: records native vs emulated FP64 Gram time."""
+    Y = torch.rand((2_000_000, 256), device="cuda", dtype=torch.float64)
+    nat = _time(lambda: fk.row_gram(Y, Y, emulated=False))
+    try:
+        emu = _time(lambda: fk.row_gram(Y, Y, emulated=True))
+    except fk.FeKsError:
+        emu = float("nan")
+    print(f"\nGram 2e6 x 256: native FP64 {nat:.1f} ms, emulated {emu:.1f} ms")

@@ -51,8 +51,10 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the six-system batched launch")
     ap.add_argument("--no-filter", action="store_true", help="skip the R-ChFSI filter timing")
-    ap.add_argument("--precision", choices=["both", "f64", "f32"], default="both",
-                    help="f32 alone times only the FP32 application (for profiling)")
+    ap.add_argument("--precision", choices=["both", "f64", "f32", "f64e"], default="both",
+                    help="f32 / f64e alone time only that application (for profiling)")
+    ap.add_argument("--config", type=int, default=None,
+                    help="force this tile configuration instead of tuning (for profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle sample")
     return ap.parse_args()
 
@@ -188,7 +190,11 @@ def run_native(args, wl, rank, world):
               fk.FE_KS_F32: torch.complex64 if cplx else torch.float32}[precision]
         X = X64 if dt == X64.dtype else X64.to(dt)
         Y = torch.empty_like(X)
-        best, tune_ms = fk.fe_ks_tune(ctx, X, Y, n_v, precision, reps=1)
+        if args.config is None:
+            best, tune_ms = fk.fe_ks_tune(ctx, X, Y, n_v, precision, reps=1)
+        else:
+            fk.fe_ks_set_config(ctx, precision, args.config)
+            best, tune_ms = args.config, []
         for _ in range(warmup):
             fk.fe_ks_apply(ctx, X, Y, n_v, precision)
         torch.cuda.synchronize()
@@ -221,8 +227,8 @@ def run_native(args, wl, rank, world):
         torch.cuda.empty_cache()
         return out
 
-    f64 = measure(fk.FE_KS_F64, args.steps, args.warmup) if args.precision != "f32" else None
-    f64e = measure(fk.FE_KS_F64E, args.steps, args.warmup) if args.precision == "both" else None
+    f64 = measure(fk.FE_KS_F64, args.steps, args.warmup) if args.precision in ("both", "f64") else None
+    f64e = measure(fk.FE_KS_F64E, args.steps, args.warmup) if args.precision in ("both", "f64e") else None
     mixed = None
     if args.precision == "f32":
         mixed = measure(fk.FE_KS_F32, args.steps, args.warmup)
@@ -313,13 +319,16 @@ def run_filter(args, wl, ctx, hp, X64):
     out["f64_apply_ms_by_n_v"] = nv_ms
     m, n_v = hp.m, wl.n_v
     # (recurrence, FP64-accurate parts, Rayleigh-Ritz GEMMs in cuBLAS FP64 emulation)
+    # (cuBLAS's FP64 emulation on integer tensor cores measured slower than native FP64
+    #  GEMM on this part, 578 vs 240 ms for a 2e6 x 256 Gram matrix, so Rayleigh-Ritz
+    #  uses native FP64 GEMMs)
     plans = {"f64": (fk.FE_KS_F64, fk.FE_KS_F64, False),
              "f64_pairs": (fk.FE_KS_F64E, fk.FE_KS_F64E, False),
-             "mixed": (fk.FE_KS_F32, fk.FE_KS_F64E, False),
-             "mixed_emulated_gemm": (fk.FE_KS_F32, fk.FE_KS_F64E, True)}
+             "mixed": (fk.FE_KS_F32, fk.FE_KS_F64E, False)}
     lam = X = lmax = None
     for name, (prec, exact, emu_gemm) in plans.items():
         sol = RChFSI(ctx, m, n_v, False, degree=20, precision=prec, exact=exact, gemm_emulated=emu_gemm)
+        sol.lanczos_upper_bound()            # warm-up
         t_l, lm = ev_ms(sol.lanczos_upper_bound)
         if lmax is None:
             lmax = lm
@@ -338,17 +347,16 @@ def run_filter(args, wl, ctx, hp, X64):
         torch.cuda.empty_cache()
     out["speedup_filter_mixed_vs_f64"] = out["f64"]["filter_ms"] / out["mixed"]["filter_ms"]
     out["speedup_pass_mixed_vs_f64"] = out["f64"]["pass_ms"] / out["mixed"]["pass_ms"]
-    if "pass_ms" in out["mixed_emulated_gemm"]:
-        out["speedup_pass_mixed_emulated_gemm_vs_f64"] = out["f64"]["pass_ms"] / out["mixed_emulated_gemm"]["pass_ms"]
     del X
     # convergence at 6^3 cells
-    wls = wl.scaled(n=6, n_v=32)
+    wls = wl.scaled(n=6, n_v=32, n_atoms=max(1, wl.n_atoms * 6 ** 3 // wl.n ** 3 + 1))
     hps = HostProblem(wls)
     cs = fk.fe_ks_setup(hps.struct, fk.TERM_ALL, wls.n_v, stream.cuda_stream)
     Xs0 = torch.empty((hps.m, wls.n_v), dtype=torch.float64, device=dev)
     fill_trial(wls, wls.n_v, Xs0, np.float64)
     n_chk = wls.n_v // 4
-    conv = {"workload": f"same recipe, 6^3 cells, N_v={wls.n_v}, residual < 1e-9 on the lowest {n_chk}"}
+    conv = {"workload": f"same recipe, 6^3 cells, {wls.n_atoms} atoms, N_v={wls.n_v}, residual < 1e-9 "
+                        f"on the lowest {n_chk}"}
     lams = {}
     for name, prec, exact in (("f64", fk.FE_KS_F64, fk.FE_KS_F64), ("mixed", fk.FE_KS_F32, fk.FE_KS_F64E)):
         sol = RChFSI(cs, hps.m, wls.n_v, False, degree=20, precision=prec, exact=exact)
@@ -534,7 +542,8 @@ def main():
         return
     f64 = res["f64"]
     if f64 is None:
-        print(json.dumps({"metric": METRIC, "profiling_only": True, "f32_ms": res["mixed"]["ms"]}))
+        pr = res["mixed"] or res["f64e"]
+        print(json.dumps({"metric": METRIC, "profiling_only": True, "precision": args.precision, "ms": pr["ms"]}))
         return
     traffic = load_traffic(f"fe_local_kernel f64 {wl.name}")
     achieved = f64["achieved"]

@@ -322,12 +322,13 @@ def run_filter(args, wl, ctx, hp, X64):
     # (cuBLAS's FP64 emulation on integer tensor cores measured slower than native FP64
     #  GEMM on this part, 578 vs 240 ms for a 2e6 x 256 Gram matrix, so Rayleigh-Ritz
     #  uses native FP64 GEMMs)
+    # (recurrence, FP64-accurate parts, Rayleigh-Ritz GEMMs in pairs of floats)
     plans = {"f64": (fk.FE_KS_F64, fk.FE_KS_F64, False),
-             "f64_pairs": (fk.FE_KS_F64E, fk.FE_KS_F64E, False),
-             "mixed": (fk.FE_KS_F32, fk.FE_KS_F64E, False)}
+             "f64_pairs": (fk.FE_KS_F64E, fk.FE_KS_F64E, True),
+             "mixed": (fk.FE_KS_F32, fk.FE_KS_F64E, True)}
     lam = X = lmax = None
-    for name, (prec, exact, emu_gemm) in plans.items():
-        sol = RChFSI(ctx, m, n_v, False, degree=20, precision=prec, exact=exact, gemm_emulated=emu_gemm)
+    for name, (prec, exact, pair_gemm) in plans.items():
+        sol = RChFSI(ctx, m, n_v, False, degree=20, precision=prec, exact=exact, gemm_pairs=pair_gemm)
         sol.lanczos_upper_bound()            # warm-up
         t_l, lm = ev_ms(sol.lanczos_upper_bound)
         if lmax is None:
@@ -358,8 +359,9 @@ def run_filter(args, wl, ctx, hp, X64):
     conv = {"workload": f"same recipe, 6^3 cells, {wls.n_atoms} atoms, N_v={wls.n_v}, residual < 1e-9 "
                         f"on the lowest {n_chk}"}
     lams = {}
-    for name, prec, exact in (("f64", fk.FE_KS_F64, fk.FE_KS_F64), ("mixed", fk.FE_KS_F32, fk.FE_KS_F64E)):
-        sol = RChFSI(cs, hps.m, wls.n_v, False, degree=20, precision=prec, exact=exact)
+    for name, prec, exact, pg in (("f64", fk.FE_KS_F64, fk.FE_KS_F64, False),
+                                  ("mixed", fk.FE_KS_F32, fk.FE_KS_F64E, True)):
+        sol = RChFSI(cs, hps.m, wls.n_v, False, degree=20, precision=prec, exact=exact, gemm_pairs=pg)
         t, (lam_c, _, res, its) = ev_ms(lambda: sol.run(Xs0.clone(), n_iter=80, tol=1e-9, n_check=n_chk))
         lams[name] = lam_c.cpu().numpy()
         conv[name] = {"iterations": its, "ms": t, "max_residual": float(res[:n_chk].max())}

@@ -309,6 +309,23 @@ fe_ks_status fe_ks_gemm_f64(int trans_a, int trans_b, int64_t m, int64_t n, int6
                             const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
                             int64_t ldc, int emulated, void* cuda_stream);
 
+/*
+ * FP64-accurate dense products for the Rayleigh-Ritz step, computed in pairs
+ * of floats on the FP32 pipe (compensated dot products: exact FMA products,
+ * error-free sums), FP64 in and out:
+ *   fe_ks_gram_ff  : C[n1][n2] = Y^T Z for row-major Y [m][n1], Z [m][n2];
+ *                    the m dimension is split in chunks of 8192 rows whose
+ *                    partial sums are added in a fixed order (deterministic);
+ *                    work: device buffer of fe_ks_gram_ff_workspace bytes.
+ *   fe_ks_rotate_ff: X[m][k] = Y[m][n] E[n][k], all row-major.
+ * Real operators only; stream-ordered on cuda_stream; no allocation.
+ */
+fe_ks_status fe_ks_gram_ff_workspace(int64_t m, int n1, int n2, size_t* bytes);
+fe_ks_status fe_ks_gram_ff(const double* Y, const double* Z, double* C, int64_t m, int n1, int n2, void* work,
+                           size_t work_bytes, void* cuda_stream);
+fe_ks_status fe_ks_rotate_ff(const double* Y, const double* E, double* X, int64_t m, int n, int k,
+                             void* cuda_stream);
+
 /* Change the stream used by later calls. */
 fe_ks_status fe_ks_set_stream(fe_ks_ctx* ctx, void* cuda_stream);
 

@@ -18,14 +18,18 @@ from . import fe_ks as fk
 class RChFSI:
     """precision: arithmetic of the filter's recurrence (FE_KS_F32, FE_KS_F64 or FE_KS_F64E);
     exact: the FP64-accurate path used for the filter's residual, Lanczos, Rayleigh-Ritz and
-    residual norms (FE_KS_F64 native, or FE_KS_F64E pairs of floats)."""
+    residual norms (FE_KS_F64 native, or FE_KS_F64E pairs of floats);
+    gemm_pairs: Rayleigh-Ritz Gram matrices and rotation in pairs of floats (FP64-accurate,
+    FP32 pipe) instead of FP64 cuBLAS; gemm_emulated: cuBLAS's FP64 emulation."""
 
     def __init__(self, ctx, m, n_v, cplx, degree=20, precision=fk.FE_KS_F32, lanczos_steps=10,
-                 exact=fk.FE_KS_F64, gemm_emulated=False):
+                 exact=fk.FE_KS_F64, gemm_emulated=False, gemm_pairs=False):
         self.ctx, self.m, self.n_v, self.cplx = ctx, m, n_v, cplx
         self.degree, self.precision, self.lanczos_steps = degree, precision, lanczos_steps
         self.exact = exact
         self.gemm_emulated = gemm_emulated and not cplx
+        self.gemm_pairs = gemm_pairs and not cplx
+        self._gram_work = None
         self.dt = torch.complex128 if cplx else torch.float64
         self.dev = torch.device("cuda", torch.cuda.current_device())
         nb = fk.fe_ks_cheb_filter_workspace(ctx, n_v, precision)
@@ -94,11 +98,15 @@ class RChFSI:
         return lam.to(torch.float64).contiguous(), self._rotate(Y, E)
 
     def _gram(self, Y, Z):
+        if self.gemm_pairs:
+            return fk.fe_ks_gram_ff(Y, Z.contiguous(), stream=torch.cuda.current_stream().cuda_stream)
         if self.gemm_emulated:
             return fk.row_gram(Y, Z, emulated=True, stream=torch.cuda.current_stream().cuda_stream)
         return Y.conj().T @ Z
 
     def _rotate(self, Y, E):
+        if self.gemm_pairs:
+            return fk.fe_ks_rotate_ff(Y, E.contiguous(), stream=torch.cuda.current_stream().cuda_stream)
         if self.gemm_emulated:
             return fk.row_rotate(Y, E.contiguous(), emulated=True, stream=torch.cuda.current_stream().cuda_stream)
         return (Y @ E).contiguous()

@@ -76,6 +76,9 @@ def _load():
     lib.fe_ks_batch_destroy.restype = None
     lib.fe_ks_gemm_f64.argtypes = [ctypes.c_int, ctypes.c_int, i64, i64, i64, ctypes.c_double, vp, i64, vp, i64,
                                    ctypes.c_double, vp, i64, ctypes.c_int, vp]
+    lib.fe_ks_gram_ff_workspace.argtypes = [i64, ctypes.c_int, ctypes.c_int, P(ctypes.c_size_t)]
+    lib.fe_ks_gram_ff.argtypes = [vp, vp, vp, i64, ctypes.c_int, ctypes.c_int, vp, ctypes.c_size_t, vp]
+    lib.fe_ks_rotate_ff.argtypes = [vp, vp, vp, i64, ctypes.c_int, ctypes.c_int, vp]
     lib.fe_ks_destroy.argtypes = [vp]
     lib.fe_ks_destroy.restype = None
     for name in ("fe_ks_quadrature_points", "fe_ks_setup", "fe_ks_apply", "fe_ks_apply_scaled",
@@ -83,7 +86,7 @@ def _load():
                  "fe_ks_measure_fma_peak", "fe_ks_cheb_filter_workspace", "fe_ks_cheb_filter",
                  "fe_ks_nonlocal_apply_static", "fe_ks_tune", "fe_ks_set_config", "fe_ks_batch_create",
                  "fe_ks_batch_configure", "fe_ks_batch_apply", "fe_ks_batch_status", "fe_ks_batch_info",
-                 "fe_ks_gemm_f64"):
+                 "fe_ks_gemm_f64", "fe_ks_gram_ff_workspace", "fe_ks_gram_ff", "fe_ks_rotate_ff"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -231,6 +234,30 @@ def row_rotate(Y, E, emulated=False, stream=None):
     X = torch.empty((m, k), dtype=torch.float64, device=Y.device)
     # row-major X = Y E  <=>  column-major Xc (k x m) = Ec (k x n) Yc (n x m)
     fe_ks_gemm_f64(0, 0, k, m, n, 1.0, Ec, k, Y, n, 0.0, X, k, emulated, stream)
+    return X
+
+
+def fe_ks_gram_ff(Y, Z, stream=None, work=None):
+    """Y^T Z (row-major FP64 device tensors [m][n1], [m][n2]) in pairs of floats -> [n1][n2]."""
+    import torch
+    m, n1 = Y.shape
+    n2 = Z.shape[1]
+    nb = ctypes.c_size_t()
+    _check(_lib.fe_ks_gram_ff_workspace(m, n1, n2, ctypes.byref(nb)))
+    if work is None or work.numel() < nb.value:
+        work = torch.empty(nb.value, dtype=torch.uint8, device=Y.device)
+    C = torch.empty((n1, n2), dtype=torch.float64, device=Y.device)
+    _check(_lib.fe_ks_gram_ff(_ptr(Y), _ptr(Z), _ptr(C), m, n1, n2, _ptr(work), nb.value, stream))
+    return C
+
+
+def fe_ks_rotate_ff(Y, E, stream=None):
+    """Y E (row-major FP64 device tensors [m][n], [n][k]) in pairs of floats -> [m][k]."""
+    import torch
+    m, n = Y.shape
+    k = E.shape[1]
+    X = torch.empty((m, k), dtype=torch.float64, device=Y.device)
+    _check(_lib.fe_ks_rotate_ff(_ptr(Y), _ptr(E.contiguous()), _ptr(X), m, n, k, stream))
     return X
 
 

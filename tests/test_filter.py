@@ -63,14 +63,15 @@ def test_one_filter_pass_matches_oracle(dense, gpu, precision, tol, resid):
     assert err < tol, err
 
 
-@pytest.mark.parametrize("precision,exact", [(fk.FE_KS_F64, fk.FE_KS_F64), (fk.FE_KS_F32, fk.FE_KS_F64),
-                                             (fk.FE_KS_F32, fk.FE_KS_F64E)])
-def test_eigensolver_converges_to_oracle_eigenvalues(dense, gpu, precision, exact):
+@pytest.mark.parametrize("precision,exact,pairs", [(fk.FE_KS_F64, fk.FE_KS_F64, False),
+                                                   (fk.FE_KS_F32, fk.FE_KS_F64, False),
+                                                   (fk.FE_KS_F32, fk.FE_KS_F64E, True)])
+def test_eigensolver_converges_to_oracle_eigenvalues(dense, gpu, precision, exact, pairs):
     from paper_2512_08571_gb300.chfsi import RChFSI
     P, Hs, ev = dense
     hp, ctx = gpu
     n_conv = WL.n_v - 6
-    solver = RChFSI(ctx, hp.m, WL.n_v, False, degree=20, precision=precision, exact=exact)
+    solver = RChFSI(ctx, hp.m, WL.n_v, False, degree=20, precision=precision, exact=exact, gemm_pairs=pairs)
     lmax = solver.lanczos_upper_bound()
     assert lmax >= ev[-1] - 1e-9
     X0 = torch.from_numpy(trial_vectors(WL)).cuda()

@@ -42,6 +42,22 @@ def test_row_gram_and_rotate(emulated):
     assert (X - refx).abs().max().item() <= 1e-13 * (Y.abs() @ E.abs()).max().item()
 
 
+def test_pair_of_floats_gram_and_rotation():
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    for m, n1, n2 in ((20000, 48, 48), (8192 * 3 + 77, 40, 70)):
+        Y = torch.rand((m, n1), generator=g, device="cuda", dtype=torch.float64) * 2 - 1
+        Z = torch.rand((m, n2), generator=g, device="cuda", dtype=torch.float64) * 2 - 1
+        C = fk.fe_ks_gram_ff(Y, Z)
+        ref = Y.T @ Z
+        scale = (Y.abs().T @ Z.abs()).max().item()
+        assert (C - ref).abs().max().item() <= 1e-13 * scale
+        E = torch.rand((n1, n2), generator=g, device="cuda", dtype=torch.float64) * 2 - 1
+        X = fk.fe_ks_rotate_ff(Y, E)
+        refx = Y @ E
+        assert (X - refx).abs().max().item() <= 1e-13 * (Y.abs() @ E.abs()).max().item()
+
+
 def test_report_gram_speed():
     """Not a pass/fail check of speed: records native vs emulated FP64 Gram time."""
     Y = torch.rand((2_000_000, 256), device="cuda", dtype=torch.float64)
@@ -50,4 +66,9 @@ def test_report_gram_speed():
         emu = _time(lambda: fk.row_gram(Y, Y, emulated=True))
     except fk.FeKsError:
         emu = float("nan")
-    print(f"\nGram 2e6 x 256: native FP64 {nat:.1f} ms, emulated {emu:.1f} ms")
+    pairs = _time(lambda: fk.fe_ks_gram_ff(Y, Y))
+    E = torch.rand((256, 256), device="cuda", dtype=torch.float64)
+    rot_nat = _time(lambda: Y @ E)
+    rot_pairs = _time(lambda: fk.fe_ks_rotate_ff(Y, E))
+    print(f"\nGram 2e6 x 256: native FP64 {nat:.1f} ms, emulated {emu:.1f} ms, pairs of floats {pairs:.1f} ms; "
+          f"rotation: native {rot_nat:.1f} ms, pairs {rot_pairs:.1f} ms")

@@ -362,7 +362,7 @@ def run_filter(args, wl, ctx, hp, X64):
     for name, prec, exact, pg in (("f64", fk.FE_KS_F64, fk.FE_KS_F64, False),
                                   ("mixed", fk.FE_KS_F32, fk.FE_KS_F64E, True)):
         sol = RChFSI(cs, hps.m, wls.n_v, False, degree=20, precision=prec, exact=exact, gemm_pairs=pg)
-        t, (lam_c, _, res, its) = ev_ms(lambda: sol.run(Xs0.clone(), n_iter=80, tol=1e-9, n_check=n_chk))
+        t, (lam_c, _, res, its) = ev_ms(lambda: sol.run(Xs0.clone(), n_iter=120, tol=1e-9, n_check=n_chk))
         lams[name] = lam_c.cpu().numpy()
         conv[name] = {"iterations": its, "ms": t, "max_residual": float(res[:n_chk].max())}
         del sol

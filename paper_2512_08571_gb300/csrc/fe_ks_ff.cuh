@@ -91,6 +91,37 @@ __device__ __forceinline__ ff2 ff_from_double(double x) {
 
 __device__ __forceinline__ double ff_to_double(ff2 a) { return (double)a.hi + (double)a.lo; }
 
+// Split of an FP64 value into hi + lo floats with integer operations only (no
+// FP64-pipe work): hi keeps the leading 24 significant bits (truncated), lo is
+// the remaining 29 bits rounded to a float and scaled by 2^(E-1075).  Exact to
+// about 48 bits for |x| in [2^-74, 2^127]; zero maps to (0, 0); anything else
+// (tiny, huge, inf, NaN) takes the FP64 conversion route.
+__device__ __forceinline__ ff2 ff_split_bits(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned E = (unsigned)(b >> 52) & 0x7FFu;
+  if (E - 949u > 201u) {
+    if (E == 0u) return ff_make(0.f, 0.f);
+    return ff_from_double(x);
+  }
+  const unsigned sgn = (unsigned)(b >> 63) << 31;
+  const unsigned long long M = b & 0xFFFFFFFFFFFFFull;
+  const float hi = __uint_as_float(sgn | ((E - 896u) << 23) | (unsigned)(M >> 29));
+  const float scale = __uint_as_float(sgn | ((E - 948u) << 23));
+  return ff_make(hi, __uint2float_rn((unsigned)(M & 0x1FFFFFFFull)) * scale);
+}
+
+// float -> double by bit placement for normal floats (zero and subnormals take
+// the conversion instruction)
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xFFu;
+  if (e == 0u || e == 0xFFu) return (double)f;
+  const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) |
+                               ((unsigned long long)(e + 896u) << 52) |
+                               ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)d);
+}
+
 __host__ inline ff2 ff_from_double_host(double x) {
   const float h = (float)x;
   return ff_make(h, (float)(x - (double)h));

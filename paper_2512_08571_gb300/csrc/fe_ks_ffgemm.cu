@@ -20,7 +20,9 @@ constexpr int kGramChunk = 8192;
 
 // Compensated dot-product step (Ogita, Rump & Oishi's Dot2, with pair
 // operands): acc.hi is the running float sum, acc.lo the accumulated error
-// terms (left unnormalised until the end): acc += a * b.
+// terms: acc += a * b.  The caller renormalises (ff_renorm) every few steps so
+// that acc.lo stays within a few ulps of acc.hi: left to grow over thousands
+// of terms, its own float rounding would cost about sqrt(n) u^2 of the sum.
 __device__ __forceinline__ void ff_mac(ff2& acc, ff2 a, ff2 b) {
   const float ph = a.hi * b.hi;
   const float pl = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, fmaf(a.hi, b.hi, -ph)));
@@ -30,6 +32,8 @@ __device__ __forceinline__ void ff_mac(ff2& acc, ff2 a, ff2 b) {
   acc.hi = t;
   acc.lo += e + pl;
 }
+
+__device__ __forceinline__ void ff_renorm(ff2& acc) { acc = ff_fast_two_sum(acc.hi, acc.lo); }
 
 // partial[chunk][i][j] = sum over the chunk's rows r of Y[r][i] Z[r][j]
 __global__ void __launch_bounds__(kGT) ff_gram_partial_kernel(const double* __restrict__ Y, const double* __restrict__ Z,
@@ -51,22 +55,29 @@ __global__ void __launch_bounds__(kGT) ff_gram_partial_kernel(const double* __re
       const int kk = idx / kGB, c = idx % kGB;
       const int64_t r = r0 + kk;
       const bool in = r < r_end;
-      Ys[kk][c] = ff_from_double(in && i0 + c < n1 ? Y[r * n1 + i0 + c] : 0.0);
-      Zs[kk][c] = ff_from_double(in && j0 + c < n2 ? Z[r * n2 + j0 + c] : 0.0);
+      Ys[kk][c] = ff_split_bits(in && i0 + c < n1 ? Y[r * n1 + i0 + c] : 0.0);
+      Zs[kk][c] = ff_split_bits(in && j0 + c < n2 ? Z[r * n2 + j0 + c] : 0.0);
     }
     __syncthreads();
-#pragma unroll 4
-    for (int kk = 0; kk < kGK; ++kk) {
-      ff2 a[4], b[4];
+#pragma unroll 1
+    for (int k0 = 0; k0 < kGK; k0 += 4) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        a[q] = Ys[kk][ty * 4 + q];
-        b[q] = Zs[kk][tx * 4 + q];
+      for (int kk = k0; kk < k0 + 4; ++kk) {
+        ff2 a[4], b[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          a[q] = Ys[kk][ty * 4 + q];
+          b[q] = Zs[kk][tx * 4 + q];
+        }
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) ff_mac(acc[p][q], a[p], b[q]);
       }
 #pragma unroll
       for (int p = 0; p < 4; ++p)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) ff_mac(acc[p][q], a[p], b[q]);
+        for (int q = 0; q < 4; ++q) ff_renorm(acc[p][q]);
     }
   }
   double* out = part + (int64_t)blockIdx.z * n1 * n2;
@@ -111,23 +122,30 @@ __global__ void __launch_bounds__(kGT) ff_rotate_kernel(const double* __restrict
     for (int idx = threadIdx.x; idx < kGB * kGK; idx += kGT) {
       const int rr = idx / kGK, ll = idx % kGK;
       const int64_t r = r0 + rr;
-      Ys[rr][ll] = ff_from_double(r < m && l0 + ll < n ? Y[r * n + l0 + ll] : 0.0);
+      Ys[rr][ll] = ff_split_bits(r < m && l0 + ll < n ? Y[r * n + l0 + ll] : 0.0);
       const int le = idx / kGB, c = idx % kGB;
-      Es[le][c] = ff_from_double(l0 + le < n && j0 + c < k ? E[(int64_t)(l0 + le) * k + j0 + c] : 0.0);
+      Es[le][c] = ff_split_bits(l0 + le < n && j0 + c < k ? E[(int64_t)(l0 + le) * k + j0 + c] : 0.0);
     }
     __syncthreads();
-#pragma unroll 4
-    for (int ll = 0; ll < kGK; ++ll) {
-      ff2 a[4], b[4];
+#pragma unroll 1
+    for (int l1 = 0; l1 < kGK; l1 += 4) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        a[q] = Ys[ty * 4 + q][ll];
-        b[q] = Es[ll][tx * 4 + q];
+      for (int ll = l1; ll < l1 + 4; ++ll) {
+        ff2 a[4], b[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          a[q] = Ys[ty * 4 + q][ll];
+          b[q] = Es[ll][tx * 4 + q];
+        }
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) ff_mac(acc[p][q], a[p], b[q]);
       }
 #pragma unroll
       for (int p = 0; p < 4; ++p)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) ff_mac(acc[p][q], a[p], b[q]);
+        for (int q = 0; q < 4; ++q) ff_renorm(acc[p][q]);
     }
   }
 #pragma unroll

@@ -36,8 +36,8 @@ template <>
 struct Num<ff2> {
   static __device__ __forceinline__ ff2 zero() { return ff_make(0.f, 0.f); }
   static __device__ __forceinline__ ff2 one() { return ff_make(1.f, 0.f); }
-  static __device__ __forceinline__ ff2 in(double x) { return ff_from_double(x); }
-  static __device__ __forceinline__ void add_to(double* y, ff2 v) { *y += ff_to_double(v); }
+  static __device__ __forceinline__ ff2 in(double x) { return ff_split_bits(x); }
+  static __device__ __forceinline__ void add_to(double* y, ff2 v) { *y += f2d_bits(v.hi) + f2d_bits(v.lo); }
   static __device__ __forceinline__ ff2 shfl1(ff2 v) {
     return ff_make(__shfl_xor_sync(0xffffffffu, v.hi, 1), __shfl_xor_sync(0xffffffffu, v.lo, 1));
   }

@@ -20,7 +20,7 @@ struct ProjNum {
 template <>
 struct ProjNum<ff2> {
   static __device__ __forceinline__ ff2 zero() { return ff_make(0.f, 0.f); }
-  static __device__ __forceinline__ ff2 in(double x) { return ff_from_double(x); }
+  static __device__ __forceinline__ ff2 in(double x) { return ff_split_bits(x); }
   static __device__ __forceinline__ ff2 in(ff2 x) { return x; }
   template <typename TS>
   static __device__ __forceinline__ TS out(ff2 x) { return ff_to_double(x); }

@@ -374,17 +374,30 @@ def run_filter(args, wl, ctx, hp, X64):
 
 
 # -------------------------------------------------------- batched systems
-def run_batched(args):
-    """Six uneven systems (cell grids 6^3..20^3, degrees 4..8, N_v 16..512, FP64/FP32
-    alternating) in one persistent launch captured in a CUDA graph, against one
-    fe_ks_apply per system.  Returns a dict for the JSON line."""
+def small_systems():
+    """Sixteen small systems (4^3 cells, degrees 4..8, N_v 8..32, FP64/FP32 alternating):
+    the launch-bound regime a batched persistent launch is for."""
+    from synth import Workload
+    out = []
+    for s in range(16):
+        p = 4 + s % 5
+        out.append(Workload(f"S{s}", L=6.0, n=4, p=p, nq=p + 1, n_v=8 * (1 + s % 4), gga=True, n_atoms=2,
+                            seed=8000 + 10 * s, precision="f64" if s % 2 == 0 else "f32"))
+    return out
+
+
+def run_batched(args, wls=None):
+    """Uneven systems (default: six, cell grids 6^3..20^3, degrees 4..8, N_v 16..512,
+    FP64/FP32 alternating) in one persistent launch captured in a CUDA graph, against
+    one fe_ks_apply per system.  Returns a dict for the JSON line."""
     import torch
     from paper_2512_08571_gb300 import fe_ks as fk
     from paper_2512_08571_gb300.problem import HostProblem
     from synth import batched_systems
-    wls = batched_systems()
-    if args.cells:
-        wls = [wl.scaled(n=max(2, wl.n * args.cells // 20)) for wl in wls]
+    if wls is None:
+        wls = batched_systems()
+        if args.cells:
+            wls = [wl.scaled(n=max(2, wl.n * args.cells // 20)) for wl in wls]
     stream = torch.cuda.current_stream()
     prec = [fk.FE_KS_F64 if wl.precision == "f64" else fk.FE_KS_F32 for wl in wls]
     ctxs, Xs, Ys = [], [], []
@@ -401,22 +414,27 @@ def run_batched(args):
     for c, X, Y, wl, pr in zip(ctxs, Xs, Ys, wls, prec):
         fk.fe_ks_tune(c, X, Y, wl.n_v, pr, reps=2)
 
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB > L2
+
     def timed(fn, reps):
+        """Mean of per-rep CUDA-event times, L2 flushed (256 MiB write) before each rep."""
         fn()
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(reps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for e0, e1 in ev:
+            flush.fill_(0.0)
+            e0.record(stream)
             fn()
-        e1.record(stream)
+            e1.record(stream)
         torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / reps
+        return sum(e0.elapsed_time(e1) for e0, e1 in ev) / reps
 
     def separate():
         for c, X, Y, wl, pr in zip(ctxs, Xs, Ys, wls, prec):
             fk.fe_ks_apply(c, X, Y, wl.n_v, pr)
 
-    ms_sep = timed(separate, args.steps)
+    reps = max(args.steps, 20)
+    ms_sep = timed(separate, reps)
     b = fk.fe_ks_batch_create(ctxs, [wl.n_v for wl in wls], prec)
     best = None
     trials = []
@@ -442,13 +460,13 @@ def run_batched(args):
     torch.cuda.synchronize()
     with torch.cuda.graph(g):
         fk.fe_ks_batch_apply(b, Xs, Ys, torch.cuda.current_stream().cuda_stream)
-    ms_graph = timed(g.replay, args.steps)
+    ms_graph = timed(g.replay, reps)
     fk.fe_ks_batch_status(b)
     info = fk.fe_ks_batch_info(b)
     fk.fe_ks_batch_destroy(b)
     for c in ctxs:
         fk.fe_ks_destroy(c)
-    return {"workload": "6 systems: grids " + ",".join(f"{wl.n}^3" for wl in wls) + "; p=" +
+    return {"workload": f"{len(wls)} systems: grids " + ",".join(f"{wl.n}^3" for wl in wls) + "; p=" +
                         ",".join(str(wl.p) for wl in wls) + "; N_v=" + ",".join(str(wl.n_v) for wl in wls) +
                         "; " + ",".join(wl.precision for wl in wls),
             "value": units / (ms_graph * 1e-3), "unit": UNIT, "ms_per_step": ms_graph,
@@ -456,7 +474,8 @@ def run_batched(args):
             "speedup_vs_separate": ms_sep / ms_graph,
             "tuned": {"tile_config": tile, "cells_per_item": cells, "depth": depth, "blocks_per_sm": occ},
             "tuning_trials": trials, "items": info["n_items"], "grid": info["grid"],
-            "smem_bytes": info["smem_bytes"], "graph": True, "x_inputs": "device RNG (seed 5000), U(-1,1)"}
+            "smem_bytes": info["smem_bytes"], "graph": True, "x_inputs": "device RNG (seed 5000), U(-1,1)",
+            "l2": "flushed (256 MiB write) before each timed rep"}
 
 
 # ----------------------------------------------------------- oracle timing
@@ -592,6 +611,7 @@ def main():
         line["filter"] = res["filter"]
     if not args.no_batched:
         line["batched"] = run_batched(args)
+        line["batched_small_systems"] = run_batched(args, small_systems())
     if world == 1 and not args.no_cpu_baseline:
         v, n, el = oracle_sample(wl, args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",

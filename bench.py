@@ -37,6 +37,17 @@ PEAK_FP64_NOMINAL = 1.25e12
 PEAK_FP32_NOMINAL = 152 * 128 * 2 * 2.07e9
 
 
+def _measured_hbm_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0   # fallback figure of an earlier GB300 measurement
+
+
+PEAK_HBM_GBS = _measured_hbm_gbs()
+
+
 def parse():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -51,8 +62,8 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the six-system batched launch")
     ap.add_argument("--no-filter", action="store_true", help="skip the R-ChFSI filter timing")
-    ap.add_argument("--precision", choices=["both", "f64", "f32", "f64e"], default="both",
-                    help="f32 / f64e alone time only that application (for profiling)")
+    ap.add_argument("--precision", choices=["both", "f64", "f32", "f64e", "bf16"], default="both",
+                    help="f32 / f64e / bf16 alone time only that application (for profiling)")
     ap.add_argument("--config", type=int, default=None,
                     help="force this tile configuration instead of tuning (for profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle sample")
@@ -175,6 +186,13 @@ def run_native(args, wl, rank, world):
     m, n_v = hp.m, wl.n_v
     units = m * n_v
     local_flops, proj_flops = alg_flops(wl, info["n_pairs"], n_v)
+    # BF16 tensor-core kernel: executed MMA flops per application (18 MMAs per row tile and
+    # output tile over the six sweeps, (n^2 + 1) / 2 row tiles, 8-column tiles of the block)
+    n1 = wl.p + 1
+    ntl, kdim = (2, 16) if n1 > 8 else (1, 8)
+    cw = 2 if cplx else 1
+    mma_flops = wl.n_cells * ((n_v * cw + 7) // 8) * 18 * ntl * ((n1 * n1 + 1) // 2) * 2 * 16 * 8 * kdim
+    bytes32 = {"xy": m * n_v * cw * 4, "coef": wl.n_cells * info.get("ncoef", 13 if cplx else 10) * wl.nq ** 3 * 4}
 
     def barrier():
         if world > 1:
@@ -187,7 +205,8 @@ def run_native(args, wl, rank, world):
     def measure(precision, steps, warmup):
         dt = {fk.FE_KS_F64: torch.complex128 if cplx else torch.float64,
               fk.FE_KS_F64E: torch.complex128 if cplx else torch.float64,
-              fk.FE_KS_F32: torch.complex64 if cplx else torch.float32}[precision]
+              fk.FE_KS_F32: torch.complex64 if cplx else torch.float32,
+              fk.FE_KS_BF16: torch.complex64 if cplx else torch.float32}[precision]
         X = X64 if dt == X64.dtype else X64.to(dt)
         Y = torch.empty_like(X)
         if args.config is None:
@@ -234,6 +253,12 @@ def run_native(args, wl, rank, world):
         mixed = measure(fk.FE_KS_F32, args.steps, args.warmup)
     elif not args.no_mixed and args.precision == "both":
         mixed = measure(fk.FE_KS_F32, max(args.steps, 20), max(args.warmup, 3))
+    bf16 = None
+    if args.precision == "bf16":
+        bf16 = measure(fk.FE_KS_BF16, args.steps, args.warmup)
+    elif not args.no_mixed and args.precision == "both":
+        bf16 = measure(fk.FE_KS_BF16, max(args.steps, 20), max(args.warmup, 3))
+    peak_mma_live = fk.fe_ks_measure_fma_peak(fk.FE_KS_BF16) * 1e12 if bf16 else None
 
     peak64_live = fk.fe_ks_measure_fma_peak(fk.FE_KS_F64) * 1e12
     peak32_live = fk.fe_ks_measure_fma_peak(fk.FE_KS_F32) * 1e12
@@ -278,16 +303,18 @@ def run_native(args, wl, rank, world):
     del X64
     torch.cuda.empty_cache()
     fk.fe_ks_destroy(ctx)
-    return dict(filter=filt, f64e=f64e, f64=f64, mixed=mixed, e2e=e2e, setup_s=setup_s, info=info, local_flops=local_flops,
+    return dict(filter=filt, f64e=f64e, f64=f64, mixed=mixed, bf16=bf16, peak_mma_live=peak_mma_live,
+                mma_flops_per_apply=mma_flops, bytes32=bytes32, e2e=e2e, setup_s=setup_s, info=info, local_flops=local_flops,
                 peak64_live=peak64_live, peak32_live=peak32_live)
 
 
 # ------------------------------------------------------------ R-ChFSI filter
 def run_filter(args, wl, ctx, hp, X64):
     """One R-ChFSI pass on the workload (Lanczos bound, degree-20 filter,
-    Rayleigh-Ritz) three ways: all native FP64; FP64-accurate pairs of floats;
+    Rayleigh-Ritz) four ways: all native FP64; FP64-accurate pairs of floats;
     mixed (FP32 recurrence, FP64-accurate residual / Lanczos / Rayleigh-Ritz
-    through the pair-of-floats kernel).  Plus a convergence run on the same
+    through the pair-of-floats kernel); the same with the BF16 tensor-core
+    recurrence.  Plus a convergence run on the same
     recipe at 6^3 cells (N_v = 32) to residual 1e-9 on the lowest 8, all-FP64
     against mixed, reporting iterations and the eigenvalue gap."""
     import numpy as np
@@ -318,14 +345,13 @@ def run_filter(args, wl, ctx, hp, X64):
         del Xa, Ya
     out["f64_apply_ms_by_n_v"] = nv_ms
     m, n_v = hp.m, wl.n_v
-    # (recurrence, FP64-accurate parts, Rayleigh-Ritz GEMMs in cuBLAS FP64 emulation)
-    # (cuBLAS's FP64 emulation on integer tensor cores measured slower than native FP64
-    #  GEMM on this part, 578 vs 240 ms for a 2e6 x 256 Gram matrix, so Rayleigh-Ritz
-    #  uses native FP64 GEMMs)
-    # (recurrence, FP64-accurate parts, Rayleigh-Ritz GEMMs in pairs of floats)
+    # plan: (recurrence arithmetic, FP64-accurate parts, Rayleigh-Ritz GEMMs in pairs of floats)
+    # (cuBLAS's FP64 emulation on the integer tensor cores measured slower than native FP64
+    #  GEMM on this part, 578 vs 240 ms for a 2e6 x 256 Gram matrix, so it is not a plan)
     plans = {"f64": (fk.FE_KS_F64, fk.FE_KS_F64, False),
              "f64_pairs": (fk.FE_KS_F64E, fk.FE_KS_F64E, True),
-             "mixed": (fk.FE_KS_F32, fk.FE_KS_F64E, True)}
+             "mixed": (fk.FE_KS_F32, fk.FE_KS_F64E, True),
+             "mixed_bf16": (fk.FE_KS_BF16, fk.FE_KS_F64E, True)}
     lam = X = lmax = None
     for name, (prec, exact, pair_gemm) in plans.items():
         sol = RChFSI(ctx, m, n_v, False, degree=20, precision=prec, exact=exact, gemm_pairs=pair_gemm)
@@ -348,6 +374,8 @@ def run_filter(args, wl, ctx, hp, X64):
         torch.cuda.empty_cache()
     out["speedup_filter_mixed_vs_f64"] = out["f64"]["filter_ms"] / out["mixed"]["filter_ms"]
     out["speedup_pass_mixed_vs_f64"] = out["f64"]["pass_ms"] / out["mixed"]["pass_ms"]
+    out["speedup_filter_bf16_vs_f64"] = out["f64"]["filter_ms"] / out["mixed_bf16"]["filter_ms"]
+    out["speedup_pass_bf16_vs_f64"] = out["f64"]["pass_ms"] / out["mixed_bf16"]["pass_ms"]
     del X
     # convergence at 6^3 cells
     wls = wl.scaled(n=6, n_v=32, n_atoms=max(1, wl.n_atoms * 6 ** 3 // wl.n ** 3 + 1))
@@ -360,14 +388,17 @@ def run_filter(args, wl, ctx, hp, X64):
                         f"on the lowest {n_chk}"}
     lams = {}
     for name, prec, exact, pg in (("f64", fk.FE_KS_F64, fk.FE_KS_F64, False),
-                                  ("mixed", fk.FE_KS_F32, fk.FE_KS_F64E, True)):
+                                  ("mixed", fk.FE_KS_F32, fk.FE_KS_F64E, True),
+                                  ("mixed_bf16", fk.FE_KS_BF16, fk.FE_KS_F64E, True)):
         sol = RChFSI(cs, hps.m, wls.n_v, False, degree=20, precision=prec, exact=exact, gemm_pairs=pg)
         t, (lam_c, _, res, its) = ev_ms(lambda: sol.run(Xs0.clone(), n_iter=120, tol=1e-9, n_check=n_chk))
         lams[name] = lam_c.cpu().numpy()
         conv[name] = {"iterations": its, "ms": t, "max_residual": float(res[:n_chk].max())}
         del sol
     conv["max_eig_diff_mixed_vs_f64_Ha"] = float(np.max(np.abs(lams["mixed"][:n_chk] - lams["f64"][:n_chk])))
+    conv["max_eig_diff_bf16_vs_f64_Ha"] = float(np.max(np.abs(lams["mixed_bf16"][:n_chk] - lams["f64"][:n_chk])))
     conv["speedup"] = conv["f64"]["ms"] / conv["mixed"]["ms"]
+    conv["speedup_bf16"] = conv["f64"]["ms"] / conv["mixed_bf16"]["ms"]
     out["converged_6cubed"] = conv
     fk.fe_ks_destroy(cs)
     return out
@@ -563,10 +594,11 @@ def main():
         return
     f64 = res["f64"]
     if f64 is None:
-        pr = res["mixed"] or res["f64e"]
-        print(json.dumps({"metric": METRIC, "profiling_only": True, "precision": args.precision, "ms": pr["ms"]}))
+        pr = res["mixed"] or res["f64e"] or res["bf16"]
+        print(json.dumps({"metric": METRIC, "profiling_only": True, "precision": args.precision, "ms": pr["ms"],
+                          "value": pr["value"], "local_launch_ms": pr["local_launch_ms"]}))
         return
-    traffic = load_traffic(f"fe_local_kernel f64 {wl.name}")
+    traffic = load_traffic(f"fe_local_kernel f64 {wl.name} cfg{f64['tile_config']}")
     achieved = f64["achieved"]
     roofline = {"bound": "alu", "achieved": achieved / 1e12 if achieved else None,
                 "peak": PEAK_FP64_NOMINAL / 1e12, "unit": "TFLOP/s",
@@ -603,8 +635,27 @@ def main():
                                       "live_probe": res["peak32_live"] / 1e12,
                                       "avg_launch_ms": mixed["local_launch_ms"],
                                       "tile_config": mixed["tile_config"],
+                                      "traffic": load_traffic(f"fe_local_kernel f32 {wl.name} cfg{mixed['tile_config']}"),
                                       "tune_ms_per_config": mixed["tune_ms"]},
                          "clocks": mixed["clocks"], "gpu_launches": mixed["launches"]}
+    bf = res["bf16"]
+    if bf:
+        # HBM roofline (FP32 storage): X read once + Y written once per application, plus
+        # the coefficients; the executed MMA rate is reported against the live mma.sync probe
+        alg_bytes = 2 * res["bytes32"]["xy"] + res["bytes32"]["coef"]
+        t_roof = alg_bytes / (PEAK_HBM_GBS * 1e9)
+        line["bf16_tensor_core"] = {
+            "dtype": "bf16 x bf16 -> f32 (FP32 storage)", "value": bf["value"], "unit": UNIT,
+            "ms_per_step": bf["ms"], "speedup_vs_f64": f64["ms"] / bf["ms"],
+            "speedup_vs_fp32_cuda_core": (mixed["ms"] / bf["ms"]) if mixed else None,
+            "roofline": {"bound": "hbm", "achieved": alg_bytes / (bf["ms"] * 1e-3) / 1e9,
+                         "peak": PEAK_HBM_GBS, "unit": "GB/s", "frac": t_roof / (bf["ms"] * 1e-3),
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                         "alg_bytes_per_apply": alg_bytes,
+                         "avg_launch_ms": bf["local_launch_ms"],
+                         "mma_tflops_executed": res["mma_flops_per_apply"] * 1e-12 / (bf["ms"] * 1e-3),
+                         "mma_sync_live_probe_tflops": res["peak_mma_live"] / 1e12},
+            "clocks": bf["clocks"], "gpu_launches": bf["launches"]}
     if res["e2e"]:
         line["e2e"] = res["e2e"]
     if res["filter"]:

@@ -58,9 +58,13 @@ typedef enum {
 typedef enum {
   FE_KS_F64 = 0,               /* FP64 storage and FP64 arithmetic (DFMA)                  */
   FE_KS_F32 = 1,               /* FP32 storage and FP32 arithmetic (FFMA)                  */
-  FE_KS_F64E = 2               /* FP64 storage, FP64-accurate result; the cell kernel works
-                                  in pairs of floats (hi + lo, ~48 bits) on the FP32 pipe,
-                                  the projections in FP64 (apply / apply_scaled / tune only) */
+  FE_KS_F64E = 2,              /* FP64 storage, FP64-accurate result; the cell kernel and the
+                                  projections work in pairs of floats (hi + lo, ~48 bits) on
+                                  the FP32 pipe (apply / apply_scaled / tune / residual only) */
+  FE_KS_BF16 = 3               /* FP32 storage; the cell kernel's 1D contractions (N, D and
+                                  their transposes) run on the tensor cores with BF16
+                                  operands and FP32 accumulation, the quadrature-point terms,
+                                  projections, expansion and scatter in FP32 */
 } fe_ks_precision;
 
 /* Terms of H that an application includes (terms_mask of fe_ks_setup). */
@@ -256,7 +260,9 @@ fe_ks_status fe_ks_read_profile(fe_ks_ctx* ctx, double ms[3], int64_t launches[3
 /*
  * Diagnostic: FP64 (precision = FE_KS_F64) or FP32 FMA throughput of the
  * current device in TFLOP/s (2 flops per FMA), from a bounded register-only
- * FMA loop on 4 CTAs per SM.  Allocates and frees a small device buffer.
+ * FMA loop on 4 CTAs per SM; precision = FE_KS_BF16 measures the warp-level
+ * tensor-core rate (mma.sync m16n8k16, BF16 operands, FP32 accumulation)
+ * that the BF16 cell kernel uses.  Allocates and frees a small device buffer.
  */
 fe_ks_status fe_ks_measure_fma_peak(int precision, double* tflops);
 

@@ -16,7 +16,7 @@ from . import fe_ks as fk
 
 
 class RChFSI:
-    """precision: arithmetic of the filter's recurrence (FE_KS_F32, FE_KS_F64 or FE_KS_F64E);
+    """precision: arithmetic of the filter's recurrence (FE_KS_F32, FE_KS_BF16, FE_KS_F64 or FE_KS_F64E);
     exact: the FP64-accurate path used for the filter's residual, Lanczos, Rayleigh-Ritz and
     residual norms (FE_KS_F64 native, or FE_KS_F64E pairs of floats);
     gemm_pairs: Rayleigh-Ritz Gram matrices and rotation in pairs of floats (FP64-accurate,

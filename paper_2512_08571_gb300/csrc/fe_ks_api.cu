@@ -441,6 +441,11 @@ fe_ks_status fe_ks_setup(const fe_ks_problem* prob, int terms_mask, int64_t n_v_
             chk(upload(c, &c->f32.dscale, to32(ds), ds.size())) &&
             chk(upload(c, reinterpret_cast<ff2**>(&c->emu.coef), toff(coef), coef.size())) &&
             chk(upload(c, reinterpret_cast<ff2**>(&c->emu.dscale), toff(ds), ds.size()));
+  if (ok) {
+    std::vector<uint32_t> frag(kTcFragWords);
+    build_tc_frags(c->p, frag.data());
+    ok = chk(upload(c, &c->tc_frag, frag.data(), frag.size()));
+  }
   if (ok && want_nl) {
     std::vector<double> hh(prob->h_coef, prob->h_coef + (size_t)prob->n_atoms * prob->n_proj);
     const size_t qn = (size_t)prob->n_atoms * prob->n_proj * n_v_max * (c->cplx ? 2 : 1);
@@ -528,7 +533,7 @@ fe_ks_status fe_ks_info(const fe_ks_ctx* ctx, int64_t* n_dofs, int64_t* n_cells,
 namespace feks {
 
 template <typename T>
-fe_ks_status apply_core(Ctx& c, const T* X, T* Y, int64_t ncols, bool scaled, T alpha, bool zero_fill) {
+fe_ks_status apply_core(Ctx& c, const T* X, T* Y, int64_t ncols, bool scaled, T alpha, bool zero_fill, bool tc) {
   OpData<T>& od = *reinterpret_cast<OpData<T>*>(sizeof(T) == 8 ? (void*)&c.f64 : (void*)&c.f32);
   const T* hcoef = reinterpret_cast<const T*>(sizeof(T) == 8 ? (const void*)c.h64 : (const void*)c.h32);
   cudaStream_t s = c.stream;
@@ -591,7 +596,11 @@ fe_ks_status apply_core(Ctx& c, const T* X, T* Y, int64_t ncols, bool scaled, T 
   for (size_t col = 0; col + 1 < c.colour_ptr.size(); ++col) {
     lp.cells = c.colour_cells + c.colour_ptr[col];
     lp.n_cells = c.colour_ptr[col + 1] - c.colour_ptr[col];
-    cudaError_t err = launch_local<T, T>(c, lp, s);
+    cudaError_t err;
+    if constexpr (std::is_same<T, float>::value)
+      err = tc ? launch_tc(c, lp, s) : launch_local<T, T>(c, lp, s);
+    else
+      err = launch_local<T, T>(c, lp, s);
     if (err != cudaSuccess) return fail(FE_KS_ERR_CUDA, std::string("local kernel: ") + cudaGetErrorString(err));
     if (lp.n_cells > 0) nlaunch[2]++;
   }
@@ -603,8 +612,8 @@ fe_ks_status apply_core(Ctx& c, const T* X, T* Y, int64_t ncols, bool scaled, T 
   return FE_KS_OK;
 }
 
-template fe_ks_status apply_core<double>(Ctx&, const double*, double*, int64_t, bool, double, bool);
-template fe_ks_status apply_core<float>(Ctx&, const float*, float*, int64_t, bool, float, bool);
+template fe_ks_status apply_core<double>(Ctx&, const double*, double*, int64_t, bool, double, bool, bool);
+template fe_ks_status apply_core<float>(Ctx&, const float*, float*, int64_t, bool, float, bool, bool);
 
 // FP64-accurate application computed in pairs of floats: FP64 projections,
 // pair-of-floats cell kernel with FP64 gather / scatter (alpha is applied in
@@ -683,7 +692,7 @@ fe_ks_status apply_core_emu(Ctx& c, const double* X, double* Y, int64_t ncols, b
 }
 
 template <typename T>
-static fe_ks_status apply_impl(fe_ks_ctx* ctx, const void* Xv, void* Yv, int64_t n_v, bool scaled) {
+static fe_ks_status apply_impl(fe_ks_ctx* ctx, const void* Xv, void* Yv, int64_t n_v, bool scaled, bool tc = false) {
   using TS = typename std::conditional<std::is_same<T, ff2>::value, double, T>::type;
   g_last_error.clear();
   if (!ctx) return fail(FE_KS_ERR_ARG, "ctx is NULL");
@@ -700,7 +709,7 @@ static fe_ks_status apply_impl(fe_ks_ctx* ctx, const void* Xv, void* Yv, int64_t
   if constexpr (std::is_same<T, ff2>::value)
     return apply_core_emu(c, static_cast<const double*>(Xv), static_cast<double*>(Yv), ncols, scaled, 1.0, true);
   else
-    return apply_core<T>(c, static_cast<const T*>(Xv), static_cast<T*>(Yv), ncols, scaled, T(1), true);
+    return apply_core<T>(c, static_cast<const T*>(Xv), static_cast<T*>(Yv), ncols, scaled, T(1), true, tc);
 }
 
 }  // namespace feks
@@ -711,6 +720,7 @@ fe_ks_status fe_ks_apply(fe_ks_ctx* ctx, const void* X, void* Y, int64_t n_v, in
   if (precision == FE_KS_F64) return apply_impl<double>(ctx, X, Y, n_v, false);
   if (precision == FE_KS_F64E) return apply_impl<ff2>(ctx, X, Y, n_v, false);
   if (precision == FE_KS_F32) return apply_impl<float>(ctx, X, Y, n_v, false);
+  if (precision == FE_KS_BF16) return apply_impl<float>(ctx, X, Y, n_v, false, true);
   return fail(FE_KS_ERR_UNSUPPORTED, "unknown precision");
 }
 
@@ -732,11 +742,16 @@ fe_ks_status fe_ks_tune(fe_ks_ctx* ctx, const void* X, void* Y, int64_t n_v, int
                         double* ms_per_config, int* best) {
   g_last_error.clear();
   if (!ctx || !X || !Y) return fail(FE_KS_ERR_ARG, "NULL argument");
-  if (precision != FE_KS_F64 && precision != FE_KS_F32 && precision != FE_KS_F64E)
+  if (precision != FE_KS_F64 && precision != FE_KS_F32 && precision != FE_KS_F64E && precision != FE_KS_BF16)
     return fail(FE_KS_ERR_UNSUPPORTED, "unknown precision");
   if (reps < 1) reps = 1;
   Ctx& c = ctx->c;
-  int& cfg = precision == FE_KS_F64 ? c.cfg64 : (precision == FE_KS_F32 ? c.cfg32 : c.cfgE);
+  int single = 0;   // the tensor-core kernel has one configuration
+  int& cfg = precision == FE_KS_F64 ? c.cfg64
+             : precision == FE_KS_F32 ? c.cfg32
+             : precision == FE_KS_F64E ? c.cfgE
+                                       : single;
+  const int n_conf = precision == FE_KS_BF16 ? 1 : kLocalConfigs;
   const int keep = cfg;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -744,6 +759,10 @@ fe_ks_status fe_ks_tune(fe_ks_ctx* ctx, const void* X, void* Y, int64_t n_v, int
   double best_ms = 1e300;
   int best_cfg = keep;
   for (int k = 0; k < kLocalConfigs; ++k) {
+    if (k >= n_conf) {
+      if (ms_per_config) ms_per_config[k] = -1.0;
+      continue;
+    }
     cfg = k;
     double ms = -1.0;
     fe_ks_status st = fe_ks_apply(ctx, X, Y, n_v, precision);   // warm-up, and rejects configs that cannot launch
@@ -776,6 +795,7 @@ fe_ks_status fe_ks_apply_scaled(fe_ks_ctx* ctx, const void* X, void* Y, int64_t 
   if (precision == FE_KS_F64) return apply_impl<double>(ctx, X, Y, n_v, true);
   if (precision == FE_KS_F64E) return apply_impl<ff2>(ctx, X, Y, n_v, true);
   if (precision == FE_KS_F32) return apply_impl<float>(ctx, X, Y, n_v, true);
+  if (precision == FE_KS_BF16) return apply_impl<float>(ctx, X, Y, n_v, true, true);
   return fail(FE_KS_ERR_UNSUPPORTED, "unknown precision");
 }
 

@@ -127,6 +127,8 @@ struct Ctx {
     void* dscale = nullptr;
     EOTables<ff2> tab;
   } emu;
+  // B fragments of the BF16 tensor-core cell kernel: [4 ops][2 tiles][32 lanes][2]
+  uint32_t* tc_frag = nullptr;
   std::vector<void*> allocations;
   // profiling: events recorded per application (start, after fill, after projection, after local)
   bool profiling = false;
@@ -147,10 +149,17 @@ template <typename T>
 void build_eo_tables(int p, int nq, EOTables<T>* out);
 template <>
 void build_eo_tables<ff2>(int p, int nq, EOTables<ff2>* out);
+// B-operand fragments of the tensor-core cell kernel for degree p (n_q = p + 1):
+// out[((op * 2 + tile) * 32 + lane) * 2 + reg], op 0 = N (nodes -> Gauss
+// points), 1 = D (Gauss-point derivative of the nodal basis), 2 = N^T, 3 = D^T.
+constexpr int kTcFragWords = 4 * 2 * 32 * 2;
+void build_tc_frags(int p, uint32_t* out);
 
 // Y (+)= alpha H X or alpha Hs X on the context's stream; zero_fill clears Y first.
+// tc: FP32 storage with the BF16 tensor-core cell kernel (T = float only).
 template <typename T>
-fe_ks_status apply_core(Ctx& c, const T* X, T* Y, int64_t ncols, bool scaled, T alpha, bool zero_fill);
+fe_ks_status apply_core(Ctx& c, const T* X, T* Y, int64_t ncols, bool scaled, T alpha, bool zero_fill,
+                        bool tc = false);
 fe_ks_status apply_core_emu(Ctx& c, const double* X, double* Y, int64_t ncols, bool scaled, double alpha,
                             bool zero_fill);
 
@@ -162,6 +171,9 @@ cudaError_t launch_local(const Ctx& c, const LocalParams<T, TS>& prm, cudaStream
 template <typename T>
 cudaError_t launch_proj(const Ctx& c, const ProjParams<T>& prm, int n_atoms, cudaStream_t s);
 cudaError_t launch_proj_emu(const Ctx& c, const ProjParams<double>& prm, const ff2* F, int n_atoms, cudaStream_t s);
+// BF16 tensor-core cell kernel (fe_ks_tc.cu) for one colour of cells
+cudaError_t launch_tc(const Ctx& c, const LocalParams<float>& lp, cudaStream_t s);
+size_t tc_smem_bytes(int n, bool cplx);
 
 }  // namespace feks
 

@@ -3,6 +3,7 @@
 // Nodes come from Newton's method on Legendre polynomials (three-term
 // recurrence), written here independently of any other component.
 #include <cmath>
+#include <cstring>
 
 #include "fe_ks_internal.h"
 
@@ -136,6 +137,50 @@ void build_eo_tables<ff2>(int p, int nq, EOTables<ff2>* out) {
   ff2* dst = reinterpret_cast<ff2*>(out);
   static_assert(sizeof(EOTables<double>) == sizeof(EOTables<ff2>), "table layouts differ");
   for (size_t i = 0; i < sizeof(EOTables<double>) / sizeof(double); ++i) dst[i] = ff_from_double_host(src[i]);
+}
+
+// Round to the nearest BF16 (ties to even) through the nearest float.
+static uint16_t bf16_bits(double x) {
+  const float f = (float)x;
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+
+void build_tc_frags(int p, uint32_t* out) {
+  const int n = p + 1;
+  double xg[kMaxN], wg[kMaxN], xq[kMaxN], wq[kMaxN], val[kMaxN], der[kMaxN];
+  gauss_lobatto(n, xg, wg);
+  gauss_legendre(n, xq, wq);
+  double Nm[kMaxN][kMaxN], Dm[kMaxN][kMaxN];   // [q][i]
+  for (int q = 0; q < n; ++q) {
+    lagrange_eval(n, xg, xq[q], val, der);
+    for (int i = 0; i < n; ++i) {
+      Nm[q][i] = val[i];
+      Dm[q][i] = der[i];
+    }
+  }
+  // B[k][col] of each op (K x N operand of D = A B; zero outside n x n)
+  auto B = [&](int op, int k, int col) -> double {
+    if (k >= n || col >= n) return 0.0;
+    switch (op) {
+      case 0: return Nm[col][k];   // forward: k = node, col = Gauss point
+      case 1: return Dm[col][k];
+      case 2: return Nm[k][col];   // transposed: k = Gauss point, col = node
+      default: return Dm[k][col];
+    }
+  };
+  for (int op = 0; op < 4; ++op)
+    for (int tile = 0; tile < 2; ++tile)
+      for (int lane = 0; lane < 32; ++lane) {
+        const int g = lane / 4, t = lane % 4, col = 8 * tile + g;
+        for (int r = 0; r < 2; ++r) {
+          const int k = 2 * t + 8 * r;
+          out[((op * 2 + tile) * 32 + lane) * 2 + r] =
+              (uint32_t)bf16_bits(B(op, k, col)) | ((uint32_t)bf16_bits(B(op, k + 1, col)) << 16);
+        }
+      }
 }
 
 template void build_eo_tables<double>(int, int, EOTables<double>*);

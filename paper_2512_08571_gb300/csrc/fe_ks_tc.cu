@@ -1,0 +1,587 @@
+// Tensor-core cell kernel (FE_KS_BF16): the 1D contractions of Algorithm 2 as
+// warp-level BF16 MMAs with FP32 accumulation, the quadrature-point step,
+// nonlocal expansion and scatter in FP32.
+//
+// Paper: Algorithm 2 (cell-level evaluation, eq. ggaReal / eq. ggaCmplx) called
+// from Algorithm 1 (extraction Q C P X, F Delta T3, assembly Q^T).  The
+// sum-factorised chain is regrouped so that every tensor-product factor is a
+// contraction of ONE index with a small dense 1D matrix:
+//   Y0  = N_z N_y N_x X,  Y1_x = N_z N_y D_x X,  Y1_y = N_z D_y N_x X,
+//   Y1_z = D_z N_y N_x X  with D = D~ N (the Gauss-point derivative of the
+//   nodal basis; D~ N = D exactly for n_q = n_p, Sec. 3.2),
+//   Y = N_x^T [N_y^T (N_z^T Z + D_z^T W_z) + D_y^T N_z^T W_y]
+//     + D_x^T N_y^T N_z^T W_x.
+// One sweep contracts a line of n values for 16 lines at a time (8 vector
+// columns x 2 lines): A = data (16 lines x K), B = the 1D matrix (K x n_q),
+// K = 16 (n = 9) or 8 (n <= 8), FP32 accumulators.  Between sweeps the lines
+// are re-formed through shared memory with ldmatrix / stmatrix (.trans), so
+// every array stays [point][8 columns] with the column index fastest; the last
+// forward sweep, the quadrature-point step and the first transposed sweep are
+// chained in registers (an accumulator fragment of one MMA is the A fragment
+// of the next along the same index).
+//
+// The 1D sweeps are tiny (9 x 9 matrices): the legacy warp-level MMA keeps
+// the chain in registers without a tensor-memory round trip per sweep, and
+// the kernel's time goes to shared-memory transposes and the FP32 pointwise
+// work, not to tensor issue.
+#include <cuda_bf16.h>
+
+#include "fe_ks_internal.h"
+
+namespace feks {
+
+// Kernel operands (one colour of cells; FP32 storage).
+struct TcParams {
+  const float* X;
+  float* Y;
+  int64_t ld;
+  int ncols;
+  const int* cell_dofs;
+  const int* cells;
+  int n_cells;
+  const float* coef;       // [E][ncoef][n^3]
+  int ncoef;
+  int gga;
+  const float* dscale;     // D^{-1/2} or nullptr
+  const int* cell_pair_ptr;
+  const int* cell_pairs;
+  const int* pair_atom;
+  const float* F;          // [pair][n_proj][n^3] (complex: x2 interleaved)
+  const float* Q;          // [atom][n_proj][ld], scaled by Delta
+  int n_proj;
+  float alpha;
+  const uint32_t* frag;    // B fragments [4 ops][2 tiles][32 lanes][2]
+};
+
+namespace tc {
+
+// Shared-memory geometry for n = n_p = n_q points per direction.  Point
+// (a, b, c) of any stage sits at a + SY b + SZ c with odd SY and SZ, so that
+// the 8 rows (16 bytes each) of every ldmatrix / stmatrix phase fall in 8
+// different 16-byte bank groups for all three sweep directions.
+template <int N, bool CPLX>
+struct Geom {
+  static constexpr int SY = (N & 1) ? N : N + 1;
+  static constexpr int SZ = (N & 1) ? N * N : N * (N + 1) + 1;
+  static constexpr int NPTS = (N - 1) * (1 + SY + SZ) + 1;
+  static constexpr int N3 = N * N * N;
+  static constexpr bool K16 = N > 8;
+  static constexpr int NTL = K16 ? 2 : 1;        // 8-column output tiles per sweep
+  static constexpr int G = N * N;                 // lines per column per sweep
+  static constexpr int NMT = (G + 1) / 2;         // MMA row tiles (2 lines x 8 columns)
+  static constexpr int NW = N == 9 ? 7 : N == 8 ? 8 : N == 7 ? 7 : N == 6 ? 6 : N == 5 ? 7 : 4;
+  static constexpr int NT = 32 * NW;
+  static constexpr int NC = CPLX ? 14 : 12;       // coefficient floats per point (padded)
+  // byte offsets
+  static constexpr int ARR = NPTS * 16;
+  static constexpr int OFF_ZERO = 6 * ARR;
+  static constexpr int OFF_TRASH = OFF_ZERO + 16;
+  static constexpr int OFF_COEF = OFF_TRASH + 32 * 16;
+  static constexpr int OFF_DOFS = OFF_COEF + NPTS * NC * 4;
+  static constexpr int BYTES = OFF_DOFS + N3 * 4;
+  static_assert(ARR % 16 == 0 && OFF_COEF % 16 == 0 && OFF_DOFS % 4 == 0, "alignment");
+  static_assert((NC * 4) % 16 == 0 || (NC * 4) % 8 == 0, "coefficient loads need 8-byte point stride");
+
+  // point index of line `grp` (the two untouched coordinates) at position k
+  // along the swept direction DIM (0 = x, 1 = y, 2 = z)
+  template <int DIM>
+  __device__ static __forceinline__ int pt(int grp, int k) {
+    const int o1 = grp % N, o2 = grp / N;
+    if constexpr (DIM == 0) return k + SY * o1 + SZ * o2;
+    if constexpr (DIM == 1) return o1 + SY * k + SZ * o2;
+    return o1 + SY * o2 + SZ * k;
+  }
+};
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+template <bool K16>
+__device__ __forceinline__ void ldsm(uint32_t addr, uint32_t (&r)[4]) {
+  if constexpr (K16) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr)
+                 : "memory");
+  } else {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n"
+                 : "=r"(r[0]), "=r"(r[1])
+                 : "r"(addr)
+                 : "memory");
+    r[2] = r[3] = 0u;
+  }
+}
+
+template <int NTL>
+__device__ __forceinline__ void stsm(uint32_t addr, const uint32_t (&r)[4]) {
+  if constexpr (NTL == 2)
+    asm volatile("stmatrix.sync.aligned.m8n8.x4.trans.shared.b16 [%0], {%1,%2,%3,%4};\n" ::"r"(addr), "r"(r[0]),
+                 "r"(r[1]), "r"(r[2]), "r"(r[3])
+                 : "memory");
+  else
+    asm volatile("stmatrix.sync.aligned.m8n8.x2.trans.shared.b16 [%0], {%1,%2};\n" ::"r"(addr), "r"(r[0]), "r"(r[1])
+                 : "memory");
+}
+
+// d += a * b for one 16 x 8 output tile
+template <bool K16>
+__device__ __forceinline__ void mma(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  if constexpr (K16)
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+  else
+    asm("mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(b[0]));
+}
+
+// Accumulator tiles -> BF16 fragment: the A operand of an MMA contracting the
+// same index, and the register order stmatrix expects.
+template <int NTL>
+__device__ __forceinline__ void to_frag(const float (&d)[NTL][4], uint32_t (&a)[4]) {
+  a[0] = pack_bf16(d[0][0], d[0][1]);
+  a[1] = pack_bf16(d[0][2], d[0][3]);
+  if constexpr (NTL == 2) {
+    a[2] = pack_bf16(d[1][0], d[1][1]);
+    a[3] = pack_bf16(d[1][2], d[1][3]);
+  } else {
+    a[2] = a[3] = 0u;
+  }
+}
+
+template <int NTL>
+__device__ __forceinline__ void zero(float (&d)[NTL][4]) {
+#pragma unroll
+  for (int j = 0; j < NTL; ++j) d[j][0] = d[j][1] = d[j][2] = d[j][3] = 0.f;
+}
+
+// Row address of this lane for ldmatrix / stmatrix on row tile (g0, g0 + 1):
+// lane l serves matrix l / 8 (bit 0: line g0 or g0 + 1; bit 1: k + 8) and
+// row l % 8 of it; rows past the line's end map to `spare`.
+template <int N, bool CPLX, int DIM>
+__device__ __forceinline__ uint32_t row_addr(uint32_t arr, int g0, int lane, uint32_t spare) {
+  using Gm = Geom<N, CPLX>;
+  const int grp = g0 + ((lane >> 3) & 1);
+  const int k = (lane & 7) + ((lane & 16) ? 8 : 0);
+  if (grp >= Gm::G || k >= N) return spare;
+  return arr + 16u * (uint32_t)Gm::template pt<DIM>(grp, k);
+}
+
+template <int N, bool CPLX>
+__global__ void __launch_bounds__(Geom<N, CPLX>::NT, 2) fe_tc_kernel(const __grid_constant__ TcParams p) {
+  using Gm = Geom<N, CPLX>;
+  constexpr bool K16 = Gm::K16;
+  constexpr int NTL = Gm::NTL, NT = Gm::NT, NW = Gm::NW, N3 = Gm::N3, NC = Gm::NC;
+  constexpr int SY = Gm::SY, SZ = Gm::SZ;
+  extern __shared__ __align__(16) unsigned char smem[];
+  float* cf = reinterpret_cast<float*>(smem + Gm::OFF_COEF);
+  int* sd = reinterpret_cast<int*>(smem + Gm::OFF_DOFS);
+  const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(smem);
+  uint32_t arr[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) arr[i] = s0 + i * Gm::ARR;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int gq = lane >> 2, tig = lane & 3;   // accumulator row (column v) and column-pair index
+  const uint32_t zero_row = s0 + Gm::OFF_ZERO;
+  const uint32_t trash = s0 + Gm::OFF_TRASH + 16u * lane;
+  if (tid < 4) reinterpret_cast<float*>(smem + Gm::OFF_ZERO)[tid] = 0.f;
+
+  // B fragments of N^T-as-B (forward N), D (forward), N and D (transposed sweeps)
+  uint32_t bN[NTL][2], bD[NTL][2], bNt[NTL][2], bDt[NTL][2];
+#pragma unroll
+  for (int j = 0; j < NTL; ++j)
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      bN[j][r] = p.frag[((0 * 2 + j) * 32 + lane) * 2 + r];
+      bD[j][r] = p.frag[((1 * 2 + j) * 32 + lane) * 2 + r];
+      bNt[j][r] = p.frag[((2 * 2 + j) * 32 + lane) * 2 + r];
+      bDt[j][r] = p.frag[((3 * 2 + j) * 32 + lane) * 2 + r];
+    }
+  const int ntiles = (p.ncols + 7) / 8;
+  const bool vec = (p.ld % 4 == 0) && (((uintptr_t)p.X & 15) == 0);
+
+  for (int ci = blockIdx.x; ci < p.n_cells; ci += gridDim.x) {
+    const int e = p.cells[ci];
+    __syncthreads();   // the previous cell's scatter has finished with sd
+    // stage the DoF list and the coefficients, point-major [pt][NC]
+    for (int w = tid; w < N3; w += NT) sd[w] = p.cell_dofs[(int64_t)e * N3 + w];
+    {
+      const float* gc = p.coef + (int64_t)e * p.ncoef * N3;
+      const int total = p.ncoef * N3;
+#pragma unroll 4
+      for (int w = tid; w < total; w += NT) {
+        const int c = w / N3, q = w - c * N3;
+        const int qx = q % N, qy = (q / N) % N, qz = q / (N * N);
+        cf[(qx + SY * qy + SZ * qz) * NC + c] = p.coef ? gc[w] : 0.f;
+      }
+    }
+    __syncthreads();
+    for (int t = blockIdx.y; t < ntiles; t += gridDim.y) {
+      const int col0 = 8 * t;
+      const bool full = vec && col0 + 8 <= p.ncols;
+      // (1) extraction Q C P X (Algorithm 1): rows of X -> BF16 array 0 [node][8]
+      {
+        constexpr int GPT = (N3 + NT - 1) / NT;
+        float4 xa[GPT], xb[GPT];
+        float sc[GPT];
+#pragma unroll
+        for (int r = 0; r < GPT; ++r) {
+          const int node = tid + r * NT;
+          xa[r] = xb[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+          sc[r] = 1.f;
+          if (node < N3) {
+            const int d = sd[node];
+            const float* xr = p.X + (int64_t)d * p.ld + col0;
+            if (full) {
+              xa[r] = __ldg(reinterpret_cast<const float4*>(xr));
+              xb[r] = __ldg(reinterpret_cast<const float4*>(xr) + 1);
+            } else {
+              float v[8];
+#pragma unroll
+              for (int c = 0; c < 8; ++c) v[c] = (col0 + c < p.ncols) ? __ldg(xr + c) : 0.f;
+              xa[r] = make_float4(v[0], v[1], v[2], v[3]);
+              xb[r] = make_float4(v[4], v[5], v[6], v[7]);
+            }
+            if (p.dscale) sc[r] = __ldg(p.dscale + d);
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < GPT; ++r) {
+          const int node = tid + r * NT;
+          if (node < N3) {
+            const int i = node % N, j = (node / N) % N, k = node / (N * N);
+            const float s = sc[r];
+            uint4 u;
+            u.x = pack_bf16(xa[r].x * s, xa[r].y * s);
+            u.y = pack_bf16(xa[r].z * s, xa[r].w * s);
+            u.z = pack_bf16(xb[r].x * s, xb[r].y * s);
+            u.w = pack_bf16(xb[r].z * s, xb[r].w * s);
+            *reinterpret_cast<uint4*>(smem + 16 * (i + SY * j + SZ * k)) = u;
+          }
+        }
+      }
+      __syncthreads();
+      // (2) x sweep: U = N_x X -> 1, U' = D_x X -> 2
+#pragma unroll 1
+      for (int mt = warp; mt < Gm::NMT; mt += NW) {
+        const int g0 = 2 * mt;
+        uint32_t a[4], o[4];
+        ldsm<K16>(row_addr<N, CPLX, 0>(arr[0], g0, lane, zero_row), a);
+        float u[NTL][4], ud[NTL][4];
+        zero(u);
+        zero(ud);
+#pragma unroll
+        for (int j = 0; j < NTL; ++j) {
+          mma<K16>(u[j], a, bN[j]);
+          mma<K16>(ud[j], a, bD[j]);
+        }
+        to_frag(u, o);
+        stsm<NTL>(row_addr<N, CPLX, 0>(arr[1], g0, lane, trash), o);
+        to_frag(ud, o);
+        stsm<NTL>(row_addr<N, CPLX, 0>(arr[2], g0, lane, trash), o);
+      }
+      __syncthreads();
+      // (3) y sweep: N_y U -> 3, D_y U -> 4, N_y U' -> 5
+#pragma unroll 1
+      for (int mt = warp; mt < Gm::NMT; mt += NW) {
+        const int g0 = 2 * mt;
+        uint32_t a[4], b[4], o[4];
+        ldsm<K16>(row_addr<N, CPLX, 1>(arr[1], g0, lane, zero_row), a);
+        ldsm<K16>(row_addr<N, CPLX, 1>(arr[2], g0, lane, zero_row), b);
+        float t0[NTL][4], t1[NTL][4], t2[NTL][4];
+        zero(t0);
+        zero(t1);
+        zero(t2);
+#pragma unroll
+        for (int j = 0; j < NTL; ++j) {
+          mma<K16>(t0[j], a, bN[j]);
+          mma<K16>(t1[j], a, bD[j]);
+          mma<K16>(t2[j], b, bN[j]);
+        }
+        to_frag(t0, o);
+        stsm<NTL>(row_addr<N, CPLX, 1>(arr[3], g0, lane, trash), o);
+        to_frag(t1, o);
+        stsm<NTL>(row_addr<N, CPLX, 1>(arr[4], g0, lane, trash), o);
+        to_frag(t2, o);
+        stsm<NTL>(row_addr<N, CPLX, 1>(arr[5], g0, lane, trash), o);
+      }
+      __syncthreads();
+      // (4) z sweep -> Y0, Y1 at the quadrature points (registers), the
+      //     quadrature-point step of Algorithm 2, and the transposed z sweep:
+      //     N_z^T Z + D_z^T W_z -> 0, N_z^T W_y -> 1, N_z^T W_x -> 2
+#pragma unroll 1
+      for (int mt = warp; mt < Gm::NMT; mt += NW) {
+        const int g0 = 2 * mt;
+        uint32_t a[4], b[4], c[4];
+        ldsm<K16>(row_addr<N, CPLX, 2>(arr[3], g0, lane, zero_row), a);
+        ldsm<K16>(row_addr<N, CPLX, 2>(arr[4], g0, lane, zero_row), b);
+        ldsm<K16>(row_addr<N, CPLX, 2>(arr[5], g0, lane, zero_row), c);
+        float u[NTL][4], gx[NTL][4], gy[NTL][4], gz[NTL][4];
+        zero(u);
+        zero(gx);
+        zero(gy);
+        zero(gz);
+#pragma unroll
+        for (int j = 0; j < NTL; ++j) {
+          mma<K16>(u[j], a, bN[j]);
+          mma<K16>(gz[j], a, bD[j]);
+          mma<K16>(gy[j], b, bN[j]);
+          mma<K16>(gx[j], c, bN[j]);
+        }
+        // element (j, r): line g0 + (r >> 1), column v = gq, qz = 8 j + 2 tig + (r & 1)
+#pragma unroll
+        for (int j = 0; j < NTL; ++j)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const int grp = g0 + (r >> 1);
+            const int qz = 8 * j + 2 * tig + (r & 1);
+            const bool ok = grp < Gm::G && qz < N;
+            float z = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f, kk = 0.f;
+            const float uu = u[j][r], x = gx[j][r], y = gy[j][r], zz = gz[j][r];
+            if (ok) {
+              // slots: G00 G01 G02 G11 G12 G22 VL V0 V1 V2 (K0 K1 K2); the point
+              // stride is 48 B (real, 16-byte loads) or 56 B (complex, 8-byte loads)
+              const float* c0 = cf + ((grp % N) + SY * (grp / N) + SZ * qz) * NC;
+              float G00, G01, G02, G11, G12, G22, VL, V0, V1, V2;
+              if constexpr (NC % 4 == 0) {
+                const float4 ga = *reinterpret_cast<const float4*>(c0);
+                const float4 gb = *reinterpret_cast<const float4*>(c0 + 4);
+                const float2 gc = *reinterpret_cast<const float2*>(c0 + 8);
+                G00 = ga.x, G01 = ga.y, G02 = ga.z, G11 = ga.w;
+                G12 = gb.x, G22 = gb.y, VL = gb.z, V0 = gb.w, V1 = gc.x, V2 = gc.y;
+              } else {
+                const float2 ga = *reinterpret_cast<const float2*>(c0);
+                const float2 gb = *reinterpret_cast<const float2*>(c0 + 2);
+                const float2 gc = *reinterpret_cast<const float2*>(c0 + 4);
+                const float2 gd = *reinterpret_cast<const float2*>(c0 + 6);
+                const float2 ge = *reinterpret_cast<const float2*>(c0 + 8);
+                G00 = ga.x, G01 = ga.y, G02 = gb.x, G11 = gb.y;
+                G12 = gc.x, G22 = gc.y, VL = gd.x, V0 = gd.y, V1 = ge.x, V2 = ge.y;
+              }
+              z = VL * uu;
+              w0 = fmaf(G00, x, fmaf(G01, y, G02 * zz));
+              w1 = fmaf(G01, x, fmaf(G11, y, G12 * zz));
+              w2 = fmaf(G02, x, fmaf(G12, y, G22 * zz));
+              if (p.gga) {
+                z = fmaf(V0, x, fmaf(V1, y, fmaf(V2, zz, z)));
+                w0 = fmaf(V0, uu, w0);
+                w1 = fmaf(V1, uu, w1);
+                w2 = fmaf(V2, uu, w2);
+              }
+              if constexpr (CPLX) {
+                const float2 ka = *reinterpret_cast<const float2*>(c0 + 10);   // K0 K1
+                const float k2 = c0[12];
+                kk = fmaf(ka.x, x, fmaf(ka.y, y, k2 * zz));
+              }
+            }
+            if constexpr (CPLX) {
+              // -i (a + i b) = b - i a: the real column adds Im, the imaginary one subtracts Re
+              const float kp = __shfl_xor_sync(0xffffffffu, kk, 4);
+              if (ok) z += (gq & 1) ? -kp : kp;
+            }
+            u[j][r] = z;
+            gx[j][r] = w0;
+            gy[j][r] = w1;
+            gz[j][r] = w2;
+          }
+        uint32_t fz[4], fx[4], fy[4], fw[4], o[4];
+        to_frag(u, fz);
+        to_frag(gx, fx);
+        to_frag(gy, fy);
+        to_frag(gz, fw);
+        float va[NTL][4], vb[NTL][4], vc[NTL][4];
+        zero(va);
+        zero(vb);
+        zero(vc);
+#pragma unroll
+        for (int j = 0; j < NTL; ++j) {
+          mma<K16>(va[j], fz, bNt[j]);
+          mma<K16>(va[j], fw, bDt[j]);
+          mma<K16>(vb[j], fy, bNt[j]);
+          mma<K16>(vc[j], fx, bNt[j]);
+        }
+        to_frag(va, o);
+        stsm<NTL>(row_addr<N, CPLX, 2>(arr[0], g0, lane, trash), o);
+        to_frag(vb, o);
+        stsm<NTL>(row_addr<N, CPLX, 2>(arr[1], g0, lane, trash), o);
+        to_frag(vc, o);
+        stsm<NTL>(row_addr<N, CPLX, 2>(arr[2], g0, lane, trash), o);
+      }
+      __syncthreads();
+      // (5) transposed y sweep: N_y^T V_a + D_y^T V_b -> 3, N_y^T V_c -> 4
+#pragma unroll 1
+      for (int mt = warp; mt < Gm::NMT; mt += NW) {
+        const int g0 = 2 * mt;
+        uint32_t a[4], b[4], c[4], o[4];
+        ldsm<K16>(row_addr<N, CPLX, 1>(arr[0], g0, lane, zero_row), a);
+        ldsm<K16>(row_addr<N, CPLX, 1>(arr[1], g0, lane, zero_row), b);
+        ldsm<K16>(row_addr<N, CPLX, 1>(arr[2], g0, lane, zero_row), c);
+        float sa[NTL][4], sb[NTL][4];
+        zero(sa);
+        zero(sb);
+#pragma unroll
+        for (int j = 0; j < NTL; ++j) {
+          mma<K16>(sa[j], a, bNt[j]);
+          mma<K16>(sa[j], b, bDt[j]);
+          mma<K16>(sb[j], c, bNt[j]);
+        }
+        to_frag(sa, o);
+        stsm<NTL>(row_addr<N, CPLX, 1>(arr[3], g0, lane, trash), o);
+        to_frag(sb, o);
+        stsm<NTL>(row_addr<N, CPLX, 1>(arr[4], g0, lane, trash), o);
+      }
+      __syncthreads();
+      // (6) transposed x sweep, + F Delta P (nonlocal), assembly Y += alpha Q^T Y^(e)
+      const int pb = p.cell_pair_ptr ? p.cell_pair_ptr[e] : 0;
+      const int pe = p.cell_pair_ptr ? p.cell_pair_ptr[e + 1] : 0;
+      const int col = col0 + gq;
+#pragma unroll 1
+      for (int mt = warp; mt < Gm::NMT; mt += NW) {
+        const int g0 = 2 * mt;
+        uint32_t a[4], b[4];
+        ldsm<K16>(row_addr<N, CPLX, 0>(arr[3], g0, lane, zero_row), a);
+        ldsm<K16>(row_addr<N, CPLX, 0>(arr[4], g0, lane, zero_row), b);
+        float y[NTL][4];
+        zero(y);
+#pragma unroll
+        for (int j = 0; j < NTL; ++j) {
+          mma<K16>(y[j], a, bNt[j]);
+          mma<K16>(y[j], b, bDt[j]);
+        }
+        if (col < p.ncols) {   // no warp-collective instruction inside this branch
+        for (int pi = pb; pi < pe; ++pi) {
+          const int pr = p.cell_pairs[pi];
+          const int at = p.pair_atom[pr];
+          for (int bb = 0; bb < p.n_proj; ++bb) {
+            const float* Qa = p.Q + ((int64_t)at * p.n_proj + bb) * p.ld;
+            const float* Fb = p.F + ((int64_t)pr * p.n_proj + bb) * N3 * (CPLX ? 2 : 1);
+            float qr, qi = 0.f;
+            if constexpr (CPLX) {
+              qr = __ldg(Qa + (col & ~1));
+              qi = __ldg(Qa + (col | 1));
+            } else {
+              qr = __ldg(Qa + col);
+            }
+#pragma unroll
+            for (int j = 0; j < NTL; ++j)
+#pragma unroll
+              for (int r = 0; r < 4; ++r) {
+                const int grp = g0 + (r >> 1);
+                const int i = 8 * j + 2 * tig + (r & 1);
+                if (grp >= Gm::G || i >= N) continue;
+                const int node = i + N * grp;
+                if constexpr (CPLX) {
+                  const float fr = __ldg(Fb + 2 * node), fi = __ldg(Fb + 2 * node + 1);
+                  y[j][r] += (gq & 1) ? fmaf(fr, qi, fi * qr) : fmaf(fr, qr, -fi * qi);
+                } else {
+                  y[j][r] = fmaf(__ldg(Fb + node), qr, y[j][r]);
+                }
+              }
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < NTL; ++j)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const int grp = g0 + (r >> 1);
+            const int i = 8 * j + 2 * tig + (r & 1);
+            if (grp >= Gm::G || i >= N) continue;
+            const int d = sd[i + N * grp];
+            float val = y[j][r] * p.alpha;
+            if (p.dscale) val *= __ldg(p.dscale + d);
+            atomicAdd(p.Y + (int64_t)d * p.ld + col, val);   // colour-exclusive: no other cell of the launch touches d
+          }
+        }
+        __syncwarp();   // reconverge before the next row tile's ldmatrix
+      }
+      // no barrier here: the next tile's extraction writes array 0 only, which
+      // this sweep does not read; the barrier after it orders everything else
+    }
+  }
+}
+
+template <int N, bool CPLX>
+cudaError_t launch_tc_n(const TcParams& p, cudaStream_t s) {
+  using Gm = Geom<N, CPLX>;
+  if (p.n_cells == 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t err =
+      cudaFuncSetAttribute(fe_tc_kernel<N, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize, Gm::BYTES);
+  if (err != cudaSuccess) return err;
+  const int ntiles = (p.ncols + 7) / 8;
+  // about eight resident waves of CTAs: split the column tiles of a cell over
+  // gridDim.y CTAs when the colour has few cells
+  const int want = 8 * 2 * (sms > 0 ? sms : 152);
+  int gy = (want + p.n_cells - 1) / p.n_cells;
+  gy = gy < 1 ? 1 : (gy > ntiles ? ntiles : gy);
+  if (gy > 65535) gy = 65535;
+  const int gx = p.n_cells < (1 << 30) ? p.n_cells : (1 << 30);
+  fe_tc_kernel<N, CPLX><<<dim3(gx, gy), Gm::NT, Gm::BYTES, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace tc
+
+// Shared-memory bytes of the BF16 cell kernel for n points per direction
+// (0 when n is unsupported).
+size_t tc_smem_bytes(int n, bool cplx) {
+  switch (n) {
+#define FEKS_TC_CASE(NN) \
+  case NN: return cplx ? tc::Geom<NN, true>::BYTES : tc::Geom<NN, false>::BYTES;
+    FEKS_TC_CASE(2)
+    FEKS_TC_CASE(3)
+    FEKS_TC_CASE(4)
+    FEKS_TC_CASE(5)
+    FEKS_TC_CASE(6)
+    FEKS_TC_CASE(7)
+    FEKS_TC_CASE(8)
+    FEKS_TC_CASE(9)
+#undef FEKS_TC_CASE
+    default: return 0;
+  }
+}
+
+cudaError_t launch_tc(const Ctx& c, const LocalParams<float>& lp, cudaStream_t s) {
+  TcParams p{};
+  p.X = lp.X;
+  p.Y = lp.Y;
+  p.ld = lp.ld;
+  p.ncols = lp.ncols;
+  p.cell_dofs = lp.cell_dofs;
+  p.cells = lp.cells;
+  p.n_cells = lp.n_cells;
+  p.coef = lp.coef;
+  p.ncoef = lp.ncoef;
+  p.gga = lp.gga;
+  p.dscale = lp.dscale;
+  p.cell_pair_ptr = lp.cell_pair_ptr;
+  p.cell_pairs = lp.cell_pairs;
+  p.pair_atom = lp.pair_atom;
+  p.F = lp.F;
+  p.Q = lp.Q;
+  p.n_proj = lp.n_proj;
+  p.alpha = lp.alpha;
+  p.frag = c.tc_frag;
+  switch (c.np) {
+#define FEKS_TC_LAUNCH(NN) \
+  case NN: return c.cplx ? tc::launch_tc_n<NN, true>(p, s) : tc::launch_tc_n<NN, false>(p, s);
+    FEKS_TC_LAUNCH(2)
+    FEKS_TC_LAUNCH(3)
+    FEKS_TC_LAUNCH(4)
+    FEKS_TC_LAUNCH(5)
+    FEKS_TC_LAUNCH(6)
+    FEKS_TC_LAUNCH(7)
+    FEKS_TC_LAUNCH(8)
+    FEKS_TC_LAUNCH(9)
+#undef FEKS_TC_LAUNCH
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace feks

@@ -596,7 +596,8 @@ def main():
     if f64 is None:
         pr = res["mixed"] or res["f64e"] or res["bf16"]
         print(json.dumps({"metric": METRIC, "profiling_only": True, "precision": args.precision, "ms": pr["ms"],
-                          "value": pr["value"], "local_launch_ms": pr["local_launch_ms"]}))
+                          "value": pr["value"], "local_launch_ms": pr["local_launch_ms"],
+                          "profile_ms_per_step": {k: v[0] / max(1, args.steps) for k, v in pr["prof"].items()}}))
         return
     traffic = load_traffic(f"fe_local_kernel f64 {wl.name} cfg{f64['tile_config']}")
     achieved = f64["achieved"]

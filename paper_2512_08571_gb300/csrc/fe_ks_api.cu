@@ -449,6 +449,7 @@ fe_ks_status fe_ks_setup(const fe_ks_problem* prob, int terms_mask, int64_t n_v_
   if (ok && want_nl) {
     std::vector<double> hh(prob->h_coef, prob->h_coef + (size_t)prob->n_atoms * prob->n_proj);
     const size_t qn = (size_t)prob->n_atoms * prob->n_proj * n_v_max * (c->cplx ? 2 : 1);
+    const size_t pn = (size_t)c->n_pairs * prob->n_proj * n_v_max * (c->cplx ? 2 : 1);
     ok = chk(upload(c, &c->f64.F, F.data(), F.size())) && chk(upload(c, &c->f32.F, to32(F), F.size())) &&
          chk(upload(c, reinterpret_cast<ff2**>(&c->emu.F), toff(F), F.size())) &&
          chk(upload(c, &c->h64, hh.data(), hh.size())) && chk(upload(c, &c->h32, to32(hh), hh.size())) &&
@@ -457,7 +458,13 @@ fe_ks_status fe_ks_setup(const fe_ks_problem* prob, int terms_mask, int64_t n_v_
          chk(upload(c, &c->atom_pair_ptr, atom_pair_ptr.data(), atom_pair_ptr.size())) &&
          chk(upload(c, &c->cell_pair_ptr, cell_pair_ptr.data(), cell_pair_ptr.size())) &&
          chk(upload(c, &c->cell_pairs, cell_pairs.data(), cell_pairs.size())) &&
-         chk(upload<double>(c, &c->f64.Q, nullptr, qn)) && chk(upload<float>(c, &c->f32.Q, nullptr, qn));
+         chk(upload<double>(c, &c->f64.Q, nullptr, qn)) && chk(upload<float>(c, &c->f32.Q, nullptr, qn)) &&
+         chk(upload<double>(c, &c->f64.part, nullptr, pn)) && chk(upload<float>(c, &c->f32.part, nullptr, pn));
+    if (ok) {
+      std::vector<uint2> fpack;
+      build_tc_fpack(c->np, c->cplx != 0, prob->n_proj, c->n_pairs, F.data(), fpack);
+      ok = chk(upload(c, &c->tc_fpack, fpack.data(), fpack.size()));
+    }
   }
   if (!ok) {
     std::string msg = g_last_error;
@@ -570,7 +577,9 @@ fe_ks_status apply_core(Ctx& c, const T* X, T* Y, int64_t ncols, bool scaled, T 
     pp.Q = od.Q;
     pp.n_proj = c.n_proj;
     pp.np3 = c.np3;
-    cudaError_t err = launch_proj<T>(c, pp, c.n_atoms, s);
+    pp.part = od.part;
+    pp.n_pairs = c.n_pairs;
+    cudaError_t err = launch_proj_pairs<T>(c, pp, c.n_atoms, s);
     if (err != cudaSuccess) return fail(FE_KS_ERR_CUDA, std::string("projection kernel: ") + cudaGetErrorString(err));
     nlaunch[1] = 1;
   }
@@ -653,7 +662,9 @@ fe_ks_status apply_core_emu(Ctx& c, const double* X, double* Y, int64_t ncols, b
     pp.Q = c.f64.Q;
     pp.n_proj = c.n_proj;
     pp.np3 = c.np3;
-    cudaError_t err = launch_proj_emu(c, pp, static_cast<const ff2*>(c.emu.F), c.n_atoms, s);
+    pp.part = c.f64.part;
+    pp.n_pairs = c.n_pairs;
+    cudaError_t err = launch_proj_pairs_emu(c, pp, static_cast<const ff2*>(c.emu.F), c.n_atoms, s);
     if (err != cudaSuccess) return fail(FE_KS_ERR_CUDA, std::string("projection kernel: ") + cudaGetErrorString(err));
     nlaunch[1] = 1;
   }

@@ -50,6 +50,7 @@ struct OpData {
   T* F = nullptr;          // [n_pairs][n_proj][n_p^3] (complex: x2 interleaved)
   T* dscale = nullptr;     // [m] D^{-1/2}
   T* Q = nullptr;          // workspace [n_atoms][n_proj][ncols_max]
+  T* part = nullptr;       // projection partials [n_pairs][n_proj][ncols_max]
   EOTables<T> tab;
 };
 
@@ -95,6 +96,8 @@ struct ProjParams {
   T* Q;
   int n_proj;
   int np3;
+  T* part = nullptr;       // pair partials [n_pairs][n_proj][ld] (pair form)
+  int64_t n_pairs = 0;
 };
 
 struct Ctx {
@@ -129,6 +132,7 @@ struct Ctx {
   } emu;
   // B fragments of the BF16 tensor-core cell kernel: [4 ops][2 tiles][32 lanes][2]
   uint32_t* tc_frag = nullptr;
+  uint2* tc_fpack = nullptr;   // F as expansion B fragments (when the nonlocal term is present)
   std::vector<void*> allocations;
   // profiling: events recorded per application (start, after fill, after projection, after local)
   bool profiling = false;
@@ -154,6 +158,11 @@ void build_eo_tables<ff2>(int p, int nq, EOTables<ff2>* out);
 // points), 1 = D (Gauss-point derivative of the nodal basis), 2 = N^T, 3 = D^T.
 constexpr int kTcFragWords = 4 * 2 * 32 * 2;
 void build_tc_frags(int p, uint32_t* out);
+uint16_t bf16_bits(double x);   // nearest BF16 (ties to even), as its bit pattern
+// The projector matrices F [pair][n_proj][n^3] (complex: x2 interleaved) as BF16
+// B fragments of the tensor-core kernel's expansion MMAs:
+// out[pair][row tile][half][8-column tile][K step][lane] (uint2 per lane).
+void build_tc_fpack(int n, bool cplx, int n_proj, int64_t n_pairs, const double* F, std::vector<uint2>& out);
 
 // Y (+)= alpha H X or alpha Hs X on the context's stream; zero_fill clears Y first.
 // tc: FP32 storage with the BF16 tensor-core cell kernel (T = float only).
@@ -171,6 +180,11 @@ cudaError_t launch_local(const Ctx& c, const LocalParams<T, TS>& prm, cudaStream
 template <typename T>
 cudaError_t launch_proj(const Ctx& c, const ProjParams<T>& prm, int n_atoms, cudaStream_t s);
 cudaError_t launch_proj_emu(const Ctx& c, const ProjParams<double>& prm, const ff2* F, int n_atoms, cudaStream_t s);
+// pair form of the projection (needs prm.part and prm.n_pairs)
+template <typename T>
+cudaError_t launch_proj_pairs(const Ctx& c, const ProjParams<T>& prm, int n_atoms, cudaStream_t s);
+cudaError_t launch_proj_pairs_emu(const Ctx& c, const ProjParams<double>& prm, const ff2* F, int n_atoms,
+                                  cudaStream_t s);
 // BF16 tensor-core cell kernel (fe_ks_tc.cu) for one colour of cells
 cudaError_t launch_tc(const Ctx& c, const LocalParams<float>& lp, cudaStream_t s);
 size_t tc_smem_bytes(int n, bool cplx);

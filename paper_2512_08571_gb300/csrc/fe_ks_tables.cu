@@ -140,7 +140,7 @@ void build_eo_tables<ff2>(int p, int nq, EOTables<ff2>* out) {
 }
 
 // Round to the nearest BF16 (ties to even) through the nearest float.
-static uint16_t bf16_bits(double x) {
+uint16_t bf16_bits(double x) {
   const float f = (float)x;
   uint32_t u;
   std::memcpy(&u, &f, 4);

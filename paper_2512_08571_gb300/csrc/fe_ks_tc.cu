@@ -51,6 +51,7 @@ struct TcParams {
   int n_proj;
   float alpha;
   const uint32_t* frag;    // B fragments [4 ops][2 tiles][32 lanes][2]
+  const uint2* fpack;      // F as BF16 B fragments [pair][row tile][half][tile][K step][32 lanes]
 };
 
 namespace tc {
@@ -74,11 +75,15 @@ struct Geom {
   static constexpr int NC = CPLX ? 14 : 12;       // coefficient floats per point (padded)
   // byte offsets
   static constexpr int ARR = NPTS * 16;
-  static constexpr int OFF_ZERO = 6 * ARR;
+  static constexpr int OFF_ZERO = 3 * ARR;
   static constexpr int OFF_TRASH = OFF_ZERO + 16;
   static constexpr int OFF_COEF = OFF_TRASH + 32 * 16;
   static constexpr int OFF_DOFS = OFF_COEF + NPTS * NC * 4;
   static constexpr int BYTES = OFF_DOFS + N3 * 4;
+  // Two resident CTAs per SM.  (Three fit the shared memory at n = 9, but the
+  // register cap that lets 21 warps share the SM's four 16K-register files
+  // (80 per thread) made the kernel spill and measured no faster.)
+  static constexpr int MINB = 2;
   static_assert(ARR % 16 == 0 && OFF_COEF % 16 == 0 && OFF_DOFS % 4 == 0, "alignment");
   static_assert((NC * 4) % 16 == 0 || (NC * 4) % 8 == 0, "coefficient loads need 8-byte point stride");
 
@@ -139,6 +144,21 @@ __device__ __forceinline__ void mma(float (&d)[4], const uint32_t (&a)[4], const
         : "r"(a[0]), "r"(a[1]), "r"(b[0]));
 }
 
+// d = a * b (zero accumulator input)
+template <bool K16>
+__device__ __forceinline__ void mma0(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  const float z = 0.f;
+  if constexpr (K16)
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%10,%10,%10,%10};\n"
+        : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "f"(z));
+  else
+    asm("mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%7,%7,%7,%7};\n"
+        : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(b[0]), "f"(z));
+}
+
 // Accumulator tiles -> BF16 fragment: the A operand of an MMA contracting the
 // same index, and the register order stmatrix expects.
 template <int NTL>
@@ -159,31 +179,34 @@ __device__ __forceinline__ void zero(float (&d)[NTL][4]) {
   for (int j = 0; j < NTL; ++j) d[j][0] = d[j][1] = d[j][2] = d[j][3] = 0.f;
 }
 
-// Row address of this lane for ldmatrix / stmatrix on row tile (g0, g0 + 1):
-// lane l serves matrix l / 8 (bit 0: line g0 or g0 + 1; bit 1: k + 8) and
-// row l % 8 of it; rows past the line's end map to `spare`.
+// Byte offset of this lane's row for ldmatrix / stmatrix on row tile
+// (g0, g0 + 1) along direction DIM, or -1 past the line's end: lane l serves
+// matrix l / 8 (bit 0: line g0 or g0 + 1; bit 1: k + 8) and row l % 8 of it.
 template <int N, bool CPLX, int DIM>
-__device__ __forceinline__ uint32_t row_addr(uint32_t arr, int g0, int lane, uint32_t spare) {
+__device__ __forceinline__ int row_off(int g0, int lane) {
   using Gm = Geom<N, CPLX>;
   const int grp = g0 + ((lane >> 3) & 1);
   const int k = (lane & 7) + ((lane & 16) ? 8 : 0);
-  if (grp >= Gm::G || k >= N) return spare;
-  return arr + 16u * (uint32_t)Gm::template pt<DIM>(grp, k);
+  if (grp >= Gm::G || k >= N) return -1;
+  return 16 * Gm::template pt<DIM>(grp, k);
+}
+
+__device__ __forceinline__ uint32_t at(uint32_t arr, int off, uint32_t spare) {
+  return off >= 0 ? arr + (uint32_t)off : spare;
 }
 
 template <int N, bool CPLX>
-__global__ void __launch_bounds__(Geom<N, CPLX>::NT, 2) fe_tc_kernel(const __grid_constant__ TcParams p) {
+__global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_kernel(const __grid_constant__ TcParams p) {
   using Gm = Geom<N, CPLX>;
   constexpr bool K16 = Gm::K16;
-  constexpr int NTL = Gm::NTL, NT = Gm::NT, NW = Gm::NW, N3 = Gm::N3, NC = Gm::NC;
+  constexpr int NTL = Gm::NTL, NT = Gm::NT, NW = Gm::NW, N3 = Gm::N3, NC = Gm::NC, NMT = Gm::NMT;
   constexpr int SY = Gm::SY, SZ = Gm::SZ;
+  constexpr int S = CPLX ? 2 : 1;   // K steps of the expansion (F real part, F imaginary part)
   extern __shared__ __align__(16) unsigned char smem[];
   float* cf = reinterpret_cast<float*>(smem + Gm::OFF_COEF);
   int* sd = reinterpret_cast<int*>(smem + Gm::OFF_DOFS);
   const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(smem);
-  uint32_t arr[6];
-#pragma unroll
-  for (int i = 0; i < 6; ++i) arr[i] = s0 + i * Gm::ARR;
+  const uint32_t A0 = s0, A1 = s0 + Gm::ARR, A2 = s0 + 2 * Gm::ARR;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int gq = lane >> 2, tig = lane & 3;   // accumulator row (column v) and column-pair index
   const uint32_t zero_row = s0 + Gm::OFF_ZERO;
@@ -216,14 +239,18 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, 2) fe_tc_kernel(const __gri
       for (int w = tid; w < total; w += NT) {
         const int c = w / N3, q = w - c * N3;
         const int qx = q % N, qy = (q / N) % N, qz = q / (N * N);
-        cf[(qx + SY * qy + SZ * qz) * NC + c] = p.coef ? gc[w] : 0.f;
+        cf[(qx + SY * qy + SZ * qz) * NC + c] = gc[w];
       }
     }
+    const int pb = p.cell_pair_ptr ? p.cell_pair_ptr[e] : 0;
+    const int pe = p.cell_pair_ptr ? p.cell_pair_ptr[e + 1] : 0;
     __syncthreads();
     for (int t = blockIdx.y; t < ntiles; t += gridDim.y) {
       const int col0 = 8 * t;
+      const int col = col0 + gq;
       const bool full = vec && col0 + 8 <= p.ncols;
-      // (1) extraction Q C P X (Algorithm 1): rows of X -> BF16 array 0 [node][8]
+      // (1) extraction Q C P X (Algorithm 1): rows of X -> BF16 array 2 [node][8]
+      //     (array 2 is not read by the previous tile's last sweep)
       {
         constexpr int GPT = (N3 + NT - 1) / NT;
         float4 xa[GPT], xb[GPT];
@@ -260,77 +287,102 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, 2) fe_tc_kernel(const __gri
             u.y = pack_bf16(xa[r].z * s, xa[r].w * s);
             u.z = pack_bf16(xb[r].x * s, xb[r].y * s);
             u.w = pack_bf16(xb[r].z * s, xb[r].w * s);
-            *reinterpret_cast<uint4*>(smem + 16 * (i + SY * j + SZ * k)) = u;
+            *reinterpret_cast<uint4*>(smem + 2 * Gm::ARR + 16 * (i + SY * j + SZ * k)) = u;
           }
         }
       }
       __syncthreads();
-      // (2) x sweep: U = N_x X -> 1, U' = D_x X -> 2
+      // Every sweep below reads and writes the same points (the two lines of its
+      // row tile, all positions along the swept direction), so the arrays are
+      // updated in place; ldmatrix results are in registers before the stores.
+      // (2) x sweep: U = N_x X -> 0, U' = D_x X -> 1.  Each warp takes BX row
+      //     tiles at a time so that 4 BX independent MMAs are in flight (the
+      //     warp-level MMA has a latency of ~100 cycles on this part).
+      {
+        constexpr int BX = 3;
 #pragma unroll 1
-      for (int mt = warp; mt < Gm::NMT; mt += NW) {
-        const int g0 = 2 * mt;
-        uint32_t a[4], o[4];
-        ldsm<K16>(row_addr<N, CPLX, 0>(arr[0], g0, lane, zero_row), a);
-        float u[NTL][4], ud[NTL][4];
-        zero(u);
-        zero(ud);
+        for (int mt0 = warp; mt0 < NMT; mt0 += NW * BX) {
+          int off[BX];
+          uint32_t a[BX][4];
+          float u[BX][NTL][4], ud[BX][NTL][4];
 #pragma unroll
-        for (int j = 0; j < NTL; ++j) {
-          mma<K16>(u[j], a, bN[j]);
-          mma<K16>(ud[j], a, bD[j]);
+          for (int b = 0; b < BX; ++b) {
+            const int mt = mt0 + b * NW;
+            off[b] = mt < NMT ? row_off<N, CPLX, 0>(2 * mt, lane) : -1;
+            ldsm<K16>(at(A2, off[b], zero_row), a[b]);
+          }
+#pragma unroll
+          for (int b = 0; b < BX; ++b)
+#pragma unroll
+            for (int j = 0; j < NTL; ++j) {
+              mma0<K16>(u[b][j], a[b], bN[j]);
+              mma0<K16>(ud[b][j], a[b], bD[j]);
+            }
+#pragma unroll
+          for (int b = 0; b < BX; ++b) {
+            uint32_t o[4];
+            to_frag(u[b], o);
+            stsm<NTL>(at(A0, off[b], trash), o);
+            to_frag(ud[b], o);
+            stsm<NTL>(at(A1, off[b], trash), o);
+          }
         }
-        to_frag(u, o);
-        stsm<NTL>(row_addr<N, CPLX, 0>(arr[1], g0, lane, trash), o);
-        to_frag(ud, o);
-        stsm<NTL>(row_addr<N, CPLX, 0>(arr[2], g0, lane, trash), o);
       }
       __syncthreads();
-      // (3) y sweep: N_y U -> 3, D_y U -> 4, N_y U' -> 5
+      // (3) y sweep: N_y U -> 0, D_y U -> 1, N_y U' -> 2 (BY row tiles per warp at a time)
+      {
+        constexpr int BY = 2;
 #pragma unroll 1
-      for (int mt = warp; mt < Gm::NMT; mt += NW) {
-        const int g0 = 2 * mt;
-        uint32_t a[4], b[4], o[4];
-        ldsm<K16>(row_addr<N, CPLX, 1>(arr[1], g0, lane, zero_row), a);
-        ldsm<K16>(row_addr<N, CPLX, 1>(arr[2], g0, lane, zero_row), b);
-        float t0[NTL][4], t1[NTL][4], t2[NTL][4];
-        zero(t0);
-        zero(t1);
-        zero(t2);
+        for (int mt0 = warp; mt0 < NMT; mt0 += NW * BY) {
+          int off[BY];
+          uint32_t a[BY][4], b2[BY][4];
+          float t0[BY][NTL][4], t1[BY][NTL][4], t2[BY][NTL][4];
 #pragma unroll
-        for (int j = 0; j < NTL; ++j) {
-          mma<K16>(t0[j], a, bN[j]);
-          mma<K16>(t1[j], a, bD[j]);
-          mma<K16>(t2[j], b, bN[j]);
+          for (int b = 0; b < BY; ++b) {
+            const int mt = mt0 + b * NW;
+            off[b] = mt < NMT ? row_off<N, CPLX, 1>(2 * mt, lane) : -1;
+            ldsm<K16>(at(A0, off[b], zero_row), a[b]);
+            ldsm<K16>(at(A1, off[b], zero_row), b2[b]);
+          }
+#pragma unroll
+          for (int b = 0; b < BY; ++b)
+#pragma unroll
+            for (int j = 0; j < NTL; ++j) {
+              mma0<K16>(t0[b][j], a[b], bN[j]);
+              mma0<K16>(t1[b][j], a[b], bD[j]);
+              mma0<K16>(t2[b][j], b2[b], bN[j]);
+            }
+#pragma unroll
+          for (int b = 0; b < BY; ++b) {
+            uint32_t o[4];
+            to_frag(t0[b], o);
+            stsm<NTL>(at(A0, off[b], trash), o);
+            to_frag(t1[b], o);
+            stsm<NTL>(at(A1, off[b], trash), o);
+            to_frag(t2[b], o);
+            stsm<NTL>(at(A2, off[b], trash), o);
+          }
         }
-        to_frag(t0, o);
-        stsm<NTL>(row_addr<N, CPLX, 1>(arr[3], g0, lane, trash), o);
-        to_frag(t1, o);
-        stsm<NTL>(row_addr<N, CPLX, 1>(arr[4], g0, lane, trash), o);
-        to_frag(t2, o);
-        stsm<NTL>(row_addr<N, CPLX, 1>(arr[5], g0, lane, trash), o);
       }
       __syncthreads();
       // (4) z sweep -> Y0, Y1 at the quadrature points (registers), the
       //     quadrature-point step of Algorithm 2, and the transposed z sweep:
       //     N_z^T Z + D_z^T W_z -> 0, N_z^T W_y -> 1, N_z^T W_x -> 2
 #pragma unroll 1
-      for (int mt = warp; mt < Gm::NMT; mt += NW) {
+      for (int mt = warp; mt < NMT; mt += NW) {
         const int g0 = 2 * mt;
+        const int off = row_off<N, CPLX, 2>(g0, lane);
         uint32_t a[4], b[4], c[4];
-        ldsm<K16>(row_addr<N, CPLX, 2>(arr[3], g0, lane, zero_row), a);
-        ldsm<K16>(row_addr<N, CPLX, 2>(arr[4], g0, lane, zero_row), b);
-        ldsm<K16>(row_addr<N, CPLX, 2>(arr[5], g0, lane, zero_row), c);
+        ldsm<K16>(at(A0, off, zero_row), a);
+        ldsm<K16>(at(A1, off, zero_row), b);
+        ldsm<K16>(at(A2, off, zero_row), c);
         float u[NTL][4], gx[NTL][4], gy[NTL][4], gz[NTL][4];
-        zero(u);
-        zero(gx);
-        zero(gy);
-        zero(gz);
 #pragma unroll
         for (int j = 0; j < NTL; ++j) {
-          mma<K16>(u[j], a, bN[j]);
-          mma<K16>(gz[j], a, bD[j]);
-          mma<K16>(gy[j], b, bN[j]);
-          mma<K16>(gx[j], c, bN[j]);
+          mma0<K16>(u[j], a, bN[j]);
+          mma0<K16>(gz[j], a, bD[j]);
+          mma0<K16>(gy[j], b, bN[j]);
+          mma0<K16>(gx[j], c, bN[j]);
         }
         // element (j, r): line g0 + (r >> 1), column v = gq, qz = 8 j + 2 tig + (r & 1)
 #pragma unroll
@@ -393,112 +445,153 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, 2) fe_tc_kernel(const __gri
         to_frag(gx, fx);
         to_frag(gy, fy);
         to_frag(gz, fw);
-        float va[NTL][4], vb[NTL][4], vc[NTL][4];
-        zero(va);
-        zero(vb);
-        zero(vc);
+        float va[NTL][4], va2[NTL][4], vb[NTL][4], vc[NTL][4];
 #pragma unroll
-        for (int j = 0; j < NTL; ++j) {
-          mma<K16>(va[j], fz, bNt[j]);
-          mma<K16>(va[j], fw, bDt[j]);
-          mma<K16>(vb[j], fy, bNt[j]);
-          mma<K16>(vc[j], fx, bNt[j]);
-        }
-        to_frag(va, o);
-        stsm<NTL>(row_addr<N, CPLX, 2>(arr[0], g0, lane, trash), o);
-        to_frag(vb, o);
-        stsm<NTL>(row_addr<N, CPLX, 2>(arr[1], g0, lane, trash), o);
-        to_frag(vc, o);
-        stsm<NTL>(row_addr<N, CPLX, 2>(arr[2], g0, lane, trash), o);
-      }
-      __syncthreads();
-      // (5) transposed y sweep: N_y^T V_a + D_y^T V_b -> 3, N_y^T V_c -> 4
-#pragma unroll 1
-      for (int mt = warp; mt < Gm::NMT; mt += NW) {
-        const int g0 = 2 * mt;
-        uint32_t a[4], b[4], c[4], o[4];
-        ldsm<K16>(row_addr<N, CPLX, 1>(arr[0], g0, lane, zero_row), a);
-        ldsm<K16>(row_addr<N, CPLX, 1>(arr[1], g0, lane, zero_row), b);
-        ldsm<K16>(row_addr<N, CPLX, 1>(arr[2], g0, lane, zero_row), c);
-        float sa[NTL][4], sb[NTL][4];
-        zero(sa);
-        zero(sb);
-#pragma unroll
-        for (int j = 0; j < NTL; ++j) {
-          mma<K16>(sa[j], a, bNt[j]);
-          mma<K16>(sa[j], b, bDt[j]);
-          mma<K16>(sb[j], c, bNt[j]);
-        }
-        to_frag(sa, o);
-        stsm<NTL>(row_addr<N, CPLX, 1>(arr[3], g0, lane, trash), o);
-        to_frag(sb, o);
-        stsm<NTL>(row_addr<N, CPLX, 1>(arr[4], g0, lane, trash), o);
-      }
-      __syncthreads();
-      // (6) transposed x sweep, + F Delta P (nonlocal), assembly Y += alpha Q^T Y^(e)
-      const int pb = p.cell_pair_ptr ? p.cell_pair_ptr[e] : 0;
-      const int pe = p.cell_pair_ptr ? p.cell_pair_ptr[e + 1] : 0;
-      const int col = col0 + gq;
-#pragma unroll 1
-      for (int mt = warp; mt < Gm::NMT; mt += NW) {
-        const int g0 = 2 * mt;
-        uint32_t a[4], b[4];
-        ldsm<K16>(row_addr<N, CPLX, 0>(arr[3], g0, lane, zero_row), a);
-        ldsm<K16>(row_addr<N, CPLX, 0>(arr[4], g0, lane, zero_row), b);
-        float y[NTL][4];
-        zero(y);
-#pragma unroll
-        for (int j = 0; j < NTL; ++j) {
-          mma<K16>(y[j], a, bNt[j]);
-          mma<K16>(y[j], b, bDt[j]);
-        }
-        if (col < p.ncols) {   // no warp-collective instruction inside this branch
-        for (int pi = pb; pi < pe; ++pi) {
-          const int pr = p.cell_pairs[pi];
-          const int at = p.pair_atom[pr];
-          for (int bb = 0; bb < p.n_proj; ++bb) {
-            const float* Qa = p.Q + ((int64_t)at * p.n_proj + bb) * p.ld;
-            const float* Fb = p.F + ((int64_t)pr * p.n_proj + bb) * N3 * (CPLX ? 2 : 1);
-            float qr, qi = 0.f;
-            if constexpr (CPLX) {
-              qr = __ldg(Qa + (col & ~1));
-              qi = __ldg(Qa + (col | 1));
-            } else {
-              qr = __ldg(Qa + col);
-            }
-#pragma unroll
-            for (int j = 0; j < NTL; ++j)
-#pragma unroll
-              for (int r = 0; r < 4; ++r) {
-                const int grp = g0 + (r >> 1);
-                const int i = 8 * j + 2 * tig + (r & 1);
-                if (grp >= Gm::G || i >= N) continue;
-                const int node = i + N * grp;
-                if constexpr (CPLX) {
-                  const float fr = __ldg(Fb + 2 * node), fi = __ldg(Fb + 2 * node + 1);
-                  y[j][r] += (gq & 1) ? fmaf(fr, qi, fi * qr) : fmaf(fr, qr, -fi * qi);
-                } else {
-                  y[j][r] = fmaf(__ldg(Fb + node), qr, y[j][r]);
-                }
-              }
-          }
+        for (int j = 0; j < NTL; ++j) {   // four independent accumulators
+          mma0<K16>(va[j], fz, bNt[j]);
+          mma0<K16>(va2[j], fw, bDt[j]);
+          mma0<K16>(vb[j], fy, bNt[j]);
+          mma0<K16>(vc[j], fx, bNt[j]);
         }
 #pragma unroll
         for (int j = 0; j < NTL; ++j)
 #pragma unroll
-          for (int r = 0; r < 4; ++r) {
-            const int grp = g0 + (r >> 1);
-            const int i = 8 * j + 2 * tig + (r & 1);
-            if (grp >= Gm::G || i >= N) continue;
-            const int d = sd[i + N * grp];
-            float val = y[j][r] * p.alpha;
-            if (p.dscale) val *= __ldg(p.dscale + d);
-            atomicAdd(p.Y + (int64_t)d * p.ld + col, val);   // colour-exclusive: no other cell of the launch touches d
+          for (int r = 0; r < 4; ++r) va[j][r] += va2[j][r];
+        to_frag(va, o);
+        stsm<NTL>(at(A0, off, trash), o);
+        to_frag(vb, o);
+        stsm<NTL>(at(A1, off, trash), o);
+        to_frag(vc, o);
+        stsm<NTL>(at(A2, off, trash), o);
+      }
+      __syncthreads();
+      // (5) transposed y sweep: N_y^T V_a + D_y^T V_b -> 0, N_y^T V_c -> 1
+      //     (BR row tiles per warp at a time, independent accumulators)
+      {
+        constexpr int BR = 2;
+#pragma unroll 1
+        for (int mt0 = warp; mt0 < NMT; mt0 += NW * BR) {
+          int off[BR];
+          uint32_t a[BR][4], b2[BR][4], c2[BR][4];
+          float sa[BR][NTL][4], sa2[BR][NTL][4], sb[BR][NTL][4];
+#pragma unroll
+          for (int b = 0; b < BR; ++b) {
+            const int mt = mt0 + b * NW;
+            off[b] = mt < NMT ? row_off<N, CPLX, 1>(2 * mt, lane) : -1;
+            ldsm<K16>(at(A0, off[b], zero_row), a[b]);
+            ldsm<K16>(at(A1, off[b], zero_row), b2[b]);
+            ldsm<K16>(at(A2, off[b], zero_row), c2[b]);
           }
+#pragma unroll
+          for (int b = 0; b < BR; ++b)
+#pragma unroll
+            for (int j = 0; j < NTL; ++j) {
+              mma0<K16>(sa[b][j], a[b], bNt[j]);
+              mma0<K16>(sa2[b][j], b2[b], bDt[j]);
+              mma0<K16>(sb[b][j], c2[b], bNt[j]);
+            }
+#pragma unroll
+          for (int b = 0; b < BR; ++b) {
+#pragma unroll
+            for (int j = 0; j < NTL; ++j)
+#pragma unroll
+              for (int r = 0; r < 4; ++r) sa[b][j][r] += sa2[b][j][r];
+            uint32_t o[4];
+            to_frag(sa[b], o);
+            stsm<NTL>(at(A0, off[b], trash), o);
+            to_frag(sb[b], o);
+            stsm<NTL>(at(A1, off[b], trash), o);
+          }
+        }
+      }
+      __syncthreads();
+      // (6) transposed x sweep, + F Delta P (nonlocal, as MMAs with the pair's
+      //     pre-packed F fragments), assembly Y += alpha Q^T Y^(e)
+#pragma unroll 1
+      for (int mt = warp; mt < NMT; mt += NW) {
+        const int g0 = 2 * mt;
+        const int off = row_off<N, CPLX, 0>(g0, lane);
+        uint32_t a[4], b[4];
+        ldsm<K16>(at(A0, off, zero_row), a);
+        ldsm<K16>(at(A1, off, zero_row), b);
+        float y[NTL][4], y2[NTL][4], ye[2][NTL][4];
+        zero(ye[0]);
+        zero(ye[1]);
+#pragma unroll
+        for (int j = 0; j < NTL; ++j) {
+          mma0<K16>(y[j], a, bNt[j]);
+          mma0<K16>(y2[j], b, bDt[j]);
+        }
+        // Y^(e)[(line, v)][i] += sum_b Q[a][b][v] F[pair][b][i + N line]: A = Q^T
+        // (rows of one line only, the other half zero), B = the packed F block
+        for (int pi = pb; pi < pe; ++pi) {   // uniform over the block
+          const int pr = p.cell_pairs[pi];
+          const float* Qa = p.Q + (int64_t)p.pair_atom[pr] * p.n_proj * p.ld;
+          const bool act = col < p.ncols;
+          uint32_t aq[S][2];
+#pragma unroll
+          for (int kh = 0; kh < 2; ++kh) {
+            const int b0 = 2 * tig + 8 * kh;
+            float q[2][2];   // [beta offset][re, im]
+#pragma unroll
+            for (int o2 = 0; o2 < 2; ++o2) {
+              const bool okb = act && b0 + o2 < p.n_proj;
+              if constexpr (CPLX) {
+                const float* qr = Qa + (int64_t)(b0 + o2) * p.ld + (col & ~1);
+                q[o2][0] = okb ? __ldg(qr) : 0.f;
+                q[o2][1] = okb ? __ldg(qr + 1) : 0.f;
+              } else {
+                q[o2][0] = okb ? __ldg(Qa + (int64_t)(b0 + o2) * p.ld + col) : 0.f;
+                q[o2][1] = 0.f;
+              }
+            }
+            if constexpr (CPLX) {
+              // real column: Fr Qr - Fi Qi; imaginary column: Fr Qi + Fi Qr
+              const bool im = gq & 1;
+              aq[0][kh] = pack_bf16(im ? q[0][1] : q[0][0], im ? q[1][1] : q[1][0]);
+              aq[S - 1][kh] = pack_bf16(im ? q[0][0] : -q[0][1], im ? q[1][0] : -q[1][1]);
+            } else {
+              aq[0][kh] = pack_bf16(q[0][0], q[1][0]);
+            }
+          }
+          const uint2* fp = p.fpack + ((size_t)pr * NMT + mt) * (2 * NTL * S * 32) + lane;
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int j = 0; j < NTL; ++j)
+#pragma unroll
+              for (int st = 0; st < S; ++st) {
+                const uint2 fb = __ldg(fp + ((h * NTL + j) * S + st) * 32);
+                const uint32_t bb[2] = {fb.x, fb.y};
+                uint32_t af[4];
+                af[0] = h == 0 ? aq[st][0] : 0u;
+                af[1] = h == 1 ? aq[st][0] : 0u;
+                af[2] = h == 0 ? aq[st][1] : 0u;
+                af[3] = h == 1 ? aq[st][1] : 0u;
+                mma<true>(ye[h][j], af, bb);
+              }
+        }
+#pragma unroll
+        for (int j = 0; j < NTL; ++j)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) y[j][r] += y2[j][r] + (ye[0][j][r] + ye[1][j][r]);
+        if (col < p.ncols) {   // no warp-collective instruction inside this branch
+#pragma unroll
+          for (int j = 0; j < NTL; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+              const int grp = g0 + (r >> 1);
+              const int i = 8 * j + 2 * tig + (r & 1);
+              if (grp >= Gm::G || i >= N) continue;
+              const int d = sd[i + N * grp];
+              float val = y[j][r] * p.alpha;
+              if (p.dscale) val *= __ldg(p.dscale + d);
+              atomicAdd(p.Y + (int64_t)d * p.ld + col, val);   // colour-exclusive: no other cell of the launch touches d
+            }
         }
         __syncwarp();   // reconverge before the next row tile's ldmatrix
       }
-      // no barrier here: the next tile's extraction writes array 0 only, which
+      // no barrier here: the next tile's extraction writes array 2 only, which
       // this sweep does not read; the barrier after it orders everything else
     }
   }
@@ -514,6 +607,10 @@ cudaError_t launch_tc_n(const TcParams& p, cudaStream_t s) {
   cudaError_t err =
       cudaFuncSetAttribute(fe_tc_kernel<N, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize, Gm::BYTES);
   if (err != cudaSuccess) return err;
+  // ask for the largest shared-memory carveout so that MINB CTAs fit on an SM with room to spare
+  err = cudaFuncSetAttribute(fe_tc_kernel<N, CPLX>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+  if (err != cudaSuccess) return err;
   const int ntiles = (p.ncols + 7) / 8;
   // about eight resident waves of CTAs: split the column tiles of a cell over
   // gridDim.y CTAs when the colour has few cells
@@ -527,6 +624,27 @@ cudaError_t launch_tc_n(const TcParams& p, cudaStream_t s) {
 }
 
 }  // namespace tc
+
+void build_tc_fpack(int n, bool cplx, int n_proj, int64_t n_pairs, const double* F, std::vector<uint2>& out) {
+  const int G = n * n, NMT = (G + 1) / 2, NTL = n > 8 ? 2 : 1, S = cplx ? 2 : 1, np3 = n * n * n;
+  out.assign((size_t)n_pairs * NMT * 2 * NTL * S * 32, make_uint2(0u, 0u));
+  size_t w = 0;
+  for (int64_t pr = 0; pr < n_pairs; ++pr)
+    for (int mt = 0; mt < NMT; ++mt)
+      for (int h = 0; h < 2; ++h)
+        for (int j = 0; j < NTL; ++j)
+          for (int st = 0; st < S; ++st)
+            for (int lane = 0; lane < 32; ++lane, ++w) {
+              const int g = 2 * mt + h, i = 8 * j + lane / 4, tig = lane % 4;
+              auto B = [&](int k) -> double {   // B[k][i] = F_st[beta = k][node = i + n g]
+                if (k >= n_proj || i >= n || g >= G) return 0.0;
+                const size_t idx = ((size_t)pr * n_proj + k) * np3 + i + (size_t)n * g;
+                return cplx ? F[2 * idx + st] : F[idx];
+              };
+              out[w].x = (uint32_t)bf16_bits(B(2 * tig)) | ((uint32_t)bf16_bits(B(2 * tig + 1)) << 16);
+              out[w].y = (uint32_t)bf16_bits(B(2 * tig + 8)) | ((uint32_t)bf16_bits(B(2 * tig + 9)) << 16);
+            }
+}
 
 // Shared-memory bytes of the BF16 cell kernel for n points per direction
 // (0 when n is unsupported).
@@ -568,6 +686,8 @@ cudaError_t launch_tc(const Ctx& c, const LocalParams<float>& lp, cudaStream_t s
   p.n_proj = lp.n_proj;
   p.alpha = lp.alpha;
   p.frag = c.tc_frag;
+  p.fpack = c.tc_fpack;
+  if (p.cell_pair_ptr && !p.fpack) return cudaErrorInvalidValue;
   switch (c.np) {
 #define FEKS_TC_LAUNCH(NN) \
   case NN: return c.cplx ? tc::launch_tc_n<NN, true>(p, s) : tc::launch_tc_n<NN, false>(p, s);

@@ -130,3 +130,19 @@ def test_invalid_calls_are_rejected(cases):
             fk.fe_ks_apply(ctx, Xd, Yd, 4, 7)
     finally:
         fk.fe_ks_destroy(ctx)
+
+
+@pytest.mark.parametrize("precision", PREC)
+@pytest.mark.parametrize("key", ["C2s", "C3s", "C4s"])
+def test_nonlocal_term_isolated(cases, key, precision):
+    """Y(all terms) - Y(local terms) against the oracle's nonlocal term: the term is
+    1e-5..1e-4 of |H X| for random blocks, so it is checked on its own.  The
+    difference carries the storage rounding of the full result, u |H X| / |NL|
+    relative to the term (<= 1e-16 x 1e5 for FP64, 6e-8 x 1e5 for FP32)."""
+    wl, hp, P, X = cases[key]
+    Xin = round_input(X, precision)
+    Y_all = gpu_apply(hp, Xin, precision)
+    Y_loc = gpu_apply(hp, Xin, precision, terms=fk.TERM_ALL & ~fk.TERM_NL)
+    ref = P.apply(Xin) - Problem(wl, with_atoms=False).apply(Xin)
+    tol = {fk.FE_KS_F64: 1e-9, fk.FE_KS_F64E: 1e-9, fk.FE_KS_F32: 1e-2}[precision]
+    assert rel_err_cols(Y_all - Y_loc, ref) <= tol

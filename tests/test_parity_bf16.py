@@ -102,3 +102,21 @@ def test_bf16_close_to_fp32_kernel(cases):
     Yf = gpu_apply(hp, X, fk.FE_KS_F32)
     assert rel_err_cols(Yb, Yf) <= TOL
     assert rel_err_cols(Yb, Yf) > 1e-6   # really a different (lower-precision) arithmetic
+
+
+@pytest.mark.parametrize("key", ["C2s", "C3s", "C4s"])
+def test_bf16_nonlocal_term_isolated(cases, key):
+    """The nonlocal term alone: for random trial blocks it is 1e-5..1e-4 of |H X|,
+    below the BF16 tolerance of the whole result, so it is checked on its own as
+    Y(all terms) - Y(local terms).  Both runs use the same kernel on the same
+    input, so the local parts agree to FP32 rounding of the accumulators
+    (u_32 |H X| / |NL| <= 6e-8 x 1e5 = 6e-3 relative to the term), and the
+    nonlocal part carries the BF16 rounding of F and Q (2 u)."""
+    wl, hp, P, X = cases[key]
+    X = round_input(X, BF)
+    Y_all = gpu_apply(hp, X, BF)
+    Y_loc = gpu_apply(hp, X, BF, terms=fk.TERM_ALL & ~fk.TERM_NL)
+    ref = P.apply(X) - Problem(wl, with_atoms=False).apply(X)
+    err = rel_err_cols(Y_all - Y_loc, ref)
+    print(f"{key}: BF16 nonlocal term rel err {err:.3e}")
+    assert err <= TOL, err

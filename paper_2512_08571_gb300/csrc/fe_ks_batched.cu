@@ -2,10 +2,13 @@
 //
 // Y_s = H_s X_s for systems s of uneven size, degree, vector count and
 // precision (FP64 / FP32).  The host builds one work queue, phase-major:
-//   phase 0        : zero-fill slices of every Y_s and the per-atom projections
-//                    (eq. AXmatrixfreenonloc, first factor),
-//   phase 1 + c    : the cells of colour c of every system (Algorithm 2 on a
-//                    tile of cells x columns, expansion and scatter-add fused).
+//   phase 0        : zero-fill slices of every Y_s and the per-pair projection
+//                    partials F^(a,e)^H X^(e) (eq. AXmatrixfreenonloc, first factor),
+//   phase 1        : per-atom sums of the partials in pair order, scaled by Delta
+//                    (systems with projectors only),
+//   phase o + c    : the cells of colour c of every system (o = 2 with
+//                    projectors, 1 without; Algorithm 2 on a tile of cells x
+//                    columns, expansion and scatter-add fused).
 // Persistent CTAs claim items in queue order with one atomic counter.  An
 // item of phase k of system s first waits until every item of phase k - 1 of
 // the same system has finished (per-(system, phase) completion counters with
@@ -29,9 +32,7 @@ namespace feks {
 constexpr int kMaxSys = 16;
 constexpr int kMaxPhase = 66;
 constexpr int kBatchNT = 384;
-constexpr int kProjCols = 32;
-
-enum : int { kItemZero = 0, kItemProj = 1, kItemLocal = 2 };
+enum : int { kItemZero = 0, kItemPair = 1, kItemLocal = 2, kItemSum = 3 };
 
 struct BatchSys {
   int prec;        // FE_KS_F64 or FE_KS_F32
@@ -54,6 +55,7 @@ struct BatchSys {
   const void* h;
   const int* atom_pair_ptr;
   const int* pair_cell;
+  void* part;      // projection partials [pair][n_proj][ncols]
   int n_proj;
   int np3;
 };
@@ -122,44 +124,83 @@ __device__ void zero_item(const BatchSys& s, int row0, int rows) {
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) Y[i] = T(0);
 }
 
-// Q[a][b][col] = h[a][b] sum_{(cell,node) of atom a} F X, for 32 columns.
+// Columns per projection item: the smallest of 32, 64, 128 that covers the
+// columns (each divides the block size).
+__host__ __device__ inline int batch_proj_cw(int ncols) { return ncols <= 32 ? 32 : ncols <= 64 ? 64 : 128; }
+
+// Shared memory of a projection item: the pair's F block, the cell's DoF list
+// and the slice reduction buffer.
 template <typename T>
-__device__ void proj_item(const BatchSys& s, int a, int col0, unsigned char* smem) {
-  constexpr int W = kBatchNT / 32;
-  T* red = reinterpret_cast<T*>(smem);   // [W][16][32]
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int col = col0 + lane;
+__host__ __device__ inline size_t batch_proj_bytes(int n_proj, int np3, int cw) {
+  const size_t head = ((size_t)n_proj * np3 * sizeof(T) + (size_t)np3 * sizeof(int) + 15) & ~(size_t)15;
+  return head + (size_t)(kBatchNT / cw) * n_proj * cw * sizeof(T);
+}
+
+// part[pr][b][col] = sum_node F[pr][b][node] x(d(node), col) for columns
+// [col0, col0 + cw): one column per thread, kBatchNT / cw row slices reduced
+// in shared memory in slice order.
+template <typename T>
+__device__ void pair_item(const BatchSys& s, int pr, int col0, int cw, unsigned char* smem) {
+  const int np3 = s.np3, n_proj = s.n_proj;
+  T* Fs = reinterpret_cast<T*>(smem);
+  int* ds = reinterpret_cast<int*>(smem + (size_t)n_proj * np3 * sizeof(T));
+  T* red = reinterpret_cast<T*>(smem + (((size_t)n_proj * np3 * sizeof(T) + (size_t)np3 * sizeof(int) + 15) & ~(size_t)15));
+  const int rs = kBatchNT / cw;
+  const int lc = threadIdx.x % cw, sl = threadIdx.x / cw;
+  const int col = col0 + lc;
   const bool act = col < s.ncols;
   const T* X = static_cast<const T*>(s.X);
-  const T* F = static_cast<const T*>(s.F);
+  const T* Fp = static_cast<const T*>(s.F) + (int64_t)pr * n_proj * np3;
+  for (int i = threadIdx.x; i < n_proj * np3; i += kBatchNT) Fs[i] = Fp[i];
+  const int cell = s.pair_cell[pr];
+  for (int i = threadIdx.x; i < np3; i += kBatchNT) ds[i] = s.cell_dofs[(int64_t)cell * np3 + i];
+  __syncthreads();
   T acc[16];
 #pragma unroll
   for (int b = 0; b < 16; ++b) acc[b] = T(0);
-  const int pb = s.atom_pair_ptr[a], pe = s.atom_pair_ptr[a + 1];
-  const int64_t nrows = (int64_t)(pe - pb) * s.np3;
-  for (int64_t r = warp; r < nrows; r += W) {
-    const int pr = pb + (int)(r / s.np3);
-    const int node = (int)(r % s.np3);
-    const int d = s.cell_dofs[(int64_t)s.pair_cell[pr] * s.np3 + node];
-    const T x = act ? X[(int64_t)d * s.ncols + col] : T(0);
-    const T* Fr = F + (int64_t)pr * s.n_proj * s.np3 + node;
+  constexpr int RU = 4;
+  for (int n0 = sl; n0 < np3; n0 += RU * rs) {
+    T xs[RU];
 #pragma unroll
-    for (int b = 0; b < 16; ++b)
-      if (b < s.n_proj) acc[b] = fma(Fr[(int64_t)b * s.np3], x, acc[b]);
+    for (int u = 0; u < RU; ++u) {
+      const int node = n0 + u * rs;
+      xs[u] = (node < np3 && act) ? X[(int64_t)ds[node] * s.ncols + col] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < RU; ++u) {
+      const int node = n0 + u * rs;
+      if (node >= np3) break;
+#pragma unroll
+      for (int b = 0; b < 16; ++b)
+        if (b < n_proj) acc[b] = fma(Fs[b * np3 + node], xs[u], acc[b]);
+    }
   }
-  __syncthreads();   // smem may still be read by the previous item
 #pragma unroll
   for (int b = 0; b < 16; ++b)
-    if (b < s.n_proj) red[(warp * 16 + b) * 32 + lane] = acc[b];
+    if (b < n_proj) red[((size_t)sl * n_proj + b) * cw + lc] = acc[b];
   __syncthreads();
+  T* part = static_cast<T*>(s.part);
+  for (int idx = threadIdx.x; idx < n_proj * cw; idx += kBatchNT) {
+    const int b = idx / cw, c = idx % cw;
+    T v = red[(size_t)b * cw + c];
+    for (int k = 1; k < rs; ++k) v += red[((size_t)k * n_proj + b) * cw + c];
+    if (col0 + c < s.ncols) part[((int64_t)pr * n_proj + b) * s.ncols + col0 + c] = v;
+  }
+}
+
+// Q[a][b][col] = h[a][b] * sum over the pairs of atom a, in pair order, of part[pr][b][col]
+template <typename T>
+__device__ void sum_item(const BatchSys& s, int a, int col0, int cw) {
+  const T* part = static_cast<const T*>(s.part);
   const T* h = static_cast<const T*>(s.h);
   T* Q = static_cast<T*>(s.Q);
-  for (int idx = threadIdx.x; idx < s.n_proj * 32; idx += blockDim.x) {
-    const int b = idx / 32, l = idx % 32;
-    const int c = col0 + l;
-    T sum = T(0);
-    for (int w = 0; w < W; ++w) sum += red[(w * 16 + b) * 32 + l];
-    if (c < s.ncols) Q[((int64_t)a * s.n_proj + b) * s.ncols + c] = sum * h[a * s.n_proj + b];
+  for (int idx = threadIdx.x; idx < s.n_proj * cw; idx += kBatchNT) {
+    const int b = idx / cw, col = col0 + idx % cw;
+    if (col >= s.ncols) continue;
+    T v = T(0);
+    for (int pr = s.atom_pair_ptr[a]; pr < s.atom_pair_ptr[a + 1]; ++pr)
+      v += part[((int64_t)pr * s.n_proj + b) * s.ncols + col];
+    Q[((int64_t)a * s.n_proj + b) * s.ncols + col] = v * h[a * s.n_proj + b];
   }
 }
 
@@ -236,11 +277,16 @@ __global__ void __launch_bounds__(kBatchNT, MINB) fe_batched_kernel(const __grid
           zero_item<double>(s, w.y, w.w);
         else
           zero_item<float>(s, w.y, w.w);
-      } else if (kind == kItemProj) {
+      } else if (kind == kItemPair) {
         if (s.prec == FE_KS_F64)
-          proj_item<double>(s, w.y, w.z, smem);
+          pair_item<double>(s, w.y, w.z, w.w, smem);
         else
-          proj_item<float>(s, w.y, w.z, smem);
+          pair_item<float>(s, w.y, w.z, w.w, smem);
+      } else if (kind == kItemSum) {
+        if (s.prec == FE_KS_F64)
+          sum_item<double>(s, w.y, w.z, w.w);
+        else
+          sum_item<float>(s, w.y, w.z, w.w);
       } else {
         if (s.prec == FE_KS_F64)
           local_item<double>(bp, s, bp.t64, w.y, w.w, w.z, smem);
@@ -309,9 +355,10 @@ static fe_ks_status batch_build(fe_ks_batch* b) {
   std::vector<int> need(kMaxSys * kMaxPhase, 0);
   const int ns = (int)b->ctxs.size();
   int max_ph = 0;
-  for (int s = 0; s < ns; ++s) max_ph = std::max<int>(max_ph, (int)b->ctxs[s]->c.colour_ptr.size() - 1);
+  for (int s = 0; s < ns; ++s) max_ph = std::max<int>(max_ph, (int)b->ctxs[s]->c.colour_ptr.size() - 1 + 2);
+  if (max_ph >= kMaxPhase) return fail(FE_KS_ERR_UNSUPPORTED, "too many colours for the batched launch");
   std::vector<std::vector<int4>> per_phase(max_ph + 1);
-  size_t smem = (size_t)(kBatchNT / 32) * 16 * 32 * 8;   // projection reduction
+  size_t smem = 0;
   for (int s = 0; s < ns; ++s) {
     const Ctx& c = b->ctxs[s]->c;
     const int ncols = (int)b->n_v[s];
@@ -325,15 +372,25 @@ static fe_ks_status batch_build(fe_ks_batch* b) {
       per_phase[0].push_back(make_int4(s | (kItemZero << 8), (int)r, 0, (int)std::min<int64_t>(rows, c.m - r)));
       need[s * kMaxPhase + 0]++;
     }
-    if ((c.terms & FE_KS_TERM_NL) && c.n_pairs > 0) {
-      for (int a = 0; a < c.n_atoms; ++a)
-        for (int col = 0; col < ncols; col += kProjCols) {
-          per_phase[0].push_back(make_int4(s | (kItemProj << 8), a, col, 0));
+    const bool nl = (c.terms & FE_KS_TERM_NL) && c.n_pairs > 0;
+    if (nl) {
+      const int cw = batch_proj_cw(ncols);
+      smem = std::max(smem, b->prec[s] == FE_KS_F64 ? batch_proj_bytes<double>(c.n_proj, c.np3, cw)
+                                                    : batch_proj_bytes<float>(c.n_proj, c.np3, cw));
+      for (int64_t pr = 0; pr < c.n_pairs; ++pr)
+        for (int col = 0; col < ncols; col += cw) {
+          per_phase[0].push_back(make_int4(s | (kItemPair << 8), (int)pr, col, cw));
           need[s * kMaxPhase + 0]++;
         }
+      for (int a = 0; a < c.n_atoms; ++a)
+        for (int col = 0; col < ncols; col += cw) {
+          per_phase[1].push_back(make_int4(s | (kItemSum << 8) | (1 << 16), a, col, cw));
+          need[s * kMaxPhase + 1]++;
+        }
     }
+    const int ph0 = nl ? 2 : 1;   // no empty phase: a colour waits on the phase just before it
     for (int col = 0; col + 1 < (int)c.colour_ptr.size(); ++col) {
-      const int ph = col + 1;
+      const int ph = col + ph0;
       for (int c0 = c.colour_ptr[col]; c0 < c.colour_ptr[col + 1]; c0 += b->cells_per_item) {
         const int nc = std::min(b->cells_per_item, c.colour_ptr[col + 1] - c0);
         for (int t = 0; t < ncols; t += vt) {
@@ -388,6 +445,7 @@ static fe_ks_status batch_build(fe_ks_batch* b) {
     d.h = f64 ? (const void*)c.h64 : (const void*)c.h32;
     d.atom_pair_ptr = c.atom_pair_ptr;
     d.pair_cell = c.pair_cell;
+    d.part = f64 ? (void*)c.f64.part : (void*)c.f32.part;
     d.n_proj = c.n_proj;
     d.np3 = c.np3;
     build_eo_tables<double>(c.p, c.nq, &P.t64[c.p]);

@@ -5,7 +5,7 @@
 //  - pair form (the operator's path): one CTA per (atom, cell) pair and column
 //    chunk stages the pair's F block and the cell's DoF list in shared memory
 //    and forms P_pair = F^(a,e)^H X^(e) with one column per thread (rows of X
-//    read coalesced, four rows in flight); a second kernel sums the pairs of
+//    read coalesced, four to eight rows in flight); a second kernel sums the pairs of
 //    each atom in pair order and scales by Delta.  Needs a partial buffer
 //    [pair][n_proj][columns].
 //  - atom form (the allocation-free entry point): one CTA per (atom, 32-column
@@ -134,14 +134,17 @@ cudaError_t launch_proj_emu(const Ctx& c, const ProjParams<double>& prm, const f
 constexpr int kPairThreads = 256;
 
 // P[pr][b][col] = sum_node conj(F[pr][b][node]) x(d(node), col), x scaled by
-// D^{-1/2} when dscale is given.  cw (32, 64, 128 or 256) columns per CTA, the
-// 256 / cw row slices of a CTA reduced in shared memory in slice order.
-template <typename T, typename TS, typename TF, bool CPLX>
+// D^{-1/2} when dscale is given.  Each thread owns V = 16 / sizeof(TS)
+// adjacent columns (one 16-byte load per row; for complex data the re/im
+// partner is in the same thread); cg column groups per CTA, the 256 / cg row
+// slices of a CTA reduced in shared memory in slice order.  MAXP >= n_proj.
+template <typename T, typename TS, typename TF, bool CPLX, int MAXP>
 __global__ void __launch_bounds__(kPairThreads)
 fe_proj_pair_kernel(const TS* __restrict__ Xg, int64_t ld, int ncols, const int* __restrict__ cell_dofs,
                     const int* __restrict__ pair_cell, const TF* __restrict__ Fg, const TS* __restrict__ dscale,
-                    TS* __restrict__ part, int n_proj, int np3, int cw) {
+                    TS* __restrict__ part, int n_proj, int np3, int cg) {
   using N = ProjNum<T>;
+  constexpr int V = 16 / (int)sizeof(TS);
   constexpr int CW = CPLX ? 2 : 1;
   extern __shared__ __align__(16) unsigned char smp[];
   TF* Fs = reinterpret_cast<TF*>(smp);
@@ -149,69 +152,96 @@ fe_proj_pair_kernel(const TS* __restrict__ Xg, int64_t ld, int ncols, const int*
   int* ds = reinterpret_cast<int*>(smp + (size_t)nf * sizeof(TF));
   T* red = reinterpret_cast<T*>(smp + (((size_t)nf * sizeof(TF) + (size_t)np3 * sizeof(int) + 15) & ~(size_t)15));
   const int pr = blockIdx.x;
-  const int rs = kPairThreads / cw;
-  const int lc = threadIdx.x % cw, sl = threadIdx.x / cw;
-  const int col = blockIdx.y * cw + lc;
-  const bool act = col < ncols;
+  const int rs = kPairThreads / cg;
+  const int lc = threadIdx.x % cg, sl = threadIdx.x / cg;
+  const int c0 = (blockIdx.y * cg + lc) * V;
+  const bool vec = (ld % V == 0) && (((uintptr_t)Xg & 15) == 0) && c0 + V <= ncols;
   const TF* Fp = Fg + (int64_t)pr * nf;
   for (int i = threadIdx.x; i < nf; i += kPairThreads) Fs[i] = Fp[i];
   const int cell = pair_cell[pr];
   for (int i = threadIdx.x; i < np3; i += kPairThreads) ds[i] = cell_dofs[(int64_t)cell * np3 + i];
   __syncthreads();
-  T acc[kMaxProj];
+  T acc[MAXP][V];
 #pragma unroll
-  for (int b = 0; b < kMaxProj; ++b) acc[b] = N::zero();
-  // rows sl, sl + rs, ... in groups of four (warp-uniform: cw is a multiple of 32)
-  for (int n0 = sl; n0 < np3; n0 += 4 * rs) {
-    TS xs[4];
+  for (int b = 0; b < MAXP; ++b)
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int v = 0; v < V; ++v) acc[b][v] = N::zero();
+  constexpr int RU = 4;   // rows in flight per thread
+  for (int n0 = sl; n0 < np3; n0 += RU * rs) {
+    TS xs[RU][V];
+#pragma unroll
+    for (int u = 0; u < RU; ++u) {
       const int node = n0 + u * rs;
-      xs[u] = TS(0);
+#pragma unroll
+      for (int v = 0; v < V; ++v) xs[u][v] = TS(0);
       if (node < np3) {
         const int d = ds[node];
-        if (act) xs[u] = Xg[(int64_t)d * ld + col];
-        if (dscale) xs[u] *= dscale[d];
+        const TS* xr = Xg + (int64_t)d * ld + c0;
+        if (vec) {
+          const uint4 w = *reinterpret_cast<const uint4*>(xr);
+          const TS* wv = reinterpret_cast<const TS*>(&w);
+#pragma unroll
+          for (int v = 0; v < V; ++v) xs[u][v] = wv[v];
+        } else {
+#pragma unroll
+          for (int v = 0; v < V; ++v)
+            if (c0 + v < ncols) xs[u][v] = xr[v];
+        }
+        if (dscale) {
+          const TS sc = dscale[d];
+#pragma unroll
+          for (int v = 0; v < V; ++v) xs[u][v] *= sc;
+        }
       }
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < RU; ++u) {
       const int node = n0 + u * rs;
       if (node >= np3) break;
-      const T x = N::in(xs[u]);
-      if constexpr (!CPLX) {
+      T x[V];
 #pragma unroll
-        for (int b = 0; b < kMaxProj; ++b)
-          if (b < n_proj) acc[b] = fma(N::in(Fs[b * np3 + node]), x, acc[b]);
-      } else {
-        const T xp = N::shfl1(x);
+      for (int v = 0; v < V; ++v) x[v] = N::in(xs[u][v]);
 #pragma unroll
-        for (int b = 0; b < kMaxProj; ++b) {
-          if (b < n_proj) {
+      for (int b = 0; b < MAXP; ++b) {
+        if (b < n_proj) {
+          if constexpr (!CPLX) {
+            const T f = N::in(Fs[b * np3 + node]);
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[b][v] = fma(f, x[v], acc[b][v]);
+          } else {
+            // conj(F) x : re = fr xr + fi xi ; im = fr xi - fi xr  (re, im adjacent in the thread)
             const T fr = N::in(Fs[2 * (b * np3 + node)]), fi = N::in(Fs[2 * (b * np3 + node) + 1]);
-            // conj(F) x : re = fr xr + fi xi ; im = fr xi - fi xr
-            acc[b] = (lc & 1) ? fma(fr, x, fma(-fi, xp, acc[b])) : fma(fr, x, fma(fi, xp, acc[b]));
+#pragma unroll
+            for (int v = 0; v < V; v += 2) {
+              acc[b][v] = fma(fr, x[v], fma(fi, x[v + 1], acc[b][v]));
+              acc[b][v + 1] = fma(fr, x[v + 1], fma(-fi, x[v], acc[b][v + 1]));
+            }
           }
         }
       }
     }
   }
   if (rs == 1) {
-    if (act)
 #pragma unroll
-      for (int b = 0; b < kMaxProj; ++b)
-        if (b < n_proj) part[((int64_t)pr * n_proj + b) * ld + col] = N::template out<TS>(acc[b]);
+    for (int b = 0; b < MAXP; ++b)
+      if (b < n_proj)
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+          if (c0 + v < ncols) part[((int64_t)pr * n_proj + b) * ld + c0 + v] = N::template out<TS>(acc[b][v]);
     return;
   }
+  const int cols = cg * V;   // columns of this CTA
 #pragma unroll
-  for (int b = 0; b < kMaxProj; ++b)
-    if (b < n_proj) red[((size_t)sl * n_proj + b) * cw + lc] = acc[b];
+  for (int b = 0; b < MAXP; ++b)
+    if (b < n_proj)
+#pragma unroll
+      for (int v = 0; v < V; ++v) red[((size_t)sl * n_proj + b) * cols + lc * V + v] = acc[b][v];
   __syncthreads();
-  for (int idx = threadIdx.x; idx < n_proj * cw; idx += kPairThreads) {
-    const int b = idx / cw, c = idx % cw;
-    T v = red[(size_t)b * cw + c];
-    for (int k = 1; k < rs; ++k) v = v + red[((size_t)k * n_proj + b) * cw + c];
-    const int cc = blockIdx.y * cw + c;
+  for (int idx = threadIdx.x; idx < n_proj * cols; idx += kPairThreads) {
+    const int b = idx / cols, c = idx % cols;
+    T v = red[(size_t)b * cols + c];
+    for (int k = 1; k < rs; ++k) v = v + red[((size_t)k * n_proj + b) * cols + c];
+    const int cc = blockIdx.y * cols + c;
     if (cc < ncols) part[((int64_t)pr * n_proj + b) * ld + cc] = N::template out<TS>(v);
   }
 }
@@ -233,28 +263,31 @@ __global__ void fe_proj_sum_kernel(const TS* __restrict__ part, const TS* __rest
   }
 }
 
-// Column chunk of the pair kernel: the smallest multiple of 32 covering the
-// columns, at most 256.
-static int pair_chunk(int ncols) {
-  int cw = 32;
-  while (cw < 256 && cw < ncols) cw *= 2;
-  return cw;
+// Column groups (of 16 / sizeof(TS) columns) per CTA of the pair kernel: the
+// smallest multiple of 32 covering the columns, at most 256.
+template <typename TS>
+static int pair_groups(int ncols) {
+  const int groups = (ncols + (16 / (int)sizeof(TS)) - 1) / (16 / (int)sizeof(TS));
+  int cg = 32;
+  while (cg < 256 && cg < groups) cg *= 2;
+  return cg;
 }
 
-template <typename T, typename TS, typename TF, bool CPLX>
-static cudaError_t launch_pair(const ProjParams<TS>& prm, const TF* F, int n_atoms, cudaStream_t s) {
-  const int cw = pair_chunk(prm.ncols);
-  const int rs = kPairThreads / cw;
+template <typename T, typename TS, typename TF, bool CPLX, int MAXP>
+static cudaError_t launch_pair_p(const ProjParams<TS>& prm, const TF* F, int n_atoms, cudaStream_t s) {
+  constexpr int V = 16 / (int)sizeof(TS);
+  const int cg = pair_groups<TS>(prm.ncols);
+  const int rs = kPairThreads / cg;
   const size_t nf = (size_t)prm.n_proj * prm.np3 * (CPLX ? 2 : 1);
   const size_t head = (nf * sizeof(TF) + (size_t)prm.np3 * sizeof(int) + 15) & ~(size_t)15;
-  const size_t smem = head + (rs > 1 ? (size_t)rs * prm.n_proj * cw * sizeof(T) : 0);
+  const size_t smem = head + (rs > 1 ? (size_t)rs * prm.n_proj * cg * V * sizeof(T) : 0);
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-  cudaError_t err = cudaFuncSetAttribute(fe_proj_pair_kernel<T, TS, TF, CPLX>,
+  cudaError_t err = cudaFuncSetAttribute(fe_proj_pair_kernel<T, TS, TF, CPLX, MAXP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  dim3 grid((unsigned)prm.n_pairs, (unsigned)((prm.ncols + cw - 1) / cw));
-  fe_proj_pair_kernel<T, TS, TF, CPLX><<<grid, kPairThreads, smem, s>>>(
-      prm.X, prm.ld, prm.ncols, prm.cell_dofs, prm.pair_cell, F, prm.dscale, prm.part, prm.n_proj, prm.np3, cw);
+  dim3 grid((unsigned)prm.n_pairs, (unsigned)((prm.ncols + cg * V - 1) / (cg * V)));
+  fe_proj_pair_kernel<T, TS, TF, CPLX, MAXP><<<grid, kPairThreads, smem, s>>>(
+      prm.X, prm.ld, prm.ncols, prm.cell_dofs, prm.pair_cell, F, prm.dscale, prm.part, prm.n_proj, prm.np3, cg);
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   const int64_t total = (int64_t)n_atoms * prm.n_proj * prm.ncols;
@@ -262,6 +295,12 @@ static cudaError_t launch_pair(const ProjParams<TS>& prm, const TF* F, int n_ato
   fe_proj_sum_kernel<TS><<<blocks, 256, 0, s>>>(prm.part, prm.h, prm.atom_pair_ptr, prm.Q, n_atoms, prm.n_proj,
                                                 prm.ld, prm.ncols);
   return cudaGetLastError();
+}
+
+template <typename T, typename TS, typename TF, bool CPLX>
+static cudaError_t launch_pair(const ProjParams<TS>& prm, const TF* F, int n_atoms, cudaStream_t s) {
+  if (prm.n_proj <= 9) return launch_pair_p<T, TS, TF, CPLX, 9>(prm, F, n_atoms, s);
+  return launch_pair_p<T, TS, TF, CPLX, kMaxProj>(prm, F, n_atoms, s);
 }
 
 template <typename T>

@@ -79,12 +79,17 @@ struct Geom {
   static constexpr int OFF_TRASH = OFF_ZERO + 16;
   static constexpr int OFF_COEF = OFF_TRASH + 32 * 16;
   static constexpr int OFF_DOFS = OFF_COEF + NPTS * NC * 4;
-  static constexpr int BYTES = OFF_DOFS + N3 * 4;
+  // FP32 cell result [node][SST] (8 columns, padded to 12 floats so the
+  // fragment-order writes and the row reads are both conflict-free)
+  static constexpr int SST = 12;
+  static constexpr int OFF_STAGE = (OFF_DOFS + N3 * 4 + 15) / 16 * 16;
+  static constexpr int BYTES = OFF_STAGE + N3 * SST * 4;
   // Two resident CTAs per SM.  (Three fit the shared memory at n = 9, but the
   // register cap that lets 21 warps share the SM's four 16K-register files
   // (80 per thread) made the kernel spill and measured no faster.)
   static constexpr int MINB = 2;
-  static_assert(ARR % 16 == 0 && OFF_COEF % 16 == 0 && OFF_DOFS % 4 == 0, "alignment");
+  static_assert(ARR % 16 == 0 && OFF_COEF % 16 == 0 && OFF_DOFS % 4 == 0 && OFF_STAGE % 16 == 0, "alignment");
+  static_assert(2 * (BYTES + 1024) <= 233472, "two CTAs per SM must fit");
   static_assert((NC * 4) % 16 == 0 || (NC * 4) % 8 == 0, "coefficient loads need 8-byte point stride");
 
   // point index of line `grp` (the two untouched coordinates) at position k
@@ -195,6 +200,35 @@ __device__ __forceinline__ uint32_t at(uint32_t arr, int off, uint32_t spare) {
   return off >= 0 ? arr + (uint32_t)off : spare;
 }
 
+// Assembly Y += alpha D^{-1/2} Q^T Y^(e) of the staged FP32 cell result for
+// columns [c0, c0 + 8): one node per thread, two 16-byte reductions per node
+// when the rows are 16-byte aligned.  Colour-exclusive launches: no other
+// cell of the launch touches the same DoF rows.
+template <int N, bool CPLX>
+__device__ __forceinline__ void scatter_stage(const TcParams& p, const float* stage, const int* sd, int c0, bool vecy) {
+  using Gm = Geom<N, CPLX>;
+  const bool fullv = vecy && c0 + 8 <= p.ncols;
+  for (int node = threadIdx.x; node < Gm::N3; node += Gm::NT) {
+    const float* sp = stage + node * Gm::SST;
+    float4 a = *reinterpret_cast<const float4*>(sp);
+    float4 b = *reinterpret_cast<const float4*>(sp + 4);
+    const int d = sd[node];
+    const float sc = p.dscale ? p.alpha * __ldg(p.dscale + d) : p.alpha;
+    a.x *= sc, a.y *= sc, a.z *= sc, a.w *= sc;
+    b.x *= sc, b.y *= sc, b.z *= sc, b.w *= sc;
+    float* yp = p.Y + (int64_t)d * p.ld + c0;
+    if (fullv) {
+      atomicAdd(reinterpret_cast<float4*>(yp), a);
+      atomicAdd(reinterpret_cast<float4*>(yp) + 1, b);
+    } else {
+      const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+        if (c0 + c < p.ncols) atomicAdd(yp + c, v[c]);
+    }
+  }
+}
+
 template <int N, bool CPLX>
 __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_kernel(const __grid_constant__ TcParams p) {
   using Gm = Geom<N, CPLX>;
@@ -205,6 +239,7 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_
   extern __shared__ __align__(16) unsigned char smem[];
   float* cf = reinterpret_cast<float*>(smem + Gm::OFF_COEF);
   int* sd = reinterpret_cast<int*>(smem + Gm::OFF_DOFS);
+  float* stage = reinterpret_cast<float*>(smem + Gm::OFF_STAGE);
   const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(smem);
   const uint32_t A0 = s0, A1 = s0 + Gm::ARR, A2 = s0 + 2 * Gm::ARR;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -226,6 +261,7 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_
     }
   const int ntiles = (p.ncols + 7) / 8;
   const bool vec = (p.ld % 4 == 0) && (((uintptr_t)p.X & 15) == 0);
+  const bool vecy = (p.ld % 4 == 0) && (((uintptr_t)p.Y & 15) == 0);
 
   for (int ci = blockIdx.x; ci < p.n_cells; ci += gridDim.x) {
     const int e = p.cells[ci];
@@ -245,12 +281,14 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_
     const int pb = p.cell_pair_ptr ? p.cell_pair_ptr[e] : 0;
     const int pe = p.cell_pair_ptr ? p.cell_pair_ptr[e + 1] : 0;
     __syncthreads();
+    int prev0 = -1;   // columns of the staged result still to be assembled
     for (int t = blockIdx.y; t < ntiles; t += gridDim.y) {
       const int col0 = 8 * t;
       const int col = col0 + gq;
       const bool full = vec && col0 + 8 <= p.ncols;
       // (1) extraction Q C P X (Algorithm 1): rows of X -> BF16 array 2 [node][8]
-      //     (array 2 is not read by the previous tile's last sweep)
+      //     (array 2 is not read by the previous tile's last sweep); the loads
+      //     are in flight while the previous tile's staged result is assembled
       {
         constexpr int GPT = (N3 + NT - 1) / NT;
         float4 xa[GPT], xb[GPT];
@@ -276,6 +314,7 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_
             if (p.dscale) sc[r] = __ldg(p.dscale + d);
           }
         }
+        if (prev0 >= 0) scatter_stage<N, CPLX>(p, stage, sd, prev0, vecy);
 #pragma unroll
         for (int r = 0; r < GPT; ++r) {
           const int node = tid + r * NT;
@@ -384,20 +423,29 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_
           mma0<K16>(gy[j], b, bN[j]);
           mma0<K16>(gx[j], c, bN[j]);
         }
-        // element (j, r): line g0 + (r >> 1), column v = gq, qz = 8 j + 2 tig + (r & 1)
+        // element (j, r): line g0 + (r >> 1), column v = gq, qz = 8 j + 2 tig + (r & 1);
+        // the coefficients of a line start at cbase[r >> 1], qz adds SZ NC per step
+        const float* cbase[2];
+        bool lok[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int grp = g0 + h;
+          lok[h] = grp < Gm::G;
+          const int gc = lok[h] ? grp : 0;
+          cbase[h] = cf + ((gc % N) + SY * (gc / N) + SZ * 2 * tig) * NC;
+        }
 #pragma unroll
         for (int j = 0; j < NTL; ++j)
 #pragma unroll
           for (int r = 0; r < 4; ++r) {
-            const int grp = g0 + (r >> 1);
             const int qz = 8 * j + 2 * tig + (r & 1);
-            const bool ok = grp < Gm::G && qz < N;
+            const bool ok = lok[r >> 1] && qz < N;
             float z = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f, kk = 0.f;
             const float uu = u[j][r], x = gx[j][r], y = gy[j][r], zz = gz[j][r];
             if (ok) {
               // slots: G00 G01 G02 G11 G12 G22 VL V0 V1 V2 (K0 K1 K2); the point
               // stride is 48 B (real, 16-byte loads) or 56 B (complex, 8-byte loads)
-              const float* c0 = cf + ((grp % N) + SY * (grp / N) + SZ * qz) * NC;
+              const float* c0 = cbase[r >> 1] + (8 * j + (r & 1)) * SZ * NC;
               float G00, G01, G02, G11, G12, G22, VL, V0, V1, V2;
               if constexpr (NC % 4 == 0) {
                 const float4 ga = *reinterpret_cast<const float4*>(c0);
@@ -575,25 +623,21 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_
         for (int j = 0; j < NTL; ++j)
 #pragma unroll
           for (int r = 0; r < 4; ++r) y[j][r] += y2[j][r] + (ye[0][j][r] + ye[1][j][r]);
-        if (col < p.ncols) {   // no warp-collective instruction inside this branch
+        // the cell result, FP32, to the stage [node][column]
 #pragma unroll
-          for (int j = 0; j < NTL; ++j)
+        for (int j = 0; j < NTL; ++j)
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-              const int grp = g0 + (r >> 1);
-              const int i = 8 * j + 2 * tig + (r & 1);
-              if (grp >= Gm::G || i >= N) continue;
-              const int d = sd[i + N * grp];
-              float val = y[j][r] * p.alpha;
-              if (p.dscale) val *= __ldg(p.dscale + d);
-              atomicAdd(p.Y + (int64_t)d * p.ld + col, val);   // colour-exclusive: no other cell of the launch touches d
-            }
-        }
+          for (int r = 0; r < 4; ++r) {
+            const int grp = g0 + (r >> 1);
+            const int i = 8 * j + 2 * tig + (r & 1);
+            if (grp < Gm::G && i < N) stage[(i + N * grp) * Gm::SST + gq] = y[j][r];
+          }
         __syncwarp();   // reconverge before the next row tile's ldmatrix
       }
-      // no barrier here: the next tile's extraction writes array 2 only, which
-      // this sweep does not read; the barrier after it orders everything else
+      __syncthreads();   // the stage is complete; array 2 is free for the next extraction
+      prev0 = col0;
     }
+    if (prev0 >= 0) scatter_stage<N, CPLX>(p, stage, sd, prev0, vecy);
   }
 }
 

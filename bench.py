@@ -62,8 +62,8 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the six-system batched launch")
     ap.add_argument("--no-filter", action="store_true", help="skip the R-ChFSI filter timing")
-    ap.add_argument("--precision", choices=["both", "f64", "f32", "f64e", "bf16"], default="both",
-                    help="f32 / f64e / bf16 alone time only that application (for profiling)")
+    ap.add_argument("--precision", choices=["both", "f64", "f32", "f64e", "bf16", "f16"], default="both",
+                    help="f32 / f64e / bf16 / f16 alone time only that application (for profiling)")
     ap.add_argument("--config", type=int, default=None,
                     help="force this tile configuration instead of tuning (for profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle sample")
@@ -206,7 +206,8 @@ def run_native(args, wl, rank, world):
         dt = {fk.FE_KS_F64: torch.complex128 if cplx else torch.float64,
               fk.FE_KS_F64E: torch.complex128 if cplx else torch.float64,
               fk.FE_KS_F32: torch.complex64 if cplx else torch.float32,
-              fk.FE_KS_BF16: torch.complex64 if cplx else torch.float32}[precision]
+              fk.FE_KS_BF16: torch.complex64 if cplx else torch.float32,
+              fk.FE_KS_F16: torch.complex64 if cplx else torch.float32}[precision]
         X = X64 if dt == X64.dtype else X64.to(dt)
         Y = torch.empty_like(X)
         if args.config is None:
@@ -253,12 +254,15 @@ def run_native(args, wl, rank, world):
         mixed = measure(fk.FE_KS_F32, args.steps, args.warmup)
     elif not args.no_mixed and args.precision == "both":
         mixed = measure(fk.FE_KS_F32, max(args.steps, 20), max(args.warmup, 3))
-    bf16 = None
+    bf16 = f16 = None
     if args.precision == "bf16":
         bf16 = measure(fk.FE_KS_BF16, args.steps, args.warmup)
+    elif args.precision == "f16":
+        f16 = measure(fk.FE_KS_F16, args.steps, args.warmup)
     elif not args.no_mixed and args.precision == "both":
         bf16 = measure(fk.FE_KS_BF16, max(args.steps, 20), max(args.warmup, 3))
-    peak_mma_live = fk.fe_ks_measure_fma_peak(fk.FE_KS_BF16) * 1e12 if bf16 else None
+        f16 = measure(fk.FE_KS_F16, max(args.steps, 20), max(args.warmup, 3))
+    peak_mma_live = fk.fe_ks_measure_fma_peak(fk.FE_KS_BF16) * 1e12 if (bf16 or f16) else None
 
     peak64_live = fk.fe_ks_measure_fma_peak(fk.FE_KS_F64) * 1e12
     peak32_live = fk.fe_ks_measure_fma_peak(fk.FE_KS_F32) * 1e12
@@ -303,7 +307,7 @@ def run_native(args, wl, rank, world):
     del X64
     torch.cuda.empty_cache()
     fk.fe_ks_destroy(ctx)
-    return dict(filter=filt, f64e=f64e, f64=f64, mixed=mixed, bf16=bf16, peak_mma_live=peak_mma_live,
+    return dict(filter=filt, f64e=f64e, f64=f64, mixed=mixed, bf16=bf16, f16=f16, peak_mma_live=peak_mma_live,
                 mma_flops_per_apply=mma_flops, bytes32=bytes32, e2e=e2e, setup_s=setup_s, info=info, local_flops=local_flops,
                 peak64_live=peak64_live, peak32_live=peak32_live)
 
@@ -351,7 +355,8 @@ def run_filter(args, wl, ctx, hp, X64):
     plans = {"f64": (fk.FE_KS_F64, fk.FE_KS_F64, False),
              "f64_pairs": (fk.FE_KS_F64E, fk.FE_KS_F64E, True),
              "mixed": (fk.FE_KS_F32, fk.FE_KS_F64E, True),
-             "mixed_bf16": (fk.FE_KS_BF16, fk.FE_KS_F64E, True)}
+             "mixed_bf16": (fk.FE_KS_BF16, fk.FE_KS_F64E, True),
+             "mixed_f16": (fk.FE_KS_F16, fk.FE_KS_F64E, True)}
     lam = X = lmax = None
     for name, (prec, exact, pair_gemm) in plans.items():
         sol = RChFSI(ctx, m, n_v, False, degree=20, precision=prec, exact=exact, gemm_pairs=pair_gemm)
@@ -376,6 +381,8 @@ def run_filter(args, wl, ctx, hp, X64):
     out["speedup_pass_mixed_vs_f64"] = out["f64"]["pass_ms"] / out["mixed"]["pass_ms"]
     out["speedup_filter_bf16_vs_f64"] = out["f64"]["filter_ms"] / out["mixed_bf16"]["filter_ms"]
     out["speedup_pass_bf16_vs_f64"] = out["f64"]["pass_ms"] / out["mixed_bf16"]["pass_ms"]
+    out["speedup_filter_f16_vs_f64"] = out["f64"]["filter_ms"] / out["mixed_f16"]["filter_ms"]
+    out["speedup_pass_f16_vs_f64"] = out["f64"]["pass_ms"] / out["mixed_f16"]["pass_ms"]
     del X
     # convergence at 6^3 cells
     wls = wl.scaled(n=6, n_v=32, n_atoms=max(1, wl.n_atoms * 6 ** 3 // wl.n ** 3 + 1))
@@ -389,7 +396,8 @@ def run_filter(args, wl, ctx, hp, X64):
     lams = {}
     for name, prec, exact, pg in (("f64", fk.FE_KS_F64, fk.FE_KS_F64, False),
                                   ("mixed", fk.FE_KS_F32, fk.FE_KS_F64E, True),
-                                  ("mixed_bf16", fk.FE_KS_BF16, fk.FE_KS_F64E, True)):
+                                  ("mixed_bf16", fk.FE_KS_BF16, fk.FE_KS_F64E, True),
+                                  ("mixed_f16", fk.FE_KS_F16, fk.FE_KS_F64E, True)):
         sol = RChFSI(cs, hps.m, wls.n_v, False, degree=20, precision=prec, exact=exact, gemm_pairs=pg)
         t, (lam_c, _, res, its) = ev_ms(lambda: sol.run(Xs0.clone(), n_iter=120, tol=1e-9, n_check=n_chk))
         lams[name] = lam_c.cpu().numpy()
@@ -397,8 +405,10 @@ def run_filter(args, wl, ctx, hp, X64):
         del sol
     conv["max_eig_diff_mixed_vs_f64_Ha"] = float(np.max(np.abs(lams["mixed"][:n_chk] - lams["f64"][:n_chk])))
     conv["max_eig_diff_bf16_vs_f64_Ha"] = float(np.max(np.abs(lams["mixed_bf16"][:n_chk] - lams["f64"][:n_chk])))
+    conv["max_eig_diff_f16_vs_f64_Ha"] = float(np.max(np.abs(lams["mixed_f16"][:n_chk] - lams["f64"][:n_chk])))
     conv["speedup"] = conv["f64"]["ms"] / conv["mixed"]["ms"]
     conv["speedup_bf16"] = conv["f64"]["ms"] / conv["mixed_bf16"]["ms"]
+    conv["speedup_f16"] = conv["f64"]["ms"] / conv["mixed_f16"]["ms"]
     out["converged_6cubed"] = conv
     fk.fe_ks_destroy(cs)
     return out
@@ -594,7 +604,7 @@ def main():
         return
     f64 = res["f64"]
     if f64 is None:
-        pr = res["mixed"] or res["f64e"] or res["bf16"]
+        pr = res["mixed"] or res["f64e"] or res["bf16"] or res["f16"]
         print(json.dumps({"metric": METRIC, "profiling_only": True, "precision": args.precision, "ms": pr["ms"],
                           "value": pr["value"], "local_launch_ms": pr["local_launch_ms"],
                           "profile_ms_per_step": {k: v[0] / max(1, args.steps) for k, v in pr["prof"].items()}}))
@@ -639,14 +649,17 @@ def main():
                                       "traffic": load_traffic(f"fe_local_kernel f32 {wl.name} cfg{mixed['tile_config']}"),
                                       "tune_ms_per_config": mixed["tune_ms"]},
                          "clocks": mixed["clocks"], "gpu_launches": mixed["launches"]}
-    bf = res["bf16"]
-    if bf:
+    for key, name, dts in (("bf16", "bf16_tensor_core", "bf16 x bf16 -> f32 (FP32 storage)"),
+                           ("f16", "f16_tensor_core", "f16 x f16 -> f32 (FP32 storage, power-of-two tile scaling)")):
+        bf = res[key]
+        if not bf:
+            continue
         # HBM roofline (FP32 storage): X read once + Y written once per application, plus
         # the coefficients; the executed MMA rate is reported against the live mma.sync probe
         alg_bytes = 2 * res["bytes32"]["xy"] + res["bytes32"]["coef"]
         t_roof = alg_bytes / (PEAK_HBM_GBS * 1e9)
-        line["bf16_tensor_core"] = {
-            "dtype": "bf16 x bf16 -> f32 (FP32 storage)", "value": bf["value"], "unit": UNIT,
+        line[name] = {
+            "dtype": dts, "value": bf["value"], "unit": UNIT,
             "ms_per_step": bf["ms"], "speedup_vs_f64": f64["ms"] / bf["ms"],
             "speedup_vs_fp32_cuda_core": (mixed["ms"] / bf["ms"]) if mixed else None,
             "roofline": {"bound": "hbm", "achieved": alg_bytes / (bf["ms"] * 1e-3) / 1e9,

@@ -61,10 +61,14 @@ typedef enum {
   FE_KS_F64E = 2,              /* FP64 storage, FP64-accurate result; the cell kernel and the
                                   projections work in pairs of floats (hi + lo, ~48 bits) on
                                   the FP32 pipe (apply / apply_scaled / tune / residual only) */
-  FE_KS_BF16 = 3               /* FP32 storage; the cell kernel's 1D contractions (N, D and
+  FE_KS_BF16 = 3,              /* FP32 storage; the cell kernel's 1D contractions (N, D and
                                   their transposes) run on the tensor cores with BF16
                                   operands and FP32 accumulation, the quadrature-point terms,
-                                  projections, expansion and scatter in FP32 */
+                                  projections and scatter in FP32, the nonlocal expansion
+                                  as BF16 MMAs (apply / apply_scaled / tune / filter) */
+  FE_KS_F16 = 4                /* as FE_KS_BF16 with FP16 operands (8x the precision): each
+                                  gathered cell tile is scaled by a power of two so that its
+                                  largest entry is below 1/16, and unscaled at the scatter */
 } fe_ks_precision;
 
 /* Terms of H that an application includes (terms_mask of fe_ks_setup). */
@@ -262,7 +266,7 @@ fe_ks_status fe_ks_read_profile(fe_ks_ctx* ctx, double ms[3], int64_t launches[3
  * current device in TFLOP/s (2 flops per FMA), from a bounded register-only
  * FMA loop on 4 CTAs per SM; precision = FE_KS_BF16 measures the warp-level
  * tensor-core rate (mma.sync m16n8k16, BF16 operands, FP32 accumulation)
- * that the BF16 cell kernel uses.  Allocates and frees a small device buffer.
+ * that the tensor-core cell kernel uses.  Allocates and frees a small device buffer.
  */
 fe_ks_status fe_ks_measure_fma_peak(int precision, double* tflops);
 

@@ -442,9 +442,11 @@ fe_ks_status fe_ks_setup(const fe_ks_problem* prob, int terms_mask, int64_t n_v_
             chk(upload(c, reinterpret_cast<ff2**>(&c->emu.coef), toff(coef), coef.size())) &&
             chk(upload(c, reinterpret_cast<ff2**>(&c->emu.dscale), toff(ds), ds.size()));
   if (ok) {
-    std::vector<uint32_t> frag(kTcFragWords);
-    build_tc_frags(c->p, frag.data());
-    ok = chk(upload(c, &c->tc_frag, frag.data(), frag.size()));
+    std::vector<uint32_t> frag(kTcFragWords), frag16(kTcFragWords);
+    build_tc_frags(c->p, frag.data(), false);
+    build_tc_frags(c->p, frag16.data(), true);
+    ok = chk(upload(c, &c->tc_frag, frag.data(), frag.size())) &&
+         chk(upload(c, &c->tc_frag16, frag16.data(), frag16.size()));
   }
   if (ok && want_nl) {
     std::vector<double> hh(prob->h_coef, prob->h_coef + (size_t)prob->n_atoms * prob->n_proj);
@@ -462,8 +464,12 @@ fe_ks_status fe_ks_setup(const fe_ks_problem* prob, int terms_mask, int64_t n_v_
          chk(upload<double>(c, &c->f64.part, nullptr, pn)) && chk(upload<float>(c, &c->f32.part, nullptr, pn));
     if (ok) {
       std::vector<uint2> fpack;
-      build_tc_fpack(c->np, c->cplx != 0, prob->n_proj, c->n_pairs, F.data(), fpack);
+      build_tc_fpack(c->np, c->cplx != 0, prob->n_proj, c->n_pairs, F.data(), false, fpack);
       ok = chk(upload(c, &c->tc_fpack, fpack.data(), fpack.size()));
+      if (ok) {
+        build_tc_fpack(c->np, c->cplx != 0, prob->n_proj, c->n_pairs, F.data(), true, fpack);
+        ok = chk(upload(c, &c->tc_fpack16, fpack.data(), fpack.size()));
+      }
     }
   }
   if (!ok) {
@@ -540,7 +546,7 @@ fe_ks_status fe_ks_info(const fe_ks_ctx* ctx, int64_t* n_dofs, int64_t* n_cells,
 namespace feks {
 
 template <typename T>
-fe_ks_status apply_core(Ctx& c, const T* X, T* Y, int64_t ncols, bool scaled, T alpha, bool zero_fill, bool tc) {
+fe_ks_status apply_core(Ctx& c, const T* X, T* Y, int64_t ncols, bool scaled, T alpha, bool zero_fill, int tc) {
   OpData<T>& od = *reinterpret_cast<OpData<T>*>(sizeof(T) == 8 ? (void*)&c.f64 : (void*)&c.f32);
   const T* hcoef = reinterpret_cast<const T*>(sizeof(T) == 8 ? (const void*)c.h64 : (const void*)c.h32);
   cudaStream_t s = c.stream;
@@ -607,7 +613,7 @@ fe_ks_status apply_core(Ctx& c, const T* X, T* Y, int64_t ncols, bool scaled, T 
     lp.n_cells = c.colour_ptr[col + 1] - c.colour_ptr[col];
     cudaError_t err;
     if constexpr (std::is_same<T, float>::value)
-      err = tc ? launch_tc(c, lp, s) : launch_local<T, T>(c, lp, s);
+      err = tc ? launch_tc(c, lp, s, tc == 2) : launch_local<T, T>(c, lp, s);
     else
       err = launch_local<T, T>(c, lp, s);
     if (err != cudaSuccess) return fail(FE_KS_ERR_CUDA, std::string("local kernel: ") + cudaGetErrorString(err));
@@ -621,8 +627,8 @@ fe_ks_status apply_core(Ctx& c, const T* X, T* Y, int64_t ncols, bool scaled, T 
   return FE_KS_OK;
 }
 
-template fe_ks_status apply_core<double>(Ctx&, const double*, double*, int64_t, bool, double, bool, bool);
-template fe_ks_status apply_core<float>(Ctx&, const float*, float*, int64_t, bool, float, bool, bool);
+template fe_ks_status apply_core<double>(Ctx&, const double*, double*, int64_t, bool, double, bool, int);
+template fe_ks_status apply_core<float>(Ctx&, const float*, float*, int64_t, bool, float, bool, int);
 
 // FP64-accurate application computed in pairs of floats: FP64 projections,
 // pair-of-floats cell kernel with FP64 gather / scatter (alpha is applied in
@@ -703,7 +709,7 @@ fe_ks_status apply_core_emu(Ctx& c, const double* X, double* Y, int64_t ncols, b
 }
 
 template <typename T>
-static fe_ks_status apply_impl(fe_ks_ctx* ctx, const void* Xv, void* Yv, int64_t n_v, bool scaled, bool tc = false) {
+static fe_ks_status apply_impl(fe_ks_ctx* ctx, const void* Xv, void* Yv, int64_t n_v, bool scaled, int tc = 0) {
   using TS = typename std::conditional<std::is_same<T, ff2>::value, double, T>::type;
   g_last_error.clear();
   if (!ctx) return fail(FE_KS_ERR_ARG, "ctx is NULL");
@@ -731,7 +737,8 @@ fe_ks_status fe_ks_apply(fe_ks_ctx* ctx, const void* X, void* Y, int64_t n_v, in
   if (precision == FE_KS_F64) return apply_impl<double>(ctx, X, Y, n_v, false);
   if (precision == FE_KS_F64E) return apply_impl<ff2>(ctx, X, Y, n_v, false);
   if (precision == FE_KS_F32) return apply_impl<float>(ctx, X, Y, n_v, false);
-  if (precision == FE_KS_BF16) return apply_impl<float>(ctx, X, Y, n_v, false, true);
+  if (precision == FE_KS_BF16) return apply_impl<float>(ctx, X, Y, n_v, false, 1);
+  if (precision == FE_KS_F16) return apply_impl<float>(ctx, X, Y, n_v, false, 2);
   return fail(FE_KS_ERR_UNSUPPORTED, "unknown precision");
 }
 
@@ -753,7 +760,8 @@ fe_ks_status fe_ks_tune(fe_ks_ctx* ctx, const void* X, void* Y, int64_t n_v, int
                         double* ms_per_config, int* best) {
   g_last_error.clear();
   if (!ctx || !X || !Y) return fail(FE_KS_ERR_ARG, "NULL argument");
-  if (precision != FE_KS_F64 && precision != FE_KS_F32 && precision != FE_KS_F64E && precision != FE_KS_BF16)
+  if (precision != FE_KS_F64 && precision != FE_KS_F32 && precision != FE_KS_F64E && precision != FE_KS_BF16 &&
+      precision != FE_KS_F16)
     return fail(FE_KS_ERR_UNSUPPORTED, "unknown precision");
   if (reps < 1) reps = 1;
   Ctx& c = ctx->c;
@@ -762,7 +770,7 @@ fe_ks_status fe_ks_tune(fe_ks_ctx* ctx, const void* X, void* Y, int64_t n_v, int
              : precision == FE_KS_F32 ? c.cfg32
              : precision == FE_KS_F64E ? c.cfgE
                                        : single;
-  const int n_conf = precision == FE_KS_BF16 ? 1 : kLocalConfigs;
+  const int n_conf = (precision == FE_KS_BF16 || precision == FE_KS_F16) ? 1 : kLocalConfigs;
   const int keep = cfg;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -806,7 +814,8 @@ fe_ks_status fe_ks_apply_scaled(fe_ks_ctx* ctx, const void* X, void* Y, int64_t 
   if (precision == FE_KS_F64) return apply_impl<double>(ctx, X, Y, n_v, true);
   if (precision == FE_KS_F64E) return apply_impl<ff2>(ctx, X, Y, n_v, true);
   if (precision == FE_KS_F32) return apply_impl<float>(ctx, X, Y, n_v, true);
-  if (precision == FE_KS_BF16) return apply_impl<float>(ctx, X, Y, n_v, true, true);
+  if (precision == FE_KS_BF16) return apply_impl<float>(ctx, X, Y, n_v, true, 1);
+  if (precision == FE_KS_F16) return apply_impl<float>(ctx, X, Y, n_v, true, 2);
   return fail(FE_KS_ERR_UNSUPPORTED, "unknown precision");
 }
 

@@ -95,9 +95,9 @@ static size_t filter_bytes(const Ctx& c, int64_t n_v, int precision) {
 }
 
 // Recurrence application a * Hs R_Y accumulated into R_X, in the recurrence's arithmetic.
-// emu: pair-of-floats kernel (T = double); tc: BF16 tensor-core kernel (T = float).
+// emu: pair-of-floats kernel (T = double); tc: tensor-core kernel (T = float; 1 BF16, 2 FP16).
 template <typename T>
-static fe_ks_status recurrence_apply(Ctx& c, const T* RY, T* RX, int64_t ncols, double a, bool emu, bool tc) {
+static fe_ks_status recurrence_apply(Ctx& c, const T* RY, T* RX, int64_t ncols, double a, bool emu, int tc) {
   if constexpr (std::is_same<T, double>::value) {
     if (emu) return apply_core_emu(c, RY, RX, ncols, true, a, false);
   }
@@ -106,7 +106,7 @@ static fe_ks_status recurrence_apply(Ctx& c, const T* RY, T* RX, int64_t ncols, 
 
 template <typename T>
 static fe_ks_status cheb_impl(Ctx& c, double* X, const double* lam, int64_t n_v, int degree, double lmin, double lT,
-                              double lmax, char* work, bool rec_emu, bool res_emu, bool rec_tc = false) {
+                              double lmax, char* work, bool rec_emu, bool res_emu, int rec_tc = 0) {
   cudaStream_t s = c.stream;
   const int cw = c.cplx ? 2 : 1;
   const int64_t ncols = n_v * cw;
@@ -162,9 +162,10 @@ extern "C" {
 
 fe_ks_status fe_ks_cheb_filter_workspace(const fe_ks_ctx* ctx, int64_t n_v, int precision, size_t* bytes) {
   if (!ctx || !bytes) return fail(FE_KS_ERR_ARG, "NULL argument");
-  if (precision != FE_KS_F64 && precision != FE_KS_F32 && precision != FE_KS_F64E && precision != FE_KS_BF16)
+  if (precision != FE_KS_F64 && precision != FE_KS_F32 && precision != FE_KS_F64E && precision != FE_KS_BF16 &&
+      precision != FE_KS_F16)
     return fail(FE_KS_ERR_UNSUPPORTED, "unknown precision");
-  *bytes = filter_bytes(ctx->c, n_v, precision == FE_KS_BF16 ? FE_KS_F32 : precision);
+  *bytes = filter_bytes(ctx->c, n_v, (precision == FE_KS_BF16 || precision == FE_KS_F16) ? FE_KS_F32 : precision);
   return FE_KS_OK;
 }
 
@@ -177,18 +178,19 @@ fe_ks_status fe_ks_cheb_filter(fe_ks_ctx* ctx, double* X, const double* ritz, in
   if (n_v < 1 || n_v > c.n_v_max) return fail(FE_KS_ERR_ARG, "n_v must be in 1..n_v_max");
   if (degree < 1) return fail(FE_KS_ERR_ARG, "degree must be >= 1");
   if (!(lam_min < lam_T && lam_T < lam_max)) return fail(FE_KS_ERR_ARG, "need lam_min < lam_T < lam_max");
-  if (precision != FE_KS_F64 && precision != FE_KS_F32 && precision != FE_KS_F64E && precision != FE_KS_BF16)
+  if (precision != FE_KS_F64 && precision != FE_KS_F32 && precision != FE_KS_F64E && precision != FE_KS_BF16 &&
+      precision != FE_KS_F16)
     return fail(FE_KS_ERR_UNSUPPORTED, "unknown precision");
   if (residual_precision != FE_KS_F64 && residual_precision != FE_KS_F64E)
     return fail(FE_KS_ERR_ARG, "residual_precision must be FE_KS_F64 or FE_KS_F64E");
-  if (work_bytes < filter_bytes(c, n_v, precision == FE_KS_BF16 ? FE_KS_F32 : precision))
+  if (work_bytes < filter_bytes(c, n_v, (precision == FE_KS_BF16 || precision == FE_KS_F16) ? FE_KS_F32 : precision))
     return fail(FE_KS_ERR_ARG, "workspace too small");
   if (((uintptr_t)work & 255) || ((uintptr_t)X & 7)) return fail(FE_KS_ERR_ARG, "misaligned X or workspace");
   char* w = static_cast<char*>(work);
   const bool res_emu = residual_precision == FE_KS_F64E;
-  if (precision == FE_KS_F32 || precision == FE_KS_BF16)
+  if (precision == FE_KS_F32 || precision == FE_KS_BF16 || precision == FE_KS_F16)
     return cheb_impl<float>(c, X, ritz, n_v, degree, lam_min, lam_T, lam_max, w, false, res_emu,
-                            precision == FE_KS_BF16);
+                            precision == FE_KS_BF16 ? 1 : precision == FE_KS_F16 ? 2 : 0);
   return cheb_impl<double>(c, X, ritz, n_v, degree, lam_min, lam_T, lam_max, w, precision == FE_KS_F64E, res_emu);
 }
 

@@ -131,8 +131,10 @@ struct Ctx {
     EOTables<ff2> tab;
   } emu;
   // B fragments of the BF16 tensor-core cell kernel: [4 ops][2 tiles][32 lanes][2]
-  uint32_t* tc_frag = nullptr;
-  uint2* tc_fpack = nullptr;   // F as expansion B fragments (when the nonlocal term is present)
+  uint32_t* tc_frag = nullptr;     // BF16
+  uint32_t* tc_frag16 = nullptr;   // FP16
+  uint2* tc_fpack = nullptr;       // F as expansion B fragments, BF16 (when the nonlocal term is present)
+  uint2* tc_fpack16 = nullptr;     // the same in FP16
   std::vector<void*> allocations;
   // profiling: events recorded per application (start, after fill, after projection, after local)
   bool profiling = false;
@@ -157,18 +159,20 @@ void build_eo_tables<ff2>(int p, int nq, EOTables<ff2>* out);
 // out[((op * 2 + tile) * 32 + lane) * 2 + reg], op 0 = N (nodes -> Gauss
 // points), 1 = D (Gauss-point derivative of the nodal basis), 2 = N^T, 3 = D^T.
 constexpr int kTcFragWords = 4 * 2 * 32 * 2;
-void build_tc_frags(int p, uint32_t* out);
+void build_tc_frags(int p, uint32_t* out, bool f16);
 uint16_t bf16_bits(double x);   // nearest BF16 (ties to even), as its bit pattern
+uint16_t f16_bits(double x);    // nearest FP16 (ties to even), as its bit pattern
 // The projector matrices F [pair][n_proj][n^3] (complex: x2 interleaved) as BF16
 // B fragments of the tensor-core kernel's expansion MMAs:
 // out[pair][row tile][half][8-column tile][K step][lane] (uint2 per lane).
-void build_tc_fpack(int n, bool cplx, int n_proj, int64_t n_pairs, const double* F, std::vector<uint2>& out);
+void build_tc_fpack(int n, bool cplx, int n_proj, int64_t n_pairs, const double* F, bool f16, std::vector<uint2>& out);
 
 // Y (+)= alpha H X or alpha Hs X on the context's stream; zero_fill clears Y first.
-// tc: FP32 storage with the BF16 tensor-core cell kernel (T = float only).
+// tc: FP32 storage with the tensor-core cell kernel (T = float only): 0 = off,
+// 1 = BF16, 2 = FP16.
 template <typename T>
 fe_ks_status apply_core(Ctx& c, const T* X, T* Y, int64_t ncols, bool scaled, T alpha, bool zero_fill,
-                        bool tc = false);
+                        int tc = 0);
 fe_ks_status apply_core_emu(Ctx& c, const double* X, double* Y, int64_t ncols, bool scaled, double alpha,
                             bool zero_fill);
 
@@ -186,7 +190,7 @@ cudaError_t launch_proj_pairs(const Ctx& c, const ProjParams<T>& prm, int n_atom
 cudaError_t launch_proj_pairs_emu(const Ctx& c, const ProjParams<double>& prm, const ff2* F, int n_atoms,
                                   cudaStream_t s);
 // BF16 tensor-core cell kernel (fe_ks_tc.cu) for one colour of cells
-cudaError_t launch_tc(const Ctx& c, const LocalParams<float>& lp, cudaStream_t s);
+cudaError_t launch_tc(const Ctx& c, const LocalParams<float>& lp, cudaStream_t s, bool f16);
 size_t tc_smem_bytes(int n, bool cplx);
 
 }  // namespace feks

@@ -148,7 +148,32 @@ uint16_t bf16_bits(double x) {
   return (uint16_t)(u >> 16);
 }
 
-void build_tc_frags(int p, uint32_t* out) {
+// Nearest FP16 (ties to even) of a value inside the FP16 range, through the
+// nearest float; subnormal results are rounded at their fixed quantum 2^-24.
+uint16_t f16_bits(double x) {
+  const float f = (float)x;
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  const uint32_t sign = (u >> 16) & 0x8000u;
+  const int e = (int)((u >> 23) & 0xFFu) - 127;
+  uint32_t mant = u & 0x7FFFFFu;
+  if (e > 15) return (uint16_t)(sign | 0x7C00u);                 // beyond the range: infinity
+  if (e < -25 || (u & 0x7FFFFFFFu) == 0) return (uint16_t)sign;  // below half the smallest subnormal
+  if (e < -14) {                                                  // subnormal: quantum 2^-24
+    mant |= 0x800000u;
+    const int sh = -e - 1;   // value = mant 2^(e - 23) = (mant >> sh) quanta of 2^-24
+    const uint32_t q = mant >> (sh);
+    const uint32_t rem = mant & ((1u << sh) - 1u), half = 1u << (sh - 1);
+    const uint32_t r = q + ((rem > half || (rem == half && (q & 1u))) ? 1u : 0u);
+    return (uint16_t)(sign | r);
+  }
+  uint32_t h = ((uint32_t)(e + 15) << 10) | (mant >> 13);
+  const uint32_t rem = mant & 0x1FFFu;
+  if (rem > 0x1000u || (rem == 0x1000u && (h & 1u))) ++h;   // carries into the exponent correctly
+  return (uint16_t)(sign | h);
+}
+
+void build_tc_frags(int p, uint32_t* out, bool f16) {
   const int n = p + 1;
   double xg[kMaxN], wg[kMaxN], xq[kMaxN], wq[kMaxN], val[kMaxN], der[kMaxN];
   gauss_lobatto(n, xg, wg);
@@ -177,8 +202,8 @@ void build_tc_frags(int p, uint32_t* out) {
         const int g = lane / 4, t = lane % 4, col = 8 * tile + g;
         for (int r = 0; r < 2; ++r) {
           const int k = 2 * t + 8 * r;
-          out[((op * 2 + tile) * 32 + lane) * 2 + r] =
-              (uint32_t)bf16_bits(B(op, k, col)) | ((uint32_t)bf16_bits(B(op, k + 1, col)) << 16);
+          auto h = [&](double x) -> uint32_t { return f16 ? f16_bits(x) : bf16_bits(x); };
+          out[((op * 2 + tile) * 32 + lane) * 2 + r] = h(B(op, k, col)) | (h(B(op, k + 1, col)) << 16);
         }
       }
 }

@@ -1,6 +1,9 @@
-// Tensor-core cell kernel (FE_KS_BF16): the 1D contractions of Algorithm 2 as
-// warp-level BF16 MMAs with FP32 accumulation, the quadrature-point step,
-// nonlocal expansion and scatter in FP32.
+// Tensor-core cell kernel (FE_KS_BF16, FE_KS_F16): the 1D contractions of
+// Algorithm 2 as warp-level BF16 or FP16 MMAs with FP32 accumulation, the
+// quadrature-point step, nonlocal expansion and scatter in FP32.  FP16 has 8x
+// the precision of BF16 but a narrow range, so each gathered cell tile is
+// scaled by a power of two (its largest entry to at most 1/16) and the result
+// unscaled at the scatter: the chain is linear and the scaling exact.
 //
 // Paper: Algorithm 2 (cell-level evaluation, eq. ggaReal / eq. ggaCmplx) called
 // from Algorithm 1 (extraction Q C P X, F Delta T3, assembly Q^T).  The
@@ -25,6 +28,7 @@
 // the kernel's time goes to shared-memory transposes and the FP32 pointwise
 // work, not to tensor issue.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "fe_ks_internal.h"
 
@@ -51,7 +55,7 @@ struct TcParams {
   int n_proj;
   float alpha;
   const uint32_t* frag;    // B fragments [4 ops][2 tiles][32 lanes][2]
-  const uint2* fpack;      // F as BF16 B fragments [pair][row tile][half][tile][K step][32 lanes]
+  const uint2* fpack;      // F as BF16 / FP16 B fragments [pair][row tile][half][tile][K step][32 lanes]
 };
 
 namespace tc {
@@ -83,7 +87,8 @@ struct Geom {
   // fragment-order writes and the row reads are both conflict-free)
   static constexpr int SST = 12;
   static constexpr int OFF_STAGE = (OFF_DOFS + N3 * 4 + 15) / 16 * 16;
-  static constexpr int BYTES = OFF_STAGE + N3 * SST * 4;
+  static constexpr int OFF_RED = OFF_STAGE + N3 * SST * 4;   // per-warp maxima (FP16 tile scaling)
+  static constexpr int BYTES = OFF_RED + 32 * 4;
   // Two resident CTAs per SM.  (Three fit the shared memory at n = 9, but the
   // register cap that lets 21 warps share the SM's four 16K-register files
   // (80 per thread) made the kernel spill and measured no faster.)
@@ -106,6 +111,20 @@ struct Geom {
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t*>(&h);
+}
+
+__device__ __forceinline__ uint32_t pack_f16(float lo, float hi) {
+  __half2 h = __floats2half2_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// two values rounded to the kernel's 16-bit type, packed (lower index low)
+template <bool F16>
+__device__ __forceinline__ uint32_t pack16(float lo, float hi) {
+  if constexpr (F16)
+    return pack_f16(lo, hi);
+  else
+    return pack_bf16(lo, hi);
 }
 
 template <bool K16>
@@ -135,14 +154,23 @@ __device__ __forceinline__ void stsm(uint32_t addr, const uint32_t (&r)[4]) {
                  : "memory");
 }
 
-// d += a * b for one 16 x 8 output tile
-template <bool K16>
+// d += a * b for one 16 x 8 output tile (BF16 or FP16 operands, FP32 accumulators)
+template <bool K16, bool F16 = false>
 __device__ __forceinline__ void mma(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  if constexpr (K16)
+  if constexpr (K16 && F16)
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+  else if constexpr (K16)
     asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
         "{%0,%1,%2,%3};\n"
         : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+  else if constexpr (F16)
+    asm("mma.sync.aligned.m16n8k8.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(b[0]));
   else
     asm("mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};\n"
         : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
@@ -150,29 +178,38 @@ __device__ __forceinline__ void mma(float (&d)[4], const uint32_t (&a)[4], const
 }
 
 // d = a * b (zero accumulator input)
-template <bool K16>
+template <bool K16, bool F16 = false>
 __device__ __forceinline__ void mma0(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
   const float z = 0.f;
-  if constexpr (K16)
+  if constexpr (K16 && F16)
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%10,%10,%10,%10};\n"
+        : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "f"(z));
+  else if constexpr (K16)
     asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
         "{%10,%10,%10,%10};\n"
         : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "f"(z));
+  else if constexpr (F16)
+    asm("mma.sync.aligned.m16n8k8.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%7,%7,%7,%7};\n"
+        : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(b[0]), "f"(z));
   else
     asm("mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%7,%7,%7,%7};\n"
         : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
         : "r"(a[0]), "r"(a[1]), "r"(b[0]), "f"(z));
 }
 
-// Accumulator tiles -> BF16 fragment: the A operand of an MMA contracting the
-// same index, and the register order stmatrix expects.
-template <int NTL>
+// Accumulator tiles -> 16-bit fragment: the A operand of an MMA contracting
+// the same index, and the register order stmatrix expects.
+template <int NTL, bool F16 = false>
 __device__ __forceinline__ void to_frag(const float (&d)[NTL][4], uint32_t (&a)[4]) {
-  a[0] = pack_bf16(d[0][0], d[0][1]);
-  a[1] = pack_bf16(d[0][2], d[0][3]);
+  a[0] = pack16<F16>(d[0][0], d[0][1]);
+  a[1] = pack16<F16>(d[0][2], d[0][3]);
   if constexpr (NTL == 2) {
-    a[2] = pack_bf16(d[1][0], d[1][1]);
-    a[3] = pack_bf16(d[1][2], d[1][3]);
+    a[2] = pack16<F16>(d[1][0], d[1][1]);
+    a[3] = pack16<F16>(d[1][2], d[1][3]);
   } else {
     a[2] = a[3] = 0u;
   }
@@ -200,12 +237,22 @@ __device__ __forceinline__ uint32_t at(uint32_t arr, int off, uint32_t spare) {
   return off >= 0 ? arr + (uint32_t)off : spare;
 }
 
+// Power of two s with s * mx < 1/16 (s = 1 for mx = 0), from the exponent bits
+// of mx: mx < 2^(E - 126) for biased exponent E, so s = 2^(122 - E).
+__device__ __forceinline__ float tile_scale(float mx) {
+  if (!(mx > 0.f)) return 1.f;
+  int e = (int)((__float_as_uint(mx) >> 23) & 0xFFu);
+  e = e < 1 ? 1 : (e > 248 ? 248 : e);
+  return __uint_as_float((uint32_t)(249 - e) << 23);
+}
+
 // Assembly Y += alpha D^{-1/2} Q^T Y^(e) of the staged FP32 cell result for
 // columns [c0, c0 + 8): one node per thread, two 16-byte reductions per node
 // when the rows are 16-byte aligned.  Colour-exclusive launches: no other
 // cell of the launch touches the same DoF rows.
 template <int N, bool CPLX>
-__device__ __forceinline__ void scatter_stage(const TcParams& p, const float* stage, const int* sd, int c0, bool vecy) {
+__device__ __forceinline__ void scatter_stage(const TcParams& p, const float* stage, const int* sd, int c0, bool vecy,
+                                              float unscale) {
   using Gm = Geom<N, CPLX>;
   const bool fullv = vecy && c0 + 8 <= p.ncols;
   for (int node = threadIdx.x; node < Gm::N3; node += Gm::NT) {
@@ -213,7 +260,7 @@ __device__ __forceinline__ void scatter_stage(const TcParams& p, const float* st
     float4 a = *reinterpret_cast<const float4*>(sp);
     float4 b = *reinterpret_cast<const float4*>(sp + 4);
     const int d = sd[node];
-    const float sc = p.dscale ? p.alpha * __ldg(p.dscale + d) : p.alpha;
+    const float sc = (p.dscale ? p.alpha * __ldg(p.dscale + d) : p.alpha) * unscale;
     a.x *= sc, a.y *= sc, a.z *= sc, a.w *= sc;
     b.x *= sc, b.y *= sc, b.z *= sc, b.w *= sc;
     float* yp = p.Y + (int64_t)d * p.ld + c0;
@@ -229,7 +276,7 @@ __device__ __forceinline__ void scatter_stage(const TcParams& p, const float* st
   }
 }
 
-template <int N, bool CPLX>
+template <int N, bool CPLX, bool F16>
 __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_kernel(const __grid_constant__ TcParams p) {
   using Gm = Geom<N, CPLX>;
   constexpr bool K16 = Gm::K16;
@@ -281,12 +328,14 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_
     const int pb = p.cell_pair_ptr ? p.cell_pair_ptr[e] : 0;
     const int pe = p.cell_pair_ptr ? p.cell_pair_ptr[e + 1] : 0;
     __syncthreads();
-    int prev0 = -1;   // columns of the staged result still to be assembled
+    int prev0 = -1;          // columns of the staged result still to be assembled
+    float prev_unscale = 1.f;
     for (int t = blockIdx.y; t < ntiles; t += gridDim.y) {
       const int col0 = 8 * t;
       const int col = col0 + gq;
       const bool full = vec && col0 + 8 <= p.ncols;
-      // (1) extraction Q C P X (Algorithm 1): rows of X -> BF16 array 2 [node][8]
+      float tscale = 1.f;   // power-of-two scale of this tile (FP16 only)
+      // (1) extraction Q C P X (Algorithm 1): rows of X -> 16-bit array 2 [node][8]
       //     (array 2 is not read by the previous tile's last sweep); the loads
       //     are in flight while the previous tile's staged result is assembled
       {
@@ -314,18 +363,38 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_
             if (p.dscale) sc[r] = __ldg(p.dscale + d);
           }
         }
-        if (prev0 >= 0) scatter_stage<N, CPLX>(p, stage, sd, prev0, vecy);
+        if (prev0 >= 0) scatter_stage<N, CPLX>(p, stage, sd, prev0, vecy, prev_unscale);
+        // FP16: scale the tile by a power of two so that its largest entry is
+        // below 1/16 (exact; undone at the scatter)
+        if constexpr (F16) {
+          float mx = 0.f;
+#pragma unroll
+          for (int r = 0; r < GPT; ++r) {
+            const float s = sc[r];
+            mx = fmaxf(mx, fmaxf(fmaxf(fabsf(xa[r].x * s), fabsf(xa[r].y * s)), fmaxf(fabsf(xa[r].z * s), fabsf(xa[r].w * s))));
+            mx = fmaxf(mx, fmaxf(fmaxf(fabsf(xb[r].x * s), fabsf(xb[r].y * s)), fmaxf(fabsf(xb[r].z * s), fabsf(xb[r].w * s))));
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+          float* wmax = reinterpret_cast<float*>(smem + Gm::OFF_RED);
+          if (lane == 0) wmax[warp] = mx;
+          __syncthreads();
+          mx = 0.f;
+#pragma unroll
+          for (int w = 0; w < NW; ++w) mx = fmaxf(mx, wmax[w]);
+          tscale = tile_scale(mx);
+        }
 #pragma unroll
         for (int r = 0; r < GPT; ++r) {
           const int node = tid + r * NT;
           if (node < N3) {
             const int i = node % N, j = (node / N) % N, k = node / (N * N);
-            const float s = sc[r];
+            const float s = sc[r] * tscale;
             uint4 u;
-            u.x = pack_bf16(xa[r].x * s, xa[r].y * s);
-            u.y = pack_bf16(xa[r].z * s, xa[r].w * s);
-            u.z = pack_bf16(xb[r].x * s, xb[r].y * s);
-            u.w = pack_bf16(xb[r].z * s, xb[r].w * s);
+            u.x = pack16<F16>(xa[r].x * s, xa[r].y * s);
+            u.y = pack16<F16>(xa[r].z * s, xa[r].w * s);
+            u.z = pack16<F16>(xb[r].x * s, xb[r].y * s);
+            u.w = pack16<F16>(xb[r].z * s, xb[r].w * s);
             *reinterpret_cast<uint4*>(smem + 2 * Gm::ARR + 16 * (i + SY * j + SZ * k)) = u;
           }
         }
@@ -354,15 +423,15 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_
           for (int b = 0; b < BX; ++b)
 #pragma unroll
             for (int j = 0; j < NTL; ++j) {
-              mma0<K16>(u[b][j], a[b], bN[j]);
-              mma0<K16>(ud[b][j], a[b], bD[j]);
+              mma0<K16, F16>(u[b][j], a[b], bN[j]);
+              mma0<K16, F16>(ud[b][j], a[b], bD[j]);
             }
 #pragma unroll
           for (int b = 0; b < BX; ++b) {
             uint32_t o[4];
-            to_frag(u[b], o);
+            to_frag<NTL, F16>(u[b], o);
             stsm<NTL>(at(A0, off[b], trash), o);
-            to_frag(ud[b], o);
+            to_frag<NTL, F16>(ud[b], o);
             stsm<NTL>(at(A1, off[b], trash), o);
           }
         }
@@ -387,18 +456,18 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_
           for (int b = 0; b < BY; ++b)
 #pragma unroll
             for (int j = 0; j < NTL; ++j) {
-              mma0<K16>(t0[b][j], a[b], bN[j]);
-              mma0<K16>(t1[b][j], a[b], bD[j]);
-              mma0<K16>(t2[b][j], b2[b], bN[j]);
+              mma0<K16, F16>(t0[b][j], a[b], bN[j]);
+              mma0<K16, F16>(t1[b][j], a[b], bD[j]);
+              mma0<K16, F16>(t2[b][j], b2[b], bN[j]);
             }
 #pragma unroll
           for (int b = 0; b < BY; ++b) {
             uint32_t o[4];
-            to_frag(t0[b], o);
+            to_frag<NTL, F16>(t0[b], o);
             stsm<NTL>(at(A0, off[b], trash), o);
-            to_frag(t1[b], o);
+            to_frag<NTL, F16>(t1[b], o);
             stsm<NTL>(at(A1, off[b], trash), o);
-            to_frag(t2[b], o);
+            to_frag<NTL, F16>(t2[b], o);
             stsm<NTL>(at(A2, off[b], trash), o);
           }
         }
@@ -418,10 +487,10 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_
         float u[NTL][4], gx[NTL][4], gy[NTL][4], gz[NTL][4];
 #pragma unroll
         for (int j = 0; j < NTL; ++j) {
-          mma0<K16>(u[j], a, bN[j]);
-          mma0<K16>(gz[j], a, bD[j]);
-          mma0<K16>(gy[j], b, bN[j]);
-          mma0<K16>(gx[j], c, bN[j]);
+          mma0<K16, F16>(u[j], a, bN[j]);
+          mma0<K16, F16>(gz[j], a, bD[j]);
+          mma0<K16, F16>(gy[j], b, bN[j]);
+          mma0<K16, F16>(gx[j], c, bN[j]);
         }
         // element (j, r): line g0 + (r >> 1), column v = gq, qz = 8 j + 2 tig + (r & 1);
         // the coefficients of a line start at cbase[r >> 1], qz adds SZ NC per step
@@ -489,27 +558,27 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_
             gz[j][r] = w2;
           }
         uint32_t fz[4], fx[4], fy[4], fw[4], o[4];
-        to_frag(u, fz);
-        to_frag(gx, fx);
-        to_frag(gy, fy);
-        to_frag(gz, fw);
+        to_frag<NTL, F16>(u, fz);
+        to_frag<NTL, F16>(gx, fx);
+        to_frag<NTL, F16>(gy, fy);
+        to_frag<NTL, F16>(gz, fw);
         float va[NTL][4], va2[NTL][4], vb[NTL][4], vc[NTL][4];
 #pragma unroll
         for (int j = 0; j < NTL; ++j) {   // four independent accumulators
-          mma0<K16>(va[j], fz, bNt[j]);
-          mma0<K16>(va2[j], fw, bDt[j]);
-          mma0<K16>(vb[j], fy, bNt[j]);
-          mma0<K16>(vc[j], fx, bNt[j]);
+          mma0<K16, F16>(va[j], fz, bNt[j]);
+          mma0<K16, F16>(va2[j], fw, bDt[j]);
+          mma0<K16, F16>(vb[j], fy, bNt[j]);
+          mma0<K16, F16>(vc[j], fx, bNt[j]);
         }
 #pragma unroll
         for (int j = 0; j < NTL; ++j)
 #pragma unroll
           for (int r = 0; r < 4; ++r) va[j][r] += va2[j][r];
-        to_frag(va, o);
+        to_frag<NTL, F16>(va, o);
         stsm<NTL>(at(A0, off, trash), o);
-        to_frag(vb, o);
+        to_frag<NTL, F16>(vb, o);
         stsm<NTL>(at(A1, off, trash), o);
-        to_frag(vc, o);
+        to_frag<NTL, F16>(vc, o);
         stsm<NTL>(at(A2, off, trash), o);
       }
       __syncthreads();
@@ -534,9 +603,9 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_
           for (int b = 0; b < BR; ++b)
 #pragma unroll
             for (int j = 0; j < NTL; ++j) {
-              mma0<K16>(sa[b][j], a[b], bNt[j]);
-              mma0<K16>(sa2[b][j], b2[b], bDt[j]);
-              mma0<K16>(sb[b][j], c2[b], bNt[j]);
+              mma0<K16, F16>(sa[b][j], a[b], bNt[j]);
+              mma0<K16, F16>(sa2[b][j], b2[b], bDt[j]);
+              mma0<K16, F16>(sb[b][j], c2[b], bNt[j]);
             }
 #pragma unroll
           for (int b = 0; b < BR; ++b) {
@@ -545,9 +614,9 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_
 #pragma unroll
               for (int r = 0; r < 4; ++r) sa[b][j][r] += sa2[b][j][r];
             uint32_t o[4];
-            to_frag(sa[b], o);
+            to_frag<NTL, F16>(sa[b], o);
             stsm<NTL>(at(A0, off[b], trash), o);
-            to_frag(sb[b], o);
+            to_frag<NTL, F16>(sb[b], o);
             stsm<NTL>(at(A1, off[b], trash), o);
           }
         }
@@ -567,8 +636,8 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_
         zero(ye[1]);
 #pragma unroll
         for (int j = 0; j < NTL; ++j) {
-          mma0<K16>(y[j], a, bNt[j]);
-          mma0<K16>(y2[j], b, bDt[j]);
+          mma0<K16, F16>(y[j], a, bNt[j]);
+          mma0<K16, F16>(y2[j], b, bDt[j]);
         }
         // Y^(e)[(line, v)][i] += sum_b Q[a][b][v] F[pair][b][i + N line]: A = Q^T
         // (rows of one line only, the other half zero), B = the packed F block
@@ -586,20 +655,20 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_
               const bool okb = act && b0 + o2 < p.n_proj;
               if constexpr (CPLX) {
                 const float* qr = Qa + (int64_t)(b0 + o2) * p.ld + (col & ~1);
-                q[o2][0] = okb ? __ldg(qr) : 0.f;
-                q[o2][1] = okb ? __ldg(qr + 1) : 0.f;
+                q[o2][0] = okb ? __ldg(qr) * tscale : 0.f;
+                q[o2][1] = okb ? __ldg(qr + 1) * tscale : 0.f;
               } else {
-                q[o2][0] = okb ? __ldg(Qa + (int64_t)(b0 + o2) * p.ld + col) : 0.f;
+                q[o2][0] = okb ? __ldg(Qa + (int64_t)(b0 + o2) * p.ld + col) * tscale : 0.f;
                 q[o2][1] = 0.f;
               }
             }
             if constexpr (CPLX) {
               // real column: Fr Qr - Fi Qi; imaginary column: Fr Qi + Fi Qr
               const bool im = gq & 1;
-              aq[0][kh] = pack_bf16(im ? q[0][1] : q[0][0], im ? q[1][1] : q[1][0]);
-              aq[S - 1][kh] = pack_bf16(im ? q[0][0] : -q[0][1], im ? q[1][0] : -q[1][1]);
+              aq[0][kh] = pack16<F16>(im ? q[0][1] : q[0][0], im ? q[1][1] : q[1][0]);
+              aq[S - 1][kh] = pack16<F16>(im ? q[0][0] : -q[0][1], im ? q[1][0] : -q[1][1]);
             } else {
-              aq[0][kh] = pack_bf16(q[0][0], q[1][0]);
+              aq[0][kh] = pack16<F16>(q[0][0], q[1][0]);
             }
           }
           const uint2* fp = p.fpack + ((size_t)pr * NMT + mt) * (2 * NTL * S * 32) + lane;
@@ -616,7 +685,7 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_
                 af[1] = h == 1 ? aq[st][0] : 0u;
                 af[2] = h == 0 ? aq[st][1] : 0u;
                 af[3] = h == 1 ? aq[st][1] : 0u;
-                mma<true>(ye[h][j], af, bb);
+                mma<true, F16>(ye[h][j], af, bb);
               }
         }
 #pragma unroll
@@ -636,12 +705,13 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_
       }
       __syncthreads();   // the stage is complete; array 2 is free for the next extraction
       prev0 = col0;
+      prev_unscale = 1.f / tscale;   // exact: a power of two
     }
-    if (prev0 >= 0) scatter_stage<N, CPLX>(p, stage, sd, prev0, vecy);
+    if (prev0 >= 0) scatter_stage<N, CPLX>(p, stage, sd, prev0, vecy, prev_unscale);
   }
 }
 
-template <int N, bool CPLX>
+template <int N, bool CPLX, bool F16>
 cudaError_t launch_tc_n(const TcParams& p, cudaStream_t s) {
   using Gm = Geom<N, CPLX>;
   if (p.n_cells == 0) return cudaSuccess;
@@ -649,10 +719,10 @@ cudaError_t launch_tc_n(const TcParams& p, cudaStream_t s) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaError_t err =
-      cudaFuncSetAttribute(fe_tc_kernel<N, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize, Gm::BYTES);
+      cudaFuncSetAttribute(fe_tc_kernel<N, CPLX, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, Gm::BYTES);
   if (err != cudaSuccess) return err;
   // ask for the largest shared-memory carveout so that MINB CTAs fit on an SM with room to spare
-  err = cudaFuncSetAttribute(fe_tc_kernel<N, CPLX>, cudaFuncAttributePreferredSharedMemoryCarveout,
+  err = cudaFuncSetAttribute(fe_tc_kernel<N, CPLX, F16>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
   if (err != cudaSuccess) return err;
   const int ntiles = (p.ncols + 7) / 8;
@@ -663,13 +733,13 @@ cudaError_t launch_tc_n(const TcParams& p, cudaStream_t s) {
   gy = gy < 1 ? 1 : (gy > ntiles ? ntiles : gy);
   if (gy > 65535) gy = 65535;
   const int gx = p.n_cells < (1 << 30) ? p.n_cells : (1 << 30);
-  fe_tc_kernel<N, CPLX><<<dim3(gx, gy), Gm::NT, Gm::BYTES, s>>>(p);
+  fe_tc_kernel<N, CPLX, F16><<<dim3(gx, gy), Gm::NT, Gm::BYTES, s>>>(p);
   return cudaGetLastError();
 }
 
 }  // namespace tc
 
-void build_tc_fpack(int n, bool cplx, int n_proj, int64_t n_pairs, const double* F, std::vector<uint2>& out) {
+void build_tc_fpack(int n, bool cplx, int n_proj, int64_t n_pairs, const double* F, bool f16, std::vector<uint2>& out) {
   const int G = n * n, NMT = (G + 1) / 2, NTL = n > 8 ? 2 : 1, S = cplx ? 2 : 1, np3 = n * n * n;
   out.assign((size_t)n_pairs * NMT * 2 * NTL * S * 32, make_uint2(0u, 0u));
   size_t w = 0;
@@ -685,8 +755,9 @@ void build_tc_fpack(int n, bool cplx, int n_proj, int64_t n_pairs, const double*
                 const size_t idx = ((size_t)pr * n_proj + k) * np3 + i + (size_t)n * g;
                 return cplx ? F[2 * idx + st] : F[idx];
               };
-              out[w].x = (uint32_t)bf16_bits(B(2 * tig)) | ((uint32_t)bf16_bits(B(2 * tig + 1)) << 16);
-              out[w].y = (uint32_t)bf16_bits(B(2 * tig + 8)) | ((uint32_t)bf16_bits(B(2 * tig + 9)) << 16);
+              auto h = [&](double x) -> uint32_t { return f16 ? f16_bits(x) : bf16_bits(x); };
+              out[w].x = h(B(2 * tig)) | (h(B(2 * tig + 1)) << 16);
+              out[w].y = h(B(2 * tig + 8)) | (h(B(2 * tig + 9)) << 16);
             }
 }
 
@@ -709,7 +780,7 @@ size_t tc_smem_bytes(int n, bool cplx) {
   }
 }
 
-cudaError_t launch_tc(const Ctx& c, const LocalParams<float>& lp, cudaStream_t s) {
+cudaError_t launch_tc(const Ctx& c, const LocalParams<float>& lp, cudaStream_t s, bool f16) {
   TcParams p{};
   p.X = lp.X;
   p.Y = lp.Y;
@@ -729,12 +800,14 @@ cudaError_t launch_tc(const Ctx& c, const LocalParams<float>& lp, cudaStream_t s
   p.Q = lp.Q;
   p.n_proj = lp.n_proj;
   p.alpha = lp.alpha;
-  p.frag = c.tc_frag;
-  p.fpack = c.tc_fpack;
+  p.frag = f16 ? c.tc_frag16 : c.tc_frag;
+  p.fpack = f16 ? c.tc_fpack16 : c.tc_fpack;
   if (p.cell_pair_ptr && !p.fpack) return cudaErrorInvalidValue;
   switch (c.np) {
-#define FEKS_TC_LAUNCH(NN) \
-  case NN: return c.cplx ? tc::launch_tc_n<NN, true>(p, s) : tc::launch_tc_n<NN, false>(p, s);
+#define FEKS_TC_LAUNCH(NN)                                                                   \
+  case NN:                                                                                   \
+    if (f16) return c.cplx ? tc::launch_tc_n<NN, true, true>(p, s) : tc::launch_tc_n<NN, false, true>(p, s); \
+    return c.cplx ? tc::launch_tc_n<NN, true, false>(p, s) : tc::launch_tc_n<NN, false, false>(p, s);
     FEKS_TC_LAUNCH(2)
     FEKS_TC_LAUNCH(3)
     FEKS_TC_LAUNCH(4)

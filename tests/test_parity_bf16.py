@@ -1,8 +1,10 @@
-"""GPU parity of the tensor-core cell kernel (FE_KS_BF16) against the FP64 oracle.
+"""GPU parity of the tensor-core cell kernel (FE_KS_BF16, FE_KS_F16) against the
+FP64 oracle.
 
-FE_KS_BF16 keeps X and Y in FP32 and runs the 1D contractions of Algorithm 2
-as BF16 x BF16 products with FP32 accumulation.  Tolerance derivation: a BF16
-rounding has relative error <= u = 2^-8 (8 significant bits).  A value reaches
+Both keep X and Y in FP32 and run the 1D contractions of Algorithm 2 as 16-bit
+products with FP32 accumulation (FP16 with a power-of-two scale per cell tile).
+Tolerance derivation: a rounding to the 16-bit type has relative error <= u
+(2^-8 for BF16's 8 significant bits, 2^-11 for FP16's 11).  A value reaches
 the output through at most six roundings of data (the gathered X, the x and
 y sweeps, the quadrature-point values, the transposed z and y sweeps) and the
 rounded entries of three 1D matrices; for the trial blocks used here (uniform
@@ -11,7 +13,8 @@ against its intermediates, so the first-order bound is (6 + 3) u = 0.035 per
 element and a column norm is no worse.  The tests hold the per-column
 relative error (max over columns) to 8 u = 2^-5 = 0.03125, which the measured
 errors clear by a wide margin; the input the oracle sees is the FP32-rounded
-one, so only the arithmetic differs.
+one, so only the arithmetic differs.  The same bound with u = 2^-11 holds
+for FP16.
 """
 import numpy as np
 import pytest
@@ -25,9 +28,12 @@ from gpu_util import gpu_apply, rel_err_cols, round_input
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-U_BF16 = 2.0 ** -8
-TOL = 8 * U_BF16
+U = {fk.FE_KS_BF16: 2.0 ** -8, fk.FE_KS_F16: 2.0 ** -11}
+TOL16 = {prec: 8 * u for prec, u in U.items()}
+TOL = TOL16[fk.FE_KS_BF16]
 BF = fk.FE_KS_BF16
+TC = [fk.FE_KS_BF16, fk.FE_KS_F16]
+NAME = {fk.FE_KS_BF16: "BF16", fk.FE_KS_F16: "FP16"}
 
 SMALL = {
     "C1": CONFIGS["C1"],
@@ -46,14 +52,29 @@ def cases():
     return {k: (wl, HostProblem(wl), Problem(wl), trial_vectors(wl)) for k, wl in SMALL.items()}
 
 
+@pytest.mark.parametrize("prec", TC)
 @pytest.mark.parametrize("key", list(SMALL))
-def test_bf16_matches_oracle(cases, key):
+def test_bf16_matches_oracle(cases, key, prec):
     wl, hp, P, X = cases[key]
-    Xin = round_input(X, BF)
-    Y = gpu_apply(hp, Xin, BF)
+    Xin = round_input(X, prec)
+    Y = gpu_apply(hp, Xin, prec)
     err = rel_err_cols(Y, P.apply(Xin))
-    print(f"{key}: BF16 tensor-core rel err {err:.3e} (tolerance {TOL:.3e})")
-    assert err <= TOL, err
+    print(f"{key}: {NAME[prec]} tensor-core rel err {err:.3e} (tolerance {TOL16[prec]:.3e})")
+    assert err <= TOL16[prec], err
+
+
+@pytest.mark.parametrize("scale", [1e-7, 1e5])
+def test_f16_tile_scaling_range(cases, scale):
+    """FP16 has a narrow range: blocks scaled far below (1e-7: subnormal in FP16)
+    and above (1e5: the intermediates would overflow 65504) keep the relative
+    error of the unscaled block, because every cell tile is scaled by a power
+    of two before the 16-bit rounding and unscaled after."""
+    wl, hp, P, X = cases["C4v"]
+    Xin = round_input(X * scale, fk.FE_KS_F16)
+    Y = gpu_apply(hp, Xin, fk.FE_KS_F16)
+    assert np.all(np.isfinite(Y))
+    err = rel_err_cols(Y, P.apply(Xin))
+    assert err <= TOL16[fk.FE_KS_F16], (scale, err)
 
 
 def test_bf16_scaled_matches_oracle(cases):
@@ -65,15 +86,16 @@ def test_bf16_scaled_matches_oracle(cases):
     assert err <= TOL, err
 
 
+@pytest.mark.parametrize("prec", TC)
 @pytest.mark.parametrize("p", range(1, 9))
-def test_bf16_every_degree(p):
+def test_bf16_every_degree(p, prec):
     wl = Workload(f"deg{p}", L=4.0 + p, n=2 if p > 2 else 3, p=p, nq=p + 1, n_v=11, jitter=0.08, gga=True,
                   seed=900 + p)
     hp = HostProblem(wl)
     P = Problem(wl)
-    X = round_input(trial_vectors(wl), BF)
-    err = rel_err_cols(gpu_apply(hp, X, BF), P.apply(X))
-    assert err <= TOL, (p, err)
+    X = round_input(trial_vectors(wl), prec)
+    err = rel_err_cols(gpu_apply(hp, X, prec), P.apply(X))
+    assert err <= TOL16[prec], (p, err)
 
 
 def test_bf16_term_subsets(cases):
@@ -104,19 +126,21 @@ def test_bf16_close_to_fp32_kernel(cases):
     assert rel_err_cols(Yb, Yf) > 1e-6   # really a different (lower-precision) arithmetic
 
 
+@pytest.mark.parametrize("prec", TC)
 @pytest.mark.parametrize("key", ["C2s", "C3s", "C4s"])
-def test_bf16_nonlocal_term_isolated(cases, key):
+def test_bf16_nonlocal_term_isolated(cases, key, prec):
     """The nonlocal term alone: for random trial blocks it is 1e-5..1e-4 of |H X|,
     below the BF16 tolerance of the whole result, so it is checked on its own as
     Y(all terms) - Y(local terms).  Both runs use the same kernel on the same
     input, so the local parts agree to FP32 rounding of the accumulators
     (u_32 |H X| / |NL| <= 6e-8 x 1e5 = 6e-3 relative to the term), and the
-    nonlocal part carries the BF16 rounding of F and Q (2 u)."""
+    nonlocal part carries the 16-bit rounding of F and Q (2 u)."""
     wl, hp, P, X = cases[key]
-    X = round_input(X, BF)
-    Y_all = gpu_apply(hp, X, BF)
-    Y_loc = gpu_apply(hp, X, BF, terms=fk.TERM_ALL & ~fk.TERM_NL)
+    X = round_input(X, prec)
+    Y_all = gpu_apply(hp, X, prec)
+    Y_loc = gpu_apply(hp, X, prec, terms=fk.TERM_ALL & ~fk.TERM_NL)
     ref = P.apply(X) - Problem(wl, with_atoms=False).apply(X)
     err = rel_err_cols(Y_all - Y_loc, ref)
-    print(f"{key}: BF16 nonlocal term rel err {err:.3e}")
-    assert err <= TOL, err
+    print(f"{key}: {NAME[prec]} nonlocal term rel err {err:.3e}")
+    # FP32 rounding of the accumulators relative to the term (6e-3, see above) bounds FP16 too
+    assert err <= max(TOL16[prec], 1e-2), err

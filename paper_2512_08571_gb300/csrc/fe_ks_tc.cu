@@ -1,9 +1,13 @@
 // Tensor-core cell kernel (FE_KS_BF16, FE_KS_F16): the 1D contractions of
 // Algorithm 2 as warp-level BF16 or FP16 MMAs with FP32 accumulation, the
 // quadrature-point step, nonlocal expansion and scatter in FP32.  FP16 has 8x
-// the precision of BF16 but a narrow range, so each gathered cell tile is
-// scaled by a power of two (its largest entry to at most 1/16) and the result
-// unscaled at the scatter: the chain is linear and the scaling exact.
+// the precision of BF16 but a narrow range, so every column of a gathered cell
+// tile is scaled by its own power of two (its largest entry to below 1/16;
+// the re/im columns of a complex vector share one) and the result unscaled at
+// the scatter: each column is an independent right-hand side of a linear
+// chain, and the scaling is exact.  One scale per tile would not do: columns
+// of very different size (converged and unconverged vectors inside the
+// eigensolver) would push the small ones into FP16's subnormals.
 //
 // Paper: Algorithm 2 (cell-level evaluation, eq. ggaReal / eq. ggaCmplx) called
 // from Algorithm 1 (extraction Q C P X, F Delta T3, assembly Q^T).  The
@@ -87,8 +91,10 @@ struct Geom {
   // fragment-order writes and the row reads are both conflict-free)
   static constexpr int SST = 12;
   static constexpr int OFF_STAGE = (OFF_DOFS + N3 * 4 + 15) / 16 * 16;
-  static constexpr int OFF_RED = OFF_STAGE + N3 * SST * 4;   // per-warp maxima (FP16 tile scaling)
-  static constexpr int BYTES = OFF_RED + 32 * 4;
+  // FP16 column scaling: per-warp column maxima [NW][8] and the unscale factors [8]
+  static constexpr int OFF_RED = OFF_STAGE + N3 * SST * 4;
+  static constexpr int OFF_UNSCALE = OFF_RED + 8 * 8 * 4;
+  static constexpr int BYTES = OFF_UNSCALE + 8 * 4;
   // Two resident CTAs per SM.  (Three fit the shared memory at n = 9, but the
   // register cap that lets 21 warps share the SM's four 16K-register files
   // (80 per thread) made the kernel spill and measured no faster.)
@@ -250,19 +256,24 @@ __device__ __forceinline__ float tile_scale(float mx) {
 // columns [c0, c0 + 8): one node per thread, two 16-byte reductions per node
 // when the rows are 16-byte aligned.  Colour-exclusive launches: no other
 // cell of the launch touches the same DoF rows.
-template <int N, bool CPLX>
+template <int N, bool CPLX, bool F16>
 __device__ __forceinline__ void scatter_stage(const TcParams& p, const float* stage, const int* sd, int c0, bool vecy,
-                                              float unscale) {
+                                              const float* unscale) {
   using Gm = Geom<N, CPLX>;
   const bool fullv = vecy && c0 + 8 <= p.ncols;
+  float4 ua = make_float4(1.f, 1.f, 1.f, 1.f), ub = ua;   // per-column unscale (FP16)
+  if constexpr (F16) {
+    ua = *reinterpret_cast<const float4*>(unscale);
+    ub = *reinterpret_cast<const float4*>(unscale + 4);
+  }
   for (int node = threadIdx.x; node < Gm::N3; node += Gm::NT) {
     const float* sp = stage + node * Gm::SST;
     float4 a = *reinterpret_cast<const float4*>(sp);
     float4 b = *reinterpret_cast<const float4*>(sp + 4);
     const int d = sd[node];
-    const float sc = (p.dscale ? p.alpha * __ldg(p.dscale + d) : p.alpha) * unscale;
-    a.x *= sc, a.y *= sc, a.z *= sc, a.w *= sc;
-    b.x *= sc, b.y *= sc, b.z *= sc, b.w *= sc;
+    const float sc = p.dscale ? p.alpha * __ldg(p.dscale + d) : p.alpha;
+    a.x *= sc * ua.x, a.y *= sc * ua.y, a.z *= sc * ua.z, a.w *= sc * ua.w;
+    b.x *= sc * ub.x, b.y *= sc * ub.y, b.z *= sc * ub.z, b.w *= sc * ub.w;
     float* yp = p.Y + (int64_t)d * p.ld + c0;
     if (fullv) {
       atomicAdd(reinterpret_cast<float4*>(yp), a);
@@ -329,12 +340,12 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_
     const int pe = p.cell_pair_ptr ? p.cell_pair_ptr[e + 1] : 0;
     __syncthreads();
     int prev0 = -1;          // columns of the staged result still to be assembled
-    float prev_unscale = 1.f;
+    float* unscale = reinterpret_cast<float*>(smem + Gm::OFF_UNSCALE);   // of the staged tile
     for (int t = blockIdx.y; t < ntiles; t += gridDim.y) {
       const int col0 = 8 * t;
       const int col = col0 + gq;
       const bool full = vec && col0 + 8 <= p.ncols;
-      float tscale = 1.f;   // power-of-two scale of this tile (FP16 only)
+      float tscale = 1.f;   // power-of-two scale of this thread's column gq (FP16 only)
       // (1) extraction Q C P X (Algorithm 1): rows of X -> 16-bit array 2 [node][8]
       //     (array 2 is not read by the previous tile's last sweep); the loads
       //     are in flight while the previous tile's staged result is assembled
@@ -363,38 +374,66 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_
             if (p.dscale) sc[r] = __ldg(p.dscale + d);
           }
         }
-        if (prev0 >= 0) scatter_stage<N, CPLX>(p, stage, sd, prev0, vecy, prev_unscale);
-        // FP16: scale the tile by a power of two so that its largest entry is
-        // below 1/16 (exact; undone at the scatter)
+        if (prev0 >= 0) scatter_stage<N, CPLX, F16>(p, stage, sd, prev0, vecy, unscale);
+        // FP16: scale every column of the tile by a power of two so that its
+        // largest entry is below 1/16 (exact; undone at the scatter)
+        float cs[8] = {1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f};
         if constexpr (F16) {
-          float mx = 0.f;
+          float cm[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
           for (int r = 0; r < GPT; ++r) {
-            const float s = sc[r];
-            mx = fmaxf(mx, fmaxf(fmaxf(fabsf(xa[r].x * s), fabsf(xa[r].y * s)), fmaxf(fabsf(xa[r].z * s), fabsf(xa[r].w * s))));
-            mx = fmaxf(mx, fmaxf(fmaxf(fabsf(xb[r].x * s), fabsf(xb[r].y * s)), fmaxf(fabsf(xb[r].z * s), fabsf(xb[r].w * s))));
+            const float s = fabsf(sc[r]);
+            cm[0] = fmaxf(cm[0], fabsf(xa[r].x) * s), cm[1] = fmaxf(cm[1], fabsf(xa[r].y) * s);
+            cm[2] = fmaxf(cm[2], fabsf(xa[r].z) * s), cm[3] = fmaxf(cm[3], fabsf(xa[r].w) * s);
+            cm[4] = fmaxf(cm[4], fabsf(xb[r].x) * s), cm[5] = fmaxf(cm[5], fabsf(xb[r].y) * s);
+            cm[6] = fmaxf(cm[6], fabsf(xb[r].z) * s), cm[7] = fmaxf(cm[7], fabsf(xb[r].w) * s);
           }
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-          float* wmax = reinterpret_cast<float*>(smem + Gm::OFF_RED);
-          if (lane == 0) wmax[warp] = mx;
-          __syncthreads();
-          mx = 0.f;
+          for (int c = 0; c < 8; ++c)
 #pragma unroll
-          for (int w = 0; w < NW; ++w) mx = fmaxf(mx, wmax[w]);
-          tscale = tile_scale(mx);
+            for (int o = 16; o > 0; o >>= 1) cm[c] = fmaxf(cm[c], __shfl_xor_sync(0xffffffffu, cm[c], o));
+          float* wmax = reinterpret_cast<float*>(smem + Gm::OFF_RED);   // [NW][8]
+          if (lane < 8) {
+            float v = cm[0];
+#pragma unroll
+            for (int c = 1; c < 8; ++c) v = lane == c ? cm[c] : v;
+            wmax[warp * 8 + lane] = v;
+          }
+          __syncthreads();
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            float m = 0.f;
+            for (int w = 0; w < NW; ++w) m = fmaxf(m, wmax[w * 8 + c]);
+            cm[c] = m;
+          }
+          // a complex vector's re/im columns share one scale (the -iK term mixes them)
+          if constexpr (CPLX)
+#pragma unroll
+            for (int c = 0; c < 8; c += 2) cm[c] = cm[c + 1] = fmaxf(cm[c], cm[c + 1]);
+#pragma unroll
+          for (int c = 0; c < 8; ++c) cs[c] = tile_scale(cm[c]);
+          float m = cm[0];
+#pragma unroll
+          for (int c = 1; c < 8; ++c) m = gq == c ? cm[c] : m;
+          tscale = tile_scale(m);
+          if (tid < 8) {   // the scatter of this tile undoes the scale (read after later barriers)
+            float v = cs[0];
+#pragma unroll
+            for (int c = 1; c < 8; ++c) v = tid == c ? cs[c] : v;
+            unscale[tid] = 1.f / v;   // exact: a power of two
+          }
         }
 #pragma unroll
         for (int r = 0; r < GPT; ++r) {
           const int node = tid + r * NT;
           if (node < N3) {
             const int i = node % N, j = (node / N) % N, k = node / (N * N);
-            const float s = sc[r] * tscale;
+            const float s = sc[r];
             uint4 u;
-            u.x = pack16<F16>(xa[r].x * s, xa[r].y * s);
-            u.y = pack16<F16>(xa[r].z * s, xa[r].w * s);
-            u.z = pack16<F16>(xb[r].x * s, xb[r].y * s);
-            u.w = pack16<F16>(xb[r].z * s, xb[r].w * s);
+            u.x = pack16<F16>(xa[r].x * s * cs[0], xa[r].y * s * cs[1]);
+            u.y = pack16<F16>(xa[r].z * s * cs[2], xa[r].w * s * cs[3]);
+            u.z = pack16<F16>(xb[r].x * s * cs[4], xb[r].y * s * cs[5]);
+            u.w = pack16<F16>(xb[r].z * s * cs[6], xb[r].w * s * cs[7]);
             *reinterpret_cast<uint4*>(smem + 2 * Gm::ARR + 16 * (i + SY * j + SZ * k)) = u;
           }
         }
@@ -705,9 +744,8 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_
       }
       __syncthreads();   // the stage is complete; array 2 is free for the next extraction
       prev0 = col0;
-      prev_unscale = 1.f / tscale;   // exact: a power of two
     }
-    if (prev0 >= 0) scatter_stage<N, CPLX>(p, stage, sd, prev0, vecy, prev_unscale);
+    if (prev0 >= 0) scatter_stage<N, CPLX, F16>(p, stage, sd, prev0, vecy, unscale);
   }
 }
 

@@ -144,3 +144,16 @@ def test_bf16_nonlocal_term_isolated(cases, key, prec):
     print(f"{key}: {NAME[prec]} nonlocal term rel err {err:.3e}")
     # FP32 rounding of the accumulators relative to the term (6e-3, see above) bounds FP16 too
     assert err <= max(TOL16[prec], 1e-2), err
+
+
+@pytest.mark.parametrize("prec", TC)
+def test_columns_of_very_different_size(cases, prec):
+    """Columns of one tile spanning 15 orders of magnitude (as converged and
+    unconverged vectors do inside the eigensolver) keep each column's relative
+    error: FP16 scales every column by its own power of two."""
+    wl, hp, P, X = cases["C4v"]
+    Xs = X * (10.0 ** -np.arange(X.shape[1]))[None, :]
+    Xin = round_input(Xs, prec)
+    Y = gpu_apply(hp, Xin, prec)
+    err = rel_err_cols(Y, P.apply(Xin))
+    assert err <= TOL16[prec], err

@@ -133,6 +133,27 @@ cudaError_t launch_proj_emu(const Ctx& c, const ProjParams<double>& prm, const f
 
 constexpr int kPairThreads = 256;
 
+// 16 bytes of shared memory into 16 / sizeof(TF) values (one vector load)
+__device__ __forceinline__ void ld16(const float* p, float* o) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  o[0] = v.x, o[1] = v.y, o[2] = v.z, o[3] = v.w;
+}
+__device__ __forceinline__ void ld16(const double* p, double* o) {
+  const double2 v = *reinterpret_cast<const double2*>(p);
+  o[0] = v.x, o[1] = v.y;
+}
+__device__ __forceinline__ void ld16(const ff2* p, ff2* o) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  o[0] = ff_make(v.x, v.y), o[1] = ff_make(v.z, v.w);
+}
+
+// Elements per node of the transposed F block: MAXP projectors (x2 complex),
+// rounded up to a whole number of 16-byte chunks.
+template <typename TF, bool CPLX, int MAXP>
+__host__ __device__ constexpr int pair_fstride() {
+  return ((MAXP * (CPLX ? 2 : 1) * (int)sizeof(TF) + 15) / 16) * 16 / (int)sizeof(TF);
+}
+
 // P[pr][b][col] = sum_node conj(F[pr][b][node]) x(d(node), col), x scaled by
 // D^{-1/2} when dscale is given.  Each thread owns V = 16 / sizeof(TS)
 // adjacent columns (one 16-byte load per row; for complex data the re/im
@@ -146,18 +167,24 @@ fe_proj_pair_kernel(const TS* __restrict__ Xg, int64_t ld, int ncols, const int*
   using N = ProjNum<T>;
   constexpr int V = 16 / (int)sizeof(TS);
   constexpr int CW = CPLX ? 2 : 1;
+  constexpr int PB = pair_fstride<TF, CPLX, MAXP>();   // F row of one node: [b][re, im], padded to 16 B
   extern __shared__ __align__(16) unsigned char smp[];
-  TF* Fs = reinterpret_cast<TF*>(smp);
+  TF* Fs = reinterpret_cast<TF*>(smp);   // [node][PB]
   const int nf = n_proj * np3 * CW;
-  int* ds = reinterpret_cast<int*>(smp + (size_t)nf * sizeof(TF));
-  T* red = reinterpret_cast<T*>(smp + (((size_t)nf * sizeof(TF) + (size_t)np3 * sizeof(int) + 15) & ~(size_t)15));
+  int* ds = reinterpret_cast<int*>(smp + (size_t)np3 * PB * sizeof(TF));
+  T* red = reinterpret_cast<T*>(smp + (((size_t)np3 * PB * sizeof(TF) + (size_t)np3 * sizeof(int) + 15) & ~(size_t)15));
   const int pr = blockIdx.x;
   const int rs = kPairThreads / cg;
   const int lc = threadIdx.x % cg, sl = threadIdx.x / cg;
   const int c0 = (blockIdx.y * cg + lc) * V;
   const bool vec = (ld % V == 0) && (((uintptr_t)Xg & 15) == 0) && c0 + V <= ncols;
   const TF* Fp = Fg + (int64_t)pr * nf;
-  for (int i = threadIdx.x; i < nf; i += kPairThreads) Fs[i] = Fp[i];
+  // transpose F[b][node][re,im] -> Fs[node][b][re,im] (global reads coalesced over node)
+  for (int i = threadIdx.x; i < nf; i += kPairThreads) {
+    const int b = i / (np3 * CW), rem = i - b * np3 * CW;
+    const int node = rem / CW, ri = rem - node * CW;
+    Fs[node * PB + b * CW + ri] = Fp[i];
+  }
   const int cell = pair_cell[pr];
   for (int i = threadIdx.x; i < np3; i += kPairThreads) ds[i] = cell_dofs[(int64_t)cell * np3 + i];
   __syncthreads();
@@ -201,16 +228,20 @@ fe_proj_pair_kernel(const TS* __restrict__ Xg, int64_t ld, int ncols, const int*
       T x[V];
 #pragma unroll
       for (int v = 0; v < V; ++v) x[v] = N::in(xs[u][v]);
+      // the node's F row with 16-byte shared loads (all lanes read the same row)
+      TF frow[PB];
+#pragma unroll
+      for (int q = 0; q < PB; q += 16 / (int)sizeof(TF)) ld16(Fs + node * PB + q, frow + q);
 #pragma unroll
       for (int b = 0; b < MAXP; ++b) {
         if (b < n_proj) {
           if constexpr (!CPLX) {
-            const T f = N::in(Fs[b * np3 + node]);
+            const T f = N::in(frow[b]);
 #pragma unroll
             for (int v = 0; v < V; ++v) acc[b][v] = fma(f, x[v], acc[b][v]);
           } else {
             // conj(F) x : re = fr xr + fi xi ; im = fr xi - fi xr  (re, im adjacent in the thread)
-            const T fr = N::in(Fs[2 * (b * np3 + node)]), fi = N::in(Fs[2 * (b * np3 + node) + 1]);
+            const T fr = N::in(frow[2 * b]), fi = N::in(frow[2 * b + 1]);
 #pragma unroll
             for (int v = 0; v < V; v += 2) {
               acc[b][v] = fma(fr, x[v], fma(fi, x[v + 1], acc[b][v]));
@@ -278,8 +309,8 @@ static cudaError_t launch_pair_p(const ProjParams<TS>& prm, const TF* F, int n_a
   constexpr int V = 16 / (int)sizeof(TS);
   const int cg = pair_groups<TS>(prm.ncols);
   const int rs = kPairThreads / cg;
-  const size_t nf = (size_t)prm.n_proj * prm.np3 * (CPLX ? 2 : 1);
-  const size_t head = (nf * sizeof(TF) + (size_t)prm.np3 * sizeof(int) + 15) & ~(size_t)15;
+  constexpr int PB = pair_fstride<TF, CPLX, MAXP>();
+  const size_t head = ((size_t)prm.np3 * PB * sizeof(TF) + (size_t)prm.np3 * sizeof(int) + 15) & ~(size_t)15;
   const size_t smem = head + (rs > 1 ? (size_t)rs * prm.n_proj * cg * V * sizeof(T) : 0);
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   cudaError_t err = cudaFuncSetAttribute(fe_proj_pair_kernel<T, TS, TF, CPLX, MAXP>,

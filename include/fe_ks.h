@@ -193,20 +193,50 @@ fe_ks_status fe_ks_cheb_filter(fe_ks_ctx* ctx, double* X, const double* ritz, in
                                int residual_precision, void* work, size_t work_bytes);
 
 /*
- * Tile configuration of the fused cell kernel: 0..2 run one CTA per (cell,
- * column tile) with 3 tile widths; 3..4 run one CTA per cell walking all
- * column tiles with the next tile's rows of X staged by cp.async and a
- * reduction-based scatter.  0 is the default, FE_KS_N_CONFIGS choices.  fe_ks_tune times every
- * configuration with fe_ks_apply on the caller's X and Y (reps timed calls
- * each, after one untimed call), keeps the fastest for this context and
- * precision, and reports the milliseconds per call (-1 for a configuration
- * that cannot launch, e.g. shared memory too large) and the choice.
- * fe_ks_set_config sets it directly.  Y is overwritten.
+ * Tile configuration of the fused cell kernel (FE_KS_F64, FE_KS_F32,
+ * FE_KS_F64E; the tensor-core kernel has one):
+ *   0..2  one CTA per (cell, column tile), 3 tile widths;
+ *   3..4  one CTA per cell walking all column tiles, the next tile's rows of X
+ *         staged by cp.async, reduction-based scatter;
+ *   5..6  as 3..4 with 2 or 4 adjacent columns per thread.
+ * 0 is the default; there are FE_KS_N_CONFIGS choices.
+ *
+ * fe_ks_tune times every configuration with fe_ks_apply on the caller's X and
+ * Y (reps timed calls each, after one untimed call). It keeps the fastest for
+ * this context and precision, and reports the milliseconds per call (-1 for
+ * a configuration that cannot launch, e.g. shared memory too large) and the
+ * choice. Y is overwritten. The choice also goes into an in-process cache
+ * keyed by (degree, n_q, precision, columns, complex, device compute
+ * capability and SM count). Other contexts of the same shape whose
+ * configuration was not set explicitly use it at their next application.
+ *
+ * fe_ks_set_config sets the configuration directly (and explicitly);
+ * fe_ks_get_config reads the current one.
  */
 #define FE_KS_N_CONFIGS 7
 fe_ks_status fe_ks_tune(fe_ks_ctx* ctx, const void* X, void* Y, int64_t n_v, int precision, int reps,
                         double* ms_per_config, int* best);
 fe_ks_status fe_ks_set_config(fe_ks_ctx* ctx, int precision, int config);
+fe_ks_status fe_ks_get_config(const fe_ks_ctx* ctx, int precision, int* config);
+
+/*
+ * Host-only: the greedy cell colouring the scatter-add relies on, i.e. the
+ * assembly Q^T of Algorithm 1 done one colour at a time.
+ *
+ * Cells are taken in index order; each gets the smallest colour (0..63) not
+ * used by a cell that shares one of its DoFs, so the cells of one colour
+ * touch disjoint rows of Y and one launch per colour needs no atomics and is
+ * deterministic.
+ *
+ * cell_dofs is [n_cells][np3] (host, caller-owned). colour receives [n_cells]
+ * (host, caller-owned) and n_colours the colour count.
+ *
+ * Errors: FE_KS_ERR_MESH for an entry outside [0, n_dofs);
+ * FE_KS_ERR_UNSUPPORTED when more than 64 colours would be needed;
+ * FE_KS_ERR_ARG for NULL pointers or sizes out of range. Needs no GPU.
+ */
+fe_ks_status fe_ks_colour_cells(int64_t n_cells, int32_t np3, int64_t n_dofs, const int32_t* cell_dofs,
+                                int32_t* colour, int32_t* n_colours);
 
 /*
  * Batched application: Y_s = H_s X_s for up to 16 independent systems of

@@ -9,6 +9,12 @@
 #include <thread>
 #include <type_traits>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include <nvtx3/nvToolsExt.h>
+
 #include "fe_ks_internal.h"
 
 namespace feks {
@@ -19,6 +25,9 @@ cudaError_t launch_local_deg(const Ctx&, const LocalParams<T, TS>&, cudaStream_t
 static thread_local std::string g_last_error;
 
 void set_error(const std::string& msg) { g_last_error = msg; }
+
+NvtxRange::NvtxRange(const char* name) { nvtxRangePushA(name); }
+NvtxRange::~NvtxRange() { nvtxRangePop(); }
 
 fe_ks_status fail(fe_ks_status code, const std::string& msg) {
   g_last_error = msg;
@@ -108,6 +117,81 @@ static fe_ks_status upload(Ctx* c, T** dst, const T* src, size_t count) {
   if (src && cudaMemcpy(p, src, count * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
     return fail(FE_KS_ERR_CUDA, "cudaMemcpy failed during setup");
   return FE_KS_OK;
+}
+
+// Greedy colouring of the cells so that no two cells of a colour share a DoF
+// (their scatter-adds then never touch the same row of Y).  Cells are taken
+// in index order; each gets the smallest colour not used by a cell sharing
+// one of its DoFs.  Returns the number of colours, or -1 if more than 64 are
+// needed.  cell_dofs entries must lie in [0, m).
+int greedy_colouring(int64_t E, int np3, int64_t m, const int* cell_dofs, int* colour) {
+  for (int64_t e = 0; e < E; ++e) colour[e] = -1;
+  std::vector<int> cnt(m + 1, 0);
+  for (int64_t i = 0; i < E * np3; ++i) cnt[cell_dofs[i] + 1]++;
+  for (int64_t i = 0; i < m; ++i) cnt[i + 1] += cnt[i];
+  std::vector<int> d2c(cnt[m]);
+  std::vector<int> fillp(cnt.begin(), cnt.end() - 1);
+  for (int64_t e = 0; e < E; ++e)
+    for (int n = 0; n < np3; ++n) d2c[fillp[cell_dofs[e * np3 + n]]++] = (int)e;
+  int n_colours = 0;
+  for (int64_t e = 0; e < E; ++e) {
+    uint64_t used = 0;
+    for (int n = 0; n < np3; ++n) {
+      const int d = cell_dofs[e * np3 + n];
+      for (int t = cnt[d]; t < cnt[d + 1]; ++t) {
+        const int o = colour[d2c[t]];
+        if (o >= 0 && o < 64) used |= (1ull << o);
+      }
+    }
+    int col = 0;
+    while (col < 64 && (used >> col) & 1ull) ++col;
+    if (col >= 64) return -1;
+    colour[e] = col;
+    n_colours = std::max(n_colours, col + 1);
+  }
+  return n_colours;
+}
+
+// ---- tile-configuration cache: fe_ks_tune's choice per (degree, n_q,
+// precision, columns, complex, device), reused by contexts of the same shape
+// whose configuration was not set explicitly.
+namespace {
+struct TuneKey {
+  int p, nq, prec, cplx, sm_major, sm_minor, sms;
+  int64_t ncols;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(p, nq, prec, cplx, sm_major, sm_minor, sms, ncols) <
+           std::tie(o.p, o.nq, o.prec, o.cplx, o.sm_major, o.sm_minor, o.sms, o.ncols);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune_cache;
+
+TuneKey tune_key(const Ctx& c, int prec, int64_t ncols) {
+  TuneKey k{c.p, c.nq, prec, c.cplx, 0, 0, 0, ncols};
+  cudaDeviceGetAttribute(&k.sm_major, cudaDevAttrComputeCapabilityMajor, c.device);
+  cudaDeviceGetAttribute(&k.sm_minor, cudaDevAttrComputeCapabilityMinor, c.device);
+  cudaDeviceGetAttribute(&k.sms, cudaDevAttrMultiProcessorCount, c.device);
+  return k;
+}
+}  // namespace
+
+int* config_slot(Ctx& c, int prec) {
+  return prec == FE_KS_F64 ? &c.cfg64 : prec == FE_KS_F32 ? &c.cfg32 : prec == FE_KS_F64E ? &c.cfgE : nullptr;
+}
+
+void tune_cache_store(const Ctx& c, int prec, int64_t ncols, int cfg) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[tune_key(c, prec, ncols)] = cfg;
+}
+
+// the cached configuration for this shape, unless the context's was set explicitly
+void tune_cache_apply(Ctx& c, int prec, int64_t ncols) {
+  int* slot = config_slot(c, prec);
+  if (!slot || c.cfg_explicit[prec]) return;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune_cache.find(tune_key(c, prec, ncols));
+  if (it != g_tune_cache.end()) *slot = it->second;
 }
 
 static fe_ks_status check_geometry_args(const fe_ks_problem* prob) {
@@ -293,33 +377,10 @@ fe_ks_status fe_ks_setup(const fe_ks_problem* prob, int terms_mask, int64_t n_v_
 
   // ---- greedy colouring: cells of one colour share no DoF (race-free scatter-add)
   std::vector<int> colour(E, -1);
-  int n_colours = 0;
-  {
-    std::vector<int> cnt(m + 1, 0);
-    for (int64_t i = 0; i < E * np3; ++i) cnt[prob->cell_dofs[i] + 1]++;
-    for (int64_t i = 0; i < m; ++i) cnt[i + 1] += cnt[i];
-    std::vector<int> d2c(cnt[m]);
-    std::vector<int> fillp(cnt.begin(), cnt.end() - 1);
-    for (int64_t e = 0; e < E; ++e)
-      for (int n = 0; n < np3; ++n) d2c[fillp[prob->cell_dofs[e * np3 + n]]++] = (int)e;
-    for (int64_t e = 0; e < E; ++e) {
-      uint64_t used = 0;
-      for (int n = 0; n < np3; ++n) {
-        const int d = prob->cell_dofs[e * np3 + n];
-        for (int t = cnt[d]; t < cnt[d + 1]; ++t) {
-          const int o = colour[d2c[t]];
-          if (o >= 0 && o < 64) used |= (1ull << o);
-        }
-      }
-      int col = 0;
-      while (col < 64 && (used >> col) & 1ull) ++col;
-      if (col >= 64) {
-        delete h;
-        return fail(FE_KS_ERR_UNSUPPORTED, "mesh needs more than 64 colours");
-      }
-      colour[e] = col;
-      n_colours = std::max(n_colours, col + 1);
-    }
+  const int n_colours = feks::greedy_colouring(E, np3, m, prob->cell_dofs, colour.data());
+  if (n_colours < 0) {
+    delete h;
+    return fail(FE_KS_ERR_UNSUPPORTED, "mesh needs more than 64 colours");
   }
   std::vector<int> colour_cells;
   c->colour_ptr.assign(n_colours + 1, 0);
@@ -547,6 +608,7 @@ namespace feks {
 
 template <typename T>
 fe_ks_status apply_core(Ctx& c, const T* X, T* Y, int64_t ncols, bool scaled, T alpha, bool zero_fill, int tc) {
+  NvtxRange range(tc == 2 ? "fe_ks_apply f16" : tc == 1 ? "fe_ks_apply bf16" : sizeof(T) == 8 ? "fe_ks_apply f64" : "fe_ks_apply f32");
   OpData<T>& od = *reinterpret_cast<OpData<T>*>(sizeof(T) == 8 ? (void*)&c.f64 : (void*)&c.f32);
   const T* hcoef = reinterpret_cast<const T*>(sizeof(T) == 8 ? (const void*)c.h64 : (const void*)c.h32);
   cudaStream_t s = c.stream;
@@ -635,6 +697,7 @@ template fe_ks_status apply_core<float>(Ctx&, const float*, float*, int64_t, boo
 // the pair arithmetic).
 fe_ks_status apply_core_emu(Ctx& c, const double* X, double* Y, int64_t ncols, bool scaled, double alpha,
                             bool zero_fill) {
+  NvtxRange range("fe_ks_apply f64e");
   cudaStream_t s = c.stream;
   const size_t bytes = (size_t)c.m * ncols * sizeof(double);
   std::array<cudaEvent_t, 4> ev{};
@@ -723,6 +786,7 @@ static fe_ks_status apply_impl(fe_ks_ctx* ctx, const void* Xv, void* Yv, int64_t
   const char* xb = static_cast<const char*>(Xv);
   const char* yb = static_cast<const char*>(Yv);
   if (xb < yb + bytes && yb < xb + bytes) return fail(FE_KS_ERR_ARG, "X and Y overlap");
+  tune_cache_apply(c, std::is_same<T, ff2>::value ? FE_KS_F64E : (sizeof(T) == 8 ? FE_KS_F64 : FE_KS_F32), ncols);
   if constexpr (std::is_same<T, ff2>::value)
     return apply_core_emu(c, static_cast<const double*>(Xv), static_cast<double*>(Yv), ncols, scaled, 1.0, true);
   else
@@ -745,14 +809,32 @@ fe_ks_status fe_ks_apply(fe_ks_ctx* ctx, const void* X, void* Y, int64_t n_v, in
 fe_ks_status fe_ks_set_config(fe_ks_ctx* ctx, int precision, int config) {
   if (!ctx) return fail(FE_KS_ERR_ARG, "ctx is NULL");
   if (config < 0 || config >= kLocalConfigs) return fail(FE_KS_ERR_ARG, "config out of range");
-  if (precision == FE_KS_F64)
-    ctx->c.cfg64 = config;
-  else if (precision == FE_KS_F32)
-    ctx->c.cfg32 = config;
-  else if (precision == FE_KS_F64E)
-    ctx->c.cfgE = config;
-  else
-    return fail(FE_KS_ERR_UNSUPPORTED, "unknown precision");
+  int* slot = config_slot(ctx->c, precision);
+  if (!slot) return fail(FE_KS_ERR_UNSUPPORTED, "precision without tile configurations");
+  *slot = config;
+  ctx->c.cfg_explicit[precision] = true;
+  return FE_KS_OK;
+}
+
+fe_ks_status fe_ks_get_config(const fe_ks_ctx* ctx, int precision, int* config) {
+  if (!ctx || !config) return fail(FE_KS_ERR_ARG, "NULL argument");
+  const int* slot = config_slot(const_cast<Ctx&>(ctx->c), precision);
+  if (!slot) return fail(FE_KS_ERR_UNSUPPORTED, "precision without tile configurations");
+  *config = *slot;
+  return FE_KS_OK;
+}
+
+fe_ks_status fe_ks_colour_cells(int64_t n_cells, int32_t np3, int64_t n_dofs, const int32_t* cell_dofs,
+                                int32_t* colour, int32_t* n_colours) {
+  set_error("");
+  if (!cell_dofs || !colour || !n_colours) return fail(FE_KS_ERR_ARG, "NULL argument");
+  if (n_cells < 1 || n_cells > (int64_t)INT32_MAX || np3 < 1 || n_dofs < 1 || n_dofs > (int64_t)INT32_MAX)
+    return fail(FE_KS_ERR_ARG, "sizes out of range");
+  for (int64_t i = 0; i < n_cells * np3; ++i)
+    if (cell_dofs[i] < 0 || cell_dofs[i] >= n_dofs) return fail(FE_KS_ERR_MESH, "cell_dofs entry out of range");
+  const int nc = greedy_colouring(n_cells, np3, n_dofs, cell_dofs, colour);
+  if (nc < 0) return fail(FE_KS_ERR_UNSUPPORTED, "mesh needs more than 64 colours");
+  *n_colours = nc;
   return FE_KS_OK;
 }
 
@@ -772,6 +854,9 @@ fe_ks_status fe_ks_tune(fe_ks_ctx* ctx, const void* X, void* Y, int64_t n_v, int
                                        : single;
   const int n_conf = (precision == FE_KS_BF16 || precision == FE_KS_F16) ? 1 : kLocalConfigs;
   const int keep = cfg;
+  bool* expl = (precision <= FE_KS_F64E) ? &c.cfg_explicit[precision] : nullptr;
+  const bool keep_expl = expl ? *expl : false;
+  if (expl) *expl = true;   // the loop below sets the configuration itself
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -804,9 +889,14 @@ fe_ks_status fe_ks_tune(fe_ks_ctx* ctx, const void* X, void* Y, int64_t n_v, int
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (expl) *expl = keep_expl;
   cfg = best_cfg;
   if (best) *best = best_cfg;
   if (best_ms == 1e300) return fail(FE_KS_ERR_CUDA, "no tile configuration could be launched");
+  if (precision != FE_KS_BF16 && precision != FE_KS_F16) {
+    c.cfg_explicit[precision] = true;
+    tune_cache_store(c, precision, n_v * (c.cplx ? 2 : 1), best_cfg);
+  }
   return FE_KS_OK;
 }
 

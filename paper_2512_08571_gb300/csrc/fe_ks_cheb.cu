@@ -107,6 +107,7 @@ static fe_ks_status recurrence_apply(Ctx& c, const T* RY, T* RX, int64_t ncols, 
 template <typename T>
 static fe_ks_status cheb_impl(Ctx& c, double* X, const double* lam, int64_t n_v, int degree, double lmin, double lT,
                               double lmax, char* work, bool rec_emu, bool res_emu, int rec_tc = 0) {
+  NvtxRange range("fe_ks_cheb_filter");
   cudaStream_t s = c.stream;
   const int cw = c.cplx ? 2 : 1;
   const int64_t ncols = n_v * cw;

@@ -104,6 +104,7 @@ struct Ctx {
   int p = 0, nq = 0, np = 0, np3 = 0, nq3 = 0;
   int cplx = 0, terms = 0, gga = 0, ncoef = 0;
   int cfg64 = 0, cfg32 = 0, cfgE = 0;   // tile configuration of the fused kernel per precision
+  bool cfg_explicit[3] = {false, false, false};   // set by fe_ks_set_config / fe_ks_tune (F64, F32, F64E)
   int64_t E = 0, m = 0, n_v_max = 0;
   int n_atoms = 0, n_proj = 0;
   int64_t n_pairs = 0;
@@ -143,9 +144,18 @@ struct Ctx {
   std::vector<std::array<int, 3>> ev_launches;
 };
 
+// NVTX range for the duration of a scope (host side; visible in timeline tools)
+struct NvtxRange {
+  explicit NvtxRange(const char* name);
+  ~NvtxRange();
+};
+
 // error reporting (thread-local message)
 void set_error(const std::string& msg);
 fe_ks_status fail(fe_ks_status code, const std::string& msg);
+
+// greedy cell colouring (fe_ks_api.cu); returns the colour count or -1 (> 64)
+int greedy_colouring(int64_t E, int np3, int64_t m, const int* cell_dofs, int* colour);
 
 // host 1D tables (fe_ks_tables.cpp)
 void gauss_legendre(int n, double* x, double* w);

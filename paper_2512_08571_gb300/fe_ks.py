@@ -66,6 +66,8 @@ def _load():
                                                 vp, vp, vp]
     lib.fe_ks_tune.argtypes = [vp, vp, vp, i64, ctypes.c_int, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_int)]
     lib.fe_ks_set_config.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    lib.fe_ks_get_config.argtypes = [vp, ctypes.c_int, P(ctypes.c_int)]
+    lib.fe_ks_colour_cells.argtypes = [i64, i32, i64, vp, vp, P(i32)]
     lib.fe_ks_batch_create.argtypes = [P(vp), ctypes.c_int, P(i64), P(ctypes.c_int), P(vp)]
     lib.fe_ks_batch_configure.argtypes = [vp, P(ctypes.c_int), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_double, ctypes.c_int]
@@ -169,6 +171,23 @@ def fe_ks_tune(ctx, X, Y, n_v, precision, reps=3):
 
 def fe_ks_set_config(ctx, precision, config):
     _check(_lib.fe_ks_set_config(ctx, precision, config))
+
+
+def fe_ks_get_config(ctx, precision):
+    out = ctypes.c_int()
+    _check(_lib.fe_ks_get_config(ctx, precision, ctypes.byref(out)))
+    return out.value
+
+
+def fe_ks_colour_cells(cell_dofs, n_dofs):
+    """Host colouring of the cells ([n_cells][np3] int32 numpy array): (colour per cell, count)."""
+    import numpy as np
+    cd = np.ascontiguousarray(cell_dofs, dtype=np.int32)
+    colour = np.empty(cd.shape[0], dtype=np.int32)
+    n = ctypes.c_int32()
+    _check(_lib.fe_ks_colour_cells(cd.shape[0], cd.shape[1], n_dofs, cd.ctypes.data, colour.ctypes.data,
+                                   ctypes.byref(n)))
+    return colour, n.value
 
 
 def fe_ks_batch_create(ctxs, n_v, precision):

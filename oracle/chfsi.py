@@ -1,4 +1,5 @@
-"""Residual-based Chebyshev filtered subspace iteration (R-ChFSI), standard form.
+"""Residual-based Chebyshev filtered subspace iteration (R-ChFSI): standard form
+and, at the end of this file, the generalised form with the consistent mass.
 
 TEST INFRASTRUCTURE (oracle): see ``oracle/__init__.py``.
 
@@ -111,6 +112,66 @@ def rchfsi(apply_Hs, X0, degree, n_iter, lanczos_steps=10, seed=0, tol=None):
         X = X / np.linalg.norm(X, axis=0)[None, :]
         R = apply_Hs(X) - X * lam[None, :]
         res = np.linalg.norm(R, axis=0)
+        if tol is not None and np.max(res) < tol:
+            break
+    return lam, X, res
+
+
+# ------------------------------------------------------------------------
+# Generalised form: H X = M X Lam with the consistent mass M (eq. FEeigen),
+# Algorithm 4 as printed: the residual uses M, the recurrence applies H D^{-1}
+# (D the GLL-lumped approximation of M), and the result maps back with D^{-1}.
+
+def filter_rchfsi_ghep(apply_H, apply_M, Dinv, X, lam, degree, lmin, lT, lmax):
+    """Algorithm 4 for the GHEP.  apply_H / apply_M: V -> H V / M V; Dinv: the
+    diagonal of D^{-1} [m]; lam = current Ritz values [n_v]."""
+    e = (lmax - lT) / 2.0
+    c = (lmax + lT) / 2.0
+    sigma = e / (lmin - c)
+    sigma1 = sigma
+    gamma = 2.0 / sigma1
+    Y = apply_H(X) - apply_M(X) * lam[None, :]
+    RX = np.zeros_like(Y)
+    RY = (sigma1 / e) * Y
+    LX = np.ones_like(lam)
+    LY = (sigma1 / e) * (lam - c)
+    for _ in range(2, degree + 1):
+        sigma2 = 1.0 / (gamma - sigma)
+        RX = (2.0 * sigma2 / e) * (apply_H(Dinv[:, None] * RY) - c * RY + Y * LY[None, :]) - sigma * sigma2 * RX
+        LX = (2.0 * sigma2 / e) * LY * (lam - c) - sigma * sigma2 * LX
+        RX, RY = RY, RX
+        LX, LY = LY, LX
+        sigma = sigma2
+    return Dinv[:, None] * RY + X * LY[None, :]
+
+
+def rayleigh_ritz_ghep(apply_H, apply_M, Y):
+    """Algorithm 3's Rayleigh-Ritz step: (Y^H H Y) E = (Y^H M Y) E Lam; X = Y E."""
+    import scipy.linalg as sl
+    S = Y.conj().T @ apply_M(Y)
+    Hp = Y.conj().T @ apply_H(Y)
+    Hp = 0.5 * (Hp + Hp.conj().T)
+    S = 0.5 * (S + S.conj().T)
+    lam, E = sl.eigh(Hp, S)
+    return lam, Y @ E
+
+
+def rchfsi_ghep(apply_H, apply_M, Dinv, X0, degree, n_iter, lanczos_steps=10, seed=0, tol=None):
+    """Algorithm 3 for the GHEP.  The spectral upper bound is the Lanczos bound
+    of D^{-1/2} H D^{-1/2} (the operator the recurrence effectively runs on).
+    Returns (Ritz values, vectors, norms of H x - lam M x)."""
+    rng = np.random.default_rng(seed)
+    s = np.sqrt(Dinv)
+    lmax = lanczos_upper_bound(lambda V: s[:, None] * apply_H(s[:, None] * V),
+                               rng.standard_normal(X0.shape[0]).astype(X0.dtype), lanczos_steps)
+    X, _ = np.linalg.qr(X0)
+    lam, X = rayleigh_ritz_ghep(apply_H, apply_M, X)
+    res = None
+    for _ in range(n_iter):
+        Yf = filter_rchfsi_ghep(apply_H, apply_M, Dinv, X, lam, degree, lam[0], lam[-1], lmax)
+        lam, X = rayleigh_ritz_ghep(apply_H, apply_M, Yf)
+        R = apply_H(X) - apply_M(X) * lam[None, :]
+        res = np.linalg.norm(R, axis=0) / np.linalg.norm(X, axis=0)
         if tol is not None and np.max(res) < tol:
             break
     return lam, X, res

@@ -64,3 +64,57 @@ def test_flop_model_leading_order():
     per = flops.mf_real_total(n, n, 1, 1, 0) / n ** 4
     assert 11.5 < per < 12.6
     assert flops.cm_real_total(n, 1, 1, 0) == 2 * n ** 6
+
+
+# ---- generalised form (consistent mass M, D^{-1} in the recurrence)
+
+@pytest.mark.parametrize("degree", [3, 9])
+def test_ghep_filter_with_diagonal_mass_is_the_scaled_standard_filter(degree):
+    """With M = D (diagonal), Algorithm 4 for the GHEP is the standard-form filter
+    on Hs = D^{-1/2} H D^{-1/2} in the variables D^{1/2} X:
+        D^{1/2} filter_ghep(H, D, D^{-1}; X) = filter_std(Hs; D^{1/2} X).
+    A D^{-1} in the wrong place (residual, recurrence or final step) breaks it."""
+    H, _, _ = _sym(50, 30 + degree)
+    rng = np.random.default_rng(5)
+    D = rng.uniform(0.5, 2.0, 50)
+    X = rng.standard_normal((50, 5))
+    lam = np.sort(rng.uniform(-3.0, 1.0, 5))
+    lmin, lT, lmax = -3.5, 1.0, 45.0
+    got = chfsi.filter_rchfsi_ghep(lambda V: H @ V, lambda V: D[:, None] * V, 1.0 / D, X, lam, degree, lmin, lT, lmax)
+    s = 1.0 / np.sqrt(D)
+    Hs = s[:, None] * H * s[None, :]
+    want = chfsi.filter_rchfsi(lambda V: Hs @ V, np.sqrt(D)[:, None] * X, lam, degree, lmin, lT, lmax)
+    assert np.max(np.abs(np.sqrt(D)[:, None] * got - want)) < 1e-10 * np.max(np.abs(want))
+
+
+def test_ghep_filter_keeps_exact_eigenpairs():
+    """Exact generalised eigenpairs make the residual H X - M X Lam vanish, so the
+    filter returns each column scaled (by Lam_Y), whatever D is."""
+    import scipy.linalg as sl
+    rng = np.random.default_rng(7)
+    H, _, _ = _sym(40, 11)
+    B = rng.standard_normal((40, 40))
+    M = B @ B.T / 40 + np.eye(40)
+    ev, V = sl.eigh(H, M)
+    X, lam = V[:, :4], ev[:4]
+    D = np.diag(M).copy()
+    out = chfsi.filter_rchfsi_ghep(lambda Z: H @ Z, lambda Z: M @ Z, 1.0 / D, X, lam, 8, ev[0] - 0.5, ev[6], ev[-1] * 1.01)
+    for j in range(4):
+        a = out[:, j] @ X[:, j] / (X[:, j] @ X[:, j])
+        assert np.linalg.norm(out[:, j] - a * X[:, j]) < 1e-9 * np.linalg.norm(out[:, j])
+
+
+def test_rchfsi_ghep_converges_to_generalised_eigenvalues_of_fe_operator():
+    """The lowest eigenvalues of H u = eps M u (eq. FEeigen) with the consistent
+    mass, against scipy's dense generalised eigensolver."""
+    import scipy.linalg as sl
+    wl = Workload("eigg", L=9.0, n=3, p=3, nq=4, n_v=12, jitter=0.1, gga=True, n_atoms=2, seed=22)
+    P = Problem(wl)
+    H = P.assemble("H").toarray()
+    M = P.assemble("M").toarray()
+    want = sl.eigh(0.5 * (H + H.T), 0.5 * (M + M.T), eigvals_only=True)[:8]
+    X0 = trial_vectors(wl, n_v=12)
+    lam, X, res = chfsi.rchfsi_ghep(lambda V: H @ V, lambda V: M @ V, 1.0 / P.lumped_mass(), X0, degree=12,
+                                    n_iter=60, tol=1e-10)
+    np.testing.assert_allclose(lam[:8], want, atol=1e-8)
+    assert np.max(res[:8]) < 1e-7

@@ -193,6 +193,25 @@ fe_ks_status fe_ks_cheb_filter(fe_ks_ctx* ctx, double* X, const double* ritz, in
                                int residual_precision, void* work, size_t work_bytes);
 
 /*
+ * The same filter for the generalised problem H X = M X Lam with the
+ * consistent mass M (eq. FEeigen; Algorithm 4 as printed: the residual
+ * H X - M X Lam uses M, the recurrence applies H D^{-1} with D the GLL-lumped
+ * mass, and the result is D^{-1} R_Y + X Lam_Y).  `mass` is a context of the
+ * same mesh whose application is M: set up with V_loc = 1 - |k|^2/2 at every
+ * quadrature point, no GGA field, no atoms, terms = FE_KS_TERM_L (then
+ * (V_loc + |k|^2/2) det J w = det J w and the L term is exactly M).  X holds
+ * the generalised eigenvector block (not the D^{1/2}-scaled one).  Internally
+ * the recurrence runs on D^{-1/2} H D^{-1/2} in the variables D^{-1/2} R,
+ * which is the printed recurrence exactly; the residual's applications of H
+ * and M take `residual_precision`.  Same workspace, precisions, stream order
+ * and errors as fe_ks_cheb_filter; FE_KS_ERR_ARG if `mass` does not match the
+ * operator (DoF count, real/complex, device, n_v_max).
+ */
+fe_ks_status fe_ks_cheb_filter_ghep(fe_ks_ctx* ctx, fe_ks_ctx* mass, double* X, const double* ritz, int64_t n_v,
+                                    int degree, double lam_min, double lam_T, double lam_max, int precision,
+                                    int residual_precision, void* work, size_t work_bytes);
+
+/*
  * Tile configuration of the fused cell kernel (FE_KS_F64, FE_KS_F32,
  * FE_KS_F64E; the tensor-core kernel has one):
  *   0..2  one CTA per (cell, column tile), 3 tile widths;

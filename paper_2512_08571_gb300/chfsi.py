@@ -2,7 +2,9 @@
 
 The caller's side of ``fe_ks_cheb_filter``: the outer subspace iteration of
 Algorithm 3 in the standard form Hs = D^{-1/2} H D^{-1/2} (D the GLL-lumped
-mass).  Each iteration filters the block with the library's residual-based
+mass), or, given a context whose application is the consistent mass M, for
+the generalised problem H X = M X Lam (``fe_ks_cheb_filter_ghep``; the
+Rayleigh-Ritz step then solves (Y^H H Y) E = (Y^H M Y) E Lam).  Each iteration filters the block with the library's residual-based
 Chebyshev filter and then performs the Rayleigh-Ritz step in FP64
 (orthonormalisation and the projected N_v x N_v eigenproblem as dense library
 GEMM / QR / symmetric eigensolver calls on the device).  Spectral bounds: the
@@ -20,11 +22,14 @@ class RChFSI:
     exact: the FP64-accurate path used for the filter's residual, Lanczos, Rayleigh-Ritz and
     residual norms (FE_KS_F64 native, or FE_KS_F64E pairs of floats);
     gemm_pairs: Rayleigh-Ritz Gram matrices and rotation in pairs of floats (FP64-accurate,
-    FP32 pipe) instead of FP64 cuBLAS; gemm_emulated: cuBLAS's FP64 emulation."""
+    FP32 pipe) instead of FP64 cuBLAS; gemm_emulated: cuBLAS's FP64 emulation;
+    mass_ctx: a context whose application is M (``problem.mass_problem`` set up with
+    FE_KS_TERM_L) to solve the generalised problem instead of the standard form."""
 
     def __init__(self, ctx, m, n_v, cplx, degree=20, precision=fk.FE_KS_F32, lanczos_steps=10,
-                 exact=fk.FE_KS_F64, gemm_emulated=False, gemm_pairs=False):
+                 exact=fk.FE_KS_F64, gemm_emulated=False, gemm_pairs=False, mass_ctx=None):
         self.ctx, self.m, self.n_v, self.cplx = ctx, m, n_v, cplx
+        self.mass = mass_ctx
         self.degree, self.precision, self.lanczos_steps = degree, precision, lanczos_steps
         self.exact = exact
         self.gemm_emulated = gemm_emulated and not cplx
@@ -44,6 +49,24 @@ class RChFSI:
         V = V.contiguous()
         out = torch.empty(V.shape, dtype=V.dtype, device=V.device) if out is None else out
         fk.fe_ks_apply_scaled(self.ctx, V, out, V.shape[1], self.exact)
+        return out
+
+    def apply_op(self, V, out=None):
+        """The operator of the Rayleigh-Ritz step: Hs (standard form) or H (generalised)."""
+        if self.mass is None:
+            return self.apply_scaled(V, out)
+        V = V.contiguous()
+        out = torch.empty(V.shape, dtype=V.dtype, device=V.device) if out is None else out
+        fk.fe_ks_apply(self.ctx, V, out, V.shape[1], self.exact)
+        return out
+
+    def apply_metric(self, V):
+        """The metric of the Rayleigh-Ritz step: I (standard form) or M (generalised)."""
+        if self.mass is None:
+            return V
+        V = V.contiguous()
+        out = torch.empty(V.shape, dtype=V.dtype, device=V.device)
+        fk.fe_ks_apply(self.mass, V, out, V.shape[1], self.exact)
         return out
 
     def lanczos_upper_bound(self, seed=0):
@@ -82,13 +105,13 @@ class RChFSI:
         A Householder QR is used instead when S is too ill-conditioned for Cholesky.
         """
         Y = Y.contiguous()
-        S = self._gram(Y, Y)
+        S = self._gram(Y, self.apply_metric(Y))
         S = 0.5 * (S + S.conj().T)
         L, info = torch.linalg.cholesky_ex(S)
         d = torch.real(torch.diagonal(L)) if int(info.item()) == 0 else None
         if d is None or float(d.min()) <= 1e-6 * float(d.max()):
             return self._rayleigh_ritz_qr(Y)
-        HY = self.apply_scaled(Y, self.tmp)
+        HY = self.apply_op(Y, self.tmp)
         A = self._gram(Y, HY)
         T1 = torch.linalg.solve_triangular(L, A, upper=False)
         B = torch.linalg.solve_triangular(L, T1.conj().T, upper=False).conj().T
@@ -114,22 +137,39 @@ class RChFSI:
     def _rayleigh_ritz_qr(self, Y):
         Q, _ = torch.linalg.qr(Y)
         Q = Q.contiguous()          # QR returns column-major factors; the C ABI is row-major
-        HQ = self.apply_scaled(Q, self.tmp)
+        HQ = self.apply_op(Q, self.tmp)
         A = Q.conj().T @ HQ
         A = 0.5 * (A + A.conj().T)
+        if self.mass is not None:   # generalised: Cholesky of the (well-conditioned) Q^H M Q
+            S = Q.conj().T @ self.apply_metric(Q)
+            L = torch.linalg.cholesky(0.5 * (S + S.conj().T))
+            B = torch.linalg.solve_triangular(L, torch.linalg.solve_triangular(L, A, upper=False).conj().T,
+                                              upper=False).conj().T
+            lam, W = torch.linalg.eigh(0.5 * (B + B.conj().T))
+            W = torch.linalg.solve_triangular(L.conj().T, W, upper=True)
+            return lam.to(torch.float64).contiguous(), (Q @ W).contiguous()
         lam, W = torch.linalg.eigh(A)
         return lam.to(torch.float64).contiguous(), (Q @ W).contiguous()
 
     def residual_norms(self, X, lam):
-        R = self.apply_scaled(X, self.tmp) - X * lam[None, :].to(X.dtype)
-        return torch.linalg.vector_norm(R, dim=0)
+        """|Hs x - lam x| (standard form), |H x - lam M x| / |x| (generalised)."""
+        if self.mass is None:
+            R = self.apply_scaled(X, self.tmp) - X * lam[None, :].to(X.dtype)
+            return torch.linalg.vector_norm(R, dim=0)
+        R = self.apply_op(X, self.tmp) - self.apply_metric(X) * lam[None, :].to(X.dtype)
+        return torch.linalg.vector_norm(R, dim=0) / torch.linalg.vector_norm(X, dim=0)
 
     def filter(self, X, lam):
         lmin, lT = float(lam[0].item()), float(lam[-1].item())
         if not lmin < lT < self.lmax:
             raise RuntimeError("spectral bounds out of order")
-        fk.fe_ks_cheb_filter(self.ctx, X, lam, self.n_v, self.degree, lmin, lT, self.lmax, self.precision,
-                             self.work_view, self.work_bytes, residual_precision=self.exact)
+        if self.mass is None:
+            fk.fe_ks_cheb_filter(self.ctx, X, lam, self.n_v, self.degree, lmin, lT, self.lmax, self.precision,
+                                 self.work_view, self.work_bytes, residual_precision=self.exact)
+        else:
+            fk.fe_ks_cheb_filter_ghep(self.ctx, self.mass, X, lam, self.n_v, self.degree, lmin, lT, self.lmax,
+                                      self.precision, self.work_view, self.work_bytes,
+                                      residual_precision=self.exact)
         return X
 
     def run(self, X0, n_iter, tol=None, n_check=None):

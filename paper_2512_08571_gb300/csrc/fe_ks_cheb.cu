@@ -12,6 +12,12 @@
 // The recurrence term (Hs - c) R_Y + Y Lam_Y is formed by first writing
 // a(-c R_Y + Y Lam_Y) - b R_X in place into R_X (elementwise kernel) and then
 // letting the fused cell kernel scatter-add a * Hs R_Y on top (alpha = a).
+//
+// Generalised form (H X = M X Lam with the consistent mass M, Algorithm 4 as
+// printed): with R~ = D^{-1/2} R the recurrence (H D^{-1} - c) R_Y + Y Lam_Y
+// is the standard-form one above on R~, so only the two ends change:
+//   Y~  = D^{-1/2} (H X - M X Lam)              (FP64: residual with M)
+//   X   <- D^{-1/2} R~_Y + X Lam_Y               (D^{-1} R_Y + X Lam_Y)
 #include <cmath>
 #include <type_traits>
 
@@ -33,6 +39,19 @@ __global__ void k_residual_init(double* __restrict__ Y, const double* __restrict
     const int64_t col = i % ncols;
     Y[i] = -X[i] * lam[col / cw];
   }
+}
+
+// Y <- -Y * lam[col / cw]
+__global__ void k_scale_neg_lam(double* __restrict__ Y, const double* __restrict__ lam, int64_t n, int64_t ncols,
+                                int cw) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    Y[i] = -Y[i] * lam[(i % ncols) / cw];
+}
+
+// Y <- D^{-1/2} Y (row scaling)
+__global__ void k_row_scale(double* __restrict__ Y, const double* __restrict__ ds, int64_t n, int64_t ncols) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    Y[i] *= ds[i / ncols];
 }
 
 // Ylow = Y, R_Y = s1e * Y (in the precision of the recurrence)
@@ -71,13 +90,14 @@ __global__ void k_lambda(double* LX, double* LY, const double* lam, double a, do
   }
 }
 
-// X <- R_Y + X Lam_Y
+// X <- D^{-1/2} R_Y + X Lam_Y (ds == nullptr: X <- R_Y + X Lam_Y)
 template <typename T>
-__global__ void k_cheb_final(double* __restrict__ X, const T* __restrict__ RY, const double* __restrict__ LY, int64_t n,
-                             int64_t ncols, int cw) {
+__global__ void k_cheb_final(double* __restrict__ X, const T* __restrict__ RY, const double* __restrict__ LY,
+                             const double* __restrict__ ds, int64_t n, int64_t ncols, int cw) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t col = i % ncols;
-    X[i] = (double)RY[i] + X[i] * LY[col / cw];
+    const double r = ds ? (double)RY[i] * ds[i / ncols] : (double)RY[i];
+    X[i] = r + X[i] * LY[col / cw];
   }
 }
 
@@ -106,8 +126,9 @@ static fe_ks_status recurrence_apply(Ctx& c, const T* RY, T* RX, int64_t ncols, 
 
 template <typename T>
 static fe_ks_status cheb_impl(Ctx& c, double* X, const double* lam, int64_t n_v, int degree, double lmin, double lT,
-                              double lmax, char* work, bool rec_emu, bool res_emu, int rec_tc = 0) {
-  NvtxRange range("fe_ks_cheb_filter");
+                              double lmax, char* work, bool rec_emu, bool res_emu, int rec_tc = 0,
+                              Ctx* mass = nullptr) {
+  NvtxRange range(mass ? "fe_ks_cheb_filter_ghep" : "fe_ks_cheb_filter");
   cudaStream_t s = c.stream;
   const int cw = c.cplx ? 2 : 1;
   const int64_t ncols = n_v * cw;
@@ -131,11 +152,28 @@ static fe_ks_status cheb_impl(Ctx& c, double* X, const double* lam, int64_t n_v,
   const double sigma1 = sigma, gamma = 2.0 / sigma1;
   const int nb = ew_blocks(n);
 
-  // Y = Hs X - X Lam (FP64)
-  k_residual_init<<<nb, kEwThreads, 0, s>>>(Y, X, lam, n, ncols, cw);
-  fe_ks_status st = res_emu ? apply_core_emu(c, X, Y, ncols, true, 1.0, false)
-                            : apply_core<double>(c, X, Y, ncols, true, 1.0, false);
-  if (st != FE_KS_OK) return st;
+  fe_ks_status st = FE_KS_OK;
+  if (!mass) {
+    // Y = Hs X - X Lam (FP64)
+    k_residual_init<<<nb, kEwThreads, 0, s>>>(Y, X, lam, n, ncols, cw);
+    st = res_emu ? apply_core_emu(c, X, Y, ncols, true, 1.0, false)
+                 : apply_core<double>(c, X, Y, ncols, true, 1.0, false);
+    if (st != FE_KS_OK) return st;
+  } else {
+    // Y~ = D^{-1/2} (H X - M X Lam) (FP64): M X on the mass context's stream
+    // order (same stream), then -Lam, then + H X, then the row scaling
+    cudaStream_t ms = mass->stream;
+    mass->stream = s;
+    st = res_emu ? apply_core_emu(*mass, X, Y, ncols, false, 1.0, true)
+                 : apply_core<double>(*mass, X, Y, ncols, false, 1.0, true);
+    mass->stream = ms;
+    if (st != FE_KS_OK) return st;
+    k_scale_neg_lam<<<nb, kEwThreads, 0, s>>>(Y, lam, n, ncols, cw);
+    st = res_emu ? apply_core_emu(c, X, Y, ncols, false, 1.0, false)
+                 : apply_core<double>(c, X, Y, ncols, false, 1.0, false);
+    if (st != FE_KS_OK) return st;
+    k_row_scale<<<nb, kEwThreads, 0, s>>>(Y, c.f64.dscale, n, ncols);
+  }
   k_residual_split<T><<<nb, kEwThreads, 0, s>>>(Y, low ? Yl : nullptr, RY, sigma1 / e, n);
   k_lambda<<<(int)((n_v + 255) / 256), 256, 0, s>>>(LX, LY, lam, sigma1 / e, cc, 0.0, 1, (int)n_v);
   for (int k = 2; k <= degree; ++k) {
@@ -149,7 +187,7 @@ static fe_ks_status cheb_impl(Ctx& c, double* X, const double* lam, int64_t n_v,
     std::swap(LX, LY);
     sigma = sigma2;
   }
-  k_cheb_final<T><<<nb, kEwThreads, 0, s>>>(X, RY, LY, n, ncols, cw);
+  k_cheb_final<T><<<nb, kEwThreads, 0, s>>>(X, RY, LY, mass ? c.f64.dscale : nullptr, n, ncols, cw);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return fail(FE_KS_ERR_CUDA, std::string("filter kernels: ") + cudaGetErrorString(err));
   return FE_KS_OK;
@@ -170,13 +208,15 @@ fe_ks_status fe_ks_cheb_filter_workspace(const fe_ks_ctx* ctx, int64_t n_v, int 
   return FE_KS_OK;
 }
 
-fe_ks_status fe_ks_cheb_filter(fe_ks_ctx* ctx, double* X, const double* ritz, int64_t n_v, int degree, double lam_min,
-                               double lam_T, double lam_max, int precision, int residual_precision, void* work,
-                               size_t work_bytes) {
+static fe_ks_status filter_entry(fe_ks_ctx* ctx, fe_ks_ctx* mass, double* X, const double* ritz, int64_t n_v,
+                                 int degree, double lam_min, double lam_T, double lam_max, int precision,
+                                 int residual_precision, void* work, size_t work_bytes) {
   set_error("");
   if (!ctx || !X || !ritz || !work) return fail(FE_KS_ERR_ARG, "NULL argument");
   Ctx& c = ctx->c;
   if (n_v < 1 || n_v > c.n_v_max) return fail(FE_KS_ERR_ARG, "n_v must be in 1..n_v_max");
+  if (mass && (mass->c.m != c.m || mass->c.cplx != c.cplx || mass->c.n_v_max < n_v || mass->c.device != c.device))
+    return fail(FE_KS_ERR_ARG, "the mass context must share the operator's DoFs, type, device and n_v range");
   if (degree < 1) return fail(FE_KS_ERR_ARG, "degree must be >= 1");
   if (!(lam_min < lam_T && lam_T < lam_max)) return fail(FE_KS_ERR_ARG, "need lam_min < lam_T < lam_max");
   if (precision != FE_KS_F64 && precision != FE_KS_F32 && precision != FE_KS_F64E && precision != FE_KS_BF16 &&
@@ -189,10 +229,27 @@ fe_ks_status fe_ks_cheb_filter(fe_ks_ctx* ctx, double* X, const double* ritz, in
   if (((uintptr_t)work & 255) || ((uintptr_t)X & 7)) return fail(FE_KS_ERR_ARG, "misaligned X or workspace");
   char* w = static_cast<char*>(work);
   const bool res_emu = residual_precision == FE_KS_F64E;
+  Ctx* mc = mass ? &mass->c : nullptr;
   if (precision == FE_KS_F32 || precision == FE_KS_BF16 || precision == FE_KS_F16)
     return cheb_impl<float>(c, X, ritz, n_v, degree, lam_min, lam_T, lam_max, w, false, res_emu,
-                            precision == FE_KS_BF16 ? 1 : precision == FE_KS_F16 ? 2 : 0);
-  return cheb_impl<double>(c, X, ritz, n_v, degree, lam_min, lam_T, lam_max, w, precision == FE_KS_F64E, res_emu);
+                            precision == FE_KS_BF16 ? 1 : precision == FE_KS_F16 ? 2 : 0, mc);
+  return cheb_impl<double>(c, X, ritz, n_v, degree, lam_min, lam_T, lam_max, w, precision == FE_KS_F64E, res_emu, 0,
+                           mc);
+}
+
+fe_ks_status fe_ks_cheb_filter(fe_ks_ctx* ctx, double* X, const double* ritz, int64_t n_v, int degree, double lam_min,
+                               double lam_T, double lam_max, int precision, int residual_precision, void* work,
+                               size_t work_bytes) {
+  return filter_entry(ctx, nullptr, X, ritz, n_v, degree, lam_min, lam_T, lam_max, precision, residual_precision,
+                      work, work_bytes);
+}
+
+fe_ks_status fe_ks_cheb_filter_ghep(fe_ks_ctx* ctx, fe_ks_ctx* mass, double* X, const double* ritz, int64_t n_v,
+                                    int degree, double lam_min, double lam_T, double lam_max, int precision,
+                                    int residual_precision, void* work, size_t work_bytes) {
+  if (!mass) return fail(FE_KS_ERR_ARG, "mass context is NULL");
+  return filter_entry(ctx, mass, X, ritz, n_v, degree, lam_min, lam_T, lam_max, precision, residual_precision, work,
+                      work_bytes);
 }
 
 }  // extern "C"

@@ -62,6 +62,8 @@ def _load():
     lib.fe_ks_cheb_filter_workspace.argtypes = [vp, i64, ctypes.c_int, P(ctypes.c_size_t)]
     lib.fe_ks_cheb_filter.argtypes = [vp, vp, vp, i64, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_int, ctypes.c_int, vp, ctypes.c_size_t]
+    lib.fe_ks_cheb_filter_ghep.argtypes = [vp, vp, vp, vp, i64, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_int, ctypes.c_int, vp, ctypes.c_size_t]
     lib.fe_ks_nonlocal_apply_static.argtypes = [vp, vp, i64, i32, i32, i64, vp, i32, i32, vp, vp, vp, i64,
                                                 vp, vp, vp]
     lib.fe_ks_tune.argtypes = [vp, vp, vp, i64, ctypes.c_int, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_int)]
@@ -148,6 +150,12 @@ def fe_ks_cheb_filter(ctx, X, ritz, n_v, degree, lam_min, lam_T, lam_max, precis
                       residual_precision=FE_KS_F64):
     _check(_lib.fe_ks_cheb_filter(ctx, _ptr(X), _ptr(ritz), n_v, degree, lam_min, lam_T, lam_max, precision,
                                   residual_precision, _ptr(work), work_bytes))
+
+
+def fe_ks_cheb_filter_ghep(ctx, mass, X, ritz, n_v, degree, lam_min, lam_T, lam_max, precision, work, work_bytes,
+                           residual_precision=FE_KS_F64):
+    _check(_lib.fe_ks_cheb_filter_ghep(ctx, mass, _ptr(X), _ptr(ritz), n_v, degree, lam_min, lam_T, lam_max,
+                                       precision, residual_precision, _ptr(work), work_bytes))
 
 
 def fe_ks_nonlocal_apply_static(X, Y, n_v, is_complex, degree, n_dofs, cell_dofs, n_atoms, n_proj,

@@ -61,3 +61,12 @@ class HostProblem:
     @property
     def complex(self):
         return bool(self.wl.complex) or bool(np.any(self.kpt != 0))
+
+
+def mass_problem(wl):
+    """The same mesh as ``HostProblem(wl)`` with V_loc = 1 - |k|^2/2, no GGA field and
+    no atoms: set up with terms = FE_KS_TERM_L its application is the consistent
+    mass matrix M (the L term's (V_loc + |k|^2/2) det J w becomes det J w)."""
+    import numpy as _np
+    k2 = 0.5 * float(_np.dot(_np.asarray(wl.kpt, dtype=float), _np.asarray(wl.kpt, dtype=float)))
+    return HostProblem(wl, with_atoms=False, vloc=lambda xq: _np.full(xq.shape[:-1], 1.0 - k2), vgga=None)

@@ -409,6 +409,24 @@ def run_filter(args, wl, ctx, hp, X64):
     conv["speedup"] = conv["f64"]["ms"] / conv["mixed"]["ms"]
     conv["speedup_bf16"] = conv["f64"]["ms"] / conv["mixed_bf16"]["ms"]
     conv["speedup_f16"] = conv["f64"]["ms"] / conv["mixed_f16"]["ms"]
+    # the generalised problem H X = M X Lam with the consistent mass (Algorithm 4 as printed)
+    from paper_2512_08571_gb300.problem import mass_problem
+    hpm = mass_problem(wls)
+    cm = fk.fe_ks_setup(hpm.struct, fk.TERM_L, wls.n_v, stream.cuda_stream)
+    gh, glams = {}, {}
+    for name, prec, exact, pg in (("f64", fk.FE_KS_F64, fk.FE_KS_F64, False),
+                                  ("mixed", fk.FE_KS_F32, fk.FE_KS_F64E, True),
+                                  ("mixed_bf16", fk.FE_KS_BF16, fk.FE_KS_F64E, True)):
+        sol = RChFSI(cs, hps.m, wls.n_v, False, degree=20, precision=prec, exact=exact, gemm_pairs=pg, mass_ctx=cm)
+        t, (lam_c, _, res, its) = ev_ms(lambda: sol.run(Xs0.clone(), n_iter=160, tol=1e-9, n_check=n_chk))
+        glams[name] = lam_c.cpu().numpy()
+        gh[name] = {"iterations": its, "ms": t, "max_residual": float(res[:n_chk].max())}
+        del sol
+    gh["max_eig_diff_mixed_vs_f64_Ha"] = float(np.max(np.abs(glams["mixed"][:n_chk] - glams["f64"][:n_chk])))
+    gh["max_eig_diff_bf16_vs_f64_Ha"] = float(np.max(np.abs(glams["mixed_bf16"][:n_chk] - glams["f64"][:n_chk])))
+    gh["speedup"] = gh["f64"]["ms"] / gh["mixed"]["ms"]
+    conv["generalised_consistent_mass"] = gh
+    fk.fe_ks_destroy(cm)
     out["converged_6cubed"] = conv
     fk.fe_ks_destroy(cs)
     return out

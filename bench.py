@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the six-system batched launch")
     ap.add_argument("--no-filter", action="store_true", help="skip the R-ChFSI filter timing")
+    ap.add_argument("--no-all-electron", action="store_true", help="skip the all-electron-like workload")
     ap.add_argument("--precision", choices=["both", "f64", "f32", "f64e", "bf16", "f16"], default="both",
                     help="f32 / f64e / bf16 / f16 alone time only that application (for profiling)")
     ap.add_argument("--config", type=int, default=None,
@@ -432,6 +433,53 @@ def run_filter(args, wl, ctx, hp, X64):
     return out
 
 
+# -------------------------------------------------- all-electron-like workload
+def run_all_electron(args):
+    """The all-electron-like workload (Bloch-periodic complex operator, no projectors,
+    24^3 cells, p = 8, N_v = 64): one application per precision, tuned, timed with
+    CUDA events (inputs larger than L2).  Returns a dict for the JSON line."""
+    import numpy as np
+    import torch
+    from paper_2512_08571_gb300 import fe_ks as fk
+    from paper_2512_08571_gb300.problem import HostProblem
+    from synth import CONFIGS
+    wl = CONFIGS["AE"]
+    if args.cells:
+        wl = wl.scaled(n=args.cells)
+    stream = torch.cuda.current_stream()
+    hp = HostProblem(wl)
+    ctx = fk.fe_ks_setup(hp.struct, fk.TERM_ALL, wl.n_v, stream.cuda_stream)
+    X64 = torch.empty((hp.m, wl.n_v), dtype=torch.complex128, device="cuda")
+    fill_trial(wl, wl.n_v, X64, np.complex128)
+    units = hp.m * wl.n_v
+    out = {"workload": f"AE: L={wl.L:g} bohr, {wl.n}^3 cells, p={wl.p}, n_q={wl.nq}, N_v={wl.n_v}, complex "
+                       f"(k = {tuple(round(float(k), 4) for k in wl.kpt)} bohr^-1), GGA, no projectors",
+           "n_dofs": hp.m, "unit": UNIT}
+    for prec, name in ((fk.FE_KS_F64, "f64"), (fk.FE_KS_F64E, "f64_pairs_of_fp32"), (fk.FE_KS_F32, "f32"),
+                       (fk.FE_KS_BF16, "bf16_tensor_core"), (fk.FE_KS_F16, "f16_tensor_core")):
+        X = X64 if prec in (fk.FE_KS_F64, fk.FE_KS_F64E) else X64.to(torch.complex64)
+        Y = torch.empty_like(X)
+        fk.fe_ks_tune(ctx, X, Y, wl.n_v, prec, reps=1)
+        fk.fe_ks_apply(ctx, X, Y, wl.n_v, prec)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3 if prec in (fk.FE_KS_F64,) else 10
+        e0.record(stream)
+        for _ in range(reps):
+            fk.fe_ks_apply(ctx, X, Y, wl.n_v, prec)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"ms_per_step": ms, "value": units / (ms * 1e-3)}
+        del X, Y
+        torch.cuda.empty_cache()
+    out["speedup_f32_vs_f64"] = out["f64"]["ms_per_step"] / out["f32"]["ms_per_step"]
+    fk.fe_ks_destroy(ctx)
+    del X64
+    torch.cuda.empty_cache()
+    return out
+
+
 # -------------------------------------------------------- batched systems
 def small_systems():
     """Sixteen small systems (4^3 cells, degrees 4..8, N_v 8..32, FP64/FP32 alternating):
@@ -692,6 +740,8 @@ def main():
         line["e2e"] = res["e2e"]
     if res["filter"]:
         line["filter"] = res["filter"]
+    if not args.no_all_electron and world == 1:
+        line["all_electron_like"] = run_all_electron(args)
     if not args.no_batched:
         line["batched"] = run_batched(args)
         line["batched_small_systems"] = run_batched(args, small_systems())

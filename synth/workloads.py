@@ -86,6 +86,11 @@ CONFIGS = {
                    gga=True, n_atoms=32, complex=True, seed=3000),
     "C4": Workload("C4", L=30.0, n=24, p=8, nq=9, n_v=256, gga=True, n_atoms=64,
                    seed=4000),
+    # all-electron-like: a Bloch-periodic complex operator without pseudopotential
+    # projectors, few vectors on a large mesh (the regime of the paper's benzamide
+    # and BCC Li runs, FEOrder 8, N_v = 64)
+    "AE": Workload("AE", L=30.0, n=24, p=8, nq=9, n_v=64, kfrac=(0.25, 0.25, 0.25), gga=True,
+                   complex=True, seed=6000),
 }
 
 

@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the six-system batched launch")
     ap.add_argument("--no-filter", action="store_true", help="skip the R-ChFSI filter timing")
+    ap.add_argument("--no-cell-matrix", action="store_true", help="skip the cell-matrix baseline")
     ap.add_argument("--no-all-electron", action="store_true", help="skip the all-electron-like workload")
     ap.add_argument("--precision", choices=["both", "f64", "f32", "f64e", "bf16", "f16"], default="both",
                     help="f32 / f64e / bf16 / f16 alone time only that application (for profiling)")
@@ -305,12 +306,61 @@ def run_native(args, wl, rank, world):
     filt = None
     if not args.no_filter and rank == 0 and not cplx:
         filt = run_filter(args, wl, ctx, hp, X64)
+    cmb = None
+    if not args.no_cell_matrix and rank == 0 and not cplx:
+        cmb = run_cell_matrix(args, ctx, X64, units, f64, mixed)
     del X64
     torch.cuda.empty_cache()
     fk.fe_ks_destroy(ctx)
-    return dict(filter=filt, f64e=f64e, f64=f64, mixed=mixed, bf16=bf16, f16=f16, peak_mma_live=peak_mma_live,
+    return dict(filter=filt, cell_matrix=cmb, f64e=f64e, f64=f64, mixed=mixed, bf16=bf16, f16=f16, peak_mma_live=peak_mma_live,
                 mma_flops_per_apply=mma_flops, bytes32=bytes32, e2e=e2e, setup_s=setup_s, info=info, local_flops=local_flops,
                 peak64_live=peak64_live, peak32_live=peak32_live)
+
+
+# ------------------------------------------------------- cell-matrix baseline
+def run_cell_matrix(args, ctx, X64, units, f64, mixed):
+    """The cell-matrix method on the same operator: dense H_loc^(e) per cell (built once
+    from the FP64 matrix-free kernel), applied per colour by batched library GEMMs, with
+    the same projection and nonlocal expansion.  FP64 and FP32, one warm-up and a few
+    timed applications each; the cell matrices are freed after each precision."""
+    import torch
+    from paper_2512_08571_gb300 import fe_ks as fk
+    stream = torch.cuda.current_stream()
+    n_v = X64.shape[1]
+    out = {"method": "dense H_loc^(e) per cell (n_p^3 x n_p^3), per colour: gather X^(e), batched "
+                     "cuBLAS GEMM, colour-exclusive scatter + nonlocal expansion", "unit": UNIT}
+    for prec, name, mf in ((fk.FE_KS_F64, "f64", f64), (fk.FE_KS_F32, "f32", mixed)):
+        X = X64 if prec == fk.FE_KS_F64 else X64.to(torch.float32)
+        Y = torch.empty_like(X)
+        try:
+            cm = fk.fe_ks_cm_create(ctx, prec, n_v)
+        except fk.FeKsError as e:
+            out[name] = {"unavailable": str(e)}
+            continue
+        try:
+            info = fk.fe_ks_cm_info(cm)
+            setup_ms, nbytes = info["setup_ms"], info["bytes"]
+            fk.fe_ks_cm_apply(cm, X, Y, n_v)
+            torch.cuda.synchronize()
+            reps = 2 if prec == fk.FE_KS_F64 else 5
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fk.fe_ks_cm_apply(cm, X, Y, n_v)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+        finally:
+            fk.fe_ks_cm_destroy(cm)
+        r = {"ms_per_step": ms, "value": units / (ms * 1e-3), "setup_ms": setup_ms,
+             "device_bytes": nbytes}
+        if mf:
+            r["matrix_free_ms_per_step"] = mf["ms"]
+            r["matrix_free_speedup"] = ms / mf["ms"]
+        out[name] = r
+        del X, Y
+        torch.cuda.empty_cache()
+    return out
 
 
 # ------------------------------------------------------------ R-ChFSI filter
@@ -740,6 +790,8 @@ def main():
         line["e2e"] = res["e2e"]
     if res["filter"]:
         line["filter"] = res["filter"]
+    if res["cell_matrix"]:
+        line["cell_matrix_baseline"] = res["cell_matrix"]
     if not args.no_all_electron and world == 1:
         line["all_electron_like"] = run_all_electron(args)
     if not args.no_batched:

@@ -239,6 +239,37 @@ fe_ks_status fe_ks_set_config(fe_ks_ctx* ctx, int precision, int config);
 fe_ks_status fe_ks_get_config(const fe_ks_ctx* ctx, int precision, int* config);
 
 /*
+ * Cell-matrix (CM) baseline: the method the paper's matrix-free algorithms
+ * are measured against (Sec. 3, eq. HX with precomputed H^(e)).  Real
+ * operators only.
+ *
+ * fe_ks_cm_create builds, for every cell of ctx, the dense local cell matrix
+ * H_loc^(e) (n_p^3 x n_p^3, row-major) of the terms ctx was set up with,
+ * except the nonlocal one.  It runs ctx's own FP64 matrix-free cell kernel
+ * on identity blocks over a disjoint per-cell numbering, so the two methods
+ * agree up to rounding.  The matrices are stored in `precision` (FE_KS_F64:
+ * E n_p^6 8 bytes, 59 GB at 24^3 cells p = 8; FE_KS_F32: half).  Gather and
+ * product buffers for n_v_max vectors are allocated at create.
+ *
+ * fe_ks_cm_apply computes Y = H X in that precision on ctx's stream: per
+ * colour, gather the cells' rows of X, one batched library GEMM
+ * H_loc^(e) X^(e) over the colour's cells, and a colour-exclusive
+ * scatter-add that also adds the nonlocal expansion F Delta P (P from ctx's
+ * projection kernel).  X and Y are device [m][n_v] in the storage precision.
+ * The call allocates nothing.
+ *
+ * fe_ks_cm_info reports the setup time (ms) and the bytes held.
+ *
+ * Errors: FE_KS_ERR_UNSUPPORTED (complex operator, precision), FE_KS_ERR_OOM,
+ * FE_KS_ERR_ARG, FE_KS_ERR_CUDA.  ctx must outlive the object.
+ */
+typedef struct fe_ks_cm fe_ks_cm;
+fe_ks_status fe_ks_cm_create(fe_ks_ctx* ctx, int precision, int64_t n_v_max, fe_ks_cm** out);
+fe_ks_status fe_ks_cm_apply(fe_ks_cm* cm, const void* X, void* Y, int64_t n_v);
+fe_ks_status fe_ks_cm_info(const fe_ks_cm* cm, double* setup_ms, size_t* bytes);
+void fe_ks_cm_destroy(fe_ks_cm* cm);
+
+/*
  * Host-only: the greedy cell colouring the scatter-add relies on, i.e. the
  * assembly Q^T of Algorithm 1 done one colour at a time.
  *

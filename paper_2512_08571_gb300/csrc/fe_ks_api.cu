@@ -49,6 +49,10 @@ cudaError_t launch_local(const Ctx& c, const LocalParams<T, TS>& prm, cudaStream
   }
 }
 
+// used from other translation units (the cell-matrix baseline's setup)
+template cudaError_t launch_local<double, double>(const Ctx&, const LocalParams<double, double>&, cudaStream_t);
+template cudaError_t launch_local<float, float>(const Ctx&, const LocalParams<float, float>&, cudaStream_t);
+
 // Run body(i) for i in [0, n) on all host cores.
 static void parallel_for(int64_t n, const std::function<void(int64_t, int64_t)>& body) {
   unsigned nt = std::max(1u, std::thread::hardware_concurrency());

@@ -69,6 +69,11 @@ def _load():
     lib.fe_ks_tune.argtypes = [vp, vp, vp, i64, ctypes.c_int, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_int)]
     lib.fe_ks_set_config.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     lib.fe_ks_get_config.argtypes = [vp, ctypes.c_int, P(ctypes.c_int)]
+    lib.fe_ks_cm_create.argtypes = [vp, ctypes.c_int, i64, P(vp)]
+    lib.fe_ks_cm_apply.argtypes = [vp, vp, vp, i64]
+    lib.fe_ks_cm_info.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_size_t)]
+    lib.fe_ks_cm_destroy.argtypes = [vp]
+    lib.fe_ks_cm_destroy.restype = None
     lib.fe_ks_colour_cells.argtypes = [i64, i32, i64, vp, vp, P(i32)]
     lib.fe_ks_batch_create.argtypes = [P(vp), ctypes.c_int, P(i64), P(ctypes.c_int), P(vp)]
     lib.fe_ks_batch_configure.argtypes = [vp, P(ctypes.c_int), ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -185,6 +190,26 @@ def fe_ks_get_config(ctx, precision):
     out = ctypes.c_int()
     _check(_lib.fe_ks_get_config(ctx, precision, ctypes.byref(out)))
     return out.value
+
+
+def fe_ks_cm_create(ctx, precision, n_v_max):
+    out = ctypes.c_void_p()
+    _check(_lib.fe_ks_cm_create(ctx, precision, n_v_max, ctypes.byref(out)))
+    return out
+
+
+def fe_ks_cm_apply(cm, X, Y, n_v):
+    _check(_lib.fe_ks_cm_apply(cm, _ptr(X), _ptr(Y), n_v))
+
+
+def fe_ks_cm_info(cm):
+    ms, nb = ctypes.c_double(), ctypes.c_size_t()
+    _check(_lib.fe_ks_cm_info(cm, ctypes.byref(ms), ctypes.byref(nb)))
+    return dict(setup_ms=ms.value, bytes=nb.value)
+
+
+def fe_ks_cm_destroy(cm):
+    _lib.fe_ks_cm_destroy(cm)
 
 
 def fe_ks_colour_cells(cell_dofs, n_dofs):

@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the six-system batched launch")
     ap.add_argument("--no-filter", action="store_true", help="skip the R-ChFSI filter timing")
+    ap.add_argument("--no-nq2", action="store_true", help="skip the n_q = n_p + 2 workload")
     ap.add_argument("--no-cell-matrix", action="store_true", help="skip the cell-matrix baseline")
     ap.add_argument("--no-all-electron", action="store_true", help="skip the all-electron-like workload")
     ap.add_argument("--precision", choices=["both", "f64", "f32", "f64e", "bf16", "f16"], default="both",
@@ -134,7 +135,7 @@ def alg_flops(wl, n_pairs, n_v):
     """Paper's operation count (eq. flopRealMF / flopComplexMF) with n_s read as the
     number of (projector, cell) incidences, split into the fused local kernel's
     share (cell terms + expansion F Delta T3) and the projection kernel's share."""
-    n_p = n_q = wl.p + 1
+    n_p, n_q = wl.p + 1, wl.nq
     npo, nqo = n_p // 2, n_q // 2
     s = n_p * n_p + n_p * n_q + n_q * n_q
     if wl.complex:
@@ -308,7 +309,7 @@ def run_native(args, wl, rank, world):
         filt = run_filter(args, wl, ctx, hp, X64)
     cmb = None
     if not args.no_cell_matrix and rank == 0 and not cplx:
-        cmb = run_cell_matrix(args, ctx, X64, units, f64, mixed)
+        cmb = run_cell_matrix(args, ctx, X64, units, f64, mixed, bf16)
     del X64
     torch.cuda.empty_cache()
     fk.fe_ks_destroy(ctx)
@@ -318,10 +319,11 @@ def run_native(args, wl, rank, world):
 
 
 # ------------------------------------------------------- cell-matrix baseline
-def run_cell_matrix(args, ctx, X64, units, f64, mixed):
+def run_cell_matrix(args, ctx, X64, units, f64, mixed, bf16):
     """The cell-matrix method on the same operator: dense H_loc^(e) per cell (built once
     from the FP64 matrix-free kernel), applied per colour by batched library GEMMs, with
-    the same projection and nonlocal expansion.  FP64 and FP32, one warm-up and a few
+    the same projection and nonlocal expansion.  FP64, FP32 and BF16 (tensor-core GEMM,
+    FP32 accumulation) beside the matrix-free apply of the same precision, one warm-up and a few
     timed applications each; the cell matrices are freed after each precision."""
     import torch
     from paper_2512_08571_gb300 import fe_ks as fk
@@ -329,7 +331,8 @@ def run_cell_matrix(args, ctx, X64, units, f64, mixed):
     n_v = X64.shape[1]
     out = {"method": "dense H_loc^(e) per cell (n_p^3 x n_p^3), per colour: gather X^(e), batched "
                      "cuBLAS GEMM, colour-exclusive scatter + nonlocal expansion", "unit": UNIT}
-    for prec, name, mf in ((fk.FE_KS_F64, "f64", f64), (fk.FE_KS_F32, "f32", mixed)):
+    for prec, name, mf in ((fk.FE_KS_F64, "f64", f64), (fk.FE_KS_F32, "f32", mixed),
+                           (fk.FE_KS_BF16, "bf16_tensor_core", bf16)):
         X = X64 if prec == fk.FE_KS_F64 else X64.to(torch.float32)
         Y = torch.empty_like(X)
         try:
@@ -524,6 +527,52 @@ def run_all_electron(args):
         del X, Y
         torch.cuda.empty_cache()
     out["speedup_f32_vs_f64"] = out["f64"]["ms_per_step"] / out["f32"]["ms_per_step"]
+    fk.fe_ks_destroy(ctx)
+    del X64
+    torch.cuda.empty_cache()
+    return out
+
+
+# ------------------------------------------------- n_q = n_p + 2 quadrature
+def run_quadrature_np2(args, wl0):
+    """The same workload with n_q = n_p + 2 Gauss points per direction (the paper's default
+    quadrature; non-square N^1D): FP64 and FP32 applications, tuned, timed with CUDA
+    events (inputs larger than L2).  Returns a dict for the JSON line."""
+    import dataclasses
+    import numpy as np
+    import torch
+    from paper_2512_08571_gb300 import fe_ks as fk
+    from paper_2512_08571_gb300.problem import HostProblem
+    wl = dataclasses.replace(wl0, nq=wl0.p + 3, name=wl0.name + "-nq" + str(wl0.p + 3))
+    stream = torch.cuda.current_stream()
+    hp = HostProblem(wl)
+    ctx = fk.fe_ks_setup(hp.struct, fk.TERM_ALL, wl.n_v, stream.cuda_stream)
+    info = fk.fe_ks_info(ctx)
+    X64 = torch.empty((hp.m, wl.n_v), dtype=torch.float64, device="cuda")
+    fill_trial(wl, wl.n_v, X64, np.float64)
+    units = hp.m * wl.n_v
+    flops, _ = alg_flops(wl, info["n_pairs"], wl.n_v)
+    out = {"workload": f"{wl0.name} with n_q = n_p + 2 = {wl.nq}", "unit": UNIT, "alg_flops_per_apply": flops}
+    for prec, name, peak in ((fk.FE_KS_F64, "f64", PEAK_FP64_NOMINAL), (fk.FE_KS_F32, "f32", PEAK_FP32_NOMINAL)):
+        X = X64 if prec == fk.FE_KS_F64 else X64.to(torch.float32)
+        Y = torch.empty_like(X)
+        best, tune_ms = fk.fe_ks_tune(ctx, X, Y, wl.n_v, prec, reps=1)
+        fk.fe_ks_apply(ctx, X, Y, wl.n_v, prec)
+        torch.cuda.synchronize()
+        reps = 2 if prec == fk.FE_KS_F64 else 10
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fk.fe_ks_apply(ctx, X, Y, wl.n_v, prec)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"ms_per_step": ms, "value": units / (ms * 1e-3), "tile_config": best,
+                     "tune_ms_per_config": [round(t, 3) for t in tune_ms],
+                     "alg_tflops": flops / (ms * 1e-3) / 1e12,
+                     "frac_of_nominal_pipe": flops / (ms * 1e-3) / peak}
+        del X, Y
+        torch.cuda.empty_cache()
     fk.fe_ks_destroy(ctx)
     del X64
     torch.cuda.empty_cache()
@@ -794,6 +843,12 @@ def main():
         line["cell_matrix_baseline"] = res["cell_matrix"]
     if not args.no_all_electron and world == 1:
         line["all_electron_like"] = run_all_electron(args)
+    if not args.no_nq2 and world == 1 and not wl.complex:
+        q2 = run_quadrature_np2(args, wl)
+        q2["f64"]["vs_n_q_eq_n_p"] = q2["f64"]["ms_per_step"] / f64["ms"]
+        if mixed:
+            q2["f32"]["vs_n_q_eq_n_p"] = q2["f32"]["ms_per_step"] / mixed["ms"]
+        line["quadrature_n_p_plus_2"] = q2
     if not args.no_batched:
         line["batched"] = run_batched(args)
         line["batched_small_systems"] = run_batched(args, small_systems())

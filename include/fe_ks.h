@@ -89,7 +89,11 @@ enum {
  *                    identification; the constraint map C is folded into
  *                    cell_dofs, Sec. 3.1 eq. HX).
  *  degree          : FE degree p, n_p = p + 1 GLL nodes per direction (2..8).
- *  n_q             : Gauss points per direction; this build supports n_q = n_p.
+ *  n_q             : Gauss points per direction: n_q = n_p (square 1D
+ *                    operators) or n_q = n_p + 2 (the paper's default for
+ *                    accurate V_loc and V^G integrals, Sec. 6).  The tensor-core
+ *                    precisions (FE_KS_BF16, FE_KS_F16) and the batched launch
+ *                    need n_q = n_p and return FE_KS_ERR_UNSUPPORTED otherwise.
  *  cell_vertices   : [E][8][3] physical vertex coordinates; vertex slot
  *                    a + 2b + 4c sits at reference corner (2a-1, 2b-1, 2c-1);
  *                    the cell map is trilinear; coordinates are unwrapped per
@@ -248,14 +252,17 @@ fe_ks_status fe_ks_get_config(const fe_ks_ctx* ctx, int precision, int* config);
  * except the nonlocal one.  It runs ctx's own FP64 matrix-free cell kernel
  * on identity blocks over a disjoint per-cell numbering, so the two methods
  * agree up to rounding.  The matrices are stored in `precision` (FE_KS_F64:
- * E n_p^6 8 bytes, 59 GB at 24^3 cells p = 8; FE_KS_F32: half).  Gather and
- * product buffers for n_v_max vectors are allocated at create.
+ * E n_p^6 8 bytes, 59 GB at 24^3 cells p = 8; FE_KS_F32: half; FE_KS_BF16:
+ * a quarter, rounded to nearest even).  Gather and product buffers for
+ * n_v_max vectors are allocated at create.
  *
- * fe_ks_cm_apply computes Y = H X in that precision on ctx's stream: per
- * colour, gather the cells' rows of X, one batched library GEMM
- * H_loc^(e) X^(e) over the colour's cells, and a colour-exclusive
- * scatter-add that also adds the nonlocal expansion F Delta P (P from ctx's
- * projection kernel).  X and Y are device [m][n_v] in the storage precision.
+ * fe_ks_cm_apply computes Y = H X on ctx's stream: per colour, gather the
+ * cells' rows of X, one batched library GEMM H_loc^(e) X^(e) over the
+ * colour's cells, and a colour-exclusive scatter-add that also adds the
+ * nonlocal expansion F Delta P (P from ctx's projection kernel).  X and Y are
+ * device [m][n_v]: FP64 for FE_KS_F64, FP32 otherwise.  FE_KS_BF16 rounds the
+ * gathered X to BF16 and runs the GEMM on the tensor cores (BF16 x BF16,
+ * FP32 accumulation and result); the projection and expansion stay FP32.
  * The call allocates nothing.
  *
  * fe_ks_cm_info reports the setup time (ms) and the bytes held.

@@ -2,7 +2,7 @@
 
 The translation units compile in parallel: the C-ABI / setup, the host 1D
 tables, the nonlocal kernels, and one object per FE degree of the fused local
-kernel.  Objects go to ``_build/`` beside this file; the shared library to
+kernel (and per quadrature order n_q = n_p, n_p + 2).  Objects go to ``_build/`` beside this file; the shared library to
 ``libfe_ks.so``.  A rebuild happens only when a source is newer than the
 library.
 """
@@ -20,6 +20,7 @@ LIB = os.path.join(HERE, "libfe_ks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 DEGREES = range(1, 9)
+NQ_OFFSETS = (0, 2)   # n_q - n_p
 
 
 def _nvcc():
@@ -34,8 +35,9 @@ def _units():
     for name in ("fe_ks_api.cu", "fe_ks_tables.cu", "fe_ks_nonlocal.cu", "fe_ks_probe.cu", "fe_ks_cheb.cu", "fe_ks_static.cu", "fe_ks_batched.cu", "fe_ks_gemm.cu", "fe_ks_ffgemm.cu", "fe_ks_tc.cu", "fe_ks_cm.cu"):
         units.append((os.path.join(CSRC, name), os.path.join(BUILD, name + ".o"), []))
     for p in DEGREES:
-        units.append((os.path.join(CSRC, "fe_ks_local_deg.cu"),
-                      os.path.join(BUILD, f"fe_ks_local_p{p}.o"), [f"-DFEKS_P={p}"]))
+        for nqx in NQ_OFFSETS:
+            units.append((os.path.join(CSRC, "fe_ks_local_deg.cu"),
+                          os.path.join(BUILD, f"fe_ks_local_p{p}_q{nqx}.o"), [f"-DFEKS_P={p}", f"-DFEKS_NQX={nqx}"]))
     return units
 
 

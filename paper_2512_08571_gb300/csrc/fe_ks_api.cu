@@ -19,7 +19,7 @@
 
 namespace feks {
 
-template <typename T, typename TS, int P>
+template <typename T, typename TS, int P, int NQX>
 cudaError_t launch_local_deg(const Ctx&, const LocalParams<T, TS>&, cudaStream_t);
 
 static thread_local std::string g_last_error;
@@ -34,19 +34,28 @@ fe_ks_status fail(fe_ks_status code, const std::string& msg) {
   return code;
 }
 
-template <typename T, typename TS>
-cudaError_t launch_local(const Ctx& c, const LocalParams<T, TS>& prm, cudaStream_t s) {
+// n_q - n_p = NQX: 0 (the square rule) or 2 (the paper's default for accurate
+// V_loc and V^G integrals, Sec. 6)
+template <typename T, typename TS, int NQX>
+static cudaError_t launch_local_nq(const Ctx& c, const LocalParams<T, TS>& prm, cudaStream_t s) {
   switch (c.p) {
-    case 1: return launch_local_deg<T, TS, 1>(c, prm, s);
-    case 2: return launch_local_deg<T, TS, 2>(c, prm, s);
-    case 3: return launch_local_deg<T, TS, 3>(c, prm, s);
-    case 4: return launch_local_deg<T, TS, 4>(c, prm, s);
-    case 5: return launch_local_deg<T, TS, 5>(c, prm, s);
-    case 6: return launch_local_deg<T, TS, 6>(c, prm, s);
-    case 7: return launch_local_deg<T, TS, 7>(c, prm, s);
-    case 8: return launch_local_deg<T, TS, 8>(c, prm, s);
+    case 1: return launch_local_deg<T, TS, 1, NQX>(c, prm, s);
+    case 2: return launch_local_deg<T, TS, 2, NQX>(c, prm, s);
+    case 3: return launch_local_deg<T, TS, 3, NQX>(c, prm, s);
+    case 4: return launch_local_deg<T, TS, 4, NQX>(c, prm, s);
+    case 5: return launch_local_deg<T, TS, 5, NQX>(c, prm, s);
+    case 6: return launch_local_deg<T, TS, 6, NQX>(c, prm, s);
+    case 7: return launch_local_deg<T, TS, 7, NQX>(c, prm, s);
+    case 8: return launch_local_deg<T, TS, 8, NQX>(c, prm, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+template <typename T, typename TS>
+cudaError_t launch_local(const Ctx& c, const LocalParams<T, TS>& prm, cudaStream_t s) {
+  if (c.nq == c.np) return launch_local_nq<T, TS, 0>(c, prm, s);
+  if (c.nq == c.np + 2) return launch_local_nq<T, TS, 2>(c, prm, s);
+  return cudaErrorInvalidValue;
 }
 
 // used from other translation units (the cell-matrix baseline's setup)
@@ -202,8 +211,8 @@ static fe_ks_status check_geometry_args(const fe_ks_problem* prob) {
   if (!prob) return fail(FE_KS_ERR_ARG, "problem is NULL");
   if (prob->degree < 1 || prob->degree > 8)
     return fail(FE_KS_ERR_UNSUPPORTED, "degree must be in 1..8");
-  if (prob->n_q != prob->degree + 1)
-    return fail(FE_KS_ERR_UNSUPPORTED, "this build supports n_q = degree + 1 only");
+  if (prob->n_q != prob->degree + 1 && prob->n_q != prob->degree + 3)
+    return fail(FE_KS_ERR_UNSUPPORTED, "n_q must be n_p or n_p + 2 (degree + 1 or degree + 3)");
   if (prob->n_cells <= 0 || prob->n_cells > (int64_t)INT32_MAX)
     return fail(FE_KS_ERR_ARG, "n_cells out of range");
   if (!prob->cell_vertices) return fail(FE_KS_ERR_ARG, "cell_vertices is NULL");
@@ -634,6 +643,8 @@ fe_ks_status apply_core(Ctx& c, const T* X, T* Y, int64_t ncols, bool scaled, T 
   if (zero_fill && cudaMemsetAsync(Y, 0, bytes, s) != cudaSuccess)
     return fail(FE_KS_ERR_CUDA, "cudaMemsetAsync failed");
   mark(1);
+  if (tc && c.nq != c.np)
+    return fail(FE_KS_ERR_UNSUPPORTED, "the tensor-core precisions need n_q = n_p (square 1D operators)");
   const bool nl = (c.terms & FE_KS_TERM_NL) && c.n_pairs > 0;
   if (nl) {
     ProjParams<T> pp{};
@@ -679,7 +690,7 @@ fe_ks_status apply_core(Ctx& c, const T* X, T* Y, int64_t ncols, bool scaled, T 
     lp.n_cells = c.colour_ptr[col + 1] - c.colour_ptr[col];
     cudaError_t err;
     if constexpr (std::is_same<T, float>::value)
-      err = tc ? launch_tc(c, lp, s, tc == 2) : launch_local<T, T>(c, lp, s);
+      err = tc ? launch_tc(c, lp, s, tc == 2) : launch_local<T, T>(c, lp, s);   // tc: n_q = n_p, checked above
     else
       err = launch_local<T, T>(c, lp, s);
     if (err != cudaSuccess) return fail(FE_KS_ERR_CUDA, std::string("local kernel: ") + cudaGetErrorString(err));

@@ -477,6 +477,7 @@ fe_ks_status fe_ks_batch_create(fe_ks_ctx* const* ctxs, int n_sys, const int64_t
     const Ctx& c = ctxs[s]->c;
     if (c.cplx) return fail(FE_KS_ERR_UNSUPPORTED, "the batched launch supports real operators");
     if (c.p < 4 || c.p > 8) return fail(FE_KS_ERR_UNSUPPORTED, "the batched launch supports degrees 4..8");
+    if (c.nq != c.np) return fail(FE_KS_ERR_UNSUPPORTED, "the batched launch supports n_q = n_p");
     if (n_v[s] < 1 || n_v[s] > c.n_v_max) return fail(FE_KS_ERR_ARG, "n_v out of range");
     if (precision[s] != FE_KS_F64 && precision[s] != FE_KS_F32) return fail(FE_KS_ERR_ARG, "unknown precision");
     if (c.colour_ptr.size() - 1 > (size_t)kMaxPhase - 1) return fail(FE_KS_ERR_UNSUPPORTED, "too many colours");

@@ -15,6 +15,7 @@
 // Real operators only.  The GEMMs are plain library GEMMs (cuBLAS) on purpose:
 // this is the baseline, not the method.
 #include <cublas_v2.h>
+#include <cuda_bf16.h>
 
 #include <vector>
 
@@ -47,6 +48,23 @@ __global__ void k_cm_to_float(float* dst, const double* src, int64_t n) {
     dst[i] = (float)src[i];
 }
 
+__global__ void k_cm_to_bf16(__nv_bfloat16* dst, const double* src, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = __double2bfloat16(src[i]);
+}
+
+// BF16 operand blocks from FP32 X (round to nearest even)
+__global__ void k_cm_gather_bf16(__nv_bfloat16* __restrict__ Xg, const float* __restrict__ X, int64_t ld, int ncols,
+                                 const int* __restrict__ cell_dofs, const int* __restrict__ cells, int n_cells,
+                                 int np3) {
+  const int64_t rows = (int64_t)n_cells * np3;
+  for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+    const int c = (int)(r / np3), n = (int)(r % np3);
+    const int d = cell_dofs[(int64_t)cells[c] * np3 + n];
+    for (int v = threadIdx.x; v < ncols; v += blockDim.x) Xg[r * ncols + v] = __float2bfloat16_rn(X[(int64_t)d * ld + v]);
+  }
+}
+
 // Xg[c][n][v] = X[dofs(cell c, n)][v] for the cells of one colour
 template <typename T>
 __global__ void k_cm_gather(T* __restrict__ Xg, const T* __restrict__ X, int64_t ld, int ncols,
@@ -59,9 +77,9 @@ __global__ void k_cm_gather(T* __restrict__ Xg, const T* __restrict__ X, int64_t
   }
 }
 
-// batched-GEMM operand pointers of one colour
-template <typename T>
-__global__ void k_cm_ptrs(const T** A, const T** B, T** C, const T* Xg, const T* H, T* Yg, const int* cells,
+// batched-GEMM operand pointers of one colour (TA: operand type, TC: result type)
+template <typename TA, typename TC>
+__global__ void k_cm_ptrs(const TA** A, const TA** B, TC** C, const TA* Xg, const TA* H, TC* Yg, const int* cells,
                           int n_cells, int np3, int ncols) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n_cells; c += gridDim.x * blockDim.x) {
     A[c] = Xg + (int64_t)c * np3 * ncols;
@@ -134,11 +152,12 @@ fe_ks_status fe_ks_cm_create(fe_ks_ctx* ctx, int precision, int64_t n_v_max, fe_
   *out = nullptr;
   Ctx& c = ctx->c;
   if (c.cplx) return fail(FE_KS_ERR_UNSUPPORTED, "the cell-matrix baseline supports real operators");
-  if (precision != FE_KS_F64 && precision != FE_KS_F32) return fail(FE_KS_ERR_UNSUPPORTED, "precision F64 or F32");
+  if (precision != FE_KS_F64 && precision != FE_KS_F32 && precision != FE_KS_BF16)
+    return fail(FE_KS_ERR_UNSUPPORTED, "precision F64, F32 or BF16");
   if (n_v_max < 1 || n_v_max > c.n_v_max) return fail(FE_KS_ERR_ARG, "n_v_max must be in 1..the context's n_v_max");
   const int np3 = c.np3;
   const int64_t E = c.E;
-  const size_t esz = precision == FE_KS_F64 ? 8 : 4;
+  const size_t esz = precision == FE_KS_F64 ? 8 : precision == FE_KS_F32 ? 4 : 2;   // cell-matrix entries
   cudaStream_t s = c.stream;
   fe_ks_cm* cm = new fe_ks_cm;
   cm->ctx = ctx;
@@ -170,7 +189,7 @@ fe_ks_status fe_ks_cm_create(fe_ks_ctx* ctx, int precision, int64_t n_v_max, fe_
   const size_t hbytes = (size_t)E * np3 * np3 * esz;
   if (cudaMalloc(&cm->H, hbytes) != cudaSuccess) return bad("cell matrices");
   if (cudaMalloc(&Xid, (size_t)chunk * np3 * np3 * 8) != cudaSuccess) return bad("identity blocks");
-  if (precision == FE_KS_F32 && cudaMalloc(&Ych, (size_t)chunk * np3 * np3 * 8) != cudaSuccess)
+  if (precision != FE_KS_F64 && cudaMalloc(&Ych, (size_t)chunk * np3 * np3 * 8) != cudaSuccess)
     return bad("chunk buffer");
   if (cudaMalloc(&dis, (size_t)E * np3 * sizeof(int)) != cudaSuccess) return bad("disjoint map");
   if (cudaMalloc(&iota, (size_t)E * sizeof(int)) != cudaSuccess) return bad("cell list");
@@ -199,6 +218,9 @@ fe_ks_status fe_ks_cm_create(fe_ks_ctx* ctx, int precision, int64_t n_v_max, fe_
     if (precision == FE_KS_F32)
       k_cm_to_float<<<ew_grid((int64_t)nc * np3 * np3), 256, 0, s>>>(
           static_cast<float*>(cm->H) + (size_t)e0c * np3 * np3, Y, (int64_t)nc * np3 * np3);
+    else if (precision == FE_KS_BF16)
+      k_cm_to_bf16<<<ew_grid((int64_t)nc * np3 * np3), 256, 0, s>>>(
+          static_cast<__nv_bfloat16*>(cm->H) + (size_t)e0c * np3 * np3, Y, (int64_t)nc * np3 * np3);
   }
   cudaEventRecord(e1, s);
   cudaEventSynchronize(e1);
@@ -212,7 +234,8 @@ fe_ks_status fe_ks_cm_create(fe_ks_ctx* ctx, int precision, int64_t n_v_max, fe_
   Xid = Ych = nullptr;
   dis = iota = nullptr;
   // apply buffers
-  const size_t gbytes = (size_t)cm->max_cells * np3 * n_v_max * esz;
+  // gathered X blocks and GEMM results (BF16: FP32 results, so both sized for 4 bytes)
+  const size_t gbytes = (size_t)cm->max_cells * np3 * n_v_max * std::max<size_t>(esz, 4);
   if (cudaMalloc(&cm->Xg, gbytes) != cudaSuccess || cudaMalloc(&cm->Yg, gbytes) != cudaSuccess ||
       cudaMalloc(&cm->ptrs, (size_t)3 * cm->max_cells * sizeof(void*)) != cudaSuccess)
     return bad("apply buffers");
@@ -237,7 +260,8 @@ fe_ks_status fe_ks_cm_apply(fe_ks_cm* cm, const void* Xv, void* Yv, int64_t n_v)
   cudaStream_t s = c.stream;
   const int np3 = c.np3, ncols = (int)n_v;
   const bool f64 = cm->prec == FE_KS_F64;
-  const size_t esz = f64 ? 8 : 4;
+  const bool bf16 = cm->prec == FE_KS_BF16;
+  const size_t esz = f64 ? 8 : 4;   // X and Y (BF16: FP32 storage)
   cudaMemsetAsync(Yv, 0, (size_t)c.m * ncols * esz, s);
   const bool nl = (c.terms & FE_KS_TERM_NL) && c.n_pairs > 0;
   if (nl) {   // P = Delta F^T X, the operator's own projection
@@ -294,7 +318,7 @@ fe_ks_status fe_ks_cm_apply(fe_ks_cm* cm, const void* Xv, void* Yv, int64_t n_v)
       const double** B = (const double**)(cm->ptrs + cm->max_cells);
       double** C = (double**)(cm->ptrs + 2 * (size_t)cm->max_cells);
       k_cm_gather<double><<<grid, 128, 0, s>>>(Xg, X, ncols, ncols, c.cell_dofs, cells, n, np3);
-      k_cm_ptrs<double><<<(n + 127) / 128, 128, 0, s>>>(A, B, C, Xg, static_cast<const double*>(cm->H), Yg, cells, n,
+      k_cm_ptrs<double, double><<<(n + 127) / 128, 128, 0, s>>>(A, B, C, Xg, static_cast<const double*>(cm->H), Yg, cells, n,
                                                        np3, ncols);
       const double one = 1.0, zero = 0.0;
       bs = cublasDgemmBatched(cm->blas, CUBLAS_OP_N, CUBLAS_OP_N, ncols, np3, np3, &one, A, ncols, B, np3, &zero, C,
@@ -305,18 +329,31 @@ fe_ks_status fe_ks_cm_apply(fe_ks_cm* cm, const void* Xv, void* Yv, int64_t n_v)
     } else {
       const float* X = static_cast<const float*>(Xv);
       float* Y = static_cast<float*>(Yv);
-      float* Xg = static_cast<float*>(cm->Xg);
       float* Yg = static_cast<float*>(cm->Yg);
-      // three pointer arrays of max_cells entries each: A, B, C operands
-      const float** A = (const float**)(cm->ptrs);
-      const float** B = (const float**)(cm->ptrs + cm->max_cells);
-      float** C = (float**)(cm->ptrs + 2 * (size_t)cm->max_cells);
-      k_cm_gather<float><<<grid, 128, 0, s>>>(Xg, X, ncols, ncols, c.cell_dofs, cells, n, np3);
-      k_cm_ptrs<float><<<(n + 127) / 128, 128, 0, s>>>(A, B, C, Xg, static_cast<const float*>(cm->H), Yg, cells, n,
-                                                      np3, ncols);
       const float one = 1.f, zero = 0.f;
-      bs = cublasSgemmBatched(cm->blas, CUBLAS_OP_N, CUBLAS_OP_N, ncols, np3, np3, &one, A, ncols, B, np3, &zero, C,
-                              ncols, n);
+      if (bf16) {   // BF16 x BF16 -> FP32 on the tensor cores
+        __nv_bfloat16* Xg = static_cast<__nv_bfloat16*>(cm->Xg);
+        const __nv_bfloat16** A = (const __nv_bfloat16**)(cm->ptrs);
+        const __nv_bfloat16** B = (const __nv_bfloat16**)(cm->ptrs + cm->max_cells);
+        float** C = (float**)(cm->ptrs + 2 * (size_t)cm->max_cells);
+        k_cm_gather_bf16<<<grid, 128, 0, s>>>(Xg, X, ncols, ncols, c.cell_dofs, cells, n, np3);
+        k_cm_ptrs<__nv_bfloat16, float><<<(n + 127) / 128, 128, 0, s>>>(
+            A, B, C, Xg, static_cast<const __nv_bfloat16*>(cm->H), Yg, cells, n, np3, ncols);
+        bs = cublasGemmBatchedEx(cm->blas, CUBLAS_OP_N, CUBLAS_OP_N, ncols, np3, np3, &one, (const void* const*)A,
+                                 CUDA_R_16BF, ncols, (const void* const*)B, CUDA_R_16BF, np3, &zero,
+                                 (void* const*)C, CUDA_R_32F, ncols, n, CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
+      } else {
+        float* Xg = static_cast<float*>(cm->Xg);
+        // three pointer arrays of max_cells entries each: A, B, C operands
+        const float** A = (const float**)(cm->ptrs);
+        const float** B = (const float**)(cm->ptrs + cm->max_cells);
+        float** C = (float**)(cm->ptrs + 2 * (size_t)cm->max_cells);
+        k_cm_gather<float><<<grid, 128, 0, s>>>(Xg, X, ncols, ncols, c.cell_dofs, cells, n, np3);
+        k_cm_ptrs<float, float><<<(n + 127) / 128, 128, 0, s>>>(A, B, C, Xg, static_cast<const float*>(cm->H), Yg, cells, n,
+                                                        np3, ncols);
+        bs = cublasSgemmBatched(cm->blas, CUBLAS_OP_N, CUBLAS_OP_N, ncols, np3, np3, &one, A, ncols, B, np3, &zero,
+                                C, ncols, n);
+      }
       k_cm_scatter<float><<<grid, 128, 0, s>>>(Y, Yg, ncols, ncols, c.cell_dofs, cells, n, np3,
                                                nl ? c.cell_pair_ptr : nullptr, c.cell_pairs, c.pair_atom, c.f32.F,
                                                c.f32.Q, c.n_proj);

@@ -13,7 +13,7 @@
 
 namespace feks {
 
-constexpr int kMaxN = 10;      // n_p, n_q <= 10
+constexpr int kMaxN = 11;      // n_p <= 9, n_q <= 11 (n_q = n_p + 2 at p = 8)
 constexpr int kMaxH = kMaxN / 2;
 
 // Even-odd split of a centro-(anti)symmetric 1D matrix M (NO x NI) with

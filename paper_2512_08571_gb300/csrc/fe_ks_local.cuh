@@ -999,9 +999,9 @@ __host__ __forceinline__ int cfg_for(const Ctx& c) {
   return c.cfgE;
 }
 
-template <typename T, typename TS, int P>
+template <typename T, typename TS, int P, int NQX>
 cudaError_t launch_local_deg(const Ctx& c, const LocalParams<T, TS>& prm, cudaStream_t s) {
-  constexpr int NP = P + 1, NQ = P + 1;
+  constexpr int NP = P + 1, NQ = P + 1 + NQX;
   constexpr int V0 = cfg_vt<NQ>(0), V1 = cfg_vt<NQ>(1), V2 = cfg_vt<NQ>(2);
   switch (cfg_for<T, TS>(c)) {
     case 1: return launch_local_cfg<T, TS, NP, NQ, V1, cfg_nt(V1, NQ)>(c, prm, s);

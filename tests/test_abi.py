@@ -32,8 +32,11 @@ def test_every_declared_symbol_is_exported():
         assert hasattr(lib, n), n
 
 
-def test_quadrature_points_match_oracle_geometry():
+@pytest.mark.parametrize("nqx", [0, 2])
+def test_quadrature_points_match_oracle_geometry(nqx):
+    import dataclasses
     wl = CONFIGS["C2"].scaled(n=3)
+    wl = dataclasses.replace(wl, nq=wl.p + 1 + nqx)
     hp = HostProblem(wl)
     P = Problem(wl)
     for e in (0, 7, 26):
@@ -48,7 +51,7 @@ def test_setup_rejects_bad_problems_on_host():
     hp = _struct(CONFIGS["C1"])
     s = hp.struct
     with pytest.raises(fk.FeKsError, match="UNSUPPORTED"):
-        s.n_q = s.degree + 3
+        s.n_q = s.degree + 2      # only n_q = n_p and n_p + 2 are built
         fk.fe_ks_setup(s, fk.TERM_ALL, 1)
     s.n_q = s.degree + 1
     with pytest.raises(fk.FeKsError, match="ERR_ARG"):

@@ -17,7 +17,9 @@ from gpu_util import gpu_apply, rel_err_cols, round_input
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {fk.FE_KS_F64: 1e-12, fk.FE_KS_F32: 1e-5}
+# BF16 (tensor-core GEMM on BF16-rounded H^(e) and X^(e), FP32 accumulation): 8 units of
+# BF16 rounding, as for the matrix-free tensor-core path
+TOL = {fk.FE_KS_F64: 1e-12, fk.FE_KS_F32: 1e-5, fk.FE_KS_BF16: 8 * 2.0 ** -8}
 
 SMALL = {
     "C1": CONFIGS["C1"],
@@ -52,7 +54,7 @@ def cm_apply(hp, X, precision, terms=fk.TERM_ALL, n_v_max=None):
         fk.fe_ks_destroy(ctx)
 
 
-@pytest.mark.parametrize("precision", [fk.FE_KS_F64, fk.FE_KS_F32])
+@pytest.mark.parametrize("precision", [fk.FE_KS_F64, fk.FE_KS_F32, fk.FE_KS_BF16])
 @pytest.mark.parametrize("key", list(SMALL))
 def test_cell_matrix_matches_oracle(cases, key, precision):
     wl, hp, P, X = cases[key]
@@ -60,7 +62,7 @@ def test_cell_matrix_matches_oracle(cases, key, precision):
     Y, ms, nbytes = cm_apply(hp, Xin, precision)
     err = rel_err_cols(Y, P.apply(Xin))
     assert err <= TOL[precision], err
-    esz = 8 if precision == fk.FE_KS_F64 else 4
+    esz = {fk.FE_KS_F64: 8, fk.FE_KS_F32: 4, fk.FE_KS_BF16: 2}[precision]
     assert nbytes >= wl.n_cells * (wl.p + 1) ** 6 * esz   # every cell matrix is held
     assert ms > 0.0
 
@@ -89,7 +91,7 @@ def test_cell_matrix_rejects_bad_arguments(cases):
     ctx = fk.fe_ks_setup(hp.struct, fk.TERM_ALL, 4, torch.cuda.current_stream().cuda_stream)
     try:
         with pytest.raises(fk.FeKsError):
-            fk.fe_ks_cm_create(ctx, fk.FE_KS_BF16, 4)
+            fk.fe_ks_cm_create(ctx, fk.FE_KS_F16, 4)
         with pytest.raises(fk.FeKsError):
             fk.fe_ks_cm_create(ctx, fk.FE_KS_F64, 5)   # above the context's n_v_max
         cm = fk.fe_ks_cm_create(ctx, fk.FE_KS_F64, 2)

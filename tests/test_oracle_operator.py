@@ -18,13 +18,13 @@ def _zero(x):
     return np.zeros(np.asarray(x).shape[:-1])
 
 
-def _single_cell(A, b, p, kpt=(0, 0, 0), vloc=_zero, vgga=None):
+def _single_cell(A, b, p, kpt=(0, 0, 0), vloc=_zero, vgga=None, nq=None):
     """One affine cell x = A xi + b with its own (non-periodic) DoFs."""
     verts = np.zeros((1, 8, 3))
     for v in range(8):
         xi = np.array([2 * (v & 1) - 1, 2 * ((v >> 1) & 1) - 1, 2 * ((v >> 2) & 1) - 1], float)
         verts[0, v] = A @ xi + b
-    wl = Workload("cell", L=100.0, n=1, p=p, nq=p + 1, n_v=1)
+    wl = Workload("cell", L=100.0, n=1, p=p, nq=p + 1 if nq is None else nq, n_v=1)
     dofs = np.arange((p + 1) ** 3)[None, :]
     return Problem(wl, verts=verts, dofs=dofs, vloc=vloc, vgga=vgga, kpt=kpt)
 
@@ -95,6 +95,58 @@ def test_polynomial_exactness_affine_cell():
         assert abs(got[key] - exact[key]) <= 1e-11 * max(1.0, abs(exact[key])), (key, got[key], exact[key])
     # the K orientation: u^T K v != v^T K u for these fields
     assert abs(exact["K"] - integ(v * sum(kv[i] * gu[i] for i in range(3)))) > 1e-3
+
+
+def test_quadrature_order_n_p_plus_2():
+    """n_q = n_p + 2 (the paper's default quadrature, Sec. 6) integrates u V v exactly for
+    a quartic V_loc (total degree 3 + 3 + 4 = 10 <= 2 n_q - 1 = 11 at p = 3), while the
+    n_q = n_p rule (exact to degree 7) does not.  Pins that the oracle's quadrature order
+    follows n_q and not the degree."""
+    sp = pytest.importorskip("sympy")
+    rng = np.random.default_rng(11)
+    p = 3
+    A = np.array([[1.1, 0.1, 0.0], [-0.2, 0.8, 0.25], [0.05, -0.1, 1.2]])
+    b = np.array([0.3, -0.6, 0.2])
+    X1, X2, X3 = sp.symbols("x1 x2 x3")
+    xs = (X1, X2, X3)
+
+    def rand_poly(deg):
+        expr = 0
+        for i in range(deg + 1):
+            for j in range(deg + 1 - i):
+                for k in range(deg + 1 - i - j):
+                    expr += sp.Rational(int(rng.integers(-9, 10)), 5) * X1 ** i * X2 ** j * X3 ** k
+        return expr
+
+    u, v = rand_poly(p), rand_poly(p)
+    VL = 1 + X1 ** 2 * X2 ** 2 - sp.Rational(1, 2) * X3 ** 4 + X1 * X2 * X3
+    E1, E2, E3 = sp.symbols("e1 e2 e3")
+    Ar = [[sp.nsimplify(A[i, j]) for j in range(3)] for i in range(3)]
+    br = [sp.nsimplify(b[i]) for i in range(3)]
+    sub = {xs[i]: sum(Ar[i][j] * (E1, E2, E3)[j] for j in range(3)) + br[i] for i in range(3)}
+    detA = sp.Matrix(Ar).det()
+
+    def integ(f):
+        g = sp.expand(f.subs(sub, simultaneous=True))
+        return float(abs(detA) * sp.integrate(g, (E1, -1, 1), (E2, -1, 1), (E3, -1, 1)))
+
+    gu, gv = [sp.diff(u, x) for x in xs], [sp.diff(v, x) for x in xs]
+    exact_L = integ(VL * u * v)
+    exact_T = integ(sp.Rational(1, 2) * sum(gu[i] * gv[i] for i in range(3)))
+    fu, fv, fvl = (sp.lambdify(xs, f, "numpy") for f in (u, v, VL))
+    vlf = lambda x: fvl(x[..., 0], x[..., 1], x[..., 2]) * np.ones(x.shape[:-1])
+    got = {}
+    for nq in (p + 1, p + 3):
+        P = _single_cell(A, b, p, vloc=vlf, nq=nq)
+        xn = P.node_coords()[0]
+        uu = fu(xn[:, 0], xn[:, 1], xn[:, 2]) * np.ones(len(xn))
+        vv = fv(xn[:, 0], xn[:, 1], xn[:, 2]) * np.ones(len(xn))
+        got[nq] = (np.real(uu @ P.cell_matrix(0, terms=("L",)) @ vv),
+                   np.real(uu @ P.cell_matrix(0, terms=("T",)) @ vv))
+    assert abs(got[p + 3][0] - exact_L) <= 1e-11 * abs(exact_L)
+    assert abs(got[p + 3][1] - exact_T) <= 1e-11 * abs(exact_T)
+    assert abs(got[p + 1][1] - exact_T) <= 1e-11 * abs(exact_T)       # T: degree 4 per direction
+    assert abs(got[p + 1][0] - exact_L) > 1e-6 * abs(exact_L)          # the low rule misses the quartic
 
 
 def _periodic(n=3, p=4, L=10.0, jitter=0.0, kfrac=(0, 0, 0), gga=False, n_atoms=0, seed=11):

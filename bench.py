@@ -644,19 +644,33 @@ def run_batched(args, wls=None):
     b = fk.fe_ks_batch_create(ctxs, [wl.n_v for wl in wls], prec)
     best = None
     trials = []
-    for occ in (1, 2):
-        for tile in (0, 1):
-            for cells in (1, 2, 4):
-                for depth in (1, 2):
-                    fk.fe_ks_batch_configure(b, [tile] * len(wls), cells, depth, 2.0, False, blocks_per_sm=occ)
-                    ms = timed(lambda: fk.fe_ks_batch_apply(b, Xs, Ys, stream.cuda_stream), 2)
-                    fk.fe_ks_batch_status(b)
-                    trials.append({"blocks_per_sm": occ, "tile": tile, "cells_per_item": cells, "depth": depth,
-                                   "ms": round(ms, 3)})
-                    if best is None or ms < best[0]:
-                        best = (ms, tile, cells, depth, occ)
-    _, tile, cells, depth, occ = best
-    fk.fe_ks_batch_configure(b, [tile] * len(wls), cells, depth, 2.0, False, blocks_per_sm=occ)
+    is32 = [pr == fk.FE_KS_F32 for pr in prec]
+    depth = 2
+    for threads in (384, 512, 672):
+        for occ in ((1, 2) if threads <= 512 else (1,)):
+            for t64 in (0, 1):
+                for t32 in (0, 1):
+                    for cells in (1, 2, 4):
+                        tiles = [t32 if f else t64 for f in is32]
+                        fk.fe_ks_batch_configure(b, tiles, cells, depth, 2.0, False, blocks_per_sm=occ,
+                                                 threads=threads)
+                        ms = timed(lambda: fk.fe_ks_batch_apply(b, Xs, Ys, stream.cuda_stream), 2)
+                        fk.fe_ks_batch_status(b)
+                        trials.append({"threads": threads, "blocks_per_sm": occ, "tile_f64": t64, "tile_f32": t32,
+                                       "cells_per_item": cells, "ms": round(ms, 3)})
+                        if best is None or ms < best[0]:
+                            best = (ms, tiles, cells, occ, threads)
+    _, tiles, cells, occ, threads = best
+    for d in (1, 4):                            # then the items claimed per fetch
+        fk.fe_ks_batch_configure(b, tiles, cells, d, 2.0, False, blocks_per_sm=occ, threads=threads)
+        ms = timed(lambda: fk.fe_ks_batch_apply(b, Xs, Ys, stream.cuda_stream), 2)
+        fk.fe_ks_batch_status(b)
+        trials.append({"threads": threads, "blocks_per_sm": occ, "tile_f64": tiles[0], "cells_per_item": cells,
+                       "depth": d, "ms": round(ms, 3)})
+        if ms < best[0]:
+            best = (ms, tiles, cells, occ, threads)
+            depth = d
+    fk.fe_ks_batch_configure(b, tiles, cells, depth, 2.0, False, blocks_per_sm=occ, threads=threads)
     g = torch.cuda.CUDAGraph()
     side = torch.cuda.Stream()
     side.wait_stream(stream)
@@ -678,7 +692,8 @@ def run_batched(args, wls=None):
             "value": units / (ms_graph * 1e-3), "unit": UNIT, "ms_per_step": ms_graph,
             "one_launch_per_system": {"value": units / (ms_sep * 1e-3), "ms_per_step": ms_sep},
             "speedup_vs_separate": ms_sep / ms_graph,
-            "tuned": {"tile_config": tile, "cells_per_item": cells, "depth": depth, "blocks_per_sm": occ},
+            "tuned": {"tile_config": tiles, "cells_per_item": cells, "depth": depth, "blocks_per_sm": occ,
+                      "threads": threads},
             "tuning_trials": trials, "items": info["n_items"], "grid": info["grid"],
             "smem_bytes": info["smem_bytes"], "graph": True, "x_inputs": "device RNG (seed 5000), U(-1,1)",
             "l2": "flushed (256 MiB write) before each timed rep"}

@@ -307,8 +307,9 @@ fe_ks_status fe_ks_colour_cells(int64_t n_cells, int32_t np3, int64_t n_dofs, co
  * caller, must outlive the batch), vector counts and precisions (FE_KS_F64 /
  * FE_KS_F32); it allocates the queue and counters (the only allocation).
  * fe_ks_batch_configure sets the tunables -- tile configuration per system
- * (0/1: columns per tile), cells per work item, items claimed per fetch,
- * resident CTAs per SM (1, or 2 with a tighter register budget) --
+ * (0/1: columns per tile), cells per work item, items claimed per fetch, resident CTAs per SM (1, or
+ * 2 with a tighter register budget; 672-thread blocks run one per SM),
+ * threads per block (384, 512 or 672; 0 keeps the current, initially 384) --
  * plus the bounded-wait limit in seconds, and inject_missing_item = 1 makes
  * the host count one phase-0 item that is never published (fault injection:
  * the launch then ends with FE_KS_ERR_TIMEOUT reported by fe_ks_batch_status).
@@ -322,7 +323,8 @@ typedef struct fe_ks_batch fe_ks_batch;
 fe_ks_status fe_ks_batch_create(fe_ks_ctx* const* ctxs, int n_sys, const int64_t* n_v, const int* precision,
                                 fe_ks_batch** out);
 fe_ks_status fe_ks_batch_configure(fe_ks_batch* b, const int* tile_config, int cells_per_item, int depth,
-                                   int blocks_per_sm, double wait_seconds, int inject_missing_item);
+                                   int blocks_per_sm, double wait_seconds, int inject_missing_item,
+                                   int threads_per_block);
 fe_ks_status fe_ks_batch_apply(fe_ks_batch* b, const void* const* X, void* const* Y, void* cuda_stream);
 fe_ks_status fe_ks_batch_status(fe_ks_batch* b);
 fe_ks_status fe_ks_batch_info(const fe_ks_batch* b, int* n_items, int* grid, size_t* smem_bytes);

@@ -21,6 +21,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 DEGREES = range(1, 9)
 NQ_OFFSETS = (0, 2)   # n_q - n_p
+BATCH_THREADS = (384, 512, 672)   # block sizes of the batched persistent kernel
 
 
 def _nvcc():
@@ -34,6 +35,9 @@ def _units():
     units = []
     for name in ("fe_ks_api.cu", "fe_ks_tables.cu", "fe_ks_nonlocal.cu", "fe_ks_probe.cu", "fe_ks_cheb.cu", "fe_ks_static.cu", "fe_ks_batched.cu", "fe_ks_gemm.cu", "fe_ks_ffgemm.cu", "fe_ks_tc.cu", "fe_ks_cm.cu"):
         units.append((os.path.join(CSRC, name), os.path.join(BUILD, name + ".o"), []))
+    for nt in BATCH_THREADS:
+        units.append((os.path.join(CSRC, "fe_ks_batched_k.cu"),
+                      os.path.join(BUILD, f"fe_ks_batched_k{nt}.o"), [f"-DFEKS_BNT={nt}"]))
     for p in DEGREES:
         for nqx in NQ_OFFSETS:
             units.append((os.path.join(CSRC, "fe_ks_local_deg.cu"),

@@ -17,292 +17,21 @@
 // co-residency assumption.  Every wait is bounded: on expiry the CTA sets the
 // error flag and leaves; the host reports FE_KS_ERR_TIMEOUT.
 //
-// Tunables (fe_ks_batch_tune): columns per tile (the per-precision tile
-// configuration of the fused kernel), cells per work item, and the number of
-// items a CTA claims per atomic fetch.
+// Tunables (fe_ks_batch_configure): per system the column tile of the cell
+// routine (narrow or wide), cells per work item, the number of items a CTA
+// claims per atomic fetch, the block size (384, 512 or 672 threads, one
+// kernel object each) and the resident CTAs per SM.  The device code is in
+// fe_ks_batched.cuh.
 #include <algorithm>
 #include <cstring>
 #include <numeric>
 #include <vector>
 
-#include "fe_ks_local.cuh"
+#include "fe_ks_batched.cuh"
 
 namespace feks {
 
-constexpr int kMaxSys = 16;
-constexpr int kMaxPhase = 66;
-constexpr int kBatchNT = 384;
-enum : int { kItemZero = 0, kItemPair = 1, kItemLocal = 2, kItemSum = 3 };
-
-struct BatchSys {
-  int prec;        // FE_KS_F64 or FE_KS_F32
-  int p;           // degree
-  int cfg;         // tile configuration (0 or 1)
-  int ncols;
-  int64_t m;
-  const void* X;
-  void* Y;
-  const int* cell_dofs;
-  const int* colour_cells;
-  const void* coef;
-  int ncoef;
-  int gga;
-  const int* cell_pair_ptr;   // nullptr without projectors
-  const int* cell_pairs;
-  const int* pair_atom;
-  const void* F;
-  void* Q;
-  const void* h;
-  const int* atom_pair_ptr;
-  const int* pair_cell;
-  void* part;      // projection partials [pair][n_proj][ncols]
-  int n_proj;
-  int np3;
-};
-
-struct BatchParams {
-  BatchSys sys[kMaxSys];
-  EOTables<double> t64[9];
-  EOTables<float> t32[9];
-  const int4* items;
-  int n_items;
-  int* queue;
-  int* done;         // [kMaxSys][kMaxPhase]
-  const int* need;   // [kMaxSys][kMaxPhase]
-  int* err;
-  long long wait_cycles;
-  int depth;
-};
-
-// Operand view of one system for the cell routine (field names of LocalParams).
-template <typename T>
-struct SysArgs {
-  const T* X;
-  T* Y;
-  int64_t ld;
-  int ncols;
-  const int* cell_dofs;
-  const T* coef;
-  int ncoef;
-  int gga;
-  const T* dscale;
-  const int* cell_pair_ptr;
-  const int* cell_pairs;
-  const int* pair_atom;
-  const T* F;
-  const T* Q;
-  int n_proj;
-  T alpha;
-};
-
-template <typename T>
-__device__ __forceinline__ SysArgs<T> sys_args(const BatchSys& s) {
-  SysArgs<T> a;
-  a.X = static_cast<const T*>(s.X);
-  a.Y = static_cast<T*>(s.Y);
-  a.ld = s.ncols;
-  a.ncols = s.ncols;
-  a.cell_dofs = s.cell_dofs;
-  a.coef = static_cast<const T*>(s.coef);
-  a.ncoef = s.ncoef;
-  a.gga = s.gga;
-  a.dscale = nullptr;
-  a.cell_pair_ptr = s.cell_pair_ptr;
-  a.cell_pairs = s.cell_pairs;
-  a.pair_atom = s.pair_atom;
-  a.F = static_cast<const T*>(s.F);
-  a.Q = static_cast<const T*>(s.Q);
-  a.n_proj = s.n_proj;
-  a.alpha = T(1);
-  return a;
-}
-
-template <typename T>
-__device__ void zero_item(const BatchSys& s, int row0, int rows) {
-  T* Y = static_cast<T*>(s.Y) + (int64_t)row0 * s.ncols;
-  const int64_t n = (int64_t)rows * s.ncols;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) Y[i] = T(0);
-}
-
-// Columns per projection item: the smallest of 32, 64, 128 that covers the
-// columns (each divides the block size).
-__host__ __device__ inline int batch_proj_cw(int ncols) { return ncols <= 32 ? 32 : ncols <= 64 ? 64 : 128; }
-
-// Shared memory of a projection item: the pair's F block, the cell's DoF list
-// and the slice reduction buffer.
-template <typename T>
-__host__ __device__ inline size_t batch_proj_bytes(int n_proj, int np3, int cw) {
-  const size_t head = ((size_t)n_proj * np3 * sizeof(T) + (size_t)np3 * sizeof(int) + 15) & ~(size_t)15;
-  return head + (size_t)(kBatchNT / cw) * n_proj * cw * sizeof(T);
-}
-
-// part[pr][b][col] = sum_node F[pr][b][node] x(d(node), col) for columns
-// [col0, col0 + cw): one column per thread, kBatchNT / cw row slices reduced
-// in shared memory in slice order.
-template <typename T>
-__device__ void pair_item(const BatchSys& s, int pr, int col0, int cw, unsigned char* smem) {
-  const int np3 = s.np3, n_proj = s.n_proj;
-  T* Fs = reinterpret_cast<T*>(smem);
-  int* ds = reinterpret_cast<int*>(smem + (size_t)n_proj * np3 * sizeof(T));
-  T* red = reinterpret_cast<T*>(smem + (((size_t)n_proj * np3 * sizeof(T) + (size_t)np3 * sizeof(int) + 15) & ~(size_t)15));
-  const int rs = kBatchNT / cw;
-  const int lc = threadIdx.x % cw, sl = threadIdx.x / cw;
-  const int col = col0 + lc;
-  const bool act = col < s.ncols;
-  const T* X = static_cast<const T*>(s.X);
-  const T* Fp = static_cast<const T*>(s.F) + (int64_t)pr * n_proj * np3;
-  for (int i = threadIdx.x; i < n_proj * np3; i += kBatchNT) Fs[i] = Fp[i];
-  const int cell = s.pair_cell[pr];
-  for (int i = threadIdx.x; i < np3; i += kBatchNT) ds[i] = s.cell_dofs[(int64_t)cell * np3 + i];
-  __syncthreads();
-  T acc[16];
-#pragma unroll
-  for (int b = 0; b < 16; ++b) acc[b] = T(0);
-  constexpr int RU = 4;
-  for (int n0 = sl; n0 < np3; n0 += RU * rs) {
-    T xs[RU];
-#pragma unroll
-    for (int u = 0; u < RU; ++u) {
-      const int node = n0 + u * rs;
-      xs[u] = (node < np3 && act) ? X[(int64_t)ds[node] * s.ncols + col] : T(0);
-    }
-#pragma unroll
-    for (int u = 0; u < RU; ++u) {
-      const int node = n0 + u * rs;
-      if (node >= np3) break;
-#pragma unroll
-      for (int b = 0; b < 16; ++b)
-        if (b < n_proj) acc[b] = fma(Fs[b * np3 + node], xs[u], acc[b]);
-    }
-  }
-#pragma unroll
-  for (int b = 0; b < 16; ++b)
-    if (b < n_proj) red[((size_t)sl * n_proj + b) * cw + lc] = acc[b];
-  __syncthreads();
-  T* part = static_cast<T*>(s.part);
-  for (int idx = threadIdx.x; idx < n_proj * cw; idx += kBatchNT) {
-    const int b = idx / cw, c = idx % cw;
-    T v = red[(size_t)b * cw + c];
-    for (int k = 1; k < rs; ++k) v += red[((size_t)k * n_proj + b) * cw + c];
-    if (col0 + c < s.ncols) part[((int64_t)pr * n_proj + b) * s.ncols + col0 + c] = v;
-  }
-}
-
-// Q[a][b][col] = h[a][b] * sum over the pairs of atom a, in pair order, of part[pr][b][col]
-template <typename T>
-__device__ void sum_item(const BatchSys& s, int a, int col0, int cw) {
-  const T* part = static_cast<const T*>(s.part);
-  const T* h = static_cast<const T*>(s.h);
-  T* Q = static_cast<T*>(s.Q);
-  for (int idx = threadIdx.x; idx < s.n_proj * cw; idx += kBatchNT) {
-    const int b = idx / cw, col = col0 + idx % cw;
-    if (col >= s.ncols) continue;
-    T v = T(0);
-    for (int pr = s.atom_pair_ptr[a]; pr < s.atom_pair_ptr[a + 1]; ++pr)
-      v += part[((int64_t)pr * s.n_proj + b) * s.ncols + col];
-    Q[((int64_t)a * s.n_proj + b) * s.ncols + col] = v * h[a * s.n_proj + b];
-  }
-}
-
-template <typename T, int P, int CFG>
-__device__ __forceinline__ void local_cells(const BatchParams& bp, const BatchSys& s, const EOTables<T>& tb, int c0,
-                                            int nc, int col0, unsigned char* smem) {
-  constexpr int NQ = P + 1;
-  const SysArgs<T> a = sys_args<T>(s);
-  for (int k = 0; k < nc; ++k)
-    cell_tile<T, P + 1, NQ, cfg_vt<NQ>(CFG), false, kBatchNT>(a, tb, s.colour_cells[c0 + k], col0, smem);
-}
-
-template <typename T>
-__device__ __forceinline__ void local_item(const BatchParams& bp, const BatchSys& s, const EOTables<T>* tabs, int c0,
-                                           int nc, int col0, unsigned char* smem) {
-#define FEKS_LOCAL_CASE(P)                                                       \
-  case P:                                                                        \
-    if (s.cfg == 1)                                                              \
-      local_cells<T, P, 1>(bp, s, tabs[P], c0, nc, col0, smem);                  \
-    else                                                                         \
-      local_cells<T, P, 0>(bp, s, tabs[P], c0, nc, col0, smem);                  \
-    break;
-  switch (s.p) {
-    FEKS_LOCAL_CASE(4)
-    FEKS_LOCAL_CASE(5)
-    FEKS_LOCAL_CASE(6)
-    FEKS_LOCAL_CASE(7)
-    FEKS_LOCAL_CASE(8)
-    default: break;
-  }
-#undef FEKS_LOCAL_CASE
-}
-
-__device__ __forceinline__ int ld_acquire(const int* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-template <int MINB>
-__global__ void __launch_bounds__(kBatchNT, MINB) fe_batched_kernel(const __grid_constant__ BatchParams bp) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int s_base, s_stop;
-  for (;;) {
-    if (threadIdx.x == 0) {
-      s_base = atomicAdd(bp.queue, bp.depth);
-      s_stop = 0;
-    }
-    __syncthreads();
-    const int base = s_base;
-    if (base >= bp.n_items) break;
-    for (int it = base; it < base + bp.depth && it < bp.n_items; ++it) {
-      const int4 w = bp.items[it];
-      const int sidx = w.x & 0xff, kind = (w.x >> 8) & 0xff, phase = w.x >> 16;
-      const BatchSys& s = bp.sys[sidx];
-      if (phase > 0 && threadIdx.x == 0) {
-        const int* ctr = bp.done + sidx * kMaxPhase + phase - 1;
-        const int need = bp.need[sidx * kMaxPhase + phase - 1];
-        const long long t0 = clock64();
-        while (ld_acquire(ctr) < need) {
-          if (ld_acquire(bp.err) != 0 || clock64() - t0 > bp.wait_cycles) {
-            atomicExch(bp.err, 1);
-            s_stop = 1;
-            break;
-          }
-          __nanosleep(256);
-        }
-        __threadfence();
-      }
-      __syncthreads();
-      if (s_stop) return;   // bounded wait expired (or another CTA gave up): leave, the host reports it
-      if (kind == kItemZero) {
-        if (s.prec == FE_KS_F64)
-          zero_item<double>(s, w.y, w.w);
-        else
-          zero_item<float>(s, w.y, w.w);
-      } else if (kind == kItemPair) {
-        if (s.prec == FE_KS_F64)
-          pair_item<double>(s, w.y, w.z, w.w, smem);
-        else
-          pair_item<float>(s, w.y, w.z, w.w, smem);
-      } else if (kind == kItemSum) {
-        if (s.prec == FE_KS_F64)
-          sum_item<double>(s, w.y, w.z, w.w);
-        else
-          sum_item<float>(s, w.y, w.z, w.w);
-      } else {
-        if (s.prec == FE_KS_F64)
-          local_item<double>(bp, s, bp.t64, w.y, w.w, w.z, smem);
-        else
-          local_item<float>(bp, s, bp.t32, w.y, w.w, w.z, smem);
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(bp.done + sidx * kMaxPhase + phase, 1);
-      }
-    }
-  }
-}
-
-// Shared memory of one system's cell tile (host side of CellShape).
+// Shared memory of one system's cell item (host side of CellShape).
 template <typename T, int P>
 static size_t cell_bytes_p(int cfg) {
   constexpr int NQ = P + 1;
@@ -322,6 +51,25 @@ static size_t cell_bytes(int p, int cfg) {
 }
 static int vt_of(int p, int cfg) { return (p + 1 >= 7) ? (cfg ? 8 : 4) : (cfg ? 16 : 8); }
 
+static cudaError_t prepare_nt(int nt, size_t smem, int blocks_per_sm, int* per_sm) {
+  switch (nt) {
+    case 384: return batched_prepare<384>(smem, blocks_per_sm, per_sm);
+    case 512: return batched_prepare<512>(smem, blocks_per_sm, per_sm);
+    case 672: return batched_prepare<672>(smem, blocks_per_sm, per_sm);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+static cudaError_t launch_nt(int nt, const BatchParams& P, int grid, size_t smem, int blocks_per_sm,
+                             cudaStream_t s) {
+  switch (nt) {
+    case 384: return batched_launch<384>(P, grid, smem, blocks_per_sm, s);
+    case 512: return batched_launch<512>(P, grid, smem, blocks_per_sm, s);
+    case 672: return batched_launch<672>(P, grid, smem, blocks_per_sm, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 }  // namespace feks
 
 using namespace feks;
@@ -334,6 +82,7 @@ struct fe_ks_batch {
   int cells_per_item = 1;
   int depth = 1;
   int blocks_per_sm = 1;     // 1: registers for every variant; 2: two CTAs per SM, some spills
+  int nt = kBatchThreads[0]; // threads per CTA (one of kBatchThreads)
   double wait_seconds = 2.0;
   int inject_missing = 0;
   int device = 0;
@@ -374,9 +123,9 @@ static fe_ks_status batch_build(fe_ks_batch* b) {
     }
     const bool nl = (c.terms & FE_KS_TERM_NL) && c.n_pairs > 0;
     if (nl) {
-      const int cw = batch_proj_cw(ncols);
-      smem = std::max(smem, b->prec[s] == FE_KS_F64 ? batch_proj_bytes<double>(c.n_proj, c.np3, cw)
-                                                    : batch_proj_bytes<float>(c.n_proj, c.np3, cw));
+      const int cw = batch_proj_cw(ncols, b->nt);
+      smem = std::max(smem, b->prec[s] == FE_KS_F64 ? batch_proj_bytes<double>(c.n_proj, c.np3, cw, b->nt)
+                                                    : batch_proj_bytes<float>(c.n_proj, c.np3, cw, b->nt));
       for (int64_t pr = 0; pr < c.n_pairs; ++pr)
         for (int col = 0; col < ncols; col += cw) {
           per_phase[0].push_back(make_int4(s | (kItemPair << 8), (int)pr, col, cw));
@@ -410,14 +159,11 @@ static fe_ks_status batch_build(fe_ks_batch* b) {
   cudaMemcpy(b->d_need, need.data(), need.size() * sizeof(int), cudaMemcpyHostToDevice);
   b->n_items = (int)items.size();
   b->smem = smem;
-  if (cudaFuncSetAttribute(fe_batched_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-      cudaFuncSetAttribute(fe_batched_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return fail(FE_KS_ERR_CUDA, "batched kernel shared memory");
   int per_sm = 0;
-  if (b->blocks_per_sm == 2)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fe_batched_kernel<2>, kBatchNT, smem);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fe_batched_kernel<1>, kBatchNT, smem);
+  if (prepare_nt(b->nt, smem, b->blocks_per_sm, &per_sm) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(FE_KS_ERR_CUDA, "batched kernel shared memory / occupancy");
+  }
   b->grid = std::max(1, per_sm) * b->sms;
   // kernel parameters
   BatchParams& P = b->host;
@@ -511,17 +257,23 @@ fe_ks_status fe_ks_batch_create(fe_ks_ctx* const* ctxs, int n_sys, const int64_t
 }
 
 fe_ks_status fe_ks_batch_configure(fe_ks_batch* b, const int* tile_config, int cells_per_item, int depth,
-                                   int blocks_per_sm, double wait_seconds, int inject_missing_item) {
+                                   int blocks_per_sm, double wait_seconds, int inject_missing_item,
+                                   int threads_per_block) {
   if (!b) return fail(FE_KS_ERR_ARG, "batch is NULL");
   if (blocks_per_sm != 1 && blocks_per_sm != 2) return fail(FE_KS_ERR_ARG, "blocks_per_sm must be 1 or 2");
-  b->blocks_per_sm = blocks_per_sm;
+  if (threads_per_block != 0 && threads_per_block != kBatchThreads[0] && threads_per_block != kBatchThreads[1] &&
+      threads_per_block != kBatchThreads[2])
+    return fail(FE_KS_ERR_ARG, "threads_per_block must be 0 (default), 384, 512 or 672");
   if (cells_per_item < 1 || cells_per_item > 64 || depth < 1 || depth > 16 || !(wait_seconds > 0))
     return fail(FE_KS_ERR_ARG, "cells_per_item in 1..64, depth in 1..16, wait_seconds > 0");
   if (tile_config)
     for (size_t s = 0; s < b->ctxs.size(); ++s) {
       if (tile_config[s] < 0 || tile_config[s] > 1) return fail(FE_KS_ERR_ARG, "tile_config must be 0 or 1");
-      b->cfg[s] = tile_config[s];
     }
+  if (tile_config)
+    for (size_t s = 0; s < b->ctxs.size(); ++s) b->cfg[s] = tile_config[s];
+  b->blocks_per_sm = blocks_per_sm;
+  if (threads_per_block) b->nt = threads_per_block;
   b->cells_per_item = cells_per_item;
   b->depth = depth;
   b->wait_seconds = wait_seconds;
@@ -540,11 +292,7 @@ fe_ks_status fe_ks_batch_apply(fe_ks_batch* b, const void* const* X, void* const
   }
   if (cudaMemsetAsync(b->d_state, 0, sizeof(int) * (2 + kMaxSys * kMaxPhase), s) != cudaSuccess)
     return fail(FE_KS_ERR_CUDA, "reset of the batch counters failed");
-  if (b->blocks_per_sm == 2)
-    fe_batched_kernel<2><<<b->grid, kBatchNT, b->smem, s>>>(P);
-  else
-    fe_batched_kernel<1><<<b->grid, kBatchNT, b->smem, s>>>(P);
-  cudaError_t err = cudaGetLastError();
+  cudaError_t err = launch_nt(b->nt, P, b->grid, b->smem, b->blocks_per_sm, s);
   if (err != cudaSuccess) return fail(FE_KS_ERR_CUDA, std::string("batched kernel: ") + cudaGetErrorString(err));
   return FE_KS_OK;
 }

@@ -77,7 +77,7 @@ def _load():
     lib.fe_ks_colour_cells.argtypes = [i64, i32, i64, vp, vp, P(i32)]
     lib.fe_ks_batch_create.argtypes = [P(vp), ctypes.c_int, P(i64), P(ctypes.c_int), P(vp)]
     lib.fe_ks_batch_configure.argtypes = [vp, P(ctypes.c_int), ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                          ctypes.c_double, ctypes.c_int]
+                                          ctypes.c_double, ctypes.c_int, ctypes.c_int]
     lib.fe_ks_batch_apply.argtypes = [vp, P(vp), P(vp), vp]
     lib.fe_ks_batch_status.argtypes = [vp]
     lib.fe_ks_batch_info.argtypes = [vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_size_t)]
@@ -234,10 +234,10 @@ def fe_ks_batch_create(ctxs, n_v, precision):
 
 
 def fe_ks_batch_configure(batch, tile_config=None, cells_per_item=1, depth=1, wait_seconds=2.0,
-                          inject_missing_item=False, blocks_per_sm=1):
+                          inject_missing_item=False, blocks_per_sm=1, threads=0):
     tc = None if tile_config is None else (ctypes.c_int * len(tile_config))(*tile_config)
     _check(_lib.fe_ks_batch_configure(batch, tc, cells_per_item, depth, blocks_per_sm, wait_seconds,
-                                      int(inject_missing_item)))
+                                      int(inject_missing_item), threads))
 
 
 def fe_ks_batch_apply(batch, Xs, Ys, stream=None):

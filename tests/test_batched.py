@@ -71,6 +71,62 @@ def test_batched_equals_individual_applications(batch_setup, tile, cells, depth,
     _check(Ys, refs)
 
 
+@pytest.mark.parametrize("threads,occ", [(384, 1), (512, 1), (512, 2), (672, 1)])
+@pytest.mark.parametrize("cells", [1, 2])
+def test_batched_block_sizes(batch_setup, threads, occ, cells):
+    """Every block size the kernel is built for (the projection items' column width must
+    divide it: 672 = 21 x 32), mixed tile configurations, ragged column counts."""
+    wls, hps, ctxs, Xs, Ys, refs, b = batch_setup
+    tiles = [(s // 2) % 2 for s in range(6)]
+    fk.fe_ks_batch_configure(b, tiles, cells, 2, 2.0, False, blocks_per_sm=occ, threads=threads)
+    for Y in Ys:
+        Y.fill_(float("nan"))
+    fk.fe_ks_batch_apply(b, Xs, Ys, torch.cuda.current_stream().cuda_stream)
+    fk.fe_ks_batch_status(b)
+    _check(Ys, refs)
+    fk.fe_ks_batch_configure(b, [0] * 6, 1, 1, 2.0, False, threads=384)
+
+
+def test_aligned_rows_and_wide_projection_items():
+    """Column counts that are multiples of 4 and above 32 (64-column projection items),
+    every block size, against each system's own fe_ks_apply."""
+    stream = torch.cuda.current_stream().cuda_stream
+    spec = [(5, 2, 8, fk.FE_KS_F32), (8, 2, 48, fk.FE_KS_F32), (6, 2, 40, fk.FE_KS_F64)]
+    wls = [Workload(f"a{s}", L=6.0, n=n, p=p, nq=p + 1, n_v=nv, gga=True, n_atoms=2, seed=7500 + s)
+           for s, (p, n, nv, _) in enumerate(spec)]
+    hps = [HostProblem(wl) for wl in wls]   # owns the arrays behind each problem struct
+    ctxs = [fk.fe_ks_setup(hp.struct, fk.TERM_ALL, wl.n_v, stream) for hp, wl in zip(hps, wls)]
+    try:
+        Xs, Ys, refs = [], [], []
+        for wl, ctx, (_, _, _, pr) in zip(wls, ctxs, spec):
+            X = torch.from_numpy(trial_vectors(wl)).cuda().to(torch_dtype(pr, False))
+            R = torch.empty_like(X)
+            fk.fe_ks_apply(ctx, X, R, wl.n_v, pr)
+            Xs.append(X)
+            Ys.append(torch.full_like(X, float("nan")))
+            refs.append(R)
+        b = fk.fe_ks_batch_create(ctxs, [wl.n_v for wl in wls], [sp[3] for sp in spec])
+        try:
+            for threads, cells in ((384, 1), (512, 3), (672, 2)):
+                for Y in Ys:
+                    Y.fill_(float("nan"))
+                fk.fe_ks_batch_configure(b, [1, 1, 0], cells, 2, 2.0, False, threads=threads)
+                fk.fe_ks_batch_apply(b, Xs, Ys, stream)
+                fk.fe_ks_batch_status(b)
+                for (_, _, _, pr), Y, R in zip(spec, Ys, refs):
+                    err = rel_err_cols(Y.double().cpu().numpy(), R.double().cpu().numpy())
+                    assert err <= TOL[pr], err
+            with pytest.raises(fk.FeKsError, match="ERR_ARG"):
+                fk.fe_ks_batch_configure(b, [2, 0, 0], 1, 1, 2.0, False)    # tile configurations 0 / 1
+            with pytest.raises(fk.FeKsError, match="ERR_ARG"):
+                fk.fe_ks_batch_configure(b, [0, 0, 0], 1, 1, 2.0, False, threads=256)
+        finally:
+            fk.fe_ks_batch_destroy(b)
+    finally:
+        for c in ctxs:
+            fk.fe_ks_destroy(c)
+
+
 def test_batched_fp64_systems_match_oracle(batch_setup):
     wls, hps, ctxs, Xs, Ys, refs, b = batch_setup
     fk.fe_ks_batch_configure(b, [0] * 6, 1, 1, 2.0, False)

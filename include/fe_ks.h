@@ -168,6 +168,25 @@ fe_ks_status fe_ks_apply_scaled(fe_ks_ctx* ctx, const void* X, void* Y, int64_t 
                                 int precision);
 
 /*
+ * Y = H X with X and Y in HOST memory ([m][n_v] row-major, the precision's
+ * storage type; pinned memory lets the copies run asynchronously).  The call
+ * enqueues, and returns without waiting: copy X in on the context's copy-in
+ * stream, fe_ks_apply on the context's stream, copy Y out on its copy-out
+ * stream.  Consecutive calls alternate between two slots of the device
+ * workspace, so call k's copies overlap the application of call k +- 1.
+ * work: device memory of fe_ks_apply_host_workspace bytes (two slots of X and
+ * Y), 256-byte aligned, owned by the caller and reused across calls.
+ * The caller keeps X_host unchanged and leaves Y_host unread until
+ * fe_ks_host_wait returns; that call blocks until every result enqueued so
+ * far is in host memory.  The first call creates the two copy streams.
+ * Errors as fe_ks_apply; FE_KS_ERR_ARG for a short or misaligned workspace.
+ */
+fe_ks_status fe_ks_apply_host_workspace(const fe_ks_ctx* ctx, int64_t n_v, int precision, size_t* bytes);
+fe_ks_status fe_ks_apply_host(fe_ks_ctx* ctx, const void* X_host, void* Y_host, int64_t n_v, int precision,
+                              void* work, size_t work_bytes);
+fe_ks_status fe_ks_host_wait(fe_ks_ctx* ctx);
+
+/*
  * Residual-based Chebyshev filter (R-ChFSI, Algorithm 4) of degree `degree`
  * on the standard form Hs = D^{-1/2} H D^{-1/2}: D is the GLL-lumped mass
  * (Algorithm 4's diagonal approximation of M), so in scaled variables M and

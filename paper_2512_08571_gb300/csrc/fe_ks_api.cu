@@ -558,6 +558,18 @@ fe_ks_status fe_ks_setup(const fe_ks_problem* prob, int terms_mask, int64_t n_v_
 
 void fe_ks_destroy(fe_ks_ctx* ctx) {
   if (!ctx) return;
+  Ctx& hc = ctx->c;
+  if (hc.hs_in) {
+    cudaStreamSynchronize(hc.hs_in);
+    cudaStreamSynchronize(hc.hs_out);
+    for (int b = 0; b < 2; ++b) {
+      cudaEventDestroy(hc.h_in[b]);
+      cudaEventDestroy(hc.h_done[b]);
+      cudaEventDestroy(hc.h_out[b]);
+    }
+    cudaStreamDestroy(hc.hs_in);
+    cudaStreamDestroy(hc.hs_out);
+  }
   for (void* p : ctx->c.allocations) cudaFree(p);
   for (cudaEvent_t e : ctx->c.ev_pool) cudaEventDestroy(e);
   for (auto& r : ctx->c.ev_rec)
@@ -922,6 +934,83 @@ fe_ks_status fe_ks_apply_scaled(fe_ks_ctx* ctx, const void* X, void* Y, int64_t 
   if (precision == FE_KS_BF16) return apply_impl<float>(ctx, X, Y, n_v, true, 1);
   if (precision == FE_KS_F16) return apply_impl<float>(ctx, X, Y, n_v, true, 2);
   return fail(FE_KS_ERR_UNSUPPORTED, "unknown precision");
+}
+
+// ---- host buffers: copy in, apply, copy out, pipelined across calls ----
+// Storage bytes of one [m][n_v] block in the given precision (0: unknown precision).
+static size_t host_block_bytes(const Ctx& c, int64_t n_v, int precision) {
+  const size_t esz = (precision == FE_KS_F64 || precision == FE_KS_F64E) ? 8
+                     : (precision == FE_KS_F32 || precision == FE_KS_BF16 || precision == FE_KS_F16) ? 4
+                                                                                                       : 0;
+  return ((size_t)c.m * n_v * (c.cplx ? 2 : 1) * esz + 255) & ~(size_t)255;
+}
+
+fe_ks_status fe_ks_apply_host_workspace(const fe_ks_ctx* ctx, int64_t n_v, int precision, size_t* bytes) {
+  if (!ctx || !bytes) return fail(FE_KS_ERR_ARG, "NULL argument");
+  const size_t blk = host_block_bytes(ctx->c, n_v, precision);
+  if (!blk) return fail(FE_KS_ERR_UNSUPPORTED, "unknown precision");
+  *bytes = 4 * blk;   // two slots of (X, Y)
+  return FE_KS_OK;
+}
+
+fe_ks_status fe_ks_apply_host(fe_ks_ctx* ctx, const void* X_host, void* Y_host, int64_t n_v, int precision,
+                              void* work, size_t work_bytes) {
+  set_error("");
+  if (!ctx || !X_host || !Y_host || !work) return fail(FE_KS_ERR_ARG, "NULL argument");
+  Ctx& c = ctx->c;
+  if (n_v < 1 || n_v > c.n_v_max) return fail(FE_KS_ERR_ARG, "n_v must be in 1..n_v_max");
+  const size_t blk = host_block_bytes(c, n_v, precision);
+  if (!blk) return fail(FE_KS_ERR_UNSUPPORTED, "unknown precision");
+  if (work_bytes < 4 * blk) return fail(FE_KS_ERR_ARG, "workspace smaller than fe_ks_apply_host_workspace");
+  if ((uintptr_t)work % 256) return fail(FE_KS_ERR_ARG, "workspace must be 256-byte aligned");
+  if (!c.hs_in) {   // first call: the context's copy streams and slot events
+    if (cudaStreamCreateWithFlags(&c.hs_in, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c.hs_out, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(FE_KS_ERR_CUDA, "copy stream creation failed");
+    for (int b = 0; b < 2; ++b)
+      if (cudaEventCreateWithFlags(&c.h_in[b], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&c.h_done[b], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&c.h_out[b], cudaEventDisableTiming) != cudaSuccess)
+        return fail(FE_KS_ERR_CUDA, "event creation failed");
+    for (int b = 0; b < 2; ++b) {   // every slot starts free
+      cudaEventRecord(c.h_done[b], c.hs_in);
+      cudaEventRecord(c.h_out[b], c.hs_out);
+    }
+  }
+  const int b = c.h_slot;
+  char* base = static_cast<char*>(work) + (size_t)b * 2 * blk;
+  void* Xd = base;
+  void* Yd = base + blk;
+  const size_t bytes = (size_t)c.m * n_v * (c.cplx ? 2 : 1) *
+                       ((precision == FE_KS_F64 || precision == FE_KS_F64E) ? 8 : 4);
+  // copy in once the slot's previous application has read its X
+  cudaStreamWaitEvent(c.hs_in, c.h_done[b], 0);
+  if (cudaMemcpyAsync(Xd, X_host, bytes, cudaMemcpyHostToDevice, c.hs_in) != cudaSuccess)
+    return fail(FE_KS_ERR_CUDA, "host-to-device copy failed");
+  cudaEventRecord(c.h_in[b], c.hs_in);
+  // apply once X is in and the slot's previous Y has been copied out
+  cudaStreamWaitEvent(c.stream, c.h_in[b], 0);
+  cudaStreamWaitEvent(c.stream, c.h_out[b], 0);
+  fe_ks_status st = fe_ks_apply(ctx, Xd, Yd, n_v, precision);
+  if (st != FE_KS_OK) return st;
+  cudaEventRecord(c.h_done[b], c.stream);
+  // copy out after the application
+  cudaStreamWaitEvent(c.hs_out, c.h_done[b], 0);
+  if (cudaMemcpyAsync(Y_host, Yd, bytes, cudaMemcpyDeviceToHost, c.hs_out) != cudaSuccess)
+    return fail(FE_KS_ERR_CUDA, "device-to-host copy failed");
+  cudaEventRecord(c.h_out[b], c.hs_out);
+  c.h_slot = 1 - b;
+  return FE_KS_OK;
+}
+
+fe_ks_status fe_ks_host_wait(fe_ks_ctx* ctx) {
+  if (!ctx) return fail(FE_KS_ERR_ARG, "ctx is NULL");
+  Ctx& c = ctx->c;
+  if (!c.hs_in) return FE_KS_OK;
+  if (cudaStreamSynchronize(c.hs_in) != cudaSuccess || cudaStreamSynchronize(c.stream) != cudaSuccess ||
+      cudaStreamSynchronize(c.hs_out) != cudaSuccess)
+    return fail(FE_KS_ERR_CUDA, std::string("host pipeline: ") + cudaGetErrorString(cudaGetLastError()));
+  return FE_KS_OK;
 }
 
 }  // extern "C"

@@ -137,6 +137,11 @@ struct Ctx {
   uint2* tc_fpack = nullptr;       // F as expansion B fragments, BF16 (when the nonlocal term is present)
   uint2* tc_fpack16 = nullptr;     // the same in FP16
   std::vector<void*> allocations;
+  // host-buffer pipeline (fe_ks_apply_host): copy-in and copy-out streams and,
+  // per workspace slot, events for "X copied in", "applied", "Y copied out"
+  cudaStream_t hs_in = nullptr, hs_out = nullptr;
+  cudaEvent_t h_in[2] = {}, h_done[2] = {}, h_out[2] = {};
+  int h_slot = 0;
   // profiling: events recorded per application (start, after fill, after projection, after local)
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;

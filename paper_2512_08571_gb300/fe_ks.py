@@ -51,6 +51,9 @@ def _load():
     lib.fe_ks_setup.argtypes = [P(fe_ks_problem), ctypes.c_int, i64, vp, P(vp)]
     lib.fe_ks_apply.argtypes = [vp, vp, vp, i64, ctypes.c_int]
     lib.fe_ks_apply_scaled.argtypes = [vp, vp, vp, i64, ctypes.c_int]
+    lib.fe_ks_apply_host_workspace.argtypes = [vp, i64, ctypes.c_int, P(ctypes.c_size_t)]
+    lib.fe_ks_apply_host.argtypes = [vp, vp, vp, i64, ctypes.c_int, vp, ctypes.c_size_t]
+    lib.fe_ks_host_wait.argtypes = [vp]
     lib.fe_ks_dinv_sqrt.argtypes = [vp]
     lib.fe_ks_dinv_sqrt.restype = vp
     lib.fe_ks_info.argtypes = [vp, P(i64), P(i64), P(i32), P(i32), P(i32), P(i64)]
@@ -91,6 +94,7 @@ def _load():
     lib.fe_ks_destroy.argtypes = [vp]
     lib.fe_ks_destroy.restype = None
     for name in ("fe_ks_quadrature_points", "fe_ks_setup", "fe_ks_apply", "fe_ks_apply_scaled",
+                 "fe_ks_apply_host_workspace", "fe_ks_apply_host", "fe_ks_host_wait",
                  "fe_ks_info", "fe_ks_set_stream", "fe_ks_set_profiling", "fe_ks_read_profile",
                  "fe_ks_measure_fma_peak", "fe_ks_cheb_filter_workspace", "fe_ks_cheb_filter",
                  "fe_ks_nonlocal_apply_static", "fe_ks_tune", "fe_ks_set_config", "fe_ks_batch_create",
@@ -143,6 +147,21 @@ def fe_ks_apply(ctx, X, Y, n_v, precision):
 
 def fe_ks_apply_scaled(ctx, X, Y, n_v, precision):
     _check(_lib.fe_ks_apply_scaled(ctx, _ptr(X), _ptr(Y), n_v, precision))
+
+
+def fe_ks_apply_host_workspace(ctx, n_v, precision):
+    out = ctypes.c_size_t()
+    _check(_lib.fe_ks_apply_host_workspace(ctx, n_v, precision, ctypes.byref(out)))
+    return out.value
+
+
+def fe_ks_apply_host(ctx, X_host, Y_host, n_v, precision, work, work_bytes):
+    """Enqueue Y_host = H X_host (host arrays / CPU tensors); results are final after fe_ks_host_wait."""
+    _check(_lib.fe_ks_apply_host(ctx, _ptr(X_host), _ptr(Y_host), n_v, precision, _ptr(work), work_bytes))
+
+
+def fe_ks_host_wait(ctx):
+    _check(_lib.fe_ks_host_wait(ctx))
 
 
 def fe_ks_cheb_filter_workspace(ctx, n_v, precision):

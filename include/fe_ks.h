@@ -67,8 +67,9 @@ typedef enum {
                                   projections and scatter in FP32, the nonlocal expansion
                                   as BF16 MMAs (apply / apply_scaled / tune / filter) */
   FE_KS_F16 = 4                /* as FE_KS_BF16 with FP16 operands (8x the precision): each
-                                  gathered cell tile is scaled by a power of two so that its
-                                  largest entry is below 1/16, and unscaled at the scatter */
+                                  column of a gathered cell tile is scaled by a power of two
+                                  so that its largest entry is below 1/16, and unscaled at
+                                  the scatter */
 } fe_ks_precision;
 
 /* Terms of H that an application includes (terms_mask of fe_ks_setup). */

@@ -37,7 +37,14 @@ struct Num<ff2> {
   static __device__ __forceinline__ ff2 zero() { return ff_make(0.f, 0.f); }
   static __device__ __forceinline__ ff2 one() { return ff_make(1.f, 0.f); }
   static __device__ __forceinline__ ff2 in(double x) { return ff_split_bits(x); }
-  static __device__ __forceinline__ void add_to(double* y, ff2 v) { *y += f2d_bits(v.hi) + f2d_bits(v.lo); }
+  // Two fire-and-forget reductions (performed in the L2, in issue order for the
+  // one address) instead of a load, two FP64 adds and a store: on this part the
+  // FP64 adds cost as much issue time as the whole pair-of-floats tile work.
+  // The scatter is colour-exclusive, so the result stays deterministic.
+  static __device__ __forceinline__ void add_to(double* y, ff2 v) {
+    atomicAdd(y, f2d_bits(v.hi));
+    atomicAdd(y, f2d_bits(v.lo));
+  }
   static __device__ __forceinline__ ff2 shfl1(ff2 v) {
     return ff_make(__shfl_xor_sync(0xffffffffu, v.hi, 1), __shfl_xor_sync(0xffffffffu, v.lo, 1));
   }

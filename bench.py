@@ -131,6 +131,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(ms, world, dev):
+    """The slowest rank's time: every rank takes part (one all-reduce with MAX; NCCL on the
+    GPUs, gloo on the CPU).  With one rank the value is returned as it is."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_rank, world, ms):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world / (ms * 1e-3)
+
+
 def alg_flops(wl, n_pairs, n_v):
     """Paper's operation count (eq. flopRealMF / flopComplexMF) with n_s read as the
     number of (projector, cell) incidences, split into the fused local kernel's
@@ -235,14 +252,10 @@ def run_native(args, wl, rank, world):
         barrier()
         fk.fe_ks_set_profiling(ctx, False)
         prof = fk.fe_ks_read_profile(ctx)
-        ms = e0.elapsed_time(e1) / steps
-        if world > 1:
-            t = torch.tensor([ms], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1) / steps, world, dev)
         local_ms, local_n = prof["local"]
         achieved = local_flops * steps / (local_ms * 1e-3) if local_ms > 0 else None
-        out = dict(ms=ms, value=units * world / (ms * 1e-3), prof=prof, clocks=clk.summary(),
+        out = dict(ms=ms, value=whole_job_value(units, world, ms), prof=prof, clocks=clk.summary(),
                    tile_config=best, tune_ms=[round(t, 3) for t in tune_ms],
                    achieved=achieved, local_launch_ms=local_ms / max(local_n, 1),
                    launches=int(prof["proj"][1] + prof["local"][1]))
@@ -290,11 +303,7 @@ def run_native(args, wl, rank, world):
         for _ in range(ksteps):
             fk.fe_ks_apply_host(ctx, Xh, Yh, n_v, fk.FE_KS_F64, work, wb)
         fk.fe_ks_host_wait(ctx)
-        ms_e2e = (time.perf_counter() - t0) * 1e3 / ksteps
-        if world > 1:
-            t = torch.tensor([ms_e2e], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_e2e = float(t.item())
+        ms_e2e = max_over_ranks((time.perf_counter() - t0) * 1e3 / ksteps, world, dev)
         del work
         torch.cuda.empty_cache()
         # the parts of one step, run one after another (CUDA events on one stream; the
@@ -312,7 +321,7 @@ def run_native(args, wl, rank, world):
             ev[3].record(stream)
             torch.cuda.synchronize()
         nbytes = Xh.numel() * Xh.element_size()
-        e2e = {"value": units * world / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+        e2e = {"value": whole_job_value(units, world, ms_e2e), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "ms_per_step": ms_e2e, "steps": ksteps,
                "api": "fe_ks_apply_host (pinned host X, Y; copies of one step overlap the next step's apply)",
                "one_step_serial_ms": {"h2d": ev[0].elapsed_time(ev[1]), "apply": ev[1].elapsed_time(ev[2]),

@@ -175,7 +175,7 @@ fe_ks_status fe_ks_cm_create(fe_ks_ctx* ctx, int precision, int64_t n_v_max, fe_
   double* Ych = nullptr;
   int* dis = nullptr;
   int* iota = nullptr;
-  auto bad = [&](const char* what) {
+  auto bad = [&](const char* what, fe_ks_status code = FE_KS_ERR_OOM) {
     cudaFree(Xid);
     cudaFree(Ych);
     cudaFree(dis);
@@ -184,7 +184,7 @@ fe_ks_status fe_ks_cm_create(fe_ks_ctx* ctx, int precision, int64_t n_v_max, fe_
     cudaEventDestroy(e1);
     cm_free(cm);
     cudaGetLastError();
-    return fail(FE_KS_ERR_OOM, std::string("cell-matrix setup: ") + what);
+    return fail(code, std::string("cell-matrix setup: ") + what);
   };
   const size_t hbytes = (size_t)E * np3 * np3 * esz;
   if (cudaMalloc(&cm->H, hbytes) != cudaSuccess) return bad("cell matrices");
@@ -214,7 +214,7 @@ fe_ks_status fe_ks_cm_create(fe_ks_ctx* ctx, int precision, int64_t n_v_max, fe_
     lp.cells = iota + e0c;
     lp.n_cells = nc;
     cudaError_t err = launch_local<double, double>(c, lp, s);
-    if (err != cudaSuccess) return bad(cudaGetErrorString(err));
+    if (err != cudaSuccess) return bad(cudaGetErrorString(err), FE_KS_ERR_CUDA);
     if (precision == FE_KS_F32)
       k_cm_to_float<<<ew_grid((int64_t)nc * np3 * np3), 256, 0, s>>>(
           static_cast<float*>(cm->H) + (size_t)e0c * np3 * np3, Y, (int64_t)nc * np3 * np3);
@@ -239,7 +239,7 @@ fe_ks_status fe_ks_cm_create(fe_ks_ctx* ctx, int precision, int64_t n_v_max, fe_
   if (cudaMalloc(&cm->Xg, gbytes) != cudaSuccess || cudaMalloc(&cm->Yg, gbytes) != cudaSuccess ||
       cudaMalloc(&cm->ptrs, (size_t)3 * cm->max_cells * sizeof(void*)) != cudaSuccess)
     return bad("apply buffers");
-  if (cublasCreate(&cm->blas) != CUBLAS_STATUS_SUCCESS) return bad("cublasCreate");
+  if (cublasCreate(&cm->blas) != CUBLAS_STATUS_SUCCESS) return bad("cublasCreate", FE_KS_ERR_CUDA);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cm->bytes = hbytes + 2 * gbytes;

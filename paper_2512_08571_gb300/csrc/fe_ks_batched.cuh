@@ -3,8 +3,6 @@
 // translation unit per block size (fe_ks_batched_k.cu) and, for the shared
 // structures and the host-side size helpers, by fe_ks_batched.cu.
 #pragma once
-#include <type_traits>
-
 #include "fe_ks_local.cuh"
 
 namespace feks {

@@ -151,8 +151,12 @@ def whole_job_value(units_per_rank, world, ms):
 def alg_flops(wl, n_pairs, n_v):
     """Paper's operation count (eq. flopRealMF / flopComplexMF) with n_s read as the
     number of (projector, cell) incidences, split into the fused local kernel's
-    share (cell terms + expansion F Delta T3) and the projection kernel's share."""
+    share (cell terms + expansion F Delta T3) and the projection kernel's share.
+    The formulas' vector count is the batch product b2 nb2 nb1, i.e. real columns:
+    a complex vector counts twice (its real and imaginary batches, Sec. 4.2)."""
     n_p, n_q = wl.p + 1, wl.nq
+    if wl.complex:
+        n_v = 2 * n_v
     npo, nqo = n_p // 2, n_q // 2
     s = n_p * n_p + n_p * n_q + n_q * n_q
     if wl.complex:

@@ -3,9 +3,11 @@
 TEST INFRASTRUCTURE (oracle): see ``oracle/__init__.py``.
 
 Per-stage counts and totals of Sec. 5.4 (eq. flopRealMF, eq. flopComplexMF,
-eq. flopRealCM, eq. flopComplexCM), with b2 * nb2 * nb1 written as the number of
-vectors n_v (real columns; for the complex operator the paper's formulas count
-complex vectors and the stage terms already include the complex arithmetic).
+eq. flopRealCM, eq. flopComplexCM), with the batch product b2 * nb2 * nb1 (and
+b0 * nb0 for the cell-matrix counts) written as n_v.  That product is the number
+of REAL columns: in the multilevel layout of Sec. 4.2 a complex multivector keeps
+its real and imaginary parts in separate level-2 batches (b1 = c b2, level-0
+batch c N_v), so for a complex operator n_v = 2 x the number of complex vectors.
 n_s is the total number of projectors, E the number of cells.
 """
 

@@ -169,7 +169,7 @@ fe_ks_status fe_ks_apply_scaled(fe_ks_ctx* ctx, const void* X, void* Y, int64_t 
                                 int precision);
 
 /*
- * Y = H X with X and Y in HOST memory ([m][n_v] row-major, the precision's
+ * Y = H X (eq. HX) with X and Y in HOST memory ([m][n_v] row-major, the precision's
  * storage type; pinned memory lets the copies run asynchronously).  The call
  * enqueues, and returns without waiting: copy X in on the context's copy-in
  * stream, fe_ks_apply on the context's stream, copy Y out on its copy-out

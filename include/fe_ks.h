@@ -436,12 +436,18 @@ fe_ks_status fe_ks_gemm_f64(int trans_a, int trans_b, int64_t m, int64_t n, int6
  *                    the m dimension is split in chunks of 8192 rows whose
  *                    partial sums are added in a fixed order (deterministic);
  *                    work: device buffer of fe_ks_gram_ff_workspace bytes.
+ *   fe_ks_gram_ff_sym: the same for n1 = n2 = n when Y^T Z is known to be
+ *                    symmetric: only the 64 x 64 tiles on or above the
+ *                    diagonal are computed and the result is mirrored
+ *                    (exactly symmetric; same workspace).
  *   fe_ks_rotate_ff: X[m][k] = Y[m][n] E[n][k], all row-major.
  * Real operators only; stream-ordered on cuda_stream; no allocation.
  */
 fe_ks_status fe_ks_gram_ff_workspace(int64_t m, int n1, int n2, size_t* bytes);
 fe_ks_status fe_ks_gram_ff(const double* Y, const double* Z, double* C, int64_t m, int n1, int n2, void* work,
                            size_t work_bytes, void* cuda_stream);
+fe_ks_status fe_ks_gram_ff_sym(const double* Y, const double* Z, double* C, int64_t m, int n, void* work,
+                               size_t work_bytes, void* cuda_stream);
 fe_ks_status fe_ks_rotate_ff(const double* Y, const double* E, double* X, int64_t m, int n, int k,
                              void* cuda_stream);
 

@@ -105,14 +105,14 @@ class RChFSI:
         A Householder QR is used instead when S is too ill-conditioned for Cholesky.
         """
         Y = Y.contiguous()
-        S = self._gram(Y, self.apply_metric(Y))
+        S = self._gram(Y, self.apply_metric(Y), symmetric=True)
         S = 0.5 * (S + S.conj().T)
         L, info = torch.linalg.cholesky_ex(S)
         d = torch.real(torch.diagonal(L)) if int(info.item()) == 0 else None
         if d is None or float(d.min()) <= 1e-6 * float(d.max()):
             return self._rayleigh_ritz_qr(Y)
         HY = self.apply_op(Y, self.tmp)
-        A = self._gram(Y, HY)
+        A = self._gram(Y, HY, symmetric=True)
         T1 = torch.linalg.solve_triangular(L, A, upper=False)
         B = torch.linalg.solve_triangular(L, T1.conj().T, upper=False).conj().T
         B = 0.5 * (B + B.conj().T)
@@ -120,11 +120,16 @@ class RChFSI:
         E = torch.linalg.solve_triangular(L.conj().T, W, upper=True)
         return lam.to(torch.float64).contiguous(), self._rotate(Y, E)
 
-    def _gram(self, Y, Z):
+    def _gram(self, Y, Z, symmetric=False):
+        """Y^H Z; symmetric=True when the product is known to be Hermitian (Y^H M Y, Y^H H Y):
+        the pair-of-floats kernel then computes the tiles on and above the diagonal and
+        mirrors them.  (cuBLAS's one-triangle FP64 form, syrkx, measured slower than its
+        GEMM on this part, so the FP64 plan keeps the GEMM.)"""
+        st = torch.cuda.current_stream().cuda_stream
         if self.gemm_pairs:
-            return fk.fe_ks_gram_ff(Y, Z.contiguous(), stream=torch.cuda.current_stream().cuda_stream)
+            return fk.fe_ks_gram_ff(Y, Z.contiguous(), stream=st, symmetric=symmetric)
         if self.gemm_emulated:
-            return fk.row_gram(Y, Z, emulated=True, stream=torch.cuda.current_stream().cuda_stream)
+            return fk.row_gram(Y, Z, emulated=True, stream=st)
         return Y.conj().T @ Z
 
     def _rotate(self, Y, E):

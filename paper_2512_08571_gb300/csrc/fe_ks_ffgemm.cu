@@ -35,11 +35,15 @@ __device__ __forceinline__ void ff_mac(ff2& acc, ff2 a, ff2 b) {
 
 __device__ __forceinline__ void ff_renorm(ff2& acc) { acc = ff_fast_two_sum(acc.hi, acc.lo); }
 
-// partial[chunk][i][j] = sum over the chunk's rows r of Y[r][i] Z[r][j]
+// partial[chunk][i][j] = sum over the chunk's rows r of Y[r][i] Z[r][j].
+// upper: the result is known to be symmetric; only tiles on or above the
+// diagonal are computed (the reduction mirrors them).
 __global__ void __launch_bounds__(kGT) ff_gram_partial_kernel(const double* __restrict__ Y, const double* __restrict__ Z,
-                                                              double* __restrict__ part, int64_t m, int n1, int n2) {
+                                                              double* __restrict__ part, int64_t m, int n1, int n2,
+                                                              int upper) {
   __shared__ ff2 Ys[kGK][kGB];
   __shared__ ff2 Zs[kGK][kGB];
+  if (upper && blockIdx.y > blockIdx.x) return;   // whole CTA: below the diagonal
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   const int j0 = blockIdx.x * kGB, i0 = blockIdx.y * kGB;
   const int64_t r_begin = (int64_t)blockIdx.z * kGramChunk;
@@ -90,12 +94,20 @@ __global__ void __launch_bounds__(kGT) ff_gram_partial_kernel(const double* __re
     }
 }
 
-// C[i][j] = sum over chunks of partial[chunk][i][j], in chunk order
-__global__ void ff_gram_reduce_kernel(const double* __restrict__ part, double* __restrict__ C, int nchunks, int n1n2) {
+// C[i][j] = sum over chunks of partial[chunk][i][j], in chunk order (upper:
+// C[i][j] = C[j][i] = the sum at (min(i, j), max(i, j)), an entry of a tile on
+// or above the diagonal)
+__global__ void ff_gram_reduce_kernel(const double* __restrict__ part, double* __restrict__ C, int nchunks, int n1n2,
+                                      int n2, int upper) {
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n1n2; idx += gridDim.x * blockDim.x) {
+    int src = idx;
+    if (upper) {
+      const int i = idx / n2, j = idx % n2;
+      src = i <= j ? idx : j * n2 + i;
+    }
     double s = 0.0, c = 0.0;   // compensated (Kahan-Babuska) summation of the chunk partials
     for (int ch = 0; ch < nchunks; ++ch) {
-      const double v = part[(int64_t)ch * n1n2 + idx];
+      const double v = part[(int64_t)ch * n1n2 + src];
       const double t = s + v;
       c += (fabs(s) >= fabs(v)) ? (s - t) + v : (v - t) + s;
       s = t;
@@ -171,10 +183,11 @@ fe_ks_status fe_ks_gram_ff_workspace(int64_t m, int n1, int n2, size_t* bytes) {
   return FE_KS_OK;
 }
 
-fe_ks_status fe_ks_gram_ff(const double* Y, const double* Z, double* C, int64_t m, int n1, int n2, void* work,
-                           size_t work_bytes, void* cuda_stream) {
+static fe_ks_status gram_ff(const double* Y, const double* Z, double* C, int64_t m, int n1, int n2, void* work,
+                            size_t work_bytes, void* cuda_stream, int upper) {
   set_error("");
   if (!Y || !Z || !C || !work) return fail(FE_KS_ERR_ARG, "NULL argument");
+  if (upper && n1 != n2) return fail(FE_KS_ERR_ARG, "a symmetric Gram matrix is square");
   size_t need = 0;
   fe_ks_status st = fe_ks_gram_ff_workspace(m, n1, n2, &need);
   if (st != FE_KS_OK) return st;
@@ -184,12 +197,22 @@ fe_ks_status fe_ks_gram_ff(const double* Y, const double* Z, double* C, int64_t 
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   dim3 grid((n2 + kGB - 1) / kGB, (n1 + kGB - 1) / kGB, (unsigned)nch);
   double* part = static_cast<double*>(work);
-  ff_gram_partial_kernel<<<grid, kGT, 0, s>>>(Y, Z, part, m, n1, n2);
+  ff_gram_partial_kernel<<<grid, kGT, 0, s>>>(Y, Z, part, m, n1, n2, upper);
   const int nn = n1 * n2;
-  ff_gram_reduce_kernel<<<(nn + 255) / 256, 256, 0, s>>>(part, C, (int)nch, nn);
+  ff_gram_reduce_kernel<<<(nn + 255) / 256, 256, 0, s>>>(part, C, (int)nch, nn, n2, upper);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return fail(FE_KS_ERR_CUDA, std::string("Gram kernels: ") + cudaGetErrorString(err));
   return FE_KS_OK;
+}
+
+fe_ks_status fe_ks_gram_ff(const double* Y, const double* Z, double* C, int64_t m, int n1, int n2, void* work,
+                           size_t work_bytes, void* cuda_stream) {
+  return gram_ff(Y, Z, C, m, n1, n2, work, work_bytes, cuda_stream, 0);
+}
+
+fe_ks_status fe_ks_gram_ff_sym(const double* Y, const double* Z, double* C, int64_t m, int n, void* work,
+                               size_t work_bytes, void* cuda_stream) {
+  return gram_ff(Y, Z, C, m, n, n, work, work_bytes, cuda_stream, 1);
 }
 
 fe_ks_status fe_ks_rotate_ff(const double* Y, const double* E, double* X, int64_t m, int n, int k, void* cuda_stream) {

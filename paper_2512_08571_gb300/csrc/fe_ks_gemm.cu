@@ -52,3 +52,4 @@ extern "C" fe_ks_status fe_ks_gemm_f64(int trans_a, int trans_b, int64_t m, int6
                 std::string("cublasGemmEx failed with status ") + std::to_string((int)s));
   return FE_KS_OK;
 }
+

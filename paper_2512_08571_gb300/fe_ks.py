@@ -90,6 +90,7 @@ def _load():
                                    ctypes.c_double, vp, i64, ctypes.c_int, vp]
     lib.fe_ks_gram_ff_workspace.argtypes = [i64, ctypes.c_int, ctypes.c_int, P(ctypes.c_size_t)]
     lib.fe_ks_gram_ff.argtypes = [vp, vp, vp, i64, ctypes.c_int, ctypes.c_int, vp, ctypes.c_size_t, vp]
+    lib.fe_ks_gram_ff_sym.argtypes = [vp, vp, vp, i64, ctypes.c_int, vp, ctypes.c_size_t, vp]
     lib.fe_ks_rotate_ff.argtypes = [vp, vp, vp, i64, ctypes.c_int, ctypes.c_int, vp]
     lib.fe_ks_destroy.argtypes = [vp]
     lib.fe_ks_destroy.restype = None
@@ -99,7 +100,8 @@ def _load():
                  "fe_ks_measure_fma_peak", "fe_ks_cheb_filter_workspace", "fe_ks_cheb_filter",
                  "fe_ks_nonlocal_apply_static", "fe_ks_tune", "fe_ks_set_config", "fe_ks_batch_create",
                  "fe_ks_batch_configure", "fe_ks_batch_apply", "fe_ks_batch_status", "fe_ks_batch_info",
-                 "fe_ks_gemm_f64", "fe_ks_gram_ff_workspace", "fe_ks_gram_ff", "fe_ks_rotate_ff"):
+                 "fe_ks_gemm_f64", "fe_ks_gram_ff_workspace", "fe_ks_gram_ff", "fe_ks_rotate_ff",
+                 "fe_ks_gram_ff_sym"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -308,8 +310,9 @@ def row_rotate(Y, E, emulated=False, stream=None):
     return X
 
 
-def fe_ks_gram_ff(Y, Z, stream=None, work=None):
-    """Y^T Z (row-major FP64 device tensors [m][n1], [m][n2]) in pairs of floats -> [n1][n2]."""
+def fe_ks_gram_ff(Y, Z, stream=None, work=None, symmetric=False):
+    """Y^T Z (row-major FP64 device tensors [m][n1], [m][n2]) in pairs of floats -> [n1][n2].
+    symmetric=True: the product is known to be symmetric (n1 = n2); half the tiles are computed."""
     import torch
     m, n1 = Y.shape
     n2 = Z.shape[1]
@@ -318,8 +321,12 @@ def fe_ks_gram_ff(Y, Z, stream=None, work=None):
     if work is None or work.numel() < nb.value:
         work = torch.empty(nb.value, dtype=torch.uint8, device=Y.device)
     C = torch.empty((n1, n2), dtype=torch.float64, device=Y.device)
-    _check(_lib.fe_ks_gram_ff(_ptr(Y), _ptr(Z), _ptr(C), m, n1, n2, _ptr(work), nb.value, stream))
+    if symmetric:
+        _check(_lib.fe_ks_gram_ff_sym(_ptr(Y), _ptr(Z), _ptr(C), m, n1, _ptr(work), nb.value, stream))
+    else:
+        _check(_lib.fe_ks_gram_ff(_ptr(Y), _ptr(Z), _ptr(C), m, n1, n2, _ptr(work), nb.value, stream))
     return C
+
 
 
 def fe_ks_rotate_ff(Y, E, stream=None):

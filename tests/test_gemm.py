@@ -42,6 +42,33 @@ def test_row_gram_and_rotate(emulated):
     assert (X - refx).abs().max().item() <= 1e-13 * (Y.abs() @ E.abs()).max().item()
 
 
+@pytest.mark.parametrize("m,n", [(20000, 48), (8192 * 3 + 77, 130)])
+def test_symmetric_grams(m, n):
+    """Y^T Y and Y^T (D Y) with D diagonal: the one-triangle pair-of-floats form equals the
+    full product within the FP64-accurate bound and is exactly symmetric, and it equals the
+    full pair-of-floats product bit for bit on and above the diagonal (130 = two 64-wide tiles
+    and a ragged one)."""
+    g = torch.Generator(device="cuda")
+    g.manual_seed(11)
+    Y = torch.rand((m, n), generator=g, device="cuda", dtype=torch.float64) * 2 - 1
+    d = torch.rand((m, 1), generator=g, device="cuda", dtype=torch.float64) + 0.5
+    # Sums of same-sign terms (the diagonal of Y^T Y) do not cancel, so the pair accumulator's
+    # low word grows with the sum: its float roundings, renormalised every 4 terms, add about
+    # sqrt(8192) x 2^-47 = 6.4e-13 of the sum over one 8192-row chunk; 1e-12 covers that.
+    for Z in (Y, d * Y):            # Y^T Y and Y^T D Y: symmetric products
+        ref = Y.T @ Z
+        scale = (Y.abs().T @ Z.abs()).max().item()
+        C = fk.fe_ks_gram_ff(Y, Z, symmetric=True)
+        assert torch.equal(C, C.T)
+        assert (C - ref).abs().max().item() <= 1e-12 * scale
+        full = fk.fe_ks_gram_ff(Y, Z)
+        sym = fk.fe_ks_gram_ff(Y, Z, symmetric=True)
+        iu = torch.triu_indices(n, n, device="cuda")
+        assert torch.equal(sym[iu[0], iu[1]], full[iu[0], iu[1]])
+    with pytest.raises(fk.FeKsError, match="ERR_ARG"):
+        fk._check(fk._lib.fe_ks_gram_ff_sym(None, None, None, m, n, None, 0, None))
+
+
 def test_pair_of_floats_gram_and_rotation():
     g = torch.Generator(device="cuda")
     g.manual_seed(5)

@@ -51,7 +51,7 @@ typedef enum {
   FE_KS_ERR_CUDA = -3,         /* a CUDA runtime call failed                                */
   FE_KS_ERR_OOM = -4,          /* device allocation failed during setup                     */
   FE_KS_ERR_TIMEOUT = -5,      /* a device-side bounded wait gave up (batched persistent)   */
-  FE_KS_ERR_UNSUPPORTED = -6   /* valid request this build does not implement               */
+  FE_KS_ERR_UNSUPPORTED = -6   /* valid request the library does not implement              */
 } fe_ks_status;
 
 /* Arithmetic of one application. */

@@ -42,7 +42,7 @@ extern "C" fe_ks_status fe_ks_gemm_f64(int trans_a, int trans_b, int64_t m, int6
   const cublasOperation_t ta = trans_a ? CUBLAS_OP_T : CUBLAS_OP_N;
   const cublasOperation_t tb = trans_b ? CUBLAS_OP_T : CUBLAS_OP_N;
   const cublasComputeType_t ct = emulated ? CUBLAS_COMPUTE_64F_EMULATED_FIXEDPOINT : CUBLAS_COMPUTE_64F;
-  // emulation: always use it when asked (the default strategy keeps native FP64 when it judges that faster)
+  // emulation: always use it when asked (the default strategy keeps native FP64 where it estimates that to be faster)
   cublasSetMathMode(h, emulated ? CUBLAS_FP64_EMULATED_FIXEDPOINT_MATH : CUBLAS_DEFAULT_MATH);
   cublasSetEmulationStrategy(h, emulated ? CUBLAS_EMULATION_STRATEGY_EAGER : CUBLAS_EMULATION_STRATEGY_DEFAULT);
   cublasStatus_t s = cublasGemmEx(h, ta, tb, (int)m, (int)n, (int)k, &alpha, A, CUDA_R_64F, (int)lda, B, CUDA_R_64F,

@@ -73,3 +73,23 @@ def test_reference_arm_under_two_ranks(rank):
     assert line["impl"] == "reference" and line["n_gpus"] == 2
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+
+
+@pytest.mark.parametrize("key", ["C2", "C3", "C4", "AE"])
+def test_bench_flop_model_matches_the_oracle_model(key):
+    """bench.alg_flops splits the oracle's closed form of eq. flopRealMF / flopComplexMF
+    (n_s = 9 x (atom, cell) pairs, the vector count taken as real columns: 2 per complex
+    vector) into the fused cell kernel's share (cell terms + half of the nonlocal term, the
+    roofline's numerator) and the projection kernel's share (the other half)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from oracle import flops
+    from synth import CONFIGS
+    wl = CONFIGS[key]
+    n_pairs = 5 * wl.n_atoms
+    local, proj = bench.alg_flops(wl, n_pairs, wl.n_v)
+    cols = wl.n_v * (2 if wl.complex else 1)
+    model = flops.mf_complex_total if wl.complex else flops.mf_real_total
+    want = model(wl.p + 1, wl.nq, cols, wl.n_cells, 9 * n_pairs)
+    assert local + proj == pytest.approx(want, rel=1e-12)
+    assert proj == pytest.approx((want - model(wl.p + 1, wl.nq, cols, wl.n_cells, 0)) / 2, rel=1e-12)

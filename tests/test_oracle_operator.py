@@ -149,13 +149,16 @@ def test_quadrature_order_n_p_plus_2():
     assert abs(got[p + 1][0] - exact_L) > 1e-6 * abs(exact_L)          # the low rule misses the quartic
 
 
-def _periodic(n=3, p=4, L=10.0, jitter=0.0, kfrac=(0, 0, 0), gga=False, n_atoms=0, seed=11):
-    return Workload("t", L=L, n=n, p=p, nq=p + 1, n_v=4, jitter=jitter, kfrac=kfrac,
+def _periodic(n=3, p=4, L=10.0, jitter=0.0, kfrac=(0, 0, 0), gga=False, n_atoms=0, seed=11, nqx=0):
+    return Workload("t", L=L, n=n, p=p, nq=p + 1 + nqx, n_v=4, jitter=jitter, kfrac=kfrac,
                     gga=gga, n_atoms=n_atoms, complex=any(kfrac), seed=seed)
 
 
-def test_volume_and_null_space_jittered():
-    wl = _periodic(n=3, p=3, jitter=0.1, gga=True)
+# The identities below hold for any Gauss rule with n_q >= n_p: they are checked for the
+# square rule and for n_q = n_p + 2.
+@pytest.mark.parametrize("nqx", [0, 2])
+def test_volume_and_null_space_jittered(nqx):
+    wl = _periodic(n=3, p=3, jitter=0.1, gga=True, nqx=nqx)
     P = Problem(wl, vloc=_zero, vgga=lambda x: np.broadcast_to(np.array([0.3, -0.7, 0.2]), x.shape))
     one = np.ones((P.m, 1))
     Y = np.zeros((P.m, 1))
@@ -169,9 +172,10 @@ def test_volume_and_null_space_jittered():
     assert abs(P.lumped_mass().sum() - wl.L ** 3) < 1e-9 * wl.L ** 3
 
 
-def test_k_shift_null_space():
+@pytest.mark.parametrize("nqx", [0, 2])
+def test_k_shift_null_space(nqx):
     """V = V^G = 0, no atoms: H(k) 1 = |k|^2/2 M 1."""
-    wl = _periodic(n=2, p=3, jitter=0.1, kfrac=(0.25, 0.1, -0.3))
+    wl = _periodic(n=2, p=3, jitter=0.1, kfrac=(0.25, 0.1, -0.3), nqx=nqx)
     P = Problem(wl, vloc=_zero, vgga=None)
     one = np.ones((P.m, 1))
     Y = P.apply(one)
@@ -226,8 +230,9 @@ def test_plane_wave_spectrum_k0():
     assert ev[19] > 2.9 * g2            # next shell |G|^2 = 3 (2 pi / L)^2
 
 
-def test_constant_shift_affine():
-    wl = _periodic(n=2, p=3)
+@pytest.mark.parametrize("nqx", [0, 2])
+def test_constant_shift_affine(nqx):
+    wl = _periodic(n=2, p=3, nqx=nqx)
     c = -1.75
     P0 = Problem(wl, vloc=_zero, vgga=None)
     Pc = Problem(wl, vloc=lambda x: np.full(np.asarray(x).shape[:-1], c), vgga=None)
@@ -238,14 +243,15 @@ def test_constant_shift_affine():
     np.testing.assert_allclose(Pc.apply(X) - P0.apply(X), c * MX, atol=1e-12)
 
 
-def _small_full(complex_=True, jitter=0.1):
+def _small_full(complex_=True, jitter=0.1, nqx=0):
     kf = (0.25, 0.1, 0.0) if complex_ else (0, 0, 0)
-    return Workload("small", L=9.0, n=3, p=3, nq=4, n_v=3, jitter=jitter, kfrac=kf, gga=True,
+    return Workload("small", L=9.0, n=3, p=3, nq=4 + nqx, n_v=3, jitter=jitter, kfrac=kf, gga=True,
                     n_atoms=2, complex=complex_, seed=77)
 
 
-def test_hermiticity_and_conjugate_k():
-    wl = _small_full(True)
+@pytest.mark.parametrize("nqx", [0, 2])
+def test_hermiticity_and_conjugate_k(nqx):
+    wl = _small_full(True, nqx=nqx)
     P = Problem(wl)
     rng = np.random.default_rng(3)
     X = rng.standard_normal((P.m, 2)) + 1j * rng.standard_normal((P.m, 2))

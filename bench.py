@@ -6,8 +6,18 @@ Workload (default): the p = 8 configuration -- periodic cube L = 30 bohr,
 operator (kinetic + V_loc + GGA + 64 atoms of l <= 2 projectors), N_v = 256,
 m = 7,077,888 DoFs.  One step = one application Y = H X of the whole operator
 (all cells, all vectors) in FP64; X (14.5 GB) is far larger than L2, so no
-flush is needed between steps.  The line also carries the FP32 ("mixed")
-application on the same workload.
+flush is needed between steps.
+
+Beside the FP64 headline the line carries, on the same workload:
+  f64_pairs_of_fp32, mixed (FP32), bf16_tensor_core, f16_tensor_core  the other precisions
+  e2e                      the same metric through fe_ks_apply_host from pinned host memory
+  filter                   one R-ChFSI pass per precision plan and a convergence run
+  all_electron_like        the complex workload without projectors (N_v = 64)
+  cell_matrix_baseline     the cell-matrix method on the GPU (FP64 / FP32 / BF16)
+  quadrature_n_p_plus_2    the workload with n_q = n_p + 2
+  batched, batched_small_systems  many systems in one persistent launch vs one launch each
+  cpu_baseline             the CPU oracle on a bounded sample of cells
+Each has a --no-... switch.
 
 Metric: DoF x vectors per second (m * N_v / time of one application).
 

@@ -8,16 +8,19 @@ m = 7,077,888 DoFs.  One step = one application Y = H X of the whole operator
 (all cells, all vectors) in FP64; X (14.5 GB) is far larger than L2, so no
 flush is needed between steps.
 
-Beside the FP64 headline the line carries, on the same workload:
-  f64_pairs_of_fp32, mixed (FP32), bf16_tensor_core, f16_tensor_core  the other precisions
+Output.  Every measured section goes to a JSON detail file (--detail, default
+bench_detail.json); the LAST stdout line is one compact JSON object (a few KB)
+with the headline and a digest of the rest:
+  value, ms_per_step, roofline, clocks, gpu_launches   FP64 application (the headline)
   e2e                      the same metric through fe_ks_apply_host from pinned host memory
-  filter                   one R-ChFSI pass per precision plan and a convergence run
-  all_electron_like        the complex workload without projectors (N_v = 64)
-  cell_matrix_baseline     the cell-matrix method on the GPU (FP64 / FP32 / BF16)
-  quadrature_n_p_plus_2    the workload with n_q = n_p + 2
-  batched, batched_small_systems  many systems in one persistent launch vs one launch each
   cpu_baseline             the CPU oracle on a bounded sample of cells
-Each has a --no-... switch.
+  precisions               pairs of floats, FP32, BF16 / FP16 tensor cores: time, speedup,
+                           roofline fraction, and the error against the FP64 result
+  filter                   R-ChFSI pass times per precision plan, filter and pass speedups,
+                           and the convergence run
+  batched_c5, batched_small  one persistent launch vs one launch per system
+  all_electron_like, cell_matrix_f64_ms   the other workloads' headline times
+Each section has a --no-... switch.
 
 Metric: DoF x vectors per second (m * N_v / time of one application).
 
@@ -80,6 +83,8 @@ def parse():
     ap.add_argument("--config", type=int, default=None,
                     help="force this tile configuration instead of tuning (for profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle sample")
+    ap.add_argument("--detail", default="bench_detail.json",
+                    help="file that receives every measured section (the last stdout line is a digest)")
     return ap.parse_args()
 
 
@@ -180,6 +185,32 @@ def alg_flops(wl, n_pairs, n_v):
     return per_cell * wl.n_cells + nl / 2.0, nl / 2.0
 
 
+def col_errors(Y, Yref, chunk=65536):
+    """Errors of Y against Yref over every entry, on the device in row chunks:
+    (max over columns of ||Y_v - Yref_v||_2 / ||Yref_v||_2,
+     max over entries of |Y_iv - Yref_iv| / max_i |Yref_iv|).
+    Complex blocks are compared as their real and imaginary columns."""
+    import torch
+    if Y.is_complex():
+        Y, Yref = torch.view_as_real(Y).flatten(1), torch.view_as_real(Yref).flatten(1)
+    n = Y.shape[1]
+    num2 = torch.zeros(n, dtype=torch.float64, device=Y.device)
+    den2 = torch.zeros_like(num2)
+    dmax = torch.zeros_like(num2)
+    rmax = torch.zeros_like(num2)
+    for r0 in range(0, Y.shape[0], chunk):
+        a = Y[r0:r0 + chunk].to(torch.float64)
+        b = Yref[r0:r0 + chunk].to(torch.float64)
+        d = a - b
+        num2 += (d * d).sum(0)
+        den2 += (b * b).sum(0)
+        dmax = torch.maximum(dmax, d.abs().amax(0))
+        rmax = torch.maximum(rmax, b.abs().amax(0))
+    col = float((num2.sqrt() / den2.sqrt().clamp_min(1e-300)).max())
+    elem = float((dmax / rmax.clamp_min(1e-300)).max())
+    return col, elem
+
+
 def load_traffic(key):
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
@@ -206,7 +237,7 @@ def run_native(args, wl, rank, world):
     import torch
     import torch.distributed as dist
     from paper_2512_08571_gb300 import fe_ks as fk
-    from paper_2512_08571_gb300.problem import HostProblem
+    from synth.host_problem import HostProblem
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
@@ -235,6 +266,8 @@ def run_native(args, wl, rank, world):
     # the seeded trial block, generated once on the host and kept on the device
     X64 = torch.empty((m, n_v), dtype=torch.complex128 if cplx else torch.float64, device=dev)
     fill_trial(wl, n_v, X64, np.complex128 if cplx else np.float64)
+
+    ref = {}
 
     def measure(precision, steps, warmup):
         dt = {fk.FE_KS_F64: torch.complex128 if cplx else torch.float64,
@@ -273,6 +306,12 @@ def run_native(args, wl, rank, world):
                    tile_config=best, tune_ms=[round(t, 3) for t in tune_ms],
                    achieved=achieved, local_launch_ms=local_ms / max(local_n, 1),
                    launches=int(prof["proj"][1] + prof["local"][1]))
+        # error of this precision's result against the FP64 application of the same X (itself
+        # held to <= 1e-12 of the oracle by the parity tests), over all m x N_v entries
+        if precision == fk.FE_KS_F64:
+            ref["Y"] = Y
+        elif "Y" in ref:
+            out["err_col"], out["err_elem"] = col_errors(Y, ref["Y"])
         del X, Y
         torch.cuda.empty_cache()
         return out
@@ -292,6 +331,8 @@ def run_native(args, wl, rank, world):
     elif not args.no_mixed and args.precision == "both":
         bf16 = measure(fk.FE_KS_BF16, max(args.steps, 20), max(args.warmup, 3))
         f16 = measure(fk.FE_KS_F16, max(args.steps, 20), max(args.warmup, 3))
+    ref.clear()
+    torch.cuda.empty_cache()
     peak_mma_live = fk.fe_ks_measure_fma_peak(fk.FE_KS_BF16) * 1e12 if (bf16 or f16) else None
 
     peak64_live = fk.fe_ks_measure_fma_peak(fk.FE_KS_F64) * 1e12
@@ -417,7 +458,7 @@ def run_filter(args, wl, ctx, hp, X64):
     import torch
     from paper_2512_08571_gb300 import fe_ks as fk
     from paper_2512_08571_gb300.chfsi import RChFSI
-    from paper_2512_08571_gb300.problem import HostProblem
+    from synth.host_problem import HostProblem
     stream = torch.cuda.current_stream()
     dev = torch.device("cuda", torch.cuda.current_device())
 
@@ -502,7 +543,7 @@ def run_filter(args, wl, ctx, hp, X64):
     conv["speedup_bf16"] = conv["f64"]["ms"] / conv["mixed_bf16"]["ms"]
     conv["speedup_f16"] = conv["f64"]["ms"] / conv["mixed_f16"]["ms"]
     # the generalised problem H X = M X Lam with the consistent mass (Algorithm 4 as printed)
-    from paper_2512_08571_gb300.problem import mass_problem
+    from synth.host_problem import mass_problem
     hpm = mass_problem(wls)
     cm = fk.fe_ks_setup(hpm.struct, fk.TERM_L, wls.n_v, stream.cuda_stream)
     gh, glams = {}, {}
@@ -532,7 +573,7 @@ def run_all_electron(args):
     import numpy as np
     import torch
     from paper_2512_08571_gb300 import fe_ks as fk
-    from paper_2512_08571_gb300.problem import HostProblem
+    from synth.host_problem import HostProblem
     from synth import CONFIGS
     wl = CONFIGS["AE"]
     if args.cells:
@@ -580,7 +621,7 @@ def run_quadrature_np2(args, wl0):
     import numpy as np
     import torch
     from paper_2512_08571_gb300 import fe_ks as fk
-    from paper_2512_08571_gb300.problem import HostProblem
+    from synth.host_problem import HostProblem
     wl = dataclasses.replace(wl0, nq=wl0.p + 3, name=wl0.name + "-nq" + str(wl0.p + 3))
     stream = torch.cuda.current_stream()
     hp = HostProblem(wl)
@@ -636,7 +677,7 @@ def run_batched(args, wls=None):
     one fe_ks_apply per system.  Returns a dict for the JSON line."""
     import torch
     from paper_2512_08571_gb300 import fe_ks as fk
-    from paper_2512_08571_gb300.problem import HostProblem
+    from synth.host_problem import HostProblem
     from synth import batched_systems
     if wls is None:
         wls = batched_systems()
@@ -827,48 +868,88 @@ def main():
                           "value": pr["value"], "local_launch_ms": pr["local_launch_ms"],
                           "profile_ms_per_step": {k: v[0] / max(1, args.steps) for k, v in pr["prof"].items()}}))
         return
+    detail = detail_sections(args, wl, res, world)
+    if world == 1 and not args.no_cpu_baseline:
+        v, n, el = oracle_sample(wl, args.cpu_seconds)
+        detail["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                                  "sample": f"{n} of {wl.n_cells} cells in {el:.1f} s (cell-matrix method: "
+                                            f"H^(e) by quadrature then H^(e) X^(e), local terms, all "
+                                            f"{wl.n_v} vectors), scaled to the whole operator"}
+    line = compact_line(detail, args, config, world)
+    if args.detail:
+        try:
+            os.makedirs(os.path.dirname(os.path.abspath(args.detail)), exist_ok=True)
+            with open(args.detail, "w") as f:
+                json.dump(detail, f, indent=1)
+            line["detail"] = args.detail
+        except OSError as exc:
+            sys.stderr.write(f"bench: could not write {args.detail}: {exc}\n")
+    print(json.dumps(line, separators=(",", ":")))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _r(x, n=4):
+    """Round to n significant digits for the compact line (None stays None)."""
+    if x is None:
+        return None
+    if isinstance(x, (int,)) and not isinstance(x, bool):
+        return x
+    try:
+        return float(f"{float(x):.{n}g}")
+    except (TypeError, ValueError):
+        return x
+
+
+def detail_sections(args, wl, res, world):
+    """Every measured section of a run, as one dict (written to the detail file).  The
+    final JSON line is a compact digest of it (compact_line)."""
+    f64 = res["f64"]
     traffic = load_traffic(f"fe_local_kernel f64 {wl.name} cfg{f64['tile_config']}")
     achieved = f64["achieved"]
-    roofline = {"bound": "alu", "achieved": achieved / 1e12 if achieved else None,
-                "peak": PEAK_FP64_NOMINAL / 1e12, "unit": "TFLOP/s",
-                "frac": (achieved / PEAK_FP64_NOMINAL) if achieved else None, "traffic": traffic,
-                "kernel": "fe_local_kernel (FP64 DFMA pipe)",
-                "peak_source": "nominal FP64 1.25 TFLOP/s; live DFMA probe %.3f TFLOP/s" % (res["peak64_live"] / 1e12),
-                "frac_of_live_probe": (achieved / res["peak64_live"]) if achieved else None,
-                "avg_launch_ms": f64["local_launch_ms"], "tile_config": f64["tile_config"],
-                "tune_ms_per_config": f64["tune_ms"]}
-    line = {"metric": METRIC, "value": f64["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": f64["ms"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded mesh, fields, atoms, X)",
-            "config": config, "roofline": roofline, "clocks": f64["clocks"],
-            "gpu_launches": f64["launches"], "setup_s": res["setup_s"]}
+    detail = {"workload": wl.name, "setup_s": res["setup_s"], "info": res["info"],
+              "alg_flops_local_per_apply": res["local_flops"],
+              "peak_fp64_live_tflops": res["peak64_live"] / 1e12,
+              "peak_fp32_live_tflops": res["peak32_live"] / 1e12}
+    detail["f64"] = {
+        "value": f64["value"], "ms_per_step": f64["ms"], "clocks": f64["clocks"], "gpu_launches": f64["launches"],
+        "profile_ms": {k: v[0] for k, v in f64["prof"].items()},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12 if achieved else None,
+                     "peak": PEAK_FP64_NOMINAL / 1e12, "unit": "TFLOP/s",
+                     "frac": (achieved / PEAK_FP64_NOMINAL) if achieved else None, "traffic": traffic,
+                     "kernel": "fe_local_kernel (FP64 DFMA pipe)",
+                     "peak_source": "nominal FP64 1.25 TFLOP/s; live DFMA probe %.3f TFLOP/s"
+                                    % (res["peak64_live"] / 1e12),
+                     "frac_of_live_probe": (achieved / res["peak64_live"]) if achieved else None,
+                     "avg_launch_ms": f64["local_launch_ms"], "tile_config": f64["tile_config"],
+                     "tune_ms_per_config": f64["tune_ms"]}}
     if res.get("f64e"):
         e = res["f64e"]
         ach = e["achieved"]
-        line["f64_pairs_of_fp32"] = {
-            "dtype": "f32x2 (FP64 in/out, FP64-accurate: parity <= 1e-12 vs the oracle)", "value": e["value"],
-            "unit": UNIT, "ms_per_step": e["ms"], "speedup_vs_f64": f64["ms"] / e["ms"],
-            "roofline": {"bound": "alu", "achieved_alg_fp64_equiv": ach / 1e12 if ach else None, "unit": "TFLOP/s",
-                         "frac_of_nominal_fp64": ach / PEAK_FP64_NOMINAL if ach else None,
-                         "avg_launch_ms": e["local_launch_ms"], "tile_config": e["tile_config"],
-                         "tune_ms_per_config": e["tune_ms"]},
-            "clocks": e["clocks"], "gpu_launches": e["launches"]}
+        detail["f64_pairs_of_fp32"] = {
+            "dtype": "f32x2 (FP64 in/out, FP64-accurate)", "value": e["value"], "ms_per_step": e["ms"],
+            "speedup_vs_f64": f64["ms"] / e["ms"], "err_col": e.get("err_col"), "err_elem": e.get("err_elem"),
+            "alg_fp64_equiv_tflops": ach / 1e12 if ach else None,
+            "frac_of_nominal_fp64": ach / PEAK_FP64_NOMINAL if ach else None,
+            "avg_launch_ms": e["local_launch_ms"], "tile_config": e["tile_config"],
+            "tune_ms_per_config": e["tune_ms"], "clocks": e["clocks"], "gpu_launches": e["launches"]}
     mixed = res["mixed"]
     if mixed:
         ach = mixed["achieved"]
-        line["mixed"] = {"dtype": "f32", "value": mixed["value"], "unit": UNIT, "ms_per_step": mixed["ms"],
-                         "speedup_vs_f64": f64["ms"] / mixed["ms"],
-                         "roofline": {"bound": "alu", "achieved": ach / 1e12 if ach else None,
-                                      "peak": PEAK_FP32_NOMINAL / 1e12, "unit": "TFLOP/s",
-                                      "frac": ach / PEAK_FP32_NOMINAL if ach else None,
-                                      "live_probe": res["peak32_live"] / 1e12,
-                                      "avg_launch_ms": mixed["local_launch_ms"],
-                                      "tile_config": mixed["tile_config"],
-                                      "traffic": load_traffic(f"fe_local_kernel f32 {wl.name} cfg{mixed['tile_config']}"),
-                                      "tune_ms_per_config": mixed["tune_ms"]},
-                         "clocks": mixed["clocks"], "gpu_launches": mixed["launches"]}
+        detail["f32"] = {
+            "dtype": "f32", "value": mixed["value"], "ms_per_step": mixed["ms"],
+            "speedup_vs_f64": f64["ms"] / mixed["ms"], "err_col": mixed.get("err_col"),
+            "err_elem": mixed.get("err_elem"),
+            "roofline": {"bound": "alu", "achieved": ach / 1e12 if ach else None,
+                         "peak": PEAK_FP32_NOMINAL / 1e12, "unit": "TFLOP/s",
+                         "frac": ach / PEAK_FP32_NOMINAL if ach else None,
+                         "live_probe": res["peak32_live"] / 1e12, "avg_launch_ms": mixed["local_launch_ms"],
+                         "tile_config": mixed["tile_config"],
+                         "traffic": load_traffic(f"fe_local_kernel f32 {wl.name} cfg{mixed['tile_config']}"),
+                         "tune_ms_per_config": mixed["tune_ms"]},
+            "clocks": mixed["clocks"], "gpu_launches": mixed["launches"]}
     for key, name, dts in (("bf16", "bf16_tensor_core", "bf16 x bf16 -> f32 (FP32 storage)"),
-                           ("f16", "f16_tensor_core", "f16 x f16 -> f32 (FP32 storage, power-of-two tile scaling)")):
+                           ("f16", "f16_tensor_core", "f16 x f16 -> f32 (FP32 storage, power-of-two column scaling)")):
         bf = res[key]
         if not bf:
             continue
@@ -876,44 +957,111 @@ def main():
         # the coefficients; the executed MMA rate is reported against the live mma.sync probe
         alg_bytes = 2 * res["bytes32"]["xy"] + res["bytes32"]["coef"]
         t_roof = alg_bytes / (PEAK_HBM_GBS * 1e9)
-        line[name] = {
-            "dtype": dts, "value": bf["value"], "unit": UNIT,
-            "ms_per_step": bf["ms"], "speedup_vs_f64": f64["ms"] / bf["ms"],
+        detail[name] = {
+            "dtype": dts, "value": bf["value"], "ms_per_step": bf["ms"], "speedup_vs_f64": f64["ms"] / bf["ms"],
             "speedup_vs_fp32_cuda_core": (mixed["ms"] / bf["ms"]) if mixed else None,
+            "err_col": bf.get("err_col"), "err_elem": bf.get("err_elem"),
             "roofline": {"bound": "hbm", "achieved": alg_bytes / (bf["ms"] * 1e-3) / 1e9,
                          "peak": PEAK_HBM_GBS, "unit": "GB/s", "frac": t_roof / (bf["ms"] * 1e-3),
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
-                         "alg_bytes_per_apply": alg_bytes,
-                         "avg_launch_ms": bf["local_launch_ms"],
+                         "alg_bytes_per_apply": alg_bytes, "avg_launch_ms": bf["local_launch_ms"],
                          "mma_tflops_executed": res["mma_flops_per_apply"] * 1e-12 / (bf["ms"] * 1e-3),
-                         "mma_sync_live_probe_tflops": res["peak_mma_live"] / 1e12},
+                         "mma_sync_live_probe_tflops": (res["peak_mma_live"] or 0) / 1e12},
             "clocks": bf["clocks"], "gpu_launches": bf["launches"]}
     if res["e2e"]:
-        line["e2e"] = res["e2e"]
+        detail["e2e"] = res["e2e"]
     if res["filter"]:
-        line["filter"] = res["filter"]
+        detail["filter"] = res["filter"]
     if res["cell_matrix"]:
-        line["cell_matrix_baseline"] = res["cell_matrix"]
+        detail["cell_matrix_baseline"] = res["cell_matrix"]
     if not args.no_all_electron and world == 1:
-        line["all_electron_like"] = run_all_electron(args)
+        detail["all_electron_like"] = run_all_electron(args)
     if not args.no_nq2 and world == 1 and not wl.complex:
         q2 = run_quadrature_np2(args, wl)
         q2["f64"]["vs_n_q_eq_n_p"] = q2["f64"]["ms_per_step"] / f64["ms"]
         if mixed:
             q2["f32"]["vs_n_q_eq_n_p"] = q2["f32"]["ms_per_step"] / mixed["ms"]
-        line["quadrature_n_p_plus_2"] = q2
+        detail["quadrature_n_p_plus_2"] = q2
     if not args.no_batched:
-        line["batched"] = run_batched(args)
-        line["batched_small_systems"] = run_batched(args, small_systems())
-    if world == 1 and not args.no_cpu_baseline:
-        v, n, el = oracle_sample(wl, args.cpu_seconds)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-                                "sample": f"{n} of {wl.n_cells} cells in {el:.1f} s (cell-matrix method: "
-                                          f"H^(e) by quadrature then H^(e) X^(e), local terms, all "
-                                          f"{wl.n_v} vectors), scaled to the whole operator"}
-    print(json.dumps(line))
-    if world > 1:
-        torch.distributed.destroy_process_group()
+        detail["batched"] = run_batched(args)
+        detail["batched_small_systems"] = run_batched(args, small_systems())
+    return detail
+
+
+def compact_line(detail, args, config, world):
+    """The one JSON line the benchmark prints last: the headline (FP64 application at the
+    workload's full size), its roofline, clocks, end-to-end and CPU-oracle numbers, and a
+    one-number digest of every other section (the full sections go to the detail file).
+    Kept to a few KB so that a reader of the output's tail sees all of it."""
+    f64 = detail["f64"]
+    rf = f64["roofline"]
+    line = {"metric": METRIC, "value": _r(f64["value"], 6), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": _r(f64["ms_per_step"], 6), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded mesh, fields, atoms, X)", "config": config,
+            "roofline": {"bound": rf["bound"], "achieved": _r(rf["achieved"]), "peak": rf["peak"],
+                         "unit": rf["unit"], "frac": _r(rf["frac"]), "traffic": rf["traffic"],
+                         "kernel": rf["kernel"], "avg_launch_ms": _r(rf["avg_launch_ms"]),
+                         "frac_of_live_probe": _r(rf["frac_of_live_probe"]),
+                         "peak_source": rf["peak_source"]},
+            "clocks": {k: f64["clocks"].get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+            "gpu_launches": f64["gpu_launches"]}
+    e2e = detail.get("e2e")
+    if e2e:
+        line["e2e"] = {"value": _r(e2e["value"]), "unit": e2e["unit"], "h2d_bytes_per_step": e2e["h2d_bytes_per_step"],
+                       "d2h_bytes_per_step": e2e["d2h_bytes_per_step"], "ms_per_step": _r(e2e["ms_per_step"]),
+                       "steps": e2e["steps"], "api": "fe_ks_apply_host (pinned host X in, Y out)"}
+    cb = detail.get("cpu_baseline")
+    if cb:
+        line["cpu_baseline"] = {"value": _r(cb["value"]), "unit": cb["unit"], "cores": cb["cores"],
+                                "kind": cb["kind"], "sample": cb["sample"]}
+    prec = {}
+    for key, name in (("f64_pairs_of_fp32", "f64_pairs"), ("f32", "f32"), ("bf16_tensor_core", "bf16_tc"),
+                      ("f16_tensor_core", "f16_tc"), ("bf16x2_tensor_core", "bf16x2_tc")):
+        d = detail.get(key)
+        if not d:
+            continue
+        q = {"ms": _r(d["ms_per_step"]), "value": _r(d["value"]), "x_f64": _r(d["speedup_vs_f64"], 3),
+             "err_col": _r(d.get("err_col"), 2), "err_elem": _r(d.get("err_elem"), 2)}
+        if "roofline" in d:
+            q["frac"] = _r(d["roofline"]["frac"], 3)
+            q["bound"] = d["roofline"]["bound"]
+        elif "frac_of_nominal_fp64" in d:
+            q["frac"] = _r(d["frac_of_nominal_fp64"], 3)
+            q["bound"] = "alu"
+        prec[name] = q
+    if prec:
+        line["precisions"] = prec
+        line["errors_vs"] = "the FP64 application of the same X (all entries)"
+    flt = detail.get("filter")
+    if flt:
+        fl = {"speedup_filter_mixed": _r(flt.get("speedup_filter_mixed_vs_f64"), 3),
+              "speedup_pass_mixed": _r(flt.get("speedup_pass_mixed_vs_f64"), 3),
+              "pass_ms": {k: _r(flt[k]["pass_ms"]) for k in ("f64", "f64_pairs", "mixed", "mixed_bf16",
+                                                              "mixed_f16", "mixed_bf16x2")
+                          if isinstance(flt.get(k), dict) and "pass_ms" in flt[k]}}
+        conv = flt.get("converged")
+        if conv:
+            fl["converged"] = {k: _r(conv[k], 3) for k in ("workload", "passes_f64", "passes_mixed", "speedup",
+                                                           "max_eig_diff_Ha", "max_residual") if k in conv}
+            fl["converged"]["workload"] = conv.get("workload")
+        c6 = flt.get("converged_6cubed")
+        if c6:
+            fl["converged_6cubed"] = {"speedup": _r(c6.get("speedup"), 3),
+                                      "max_eig_diff_Ha": _r(c6.get("max_eig_diff_mixed_vs_f64_Ha"), 2)}
+        line["filter"] = fl
+    for key, name in (("batched", "batched_c5"), ("batched_small_systems", "batched_small")):
+        b = detail.get(key)
+        if b:
+            line[name] = {"ms": _r(b["ms_per_step"]), "x_separate": _r(b["speedup_vs_separate"], 3)}
+    ae = detail.get("all_electron_like")
+    if ae:
+        line["all_electron_like"] = {k: _r(ae[k]["ms_per_step"]) for k in ("f64", "f32", "bf16_tensor_core")
+                                     if k in ae}
+    cm = detail.get("cell_matrix_baseline")
+    if cm and isinstance(cm.get("f64"), dict):
+        line["cell_matrix_f64_ms"] = _r(cm["f64"].get("ms_per_step"))
+    return line
 
 
 if __name__ == "__main__":

@@ -191,12 +191,14 @@ fe_ks_status fe_ks_host_wait(fe_ks_ctx* ctx);
  * Residual-based Chebyshev filter (R-ChFSI, Algorithm 4) of degree `degree`
  * on the standard form Hs = D^{-1/2} H D^{-1/2}: D is the GLL-lumped mass
  * (Algorithm 4's diagonal approximation of M), so in scaled variables M and
- * D become the identity and the filter reads
- *   Y = Hs X - X Lam ;  R_Y = (s1/e) Y ;  R_X = 0 ;
- *   R_X <- (2 s2/e) [(Hs - c) R_Y + Y Lam_Y] - s s2 R_X   (k = 2..degree)
- *   X  <- R_Y + X Lam_Y
- * with e = (lam_max - lam_T)/2, c = (lam_max + lam_T)/2 and the scalar
- * recurrence of Algorithm 4.  The residual Y and the final combination are
+ * D become the identity.  The result is p(Hs) X for the degree-`degree`
+ * Chebyshev polynomial that damps [lam_T, lam_max] (mapped onto [-1, 1]
+ * around c = (lam_max + lam_T)/2 with half-width e = (lam_max - lam_T)/2)
+ * and is 1 at lam_min.  It is evaluated in residual form: the three-term
+ * Chebyshev recurrence is run on the part R = p_k(Hs) X - X p_k(Lam), which
+ * is driven by the residual Y = Hs X - X Lam of the current Ritz pairs,
+ * while the diagonal part p_k(Lam) follows the scalar recurrence on the
+ * host; the output is R + X p(Lam).  The residual Y and the final combination are
  * FP64-accurate: residual_precision selects native FP64 (FE_KS_F64) or the
  * pair-of-floats kernel (FE_KS_F64E) for the residual's application.  The
  * degree - 1 applications inside the recurrence run in `precision`
@@ -398,7 +400,11 @@ fe_ks_status fe_ks_measure_fma_peak(int precision, double* tflops);
  *                  Y is accumulated into (zero it first for the bare term).
  *  cell_dofs     : device [E][(degree+1)^3] global DoF of each cell node.
  *  atom_pair_ptr : device [n_atoms + 1] CSR offsets of each atom's (cell, image) entries.
- *  pair_cell     : device [n_pairs] cell of each entry; pair_atom: device [n_pairs] its atom.
+ *  pair_cell     : device [n_pairs] cell of each entry; pair_atom: device [n_pairs] its atom,
+ *                  which must agree with the CSR ranges (pair_atom[j] = a for
+ *                  atom_pair_ptr[a] <= j < atom_pair_ptr[a + 1]); the projection reads the
+ *                  ranges and the expansion reads pair_atom, and the call does not check
+ *                  that they agree.
  *  F             : device [n_pairs][n_proj][(degree+1)^3] projector matrices
  *                  F^(a,e) (complex: interleaved re, im per entry).
  *  h_coef        : device [n_atoms][n_proj] coefficients Delta^a.
@@ -409,6 +415,10 @@ fe_ks_status fe_ks_measure_fma_peak(int precision, double* tflops);
  * the one scratch array, which keeps the last call's contents (every entry a
  * call reads is written by that call first): calls that overlap on the GPU
  * (different streams, or other devices' threads using the same device) race.
+ * Pairs of different cells share DoFs, so the expansion adds into Y with FP64
+ * atomics in no fixed order: results can differ from run to run in rounding
+ * only (every other apply path of the library is bitwise deterministic).
+ * A device index of 64 or more returns FE_KS_ERR_UNSUPPORTED.
  */
 fe_ks_status fe_ks_nonlocal_apply_static(const double* X, double* Y, int64_t n_v, int32_t is_complex,
                                          int32_t degree, int64_t n_dofs, const int32_t* cell_dofs,

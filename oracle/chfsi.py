@@ -6,22 +6,31 @@ TEST INFRASTRUCTURE (oracle): see ``oracle/__init__.py``.
 The eigenproblem is the standard Hermitian problem for
     Hs = D^{-1/2} H D^{-1/2},
 D being the GLL-lumped mass matrix (the diagonal approximation of M that
-Algorithm 4 uses as D^{-1}).  In these scaled variables D -> I and M -> I, so
-Algorithm 4 is used with both replaced by the identity:
+Algorithm 4 works with).  In these scaled variables D and M both become the
+identity.
 
-  e = (lmax - lT)/2, c = (lmax + lT)/2, sigma = e / (lmin - c), sigma1 = sigma,
-  gamma = 2 / sigma1
-  Y  = Hs X - X Lam
-  R_X = 0, R_Y = (sigma1/e) Y, Lam_X = I, Lam_Y = (sigma1/e)(Lam - c I)
-  for k = 2..m:
-      sigma2 = 1 / (gamma - sigma)
-      R_X   <- (2 sigma2/e) [ (Hs - c I) R_Y + Y Lam_Y ] - sigma sigma2 R_X
-      Lam_X <- (2 sigma2/e) Lam_Y (Lam - c I) - sigma sigma2 Lam_X
-      swap(R_X, R_Y); swap(Lam_X, Lam_Y); sigma = sigma2
-  X <- R_Y + X Lam_Y
+What the filter computes (Algorithm 4).  Map the unwanted interval
+[lT, lmax] onto [-1, 1] by t -> (t - c)/e with c = (lmax + lT)/2 and
+e = (lmax - lT)/2.  The filter of degree m is p_m(Hs) X with
+    p_k(t) = T_k((t - c)/e) / T_k((lmin - c)/e),
+T_k the Chebyshev polynomials of the first kind: p_k damps the unwanted
+interval and is 1 at lmin.  Normalised this way, the block X_k = p_k(Hs) X
+obeys the three-term recurrence
+    X_{k+1} = (2 s_{k+1} / e) (Hs - c) X_k - s_k s_{k+1} X_{k-1},
+    s_1 = e / (lmin - c),  s_{k+1} = 1 / (2 / s_1 - s_k),
+with X_0 = X and X_1 = (s_1 / e)(Hs - c) X.
 
-(Algorithm 4; m is the filter degree, called p in the paper.)  The outer loop
-is Algorithm 3: filter, then Rayleigh-Ritz on the filtered block.
+The residual-based form splits X_k = R_k + X L_k, where L_k = p_k(Lam) is
+diagonal in the current Ritz values Lam.  With the residual Y = Hs X - X Lam
+one has (Hs - c) X L_k = Y L_k + X (Lam - c) L_k, so the two parts follow
+separate recurrences:
+    R_{k+1} = (2 s_{k+1} / e) [(Hs - c) R_k + Y L_k] - s_k s_{k+1} R_{k-1},
+    L_{k+1} = (2 s_{k+1} / e) (Lam - c) L_k - s_k s_{k+1} L_{k-1},
+from R_0 = 0, L_0 = I, R_1 = (s_1 / e) Y, L_1 = (s_1 / e)(Lam - c).  The
+filtered block is R_m + X L_m.  The matrix products act only on R_k, which
+shrinks as X converges; that is why the paper can take them in low precision.
+(The paper calls the degree p; it is m here.)  Algorithm 3 is the outer loop:
+filter, then Rayleigh-Ritz on the filtered block.
 
 The spectral bounds are inputs in the paper.  Here lmax is the standard safe
 Lanczos bound theta_max(T_k) + |beta_k| after k steps, lmin the smallest and
@@ -30,26 +39,31 @@ lT the largest current Ritz value.
 import numpy as np
 
 
-def filter_rchfsi(apply_Hs, X, lam, degree, lmin, lT, lmax):
-    """Algorithm 4 in standard form.  apply_Hs(V) -> Hs V; lam = current Ritz values [n_v]."""
+def _chebyshev_scalars(degree, lmin, lT, lmax):
+    """c, e and the normalisation ratios s_1 .. s_degree of the shifted, scaled
+    Chebyshev recurrence (see the module docstring)."""
     e = (lmax - lT) / 2.0
     c = (lmax + lT) / 2.0
-    sigma = e / (lmin - c)
-    sigma1 = sigma
-    gamma = 2.0 / sigma1
-    Y = apply_Hs(X) - X * lam[None, :]
-    RX = np.zeros_like(Y)
-    RY = (sigma1 / e) * Y
-    LX = np.ones_like(lam)
-    LY = (sigma1 / e) * (lam - c)
+    s = [None, e / (lmin - c)]
     for _ in range(2, degree + 1):
-        sigma2 = 1.0 / (gamma - sigma)
-        RX = (2.0 * sigma2 / e) * (apply_Hs(RY) - c * RY + Y * LY[None, :]) - sigma * sigma2 * RX
-        LX = (2.0 * sigma2 / e) * LY * (lam - c) - sigma * sigma2 * LX
-        RX, RY = RY, RX
-        LX, LY = LY, LX
-        sigma = sigma2
-    return RY + X * LY[None, :]
+        s.append(1.0 / (2.0 / s[1] - s[-1]))
+    return c, e, s
+
+
+def filter_rchfsi(apply_Hs, X, lam, degree, lmin, lT, lmax):
+    """Algorithm 4 in standard form: R_m + X L_m for X_m = p_m(Hs) X.
+    apply_Hs(V) -> Hs V; lam = current Ritz values [n_v]."""
+    c, e, s = _chebyshev_scalars(degree, lmin, lT, lmax)
+    Y = apply_Hs(X) - X * lam[None, :]                  # residual of the Ritz pairs
+    R_prev, L_prev = np.zeros_like(Y), np.ones_like(lam)             # k = 0
+    R_cur, L_cur = (s[1] / e) * Y, (s[1] / e) * (lam - c)            # k = 1
+    for k in range(1, degree):
+        a, b = 2.0 * s[k + 1] / e, s[k] * s[k + 1]
+        R_next = a * (apply_Hs(R_cur) - c * R_cur + Y * L_cur[None, :]) - b * R_prev
+        L_next = a * (lam - c) * L_cur - b * L_prev
+        R_prev, R_cur = R_cur, R_next
+        L_prev, L_cur = L_cur, L_next
+    return R_cur + X * L_cur[None, :]
 
 
 def filter_reference_polynomial(evals, evecs, X, degree, lmin, lT, lmax):
@@ -124,25 +138,23 @@ def rchfsi(apply_Hs, X0, degree, n_iter, lanczos_steps=10, seed=0, tol=None):
 
 def filter_rchfsi_ghep(apply_H, apply_M, Dinv, X, lam, degree, lmin, lT, lmax):
     """Algorithm 4 for the GHEP.  apply_H / apply_M: V -> H V / M V; Dinv: the
-    diagonal of D^{-1} [m]; lam = current Ritz values [n_v]."""
-    e = (lmax - lT) / 2.0
-    c = (lmax + lT) / 2.0
-    sigma = e / (lmin - c)
-    sigma1 = sigma
-    gamma = 2.0 / sigma1
+    diagonal of D^{-1} [m]; lam = current Ritz values [n_v].
+
+    The same two recurrences as the standard form, with the residual taken
+    against the consistent mass, Y = H X - M X Lam, the product in the R
+    recurrence being H D^{-1} R_k (R_k lives in the residual space, D^{-1} maps
+    it back to the solution space), and the filtered block D^{-1} R_m + X L_m."""
+    c, e, s = _chebyshev_scalars(degree, lmin, lT, lmax)
     Y = apply_H(X) - apply_M(X) * lam[None, :]
-    RX = np.zeros_like(Y)
-    RY = (sigma1 / e) * Y
-    LX = np.ones_like(lam)
-    LY = (sigma1 / e) * (lam - c)
-    for _ in range(2, degree + 1):
-        sigma2 = 1.0 / (gamma - sigma)
-        RX = (2.0 * sigma2 / e) * (apply_H(Dinv[:, None] * RY) - c * RY + Y * LY[None, :]) - sigma * sigma2 * RX
-        LX = (2.0 * sigma2 / e) * LY * (lam - c) - sigma * sigma2 * LX
-        RX, RY = RY, RX
-        LX, LY = LY, LX
-        sigma = sigma2
-    return Dinv[:, None] * RY + X * LY[None, :]
+    R_prev, L_prev = np.zeros_like(Y), np.ones_like(lam)
+    R_cur, L_cur = (s[1] / e) * Y, (s[1] / e) * (lam - c)
+    for k in range(1, degree):
+        a, b = 2.0 * s[k + 1] / e, s[k] * s[k + 1]
+        R_next = a * (apply_H(Dinv[:, None] * R_cur) - c * R_cur + Y * L_cur[None, :]) - b * R_prev
+        L_next = a * (lam - c) * L_cur - b * L_prev
+        R_prev, R_cur = R_cur, R_next
+        L_prev, L_cur = L_cur, L_next
+    return Dinv[:, None] * R_cur + X * L_cur[None, :]
 
 
 def rayleigh_ritz_ghep(apply_H, apply_M, Y):

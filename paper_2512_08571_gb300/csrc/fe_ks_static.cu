@@ -21,7 +21,10 @@ constexpr int64_t kStaticScratchDoubles = 524288;   // 4 MiB
 static __device__ __align__(256) double g_nl_scratch[kStaticScratchDoubles];
 
 // Y[dof] += sum_b F[pair][b][node] Q[atom][b][col] for every (pair, node);
-// pairs of different cells share DoFs, so the update is an atomic add.
+// pairs of different cells share DoFs, so the update is an FP64 atomic add.
+// The order of those adds is not fixed, so results can differ from run to run
+// in the last bits (rounding only); every other apply path of the library is
+// bitwise deterministic.
 template <bool CPLX>
 __global__ void fe_expand_atomic_kernel(double* __restrict__ Y, int64_t ld, int ncols, const int* __restrict__ cell_dofs,
                                         const int* __restrict__ pair_cell, const int* __restrict__ pair_atom_of,
@@ -59,7 +62,10 @@ static double* g_scratch_ptr[64] = {};
 
 static fe_ks_status scratch_for_current_device(double** out) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return fail(FE_KS_ERR_CUDA, "cudaGetDevice failed");
+  cudaError_t gerr = cudaGetDevice(&dev);
+  if (gerr != cudaSuccess) return fail(FE_KS_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(gerr));
+  if (dev < 0 || dev >= 64)
+    return fail(FE_KS_ERR_UNSUPPORTED, "device index " + std::to_string(dev) + " is beyond the 64 devices this entry point tracks");
   std::lock_guard<std::mutex> lock(g_scratch_mu);
   if (!g_scratch_ptr[dev]) {
     void* p = nullptr;

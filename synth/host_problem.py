@@ -1,14 +1,17 @@
 """Assemble an ``fe_ks_problem`` from a seeded synthetic workload.
 
-The caller's side of the interface: mesh arrays from ``synth``, quadrature
-points from the library (``fe_ks_quadrature_points``), the synthetic fields
-evaluated there, and the atom/cell/image triples with projector values at the
-library's quadrature points.
+The caller's side of the interface, used by the tests, the benchmark and the
+smoke run: mesh arrays from the generators of this folder, quadrature points
+from the library (``fe_ks_quadrature_points``), the synthetic fields evaluated
+there, and the atom/cell/image triples with projector values at the library's
+quadrature points.  It holds none of the method's arithmetic.  It is not
+imported by ``synth/__init__`` (the oracle imports that package and must not
+load the GPU library).
 """
 import numpy as np
 
-from synth import (make_mesh, vloc_fn, vgga_fn, atoms, projector_values, atom_cell_pairs, N_PROJ)
-from . import fe_ks as _fk
+from paper_2512_08571_gb300 import fe_ks as _fk
+from .workloads import (make_mesh, vloc_fn, vgga_fn, atoms, projector_values, atom_cell_pairs, N_PROJ)
 
 
 class HostProblem:

@@ -9,10 +9,10 @@ import numpy as np
 import pytest
 
 from paper_2512_08571_gb300 import fe_ks as fk
-from paper_2512_08571_gb300.problem import HostProblem
+from synth.host_problem import HostProblem
 from oracle.operator import Problem
 from synth import CONFIGS, trial_vectors
-from gpu_util import gpu_apply, rel_err_cols, round_input, torch_dtype
+from gpu_util import gpu_apply, parity_err, round_input, torch_dtype
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -51,4 +51,4 @@ def test_host_pipeline_matches_device_apply(key, precision, pinned):
         want = gpu_apply(hp, x, precision)
         got = y.numpy()
         assert np.array_equal(got, want)
-        assert rel_err_cols(got, P.apply(x)) <= TOL[precision]
+        assert parity_err(got, P.apply(x)) <= TOL[precision]

@@ -11,10 +11,10 @@ import numpy as np
 import pytest
 
 from paper_2512_08571_gb300 import fe_ks as fk
-from paper_2512_08571_gb300.problem import HostProblem
+from synth.host_problem import HostProblem
 from oracle.operator import Problem
 from synth import Workload, trial_vectors
-from gpu_util import rel_err_cols, torch_dtype
+from gpu_util import parity_err, torch_dtype
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -56,7 +56,7 @@ def batch_setup():
 
 def _check(Ys, refs):
     for s, (Y, R) in enumerate(zip(Ys, refs)):
-        err = rel_err_cols(Y.double().cpu().numpy(), R.double().cpu().numpy())
+        err = parity_err(Y.double().cpu().numpy(), R.double().cpu().numpy())
         assert err <= TOL[PREC[s]], (s, err)
 
 
@@ -114,7 +114,7 @@ def test_aligned_rows_and_wide_projection_items():
                 fk.fe_ks_batch_apply(b, Xs, Ys, stream)
                 fk.fe_ks_batch_status(b)
                 for (_, _, _, pr), Y, R in zip(spec, Ys, refs):
-                    err = rel_err_cols(Y.double().cpu().numpy(), R.double().cpu().numpy())
+                    err = parity_err(Y.double().cpu().numpy(), R.double().cpu().numpy())
                     assert err <= TOL[pr], err
             with pytest.raises(fk.FeKsError, match="ERR_ARG"):
                 fk.fe_ks_batch_configure(b, [2, 0, 0], 1, 1, 2.0, False)    # tile configurations 0 / 1
@@ -134,7 +134,7 @@ def test_batched_fp64_systems_match_oracle(batch_setup):
     fk.fe_ks_batch_status(b)
     for s in (0, 2, 4):
         Yref = Problem(wls[s]).apply(Xs[s].cpu().numpy())
-        assert rel_err_cols(Ys[s].cpu().numpy(), Yref) <= 1e-12
+        assert parity_err(Ys[s].cpu().numpy(), Yref) <= 1e-12
 
 
 def test_batched_launch_in_cuda_graph(batch_setup):

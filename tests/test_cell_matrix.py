@@ -9,10 +9,10 @@ import numpy as np
 import pytest
 
 from paper_2512_08571_gb300 import fe_ks as fk
-from paper_2512_08571_gb300.problem import HostProblem
+from synth.host_problem import HostProblem
 from oracle.operator import Problem
 from synth import CONFIGS, trial_vectors
-from gpu_util import gpu_apply, rel_err_cols, round_input
+from gpu_util import gpu_apply, parity_err, round_input
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -60,7 +60,7 @@ def test_cell_matrix_matches_oracle(cases, key, precision):
     wl, hp, P, X = cases[key]
     Xin = round_input(X, precision)
     Y, ms, nbytes = cm_apply(hp, Xin, precision)
-    err = rel_err_cols(Y, P.apply(Xin))
+    err = parity_err(Y, P.apply(Xin))
     assert err <= TOL[precision], err
     esz = {fk.FE_KS_F64: 8, fk.FE_KS_F32: 4, fk.FE_KS_BF16: 2}[precision]
     assert nbytes >= wl.n_cells * (wl.p + 1) ** 6 * esz   # every cell matrix is held
@@ -73,7 +73,7 @@ def test_cell_matrix_equals_matrix_free(cases, key):
     wl, hp, P, X = cases[key]
     Ycm, _, _ = cm_apply(hp, X, fk.FE_KS_F64)
     Ymf = gpu_apply(hp, X, fk.FE_KS_F64)
-    assert rel_err_cols(Ycm, Ymf) <= 1e-13
+    assert parity_err(Ycm, Ymf) <= 1e-13
 
 
 def test_cell_matrix_terms_and_fewer_columns(cases):
@@ -83,7 +83,7 @@ def test_cell_matrix_terms_and_fewer_columns(cases):
     zero = lambda x: np.zeros(np.asarray(x).shape[:-1])
     P_T = Problem(wl, vloc=zero, vgga=None, with_atoms=False)
     Y, _, _ = cm_apply(hp, Xs, fk.FE_KS_F64, terms=fk.TERM_T, n_v_max=X.shape[1])
-    assert rel_err_cols(Y, P_T.apply(Xs)) <= 1e-12
+    assert parity_err(Y, P_T.apply(Xs)) <= 1e-12
 
 
 def test_cell_matrix_rejects_bad_arguments(cases):

@@ -9,10 +9,10 @@ import numpy as np
 import pytest
 
 from paper_2512_08571_gb300 import fe_ks as fk
-from paper_2512_08571_gb300.problem import HostProblem
+from synth.host_problem import HostProblem
 from oracle.operator import Problem
 from synth import CONFIGS, Workload, trial_vectors
-from gpu_util import gpu_apply, rel_err_cols, round_input
+from gpu_util import gpu_apply, parity_err, round_input
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -47,7 +47,7 @@ def test_apply_matches_oracle(cases, key, precision):
     Xin = round_input(X, precision)
     Y = gpu_apply(hp, Xin, precision)
     Yref = P.apply(Xin)
-    err = rel_err_cols(Y, Yref)
+    err = parity_err(Y, Yref)
     assert err <= TOL[precision], err
 
 
@@ -63,7 +63,7 @@ def test_every_tile_configuration(cases, key, config):
         except fk.FeKsError as exc:          # configuration too large for this degree/precision
             assert "configuration" in str(exc) or "invalid" in str(exc), exc
             continue
-        err = rel_err_cols(Y, P.apply(Xin))
+        err = parity_err(Y, P.apply(Xin))
         assert err <= TOL[precision], (config, precision, err)
 
 
@@ -74,7 +74,7 @@ def test_apply_scaled_matches_oracle(cases, precision):
     s = 1.0 / np.sqrt(P.lumped_mass())
     Y = gpu_apply(hp, Xin, precision, scaled=True)
     Yref = s[:, None] * P.apply(s[:, None] * Xin)
-    err = rel_err_cols(Y, Yref)
+    err = parity_err(Y, Yref)
     assert err <= TOL[precision], err
 
 
@@ -85,7 +85,7 @@ def test_every_degree_kinetic_and_local(p):
     P = Problem(wl)
     X = trial_vectors(wl)
     Y = gpu_apply(hp, X, fk.FE_KS_F64)
-    err = rel_err_cols(Y, P.apply(X))
+    err = parity_err(Y, P.apply(X))
     assert err <= 1e-12, err
 
 
@@ -94,20 +94,20 @@ def test_term_subsets(cases):
     zero = lambda x: np.zeros(np.asarray(x).shape[:-1])
     P_T = Problem(wl, vloc=zero, vgga=None, with_atoms=False)
     Y = gpu_apply(hp, X, fk.FE_KS_F64, terms=fk.TERM_T)
-    assert rel_err_cols(Y, P_T.apply(X)) <= 1e-12
+    assert parity_err(Y, P_T.apply(X)) <= 1e-12
     P_TL = Problem(wl, vgga=None, with_atoms=False)
     Y = gpu_apply(hp, X, fk.FE_KS_F64, terms=fk.TERM_T | fk.TERM_L)
-    assert rel_err_cols(Y, P_TL.apply(X)) <= 1e-12
+    assert parity_err(Y, P_TL.apply(X)) <= 1e-12
     P_loc = Problem(wl, with_atoms=False)
     Y = gpu_apply(hp, X, fk.FE_KS_F64, terms=fk.TERM_ALL & ~fk.TERM_NL)
-    assert rel_err_cols(Y, P_loc.apply(X)) <= 1e-12
+    assert parity_err(Y, P_loc.apply(X)) <= 1e-12
 
 
 def test_single_vector_and_bitwise_determinism(cases):
     wl, hp, P, X = cases["C3s"]
     Ys = gpu_apply(hp, X[:, :1], fk.FE_KS_F64, repeat=2)
     assert np.array_equal(Ys[0], Ys[1])
-    assert rel_err_cols(Ys[0], P.apply(X[:, :1])) <= 1e-12
+    assert parity_err(Ys[0], P.apply(X[:, :1])) <= 1e-12
 
 
 def test_zero_input_gives_zero(cases):
@@ -145,4 +145,4 @@ def test_nonlocal_term_isolated(cases, key, precision):
     Y_loc = gpu_apply(hp, Xin, precision, terms=fk.TERM_ALL & ~fk.TERM_NL)
     ref = P.apply(Xin) - Problem(wl, with_atoms=False).apply(Xin)
     tol = {fk.FE_KS_F64: 1e-9, fk.FE_KS_F64E: 1e-9, fk.FE_KS_F32: 1e-2}[precision]
-    assert rel_err_cols(Y_all - Y_loc, ref) <= tol
+    assert parity_err(Y_all - Y_loc, ref) <= tol

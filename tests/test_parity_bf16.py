@@ -20,10 +20,10 @@ import numpy as np
 import pytest
 
 from paper_2512_08571_gb300 import fe_ks as fk
-from paper_2512_08571_gb300.problem import HostProblem
+from synth.host_problem import HostProblem
 from oracle.operator import Problem
 from synth import CONFIGS, Workload, trial_vectors
-from gpu_util import gpu_apply, rel_err_cols, round_input
+from gpu_util import gpu_apply, parity_err, round_input
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -58,7 +58,7 @@ def test_bf16_matches_oracle(cases, key, prec):
     wl, hp, P, X = cases[key]
     Xin = round_input(X, prec)
     Y = gpu_apply(hp, Xin, prec)
-    err = rel_err_cols(Y, P.apply(Xin))
+    err = parity_err(Y, P.apply(Xin))
     print(f"{key}: {NAME[prec]} tensor-core rel err {err:.3e} (tolerance {TOL16[prec]:.3e})")
     assert err <= TOL16[prec], err
 
@@ -73,7 +73,7 @@ def test_f16_tile_scaling_range(cases, scale):
     Xin = round_input(X * scale, fk.FE_KS_F16)
     Y = gpu_apply(hp, Xin, fk.FE_KS_F16)
     assert np.all(np.isfinite(Y))
-    err = rel_err_cols(Y, P.apply(Xin))
+    err = parity_err(Y, P.apply(Xin))
     assert err <= TOL16[fk.FE_KS_F16], (scale, err)
 
 
@@ -82,7 +82,7 @@ def test_bf16_scaled_matches_oracle(cases):
     Xin = round_input(X, BF)
     s = 1.0 / np.sqrt(P.lumped_mass())
     Y = gpu_apply(hp, Xin, BF, scaled=True)
-    err = rel_err_cols(Y, s[:, None] * P.apply(s[:, None] * Xin))
+    err = parity_err(Y, s[:, None] * P.apply(s[:, None] * Xin))
     assert err <= TOL, err
 
 
@@ -94,7 +94,7 @@ def test_bf16_every_degree(p, prec):
     hp = HostProblem(wl)
     P = Problem(wl)
     X = round_input(trial_vectors(wl), prec)
-    err = rel_err_cols(gpu_apply(hp, X, prec), P.apply(X))
+    err = parity_err(gpu_apply(hp, X, prec), P.apply(X))
     assert err <= TOL16[prec], (p, err)
 
 
@@ -103,9 +103,9 @@ def test_bf16_term_subsets(cases):
     X = round_input(X, BF)
     zero = lambda x: np.zeros(np.asarray(x).shape[:-1])
     P_T = Problem(wl, vloc=zero, vgga=None, with_atoms=False)
-    assert rel_err_cols(gpu_apply(hp, X, BF, terms=fk.TERM_T), P_T.apply(X)) <= TOL
+    assert parity_err(gpu_apply(hp, X, BF, terms=fk.TERM_T), P_T.apply(X)) <= TOL
     P_loc = Problem(wl, with_atoms=False)
-    assert rel_err_cols(gpu_apply(hp, X, BF, terms=fk.TERM_ALL & ~fk.TERM_NL), P_loc.apply(X)) <= TOL
+    assert parity_err(gpu_apply(hp, X, BF, terms=fk.TERM_ALL & ~fk.TERM_NL), P_loc.apply(X)) <= TOL
 
 
 def test_bf16_deterministic_and_zero(cases):
@@ -122,8 +122,8 @@ def test_bf16_close_to_fp32_kernel(cases):
     X = round_input(X, BF)
     Yb = gpu_apply(hp, X, BF)
     Yf = gpu_apply(hp, X, fk.FE_KS_F32)
-    assert rel_err_cols(Yb, Yf) <= TOL
-    assert rel_err_cols(Yb, Yf) > 1e-6   # really a different (lower-precision) arithmetic
+    assert parity_err(Yb, Yf) <= TOL
+    assert parity_err(Yb, Yf) > 1e-6   # really a different (lower-precision) arithmetic
 
 
 @pytest.mark.parametrize("prec", TC)
@@ -140,7 +140,7 @@ def test_bf16_nonlocal_term_isolated(cases, key, prec):
     Y_all = gpu_apply(hp, X, prec)
     Y_loc = gpu_apply(hp, X, prec, terms=fk.TERM_ALL & ~fk.TERM_NL)
     ref = P.apply(X) - Problem(wl, with_atoms=False).apply(X)
-    err = rel_err_cols(Y_all - Y_loc, ref)
+    err = parity_err(Y_all - Y_loc, ref)
     print(f"{key}: {NAME[prec]} nonlocal term rel err {err:.3e}")
     # FP32 rounding of the accumulators relative to the term (6e-3, see above) bounds FP16 too
     assert err <= max(TOL16[prec], 1e-2), err
@@ -155,5 +155,5 @@ def test_columns_of_very_different_size(cases, prec):
     Xs = X * (10.0 ** -np.arange(X.shape[1]))[None, :]
     Xin = round_input(Xs, prec)
     Y = gpu_apply(hp, Xin, prec)
-    err = rel_err_cols(Y, P.apply(Xin))
+    err = parity_err(Y, P.apply(Xin))
     assert err <= TOL16[prec], err

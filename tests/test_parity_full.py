@@ -15,10 +15,10 @@ import numpy as np
 import pytest
 
 from paper_2512_08571_gb300 import fe_ks as fk
-from paper_2512_08571_gb300.problem import HostProblem
+from synth.host_problem import HostProblem
 from oracle.operator import Problem
 from synth import CONFIGS
-from gpu_util import RowCache, needed_rows, fill_device, rel_err_cols, torch_dtype
+from gpu_util import RowCache, needed_rows, fill_device, parity_err, torch_dtype
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -67,7 +67,7 @@ def test_full_size_sampled_rows(key):
             torch.cuda.empty_cache()
             Xl = RowCache(wl, need, round_to=npdt)
             Yref = P.apply_rows(Xl, rows)
-            err = rel_err_cols(Yg, Yref)
+            err = parity_err(Yg, Yref)
             assert err <= TOL[precision], (key, precision, err)
     finally:
         fk.fe_ks_destroy(ctx)
@@ -100,7 +100,7 @@ def test_cell_matrix_full_size_sampled_rows():
             torch.cuda.empty_cache()
             if npdt not in refs:
                 refs[npdt] = P.apply_rows(RowCache(wl, need, round_to=npdt), rows)
-            err = rel_err_cols(Yg, refs[npdt])
+            err = parity_err(Yg, refs[npdt])
             assert err <= tol, (precision, err)
     finally:
         fk.fe_ks_destroy(ctx)
@@ -138,7 +138,7 @@ def test_batched_c5_full_size_sampled_rows(threads, occ):
             rows = _rows(P, wl, 50 + s)
             Yg = Y[torch.from_numpy(rows).cuda()].cpu().numpy()
             Yref = P.apply_rows(RowCache(wl, needed_rows(P, rows), round_to=npdt), rows)
-            err = rel_err_cols(Yg, Yref)
+            err = parity_err(Yg, Yref)
             assert err <= (1e-12 if pr == fk.FE_KS_F64 else 1e-5), (s, err)
     finally:
         for c in ctxs:
@@ -147,8 +147,8 @@ def test_batched_c5_full_size_sampled_rows(threads, occ):
 
 def test_filter_pass_full_size():
     """One degree-20 R-ChFSI filter pass at C4 (the bench's pass): the FP32 recurrence stays
-    within 2e-4 per column and the pairs-of-floats recurrence within 1e-10 of the FP64 one
-    (the bounds of the small-size comparison with the oracle's Algorithm 4)."""
+    within 2e-4 and the pairs-of-floats recurrence within 1e-12 of the FP64 one, per column
+    and element-wise (the bounds of the small-size comparison with the oracle's Algorithm 4)."""
     from paper_2512_08571_gb300.chfsi import RChFSI
     wl = CONFIGS["C4"]
     hp = HostProblem(wl)
@@ -164,14 +164,16 @@ def test_filter_pass_full_size():
         ref.filter(X64, lam)
         del ref
         torch.cuda.empty_cache()
-        for prec, exact, tol in ((fk.FE_KS_F32, fk.FE_KS_F64E, 2e-4), (fk.FE_KS_F64E, fk.FE_KS_F64E, 1e-10)):
+        for prec, exact, tol in ((fk.FE_KS_F32, fk.FE_KS_F64E, 2e-4), (fk.FE_KS_F64E, fk.FE_KS_F64E, 1e-12)):
             sol = RChFSI(ctx, hp.m, wl.n_v, False, degree=20, precision=prec, exact=exact, gemm_pairs=True)
             sol.lmax = lmax
             Xp = X.clone()
             sol.filter(Xp, lam)
             torch.cuda.synchronize()
-            err = float(torch.max(torch.linalg.vector_norm(Xp - X64, dim=0) /
-                                  torch.linalg.vector_norm(X64, dim=0)))
+            d = Xp - X64
+            err = max(float(torch.max(torch.linalg.vector_norm(d, dim=0) / torch.linalg.vector_norm(X64, dim=0))),
+                      float(torch.max(d.abs().amax(0) / X64.abs().amax(0))))
+            del d
             assert err < tol, (prec, err)
             del sol, Xp
             torch.cuda.empty_cache()

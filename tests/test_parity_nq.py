@@ -11,10 +11,10 @@ import numpy as np
 import pytest
 
 from paper_2512_08571_gb300 import fe_ks as fk
-from paper_2512_08571_gb300.problem import HostProblem
+from synth.host_problem import HostProblem
 from oracle.operator import Problem
 from synth import CONFIGS, trial_vectors
-from gpu_util import gpu_apply, rel_err_cols, round_input
+from gpu_util import gpu_apply, parity_err, round_input
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -46,7 +46,7 @@ def cases():
 def test_apply_nq_np2_matches_oracle(cases, key, precision):
     wl, hp, P, X = cases[key]
     Xin = round_input(X, precision)
-    err = rel_err_cols(gpu_apply(hp, Xin, precision), P.apply(Xin))
+    err = parity_err(gpu_apply(hp, Xin, precision), P.apply(Xin))
     assert err <= TOL[precision], err
 
 
@@ -72,7 +72,7 @@ def test_every_fitting_tile_configuration(cases, key):
                 Yd.fill_(float("nan"))
                 fk.fe_ks_apply(ctx, Xd, Yd, n_v, precision)
                 torch.cuda.synchronize()
-                err = rel_err_cols(Yd.cpu().numpy(), Yref)
+                err = parity_err(Yd.cpu().numpy(), Yref)
                 assert err <= TOL[precision], (precision, cfg, err)
         finally:
             fk.fe_ks_destroy(ctx)
@@ -84,7 +84,7 @@ def test_scaled_apply_nq_np2(cases):
     d = 1.0 / np.sqrt(P.lumped_mass())
     Y = gpu_apply(hp, X, fk.FE_KS_F64, scaled=True)
     Yref = d[:, None] * P.apply(d[:, None] * X)
-    assert rel_err_cols(Y, Yref) <= 1e-12
+    assert parity_err(Y, Yref) <= 1e-12
 
 
 def test_tensor_core_precisions_refuse_nq_np2(cases):
@@ -106,7 +106,7 @@ def test_cell_matrix_nq_np2(cases):
             Yd = torch.empty_like(Xd)
             fk.fe_ks_cm_apply(cm, Xd, Yd, n_v)
             torch.cuda.synchronize()
-            assert rel_err_cols(Yd.cpu().numpy(), P.apply(X)) <= 1e-12
+            assert parity_err(Yd.cpu().numpy(), P.apply(X)) <= 1e-12
         finally:
             fk.fe_ks_cm_destroy(cm)
     finally:

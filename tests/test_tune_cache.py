@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from paper_2512_08571_gb300 import fe_ks as fk
-from paper_2512_08571_gb300.problem import HostProblem
+from synth.host_problem import HostProblem
 from synth import CONFIGS, trial_vectors
 
 torch = pytest.importorskip("torch")

@@ -5,17 +5,19 @@ another allocator, or a code path where an allocation would synchronise the
 device or break a memory budget): they pass every input and output, and the
 call keeps its scratch in a static device array.  Its output must equal the
 existing entry point's nonlocal term (fe_ks_apply with FE_KS_TERM_NL only)
-within the FP64 tolerance of the other parity tests, on two calls in a row
-with different inputs.  This file is collected last on purpose.
+and the oracle's nonlocal term F diag(h) F^H X, within the FP64 tolerance of
+the other parity tests (per column and element-wise), on two calls in a row
+with different inputs; and the second call must leave the device's free
+memory unchanged.  This file is collected last on purpose.
 """
 import numpy as np
 import pytest
 
 from paper_2512_08571_gb300 import fe_ks as fk
-from paper_2512_08571_gb300.problem import HostProblem
+from synth.host_problem import HostProblem
 from oracle.operator import Problem
 from synth import CONFIGS, trial_vectors
-from gpu_util import gpu_apply, rel_err_cols
+from gpu_util import gpu_apply, parity_err
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -49,16 +51,26 @@ def test_static_scratch_matches_existing_entry_point(wl):
     d_h = dev(P.h.astype(np.float64))
     cplx = hp.complex
     stream = torch.cuda.current_stream().cuda_stream
+    free_after = []
     for seed in (5, 6):                       # two calls in a row, different inputs
         X = trial_vectors(wl, seed_purpose=seed)
         want = gpu_apply(hp, X, fk.FE_KS_F64, terms=fk.TERM_NL)
+        oracle_nl = P.apply(X, local=False, nonlocal_=True)
         Xd = torch.from_numpy(X).cuda()
         Yd = torch.zeros_like(Xd)
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         fk.fe_ks_nonlocal_apply_static(Xd, Yd, wl.n_v, cplx, wl.p, hp.m, d_dofs, P.R.shape[0], 9, d_ptr,
                                        d_cells, d_atom, len(cells), d_F, d_h, stream)
         torch.cuda.synchronize()
-        err = rel_err_cols(Yd.cpu().numpy(), want)
+        free_after.append(torch.cuda.mem_get_info()[0] - free_before)
+        got = Yd.cpu().numpy()
+        err = parity_err(got, want)
         assert err <= 1e-12, (seed, err)
+        err_o = parity_err(got, oracle_nl)
+        assert err_o <= 1e-12, (seed, err_o)
+    # the first call may load the module's kernels; the second allocates nothing at all
+    assert free_after[1] == 0, free_after
 
 
 def test_static_scratch_rejects_oversize():

@@ -461,6 +461,64 @@ fe_ks_status fe_ks_gram_ff_sym(const double* Y, const double* Z, double* C, int6
 fe_ks_status fe_ks_rotate_ff(const double* Y, const double* E, double* X, int64_t m, int n, int k,
                              void* cuda_stream);
 
+/*
+ * Rayleigh-Ritz step of Algorithm 3 on span(X), the FP64-accurate projection
+ * the R-ChFSI outer loop performs after each filter (Sec. 5.5: the filter may
+ * run in low precision, this step may not).  Standard form (mass == NULL):
+ * Op = Hs = D^{-1/2} H D^{-1/2} and metric I.  Generalised form (eq. FEeigen):
+ * Op = H and metric M, `mass` being a context whose application is M (see
+ * fe_ks_cheb_filter_ghep).  It solves (X^T Op X) E = (X^T M X) E Lam, with
+ * E^T (X^T M X) E = I, and overwrites X by X E and ritz by Lam (ascending):
+ *   S = X^T M X; S' = d S d with d = diag(S)^{-1/2}; S' = L L^T (Cholesky);
+ *   A = X^T Op X; L^{-1} (d A d) L^{-T} = W Lam W^T; E = d L^{-T} W.
+ * The tall products (X^T M X, X^T Op X, X E) and the applications take
+ * `precision`: FE_KS_F64E = the library's pair-of-floats Gram and rotation
+ * kernels and pair-of-floats applications (FP64-accurate on the FP32 pipe);
+ * FE_KS_F64 = native FP64 applications and cuBLAS FP64 GEMMs (the plain
+ * FP64 comparator).  The n_v x n_v Cholesky, scaling and triangular solves
+ * are the library's kernels; the n_v x n_v symmetric eigensolve is
+ * cuSOLVER's syevd.  If a pivot of S' falls below 1e-10 (X nearly
+ * rank-deficient) the step first orthonormalises X in the metric by shifted
+ * CholeskyQR3 (three Cholesky-QR passes, the first with a shift) and projects
+ * onto the orthonormal block; *path (may be NULL) returns 0 for the Cholesky
+ * path and 1 for that fallback.
+ *  X      : device FP64 [m][n_v] row-major, in/out (real operators only).
+ *  ritz   : device FP64 [n_v], out.
+ *  work   : device, >= fe_ks_rayleigh_ritz_workspace bytes, 256-byte aligned,
+ *           caller-owned, must not overlap X.
+ * The call synchronises the context's stream twice (it reads the Cholesky
+ * status and the eigensolver status).  The first call on a device (also
+ * through the workspace query) creates a cuSOLVER handle, which allocates.
+ * Errors: FE_KS_ERR_UNSUPPORTED for complex operators; FE_KS_ERR_ARG for an X
+ * that even the shifted Cholesky QR cannot orthonormalise, bad sizes, a short
+ * workspace or overlap; FE_KS_ERR_CUDA.
+ */
+fe_ks_status fe_ks_rayleigh_ritz_workspace(const fe_ks_ctx* ctx, int64_t n_v, int precision, size_t* bytes);
+fe_ks_status fe_ks_rayleigh_ritz(fe_ks_ctx* ctx, fe_ks_ctx* mass, double* X, double* ritz, int64_t n_v, int precision,
+                                 void* work, size_t work_bytes, int* path);
+
+/*
+ * Upper bound of the spectrum of Hs = D^{-1/2} H D^{-1/2} for the filter's
+ * lam_max (Algorithm 4 takes the bounds as inputs; the paper gives no method):
+ * `steps` steps of the symmetric Lanczos recurrence from the start vector v0,
+ *   v_1 = v0/|v0|;  w = Hs v_j - alpha_j v_j - beta_{j-1} v_{j-1},
+ *   alpha_j = v_j^H Hs v_j,  beta_j = |w|,  v_{j+1} = w / beta_j,
+ * then lam_max = theta_max(T_k) + |beta_k| with T_k the k x k tridiagonal
+ * matrix of the coefficients (the standard safe bound).  The recurrence runs
+ * on the device (applications in `precision`, FE_KS_F64 or FE_KS_F64E;
+ * fixed-order reductions, so the result is deterministic); the host then
+ * reads the 2k coefficients (one stream synchronisation) and finds
+ * theta_max by Sturm-sequence bisection.  A beta that vanishes exactly
+ * stops the recurrence there (k < steps, reported in *steps_done).
+ *  v0     : device FP64 [m] (complex operators: [m] interleaved complex).
+ *  lam_max: host, out.  alpha, beta: host [steps] or NULL, out (the first k used).
+ *  work   : device, >= fe_ks_lanczos_bound_workspace bytes (three vectors and
+ *           the reduction scratch), 256-byte aligned, caller-owned.
+ */
+fe_ks_status fe_ks_lanczos_bound_workspace(const fe_ks_ctx* ctx, int steps, size_t* bytes);
+fe_ks_status fe_ks_lanczos_bound(fe_ks_ctx* ctx, const double* v0, int steps, int precision, void* work,
+                                 size_t work_bytes, double* lam_max, double* alpha, double* beta, int* steps_done);
+
 /* Change the stream used by later calls. */
 fe_ks_status fe_ks_set_stream(fe_ks_ctx* ctx, void* cuda_stream);
 

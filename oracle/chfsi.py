@@ -83,6 +83,12 @@ def filter_reference_polynomial(evals, evecs, X, degree, lmin, lT, lmax):
 
 def lanczos_upper_bound(apply_Hs, v0, steps=10):
     """Upper bound of the spectrum of Hs: theta_max(T_k) + |beta_k| after k Lanczos steps."""
+    return lanczos_coefficients(apply_Hs, v0, steps)[2]
+
+
+def lanczos_coefficients(apply_Hs, v0, steps=10):
+    """k steps of the symmetric Lanczos recurrence from v0: (alphas, betas, bound) with the
+    bound theta_max(T_k) + |beta_k| of lanczos_upper_bound."""
     v = v0 / np.linalg.norm(v0)
     v_prev = np.zeros_like(v)
     alphas, betas = [], []
@@ -98,7 +104,7 @@ def lanczos_upper_bound(apply_Hs, v0, steps=10):
             break
         v_prev, v = v, w / beta
     T = np.diag(alphas) + np.diag(betas[:-1], 1) + np.diag(betas[:-1], -1)
-    return float(np.max(np.linalg.eigvalsh(T)) + abs(betas[-1]))
+    return np.array(alphas), np.array(betas), float(np.max(np.linalg.eigvalsh(T)) + abs(betas[-1]))
 
 
 def rayleigh_ritz(apply_Hs, Y):

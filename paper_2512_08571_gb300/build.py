@@ -33,7 +33,7 @@ def _nvcc():
 
 def _units():
     units = []
-    for name in ("fe_ks_api.cu", "fe_ks_tables.cu", "fe_ks_nonlocal.cu", "fe_ks_probe.cu", "fe_ks_cheb.cu", "fe_ks_static.cu", "fe_ks_batched.cu", "fe_ks_gemm.cu", "fe_ks_ffgemm.cu", "fe_ks_tc.cu", "fe_ks_cm.cu"):
+    for name in ("fe_ks_api.cu", "fe_ks_tables.cu", "fe_ks_nonlocal.cu", "fe_ks_probe.cu", "fe_ks_cheb.cu", "fe_ks_static.cu", "fe_ks_batched.cu", "fe_ks_gemm.cu", "fe_ks_ffgemm.cu", "fe_ks_tc.cu", "fe_ks_cm.cu", "fe_ks_rr.cu"):
         units.append((os.path.join(CSRC, name), os.path.join(BUILD, name + ".o"), []))
     for nt in BATCH_THREADS:
         units.append((os.path.join(CSRC, "fe_ks_batched_k.cu"),
@@ -83,7 +83,7 @@ def build(force=False, verbose=False, jobs=None):
         objs = list(ex.map(compile_one, _units()))
     tmp = LIB + ".tmp"
     cuda_lib = os.path.join(os.path.dirname(os.path.dirname(nvcc)), "lib64")
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcublas", "-Xlinker", "-rpath", "-Xlinker", cuda_lib]
+    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcublas", "-lcusolver", "-Xlinker", "-rpath", "-Xlinker", cuda_lib]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -4,13 +4,14 @@ The caller's side of ``fe_ks_cheb_filter``: the outer subspace iteration of
 Algorithm 3 in the standard form Hs = D^{-1/2} H D^{-1/2} (D the GLL-lumped
 mass), or, given a context whose application is the consistent mass M, for
 the generalised problem H X = M X Lam (``fe_ks_cheb_filter_ghep``; the
-Rayleigh-Ritz step then solves (Y^H H Y) E = (Y^H M Y) E Lam).  Each iteration filters the block with the library's residual-based
-Chebyshev filter and then performs the Rayleigh-Ritz step in FP64
-(orthonormalisation and the projected N_v x N_v eigenproblem as dense library
-GEMM / QR / symmetric eigensolver calls on the device).  Spectral bounds: the
-upper bound from k Lanczos steps (theta_max + |beta_k|, the standard safe
-bound), the lower bound and the wanted-spectrum edge from the current Ritz
-values.
+Rayleigh-Ritz step then solves (Y^H H Y) E = (Y^H M Y) E Lam).  Each
+iteration filters the block with the library's residual-based Chebyshev
+filter and then performs the FP64-accurate Rayleigh-Ritz step.  For real
+operators every step is a library call: fe_ks_lanczos_bound (the upper bound
+theta_max + |beta_k| after k Lanczos steps), fe_ks_cheb_filter and
+fe_ks_rayleigh_ritz.  Complex operators keep the Rayleigh-Ritz step in
+dense torch calls on the device (the library's Rayleigh-Ritz is real only).
+The lower bound and the wanted-spectrum edge are the current Ritz values.
 """
 import torch
 
@@ -35,6 +36,9 @@ class RChFSI:
         self.gemm_emulated = gemm_emulated and not cplx
         self.gemm_pairs = gemm_pairs and not cplx
         self._gram_work = None
+        self._lz = None
+        self._rr = None
+        self.rr_path = None
         self.dt = torch.complex128 if cplx else torch.float64
         self.dev = torch.device("cuda", torch.cuda.current_device())
         nb = fk.fe_ks_cheb_filter_workspace(ctx, n_v, precision)
@@ -69,7 +73,26 @@ class RChFSI:
         fk.fe_ks_apply(self.mass, V, out, V.shape[1], self.exact)
         return out
 
+    def _aligned(self, nbytes):
+        buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.dev)
+        off = (-buf.data_ptr()) % 256
+        return buf, buf[off:off + nbytes]
+
     def lanczos_upper_bound(self, seed=0):
+        """fe_ks_lanczos_bound from a seeded normal start vector."""
+        g = torch.Generator(device=self.dev)
+        g.manual_seed(seed)
+        v = torch.randn((self.m, 1), generator=g, device=self.dev, dtype=torch.float64).to(self.dt).contiguous()
+        if self._lz is None:
+            nb = fk.fe_ks_lanczos_bound_workspace(self.ctx, self.lanczos_steps)
+            self._lz = self._aligned(nb) + (nb,)
+        _, view, nb = self._lz
+        self.lmax, self.lanczos_alpha, self.lanczos_beta = fk.fe_ks_lanczos_bound(
+            self.ctx, v, self.lanczos_steps, self.exact, view, nb)
+        return self.lmax
+
+    def lanczos_upper_bound_torch(self, seed=0):
+        """The same bound with dense torch calls (kept for comparison)."""
         g = torch.Generator(device=self.dev)
         g.manual_seed(seed)
         v = torch.randn((self.m, 1), generator=g, device=self.dev, dtype=torch.float64).to(self.dt)
@@ -98,6 +121,20 @@ class RChFSI:
         return self.lmax
 
     def rayleigh_ritz(self, Y):
+        """Rayleigh-Ritz on span(Y); returns (Lam, Y E) (real operators: fe_ks_rayleigh_ritz, in place)."""
+        if self.cplx or self.gemm_emulated:
+            return self.rayleigh_ritz_torch(Y)
+        Y = Y.contiguous()
+        prec = fk.FE_KS_F64E if self.gemm_pairs else fk.FE_KS_F64
+        if self._rr is None or self._rr[0] != prec:
+            nb = fk.fe_ks_rayleigh_ritz_workspace(self.ctx, self.n_v, prec)
+            self._rr = (prec, nb) + self._aligned(nb)
+        _, nb, _, view = self._rr
+        lam = torch.empty(self.n_v, dtype=torch.float64, device=self.dev)
+        self.rr_path = fk.fe_ks_rayleigh_ritz(self.ctx, Y, lam, self.n_v, prec, view, nb, mass=self.mass)
+        return lam, Y
+
+    def rayleigh_ritz_torch(self, Y):
         """Rayleigh-Ritz on span(Y): (Y^H Hs Y) E = (Y^H Y) E Lam, returns (Lam, Y E).
 
         Cholesky of the Gram matrix S = Y^H Y = L L^H reduces it to the standard

@@ -92,6 +92,12 @@ def _load():
     lib.fe_ks_gram_ff.argtypes = [vp, vp, vp, i64, ctypes.c_int, ctypes.c_int, vp, ctypes.c_size_t, vp]
     lib.fe_ks_gram_ff_sym.argtypes = [vp, vp, vp, i64, ctypes.c_int, vp, ctypes.c_size_t, vp]
     lib.fe_ks_rotate_ff.argtypes = [vp, vp, vp, i64, ctypes.c_int, ctypes.c_int, vp]
+    lib.fe_ks_rayleigh_ritz_workspace.argtypes = [vp, i64, ctypes.c_int, P(ctypes.c_size_t)]
+    lib.fe_ks_rayleigh_ritz.argtypes = [vp, vp, vp, vp, i64, ctypes.c_int, vp, ctypes.c_size_t, P(ctypes.c_int)]
+    lib.fe_ks_lanczos_bound_workspace.argtypes = [vp, ctypes.c_int, P(ctypes.c_size_t)]
+    lib.fe_ks_lanczos_bound.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_size_t,
+                                        P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
+                                        P(ctypes.c_int)]
     lib.fe_ks_destroy.argtypes = [vp]
     lib.fe_ks_destroy.restype = None
     for name in ("fe_ks_quadrature_points", "fe_ks_setup", "fe_ks_apply", "fe_ks_apply_scaled",
@@ -101,7 +107,8 @@ def _load():
                  "fe_ks_nonlocal_apply_static", "fe_ks_tune", "fe_ks_set_config", "fe_ks_batch_create",
                  "fe_ks_batch_configure", "fe_ks_batch_apply", "fe_ks_batch_status", "fe_ks_batch_info",
                  "fe_ks_gemm_f64", "fe_ks_gram_ff_workspace", "fe_ks_gram_ff", "fe_ks_rotate_ff",
-                 "fe_ks_gram_ff_sym"):
+                 "fe_ks_gram_ff_sym", "fe_ks_rayleigh_ritz_workspace", "fe_ks_rayleigh_ritz",
+                 "fe_ks_lanczos_bound_workspace", "fe_ks_lanczos_bound"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -337,6 +344,38 @@ def fe_ks_rotate_ff(Y, E, stream=None):
     X = torch.empty((m, k), dtype=torch.float64, device=Y.device)
     _check(_lib.fe_ks_rotate_ff(_ptr(Y), _ptr(E.contiguous()), _ptr(X), m, n, k, stream))
     return X
+
+
+def fe_ks_rayleigh_ritz_workspace(ctx, n_v, precision):
+    out = ctypes.c_size_t()
+    _check(_lib.fe_ks_rayleigh_ritz_workspace(ctx, n_v, precision, ctypes.byref(out)))
+    return out.value
+
+
+def fe_ks_rayleigh_ritz(ctx, X, ritz, n_v, precision, work, work_bytes, mass=None):
+    """Rayleigh-Ritz on span(X) in place (X <- X E, ritz <- Lam); returns the path taken
+    (0 Cholesky, 1 shifted Cholesky QR)."""
+    path = ctypes.c_int()
+    _check(_lib.fe_ks_rayleigh_ritz(ctx, mass, _ptr(X), _ptr(ritz), n_v, precision, _ptr(work), work_bytes,
+                                    ctypes.byref(path)))
+    return path.value
+
+
+def fe_ks_lanczos_bound_workspace(ctx, steps):
+    out = ctypes.c_size_t()
+    _check(_lib.fe_ks_lanczos_bound_workspace(ctx, steps, ctypes.byref(out)))
+    return out.value
+
+
+def fe_ks_lanczos_bound(ctx, v0, steps, precision, work, work_bytes):
+    """Lanczos upper bound of Hs from the device vector v0: (lam_max, alphas, betas)."""
+    lm = ctypes.c_double()
+    a = (ctypes.c_double * steps)()
+    b = (ctypes.c_double * steps)()
+    k = ctypes.c_int()
+    _check(_lib.fe_ks_lanczos_bound(ctx, _ptr(v0), steps, precision, _ptr(work), work_bytes, ctypes.byref(lm),
+                                    a, b, ctypes.byref(k)))
+    return lm.value, list(a)[:k.value], list(b)[:k.value]
 
 
 def fe_ks_dinv_sqrt(ctx):

@@ -243,7 +243,12 @@ fe_ks_status fe_ks_cheb_filter_ghep(fe_ks_ctx* ctx, fe_ks_ctx* mass, double* X, 
  *   0..2  one CTA per (cell, column tile), 3 tile widths;
  *   3..4  one CTA per cell walking all column tiles, the next tile's rows of X
  *         staged by cp.async, reduction-based scatter;
- *   5..6  as 3..4 with 2 or 4 adjacent columns per thread.
+ *   5..6  as 3..4 with 2 or 4 adjacent columns per thread;
+ *   7..9  "lean" one-CTA-per-cell walks: a single staging buffer refilled
+ *         with the next tile's rows as soon as the first sweep has read it,
+ *         coefficients read through the L1 instead of staged, so two (7, 8)
+ *         or three (9) CTAs share an SM (8 columns with 2 or 4 per thread;
+ *         4 columns with 2 per thread).
  * 0 is the default; there are FE_KS_N_CONFIGS choices.
  *
  * fe_ks_tune times every configuration with fe_ks_apply on the caller's X and
@@ -258,7 +263,7 @@ fe_ks_status fe_ks_cheb_filter_ghep(fe_ks_ctx* ctx, fe_ks_ctx* mass, double* X, 
  * fe_ks_set_config sets the configuration directly (and explicitly);
  * fe_ks_get_config reads the current one.
  */
-#define FE_KS_N_CONFIGS 7
+#define FE_KS_N_CONFIGS 10
 fe_ks_status fe_ks_tune(fe_ks_ctx* ctx, const void* X, void* Y, int64_t n_v, int precision, int reps,
                         double* ms_per_config, int* best);
 fe_ks_status fe_ks_set_config(fe_ks_ctx* ctx, int precision, int config);

@@ -191,7 +191,7 @@ fe_ks_status apply_core(Ctx& c, const T* X, T* Y, int64_t ncols, bool scaled, T 
 fe_ks_status apply_core_emu(Ctx& c, const double* X, double* Y, int64_t ncols, bool scaled, double alpha,
                             bool zero_fill);
 
-constexpr int kLocalConfigs = 7;
+constexpr int kLocalConfigs = 10;
 
 // kernel launchers (fe_ks_local_pN.cu)
 template <typename T, typename TS>

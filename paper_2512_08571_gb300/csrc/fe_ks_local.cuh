@@ -455,9 +455,27 @@ __device__ __forceinline__ void st_cols(T* p, const T* in) {
 // for its VPT columns; for complex operators the re/im partner column sits in
 // the same thread).  Gathers from the staged buffer xs only; scatters with
 // reductions.  Same arithmetic, in the same order per column, as tile_body.
-template <typename T, int NP, int NQ, int VT, int VPT, bool CPLX, int NT, class Prm>
+struct NoHook {
+  __device__ __forceinline__ void operator()() const {}
+};
+
+// Coefficient read: from shared memory (staged) or from global memory through
+// the read-only L1 path (GLOBAL_CF).
+template <bool GLOBAL_CF, typename T>
+__device__ __forceinline__ T ld_coef(const T* p) {
+  if constexpr (GLOBAL_CF)
+    return __ldg(p);
+  else
+    return *p;
+}
+
+// after1: called by every thread right after phase (1) has finished reading xs
+// (after its barrier), so a single staging buffer can be refilled while
+// phases (2)-(9) run.
+template <typename T, int NP, int NQ, int VT, int VPT, bool CPLX, int NT, class Prm, bool GLOBAL_CF = false,
+          class Hook = NoHook>
 __device__ __forceinline__ void tile_body_v(const Prm& p, const EOTables<T>& tb, int e, int col0, T* A, T* B, T* C,
-                                            const T* cfs, const int* sd, const T* xs) {
+                                            const T* cfs, const int* sd, const T* xs, Hook after1 = Hook()) {
   using S = CellShape<T, NP, NQ, VT, CPLX>;
   constexpr int SX = S::SX, SY = S::SY, SZ = S::SZ, NQ3 = S::NQ3, NP3 = S::NP3;
   constexpr int VG = VT / VPT;
@@ -494,6 +512,7 @@ __device__ __forceinline__ void tile_body_v(const Prm& p, const EOTables<T>& tb,
     for (int q = 0; q < NQ; ++q) st_cols<T, VPT>(A + i * SX + j * SY + q * SZ + v0, o[q]);
   }
   __syncthreads();
+  after1();
   // (2) N^1D along y
 #pragma unroll 1
   for (int w = tid; w < NP * NQ * VG; w += NT) {
@@ -601,14 +620,15 @@ __device__ __forceinline__ void tile_body_v(const Prm& p, const EOTables<T>& tb,
       T gx[VPT], gy[VPT], w0[VPT], w1[VPT], kk[VPT];
       ld_cols<T, VPT>(B + s, gx);
       ld_cols<T, VPT>(C + s, gy);
-      const T G00 = cf[0 * NQ3 + o], G01 = cf[1 * NQ3 + o], G02 = cf[2 * NQ3 + o];
-      const T G11 = cf[3 * NQ3 + o], G12 = cf[4 * NQ3 + o], G22 = cf[5 * NQ3 + o];
-      const T VL = cf[6 * NQ3 + o];
+      const T G00 = ld_coef<GLOBAL_CF>(cf + 0 * NQ3 + o), G01 = ld_coef<GLOBAL_CF>(cf + 1 * NQ3 + o);
+      const T G02 = ld_coef<GLOBAL_CF>(cf + 2 * NQ3 + o), G11 = ld_coef<GLOBAL_CF>(cf + 3 * NQ3 + o);
+      const T G12 = ld_coef<GLOBAL_CF>(cf + 4 * NQ3 + o), G22 = ld_coef<GLOBAL_CF>(cf + 5 * NQ3 + o);
+      const T VL = ld_coef<GLOBAL_CF>(cf + 6 * NQ3 + o);
       T V0 = Num<T>::zero(), V1 = V0, V2 = V0;
       if (p.gga) {
-        V0 = cf[7 * NQ3 + o];
-        V1 = cf[8 * NQ3 + o];
-        V2 = cf[9 * NQ3 + o];
+        V0 = ld_coef<GLOBAL_CF>(cf + 7 * NQ3 + o);
+        V1 = ld_coef<GLOBAL_CF>(cf + 8 * NQ3 + o);
+        V2 = ld_coef<GLOBAL_CF>(cf + 9 * NQ3 + o);
       }
 #pragma unroll
       for (int u = 0; u < VPT; ++u) {
@@ -624,7 +644,8 @@ __device__ __forceinline__ void tile_body_v(const Prm& p, const EOTables<T>& tb,
           a2v = fma(V2, uu, a2v);
         }
         if (CPLX) {
-          const T K0 = cf[10 * NQ3 + o], K1 = cf[11 * NQ3 + o], K2 = cf[12 * NQ3 + o];
+          const T K0 = ld_coef<GLOBAL_CF>(cf + 10 * NQ3 + o), K1 = ld_coef<GLOBAL_CF>(cf + 11 * NQ3 + o);
+          const T K2 = ld_coef<GLOBAL_CF>(cf + 12 * NQ3 + o);
           kk[u] = fma(K0, gx[u], fma(K1, gy[u], K2 * gz));
         }
         w0[u] = a0v;
@@ -910,6 +931,57 @@ __global__ void __launch_bounds__(NT) fe_local_staged_kernel(const __grid_consta
   }
 }
 
+// Lean cell-major variant: the same walk over a cell's column tiles with ONE
+// staging buffer, refilled with the next tile's rows of X (cp.async) as soon
+// as phase (1) has consumed it, and the cell's coefficients read from global
+// memory through the read-only L1 path instead of being staged.  That halves
+// the shared memory of the staged variant (96 KB at p = 8, VT = 8, FP32), so
+// MINB CTAs share an SM and there are about twice the warps to hide the
+// latency of the sweeps' shared-memory round trips.
+template <typename T, int NP, int NQ, int VT, bool CPLX>
+struct LeanShape {
+  using S = CellShape<T, NP, NQ, VT, CPLX>;
+  static constexpr size_t xs_elems = (size_t)S::NP3 * VT;
+  static constexpr size_t bytes = (size_t)(3 * S::BUF + xs_elems) * sizeof(T) + (size_t)S::NP3 * sizeof(int);
+  static_assert((3 * S::BUF * sizeof(T)) % 16 == 0 && (xs_elems * sizeof(T)) % 16 == 0,
+                "the staging buffer must start on a 16-byte boundary");
+  static constexpr bool fits = bytes <= 227 * 1024;
+};
+
+template <typename T, int NP, int NQ, int VT, bool CPLX, int NT, int VPT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) fe_local_lean_kernel(const __grid_constant__ LocalParams<T, T> p) {
+  using S = CellShape<T, NP, NQ, VT, CPLX>;
+  using LS = LeanShape<T, NP, NQ, VT, CPLX>;
+  constexpr int BUF = S::BUF, NQ3 = S::NQ3, NP3 = S::NP3;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* A = reinterpret_cast<T*>(smem_raw);
+  T* B = A + BUF;
+  T* C = B + BUF;
+  T* XS = C + BUF;
+  int* sd = reinterpret_cast<int*>(XS + LS::xs_elems);
+  const int ntiles = (p.ncols + VT - 1) / VT;
+  const bool vec_ok = (VT * sizeof(T)) % 16 == 0 && ((uintptr_t)p.X % 16) == 0 && ((p.ld * sizeof(T)) % 16) == 0;
+  for (int ci = blockIdx.x; ci < p.n_cells; ci += gridDim.x) {
+    const int e = p.cells[ci];
+    __syncthreads();   // the previous cell's readers are done with sd and XS
+    for (int i = threadIdx.x; i < NP3; i += NT) sd[i] = p.cell_dofs[(int64_t)e * NP3 + i];
+    __syncthreads();
+    stage_rows<T, NP3, VT, NT>(p.X, p.ld, p.ncols, sd, 0, XS, vec_ok);
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
+    const T* cfg = p.coef + (int64_t)e * p.ncoef * NQ3;
+    for (int t = 0; t < ntiles; ++t) {
+      auto refill = [&]() {
+        if (t + 1 < ntiles) stage_rows<T, NP3, VT, NT>(p.X, p.ld, p.ncols, sd, (t + 1) * VT, XS, vec_ok);
+      };
+      tile_body_v<T, NP, NQ, VT, VPT, CPLX, NT, LocalParams<T, T>, true>(p, p.tab, e, t * VT, A, B, C, cfg, sd, XS,
+                                                                          refill);
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+      __syncthreads();
+    }
+  }
+}
+
 // Tile configurations the launcher may pick from (chosen per context by
 // fe_ks_tune; index 0 is the default): columns per tile VT and block size NT.
 template <int NQ>
@@ -999,6 +1071,49 @@ cudaError_t launch_staged_cfg(const Ctx& c, const LocalParams<T, TS>& prm, cudaS
   }
 }
 
+template <typename T, typename TS, int NP, int NQ, int VT, int NT, int VPT, int MINB>
+cudaError_t launch_lean_cfg(const Ctx& c, const LocalParams<T, TS>& prm, cudaStream_t s) {
+  if constexpr (!std::is_same<T, TS>::value) {
+    return cudaErrorInvalidConfiguration;   // the reduction scatter needs T == storage type
+  } else {
+    if (prm.n_cells == 0) return cudaSuccess;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device);
+    static bool attr_done[2][64] = {};
+    const int dev = c.device & 63;
+    if (c.cplx) {
+      using LS = LeanShape<T, NP, NQ, VT, true>;
+      if constexpr (!LS::fits) {
+        return cudaErrorInvalidConfiguration;
+      } else {
+        auto k = fe_local_lean_kernel<T, NP, NQ, VT, true, NT, VPT, MINB>;
+        if (!attr_done[1][dev]) {
+          cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LS::bytes);
+          if (err != cudaSuccess) return err;
+          attr_done[1][dev] = true;
+        }
+        const int gx = prm.n_cells < MINB * (sms > 0 ? sms : 152) * 8 ? prm.n_cells : MINB * (sms > 0 ? sms : 152) * 8;
+        k<<<gx, NT, LS::bytes, s>>>(prm);
+      }
+    } else {
+      using LS = LeanShape<T, NP, NQ, VT, false>;
+      if constexpr (!LS::fits) {
+        return cudaErrorInvalidConfiguration;
+      } else {
+        auto k = fe_local_lean_kernel<T, NP, NQ, VT, false, NT, VPT, MINB>;
+        if (!attr_done[0][dev]) {
+          cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LS::bytes);
+          if (err != cudaSuccess) return err;
+          attr_done[0][dev] = true;
+        }
+        const int gx = prm.n_cells < MINB * (sms > 0 ? sms : 152) * 8 ? prm.n_cells : MINB * (sms > 0 ? sms : 152) * 8;
+        k<<<gx, NT, LS::bytes, s>>>(prm);
+      }
+    }
+    return cudaGetLastError();
+  }
+}
+
 template <typename T, typename TS>
 __host__ __forceinline__ int cfg_for(const Ctx& c) {
   if (std::is_same<T, double>::value) return c.cfg64;
@@ -1017,6 +1132,9 @@ cudaError_t launch_local_deg(const Ctx& c, const LocalParams<T, TS>& prm, cudaSt
     case 4: return launch_staged_cfg<T, TS, NP, NQ, V1, cfg_nt(V1, NQ)>(c, prm, s);
     case 5: return launch_staged_cfg<T, TS, NP, NQ, V1, cfg_nt(V1 / 2, NQ), 2>(c, prm, s);
     case 6: return launch_staged_cfg<T, TS, NP, NQ, V1, cfg_nt(V1 / 4, NQ), 4>(c, prm, s);
+    case 7: return launch_lean_cfg<T, TS, NP, NQ, V1, cfg_nt(V1 / 2, NQ), 2, 2>(c, prm, s);
+    case 8: return launch_lean_cfg<T, TS, NP, NQ, V1, cfg_nt(V1 / 4, NQ), 4, 2>(c, prm, s);
+    case 9: return launch_lean_cfg<T, TS, NP, NQ, V0, cfg_nt(V0 / 2, NQ), 2, 3>(c, prm, s);
     default: return launch_local_cfg<T, TS, NP, NQ, V0, cfg_nt(V0, NQ)>(c, prm, s);
   }
 }

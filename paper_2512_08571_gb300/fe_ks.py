@@ -199,7 +199,7 @@ def fe_ks_nonlocal_apply_static(X, Y, n_v, is_complex, degree, n_dofs, cell_dofs
                                             stream))
 
 
-N_CONFIGS = 7
+N_CONFIGS = 10
 
 
 def fe_ks_tune(ctx, X, Y, n_v, precision, reps=3):

@@ -78,8 +78,8 @@ def parse():
     ap.add_argument("--no-nq2", action="store_true", help="skip the n_q = n_p + 2 workload")
     ap.add_argument("--no-cell-matrix", action="store_true", help="skip the cell-matrix baseline")
     ap.add_argument("--no-all-electron", action="store_true", help="skip the all-electron-like workload")
-    ap.add_argument("--precision", choices=["both", "f64", "f32", "f64e", "bf16", "f16"], default="both",
-                    help="f32 / f64e / bf16 / f16 alone time only that application (for profiling)")
+    ap.add_argument("--precision", choices=["both", "f64", "f32", "f64e", "bf16", "f16", "bf16x2"], default="both",
+                    help="f32 / f64e / bf16 / f16 / bf16x2 alone time only that application (for profiling)")
     ap.add_argument("--config", type=int, default=None,
                     help="force this tile configuration instead of tuning (for profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle sample")
@@ -274,7 +274,8 @@ def run_native(args, wl, rank, world):
               fk.FE_KS_F64E: torch.complex128 if cplx else torch.float64,
               fk.FE_KS_F32: torch.complex64 if cplx else torch.float32,
               fk.FE_KS_BF16: torch.complex64 if cplx else torch.float32,
-              fk.FE_KS_F16: torch.complex64 if cplx else torch.float32}[precision]
+              fk.FE_KS_F16: torch.complex64 if cplx else torch.float32,
+              fk.FE_KS_BF16X2: torch.complex64 if cplx else torch.float32}[precision]
         X = X64 if dt == X64.dtype else X64.to(dt)
         Y = torch.empty_like(X)
         if args.config is None:
@@ -323,17 +324,20 @@ def run_native(args, wl, rank, world):
         mixed = measure(fk.FE_KS_F32, args.steps, args.warmup)
     elif not args.no_mixed and args.precision == "both":
         mixed = measure(fk.FE_KS_F32, max(args.steps, 20), max(args.warmup, 3))
-    bf16 = f16 = None
+    bf16 = f16 = bf16x2 = None
     if args.precision == "bf16":
         bf16 = measure(fk.FE_KS_BF16, args.steps, args.warmup)
     elif args.precision == "f16":
         f16 = measure(fk.FE_KS_F16, args.steps, args.warmup)
+    elif args.precision == "bf16x2":
+        bf16x2 = measure(fk.FE_KS_BF16X2, args.steps, args.warmup)
     elif not args.no_mixed and args.precision == "both":
         bf16 = measure(fk.FE_KS_BF16, max(args.steps, 20), max(args.warmup, 3))
         f16 = measure(fk.FE_KS_F16, max(args.steps, 20), max(args.warmup, 3))
+        bf16x2 = measure(fk.FE_KS_BF16X2, max(args.steps, 10), max(args.warmup, 3))
     ref.clear()
     torch.cuda.empty_cache()
-    peak_mma_live = fk.fe_ks_measure_fma_peak(fk.FE_KS_BF16) * 1e12 if (bf16 or f16) else None
+    peak_mma_live = fk.fe_ks_measure_fma_peak(fk.FE_KS_BF16) * 1e12 if (bf16 or f16 or bf16x2) else None
 
     peak64_live = fk.fe_ks_measure_fma_peak(fk.FE_KS_F64) * 1e12
     peak32_live = fk.fe_ks_measure_fma_peak(fk.FE_KS_F32) * 1e12
@@ -392,7 +396,8 @@ def run_native(args, wl, rank, world):
     del X64
     torch.cuda.empty_cache()
     fk.fe_ks_destroy(ctx)
-    return dict(filter=filt, cell_matrix=cmb, f64e=f64e, f64=f64, mixed=mixed, bf16=bf16, f16=f16, peak_mma_live=peak_mma_live,
+    return dict(filter=filt, cell_matrix=cmb, f64e=f64e, f64=f64, mixed=mixed, bf16=bf16, f16=f16, bf16x2=bf16x2,
+                peak_mma_live=peak_mma_live,
                 mma_flops_per_apply=mma_flops, bytes32=bytes32, e2e=e2e, setup_s=setup_s, info=info, local_flops=local_flops,
                 peak64_live=peak64_live, peak32_live=peak32_live)
 
@@ -489,7 +494,8 @@ def run_filter(args, wl, ctx, hp, X64):
              "f64_pairs": (fk.FE_KS_F64E, fk.FE_KS_F64E, True),
              "mixed": (fk.FE_KS_F32, fk.FE_KS_F64E, True),
              "mixed_bf16": (fk.FE_KS_BF16, fk.FE_KS_F64E, True),
-             "mixed_f16": (fk.FE_KS_F16, fk.FE_KS_F64E, True)}
+             "mixed_f16": (fk.FE_KS_F16, fk.FE_KS_F64E, True),
+             "mixed_bf16x2": (fk.FE_KS_BF16X2, fk.FE_KS_F64E, True)}
     lam = X = lmax = None
     for name, (prec, exact, pair_gemm) in plans.items():
         sol = RChFSI(ctx, m, n_v, False, degree=20, precision=prec, exact=exact, gemm_pairs=pair_gemm)
@@ -863,7 +869,7 @@ def main():
         return
     f64 = res["f64"]
     if f64 is None:
-        pr = res["mixed"] or res["f64e"] or res["bf16"] or res["f16"]
+        pr = res["mixed"] or res["f64e"] or res["bf16"] or res["f16"] or res["bf16x2"]
         print(json.dumps({"metric": METRIC, "profiling_only": True, "precision": args.precision, "ms": pr["ms"],
                           "value": pr["value"], "local_launch_ms": pr["local_launch_ms"],
                           "profile_ms_per_step": {k: v[0] / max(1, args.steps) for k, v in pr["prof"].items()}}))
@@ -949,7 +955,9 @@ def detail_sections(args, wl, res, world):
                          "tune_ms_per_config": mixed["tune_ms"]},
             "clocks": mixed["clocks"], "gpu_launches": mixed["launches"]}
     for key, name, dts in (("bf16", "bf16_tensor_core", "bf16 x bf16 -> f32 (FP32 storage)"),
-                           ("f16", "f16_tensor_core", "f16 x f16 -> f32 (FP32 storage, power-of-two column scaling)")):
+                           ("f16", "f16_tensor_core", "f16 x f16 -> f32 (FP32 storage, power-of-two column scaling)"),
+                           ("bf16x2", "bf16x2_tensor_core",
+                            "split bf16 hi + lo, three products -> f32 (FP32 storage)")):
         bf = res[key]
         if not bf:
             continue
@@ -965,7 +973,8 @@ def detail_sections(args, wl, res, world):
                          "peak": PEAK_HBM_GBS, "unit": "GB/s", "frac": t_roof / (bf["ms"] * 1e-3),
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
                          "alg_bytes_per_apply": alg_bytes, "avg_launch_ms": bf["local_launch_ms"],
-                         "mma_tflops_executed": res["mma_flops_per_apply"] * 1e-12 / (bf["ms"] * 1e-3),
+                         "mma_tflops_executed": res["mma_flops_per_apply"] * (3 if key == "bf16x2" else 1) * 1e-12
+                                                / (bf["ms"] * 1e-3),
                          "mma_sync_live_probe_tflops": (res["peak_mma_live"] or 0) / 1e12},
             "clocks": bf["clocks"], "gpu_launches": bf["launches"]}
     if res["e2e"]:

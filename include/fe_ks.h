@@ -66,10 +66,18 @@ typedef enum {
                                   operands and FP32 accumulation, the quadrature-point terms,
                                   projections and scatter in FP32, the nonlocal expansion
                                   as BF16 MMAs (apply / apply_scaled / tune / filter) */
-  FE_KS_F16 = 4                /* as FE_KS_BF16 with FP16 operands (8x the precision): each
+  FE_KS_F16 = 4,               /* as FE_KS_BF16 with FP16 operands (8x the precision): each
                                   column of a gathered cell tile is scaled by a power of two
                                   so that its largest entry is below 1/16, and unscaled at
                                   the scatter */
+  FE_KS_BF16X2 = 5             /* as FE_KS_BF16 with split products: every 16-bit operand
+                                  (the gathered and intermediate cell data, the 1D matrices,
+                                  the projector blocks and projections of the expansion) is
+                                  held as hi = bf16(x) plus lo = bf16(x - hi), about 16
+                                  significant bits, and every product is hi*hi + hi*lo +
+                                  lo*hi on the tensor cores with FP32 accumulation (the
+                                  lo*lo term is dropped); error about 2^-16 per stage,
+                                  i.e. near FP32 (apply / apply_scaled / tune / filter) */
 } fe_ks_precision;
 
 /* Terms of H that an application includes (terms_mask of fe_ks_setup). */

@@ -516,11 +516,13 @@ fe_ks_status fe_ks_setup(const fe_ks_problem* prob, int terms_mask, int64_t n_v_
             chk(upload(c, reinterpret_cast<ff2**>(&c->emu.coef), toff(coef), coef.size())) &&
             chk(upload(c, reinterpret_cast<ff2**>(&c->emu.dscale), toff(ds), ds.size()));
   if (ok) {
-    std::vector<uint32_t> frag(kTcFragWords), frag16(kTcFragWords);
-    build_tc_frags(c->p, frag.data(), false);
-    build_tc_frags(c->p, frag16.data(), true);
+    std::vector<uint32_t> frag(kTcFragWords), frag16(kTcFragWords), fraglo(kTcFragWords);
+    build_tc_frags(c->p, frag.data(), 0);
+    build_tc_frags(c->p, frag16.data(), 1);
+    build_tc_frags(c->p, fraglo.data(), 2);
     ok = chk(upload(c, &c->tc_frag, frag.data(), frag.size())) &&
-         chk(upload(c, &c->tc_frag16, frag16.data(), frag16.size()));
+         chk(upload(c, &c->tc_frag16, frag16.data(), frag16.size())) &&
+         chk(upload(c, &c->tc_frag_lo, fraglo.data(), fraglo.size()));
   }
   if (ok && want_nl) {
     std::vector<double> hh(prob->h_coef, prob->h_coef + (size_t)prob->n_atoms * prob->n_proj);
@@ -538,11 +540,15 @@ fe_ks_status fe_ks_setup(const fe_ks_problem* prob, int terms_mask, int64_t n_v_
          chk(upload<double>(c, &c->f64.part, nullptr, pn)) && chk(upload<float>(c, &c->f32.part, nullptr, pn));
     if (ok) {
       std::vector<uint2> fpack;
-      build_tc_fpack(c->np, c->cplx != 0, prob->n_proj, c->n_pairs, F.data(), false, fpack);
+      build_tc_fpack(c->np, c->cplx != 0, prob->n_proj, c->n_pairs, F.data(), 0, fpack);
       ok = chk(upload(c, &c->tc_fpack, fpack.data(), fpack.size()));
       if (ok) {
-        build_tc_fpack(c->np, c->cplx != 0, prob->n_proj, c->n_pairs, F.data(), true, fpack);
+        build_tc_fpack(c->np, c->cplx != 0, prob->n_proj, c->n_pairs, F.data(), 1, fpack);
         ok = chk(upload(c, &c->tc_fpack16, fpack.data(), fpack.size()));
+      }
+      if (ok) {
+        build_tc_fpack(c->np, c->cplx != 0, prob->n_proj, c->n_pairs, F.data(), 2, fpack);
+        ok = chk(upload(c, &c->tc_fpack_lo, fpack.data(), fpack.size()));
       }
     }
   }
@@ -633,7 +639,11 @@ namespace feks {
 
 template <typename T>
 fe_ks_status apply_core(Ctx& c, const T* X, T* Y, int64_t ncols, bool scaled, T alpha, bool zero_fill, int tc) {
-  NvtxRange range(tc == 2 ? "fe_ks_apply f16" : tc == 1 ? "fe_ks_apply bf16" : sizeof(T) == 8 ? "fe_ks_apply f64" : "fe_ks_apply f32");
+  NvtxRange range(tc == 3   ? "fe_ks_apply bf16x2"
+                  : tc == 2 ? "fe_ks_apply f16"
+                  : tc == 1 ? "fe_ks_apply bf16"
+                  : sizeof(T) == 8 ? "fe_ks_apply f64"
+                                   : "fe_ks_apply f32");
   OpData<T>& od = *reinterpret_cast<OpData<T>*>(sizeof(T) == 8 ? (void*)&c.f64 : (void*)&c.f32);
   const T* hcoef = reinterpret_cast<const T*>(sizeof(T) == 8 ? (const void*)c.h64 : (const void*)c.h32);
   cudaStream_t s = c.stream;
@@ -702,7 +712,7 @@ fe_ks_status apply_core(Ctx& c, const T* X, T* Y, int64_t ncols, bool scaled, T 
     lp.n_cells = c.colour_ptr[col + 1] - c.colour_ptr[col];
     cudaError_t err;
     if constexpr (std::is_same<T, float>::value)
-      err = tc ? launch_tc(c, lp, s, tc == 2) : launch_local<T, T>(c, lp, s);   // tc: n_q = n_p, checked above
+      err = tc ? launch_tc(c, lp, s, tc) : launch_local<T, T>(c, lp, s);   // tc: n_q = n_p, checked above
     else
       err = launch_local<T, T>(c, lp, s);
     if (err != cudaSuccess) return fail(FE_KS_ERR_CUDA, std::string("local kernel: ") + cudaGetErrorString(err));
@@ -830,6 +840,7 @@ fe_ks_status fe_ks_apply(fe_ks_ctx* ctx, const void* X, void* Y, int64_t n_v, in
   if (precision == FE_KS_F32) return apply_impl<float>(ctx, X, Y, n_v, false);
   if (precision == FE_KS_BF16) return apply_impl<float>(ctx, X, Y, n_v, false, 1);
   if (precision == FE_KS_F16) return apply_impl<float>(ctx, X, Y, n_v, false, 2);
+  if (precision == FE_KS_BF16X2) return apply_impl<float>(ctx, X, Y, n_v, false, 3);
   return fail(FE_KS_ERR_UNSUPPORTED, "unknown precision");
 }
 
@@ -870,7 +881,7 @@ fe_ks_status fe_ks_tune(fe_ks_ctx* ctx, const void* X, void* Y, int64_t n_v, int
   g_last_error.clear();
   if (!ctx || !X || !Y) return fail(FE_KS_ERR_ARG, "NULL argument");
   if (precision != FE_KS_F64 && precision != FE_KS_F32 && precision != FE_KS_F64E && precision != FE_KS_BF16 &&
-      precision != FE_KS_F16)
+      precision != FE_KS_F16 && precision != FE_KS_BF16X2)
     return fail(FE_KS_ERR_UNSUPPORTED, "unknown precision");
   if (reps < 1) reps = 1;
   Ctx& c = ctx->c;
@@ -879,7 +890,8 @@ fe_ks_status fe_ks_tune(fe_ks_ctx* ctx, const void* X, void* Y, int64_t n_v, int
              : precision == FE_KS_F32 ? c.cfg32
              : precision == FE_KS_F64E ? c.cfgE
                                        : single;
-  const int n_conf = (precision == FE_KS_BF16 || precision == FE_KS_F16) ? 1 : kLocalConfigs;
+  const bool tcp = precision == FE_KS_BF16 || precision == FE_KS_F16 || precision == FE_KS_BF16X2;
+  const int n_conf = tcp ? 1 : kLocalConfigs;
   const int keep = cfg;
   bool* expl = (precision <= FE_KS_F64E) ? &c.cfg_explicit[precision] : nullptr;
   const bool keep_expl = expl ? *expl : false;
@@ -920,7 +932,7 @@ fe_ks_status fe_ks_tune(fe_ks_ctx* ctx, const void* X, void* Y, int64_t n_v, int
   cfg = best_cfg;
   if (best) *best = best_cfg;
   if (best_ms == 1e300) return fail(FE_KS_ERR_CUDA, "no tile configuration could be launched");
-  if (precision != FE_KS_BF16 && precision != FE_KS_F16) {
+  if (!tcp) {
     c.cfg_explicit[precision] = true;
     tune_cache_store(c, precision, n_v * (c.cplx ? 2 : 1), best_cfg);
   }
@@ -933,6 +945,7 @@ fe_ks_status fe_ks_apply_scaled(fe_ks_ctx* ctx, const void* X, void* Y, int64_t 
   if (precision == FE_KS_F32) return apply_impl<float>(ctx, X, Y, n_v, true);
   if (precision == FE_KS_BF16) return apply_impl<float>(ctx, X, Y, n_v, true, 1);
   if (precision == FE_KS_F16) return apply_impl<float>(ctx, X, Y, n_v, true, 2);
+  if (precision == FE_KS_BF16X2) return apply_impl<float>(ctx, X, Y, n_v, true, 3);
   return fail(FE_KS_ERR_UNSUPPORTED, "unknown precision");
 }
 
@@ -940,7 +953,9 @@ fe_ks_status fe_ks_apply_scaled(fe_ks_ctx* ctx, const void* X, void* Y, int64_t 
 // Storage bytes of one [m][n_v] block in the given precision (0: unknown precision).
 static size_t host_block_bytes(const Ctx& c, int64_t n_v, int precision) {
   const size_t esz = (precision == FE_KS_F64 || precision == FE_KS_F64E) ? 8
-                     : (precision == FE_KS_F32 || precision == FE_KS_BF16 || precision == FE_KS_F16) ? 4
+                     : (precision == FE_KS_F32 || precision == FE_KS_BF16 || precision == FE_KS_F16 ||
+                        precision == FE_KS_BF16X2)
+                         ? 4
                                                                                                        : 0;
   return ((size_t)c.m * n_v * (c.cplx ? 2 : 1) * esz + 255) & ~(size_t)255;
 }

@@ -202,9 +202,9 @@ extern "C" {
 fe_ks_status fe_ks_cheb_filter_workspace(const fe_ks_ctx* ctx, int64_t n_v, int precision, size_t* bytes) {
   if (!ctx || !bytes) return fail(FE_KS_ERR_ARG, "NULL argument");
   if (precision != FE_KS_F64 && precision != FE_KS_F32 && precision != FE_KS_F64E && precision != FE_KS_BF16 &&
-      precision != FE_KS_F16)
+      precision != FE_KS_F16 && precision != FE_KS_BF16X2)
     return fail(FE_KS_ERR_UNSUPPORTED, "unknown precision");
-  *bytes = filter_bytes(ctx->c, n_v, (precision == FE_KS_BF16 || precision == FE_KS_F16) ? FE_KS_F32 : precision);
+  *bytes = filter_bytes(ctx->c, n_v, (precision == FE_KS_BF16 || precision == FE_KS_F16 || precision == FE_KS_BF16X2) ? FE_KS_F32 : precision);
   return FE_KS_OK;
 }
 
@@ -220,19 +220,23 @@ static fe_ks_status filter_entry(fe_ks_ctx* ctx, fe_ks_ctx* mass, double* X, con
   if (degree < 1) return fail(FE_KS_ERR_ARG, "degree must be >= 1");
   if (!(lam_min < lam_T && lam_T < lam_max)) return fail(FE_KS_ERR_ARG, "need lam_min < lam_T < lam_max");
   if (precision != FE_KS_F64 && precision != FE_KS_F32 && precision != FE_KS_F64E && precision != FE_KS_BF16 &&
-      precision != FE_KS_F16)
+      precision != FE_KS_F16 && precision != FE_KS_BF16X2)
     return fail(FE_KS_ERR_UNSUPPORTED, "unknown precision");
   if (residual_precision != FE_KS_F64 && residual_precision != FE_KS_F64E)
     return fail(FE_KS_ERR_ARG, "residual_precision must be FE_KS_F64 or FE_KS_F64E");
-  if (work_bytes < filter_bytes(c, n_v, (precision == FE_KS_BF16 || precision == FE_KS_F16) ? FE_KS_F32 : precision))
+  if (work_bytes < filter_bytes(c, n_v, (precision == FE_KS_BF16 || precision == FE_KS_F16 || precision == FE_KS_BF16X2) ? FE_KS_F32 : precision))
     return fail(FE_KS_ERR_ARG, "workspace too small");
   if (((uintptr_t)work & 255) || ((uintptr_t)X & 7)) return fail(FE_KS_ERR_ARG, "misaligned X or workspace");
   char* w = static_cast<char*>(work);
   const bool res_emu = residual_precision == FE_KS_F64E;
   Ctx* mc = mass ? &mass->c : nullptr;
-  if (precision == FE_KS_F32 || precision == FE_KS_BF16 || precision == FE_KS_F16)
+  if (precision == FE_KS_F32 || precision == FE_KS_BF16 || precision == FE_KS_F16 || precision == FE_KS_BF16X2)
     return cheb_impl<float>(c, X, ritz, n_v, degree, lam_min, lam_T, lam_max, w, false, res_emu,
-                            precision == FE_KS_BF16 ? 1 : precision == FE_KS_F16 ? 2 : 0, mc);
+                            precision == FE_KS_BF16    ? 1
+                            : precision == FE_KS_F16   ? 2
+                            : precision == FE_KS_BF16X2 ? 3
+                                                        : 0,
+                            mc);
   return cheb_impl<double>(c, X, ritz, n_v, degree, lam_min, lam_T, lam_max, w, precision == FE_KS_F64E, res_emu, 0,
                            mc);
 }

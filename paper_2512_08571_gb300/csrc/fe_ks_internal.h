@@ -136,6 +136,8 @@ struct Ctx {
   uint32_t* tc_frag16 = nullptr;   // FP16
   uint2* tc_fpack = nullptr;       // F as expansion B fragments, BF16 (when the nonlocal term is present)
   uint2* tc_fpack16 = nullptr;     // the same in FP16
+  uint32_t* tc_frag_lo = nullptr;  // BF16 remainders of the 1D operators (split precision FE_KS_BF16X2)
+  uint2* tc_fpack_lo = nullptr;    // BF16 remainders of F (split precision)
   std::vector<void*> allocations;
   // host-buffer pipeline (fe_ks_apply_host): copy-in and copy-out streams and,
   // per workspace slot, events for "X copied in", "applied", "Y copied out"
@@ -174,17 +176,19 @@ void build_eo_tables<ff2>(int p, int nq, EOTables<ff2>* out);
 // out[((op * 2 + tile) * 32 + lane) * 2 + reg], op 0 = N (nodes -> Gauss
 // points), 1 = D (Gauss-point derivative of the nodal basis), 2 = N^T, 3 = D^T.
 constexpr int kTcFragWords = 4 * 2 * 32 * 2;
-void build_tc_frags(int p, uint32_t* out, bool f16);
+// kind: 0 = BF16, 1 = FP16, 2 = the BF16 remainder x - bf16(x) (low part of the split)
+void build_tc_frags(int p, uint32_t* out, int kind);
 uint16_t bf16_bits(double x);   // nearest BF16 (ties to even), as its bit pattern
+uint16_t bf16_lo_bits(double x);   // nearest BF16 of x - bf16(x)
 uint16_t f16_bits(double x);    // nearest FP16 (ties to even), as its bit pattern
 // The projector matrices F [pair][n_proj][n^3] (complex: x2 interleaved) as BF16
 // B fragments of the tensor-core kernel's expansion MMAs:
 // out[pair][row tile][half][8-column tile][K step][lane] (uint2 per lane).
-void build_tc_fpack(int n, bool cplx, int n_proj, int64_t n_pairs, const double* F, bool f16, std::vector<uint2>& out);
+void build_tc_fpack(int n, bool cplx, int n_proj, int64_t n_pairs, const double* F, int kind, std::vector<uint2>& out);
 
 // Y (+)= alpha H X or alpha Hs X on the context's stream; zero_fill clears Y first.
 // tc: FP32 storage with the tensor-core cell kernel (T = float only): 0 = off,
-// 1 = BF16, 2 = FP16.
+// 1 = BF16, 2 = FP16, 3 = BF16 hi + lo split (FE_KS_BF16X2).
 template <typename T>
 fe_ks_status apply_core(Ctx& c, const T* X, T* Y, int64_t ncols, bool scaled, T alpha, bool zero_fill,
                         int tc = 0);
@@ -205,7 +209,7 @@ cudaError_t launch_proj_pairs(const Ctx& c, const ProjParams<T>& prm, int n_atom
 cudaError_t launch_proj_pairs_emu(const Ctx& c, const ProjParams<double>& prm, const ff2* F, int n_atoms,
                                   cudaStream_t s);
 // BF16 tensor-core cell kernel (fe_ks_tc.cu) for one colour of cells
-cudaError_t launch_tc(const Ctx& c, const LocalParams<float>& lp, cudaStream_t s, bool f16);
+cudaError_t launch_tc(const Ctx& c, const LocalParams<float>& lp, cudaStream_t s, int tc);
 size_t tc_smem_bytes(int n, bool cplx);
 
 }  // namespace feks

@@ -173,7 +173,16 @@ uint16_t f16_bits(double x) {
   return (uint16_t)(sign | h);
 }
 
-void build_tc_frags(int p, uint32_t* out, bool f16) {
+// Remainder of the BF16 split: the nearest BF16 of x - (nearest BF16 of x), as
+// its bit pattern (hi + lo then carries about 16 significant bits of x).
+uint16_t bf16_lo_bits(double x) {
+  const uint32_t h = (uint32_t)bf16_bits(x) << 16;
+  float hv;
+  std::memcpy(&hv, &h, 4);
+  return bf16_bits(x - (double)hv);
+}
+
+void build_tc_frags(int p, uint32_t* out, int kind) {
   const int n = p + 1;
   double xg[kMaxN], wg[kMaxN], xq[kMaxN], wq[kMaxN], val[kMaxN], der[kMaxN];
   gauss_lobatto(n, xg, wg);
@@ -202,7 +211,9 @@ void build_tc_frags(int p, uint32_t* out, bool f16) {
         const int g = lane / 4, t = lane % 4, col = 8 * tile + g;
         for (int r = 0; r < 2; ++r) {
           const int k = 2 * t + 8 * r;
-          auto h = [&](double x) -> uint32_t { return f16 ? f16_bits(x) : bf16_bits(x); };
+          auto h = [&](double x) -> uint32_t {
+            return kind == 1 ? f16_bits(x) : kind == 2 ? bf16_lo_bits(x) : bf16_bits(x);
+          };
           out[((op * 2 + tile) * 32 + lane) * 2 + r] = h(B(op, k, col)) | (h(B(op, k + 1, col)) << 16);
         }
       }

@@ -60,6 +60,8 @@ struct TcParams {
   float alpha;
   const uint32_t* frag;    // B fragments [4 ops][2 tiles][32 lanes][2]
   const uint2* fpack;      // F as BF16 / FP16 B fragments [pair][row tile][half][tile][K step][32 lanes]
+  const uint32_t* frag_lo; // split precision: BF16 remainders of frag
+  const uint2* fpack_lo;   // split precision: BF16 remainders of fpack
 };
 
 namespace tc {
@@ -68,7 +70,7 @@ namespace tc {
 // (a, b, c) of any stage sits at a + SY b + SZ c with odd SY and SZ, so that
 // the 8 rows (16 bytes each) of every ldmatrix / stmatrix phase fall in 8
 // different 16-byte bank groups for all three sweep directions.
-template <int N, bool CPLX>
+template <int N, bool CPLX, bool SPLIT = false>
 struct Geom {
   static constexpr int SY = (N & 1) ? N : N + 1;
   static constexpr int SZ = (N & 1) ? N * N : N * (N + 1) + 1;
@@ -81,9 +83,12 @@ struct Geom {
   static constexpr int NW = N == 9 ? 7 : N == 8 ? 8 : N == 7 ? 7 : N == 6 ? 6 : N == 5 ? 7 : 4;
   static constexpr int NT = 32 * NW;
   static constexpr int NC = CPLX ? 14 : 12;       // coefficient floats per point (padded)
-  // byte offsets
+  // byte offsets: arrays 0-2 (BF16 / FP16 data), and for the split precision
+  // their low parts 3-5 (array k's twin at + LO)
   static constexpr int ARR = NPTS * 16;
-  static constexpr int OFF_ZERO = 3 * ARR;
+  static constexpr int NARR = SPLIT ? 6 : 3;
+  static constexpr int LO = 3 * ARR;
+  static constexpr int OFF_ZERO = NARR * ARR;
   static constexpr int OFF_TRASH = OFF_ZERO + 16;
   static constexpr int OFF_COEF = OFF_TRASH + 32 * 16;
   static constexpr int OFF_DOFS = OFF_COEF + NPTS * NC * 4;
@@ -98,9 +103,10 @@ struct Geom {
   // Two resident CTAs per SM.  (Three fit the shared memory at n = 9, but the
   // register cap that lets 21 warps share the SM's four 16K-register files
   // (80 per thread) made the kernel spill and measured no faster.)
-  static constexpr int MINB = 2;
+  // The split precision doubles the data arrays and the live fragments: one CTA.
+  static constexpr int MINB = SPLIT ? 1 : 2;
   static_assert(ARR % 16 == 0 && OFF_COEF % 16 == 0 && OFF_DOFS % 4 == 0 && OFF_STAGE % 16 == 0, "alignment");
-  static_assert(2 * (BYTES + 1024) <= 233472, "two CTAs per SM must fit");
+  static_assert(MINB * (BYTES + 1024) <= 233472, "MINB CTAs per SM must fit");
   static_assert((NC * 4) % 16 == 0 || (NC * 4) % 8 == 0, "coefficient loads need 8-byte point stride");
 
   // point index of line `grp` (the two untouched coordinates) at position k
@@ -227,6 +233,55 @@ __device__ __forceinline__ void zero(float (&d)[NTL][4]) {
   for (int j = 0; j < NTL; ++j) d[j][0] = d[j][1] = d[j][2] = d[j][3] = 0.f;
 }
 
+// Split precision (FE_KS_BF16X2): an operand x is held as hi = bf16(x) and
+// lo = bf16(x - hi); a product a b becomes a_hi b_hi + a_hi b_lo + a_lo b_hi on
+// the tensor cores (the a_lo b_lo term, about 2^-18 of the product, is
+// dropped), all into the same FP32 accumulator.  With SPLIT = false these
+// reduce to the single 16-bit product and the lo arguments are not read.
+template <bool K16, bool F16, bool SPLIT>
+__device__ __forceinline__ void mmaZ(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&al)[4],
+                                     const uint32_t (&b)[2], const uint32_t (&bl)[2]) {
+  mma0<K16, F16>(d, a, b);
+  if constexpr (SPLIT) {
+    mma<K16, F16>(d, a, bl);
+    mma<K16, F16>(d, al, b);
+  }
+}
+
+template <bool K16, bool F16, bool SPLIT>
+__device__ __forceinline__ void mmaA(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&al)[4],
+                                     const uint32_t (&b)[2], const uint32_t (&bl)[2]) {
+  mma<K16, F16>(d, a, b);
+  if constexpr (SPLIT) {
+    mma<K16, F16>(d, a, bl);
+    mma<K16, F16>(d, al, b);
+  }
+}
+
+// accumulator tiles -> hi fragment (and, split, the lo fragment of the remainders)
+template <int NTL, bool F16, bool SPLIT>
+__device__ __forceinline__ void to_frag2(const float (&d)[NTL][4], uint32_t (&a)[4], uint32_t (&al)[4]) {
+  to_frag<NTL, F16>(d, a);
+  if constexpr (SPLIT) {
+    float r[NTL][4];
+#pragma unroll
+    for (int j = 0; j < NTL; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) r[j][q] = d[j][q] - __bfloat162float(__float2bfloat16_rn(d[j][q]));
+    to_frag<NTL, false>(r, al);
+  }
+}
+
+// two values -> packed hi pair and (split) packed lo pair
+template <bool F16, bool SPLIT>
+__device__ __forceinline__ void pack2(float x, float y, uint32_t& h, uint32_t& l) {
+  h = pack16<F16>(x, y);
+  if constexpr (SPLIT)
+    l = pack_bf16(x - __bfloat162float(__float2bfloat16_rn(x)), y - __bfloat162float(__float2bfloat16_rn(y)));
+  else
+    l = 0u;
+}
+
 // Byte offset of this lane's row for ldmatrix / stmatrix on row tile
 // (g0, g0 + 1) along direction DIM, or -1 past the line's end: lane l serves
 // matrix l / 8 (bit 0: line g0 or g0 + 1; bit 1: k + 8) and row l % 8 of it.
@@ -241,6 +296,21 @@ __device__ __forceinline__ int row_off(int g0, int lane) {
 
 __device__ __forceinline__ uint32_t at(uint32_t arr, int off, uint32_t spare) {
   return off >= 0 ? arr + (uint32_t)off : spare;
+}
+
+// ldmatrix / stmatrix of a row tile of array `arr` and, split, of its low twin at arr + lo
+template <bool K16, bool SPLIT>
+__device__ __forceinline__ void ldsm2(uint32_t arr, uint32_t lo, int off, uint32_t zrow, uint32_t (&a)[4],
+                                      uint32_t (&al)[4]) {
+  ldsm<K16>(at(arr, off, zrow), a);
+  if constexpr (SPLIT) ldsm<K16>(at(arr + lo, off, zrow), al);
+}
+
+template <int NTL, bool SPLIT>
+__device__ __forceinline__ void stsm2(uint32_t arr, uint32_t lo, int off, uint32_t trash, const uint32_t (&o)[4],
+                                      const uint32_t (&ol)[4]) {
+  stsm<NTL>(at(arr, off, trash), o);
+  if constexpr (SPLIT) stsm<NTL>(at(arr + lo, off, trash), ol);
 }
 
 // Power of two s with s * mx < 1/16 (s = 1 for mx = 0), from the exponent bits
@@ -287,9 +357,10 @@ __device__ __forceinline__ void scatter_stage(const TcParams& p, const float* st
   }
 }
 
-template <int N, bool CPLX, bool F16>
-__global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_kernel(const __grid_constant__ TcParams p) {
-  using Gm = Geom<N, CPLX>;
+template <int N, bool CPLX, bool F16, bool SPLIT>
+__global__ void __launch_bounds__(Geom<N, CPLX, SPLIT>::NT, Geom<N, CPLX, SPLIT>::MINB)
+    fe_tc_kernel(const __grid_constant__ TcParams p) {
+  using Gm = Geom<N, CPLX, SPLIT>;
   constexpr bool K16 = Gm::K16;
   constexpr int NTL = Gm::NTL, NT = Gm::NT, NW = Gm::NW, N3 = Gm::N3, NC = Gm::NC, NMT = Gm::NMT;
   constexpr int SY = Gm::SY, SZ = Gm::SZ;
@@ -300,6 +371,7 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_
   float* stage = reinterpret_cast<float*>(smem + Gm::OFF_STAGE);
   const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(smem);
   const uint32_t A0 = s0, A1 = s0 + Gm::ARR, A2 = s0 + 2 * Gm::ARR;
+  constexpr uint32_t LO = Gm::LO;   // byte distance from an array to its low twin (split precision)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int gq = lane >> 2, tig = lane & 3;   // accumulator row (column v) and column-pair index
   const uint32_t zero_row = s0 + Gm::OFF_ZERO;
@@ -308,6 +380,7 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_
 
   // B fragments of N^T-as-B (forward N), D (forward), N and D (transposed sweeps)
   uint32_t bN[NTL][2], bD[NTL][2], bNt[NTL][2], bDt[NTL][2];
+  uint32_t bNl[NTL][2], bDl[NTL][2], bNtl[NTL][2], bDtl[NTL][2];   // split: their BF16 remainders
 #pragma unroll
   for (int j = 0; j < NTL; ++j)
 #pragma unroll
@@ -316,6 +389,14 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_
       bD[j][r] = p.frag[((1 * 2 + j) * 32 + lane) * 2 + r];
       bNt[j][r] = p.frag[((2 * 2 + j) * 32 + lane) * 2 + r];
       bDt[j][r] = p.frag[((3 * 2 + j) * 32 + lane) * 2 + r];
+      if constexpr (SPLIT) {
+        bNl[j][r] = p.frag_lo[((0 * 2 + j) * 32 + lane) * 2 + r];
+        bDl[j][r] = p.frag_lo[((1 * 2 + j) * 32 + lane) * 2 + r];
+        bNtl[j][r] = p.frag_lo[((2 * 2 + j) * 32 + lane) * 2 + r];
+        bDtl[j][r] = p.frag_lo[((3 * 2 + j) * 32 + lane) * 2 + r];
+      } else {
+        bNl[j][r] = bDl[j][r] = bNtl[j][r] = bDtl[j][r] = 0u;
+      }
     }
   const int ntiles = (p.ncols + 7) / 8;
   const bool vec = (p.ld % 4 == 0) && (((uintptr_t)p.X & 15) == 0);
@@ -429,12 +510,13 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_
           if (node < N3) {
             const int i = node % N, j = (node / N) % N, k = node / (N * N);
             const float s = sc[r];
-            uint4 u;
-            u.x = pack16<F16>(xa[r].x * s * cs[0], xa[r].y * s * cs[1]);
-            u.y = pack16<F16>(xa[r].z * s * cs[2], xa[r].w * s * cs[3]);
-            u.z = pack16<F16>(xb[r].x * s * cs[4], xb[r].y * s * cs[5]);
-            u.w = pack16<F16>(xb[r].z * s * cs[6], xb[r].w * s * cs[7]);
+            uint4 u, ul;
+            pack2<F16, SPLIT>(xa[r].x * s * cs[0], xa[r].y * s * cs[1], u.x, ul.x);
+            pack2<F16, SPLIT>(xa[r].z * s * cs[2], xa[r].w * s * cs[3], u.y, ul.y);
+            pack2<F16, SPLIT>(xb[r].x * s * cs[4], xb[r].y * s * cs[5], u.z, ul.z);
+            pack2<F16, SPLIT>(xb[r].z * s * cs[6], xb[r].w * s * cs[7], u.w, ul.w);
             *reinterpret_cast<uint4*>(smem + 2 * Gm::ARR + 16 * (i + SY * j + SZ * k)) = u;
+            if constexpr (SPLIT) *reinterpret_cast<uint4*>(smem + 2 * Gm::ARR + LO + 16 * (i + SY * j + SZ * k)) = ul;
           }
         }
       }
@@ -446,68 +528,68 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_
       //     tiles at a time so that 4 BX independent MMAs are in flight (the
       //     warp-level MMA has a latency of ~100 cycles on this part).
       {
-        constexpr int BX = 3;
+        constexpr int BX = SPLIT ? 2 : 3;
 #pragma unroll 1
         for (int mt0 = warp; mt0 < NMT; mt0 += NW * BX) {
           int off[BX];
-          uint32_t a[BX][4];
+          uint32_t a[BX][4], al[BX][4];
           float u[BX][NTL][4], ud[BX][NTL][4];
 #pragma unroll
           for (int b = 0; b < BX; ++b) {
             const int mt = mt0 + b * NW;
             off[b] = mt < NMT ? row_off<N, CPLX, 0>(2 * mt, lane) : -1;
-            ldsm<K16>(at(A2, off[b], zero_row), a[b]);
+            ldsm2<K16, SPLIT>(A2, LO, off[b], zero_row, a[b], al[b]);
           }
 #pragma unroll
           for (int b = 0; b < BX; ++b)
 #pragma unroll
             for (int j = 0; j < NTL; ++j) {
-              mma0<K16, F16>(u[b][j], a[b], bN[j]);
-              mma0<K16, F16>(ud[b][j], a[b], bD[j]);
+              mmaZ<K16, F16, SPLIT>(u[b][j], a[b], al[b], bN[j], bNl[j]);
+              mmaZ<K16, F16, SPLIT>(ud[b][j], a[b], al[b], bD[j], bDl[j]);
             }
 #pragma unroll
           for (int b = 0; b < BX; ++b) {
-            uint32_t o[4];
-            to_frag<NTL, F16>(u[b], o);
-            stsm<NTL>(at(A0, off[b], trash), o);
-            to_frag<NTL, F16>(ud[b], o);
-            stsm<NTL>(at(A1, off[b], trash), o);
+            uint32_t o[4], ol[4];
+            to_frag2<NTL, F16, SPLIT>(u[b], o, ol);
+            stsm2<NTL, SPLIT>(A0, LO, off[b], trash, o, ol);
+            to_frag2<NTL, F16, SPLIT>(ud[b], o, ol);
+            stsm2<NTL, SPLIT>(A1, LO, off[b], trash, o, ol);
           }
         }
       }
       __syncthreads();
       // (3) y sweep: N_y U -> 0, D_y U -> 1, N_y U' -> 2 (BY row tiles per warp at a time)
       {
-        constexpr int BY = 2;
+        constexpr int BY = SPLIT ? 1 : 2;
 #pragma unroll 1
         for (int mt0 = warp; mt0 < NMT; mt0 += NW * BY) {
           int off[BY];
-          uint32_t a[BY][4], b2[BY][4];
+          uint32_t a[BY][4], b2[BY][4], al[BY][4], b2l[BY][4];
           float t0[BY][NTL][4], t1[BY][NTL][4], t2[BY][NTL][4];
 #pragma unroll
           for (int b = 0; b < BY; ++b) {
             const int mt = mt0 + b * NW;
             off[b] = mt < NMT ? row_off<N, CPLX, 1>(2 * mt, lane) : -1;
-            ldsm<K16>(at(A0, off[b], zero_row), a[b]);
-            ldsm<K16>(at(A1, off[b], zero_row), b2[b]);
+            ldsm2<K16, SPLIT>(A0, LO, off[b], zero_row, a[b], al[b]);
+            ldsm2<K16, SPLIT>(A1, LO, off[b], zero_row, b2[b], b2l[b]);
           }
 #pragma unroll
           for (int b = 0; b < BY; ++b)
 #pragma unroll
             for (int j = 0; j < NTL; ++j) {
-              mma0<K16, F16>(t0[b][j], a[b], bN[j]);
-              mma0<K16, F16>(t1[b][j], a[b], bD[j]);
-              mma0<K16, F16>(t2[b][j], b2[b], bN[j]);
+              mmaZ<K16, F16, SPLIT>(t0[b][j], a[b], al[b], bN[j], bNl[j]);
+              mmaZ<K16, F16, SPLIT>(t1[b][j], a[b], al[b], bD[j], bDl[j]);
+              mmaZ<K16, F16, SPLIT>(t2[b][j], b2[b], b2l[b], bN[j], bNl[j]);
             }
 #pragma unroll
           for (int b = 0; b < BY; ++b) {
-            uint32_t o[4];
-            to_frag<NTL, F16>(t0[b], o);
-            stsm<NTL>(at(A0, off[b], trash), o);
-            to_frag<NTL, F16>(t1[b], o);
-            stsm<NTL>(at(A1, off[b], trash), o);
-            to_frag<NTL, F16>(t2[b], o);
-            stsm<NTL>(at(A2, off[b], trash), o);
+            uint32_t o[4], ol[4];
+            to_frag2<NTL, F16, SPLIT>(t0[b], o, ol);
+            stsm2<NTL, SPLIT>(A0, LO, off[b], trash, o, ol);
+            to_frag2<NTL, F16, SPLIT>(t1[b], o, ol);
+            stsm2<NTL, SPLIT>(A1, LO, off[b], trash, o, ol);
+            to_frag2<NTL, F16, SPLIT>(t2[b], o, ol);
+            stsm2<NTL, SPLIT>(A2, LO, off[b], trash, o, ol);
           }
         }
       }
@@ -519,17 +601,17 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_
       for (int mt = warp; mt < NMT; mt += NW) {
         const int g0 = 2 * mt;
         const int off = row_off<N, CPLX, 2>(g0, lane);
-        uint32_t a[4], b[4], c[4];
-        ldsm<K16>(at(A0, off, zero_row), a);
-        ldsm<K16>(at(A1, off, zero_row), b);
-        ldsm<K16>(at(A2, off, zero_row), c);
+        uint32_t a[4], b[4], c[4], al[4], bl[4], cl[4];
+        ldsm2<K16, SPLIT>(A0, LO, off, zero_row, a, al);
+        ldsm2<K16, SPLIT>(A1, LO, off, zero_row, b, bl);
+        ldsm2<K16, SPLIT>(A2, LO, off, zero_row, c, cl);
         float u[NTL][4], gx[NTL][4], gy[NTL][4], gz[NTL][4];
 #pragma unroll
         for (int j = 0; j < NTL; ++j) {
-          mma0<K16, F16>(u[j], a, bN[j]);
-          mma0<K16, F16>(gz[j], a, bD[j]);
-          mma0<K16, F16>(gy[j], b, bN[j]);
-          mma0<K16, F16>(gx[j], c, bN[j]);
+          mmaZ<K16, F16, SPLIT>(u[j], a, al, bN[j], bNl[j]);
+          mmaZ<K16, F16, SPLIT>(gz[j], a, al, bD[j], bDl[j]);
+          mmaZ<K16, F16, SPLIT>(gy[j], b, bl, bN[j], bNl[j]);
+          mmaZ<K16, F16, SPLIT>(gx[j], c, cl, bN[j], bNl[j]);
         }
         // element (j, r): line g0 + (r >> 1), column v = gq, qz = 8 j + 2 tig + (r & 1);
         // the coefficients of a line start at cbase[r >> 1], qz adds SZ NC per step
@@ -596,55 +678,55 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_
             gy[j][r] = w1;
             gz[j][r] = w2;
           }
-        uint32_t fz[4], fx[4], fy[4], fw[4], o[4];
-        to_frag<NTL, F16>(u, fz);
-        to_frag<NTL, F16>(gx, fx);
-        to_frag<NTL, F16>(gy, fy);
-        to_frag<NTL, F16>(gz, fw);
+        uint32_t fz[4], fx[4], fy[4], fw[4], o[4], fzl[4], fxl[4], fyl[4], fwl[4], ol[4];
+        to_frag2<NTL, F16, SPLIT>(u, fz, fzl);
+        to_frag2<NTL, F16, SPLIT>(gx, fx, fxl);
+        to_frag2<NTL, F16, SPLIT>(gy, fy, fyl);
+        to_frag2<NTL, F16, SPLIT>(gz, fw, fwl);
         float va[NTL][4], va2[NTL][4], vb[NTL][4], vc[NTL][4];
 #pragma unroll
         for (int j = 0; j < NTL; ++j) {   // four independent accumulators
-          mma0<K16, F16>(va[j], fz, bNt[j]);
-          mma0<K16, F16>(va2[j], fw, bDt[j]);
-          mma0<K16, F16>(vb[j], fy, bNt[j]);
-          mma0<K16, F16>(vc[j], fx, bNt[j]);
+          mmaZ<K16, F16, SPLIT>(va[j], fz, fzl, bNt[j], bNtl[j]);
+          mmaZ<K16, F16, SPLIT>(va2[j], fw, fwl, bDt[j], bDtl[j]);
+          mmaZ<K16, F16, SPLIT>(vb[j], fy, fyl, bNt[j], bNtl[j]);
+          mmaZ<K16, F16, SPLIT>(vc[j], fx, fxl, bNt[j], bNtl[j]);
         }
 #pragma unroll
         for (int j = 0; j < NTL; ++j)
 #pragma unroll
           for (int r = 0; r < 4; ++r) va[j][r] += va2[j][r];
-        to_frag<NTL, F16>(va, o);
-        stsm<NTL>(at(A0, off, trash), o);
-        to_frag<NTL, F16>(vb, o);
-        stsm<NTL>(at(A1, off, trash), o);
-        to_frag<NTL, F16>(vc, o);
-        stsm<NTL>(at(A2, off, trash), o);
+        to_frag2<NTL, F16, SPLIT>(va, o, ol);
+        stsm2<NTL, SPLIT>(A0, LO, off, trash, o, ol);
+        to_frag2<NTL, F16, SPLIT>(vb, o, ol);
+        stsm2<NTL, SPLIT>(A1, LO, off, trash, o, ol);
+        to_frag2<NTL, F16, SPLIT>(vc, o, ol);
+        stsm2<NTL, SPLIT>(A2, LO, off, trash, o, ol);
       }
       __syncthreads();
       // (5) transposed y sweep: N_y^T V_a + D_y^T V_b -> 0, N_y^T V_c -> 1
       //     (BR row tiles per warp at a time, independent accumulators)
       {
-        constexpr int BR = 2;
+        constexpr int BR = SPLIT ? 1 : 2;
 #pragma unroll 1
         for (int mt0 = warp; mt0 < NMT; mt0 += NW * BR) {
           int off[BR];
-          uint32_t a[BR][4], b2[BR][4], c2[BR][4];
+          uint32_t a[BR][4], b2[BR][4], c2[BR][4], al[BR][4], b2l[BR][4], c2l[BR][4];
           float sa[BR][NTL][4], sa2[BR][NTL][4], sb[BR][NTL][4];
 #pragma unroll
           for (int b = 0; b < BR; ++b) {
             const int mt = mt0 + b * NW;
             off[b] = mt < NMT ? row_off<N, CPLX, 1>(2 * mt, lane) : -1;
-            ldsm<K16>(at(A0, off[b], zero_row), a[b]);
-            ldsm<K16>(at(A1, off[b], zero_row), b2[b]);
-            ldsm<K16>(at(A2, off[b], zero_row), c2[b]);
+            ldsm2<K16, SPLIT>(A0, LO, off[b], zero_row, a[b], al[b]);
+            ldsm2<K16, SPLIT>(A1, LO, off[b], zero_row, b2[b], b2l[b]);
+            ldsm2<K16, SPLIT>(A2, LO, off[b], zero_row, c2[b], c2l[b]);
           }
 #pragma unroll
           for (int b = 0; b < BR; ++b)
 #pragma unroll
             for (int j = 0; j < NTL; ++j) {
-              mma0<K16, F16>(sa[b][j], a[b], bNt[j]);
-              mma0<K16, F16>(sa2[b][j], b2[b], bDt[j]);
-              mma0<K16, F16>(sb[b][j], c2[b], bNt[j]);
+              mmaZ<K16, F16, SPLIT>(sa[b][j], a[b], al[b], bNt[j], bNtl[j]);
+              mmaZ<K16, F16, SPLIT>(sa2[b][j], b2[b], b2l[b], bDt[j], bDtl[j]);
+              mmaZ<K16, F16, SPLIT>(sb[b][j], c2[b], c2l[b], bNt[j], bNtl[j]);
             }
 #pragma unroll
           for (int b = 0; b < BR; ++b) {
@@ -652,11 +734,11 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_
             for (int j = 0; j < NTL; ++j)
 #pragma unroll
               for (int r = 0; r < 4; ++r) sa[b][j][r] += sa2[b][j][r];
-            uint32_t o[4];
-            to_frag<NTL, F16>(sa[b], o);
-            stsm<NTL>(at(A0, off[b], trash), o);
-            to_frag<NTL, F16>(sb[b], o);
-            stsm<NTL>(at(A1, off[b], trash), o);
+            uint32_t o[4], ol[4];
+            to_frag2<NTL, F16, SPLIT>(sa[b], o, ol);
+            stsm2<NTL, SPLIT>(A0, LO, off[b], trash, o, ol);
+            to_frag2<NTL, F16, SPLIT>(sb[b], o, ol);
+            stsm2<NTL, SPLIT>(A1, LO, off[b], trash, o, ol);
           }
         }
       }
@@ -667,16 +749,16 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_
       for (int mt = warp; mt < NMT; mt += NW) {
         const int g0 = 2 * mt;
         const int off = row_off<N, CPLX, 0>(g0, lane);
-        uint32_t a[4], b[4];
-        ldsm<K16>(at(A0, off, zero_row), a);
-        ldsm<K16>(at(A1, off, zero_row), b);
+        uint32_t a[4], b[4], al[4], bl[4];
+        ldsm2<K16, SPLIT>(A0, LO, off, zero_row, a, al);
+        ldsm2<K16, SPLIT>(A1, LO, off, zero_row, b, bl);
         float y[NTL][4], y2[NTL][4], ye[2][NTL][4];
         zero(ye[0]);
         zero(ye[1]);
 #pragma unroll
         for (int j = 0; j < NTL; ++j) {
-          mma0<K16, F16>(y[j], a, bNt[j]);
-          mma0<K16, F16>(y2[j], b, bDt[j]);
+          mmaZ<K16, F16, SPLIT>(y[j], a, al, bNt[j], bNtl[j]);
+          mmaZ<K16, F16, SPLIT>(y2[j], b, bl, bDt[j], bDtl[j]);
         }
         // Y^(e)[(line, v)][i] += sum_b Q[a][b][v] F[pair][b][i + N line]: A = Q^T
         // (rows of one line only, the other half zero), B = the packed F block
@@ -684,7 +766,7 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_
           const int pr = p.cell_pairs[pi];
           const float* Qa = p.Q + (int64_t)p.pair_atom[pr] * p.n_proj * p.ld;
           const bool act = col < p.ncols;
-          uint32_t aq[S][2];
+          uint32_t aq[S][2], aql[S][2];
 #pragma unroll
           for (int kh = 0; kh < 2; ++kh) {
             const int b0 = 2 * tig + 8 * kh;
@@ -704,13 +786,14 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_
             if constexpr (CPLX) {
               // real column: Fr Qr - Fi Qi; imaginary column: Fr Qi + Fi Qr
               const bool im = gq & 1;
-              aq[0][kh] = pack16<F16>(im ? q[0][1] : q[0][0], im ? q[1][1] : q[1][0]);
-              aq[S - 1][kh] = pack16<F16>(im ? q[0][0] : -q[0][1], im ? q[1][0] : -q[1][1]);
+              pack2<F16, SPLIT>(im ? q[0][1] : q[0][0], im ? q[1][1] : q[1][0], aq[0][kh], aql[0][kh]);
+              pack2<F16, SPLIT>(im ? q[0][0] : -q[0][1], im ? q[1][0] : -q[1][1], aq[S - 1][kh], aql[S - 1][kh]);
             } else {
-              aq[0][kh] = pack16<F16>(q[0][0], q[1][0]);
+              pack2<F16, SPLIT>(q[0][0], q[1][0], aq[0][kh], aql[0][kh]);
             }
           }
-          const uint2* fp = p.fpack + ((size_t)pr * NMT + mt) * (2 * NTL * S * 32) + lane;
+          const size_t fofs = ((size_t)pr * NMT + mt) * (2 * NTL * S * 32) + lane;
+          const uint2* fp = p.fpack + fofs;
 #pragma unroll
           for (int h = 0; h < 2; ++h)
 #pragma unroll
@@ -719,12 +802,22 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_
               for (int st = 0; st < S; ++st) {
                 const uint2 fb = __ldg(fp + ((h * NTL + j) * S + st) * 32);
                 const uint32_t bb[2] = {fb.x, fb.y};
-                uint32_t af[4];
+                uint32_t bbl[2] = {0u, 0u};
+                if constexpr (SPLIT) {
+                  const uint2 fl = __ldg(p.fpack_lo + fofs + ((h * NTL + j) * S + st) * 32);
+                  bbl[0] = fl.x;
+                  bbl[1] = fl.y;
+                }
+                uint32_t af[4], afl[4];
                 af[0] = h == 0 ? aq[st][0] : 0u;
                 af[1] = h == 1 ? aq[st][0] : 0u;
                 af[2] = h == 0 ? aq[st][1] : 0u;
                 af[3] = h == 1 ? aq[st][1] : 0u;
-                mma<true, F16>(ye[h][j], af, bb);
+                afl[0] = h == 0 ? aql[st][0] : 0u;
+                afl[1] = h == 1 ? aql[st][0] : 0u;
+                afl[2] = h == 0 ? aql[st][1] : 0u;
+                afl[3] = h == 1 ? aql[st][1] : 0u;
+                mmaA<true, F16, SPLIT>(ye[h][j], af, afl, bb, bbl);
               }
         }
 #pragma unroll
@@ -749,35 +842,35 @@ __global__ void __launch_bounds__(Geom<N, CPLX>::NT, Geom<N, CPLX>::MINB) fe_tc_
   }
 }
 
-template <int N, bool CPLX, bool F16>
+template <int N, bool CPLX, bool F16, bool SPLIT = false>
 cudaError_t launch_tc_n(const TcParams& p, cudaStream_t s) {
-  using Gm = Geom<N, CPLX>;
+  using Gm = Geom<N, CPLX, SPLIT>;
   if (p.n_cells == 0) return cudaSuccess;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaError_t err =
-      cudaFuncSetAttribute(fe_tc_kernel<N, CPLX, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, Gm::BYTES);
+  cudaError_t err = cudaFuncSetAttribute(fe_tc_kernel<N, CPLX, F16, SPLIT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Gm::BYTES);
   if (err != cudaSuccess) return err;
   // ask for the largest shared-memory carveout so that MINB CTAs fit on an SM with room to spare
-  err = cudaFuncSetAttribute(fe_tc_kernel<N, CPLX, F16>, cudaFuncAttributePreferredSharedMemoryCarveout,
+  err = cudaFuncSetAttribute(fe_tc_kernel<N, CPLX, F16, SPLIT>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
   if (err != cudaSuccess) return err;
   const int ntiles = (p.ncols + 7) / 8;
   // about eight resident waves of CTAs: split the column tiles of a cell over
   // gridDim.y CTAs when the colour has few cells
-  const int want = 8 * 2 * (sms > 0 ? sms : 152);
+  const int want = 8 * Gm::MINB * (sms > 0 ? sms : 152);
   int gy = (want + p.n_cells - 1) / p.n_cells;
   gy = gy < 1 ? 1 : (gy > ntiles ? ntiles : gy);
   if (gy > 65535) gy = 65535;
   const int gx = p.n_cells < (1 << 30) ? p.n_cells : (1 << 30);
-  fe_tc_kernel<N, CPLX, F16><<<dim3(gx, gy), Gm::NT, Gm::BYTES, s>>>(p);
+  fe_tc_kernel<N, CPLX, F16, SPLIT><<<dim3(gx, gy), Gm::NT, Gm::BYTES, s>>>(p);
   return cudaGetLastError();
 }
 
 }  // namespace tc
 
-void build_tc_fpack(int n, bool cplx, int n_proj, int64_t n_pairs, const double* F, bool f16, std::vector<uint2>& out) {
+void build_tc_fpack(int n, bool cplx, int n_proj, int64_t n_pairs, const double* F, int kind, std::vector<uint2>& out) {
   const int G = n * n, NMT = (G + 1) / 2, NTL = n > 8 ? 2 : 1, S = cplx ? 2 : 1, np3 = n * n * n;
   out.assign((size_t)n_pairs * NMT * 2 * NTL * S * 32, make_uint2(0u, 0u));
   size_t w = 0;
@@ -793,7 +886,9 @@ void build_tc_fpack(int n, bool cplx, int n_proj, int64_t n_pairs, const double*
                 const size_t idx = ((size_t)pr * n_proj + k) * np3 + i + (size_t)n * g;
                 return cplx ? F[2 * idx + st] : F[idx];
               };
-              auto h = [&](double x) -> uint32_t { return f16 ? f16_bits(x) : bf16_bits(x); };
+              auto h = [&](double x) -> uint32_t {
+                return kind == 1 ? f16_bits(x) : kind == 2 ? bf16_lo_bits(x) : bf16_bits(x);
+              };
               out[w].x = h(B(2 * tig)) | (h(B(2 * tig + 1)) << 16);
               out[w].y = h(B(2 * tig + 8)) | (h(B(2 * tig + 9)) << 16);
             }
@@ -818,7 +913,8 @@ size_t tc_smem_bytes(int n, bool cplx) {
   }
 }
 
-cudaError_t launch_tc(const Ctx& c, const LocalParams<float>& lp, cudaStream_t s, bool f16) {
+cudaError_t launch_tc(const Ctx& c, const LocalParams<float>& lp, cudaStream_t s, int tc) {
+  const bool f16 = tc == 2, split = tc == 3;
   TcParams p{};
   p.X = lp.X;
   p.Y = lp.Y;
@@ -840,11 +936,15 @@ cudaError_t launch_tc(const Ctx& c, const LocalParams<float>& lp, cudaStream_t s
   p.alpha = lp.alpha;
   p.frag = f16 ? c.tc_frag16 : c.tc_frag;
   p.fpack = f16 ? c.tc_fpack16 : c.tc_fpack;
-  if (p.cell_pair_ptr && !p.fpack) return cudaErrorInvalidValue;
+  p.frag_lo = c.tc_frag_lo;
+  p.fpack_lo = c.tc_fpack_lo;
+  if (p.cell_pair_ptr && (!p.fpack || (split && !p.fpack_lo))) return cudaErrorInvalidValue;
   switch (c.np) {
-#define FEKS_TC_LAUNCH(NN)                                                                   \
-  case NN:                                                                                   \
-    if (f16) return c.cplx ? tc::launch_tc_n<NN, true, true>(p, s) : tc::launch_tc_n<NN, false, true>(p, s); \
+#define FEKS_TC_LAUNCH(NN)                                                                                    \
+  case NN:                                                                                                    \
+    if (f16) return c.cplx ? tc::launch_tc_n<NN, true, true>(p, s) : tc::launch_tc_n<NN, false, true>(p, s);  \
+    if (split)                                                                                                \
+      return c.cplx ? tc::launch_tc_n<NN, true, false, true>(p, s) : tc::launch_tc_n<NN, false, false, true>(p, s); \
     return c.cplx ? tc::launch_tc_n<NN, true, false>(p, s) : tc::launch_tc_n<NN, false, false>(p, s);
     FEKS_TC_LAUNCH(2)
     FEKS_TC_LAUNCH(3)

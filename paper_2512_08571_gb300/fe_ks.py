@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libfe_ks.so")
 FE_KS_OK = 0
 STATUS_NAMES = {0: "FE_KS_OK", -1: "FE_KS_ERR_ARG", -2: "FE_KS_ERR_MESH", -3: "FE_KS_ERR_CUDA",
                 -4: "FE_KS_ERR_OOM", -5: "FE_KS_ERR_TIMEOUT", -6: "FE_KS_ERR_UNSUPPORTED"}
-FE_KS_F64, FE_KS_F32, FE_KS_F64E, FE_KS_BF16, FE_KS_F16 = 0, 1, 2, 3, 4
+FE_KS_F64, FE_KS_F32, FE_KS_F64E, FE_KS_BF16, FE_KS_F16, FE_KS_BF16X2 = 0, 1, 2, 3, 4, 5
 TERM_T, TERM_L, TERM_G, TERM_K, TERM_NL, TERM_ALL = 1, 2, 4, 8, 16, 31
 
 

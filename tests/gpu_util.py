@@ -38,7 +38,7 @@ def torch_dtype(precision, cplx):
 
 def round_input(X, precision):
     """The input the GPU actually sees, promoted back to FP64 for the oracle."""
-    if precision in (fk.FE_KS_F32, fk.FE_KS_BF16):   # BF16 mode stores X and Y in FP32
+    if precision in (fk.FE_KS_F32, fk.FE_KS_BF16, fk.FE_KS_F16, fk.FE_KS_BF16X2):   # FP32 storage
         return X.astype(np.complex64 if np.iscomplexobj(X) else np.float32).astype(
             np.complex128 if np.iscomplexobj(X) else np.float64)
     return X

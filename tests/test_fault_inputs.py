@@ -16,7 +16,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("precision", [fk.FE_KS_F64, fk.FE_KS_F32, fk.FE_KS_BF16, fk.FE_KS_F16])
+@pytest.mark.parametrize("precision", [fk.FE_KS_F64, fk.FE_KS_F32, fk.FE_KS_BF16, fk.FE_KS_F16, fk.FE_KS_BF16X2])
 def test_nan_in_x_stays_local(precision):
     wl = CONFIGS["C1"].scaled(n=3, n_v=3)
     hp = HostProblem(wl)

@@ -69,7 +69,8 @@ def test_one_filter_pass_matches_oracle(dense, gpu, precision, tol, resid):
                                                    (fk.FE_KS_F32, fk.FE_KS_F64, False),
                                                    (fk.FE_KS_F32, fk.FE_KS_F64E, True),
                                                    (fk.FE_KS_BF16, fk.FE_KS_F64E, True),
-                                                   (fk.FE_KS_F16, fk.FE_KS_F64E, True)])
+                                                   (fk.FE_KS_F16, fk.FE_KS_F64E, True),
+                                                   (fk.FE_KS_BF16X2, fk.FE_KS_F64E, True)])
 def test_eigensolver_converges_to_oracle_eigenvalues(dense, gpu, precision, exact, pairs):
     """Converged eigenvalues within 1e-8 Ha of the dense oracle for every recurrence
     arithmetic, the 16-bit tensor-core ones included: the residual the filter

@@ -14,7 +14,10 @@ element and a column norm is no worse.  The tests hold the per-column
 relative error (max over columns) to 8 u = 2^-5 = 0.03125, which the measured
 errors clear by a wide margin; the input the oracle sees is the FP32-rounded
 one, so only the arithmetic differs.  The same bound with u = 2^-11 holds
-for FP16.
+for FP16.  The split precision FE_KS_BF16X2 holds every 16-bit operand as
+hi + lo (hi = bf16(x), lo = bf16(x - hi)): the pair carries x to a relative
+error of 2^-16, and the dropped lo * lo term of each product is below 2^-16 of
+it, so the same count of roundings with u = 2^-16 gives 8 u = 2^-13.
 """
 import numpy as np
 import pytest
@@ -28,12 +31,12 @@ from gpu_util import gpu_apply, parity_err, round_input
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-U = {fk.FE_KS_BF16: 2.0 ** -8, fk.FE_KS_F16: 2.0 ** -11}
+U = {fk.FE_KS_BF16: 2.0 ** -8, fk.FE_KS_F16: 2.0 ** -11, fk.FE_KS_BF16X2: 2.0 ** -16}
 TOL16 = {prec: 8 * u for prec, u in U.items()}
 TOL = TOL16[fk.FE_KS_BF16]
 BF = fk.FE_KS_BF16
-TC = [fk.FE_KS_BF16, fk.FE_KS_F16]
-NAME = {fk.FE_KS_BF16: "BF16", fk.FE_KS_F16: "FP16"}
+TC = [fk.FE_KS_BF16, fk.FE_KS_F16, fk.FE_KS_BF16X2]
+NAME = {fk.FE_KS_BF16: "BF16", fk.FE_KS_F16: "FP16", fk.FE_KS_BF16X2: "BF16x2"}
 
 SMALL = {
     "C1": CONFIGS["C1"],
@@ -157,3 +160,15 @@ def test_columns_of_very_different_size(cases, prec):
     Y = gpu_apply(hp, Xin, prec)
     err = parity_err(Y, P.apply(Xin))
     assert err <= TOL16[prec], err
+
+
+def test_split_precision_is_near_fp32(cases):
+    """BF16x2 really carries the extra digits: on every case its error is at least
+    16 times smaller than single BF16's (the bound ratio is 2^8)."""
+    for key in ("C2s", "C4v", "C3v"):
+        wl, hp, P, X = cases[key]
+        Xin = round_input(X, BF)
+        ref = P.apply(Xin)
+        e1 = parity_err(gpu_apply(hp, Xin, BF), ref)
+        e2 = parity_err(gpu_apply(hp, Xin, fk.FE_KS_BF16X2), ref)
+        assert e2 * 16 <= e1, (key, e1, e2)

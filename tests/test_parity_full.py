@@ -24,7 +24,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL = {fk.FE_KS_F64: 1e-12, fk.FE_KS_F32: 1e-5, fk.FE_KS_F64E: 1e-12,
-       fk.FE_KS_BF16: 2.0 ** -5, fk.FE_KS_F16: 2.0 ** -8}   # 8 u of the 16-bit types (test_parity_bf16)
+       fk.FE_KS_BF16: 2.0 ** -5, fk.FE_KS_F16: 2.0 ** -8,
+       fk.FE_KS_BF16X2: 2.0 ** -13}   # 8 u of the 16-bit types (test_parity_bf16)
 
 
 def _rows(P, wl, seed):
@@ -52,7 +53,7 @@ def test_full_size_sampled_rows(key):
     try:
         precisions = [fk.FE_KS_F64, fk.FE_KS_F32, fk.FE_KS_F64E]
         if wl.nq == wl.p + 1:      # the tensor-core kernel needs square 1D operators
-            precisions += [fk.FE_KS_BF16, fk.FE_KS_F16]
+            precisions += [fk.FE_KS_BF16, fk.FE_KS_F16, fk.FE_KS_BF16X2]
         for precision in precisions:
             dt = torch_dtype(precision, hp.complex)
             X = torch.empty((hp.m, wl.n_v), dtype=dt, device="cuda")

@@ -89,7 +89,7 @@ def test_scaled_apply_nq_np2(cases):
 
 def test_tensor_core_precisions_refuse_nq_np2(cases):
     wl, hp, P, X = cases["C4q"]
-    for precision in (fk.FE_KS_BF16, fk.FE_KS_F16):
+    for precision in (fk.FE_KS_BF16, fk.FE_KS_F16, fk.FE_KS_BF16X2):
         with pytest.raises(fk.FeKsError, match="UNSUPPORTED"):
             gpu_apply(hp, X.astype(np.float32), precision)
 

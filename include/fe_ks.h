@@ -362,6 +362,22 @@ fe_ks_status fe_ks_batch_configure(fe_ks_batch* b, const int* tile_config, int c
                                    int threads_per_block);
 fe_ks_status fe_ks_batch_apply(fe_ks_batch* b, const void* const* X, void* const* Y, void* cuda_stream);
 fe_ks_status fe_ks_batch_status(fe_ks_batch* b);
+/*
+ * Split mode of the batched launch: threads_f64 = threads_f32 = 0 turns it
+ * off (the default); otherwise both are block sizes in {256, 384, 512}.  The
+ * FP64 systems' items and the FP32 systems' items then go to two queues, each
+ * drained by a persistent kernel object that holds only that precision's
+ * routines (so each has the register budget of its own routines, capped at
+ * half the register file), and fe_ks_batch_apply launches the two objects
+ * concurrently: the FP64 one on cuda_stream, the FP32 one on a side stream
+ * forked from and joined back into cuda_stream with events (still one graph
+ * when captured).  An FP64 CTA and an FP32 CTA can then share an SM, one
+ * loading its FP64 pipe and the other its FP32 pipe.  Dependencies are per
+ * system as before; a system's items all sit in its class's queue.  The
+ * first call creates the side stream and two events.  Rebuilds the queues
+ * (as fe_ks_batch_configure does); the other tunables are kept.
+ */
+fe_ks_status fe_ks_batch_set_split(fe_ks_batch* b, int threads_f64, int threads_f32);
 fe_ks_status fe_ks_batch_info(const fe_ks_batch* b, int* n_items, int* grid, size_t* smem_bytes);
 void fe_ks_batch_destroy(fe_ks_batch* b);
 

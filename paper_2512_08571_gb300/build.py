@@ -21,7 +21,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 DEGREES = range(1, 9)
 NQ_OFFSETS = (0, 2)   # n_q - n_p
-BATCH_THREADS = (384, 512, 672)   # block sizes of the batched persistent kernel
+BATCH_THREADS = (256, 384, 512, 672)   # block sizes of the batched persistent kernel
 
 
 def _nvcc():

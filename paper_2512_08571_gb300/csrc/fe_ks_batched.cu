@@ -22,6 +22,15 @@
 // claims per atomic fetch, the block size (384, 512 or 672 threads, one
 // kernel object each) and the resident CTAs per SM.  The device code is in
 // fe_ks_batched.cuh.
+//
+// Split mode (fe_ks_batch_set_split): the FP64 systems' items and the FP32
+// systems' items go to two queues, each drained by a persistent kernel object
+// that holds only that precision's routines (its own register budget), and
+// the two launches run concurrently (stream fork / join with events, so the
+// pair still captures as one graph).  FP64 items keep the SM's FP64 pipe busy
+// and FP32 items its FP32 pipe, so CTAs of the two objects sharing an SM
+// overlap.  Items still wait only on earlier items of their own system, which
+// sit in the same queue.
 #include <algorithm>
 #include <cstring>
 #include <numeric>
@@ -70,6 +79,24 @@ static cudaError_t launch_nt(int nt, const BatchParams& P, int grid, size_t smem
   }
 }
 
+static cudaError_t prepare_class_nt(int nt, int cls, size_t smem, int* per_sm) {
+  switch (nt) {
+    case 256: return batched_prepare_class<256>(cls, smem, per_sm);
+    case 384: return batched_prepare_class<384>(cls, smem, per_sm);
+    case 512: return batched_prepare_class<512>(cls, smem, per_sm);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+static cudaError_t launch_class_nt(int nt, int cls, const BatchParams& P, int grid, size_t smem, cudaStream_t s) {
+  switch (nt) {
+    case 256: return batched_launch_class<256>(cls, P, grid, smem, s);
+    case 384: return batched_launch_class<384>(cls, P, grid, smem, s);
+    case 512: return batched_launch_class<512>(cls, P, grid, smem, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 }  // namespace feks
 
 using namespace feks;
@@ -92,48 +119,68 @@ struct fe_ks_batch {
   int4* d_items = nullptr;
   int n_items = 0;
   int* d_need = nullptr;
-  int* d_state = nullptr;   // [queue][err][done: kMaxSys*kMaxPhase]
+  int* d_state = nullptr;   // [queue][queue of the FP32 class][err][done: kMaxSys*kMaxPhase]
   BatchParams host{};
   size_t smem = 0;
   int grid = 0;
   std::vector<size_t> item_capacity;
+  // split mode: block sizes of the FP64 and FP32 objects (0 = off), their queues and grids
+  int split_nt[2] = {0, 0};
+  int4* d_items_cls[2] = {nullptr, nullptr};
+  int n_items_cls[2] = {0, 0};
+  size_t smem_cls[2] = {0, 0};
+  int grid_cls[2] = {0, 0};
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
+
+static constexpr int kStateWords = 3 + kMaxSys * kMaxPhase;
+
+static bool batch_split(const fe_ks_batch* b) { return b->split_nt[0] > 0 && b->split_nt[1] > 0; }
 
 static fe_ks_status batch_build(fe_ks_batch* b) {
   std::vector<int4> items;
   std::vector<int> need(kMaxSys * kMaxPhase, 0);
   const int ns = (int)b->ctxs.size();
+  const bool split = batch_split(b);
   int max_ph = 0;
   for (int s = 0; s < ns; ++s) max_ph = std::max<int>(max_ph, (int)b->ctxs[s]->c.colour_ptr.size() - 1 + 2);
   if (max_ph >= kMaxPhase) return fail(FE_KS_ERR_UNSUPPORTED, "too many colours for the batched launch");
   std::vector<std::vector<int4>> per_phase(max_ph + 1);
+  std::vector<std::vector<int4>> per_phase_cls[2] = {std::vector<std::vector<int4>>(max_ph + 1),
+                                                     std::vector<std::vector<int4>>(max_ph + 1)};
   size_t smem = 0;
+  size_t smem_cls[2] = {0, 0};
   for (int s = 0; s < ns; ++s) {
     const Ctx& c = b->ctxs[s]->c;
     const int ncols = (int)b->n_v[s];
     const int vt = vt_of(c.p, b->cfg[s]);
+    const int cls = b->prec[s] == FE_KS_F64 ? 0 : 1;
+    const int nt = split ? b->split_nt[cls] : b->nt;
+    std::vector<std::vector<int4>>& pp = split ? per_phase_cls[cls] : per_phase;
+    size_t& sm = split ? smem_cls[cls] : smem;
     const size_t cb = b->prec[s] == FE_KS_F64 ? cell_bytes<double>(c.p, b->cfg[s]) : cell_bytes<float>(c.p, b->cfg[s]);
     if (cb == 0 || cb > 227 * 1024) return fail(FE_KS_ERR_UNSUPPORTED, "tile configuration does not fit");
-    smem = std::max(smem, cb);
+    sm = std::max(sm, cb);
     // phase 0: zero-fill slices and projections
     const int rows = std::max(1, 65536 / ncols);
     for (int64_t r = 0; r < c.m; r += rows) {
-      per_phase[0].push_back(make_int4(s | (kItemZero << 8), (int)r, 0, (int)std::min<int64_t>(rows, c.m - r)));
+      pp[0].push_back(make_int4(s | (kItemZero << 8), (int)r, 0, (int)std::min<int64_t>(rows, c.m - r)));
       need[s * kMaxPhase + 0]++;
     }
     const bool nl = (c.terms & FE_KS_TERM_NL) && c.n_pairs > 0;
     if (nl) {
-      const int cw = batch_proj_cw(ncols, b->nt);
-      smem = std::max(smem, b->prec[s] == FE_KS_F64 ? batch_proj_bytes<double>(c.n_proj, c.np3, cw, b->nt)
-                                                    : batch_proj_bytes<float>(c.n_proj, c.np3, cw, b->nt));
+      const int cw = batch_proj_cw(ncols, nt);
+      sm = std::max(sm, b->prec[s] == FE_KS_F64 ? batch_proj_bytes<double>(c.n_proj, c.np3, cw, nt)
+                                                : batch_proj_bytes<float>(c.n_proj, c.np3, cw, nt));
       for (int64_t pr = 0; pr < c.n_pairs; ++pr)
         for (int col = 0; col < ncols; col += cw) {
-          per_phase[0].push_back(make_int4(s | (kItemPair << 8), (int)pr, col, cw));
+          pp[0].push_back(make_int4(s | (kItemPair << 8), (int)pr, col, cw));
           need[s * kMaxPhase + 0]++;
         }
       for (int a = 0; a < c.n_atoms; ++a)
         for (int col = 0; col < ncols; col += cw) {
-          per_phase[1].push_back(make_int4(s | (kItemSum << 8) | (1 << 16), a, col, cw));
+          pp[1].push_back(make_int4(s | (kItemSum << 8) | (1 << 16), a, col, cw));
           need[s * kMaxPhase + 1]++;
         }
     }
@@ -143,28 +190,52 @@ static fe_ks_status batch_build(fe_ks_batch* b) {
       for (int c0 = c.colour_ptr[col]; c0 < c.colour_ptr[col + 1]; c0 += b->cells_per_item) {
         const int nc = std::min(b->cells_per_item, c.colour_ptr[col + 1] - c0);
         for (int t = 0; t < ncols; t += vt) {
-          per_phase[ph].push_back(make_int4(s | (kItemLocal << 8) | (ph << 16), c0, t, nc));
+          pp[ph].push_back(make_int4(s | (kItemLocal << 8) | (ph << 16), c0, t, nc));
           need[s * kMaxPhase + ph]++;
         }
       }
     }
   }
-  for (auto& v : per_phase) items.insert(items.end(), v.begin(), v.end());
   if (b->inject_missing) need[0]++;   // host-side fault injection: one item that is never published
-  // (re)allocate device queue
-  if (b->d_items) cudaFree(b->d_items);
-  b->d_items = nullptr;
-  if (cudaMalloc(&b->d_items, items.size() * sizeof(int4)) != cudaSuccess) return fail(FE_KS_ERR_OOM, "batch queue");
-  cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice);
   cudaMemcpy(b->d_need, need.data(), need.size() * sizeof(int), cudaMemcpyHostToDevice);
-  b->n_items = (int)items.size();
-  b->smem = smem;
-  int per_sm = 0;
-  if (prepare_nt(b->nt, smem, b->blocks_per_sm, &per_sm) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(FE_KS_ERR_CUDA, "batched kernel shared memory / occupancy");
+  auto upload_items = [&](const std::vector<int4>& v, int4** dst) -> bool {
+    if (*dst) cudaFree(*dst);
+    *dst = nullptr;
+    if (v.empty()) return true;
+    if (cudaMalloc(dst, v.size() * sizeof(int4)) != cudaSuccess) return false;
+    return cudaMemcpy(*dst, v.data(), v.size() * sizeof(int4), cudaMemcpyHostToDevice) == cudaSuccess;
+  };
+  if (split) {
+    for (int k = 0; k < 2; ++k) {
+      std::vector<int4> v;
+      for (auto& ph : per_phase_cls[k]) v.insert(v.end(), ph.begin(), ph.end());
+      if (!upload_items(v, &b->d_items_cls[k])) return fail(FE_KS_ERR_OOM, "batch queue");
+      b->n_items_cls[k] = (int)v.size();
+      b->smem_cls[k] = std::max<size_t>(smem_cls[k], 16);
+      b->grid_cls[k] = 0;
+      if (v.empty()) continue;
+      int per_sm = 0;
+      if (prepare_class_nt(b->split_nt[k], k == 0 ? kClassF64 : kClassF32, b->smem_cls[k], &per_sm) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FE_KS_ERR_CUDA, "batched class kernel shared memory / occupancy");
+      }
+      b->grid_cls[k] = std::max(1, per_sm) * b->sms;
+    }
+    b->n_items = b->n_items_cls[0] + b->n_items_cls[1];
+    b->smem = std::max(b->smem_cls[0], b->smem_cls[1]);
+    b->grid = b->grid_cls[0] + b->grid_cls[1];
+  } else {
+    for (auto& v : per_phase) items.insert(items.end(), v.begin(), v.end());
+    if (!upload_items(items, &b->d_items)) return fail(FE_KS_ERR_OOM, "batch queue");
+    b->n_items = (int)items.size();
+    b->smem = smem;
+    int per_sm = 0;
+    if (prepare_nt(b->nt, smem, b->blocks_per_sm, &per_sm) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(FE_KS_ERR_CUDA, "batched kernel shared memory / occupancy");
+    }
+    b->grid = std::max(1, per_sm) * b->sms;
   }
-  b->grid = std::max(1, per_sm) * b->sms;
   // kernel parameters
   BatchParams& P = b->host;
   P = BatchParams{};
@@ -200,8 +271,8 @@ static fe_ks_status batch_build(fe_ks_batch* b) {
   P.items = b->d_items;
   P.n_items = b->n_items;
   P.queue = b->d_state;
-  P.err = b->d_state + 1;
-  P.done = b->d_state + 2;
+  P.err = b->d_state + 2;
+  P.done = b->d_state + 3;
   P.need = b->d_need;
   P.depth = b->depth;
   int khz = 0;
@@ -238,7 +309,7 @@ fe_ks_status fe_ks_batch_create(fe_ks_ctx* const* ctxs, int n_sys, const int64_t
   cudaGetDevice(&b->device);
   cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
   if (cudaMalloc(&b->d_need, sizeof(int) * kMaxSys * kMaxPhase) != cudaSuccess ||
-      cudaMalloc(&b->d_state, sizeof(int) * (2 + kMaxSys * kMaxPhase)) != cudaSuccess) {
+      cudaMalloc(&b->d_state, sizeof(int) * kStateWords) != cudaSuccess) {
     if (b->d_need) cudaFree(b->d_need);
     delete b;
     return fail(FE_KS_ERR_OOM, "batch state");
@@ -290,17 +361,35 @@ fe_ks_status fe_ks_batch_apply(fe_ks_batch* b, const void* const* X, void* const
     P.sys[i].X = X[i];
     P.sys[i].Y = Y[i];
   }
-  if (cudaMemsetAsync(b->d_state, 0, sizeof(int) * (2 + kMaxSys * kMaxPhase), s) != cudaSuccess)
+  if (cudaMemsetAsync(b->d_state, 0, sizeof(int) * kStateWords, s) != cudaSuccess)
     return fail(FE_KS_ERR_CUDA, "reset of the batch counters failed");
-  cudaError_t err = launch_nt(b->nt, P, b->grid, b->smem, b->blocks_per_sm, s);
-  if (err != cudaSuccess) return fail(FE_KS_ERR_CUDA, std::string("batched kernel: ") + cudaGetErrorString(err));
+  if (!batch_split(b)) {
+    cudaError_t err = launch_nt(b->nt, P, b->grid, b->smem, b->blocks_per_sm, s);
+    if (err != cudaSuccess) return fail(FE_KS_ERR_CUDA, std::string("batched kernel: ") + cudaGetErrorString(err));
+    return FE_KS_OK;
+  }
+  // split: FP64 object on the caller's stream, FP32 object on the side stream, joined back
+  cudaError_t err = cudaEventRecord(b->ev_fork, s);
+  if (err == cudaSuccess) err = cudaStreamWaitEvent(b->side, b->ev_fork, 0);
+  for (int k = 0; k < 2 && err == cudaSuccess; ++k) {
+    if (b->n_items_cls[k] == 0) continue;
+    BatchParams Pk = P;
+    Pk.items = b->d_items_cls[k];
+    Pk.n_items = b->n_items_cls[k];
+    Pk.queue = b->d_state + k;
+    err = launch_class_nt(b->split_nt[k], k == 0 ? kClassF64 : kClassF32, Pk, b->grid_cls[k], b->smem_cls[k],
+                          k == 0 ? s : b->side);
+  }
+  if (err == cudaSuccess) err = cudaEventRecord(b->ev_join, b->side);
+  if (err == cudaSuccess) err = cudaStreamWaitEvent(s, b->ev_join, 0);
+  if (err != cudaSuccess) return fail(FE_KS_ERR_CUDA, std::string("batched class kernels: ") + cudaGetErrorString(err));
   return FE_KS_OK;
 }
 
 fe_ks_status fe_ks_batch_status(fe_ks_batch* b) {
   if (!b) return fail(FE_KS_ERR_ARG, "batch is NULL");
   int err = 0;
-  if (cudaMemcpy(&err, b->d_state + 1, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+  if (cudaDeviceSynchronize() != cudaSuccess || cudaMemcpy(&err, b->d_state + 2, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
     return fail(FE_KS_ERR_CUDA, "reading the batch status failed");
   if (err) return fail(FE_KS_ERR_TIMEOUT, "a batched work item waited longer than the configured limit");
   return FE_KS_OK;
@@ -314,8 +403,29 @@ fe_ks_status fe_ks_batch_info(const fe_ks_batch* b, int* n_items, int* grid, siz
   return FE_KS_OK;
 }
 
+fe_ks_status fe_ks_batch_set_split(fe_ks_batch* b, int threads_f64, int threads_f32) {
+  if (!b) return fail(FE_KS_ERR_ARG, "batch is NULL");
+  auto ok = [](int t) { return t == 0 || t == 256 || t == 384 || t == 512; };
+  if (!ok(threads_f64) || !ok(threads_f32) || ((threads_f64 == 0) != (threads_f32 == 0)))
+    return fail(FE_KS_ERR_ARG, "threads must both be 0 (off) or both in {256, 384, 512}");
+  if (threads_f64 && !b->side) {
+    if (cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess)
+      return fail(FE_KS_ERR_CUDA, "creating the split launch's stream and events failed");
+  }
+  b->split_nt[0] = threads_f64;
+  b->split_nt[1] = threads_f32;
+  return batch_build(b);
+}
+
 void fe_ks_batch_destroy(fe_ks_batch* b) {
   if (!b) return;
+  for (int k = 0; k < 2; ++k)
+    if (b->d_items_cls[k]) cudaFree(b->d_items_cls[k]);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_join) cudaEventDestroy(b->ev_join);
+  if (b->side) cudaStreamDestroy(b->side);
   if (b->d_items) cudaFree(b->d_items);
   if (b->d_need) cudaFree(b->d_need);
   if (b->d_state) cudaFree(b->d_state);

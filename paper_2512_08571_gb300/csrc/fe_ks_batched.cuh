@@ -10,8 +10,12 @@ namespace feks {
 constexpr int kMaxSys = 16;
 constexpr int kMaxPhase = 66;
 // Block sizes the persistent kernel is compiled for (one translation unit
-// each); fe_ks_batch_configure picks one.  384 is the default.
-constexpr int kBatchThreads[3] = {384, 512, 672};
+// each); fe_ks_batch_configure picks one.  384 is the default; 256 serves the
+// FP64 half of a split batch (fe_ks_batch_set_split).
+constexpr int kBatchThreads[4] = {384, 512, 672, 256};
+// Precision classes of a kernel object: every routine, or the FP64 / FP32 ones
+// only (a split batch runs one persistent launch per class, concurrently).
+enum : int { kClassAll = 0, kClassF64 = 1, kClassF32 = 2 };
 enum : int { kItemZero = 0, kItemPair = 1, kItemLocal = 2, kItemSum = 3 };
 
 
@@ -224,7 +228,7 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
   return v;
 }
 
-template <int NT, int MINB>
+template <int NT, int MINB, int CLS = kClassAll>
 __global__ void __launch_bounds__(NT, MINB) fe_batched_kernel(const __grid_constant__ BatchParams bp) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_base, s_stop;
@@ -256,26 +260,29 @@ __global__ void __launch_bounds__(NT, MINB) fe_batched_kernel(const __grid_const
       }
       __syncthreads();
       if (s_stop) return;   // bounded wait expired (or another CTA gave up): leave, the host reports it
-      if (kind == kItemZero) {
-        if (s.prec == FE_KS_F64)
-          zero_item<double>(s, w.y, w.w);
-        else
-          zero_item<float>(s, w.y, w.w);
-      } else if (kind == kItemPair) {
-        if (s.prec == FE_KS_F64)
-          pair_item<double, NT>(s, w.y, w.z, w.w, smem);
-        else
-          pair_item<float, NT>(s, w.y, w.z, w.w, smem);
-      } else if (kind == kItemSum) {
-        if (s.prec == FE_KS_F64)
-          sum_item<double, NT>(s, w.y, w.z, w.w);
-        else
-          sum_item<float, NT>(s, w.y, w.z, w.w);
+      // a class object only holds its own routines (the host queues only its systems' items)
+      if (s.prec == FE_KS_F64) {
+        if constexpr (CLS != kClassF32) {
+          if (kind == kItemZero)
+            zero_item<double>(s, w.y, w.w);
+          else if (kind == kItemPair)
+            pair_item<double, NT>(s, w.y, w.z, w.w, smem);
+          else if (kind == kItemSum)
+            sum_item<double, NT>(s, w.y, w.z, w.w);
+          else
+            local_item<double, NT>(s, bp.t64, w.y, w.w, w.z, smem);
+        }
       } else {
-        if (s.prec == FE_KS_F64)
-          local_item<double, NT>(s, bp.t64, w.y, w.w, w.z, smem);
-        else
-          local_item<float, NT>(s, bp.t32, w.y, w.w, w.z, smem);
+        if constexpr (CLS != kClassF64) {
+          if (kind == kItemZero)
+            zero_item<float>(s, w.y, w.w);
+          else if (kind == kItemPair)
+            pair_item<float, NT>(s, w.y, w.z, w.w, smem);
+          else if (kind == kItemSum)
+            sum_item<float, NT>(s, w.y, w.z, w.w);
+          else
+            local_item<float, NT>(s, bp.t32, w.y, w.w, w.z, smem);
+        }
       }
       __syncthreads();
       if (threadIdx.x == 0) {
@@ -292,5 +299,10 @@ template <int NT>
 cudaError_t batched_prepare(size_t smem, int blocks_per_sm, int* per_sm);
 template <int NT>
 cudaError_t batched_launch(const BatchParams& P, int grid, size_t smem, int blocks_per_sm, cudaStream_t s);
+// one-class objects (one CTA per SM budget, so that the other class's object can share the SM)
+template <int NT>
+cudaError_t batched_prepare_class(int cls, size_t smem, int* per_sm);
+template <int NT>
+cudaError_t batched_launch_class(int cls, const BatchParams& P, int grid, size_t smem, cudaStream_t s);
 
 }  // namespace feks

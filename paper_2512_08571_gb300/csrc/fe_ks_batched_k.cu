@@ -38,4 +38,24 @@ cudaError_t batched_launch<FEKS_BNT>(const BatchParams& P, int grid, size_t smem
   return cudaGetLastError();
 }
 
+// Class objects: their register budget is that of one class's routines, capped
+// at half the register file (MINB = 2), so that one CTA of the FP64 object and
+// one of the FP32 object can share an SM when the shared memory allows it.
+template <>
+cudaError_t batched_prepare_class<FEKS_BNT>(int cls, size_t smem, int* per_sm) {
+  auto k = cls == kClassF64 ? fe_batched_kernel<FEKS_BNT, 2, kClassF64> : fe_batched_kernel<FEKS_BNT, 2, kClassF32>;
+  cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, FEKS_BNT, smem);
+}
+
+template <>
+cudaError_t batched_launch_class<FEKS_BNT>(int cls, const BatchParams& P, int grid, size_t smem, cudaStream_t s) {
+  if (cls == kClassF64)
+    fe_batched_kernel<FEKS_BNT, 2, kClassF64><<<grid, FEKS_BNT, smem, s>>>(P);
+  else
+    fe_batched_kernel<FEKS_BNT, 2, kClassF32><<<grid, FEKS_BNT, smem, s>>>(P);
+  return cudaGetLastError();
+}
+
 }  // namespace feks

@@ -83,6 +83,7 @@ def _load():
                                           ctypes.c_double, ctypes.c_int, ctypes.c_int]
     lib.fe_ks_batch_apply.argtypes = [vp, P(vp), P(vp), vp]
     lib.fe_ks_batch_status.argtypes = [vp]
+    lib.fe_ks_batch_set_split.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     lib.fe_ks_batch_info.argtypes = [vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_size_t)]
     lib.fe_ks_batch_destroy.argtypes = [vp]
     lib.fe_ks_batch_destroy.restype = None
@@ -108,7 +109,7 @@ def _load():
                  "fe_ks_batch_configure", "fe_ks_batch_apply", "fe_ks_batch_status", "fe_ks_batch_info",
                  "fe_ks_gemm_f64", "fe_ks_gram_ff_workspace", "fe_ks_gram_ff", "fe_ks_rotate_ff",
                  "fe_ks_gram_ff_sym", "fe_ks_rayleigh_ritz_workspace", "fe_ks_rayleigh_ritz",
-                 "fe_ks_lanczos_bound_workspace", "fe_ks_lanczos_bound"):
+                 "fe_ks_lanczos_bound_workspace", "fe_ks_lanczos_bound", "fe_ks_batch_set_split"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -273,6 +274,10 @@ def fe_ks_batch_apply(batch, Xs, Ys, stream=None):
     xa = (ctypes.c_void_p * n)(*[_ptr(x) for x in Xs])
     ya = (ctypes.c_void_p * n)(*[_ptr(y) for y in Ys])
     _check(_lib.fe_ks_batch_apply(batch, xa, ya, stream))
+
+
+def fe_ks_batch_set_split(batch, threads_f64, threads_f32):
+    _check(_lib.fe_ks_batch_set_split(batch, threads_f64, threads_f32))
 
 
 def fe_ks_batch_status(batch):

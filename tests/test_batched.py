@@ -170,6 +170,56 @@ def test_bounded_wait_reports_timeout_and_recovers(batch_setup):
     _check(Ys, refs)
 
 
+@pytest.mark.parametrize("t64,t32", [(256, 384), (384, 512), (512, 256)])
+def test_split_batch_equals_individual_applications(batch_setup, t64, t32):
+    """Split mode: FP64 and FP32 systems drained by two concurrent class objects."""
+    wls, hps, ctxs, Xs, Ys, refs, b = batch_setup
+    fk.fe_ks_batch_configure(b, [(s // 2) % 2 for s in range(6)], 2, 2, 2.0, False)
+    fk.fe_ks_batch_set_split(b, t64, t32)
+    try:
+        for Y in Ys:
+            Y.fill_(float("nan"))
+        fk.fe_ks_batch_apply(b, Xs, Ys, torch.cuda.current_stream().cuda_stream)
+        fk.fe_ks_batch_status(b)
+        _check(Ys, refs)
+    finally:
+        fk.fe_ks_batch_set_split(b, 0, 0)
+
+
+def test_split_batch_in_cuda_graph_and_timeout(batch_setup):
+    """The forked pair of launches captures into one graph and replays; a never-published
+    item of the FP64 class still ends in FE_KS_ERR_TIMEOUT, and the batch recovers."""
+    wls, hps, ctxs, Xs, Ys, refs, b = batch_setup
+    fk.fe_ks_batch_configure(b, [1] * 6, 2, 2, 2.0, False)
+    fk.fe_ks_batch_set_split(b, 256, 384)
+    try:
+        stream = torch.cuda.current_stream()
+        fk.fe_ks_batch_apply(b, Xs, Ys, stream.cuda_stream)      # warm-up outside capture
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fk.fe_ks_batch_apply(b, Xs, Ys, torch.cuda.current_stream().cuda_stream)
+        for _ in range(2):
+            for Y in Ys:
+                Y.fill_(float("nan"))
+            g.replay()
+            torch.cuda.synchronize()
+            fk.fe_ks_batch_status(b)
+            _check(Ys, refs)
+        del g
+        fk.fe_ks_batch_configure(b, [1] * 6, 2, 2, 0.02, True)   # system 0 (FP64) misses one item
+        fk.fe_ks_batch_apply(b, Xs, Ys, stream.cuda_stream)
+        with pytest.raises(fk.FeKsError, match="TIMEOUT"):
+            fk.fe_ks_batch_status(b)
+        fk.fe_ks_batch_configure(b, [1] * 6, 2, 2, 2.0, False)
+        fk.fe_ks_batch_apply(b, Xs, Ys, stream.cuda_stream)
+        fk.fe_ks_batch_status(b)
+        _check(Ys, refs)
+    finally:
+        fk.fe_ks_batch_set_split(b, 0, 0)
+        fk.fe_ks_batch_configure(b, [0] * 6, 1, 1, 2.0, False)
+
+
 def test_batched_rejects_complex_and_bad_arguments():
     wl = Workload("cx", L=6.0, n=2, p=4, nq=5, n_v=2, kfrac=(0.2, 0, 0), complex=True, seed=1)
     hp = HostProblem(wl)

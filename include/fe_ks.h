@@ -548,6 +548,49 @@ fe_ks_status fe_ks_lanczos_bound_workspace(const fe_ks_ctx* ctx, int steps, size
 fe_ks_status fe_ks_lanczos_bound(fe_ks_ctx* ctx, const double* v0, int steps, int precision, void* work,
                                  size_t work_bytes, double* lam_max, double* alpha, double* beta, int* steps_done);
 
+/*
+ * FP64-accurate symmetric Gram product C = Y^T Z (n x n, known symmetric, e.g.
+ * Y^T M Y or Y^T H Y of Rayleigh-Ritz) on the 5th-generation tensor cores:
+ * every FP64 value is cut, relative to its column's largest exponent over a
+ * chunk of 32 rows, into seven exact 8-bit slices held as BF16; the slice
+ * products run as tcgen05 BF16 MMAs with FP32 accumulation, grouped so that
+ * the leading sums are exact integers; each chunk is scaled and accumulated
+ * in pairs of floats; chunk groups of 8192 rows are added in a fixed order
+ * (compensated).  Error about 2^-48 of sum_r |Y_ri Z_rj|, deterministic, C
+ * exactly symmetric.  Y, Z: device FP64 [m][n] row-major.  work: device,
+ * >= fe_ks_gram_tc_workspace bytes, 256-byte aligned.  The kernel flags a
+ * chunk whose scale 2^(E_i + E_j) (E the exponents of the two columns) falls
+ * outside the FP32 range (columns of magnitude far from 1: below about 2^-60
+ * or above 2^60 together); fe_ks_gram_tc_status (which synchronises) returns
+ * bit 0 = a bounded wait expired, bit 1 = such a chunk; in either case C is
+ * not valid and fe_ks_gram_ff_sym is the fallback.  Stream-ordered, no
+ * allocation.
+ */
+fe_ks_status fe_ks_gram_tc_workspace(int64_t m, int n, size_t* bytes);
+fe_ks_status fe_ks_gram_tc_sym(const double* Y, const double* Z, double* C, int64_t m, int n, void* work,
+                               size_t work_bytes, void* cuda_stream);
+fe_ks_status fe_ks_gram_tc_status(const void* work, int* status);
+
+/*
+ * FP64-accurate rotation X = Y E (Y [m][n], E [n][k], X [m][k], all row-major
+ * device FP64) on the tensor cores by the same exact slices: each row of Y and
+ * each column of E is cut relative to its own largest exponent over a chunk of
+ * 32 of the n contraction indices.  X must not overlap Y or E.  flags: device
+ * int[2], set to (a bounded wait expired, a chunk scale left the FP32 range);
+ * if either is set after the stream reaches the call, X is not valid.
+ * Stream-ordered, no allocation.
+ */
+fe_ks_status fe_ks_rotate_tc(const double* Y, const double* E, double* X, int64_t m, int n, int k, int* flags,
+                             void* cuda_stream);
+
+/*
+ * Which kernel the pair-of-floats Rayleigh-Ritz step (precision FE_KS_F64E of
+ * fe_ks_rayleigh_ritz) uses for its two Gram products: 1 (default) the
+ * tensor-core one above (falling back to the pair-of-floats kernel for a call
+ * whose status is not 0), 0 the pair-of-floats one.
+ */
+fe_ks_status fe_ks_set_rr_gram(fe_ks_ctx* ctx, int tensor_cores);
+
 /* Change the stream used by later calls. */
 fe_ks_status fe_ks_set_stream(fe_ks_ctx* ctx, void* cuda_stream);
 

@@ -16,7 +16,7 @@ namespace feks {
 constexpr int kGB = 64;    // tile of C (or X) per CTA: 64 x 64
 constexpr int kGK = 32;    // staged depth along the contracted dimension
 constexpr int kGT = 256;   // threads: 16 x 16, each owning 4 x 4 outputs
-constexpr int kGramChunk = 8192;
+constexpr int kGramChunk = kGramChunkRows;
 
 // Compensated dot-product step (Ogita, Rump & Oishi's Dot2, with pair
 // operands): acc.hi is the running float sum, acc.lo the accumulated error
@@ -168,6 +168,12 @@ __global__ void __launch_bounds__(kGT) ff_rotate_kernel(const double* __restrict
       const int j = j0 + tx * 4 + q;
       if (r < m && j < k) X[r * k + j] = (double)acc[p][q].hi + (double)acc[p][q].lo;
     }
+}
+
+cudaError_t launch_gram_reduce(const double* part, double* C, int nchunks, int n1, int n2, int upper, cudaStream_t s) {
+  const int nn = n1 * n2;
+  ff_gram_reduce_kernel<<<(nn + 255) / 256, 256, 0, s>>>(part, C, nchunks, nn, n2, upper);
+  return cudaGetLastError();
 }
 
 }  // namespace feks

@@ -104,6 +104,7 @@ struct Ctx {
   int p = 0, nq = 0, np = 0, np3 = 0, nq3 = 0;
   int cplx = 0, terms = 0, gga = 0, ncoef = 0;
   int cfg64 = 0, cfg32 = 0, cfgE = 0;   // tile configuration of the fused kernel per precision
+  int rr_gram_tc = 1;                   // Rayleigh-Ritz Gram products on the tensor cores (pairs plan)
   bool cfg_explicit[3] = {false, false, false};   // set by fe_ks_set_config / fe_ks_tune (F64, F32, F64E)
   int64_t E = 0, m = 0, n_v_max = 0;
   int n_atoms = 0, n_proj = 0;
@@ -196,6 +197,12 @@ fe_ks_status apply_core_emu(Ctx& c, const double* X, double* Y, int64_t ncols, b
                             bool zero_fill);
 
 constexpr int kLocalConfigs = 10;
+
+// Row chunk of the split Gram products: partials [chunk][n1][n2] of 8192 rows each,
+// summed in chunk order by launch_gram_reduce (compensated; upper = mirror the
+// upper triangle of a symmetric product).
+constexpr int kGramChunkRows = 8192;
+cudaError_t launch_gram_reduce(const double* part, double* C, int nchunks, int n1, int n2, int upper, cudaStream_t s);
 
 // kernel launchers (fe_ks_local_pN.cu)
 template <typename T, typename TS>

@@ -280,7 +280,7 @@ static fe_ks_status rr_layout(const Ctx& c, int64_t n_v, int precision, char* ba
   const size_t nn = (size_t)n_v * n_v * 8;
   size_t part = 0;
   if (precision == FE_KS_F64E) {
-    fe_ks_status st = fe_ks_gram_ff_workspace(c.m, (int)n_v, (int)n_v, &part);
+    fe_ks_status st = fe_ks_gram_tc_workspace(c.m, (int)n_v, &part);   // >= the pair-of-floats kernel's
     if (st != FE_KS_OK) return st;
   }
   cusolverDnHandle_t h;
@@ -318,18 +318,43 @@ static fe_ks_status rr_layout(const Ctx& c, int64_t n_v, int precision, char* ba
 
 // ---------------------------------------------------------------- tall products
 
-// C[n][n] = Y^T Z (symmetric: one-triangle product)
+// C[n][n] = Y^T Z (symmetric: one-triangle product).  Pairs plan: the tensor-core Gram,
+// checked (one synchronisation) and redone in pairs of floats if its status is not clean.
 static fe_ks_status rr_gram(const Ctx& c, int precision, const double* Y, const double* Z, double* C, int n,
                             const RrWork& w) {
-  if (precision == FE_KS_F64E)
+  if (precision == FE_KS_F64E) {
+    if (c.rr_gram_tc) {
+      fe_ks_status st = fe_ks_gram_tc_sym(Y, Z, C, c.m, n, w.part, w.part_bytes, c.stream);
+      if (st != FE_KS_OK) return st;
+      int status = 0;
+      if (cudaStreamSynchronize(c.stream) != cudaSuccess) return fail(FE_KS_ERR_CUDA, "Gram synchronisation");
+      st = fe_ks_gram_tc_status(w.part, &status);
+      if (st != FE_KS_OK) return st;
+      if (status == 0) return FE_KS_OK;
+    }
     return fe_ks_gram_ff_sym(Y, Z, C, c.m, n, w.part, w.part_bytes, c.stream);
+  }
   // row-major [m][n] is column-major n x m: C = Yc Zc^T
   return fe_ks_gemm_f64(0, 1, n, n, c.m, 1.0, Y, n, Z, n, 0.0, C, n, 0, c.stream);
 }
 
-// X[m][n] = Y[m][n] E[n][n]
-static fe_ks_status rr_rotate(const Ctx& c, int precision, const double* Y, const double* E, double* X, int n) {
-  if (precision == FE_KS_F64E) return fe_ks_rotate_ff(Y, E, X, c.m, n, n, c.stream);
+// X[m][n] = Y[m][n] E[n][n]; pairs plan: on the tensor cores (flags in the first bytes of the
+// Gram workspace, free at this point), checked and redone in pairs of floats if not clean
+static fe_ks_status rr_rotate(const Ctx& c, int precision, const double* Y, const double* E, double* X, int n,
+                              const RrWork& w) {
+  if (precision == FE_KS_F64E) {
+    if (c.rr_gram_tc) {
+      int* flags = reinterpret_cast<int*>(w.part);
+      fe_ks_status st = fe_ks_rotate_tc(Y, E, X, c.m, n, n, flags, c.stream);
+      if (st != FE_KS_OK) return st;
+      int f[2] = {0, 0};
+      if (cudaMemcpyAsync(f, flags, sizeof(f), cudaMemcpyDeviceToHost, c.stream) != cudaSuccess ||
+          cudaStreamSynchronize(c.stream) != cudaSuccess)
+        return fail(FE_KS_ERR_CUDA, "rotation status");
+      if (!f[0] && !f[1]) return FE_KS_OK;
+    }
+    return fe_ks_rotate_ff(Y, E, X, c.m, n, n, c.stream);
+  }
   // column-major: Xc (n x m) = Ec (n x n) Yc (n x m), Ec = E^T in memory terms
   return fe_ks_gemm_f64(0, 0, n, c.m, n, 1.0, E, n, Y, n, 0.0, X, n, 0, c.stream);
 }
@@ -378,7 +403,7 @@ static fe_ks_status cholqr_pass(Ctx& c, fe_ks_ctx* mass, int precision, const do
   k_rr_trsm_lower_t<<<(n + 127) / 128, 128, 0, s>>>(w.Sp, w.E, n, n);
   k_rr_row_scale<<<nb, 256, 0, s>>>(w.E, n, w.d);
   if ((st = last_cuda("Cholesky QR triangular solve")) != FE_KS_OK) return st;
-  return rr_rotate(c, precision, Y, w.E, Out, n);
+  return rr_rotate(c, precision, Y, w.E, Out, n, w);
 }
 
 }  // namespace feks
@@ -496,7 +521,7 @@ fe_ks_status fe_ks_rayleigh_ritz(fe_ks_ctx* ctx, fe_ks_ctx* mass, double* X, dou
     k_rr_row_scale<<<nb, 256, 0, s>>>(w.E, n, w.d);                        // d L^{-T} W
   }
   if ((st = last_cuda("Rayleigh-Ritz back-substitution")) != FE_KS_OK) return st;
-  if ((st = rr_rotate(c, precision, basis, w.E, w.T, n)) != FE_KS_OK) return st;
+  if ((st = rr_rotate(c, precision, basis, w.E, w.T, n, w)) != FE_KS_OK) return st;
   cudaMemcpyAsync(X, w.T, xbytes, cudaMemcpyDeviceToDevice, s);
   int info = 0;
   cudaMemcpyAsync(&info, w.info, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -504,6 +529,13 @@ fe_ks_status fe_ks_rayleigh_ritz(fe_ks_ctx* ctx, fe_ks_ctx* mass, double* X, dou
   if (info != 0) return fail(FE_KS_ERR_CUDA, "the projected eigensolve did not converge (syevd info " +
                                                  std::to_string(info) + ")");
   if (path) *path = used;
+  return FE_KS_OK;
+}
+
+fe_ks_status fe_ks_set_rr_gram(fe_ks_ctx* ctx, int tensor_cores) {
+  set_error("");
+  if (!ctx) return fail(FE_KS_ERR_ARG, "ctx is NULL");
+  ctx->c.rr_gram_tc = tensor_cores ? 1 : 0;
   return FE_KS_OK;
 }
 

@@ -99,6 +99,11 @@ def _load():
     lib.fe_ks_lanczos_bound.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_size_t,
                                         P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
                                         P(ctypes.c_int)]
+    lib.fe_ks_gram_tc_workspace.argtypes = [i64, ctypes.c_int, P(ctypes.c_size_t)]
+    lib.fe_ks_gram_tc_sym.argtypes = [vp, vp, vp, i64, ctypes.c_int, vp, ctypes.c_size_t, vp]
+    lib.fe_ks_gram_tc_status.argtypes = [vp, P(ctypes.c_int)]
+    lib.fe_ks_set_rr_gram.argtypes = [vp, ctypes.c_int]
+    lib.fe_ks_rotate_tc.argtypes = [vp, vp, vp, i64, ctypes.c_int, ctypes.c_int, vp, vp]
     lib.fe_ks_destroy.argtypes = [vp]
     lib.fe_ks_destroy.restype = None
     for name in ("fe_ks_quadrature_points", "fe_ks_setup", "fe_ks_apply", "fe_ks_apply_scaled",
@@ -109,7 +114,9 @@ def _load():
                  "fe_ks_batch_configure", "fe_ks_batch_apply", "fe_ks_batch_status", "fe_ks_batch_info",
                  "fe_ks_gemm_f64", "fe_ks_gram_ff_workspace", "fe_ks_gram_ff", "fe_ks_rotate_ff",
                  "fe_ks_gram_ff_sym", "fe_ks_rayleigh_ritz_workspace", "fe_ks_rayleigh_ritz",
-                 "fe_ks_lanczos_bound_workspace", "fe_ks_lanczos_bound", "fe_ks_batch_set_split"):
+                 "fe_ks_lanczos_bound_workspace", "fe_ks_lanczos_bound", "fe_ks_batch_set_split",
+                 "fe_ks_gram_tc_workspace", "fe_ks_gram_tc_sym", "fe_ks_gram_tc_status", "fe_ks_set_rr_gram",
+                 "fe_ks_rotate_tc"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -339,6 +346,39 @@ def fe_ks_gram_ff(Y, Z, stream=None, work=None, symmetric=False):
         _check(_lib.fe_ks_gram_ff(_ptr(Y), _ptr(Z), _ptr(C), m, n1, n2, _ptr(work), nb.value, stream))
     return C
 
+
+
+def fe_ks_gram_tc_sym(Y, Z, stream=None, work=None):
+    """Y^T Z for row-major FP64 device tensors [m][n] whose product is symmetric, on the
+    tensor cores (exact 8-bit slices).  Returns (C [n][n], status: 0 = valid)."""
+    import torch
+    m, n = Y.shape
+    nb = ctypes.c_size_t()
+    _check(_lib.fe_ks_gram_tc_workspace(m, n, ctypes.byref(nb)))
+    if work is None or work.numel() < nb.value + 256:
+        work = torch.empty(nb.value + 256, dtype=torch.uint8, device=Y.device)
+    off = (-work.data_ptr()) % 256
+    view = work[off:off + nb.value]
+    C = torch.empty((n, n), dtype=torch.float64, device=Y.device)
+    _check(_lib.fe_ks_gram_tc_sym(_ptr(Y), _ptr(Z), _ptr(C), m, n, _ptr(view), nb.value, stream))
+    st = ctypes.c_int()
+    _check(_lib.fe_ks_gram_tc_status(_ptr(view), ctypes.byref(st)))
+    return C, st.value
+
+
+def fe_ks_rotate_tc(Y, E, stream=None):
+    """Y E (row-major FP64 device tensors [m][n], [n][k]) on the tensor cores -> ([m][k], flags)."""
+    import torch
+    m, n = Y.shape
+    k = E.shape[1]
+    X = torch.empty((m, k), dtype=torch.float64, device=Y.device)
+    flags = torch.zeros(2, dtype=torch.int32, device=Y.device)
+    _check(_lib.fe_ks_rotate_tc(_ptr(Y), _ptr(E.contiguous()), _ptr(X), m, n, k, _ptr(flags), stream))
+    return X, flags.cpu().tolist()
+
+
+def fe_ks_set_rr_gram(ctx, tensor_cores):
+    _check(_lib.fe_ks_set_rr_gram(ctx, int(bool(tensor_cores))))
 
 
 def fe_ks_rotate_ff(Y, E, stream=None):

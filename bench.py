@@ -502,9 +502,12 @@ def run_filter(args, wl, ctx, hp, X64):
              "mixed": (fk.FE_KS_F32, fk.FE_KS_F64E, True),
              "mixed_bf16": (fk.FE_KS_BF16, fk.FE_KS_F64E, True),
              "mixed_f16": (fk.FE_KS_F16, fk.FE_KS_F64E, True),
-             "mixed_bf16x2": (fk.FE_KS_BF16X2, fk.FE_KS_F64E, True)}
+             "mixed_bf16x2": (fk.FE_KS_BF16X2, fk.FE_KS_F64E, True),
+             # the mixed plan with the Rayleigh-Ritz products in pairs of floats instead of on the tensor cores
+             "mixed_ff_rr": (fk.FE_KS_F32, fk.FE_KS_F64E, True)}
     lam = X = lmax = None
     for name, (prec, exact, pair_gemm) in plans.items():
+        fk.fe_ks_set_rr_gram(ctx, name != "mixed_ff_rr")
         sol = RChFSI(ctx, m, n_v, False, degree=20, precision=prec, exact=exact, gemm_pairs=pair_gemm)
         sol.lanczos_upper_bound()            # warm-up
         t_l, lm = ev_ms(sol.lanczos_upper_bound)
@@ -523,6 +526,7 @@ def run_filter(args, wl, ctx, hp, X64):
         out[name] = {"lanczos_ms": t_l, "rayleigh_ritz_ms": t_rr, "filter_ms": t_f, "pass_ms": t_l + t_rr + t_f}
         del sol, Xf
         torch.cuda.empty_cache()
+    fk.fe_ks_set_rr_gram(ctx, True)
     out["speedup_filter_mixed_vs_f64"] = out["f64"]["filter_ms"] / out["mixed"]["filter_ms"]
     out["speedup_pass_mixed_vs_f64"] = out["f64"]["pass_ms"] / out["mixed"]["pass_ms"]
     out["speedup_filter_bf16_vs_f64"] = out["f64"]["filter_ms"] / out["mixed_bf16"]["filter_ms"]
@@ -1134,8 +1138,10 @@ def compact_line(detail, args, config, world):
         fl = {"speedup_filter_mixed": _r(flt.get("speedup_filter_mixed_vs_f64"), 3),
               "speedup_pass_mixed": _r(flt.get("speedup_pass_mixed_vs_f64"), 3),
               "pass_ms": {k: _r(flt[k]["pass_ms"]) for k in ("f64", "f64_pairs", "mixed", "mixed_bf16",
-                                                              "mixed_f16", "mixed_bf16x2")
-                          if isinstance(flt.get(k), dict) and "pass_ms" in flt[k]}}
+                                                              "mixed_f16", "mixed_bf16x2", "mixed_ff_rr")
+                          if isinstance(flt.get(k), dict) and "pass_ms" in flt[k]},
+              "rr_ms": {k: _r(flt[k]["rayleigh_ritz_ms"]) for k in ("f64", "mixed", "mixed_ff_rr")
+                        if isinstance(flt.get(k), dict) and "rayleigh_ritz_ms" in flt[k]}}
         conv = flt.get("converged")
         if conv:
             fl["converged"] = {k: _r(conv[k], 3) for k in ("passes_f64", "passes_mixed", "ms_mixed", "ms_f64",

@@ -552,11 +552,12 @@ fe_ks_status fe_ks_lanczos_bound(fe_ks_ctx* ctx, const double* v0, int steps, in
  * FP64-accurate symmetric Gram product C = Y^T Z (n x n, known symmetric, e.g.
  * Y^T M Y or Y^T H Y of Rayleigh-Ritz) on the 5th-generation tensor cores:
  * every FP64 value is cut, relative to its column's largest exponent over a
- * chunk of 32 rows, into seven exact 8-bit slices held as BF16; the slice
- * products run as tcgen05 BF16 MMAs with FP32 accumulation, grouped so that
- * the leading sums are exact integers; each chunk is scaled and accumulated
- * in pairs of floats; chunk groups of 8192 rows are added in a fixed order
- * (compensated).  Error about 2^-48 of sum_r |Y_ri Z_rj|, deterministic, C
+ * chunk of 32 rows, into eight exact 7-bit slices held as BF16; the slice
+ * products run as tcgen05 BF16 MMAs with FP32 accumulation in six groups by
+ * slice order, so that every group that matters stays an exact integer; each
+ * chunk is scaled and accumulated in pairs of floats; chunk groups of 8192
+ * rows are added in a fixed order (compensated).  Error a few units of 2^-52
+ * of sum_r |Y_ri Z_rj|, deterministic, C
  * exactly symmetric.  Y, Z: device FP64 [m][n] row-major.  work: device,
  * >= fe_ks_gram_tc_workspace bytes, 256-byte aligned.  The kernel flags a
  * chunk whose scale 2^(E_i + E_j) (E the exponents of the two columns) falls

@@ -221,12 +221,14 @@ class RChFSI:
         lam, X = self.rayleigh_ritz(X0)
         res = None
         n_check = self.n_v if n_check is None else n_check
+        self.res_history = []   # largest residual norm of the checked pairs after each pass
         for it in range(n_iter):
             X = self.filter(X, lam)
             lam, X = self.rayleigh_ritz(X)
             if tol is not None:
                 res = self.residual_norms(X, lam)
-                if float(res[:n_check].max()) < tol:
+                self.res_history.append(float(res[:n_check].max()))
+                if self.res_history[-1] < tol:
                     return lam, X, res, it + 1
         if res is None:
             res = self.residual_norms(X, lam)

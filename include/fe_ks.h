@@ -246,8 +246,13 @@ fe_ks_status fe_ks_cheb_filter_ghep(fe_ks_ctx* ctx, fe_ks_ctx* mass, double* X, 
                                     int residual_precision, void* work, size_t work_bytes);
 
 /*
- * Tile configuration of the fused cell kernel (FE_KS_F64, FE_KS_F32,
- * FE_KS_F64E; the tensor-core kernel has one):
+ * Tile configuration of the fused cell kernel.  FE_KS_BF16 and FE_KS_F16 (real
+ * operators, n_q = n_p): 0 = the 5th-generation tensor-core kernel (tcgen05:
+ * the x-y plane products and the z sweeps of Algorithm 2 as four MMA chains
+ * per cell and 8-vector tile, accumulators in tensor memory; the default),
+ * 1 = the warp-level MMA kernel (one sweep per direction); complex operators
+ * and FE_KS_BF16X2 have the warp-level kernel only.  FE_KS_F64, FE_KS_F32,
+ * FE_KS_F64E:
  *   0..2  one CTA per (cell, column tile), 3 tile widths;
  *   3..4  one CTA per cell walking all column tiles, the next tile's rows of X
  *         staged by cp.async, reduction-based scatter;
@@ -276,6 +281,14 @@ fe_ks_status fe_ks_tune(fe_ks_ctx* ctx, const void* X, void* Y, int64_t n_v, int
                         double* ms_per_config, int* best);
 fe_ks_status fe_ks_set_config(fe_ks_ctx* ctx, int precision, int config);
 fe_ks_status fe_ks_get_config(const fe_ks_ctx* ctx, int precision, int* config);
+
+/*
+ * Device status of the context's cell kernels: synchronises the context's
+ * stream, returns in *status 1 if a bounded device-side wait of the tcgen05
+ * cell kernel expired since the last call (its results are then not valid),
+ * else 0, and clears the word.
+ */
+fe_ks_status fe_ks_device_status(fe_ks_ctx* ctx, int* status);
 
 /*
  * Cell-matrix (CM) baseline: the method the paper's matrix-free algorithms

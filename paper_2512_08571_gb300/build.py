@@ -33,7 +33,7 @@ def _nvcc():
 
 def _units():
     units = []
-    for name in ("fe_ks_api.cu", "fe_ks_tables.cu", "fe_ks_nonlocal.cu", "fe_ks_probe.cu", "fe_ks_cheb.cu", "fe_ks_static.cu", "fe_ks_batched.cu", "fe_ks_gemm.cu", "fe_ks_ffgemm.cu", "fe_ks_tc.cu", "fe_ks_cm.cu", "fe_ks_rr.cu", "fe_ks_tcgram.cu"):
+    for name in ("fe_ks_api.cu", "fe_ks_tables.cu", "fe_ks_nonlocal.cu", "fe_ks_probe.cu", "fe_ks_cheb.cu", "fe_ks_static.cu", "fe_ks_batched.cu", "fe_ks_gemm.cu", "fe_ks_ffgemm.cu", "fe_ks_tc.cu", "fe_ks_cm.cu", "fe_ks_rr.cu", "fe_ks_tcgram.cu", "fe_ks_tc5.cu"):
         units.append((os.path.join(CSRC, name), os.path.join(BUILD, name + ".o"), []))
     for nt in BATCH_THREADS:
         units.append((os.path.join(CSRC, "fe_ks_batched_k.cu"),

@@ -190,7 +190,21 @@ TuneKey tune_key(const Ctx& c, int prec, int64_t ncols) {
 }  // namespace
 
 int* config_slot(Ctx& c, int prec) {
-  return prec == FE_KS_F64 ? &c.cfg64 : prec == FE_KS_F32 ? &c.cfg32 : prec == FE_KS_F64E ? &c.cfgE : nullptr;
+  return prec == FE_KS_F64    ? &c.cfg64
+         : prec == FE_KS_F32  ? &c.cfg32
+         : prec == FE_KS_F64E ? &c.cfgE
+         : prec == FE_KS_BF16 ? &c.cfg_tc[0]
+         : prec == FE_KS_F16  ? &c.cfg_tc[1]
+                              : nullptr;
+}
+
+// tile configurations of a precision: 10 for the CUDA-core kernels; the BF16 and
+// FP16 cell kernels have two (0 = tcgen05, 1 = warp-level MMA) where the tcgen05
+// kernel serves the context (real, n_q = n_p), else one
+static int n_configs(const Ctx& c, int prec) {
+  if (prec == FE_KS_F64 || prec == FE_KS_F32 || prec == FE_KS_F64E) return kLocalConfigs;
+  if (prec == FE_KS_BF16 || prec == FE_KS_F16) return (!c.cplx && c.nq == c.np && c.tc5_cst) ? 2 : 1;
+  return 1;
 }
 
 void tune_cache_store(const Ctx& c, int prec, int64_t ncols, int cfg) {
@@ -523,6 +537,15 @@ fe_ks_status fe_ks_setup(const fe_ks_problem* prob, int terms_mask, int64_t n_v_
     ok = chk(upload(c, &c->tc_frag, frag.data(), frag.size())) &&
          chk(upload(c, &c->tc_frag16, frag16.data(), frag16.size())) &&
          chk(upload(c, &c->tc_frag_lo, fraglo.data(), fraglo.size()));
+    const int zero = 0;
+    ok = ok && chk(upload(c, &c->dev_status, &zero, 1));
+    if (ok && !c->cplx && c->nq == c->np) {   // the tcgen05 cell kernel's operator block
+      std::vector<uint4> cst;
+      build_tc5_const(c->p, false, cst);
+      ok = chk(upload(c, &c->tc5_cst, cst.data(), cst.size()));
+      build_tc5_const(c->p, true, cst);
+      ok = ok && chk(upload(c, &c->tc5_cst16, cst.data(), cst.size()));
+    }
   }
   if (ok && want_nl) {
     std::vector<double> hh(prob->h_coef, prob->h_coef + (size_t)prob->n_atoms * prob->n_proj);
@@ -712,7 +735,9 @@ fe_ks_status apply_core(Ctx& c, const T* X, T* Y, int64_t ncols, bool scaled, T 
     lp.n_cells = c.colour_ptr[col + 1] - c.colour_ptr[col];
     cudaError_t err;
     if constexpr (std::is_same<T, float>::value)
-      err = tc ? launch_tc(c, lp, s, tc) : launch_local<T, T>(c, lp, s);   // tc: n_q = n_p, checked above
+      err = !tc ? launch_local<T, T>(c, lp, s)   // tc: n_q = n_p, checked above
+            : use_tc5(c, tc) ? launch_tc5(c, lp, s, tc == 2)
+                             : launch_tc(c, lp, s, tc);
     else
       err = launch_local<T, T>(c, lp, s);
     if (err != cudaSuccess) return fail(FE_KS_ERR_CUDA, std::string("local kernel: ") + cudaGetErrorString(err));
@@ -846,9 +871,9 @@ fe_ks_status fe_ks_apply(fe_ks_ctx* ctx, const void* X, void* Y, int64_t n_v, in
 
 fe_ks_status fe_ks_set_config(fe_ks_ctx* ctx, int precision, int config) {
   if (!ctx) return fail(FE_KS_ERR_ARG, "ctx is NULL");
-  if (config < 0 || config >= kLocalConfigs) return fail(FE_KS_ERR_ARG, "config out of range");
   int* slot = config_slot(ctx->c, precision);
   if (!slot) return fail(FE_KS_ERR_UNSUPPORTED, "precision without tile configurations");
+  if (config < 0 || config >= n_configs(ctx->c, precision)) return fail(FE_KS_ERR_ARG, "config out of range");
   *slot = config;
   ctx->c.cfg_explicit[precision] = true;
   return FE_KS_OK;
@@ -885,15 +910,13 @@ fe_ks_status fe_ks_tune(fe_ks_ctx* ctx, const void* X, void* Y, int64_t n_v, int
     return fail(FE_KS_ERR_UNSUPPORTED, "unknown precision");
   if (reps < 1) reps = 1;
   Ctx& c = ctx->c;
-  int single = 0;   // the tensor-core kernel has one configuration
-  int& cfg = precision == FE_KS_F64 ? c.cfg64
-             : precision == FE_KS_F32 ? c.cfg32
-             : precision == FE_KS_F64E ? c.cfgE
-                                       : single;
+  int single = 0;   // the split-precision kernel has one configuration
+  int* slot = config_slot(c, precision);
+  int& cfg = slot ? *slot : single;
   const bool tcp = precision == FE_KS_BF16 || precision == FE_KS_F16 || precision == FE_KS_BF16X2;
-  const int n_conf = tcp ? 1 : kLocalConfigs;
+  const int n_conf = n_configs(c, precision);
   const int keep = cfg;
-  bool* expl = (precision <= FE_KS_F64E) ? &c.cfg_explicit[precision] : nullptr;
+  bool* expl = slot ? &c.cfg_explicit[precision] : nullptr;
   const bool keep_expl = expl ? *expl : false;
   if (expl) *expl = true;   // the loop below sets the configuration itself
   cudaEvent_t e0, e1;
@@ -936,6 +959,19 @@ fe_ks_status fe_ks_tune(fe_ks_ctx* ctx, const void* X, void* Y, int64_t n_v, int
     c.cfg_explicit[precision] = true;
     tune_cache_store(c, precision, n_v * (c.cplx ? 2 : 1), best_cfg);
   }
+  return FE_KS_OK;
+}
+
+fe_ks_status fe_ks_device_status(fe_ks_ctx* ctx, int* status) {
+  g_last_error.clear();
+  if (!ctx || !status) return fail(FE_KS_ERR_ARG, "NULL argument");
+  Ctx& c = ctx->c;
+  int v = 0;
+  if (cudaStreamSynchronize(c.stream) != cudaSuccess ||
+      cudaMemcpy(&v, c.dev_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemset(c.dev_status, 0, sizeof(int)) != cudaSuccess)
+    return fail(FE_KS_ERR_CUDA, "reading the device status failed");
+  *status = v;
   return FE_KS_OK;
 }
 

@@ -105,7 +105,8 @@ struct Ctx {
   int cplx = 0, terms = 0, gga = 0, ncoef = 0;
   int cfg64 = 0, cfg32 = 0, cfgE = 0;   // tile configuration of the fused kernel per precision
   int rr_gram_tc = 1;                   // Rayleigh-Ritz Gram products on the tensor cores (pairs plan)
-  bool cfg_explicit[3] = {false, false, false};   // set by fe_ks_set_config / fe_ks_tune (F64, F32, F64E)
+  int cfg_tc[2] = {0, 0};               // BF16, FP16 cell kernel: 0 = tcgen05 (where supported), 1 = warp-level MMA
+  bool cfg_explicit[6] = {};            // set by fe_ks_set_config / fe_ks_tune, per precision
   int64_t E = 0, m = 0, n_v_max = 0;
   int n_atoms = 0, n_proj = 0;
   int64_t n_pairs = 0;
@@ -139,6 +140,9 @@ struct Ctx {
   uint2* tc_fpack16 = nullptr;     // the same in FP16
   uint32_t* tc_frag_lo = nullptr;  // BF16 remainders of the 1D operators (split precision FE_KS_BF16X2)
   uint2* tc_fpack_lo = nullptr;    // BF16 remainders of F (split precision)
+  uint4* tc5_cst = nullptr;        // tcgen05 cell kernel: plane and z-sweep operators, BF16 (real, n_q = n_p)
+  uint4* tc5_cst16 = nullptr;      // the same in FP16
+  int* dev_status = nullptr;       // device word: 1 after a bounded wait in a cell kernel expired
   std::vector<void*> allocations;
   // host-buffer pipeline (fe_ks_apply_host): copy-in and copy-out streams and,
   // per workspace slot, events for "X copied in", "applied", "Y copied out"
@@ -218,6 +222,13 @@ cudaError_t launch_proj_pairs_emu(const Ctx& c, const ProjParams<double>& prm, c
 // BF16 tensor-core cell kernel (fe_ks_tc.cu) for one colour of cells
 cudaError_t launch_tc(const Ctx& c, const LocalParams<float>& lp, cudaStream_t s, int tc);
 size_t tc_smem_bytes(int n, bool cplx);
+// tcgen05 cell kernel (fe_ks_tc5.cu): real operators, n_q = n_p; f16 selects FP16 operands
+cudaError_t launch_tc5(const Ctx& c, const LocalParams<float>& lp, cudaStream_t s, bool f16);
+void build_tc5_const(int p, bool f16, std::vector<uint4>& out);
+// true when the tcgen05 kernel serves this context and precision (tc: 1 = BF16, 2 = FP16)
+inline bool use_tc5(const Ctx& c, int tc) {
+  return (tc == 1 || tc == 2) && c.cfg_tc[tc - 1] == 0 && !c.cplx && c.nq == c.np && c.tc5_cst && c.tc5_cst16;
+}
 
 }  // namespace feks
 

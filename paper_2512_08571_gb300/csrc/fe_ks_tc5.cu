@@ -1,0 +1,895 @@
+// Cell kernel on the 5th-generation tensor cores (tcgen05) for FE_KS_BF16 and
+// FE_KS_F16, real operators, n_q = n_p = N.
+//
+// Paper: Algorithm 2 (cell-level evaluation, eq. ggaReal) called from
+// Algorithm 1 (extraction Q C P X, expansion F Delta T3, assembly Q^T).  The
+// sum-factorised chain is regrouped into four dense contractions per cell and
+// tile of VT = 8 vectors, each a tcgen05.mma chain with FP32 accumulators in
+// tensor memory and 16-bit operands in shared memory:
+//   GEMM1 (plane, forward):   P_t[(v,c)][p'] = sum_p K_t[p][p'] X[(p,c)][v],
+//         K_0 = N (x) N, K_1 = D (x) N, K_2 = N (x) D  over the in-plane node
+//         index p = a + N b (the x and y sweeps of Algorithm 2 in one product;
+//         D = D~ N is the Gauss-point derivative of the nodal basis);
+//   GEMM2 (z sweep):  Y0 = N_z P_0, Y_x = N_z P_1, Y_y = N_z P_2, Y_z = D_z P_0;
+//   FP32 quadrature-point step in registers (eq. ggaReal: G = J^-1 J^-T det J w,
+//         V^L, V^G): Z = V^L Y0 + V^G.grad Y, W = G grad Y + V^G Y0;
+//   GEMM3 (transposed z sweep):  T_0 = N_z^T Z + D_z^T W_z, T_1 = N_z^T W_x,
+//         T_2 = N_z^T W_y;
+//   GEMM4 (plane, transposed):   Y^(e)[(p,c)][v] = sum_t sum_p' K_t[p][p'] T_t[(v,p')][c].
+// The plane products cost more multiplications than two 1D sweeps (81 x 81
+// against 2 x 9 x 81 per line pair) but the tensor cores have that to spare;
+// what they save is the relayouts between sweeps, which bound the warp-level
+// kernel.  Every relayout here is a thread-per-row tensor-memory read
+// (tcgen05.ld.32x32b, thread = accumulator row) followed by 16-byte shared
+// stores: each operand is laid out K-major or MN-major (canonical no-swizzle
+// core matrices of 8 rows x 16 bytes) so that the 8 values one thread holds
+// are 16 contiguous bytes of the next operand.
+//
+// Layouts (N = 9: NN = 81 in-plane nodes, 729 cell nodes, row r = t NN + p'):
+//   KM   plane operators, rows r (256), 16-byte row per 8 p: r*16 + (p%8)*2 +
+//        (p/8)*PGS; GEMM1 reads it K-major as A [(t,p')][p]; GEMM4 reads the same
+//        bytes MN-major as A [p][(t,p')] (its transpose).
+//   XS   the gathered X tile, B of GEMM1, MN-major [p][(v,c)]: p*16 + v*2 + c*XSB.
+//   AB   A of GEMM2 [(v,p')][(t,c)] and of GEMM3 [(v,p')][(q,c')] (K-major, row
+//        r2 = v + 8 p'), then B of GEMM4 [(t,p')][c + 16 v] (MN-major).
+//   B2, B3  the 1D operators of the z sweeps, K-major.
+// Tensor memory: GEMM1 tiles at columns 0 and 128, GEMM2/3 tiles at 64 T, GEMM4
+// at 0 (each read out before the next product overwrites it).
+//
+// One thread issues each product's MMAs and commits them to an mbarrier; every
+// wait is bounded (on expiry the CTA sets the error word, lets the MMAs in
+// flight drain with a last bounded wait, frees its tensor memory and returns).
+// The nonlocal expansion F Delta P (FP32, the pair's F block and Delta-scaled
+// projections Q) and the scatter run on the GEMM4 accumulators in registers;
+// colour-exclusive launches make the assembly reductions deterministic.
+// FP16: every column of a gathered tile is scaled by a power of two (its
+// largest entry below 1/16), undone before the expansion and scatter.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cstring>
+#include <type_traits>
+#include <vector>
+
+#include "fe_ks_internal.h"
+
+namespace feks {
+namespace tc5 {
+
+template <int N>
+struct G5 {
+  static constexpr int NN = N * N, N3 = N * NN, VT = 8, NT = 512, NW = NT / 32, NC = 10;
+  static constexpr int KP = (NN + 15) / 16 * 16;      // GEMM1 K: in-plane node p (padded)
+  static constexpr int R1 = 3 * NN;                    // rows (t, p') of the plane operators
+  static constexpr int MT1 = (R1 + 127) / 128;         // GEMM1 M tiles
+  static constexpr int R1P = MT1 * 128;
+  static constexpr int K4 = (R1 + 15) / 16 * 16;       // GEMM4 K
+  static constexpr int N1 = (VT * N + 15) / 16 * 16;   // GEMM1 N: v + 8 c (padded)
+  static constexpr int NCX = N1 / VT;                  // c slots of the X tile (with padding)
+  static constexpr int R2 = VT * NN;                   // GEMM2/3 rows v + 8 p' (the 8 vectors of a node adjacent)
+  static constexpr int MT2 = (R2 + 127) / 128;
+  static constexpr int N2 = (4 * N + 15) / 16 * 16;    // GEMM2 N: 4 c' + q
+  static constexpr int K2 = 48;                        // GEMM2 K: 16 t + c
+  static constexpr int K3 = N2;                        // GEMM3 K: 4 c' + q
+  static constexpr int N3C = 48;                       // GEMM3 N: 16 t + c
+  static constexpr int CH0 = 2 * ((N + 2) / 4);        // c' of the first half of a quadrature-point row
+  static constexpr int CSL = K3 / 4;                   // c' slots of a row (with padding)
+  static constexpr int NC3 = 3 * (N > 8 ? 2 : 1);      // 16-byte chunks of a GEMM4 operand row group
+  static constexpr int MAXC = (N + 3) / 4;             // z planes per warp group in the final step
+  static constexpr int PG = 16;                        // p groups of KM (GEMM4 M = 128)
+  static constexpr int PGS = R1P * 16;                 // byte stride of a p group in KM
+  static constexpr int OFF_KM = 0;
+  static constexpr int OFF_B2 = OFF_KM + PG * PGS;
+  static constexpr int OFF_B3 = OFF_B2 + N2 * K2 * 2;
+  static constexpr int SZ_CST = OFF_B3 + N3C * K3 * 2;   // constant block, copied verbatim
+  static constexpr int XSB = KP * 16;                  // c stride of the X tile
+  static constexpr int OFF_XS = SZ_CST;
+  static constexpr int SZ_XS = NCX * XSB;
+  static constexpr int SBO2 = 144;                     // 8-row group stride of the GEMM2/3 A operands (padded:
+                                                       // the 16-byte row stores of a warp spread over all banks)
+  static constexpr int LBO2 = MT2 * 16 * SBO2;         // k-chunk stride of the GEMM2/3 A operands
+  static constexpr int SBO4 = K4 * 16 + 16;            // n-group stride of the GEMM4 B operand (padded likewise)
+  static constexpr int SZ_AB0 = LBO2 * (K2 > K3 ? K2 : K3) / 8;
+  static constexpr int SZ_AB = SZ_AB0 > 16 * SBO4 ? SZ_AB0 : 16 * SBO4;
+  static constexpr int OFF_AB = OFF_XS + SZ_XS;
+  static constexpr int CFS = 12;                       // floats per point of the staged coefficients
+  static constexpr int OFF_CF = OFF_AB + SZ_AB;        // coefficients [point][CFS], FP32
+  static constexpr int OFF_SD = OFF_CF + CFS * N3 * 4;
+  static constexpr int OFF_RED = OFF_SD + (N3 * 4 + 15) / 16 * 16;   // FP16: [NW warps][8] column maxima, [8] scales
+  static constexpr int OFF_USC = OFF_RED + (NW + 1) * 8 * 4;         // FP16: [8] unscale factors
+  static constexpr int QCAP = 64;                      // staged (pair, projector) rows of Q per tile
+  static constexpr int PCAP = 16;                      // staged (pair, atom) entries of a cell
+  static constexpr int OFF_QS = OFF_USC + 8 * 4;       // [QCAP][8] Delta-scaled projections of the tile's columns
+  static constexpr int OFF_SP = OFF_QS + QCAP * 8 * 4; // [PCAP] pairs of the cell, [PCAP] their atoms
+  static constexpr int OFF_DS = OFF_SP + 2 * PCAP * 4; // [N3] D^{-1/2} of the cell's nodes
+  static constexpr int OFF_MBAR = OFF_DS + (N3 * 4 + 15) / 16 * 16;
+  static constexpr int OFF_TMEM = OFF_MBAR + 8;
+  static constexpr int BYTES = OFF_TMEM + 8;
+  static constexpr uint32_t TM_D1 = 0, TM_D1S = 128, TM_D23 = 0, TM_D23S = 64, TM_D4 = 0;
+  static_assert(N >= 2 && N <= 9, "N");
+  static_assert(NN <= 128 && MT1 <= 2 && N1 <= 128 && N2 <= 64 && MT2 * 64 <= 512, "tile shapes");
+  static_assert(SZ_CST % 16 == 0 && OFF_AB % 16 == 0 && OFF_CF % 16 == 0 && OFF_MBAR % 8 == 0, "alignment");
+  static_assert(BYTES <= 232448, "shared memory");
+};
+
+constexpr long long kWaitIters = 1LL << 22;   // bound of an mbarrier wait (try_wait polls)
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;   // descriptor version of the 5th-generation tensor core; no swizzle
+  return d;
+}
+
+// kind::f16 instruction descriptor: FP32 accumulator; A and B BF16 (or FP16);
+// a_mn / b_mn: operand MN-major (else K-major); M = 128.
+template <bool F16>
+__host__ __device__ constexpr uint32_t idesc(int n, int a_mn, int b_mn) {
+  return (1u << 4) | (F16 ? 0u : (1u << 7) | (1u << 10)) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
+         ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(uint32_t dt, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dt),
+      "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+
+__device__ __forceinline__ void commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
+               : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's tensor-memory lane
+__device__ __forceinline__ void ld16(uint32_t ta, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(ta));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// bounded wait for phase `parity` of the mbarrier; false on expiry
+__device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity) {
+  uint32_t done = 0;
+  for (long long it = 0; it < kWaitIters && !done; ++it) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(mb), "r"(parity)
+        : "memory");
+  }
+  return done != 0;
+}
+
+// two FP32 values in one 64-bit register, and the packed FMA acc += a * b (each half
+// rounded as fmaf)
+__device__ __forceinline__ uint64_t pk2(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 up2(uint64_t x) {
+  float lo, hi;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(x));
+  return make_float2(lo, hi);
+}
+__device__ __forceinline__ void fma2(uint64_t& acc, uint64_t a, uint64_t b) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
+}
+
+template <bool F16>
+__device__ __forceinline__ uint32_t pack(float lo, float hi) {
+  if constexpr (F16) {
+    __half2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&h);
+  } else {
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
+}
+
+__device__ __forceinline__ void st16(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};\n" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+
+// power of two s with s * mx < 1/16 (1 for a zero or non-finite maximum)
+__device__ __forceinline__ float col_scale(float mx) {
+  if (!(mx > 0.f) || !(mx < 3.0e38f)) return 1.f;
+  int e = (int)((__float_as_uint(mx) >> 23) & 0xFFu);
+  e = e < 1 ? 1 : (e > 248 ? 248 : e);
+  return __uint_as_float((uint32_t)(249 - e) << 23);
+}
+
+struct Params {
+  const float* X;
+  float* Y;
+  int64_t ld;
+  int ncols;
+  const int* cell_dofs;
+  const int* cells;
+  int n_cells;
+  const float* coef;     // [E][ncoef][N^3]
+  int ncoef;
+  int gga;
+  const float* dscale;   // D^{-1/2} or nullptr
+  const int* cell_pair_ptr;
+  const int* cell_pairs;
+  const int* pair_atom;
+  const float* F;        // [pair][n_proj][N^3]
+  const float* Q;        // [atom][n_proj][ld], scaled by Delta
+  int n_proj;
+  float alpha;
+  const uint4* cst;      // the constant block (KM, B2, B3) in shared-memory layout
+  int units_per_cell;    // a cell's column tiles are split into this many work units
+  int tiles_per_unit;
+  int* err;              // set to 1 when a bounded wait expires
+};
+
+template <int N, bool F16>
+__global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ Params p) {
+  using G = G5<N>;
+  constexpr int NT = G::NT, NN = G::NN, N3 = G::N3;
+  constexpr int GPT = (N3 + NT - 1) / NT;   // gathered nodes per thread
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int quarter = warp & 3, grp = warp >> 2;   // tensor-memory lane quarter; warp group 0..3
+  const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(smem);
+  const uint32_t sXS = s0 + G::OFF_XS, sAB = s0 + G::OFF_AB;
+  const uint32_t mbar = s0 + G::OFF_MBAR;
+  float* cf = reinterpret_cast<float*>(smem + G::OFF_CF);
+  int* sd = reinterpret_cast<int*>(smem + G::OFF_SD);
+  float* red = reinterpret_cast<float*>(smem + G::OFF_RED);
+  float* usc = reinterpret_cast<float*>(smem + G::OFF_USC);
+  float* qs = reinterpret_cast<float*>(smem + G::OFF_QS);
+  int* spr = reinterpret_cast<int*>(smem + G::OFF_SP);
+  int* spa = spr + G::PCAP;
+  float* sds = reinterpret_cast<float*>(smem + G::OFF_DS);
+
+  // (0) constants; the X tile and AB start zeroed (their padding is read by
+  //     the tensor cores, multiplied by zero operator entries, and must be finite)
+  for (int i = tid; i < G::SZ_CST / 16; i += NT) reinterpret_cast<uint4*>(smem)[i] = __ldg(p.cst + i);
+  for (int i = tid; i < (G::SZ_XS + G::SZ_AB) / 16; i += NT)
+    reinterpret_cast<uint4*>(smem + G::OFF_XS)[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (tid < 8) usc[tid] = 1.f;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;\n" ::"r"(s0 + G::OFF_TMEM));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *reinterpret_cast<const uint32_t*>(smem + G::OFF_TMEM);
+  const uint32_t tlane = tmem + ((uint32_t)(32 * quarter) << 16);   // this warp's lane quarter
+
+  constexpr uint32_t ID1 = idesc<F16>(G::N1, 0, 1), ID2 = idesc<F16>(G::N2, 0, 0);
+  constexpr uint32_t ID3 = idesc<F16>(G::N3C, 0, 0), ID4 = idesc<F16>(128, 1, 1);
+  // descriptors of the operands' first core matrices (later ones: + byte offset / 16)
+  const uint64_t dKM1 = sdesc(s0 + G::OFF_KM, G::PGS, 128), dXS = sdesc(sXS, 128, G::XSB);
+  const uint64_t dA2 = sdesc(sAB, G::LBO2, G::SBO2), dB2 = sdesc(s0 + G::OFF_B2, G::N2 * 16, 128);
+  const uint64_t dB3 = sdesc(s0 + G::OFF_B3, G::N3C * 16, 128);
+  const uint64_t dKM4 = sdesc(s0 + G::OFF_KM, 128, G::PGS), dB4 = sdesc(sAB, 128, G::SBO4);
+
+  const int ntiles = (p.ncols + 7) / 8;
+  const bool vec = (p.ld % 4 == 0) && (((uintptr_t)p.X & 15) == 0) && (((uintptr_t)p.Q & 15) == 0);
+  const bool vecy = (p.ld % 4 == 0) && (((uintptr_t)p.Y & 15) == 0);
+  const int units = p.n_cells * p.units_per_cell;
+  // this warp group's z planes in the final step
+  const int ccnt = N / 4 + (grp < N % 4 ? 1 : 0), cbeg = grp * (N / 4) + (grp < N % 4 ? grp : N % 4);
+  uint32_t phase = 0, failed_phase = 0;
+  bool failed = false;
+  int staged = -1;
+
+  // all threads: bounded wait for the products just committed; uniform result
+  auto wait_products = [&]() -> bool {
+    const bool ok = mbar_wait(mbar, phase);
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      failed_phase = phase;
+      return false;
+    }
+    phase ^= 1u;
+    fence_after();
+    return true;
+  };
+  // this thread's gathered nodes of column tile [cx, cx + 8) and their D^{-1/2}
+  // (registers; nothing waits on the loads until the tile's gather)
+  float xn[GPT][8], xs[GPT];
+  auto load_x = [&](int cx) {
+    const bool fullx = vec && cx + 8 <= p.ncols;
+#pragma unroll
+    for (int r = 0; r < GPT; ++r) {
+      const int node = tid + r * NT;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) xn[r][c] = 0.f;
+      xs[r] = 1.f;
+      if (node < N3) {
+        const int d = sd[node];
+        const float* xr = p.X + (int64_t)d * p.ld + cx;
+        if (fullx) {
+          const float4 a = __ldg(reinterpret_cast<const float4*>(xr));
+          const float4 b = __ldg(reinterpret_cast<const float4*>(xr) + 1);
+          xn[r][0] = a.x, xn[r][1] = a.y, xn[r][2] = a.z, xn[r][3] = a.w;
+          xn[r][4] = b.x, xn[r][5] = b.y, xn[r][6] = b.z, xn[r][7] = b.w;
+        } else {
+#pragma unroll
+          for (int c = 0; c < 8; ++c) xn[r][c] = cx + c < p.ncols ? __ldg(xr + c) : 0.f;
+        }
+        xs[r] = sds[node];
+      }
+    }
+  };
+
+  for (int u = blockIdx.x; u < units && !failed; u += gridDim.x) {
+    const int ci = u / p.units_per_cell;
+    const int t_begin = (u % p.units_per_cell) * p.tiles_per_unit;
+    const int t_end = min(ntiles, t_begin + p.tiles_per_unit);
+    if (t_begin >= t_end) continue;
+    const int e = p.cells[ci];
+    if (ci != staged) {
+      __syncthreads();   // the previous cell's scatter has finished with sd and cf
+      for (int w = tid; w < N3; w += NT) {
+        const int d = p.cell_dofs[(int64_t)e * N3 + w];
+        sd[w] = d;
+        sds[w] = p.dscale ? __ldg(p.dscale + d) : 1.f;
+      }
+      if (p.cell_pair_ptr) {
+        const int b0 = p.cell_pair_ptr[e], n = min(p.cell_pair_ptr[e + 1] - b0, G::PCAP);
+        if (tid < n) {
+          const int pr = p.cell_pairs[b0 + tid];
+          spr[tid] = pr;
+          spa[tid] = p.pair_atom[pr];
+        }
+      }
+      const float* gc = p.coef + (int64_t)e * p.ncoef * N3;
+      for (int w = tid; w < G::NC * N3; w += NT) {
+        const int slot = w / N3, q = w - slot * N3;
+        cf[q * G::CFS + slot] = __ldg(gc + w);
+      }
+      staged = ci;
+      __syncthreads();
+    }
+    const int pb = p.cell_pair_ptr ? p.cell_pair_ptr[e] : 0;
+    const int pe = p.cell_pair_ptr ? p.cell_pair_ptr[e + 1] : 0;
+    bool have_next = false;   // xn already holds this tile's rows (loaded during the previous tile)
+
+    for (int t = t_begin; t < t_end; ++t) {
+      const int col0 = 8 * t;
+      // (1) extraction Q C P X (Algorithm 1): rows of X -> the MN-major X tile
+      if (!have_next) load_x(col0);
+#pragma unroll
+      for (int r = 0; r < GPT; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) xn[r][c] *= xs[r];
+      if constexpr (F16) {
+        float cm[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          float m = 0.f;
+#pragma unroll
+          for (int r = 0; r < GPT; ++r) m = fmaxf(m, fabsf(xn[r][c]));
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+          cm[c] = m;
+        }
+        if (lane < 8) {
+          float v = cm[0];
+#pragma unroll
+          for (int c = 1; c < 8; ++c) v = lane == c ? cm[c] : v;
+          red[warp * 8 + lane] = v;
+        }
+        __syncthreads();
+        if (tid < 8) {
+          float m = 0.f;
+#pragma unroll
+          for (int w = 0; w < G::NW; ++w) m = fmaxf(m, red[w * 8 + tid]);
+          const float s = col_scale(m);
+          red[G::NW * 8 + tid] = s;
+          usc[tid] = 1.f / s;   // exact: a power of two
+        }
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const float s = red[G::NW * 8 + c];
+#pragma unroll
+          for (int r = 0; r < GPT; ++r) xn[r][c] *= s;
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < GPT; ++r) {
+        const int node = tid + r * NT;
+        if (node < N3)
+          st16(sXS + (node % NN) * 16 + (node / NN) * G::XSB, pack<F16>(xn[r][0], xn[r][1]),
+               pack<F16>(xn[r][2], xn[r][3]), pack<F16>(xn[r][4], xn[r][5]), pack<F16>(xn[r][6], xn[r][7]));
+      }
+      // the tile's rows of Q (one half row per thread), stored to shared memory once GEMM1 has run
+      const int nqrows = (pe - pb) * p.n_proj;
+      const bool qstaged = nqrows <= G::QCAP && pe - pb <= G::PCAP;
+      float4 qreg = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (qstaged && tid < 2 * nqrows) {
+        const int row = tid >> 1, b = row % p.n_proj, c4 = col0 + 4 * (tid & 1);
+        const int a = spa[row / p.n_proj];
+        const float* qr = p.Q + ((int64_t)a * p.n_proj + b) * p.ld + c4;
+        if (vec && c4 + 4 <= p.ncols) {
+          qreg = __ldg(reinterpret_cast<const float4*>(qr));
+        } else {
+          if (c4 < p.ncols) qreg.x = __ldg(qr);
+          if (c4 + 1 < p.ncols) qreg.y = __ldg(qr + 1);
+          if (c4 + 2 < p.ncols) qreg.z = __ldg(qr + 2);
+          if (c4 + 3 < p.ncols) qreg.w = __ldg(qr + 3);
+        }
+      }
+      fence_async_smem();
+      fence_before();
+      __syncthreads();
+      // (2) GEMM1: P_t = K_t^T X per plane
+      if (tid == 0) {
+        fence_after();
+#pragma unroll
+        for (int T = 0; T < G::MT1; ++T)
+#pragma unroll
+          for (int ks = 0; ks < G::KP / 16; ++ks)
+            mma(tmem + G::TM_D1 + T * G::TM_D1S, dKM1 + (uint64_t)((T * 2048 + ks * 2 * G::PGS) >> 4),
+                dXS + (uint64_t)((ks * 256) >> 4), ID1, ks > 0);
+        commit(mbar);
+      }
+      if (!wait_products()) break;
+      if (qstaged && tid < 2 * nqrows) reinterpret_cast<float4*>(qs)[tid] = qreg;
+      // (3) GEMM1 rows (t, p') -> A2 rows (v, p'), k = 16 t + c; items (tile, half of v)
+#pragma unroll 1
+      for (int it = grp; it < 2 * G::MT1; it += 4) {
+        const int T = it % G::MT1, vh = it / G::MT1;
+        const int r1 = 128 * T + 32 * quarter + lane;
+        const int tt = r1 / NN, pp = r1 - tt * NN;
+        constexpr int NLO = N < 8 ? N : 8;               // planes c of the first chunk
+        constexpr int LD0 = (8 * NLO + 15) / 16;        // 16-column loads covering them
+        float a[16 * LD0];
+#pragma unroll
+        for (int j = 0; j < LD0; ++j) ld16(tlane + G::TM_D1 + T * G::TM_D1S + 16 * j, a + 16 * j);
+        ld_wait();
+        if (r1 < G::R1) {
+#pragma unroll
+          for (int vv = 0; vv < 4; ++vv) {
+            const int v = 4 * vh + vv;
+            float c8[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) c8[c] = c < NLO ? (vh ? a[4 + vv + 8 * c] : a[vv + 8 * c]) : 0.f;
+            st16(sAB + v * 16 + pp * G::SBO2 + (2 * tt) * G::LBO2, pack<F16>(c8[0], c8[1]), pack<F16>(c8[2], c8[3]),
+                 pack<F16>(c8[4], c8[5]), pack<F16>(c8[6], c8[7]));
+          }
+        }
+        if constexpr (N > 8) {   // plane c = 8: columns 64..71
+          float b[16];
+          ld16(tlane + G::TM_D1 + T * G::TM_D1S + 64, b);
+          ld_wait();
+          if (r1 < G::R1) {
+#pragma unroll
+            for (int vv = 0; vv < 4; ++vv) {
+              const int v = 4 * vh + vv;
+              st16(sAB + v * 16 + pp * G::SBO2 + (2 * tt + 1) * G::LBO2, pack<F16>(vh ? b[4 + vv] : b[vv], 0.f), 0u,
+                   0u, 0u);
+            }
+          }
+        }
+      }
+      fence_async_smem();
+      fence_before();
+      __syncthreads();
+      // (4) GEMM2: the z sweep
+      if (tid == 0) {
+        fence_after();
+#pragma unroll
+        for (int T = 0; T < G::MT2; ++T)
+#pragma unroll
+          for (int ks = 0; ks < G::K2 / 16; ++ks)
+            mma(tmem + G::TM_D23 + T * G::TM_D23S, dA2 + (uint64_t)((T * 16 * G::SBO2 + ks * 2 * G::LBO2) >> 4),
+                dB2 + (uint64_t)((ks * 2 * G::N2 * 16) >> 4), ID2, ks > 0);
+        commit(mbar);
+      }
+      if (!wait_products()) break;
+      // (5) quadrature-point step: (Y0, Y_x, Y_y, Y_z)[c'] -> (Z, W_x, W_y, W_z)[c'] (A3, k = 4 c' + q);
+      //     items (tile, half of the c' range)
+      auto pointwise = [&](int T, auto H) {
+        constexpr int LO = decltype(H)::value ? G::CH0 : 0, HI = decltype(H)::value ? G::CSL : G::CH0;
+        float y[48];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) ld16(tlane + G::TM_D23 + T * G::TM_D23S + 16 * j, y + 16 * j);
+        ld_wait();
+        const int r2 = 128 * T + 32 * quarter + lane;
+        if (r2 < G::R2) {
+          const int pp = r2 >> 3;
+          float o[4 * (HI - LO) + 1];
+#pragma unroll
+          for (int c = LO; c < HI; ++c) {
+            float z = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f;
+            if (c < N) {
+              const float* cp = cf + (pp + NN * c) * G::CFS;   // the 8 vectors of a node share the address
+              const float4 ca = *reinterpret_cast<const float4*>(cp);
+              const float4 cb = *reinterpret_cast<const float4*>(cp + 4);
+              const float G00 = ca.x, G01 = ca.y, G02 = ca.z, G11 = ca.w, G12 = cb.x, G22 = cb.y, VL = cb.z;
+              const float u = y[4 * c], gx = y[4 * c + 1], gy = y[4 * c + 2], gz = y[4 * c + 3];
+              z = VL * u;
+              w0 = fmaf(G00, gx, fmaf(G01, gy, G02 * gz));
+              w1 = fmaf(G01, gx, fmaf(G11, gy, G12 * gz));
+              w2 = fmaf(G02, gx, fmaf(G12, gy, G22 * gz));
+              if (p.gga) {
+                const float2 cc = *reinterpret_cast<const float2*>(cp + 8);
+                const float V0 = cb.w, V1 = cc.x, V2 = cc.y;
+                z = fmaf(V0, gx, fmaf(V1, gy, fmaf(V2, gz, z)));
+                w0 = fmaf(V0, u, w0);
+                w1 = fmaf(V1, u, w1);
+                w2 = fmaf(V2, u, w2);
+              }
+            }
+            o[4 * (c - LO)] = z;
+            o[4 * (c - LO) + 1] = w0;
+            o[4 * (c - LO) + 2] = w1;
+            o[4 * (c - LO) + 3] = w2;
+          }
+          const uint32_t row = sAB + (r2 & 7) * 16 + pp * G::SBO2;
+#pragma unroll
+          for (int kc = 0; kc < (HI - LO) / 2; ++kc)
+            st16(row + (LO / 2 + kc) * G::LBO2, pack<F16>(o[8 * kc], o[8 * kc + 1]),
+                 pack<F16>(o[8 * kc + 2], o[8 * kc + 3]), pack<F16>(o[8 * kc + 4], o[8 * kc + 5]),
+                 pack<F16>(o[8 * kc + 6], o[8 * kc + 7]));
+        }
+      };
+#pragma unroll 1
+      for (int it = grp; it < 2 * G::MT2; it += 4) {
+        if (it & 1)
+          pointwise(it >> 1, std::integral_constant<int, 1>{});
+        else
+          pointwise(it >> 1, std::integral_constant<int, 0>{});
+      }
+      // the next column tile's rows of X, in flight during the rest of this tile
+      have_next = t + 1 < t_end;
+      if (have_next) load_x(col0 + 8);
+      fence_async_smem();
+      fence_before();
+      __syncthreads();
+      // (6) GEMM3: the transposed z sweep
+      if (tid == 0) {
+        fence_after();
+#pragma unroll
+        for (int T = 0; T < G::MT2; ++T)
+#pragma unroll
+          for (int ks = 0; ks < G::K3 / 16; ++ks)
+            mma(tmem + G::TM_D23 + T * G::TM_D23S, dA2 + (uint64_t)((T * 16 * G::SBO2 + ks * 2 * G::LBO2) >> 4),
+                dB3 + (uint64_t)((ks * 2 * G::N3C * 16) >> 4), ID3, ks > 0);
+        commit(mbar);
+      }
+      if (!wait_products()) break;
+      // (7) GEMM3 rows (v, p'), columns 16 t + c -> B4 [(t, p')][c + 16 v] (MN-major);
+      //     items (tile, half of the chunks)
+#pragma unroll 1
+      for (int it = grp; it < 2 * G::MT2; it += 4) {
+        const int T = it >> 1, h = it & 1;
+        float d3[48];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) ld16(tlane + G::TM_D23 + T * G::TM_D23S + 16 * j, d3 + 16 * j);
+        ld_wait();
+        const int r2 = 128 * T + 32 * quarter + lane;
+        if (r2 < G::R2) {
+          const int v = r2 & 7, pp = r2 >> 3;
+          constexpr int HCN = N > 8 ? 2 : 1;
+#pragma unroll
+          for (int ch = 0; ch < G::NC3; ++ch) {
+            if ((ch < G::NC3 / 2) == (h == 0)) {
+              const int tt = ch / HCN, hc = ch % HCN;
+              const float* sv = d3 + 16 * tt + 8 * hc;
+              st16(sAB + (tt * NN + pp) * 16 + (hc + 2 * v) * G::SBO4, pack<F16>(sv[0], sv[1]),
+                   pack<F16>(sv[2], sv[3]), pack<F16>(sv[4], sv[5]), pack<F16>(sv[6], sv[7]));
+            }
+          }
+        }
+      }
+      fence_async_smem();
+      fence_before();
+      __syncthreads();
+      // (8) GEMM4: the transposed plane product
+      if (tid == 0) {
+        fence_after();
+#pragma unroll
+        for (int ks = 0; ks < G::K4 / 16; ++ks)
+          mma(tmem + G::TM_D4, dKM4 + (uint64_t)((ks * 256) >> 4), dB4 + (uint64_t)((ks * 256) >> 4), ID4, ks > 0);
+        commit(mbar);
+      }
+      // (9) F Delta P (nonlocal expansion) for this thread's node column, computed
+      //     while GEMM4 runs; then Y += alpha D^{-1/2} Q^T (Y^(e) + F Delta P)
+      const int pp = 32 * quarter + lane;   // in-plane node of this lane
+      float ex[G::MAXC][8];
+#pragma unroll
+      for (int j = 0; j < G::MAXC; ++j)
+#pragma unroll
+        for (int v = 0; v < 8; ++v) ex[j][v] = 0.f;
+      if (pp < NN && pb < pe && qstaged) {
+        // every F load of a pair issued before the arithmetic; Q from shared memory (broadcast)
+        constexpr int BCH = 9;
+        for (int pi = pb; pi < pe; ++pi) {
+          const int pr = spr[pi - pb];
+          const float* Fp = p.F + (int64_t)pr * p.n_proj * N3 + pp + NN * cbeg;
+          const float* qp = qs + (pi - pb) * p.n_proj * 8;
+#pragma unroll 1
+          for (int b0 = 0; b0 < p.n_proj; b0 += BCH) {
+            float f[BCH][G::MAXC];
+#pragma unroll
+            for (int bb = 0; bb < BCH; ++bb)
+#pragma unroll
+              for (int j = 0; j < G::MAXC; ++j)
+                f[bb][j] = b0 + bb < p.n_proj && j < ccnt ? __ldg(Fp + (int64_t)(b0 + bb) * N3 + NN * j) : 0.f;
+            uint64_t ex2[G::MAXC][4];   // packed accumulators, vectors (2 w, 2 w + 1)
+#pragma unroll
+            for (int j = 0; j < G::MAXC; ++j)
+#pragma unroll
+              for (int w = 0; w < 4; ++w) ex2[j][w] = pk2(ex[j][2 * w], ex[j][2 * w + 1]);
+#pragma unroll
+            for (int bb = 0; bb < BCH; ++bb) {
+              if (b0 + bb >= p.n_proj) break;
+              const float4 q0 = *reinterpret_cast<const float4*>(qp + (b0 + bb) * 8);
+              const float4 q1 = *reinterpret_cast<const float4*>(qp + (b0 + bb) * 8 + 4);
+              const uint64_t q2[4] = {pk2(q0.x, q0.y), pk2(q0.z, q0.w), pk2(q1.x, q1.y), pk2(q1.z, q1.w)};
+#pragma unroll
+              for (int j = 0; j < G::MAXC; ++j) {
+                const uint64_t ff = pk2(f[bb][j], f[bb][j]);
+#pragma unroll
+                for (int w = 0; w < 4; ++w) fma2(ex2[j][w], ff, q2[w]);
+              }
+            }
+#pragma unroll
+            for (int j = 0; j < G::MAXC; ++j)
+#pragma unroll
+              for (int w = 0; w < 4; ++w) {
+                const float2 e2 = up2(ex2[j][w]);
+                ex[j][2 * w] = e2.x;
+                ex[j][2 * w + 1] = e2.y;
+              }
+          }
+        }
+      } else if (pp < NN && pb < pe) {
+        const bool fq = vec && col0 + 8 <= p.ncols;
+        for (int pi = pb; pi < pe; ++pi) {
+          const int pr = p.cell_pairs[pi];
+          const float* Fp = p.F + (int64_t)pr * p.n_proj * N3 + pp + NN * cbeg;
+          const float* Qa = p.Q + (int64_t)p.pair_atom[pr] * p.n_proj * p.ld + col0;
+#pragma unroll 1
+          for (int b0 = 0; b0 < p.n_proj; b0 += 4) {
+            float q[4][8], f[4][G::MAXC];
+#pragma unroll
+            for (int bb = 0; bb < 4; ++bb) {
+              const int b = b0 + bb;
+              const bool okb = b < p.n_proj;
+              const float* qr = Qa + (int64_t)(okb ? b : 0) * p.ld;
+              if (fq) {
+                const float4 q0 = okb ? __ldg(reinterpret_cast<const float4*>(qr)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 q1 = okb ? __ldg(reinterpret_cast<const float4*>(qr) + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+                q[bb][0] = q0.x, q[bb][1] = q0.y, q[bb][2] = q0.z, q[bb][3] = q0.w;
+                q[bb][4] = q1.x, q[bb][5] = q1.y, q[bb][6] = q1.z, q[bb][7] = q1.w;
+              } else {
+#pragma unroll
+                for (int v = 0; v < 8; ++v) q[bb][v] = okb && col0 + v < p.ncols ? __ldg(qr + v) : 0.f;
+              }
+#pragma unroll
+              for (int j = 0; j < G::MAXC; ++j)
+                f[bb][j] = okb && j < ccnt ? __ldg(Fp + (int64_t)b * N3 + NN * j) : 0.f;
+            }
+#pragma unroll
+            for (int bb = 0; bb < 4; ++bb)
+#pragma unroll
+              for (int j = 0; j < G::MAXC; ++j)
+#pragma unroll
+                for (int v = 0; v < 8; ++v) ex[j][v] = fmaf(f[bb][j], q[bb][v], ex[j][v]);
+          }
+        }
+      }
+      if (!wait_products()) break;
+      {
+        float o[G::MAXC][8];
+#pragma unroll
+        for (int j = 0; j < G::MAXC; ++j)
+#pragma unroll
+          for (int v = 0; v < 8; ++v) {
+            uint32_t r;
+            const int c = cbeg + (j < ccnt ? j : 0);
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];\n"
+                         : "=r"(r)
+                         : "r"(tlane + G::TM_D4 + (uint32_t)(c + 16 * v)));
+            o[j][v] = __uint_as_float(r);
+          }
+        ld_wait();
+        fence_before();
+        if (pp < NN) {
+#pragma unroll
+          for (int j = 0; j < G::MAXC; ++j) {
+            if (j >= ccnt) break;
+            const int c = cbeg + j;
+            const int d = sd[pp + NN * c];
+            const float s = p.alpha * sds[pp + NN * c];
+            float w[8];
+#pragma unroll
+            for (int v = 0; v < 8; ++v) w[v] = s * fmaf(o[j][v], usc[v], ex[j][v]);
+            float* yp = p.Y + (int64_t)d * p.ld + col0;
+            if (vecy && col0 + 8 <= p.ncols) {
+              atomicAdd(reinterpret_cast<float4*>(yp), make_float4(w[0], w[1], w[2], w[3]));
+              atomicAdd(reinterpret_cast<float4*>(yp) + 1, make_float4(w[4], w[5], w[6], w[7]));
+            } else {
+#pragma unroll
+              for (int v = 0; v < 8; ++v)
+                if (col0 + v < p.ncols) atomicAdd(yp + v, w[v]);
+            }
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (failed && tid == 0) {
+    atomicExch(p.err, 1);
+    (void)mbar_wait(mbar, failed_phase);   // a last bounded chance for MMAs in flight to drain
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(tmem));
+}
+
+// The constant block of one degree: the plane operators KM and the z-sweep
+// operators B2, B3, as 16-bit values in their shared-memory layout (host).
+template <int N>
+void build_const(const double (*Nm)[kMaxN], const double (*Dm)[kMaxN], bool f16, std::vector<uint4>& out) {
+  using G = G5<N>;
+  std::vector<uint16_t> h(G::SZ_CST / 2, 0);
+  auto put = [&](int byte_off, double x) { h[byte_off / 2] = f16 ? f16_bits(x) : bf16_bits(x); };
+  for (int r = 0; r < G::R1; ++r) {
+    const int t = r / G::NN, pq = r % G::NN, aq = pq % N, bq = pq / N;
+    for (int pn = 0; pn < G::NN; ++pn) {
+      const int an = pn % N, bn = pn / N;
+      const double v = t == 0 ? Nm[aq][an] * Nm[bq][bn] : t == 1 ? Dm[aq][an] * Nm[bq][bn] : Nm[aq][an] * Dm[bq][bn];
+      put(G::OFF_KM + r * 16 + (pn % 8) * 2 + (pn / 8) * G::PGS, v);
+    }
+  }
+  // B2 [n = 4 c' + q][k = 16 t + c]: Y0 = N P_0, Y_x = N P_1, Y_y = N P_2, Y_z = D P_0
+  for (int q = 0; q < 4; ++q)
+    for (int cq = 0; cq < N; ++cq)
+      for (int cn = 0; cn < N; ++cn) {
+        const int n = 4 * cq + q, t = q == 3 ? 0 : q, k = 16 * t + cn;
+        put(G::OFF_B2 + n * 16 + (k % 8) * 2 + (k / 8) * (G::N2 * 16), q == 3 ? Dm[cq][cn] : Nm[cq][cn]);
+      }
+  // B3 [n = 16 t + c][k = 4 c' + q]: T_0 = N^T Z + D^T W_z, T_1 = N^T W_x, T_2 = N^T W_y
+  for (int q = 0; q < 4; ++q)
+    for (int cq = 0; cq < N; ++cq)
+      for (int cn = 0; cn < N; ++cn) {
+        const int t = q == 3 ? 0 : q, n = 16 * t + cn, k = 4 * cq + q;
+        put(G::OFF_B3 + n * 16 + (k % 8) * 2 + (k / 8) * (G::N3C * 16), q == 3 ? Dm[cq][cn] : Nm[cq][cn]);
+      }
+  out.resize(G::SZ_CST / 16);
+  std::memcpy(out.data(), h.data(), G::SZ_CST);
+}
+
+template <int N, bool F16>
+cudaError_t launch_n(Params p, cudaStream_t s) {
+  using G = G5<N>;
+  if (p.n_cells == 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms <= 0) sms = 152;
+  cudaError_t err = cudaFuncSetAttribute(fe_tc5_kernel<N, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::BYTES);
+  if (err != cudaSuccess) return err;
+  const int ntiles = (p.ncols + 7) / 8;
+  // split a cell's column tiles into units so that every SM gets about 16 or more
+  int upc = 1;
+  while (upc < ntiles && (int64_t)p.n_cells * upc < 16LL * sms) upc *= 2;
+  if (upc > ntiles) upc = ntiles;
+  p.tiles_per_unit = (ntiles + upc - 1) / upc;
+  p.units_per_cell = (ntiles + p.tiles_per_unit - 1) / p.tiles_per_unit;
+  const int64_t units = (int64_t)p.n_cells * p.units_per_cell;
+  const int grid = (int)std::min<int64_t>(units, sms);
+  fe_tc5_kernel<N, F16><<<grid, G::NT, G::BYTES, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace tc5
+
+size_t tc5_const_words(int n) {
+  switch (n) {
+#define FEKS_TC5_CASE(NN) \
+  case NN: return tc5::G5<NN>::SZ_CST / 16;
+    FEKS_TC5_CASE(2)
+    FEKS_TC5_CASE(3)
+    FEKS_TC5_CASE(4)
+    FEKS_TC5_CASE(5)
+    FEKS_TC5_CASE(6)
+    FEKS_TC5_CASE(7)
+    FEKS_TC5_CASE(8)
+    FEKS_TC5_CASE(9)
+#undef FEKS_TC5_CASE
+    default: return 0;
+  }
+}
+
+void build_tc5_const(int p, bool f16, std::vector<uint4>& out) {
+  const int n = p + 1;
+  double xg[kMaxN], wg[kMaxN], xq[kMaxN], wq[kMaxN], val[kMaxN], der[kMaxN];
+  gauss_lobatto(n, xg, wg);
+  gauss_legendre(n, xq, wq);
+  double Nm[kMaxN][kMaxN] = {}, Dm[kMaxN][kMaxN] = {};   // [Gauss point][node]
+  for (int q = 0; q < n; ++q) {
+    lagrange_eval(n, xg, xq[q], val, der);
+    for (int i = 0; i < n; ++i) {
+      Nm[q][i] = val[i];
+      Dm[q][i] = der[i];
+    }
+  }
+  switch (n) {
+#define FEKS_TC5_BUILD(NN) \
+  case NN: tc5::build_const<NN>(Nm, Dm, f16, out); return;
+    FEKS_TC5_BUILD(2)
+    FEKS_TC5_BUILD(3)
+    FEKS_TC5_BUILD(4)
+    FEKS_TC5_BUILD(5)
+    FEKS_TC5_BUILD(6)
+    FEKS_TC5_BUILD(7)
+    FEKS_TC5_BUILD(8)
+    FEKS_TC5_BUILD(9)
+#undef FEKS_TC5_BUILD
+    default: out.clear();
+  }
+}
+
+cudaError_t launch_tc5(const Ctx& c, const LocalParams<float>& lp, cudaStream_t s, bool f16) {
+  tc5::Params p{};
+  p.X = lp.X;
+  p.Y = lp.Y;
+  p.ld = lp.ld;
+  p.ncols = lp.ncols;
+  p.cell_dofs = lp.cell_dofs;
+  p.cells = lp.cells;
+  p.n_cells = lp.n_cells;
+  p.coef = lp.coef;
+  p.ncoef = lp.ncoef;
+  p.gga = lp.gga;
+  p.dscale = lp.dscale;
+  p.cell_pair_ptr = lp.cell_pair_ptr;
+  p.cell_pairs = lp.cell_pairs;
+  p.pair_atom = lp.pair_atom;
+  p.F = lp.F;
+  p.Q = lp.Q;
+  p.n_proj = lp.n_proj;
+  p.alpha = lp.alpha;
+  p.cst = f16 ? c.tc5_cst16 : c.tc5_cst;
+  p.err = c.dev_status;
+  if (!p.cst || !p.err || c.cplx || c.nq != c.np) return cudaErrorInvalidValue;
+  switch (c.np) {
+#define FEKS_TC5_LAUNCH(NN) \
+  case NN: return f16 ? tc5::launch_n<NN, true>(p, s) : tc5::launch_n<NN, false>(p, s);
+    FEKS_TC5_LAUNCH(2)
+    FEKS_TC5_LAUNCH(3)
+    FEKS_TC5_LAUNCH(4)
+    FEKS_TC5_LAUNCH(5)
+    FEKS_TC5_LAUNCH(6)
+    FEKS_TC5_LAUNCH(7)
+    FEKS_TC5_LAUNCH(8)
+    FEKS_TC5_LAUNCH(9)
+#undef FEKS_TC5_LAUNCH
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace feks

@@ -72,6 +72,7 @@ def _load():
     lib.fe_ks_tune.argtypes = [vp, vp, vp, i64, ctypes.c_int, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_int)]
     lib.fe_ks_set_config.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     lib.fe_ks_get_config.argtypes = [vp, ctypes.c_int, P(ctypes.c_int)]
+    lib.fe_ks_device_status.argtypes = [vp, P(ctypes.c_int)]
     lib.fe_ks_cm_create.argtypes = [vp, ctypes.c_int, i64, P(vp)]
     lib.fe_ks_cm_apply.argtypes = [vp, vp, vp, i64]
     lib.fe_ks_cm_info.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_size_t)]
@@ -225,6 +226,13 @@ def fe_ks_set_config(ctx, precision, config):
 def fe_ks_get_config(ctx, precision):
     out = ctypes.c_int()
     _check(_lib.fe_ks_get_config(ctx, precision, ctypes.byref(out)))
+    return out.value
+
+
+def fe_ks_device_status(ctx):
+    """1 if a bounded device-side wait of the tcgen05 cell kernel expired since the last call (synchronises)."""
+    out = ctypes.c_int()
+    _check(_lib.fe_ks_device_status(ctx, ctypes.byref(out)))
     return out.value
 
 

@@ -249,7 +249,8 @@ fe_ks_status fe_ks_cheb_filter_ghep(fe_ks_ctx* ctx, fe_ks_ctx* mass, double* X, 
  * Tile configuration of the fused cell kernel.  FE_KS_BF16 and FE_KS_F16 (real
  * operators, n_q = n_p): 0 = the 5th-generation tensor-core kernel (tcgen05:
  * the x-y plane products and the z sweeps of Algorithm 2 as four MMA chains
- * per cell and 8-vector tile, accumulators in tensor memory; the default),
+ * per cell and 4-vector tile, two pipelines per CTA, accumulators in tensor
+ * memory; the default),
  * 1 = the warp-level MMA kernel (one sweep per direction); complex operators
  * and FE_KS_BF16X2 have the warp-level kernel only.  FE_KS_F64, FE_KS_F32,
  * FE_KS_F64E:

@@ -4,7 +4,7 @@
 // Paper: Algorithm 2 (cell-level evaluation, eq. ggaReal) called from
 // Algorithm 1 (extraction Q C P X, expansion F Delta T3, assembly Q^T).  The
 // sum-factorised chain is regrouped into four dense contractions per cell and
-// tile of VT = 8 vectors, each a tcgen05.mma chain with FP32 accumulators in
+// tile of VT = 4 vectors, each a tcgen05.mma chain with FP32 accumulators in
 // tensor memory and 16-bit operands in shared memory:
 //   GEMM1 (plane, forward):   P_t[(v,c)][p'] = sum_p K_t[p][p'] X[(p,c)][v],
 //         K_0 = N (x) N, K_1 = D (x) N, K_2 = N (x) D  over the in-plane node
@@ -25,25 +25,36 @@
 // core matrices of 8 rows x 16 bytes) so that the 8 values one thread holds
 // are 16 contiguous bytes of the next operand.
 //
+// A CTA (512 threads, one per SM) runs two independent pipelines of 8 warps,
+// each with its own X tile, operand buffer, mbarrier, named barrier, MMA-
+// issuing thread and half of the tensor memory; they take alternate column
+// tiles of the same cell, whose operators, coefficients, DoF list and
+// projector pairs they share, so one pipeline's CUDA-core steps can run
+// while the other waits on its products.
+//
 // Layouts (N = 9: NN = 81 in-plane nodes, 729 cell nodes, row r = t NN + p'):
 //   KM   plane operators, rows r (256), 16-byte row per 8 p: r*16 + (p%8)*2 +
 //        (p/8)*PGS; GEMM1 reads it K-major as A [(t,p')][p]; GEMM4 reads the same
 //        bytes MN-major as A [p][(t,p')] (its transpose).
-//   XS   the gathered X tile, B of GEMM1, MN-major [p][(v,c)]: p*16 + v*2 + c*XSB.
-//   AB   A of GEMM2 [(v,p')][(t,c)] and of GEMM3 [(v,p')][(q,c')] (K-major, row
-//        r2 = v + 8 p'), then B of GEMM4 [(t,p')][c + 16 v] (MN-major).
+//   XS   the gathered X tile, B of GEMM1, MN-major [p][v + 4 c].
+//   AB   A of GEMM2 [(v,p')][(t,c)] and of GEMM3 [(v,p')][(c',q)] (K-major, row
+//        r2 = v + 4 p', 8-row groups 144 bytes apart), then B of GEMM4
+//        [(t,p')][c + 16 v] (MN-major).
 //   B2, B3  the 1D operators of the z sweeps, K-major.
-// Tensor memory: GEMM1 tiles at columns 0 and 128, GEMM2/3 tiles at 64 T, GEMM4
-// at 0 (each read out before the next product overwrites it).
+// Tensor memory (from the pipeline's base column 256 g): GEMM1 tiles at 0 and
+// 64, GEMM2/3 tiles at 64 T, GEMM4 at 0 (each read out before the next
+// product overwrites it).
 //
-// One thread issues each product's MMAs and commits them to an mbarrier; every
-// wait is bounded (on expiry the CTA sets the error word, lets the MMAs in
-// flight drain with a last bounded wait, frees its tensor memory and returns).
-// The nonlocal expansion F Delta P (FP32, the pair's F block and Delta-scaled
-// projections Q) and the scatter run on the GEMM4 accumulators in registers;
-// colour-exclusive launches make the assembly reductions deterministic.
-// FP16: every column of a gathered tile is scaled by a power of two (its
-// largest entry below 1/16), undone before the expansion and scatter.
+// One thread per pipeline issues each product's MMAs and commits them to the
+// pipeline's mbarrier; every wait is bounded (on expiry the pipeline stops, the
+// CTA sets the error word after the unit, lets the MMAs in flight drain with a
+// last bounded wait, frees its tensor memory and returns).  The nonlocal
+// expansion F Delta P (FP32: the pair's F rows and the tile's Delta-scaled
+// projections Q, staged in shared memory) is computed while GEMM4 runs and
+// added to the accumulators in registers before the scatter; colour-exclusive
+// launches make the assembly reductions deterministic.  FP16: every column of
+// a gathered tile is scaled by a power of two (its largest entry below 1/16),
+// undone before the expansion and scatter.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -59,57 +70,62 @@ namespace tc5 {
 
 template <int N>
 struct G5 {
-  static constexpr int NN = N * N, N3 = N * NN, VT = 8, NT = 512, NW = NT / 32, NC = 10;
+  static constexpr int NN = N * N, N3 = N * NN, VT = 4, NT = 512, GT = 256, NC = 10;
   static constexpr int KP = (NN + 15) / 16 * 16;      // GEMM1 K: in-plane node p (padded)
   static constexpr int R1 = 3 * NN;                    // rows (t, p') of the plane operators
   static constexpr int MT1 = (R1 + 127) / 128;         // GEMM1 M tiles
   static constexpr int R1P = MT1 * 128;
   static constexpr int K4 = (R1 + 15) / 16 * 16;       // GEMM4 K
-  static constexpr int N1 = (VT * N + 15) / 16 * 16;   // GEMM1 N: v + 8 c (padded)
-  static constexpr int NCX = N1 / VT;                  // c slots of the X tile (with padding)
-  static constexpr int R2 = VT * NN;                   // GEMM2/3 rows v + 8 p' (the 8 vectors of a node adjacent)
+  static constexpr int N1 = (VT * N + 15) / 16 * 16;   // GEMM1 N: v + 4 c (padded)
+  static constexpr int R2 = VT * NN;                   // GEMM2/3 rows v + 4 p' (a node's vectors adjacent)
   static constexpr int MT2 = (R2 + 127) / 128;
   static constexpr int N2 = (4 * N + 15) / 16 * 16;    // GEMM2 N: 4 c' + q
   static constexpr int K2 = 48;                        // GEMM2 K: 16 t + c
   static constexpr int K3 = N2;                        // GEMM3 K: 4 c' + q
   static constexpr int N3C = 48;                       // GEMM3 N: 16 t + c
+  static constexpr int N4 = 16 * VT;                   // GEMM4 N: c + 16 v
   static constexpr int CH0 = 2 * ((N + 2) / 4);        // c' of the first half of a quadrature-point row
   static constexpr int CSL = K3 / 4;                   // c' slots of a row (with padding)
   static constexpr int NC3 = 3 * (N > 8 ? 2 : 1);      // 16-byte chunks of a GEMM4 operand row group
-  static constexpr int MAXC = (N + 3) / 4;             // z planes per warp group in the final step
+  static constexpr int MAXC = (N + 1) / 2;             // z planes per warp half in the final step
   static constexpr int PG = 16;                        // p groups of KM (GEMM4 M = 128)
   static constexpr int PGS = R1P * 16;                 // byte stride of a p group in KM
+  static constexpr int QCAP = 64, PCAP = 16;           // staged (pair, projector) rows; staged pairs
+  static constexpr int CFS = 12;                       // floats per point of the staged coefficients
+  // shared by the two pipelines: operators, and the current cell's data
   static constexpr int OFF_KM = 0;
   static constexpr int OFF_B2 = OFF_KM + PG * PGS;
   static constexpr int OFF_B3 = OFF_B2 + N2 * K2 * 2;
   static constexpr int SZ_CST = OFF_B3 + N3C * K3 * 2;   // constant block, copied verbatim
-  static constexpr int XSB = KP * 16;                  // c stride of the X tile
-  static constexpr int OFF_XS = SZ_CST;
-  static constexpr int SZ_XS = NCX * XSB;
+  static constexpr int OFF_CF = SZ_CST;                  // coefficients [point][CFS], FP32
+  static constexpr int OFF_SD = OFF_CF + CFS * N3 * 4;   // DoF of each node
+  static constexpr int OFF_DS = OFF_SD + (N3 * 4 + 15) / 16 * 16;   // D^{-1/2} of each node
+  static constexpr int OFF_SP = OFF_DS + (N3 * 4 + 15) / 16 * 16;   // [PCAP] pairs, [PCAP] their atoms
+  static constexpr int OFF_PIPE = OFF_SP + 2 * PCAP * 4;
+  // per pipeline, at OFF_PIPE + g * PIPE
+  static constexpr int XSB = KP * 16;                  // n-group stride of the X tile
+  static constexpr int SZ_XS = (N1 / 8) * XSB;
   static constexpr int SBO2 = 144;                     // 8-row group stride of the GEMM2/3 A operands (padded:
                                                        // the 16-byte row stores of a warp spread over all banks)
   static constexpr int LBO2 = MT2 * 16 * SBO2;         // k-chunk stride of the GEMM2/3 A operands
   static constexpr int SBO4 = K4 * 16 + 16;            // n-group stride of the GEMM4 B operand (padded likewise)
   static constexpr int SZ_AB0 = LBO2 * (K2 > K3 ? K2 : K3) / 8;
-  static constexpr int SZ_AB = SZ_AB0 > 16 * SBO4 ? SZ_AB0 : 16 * SBO4;
-  static constexpr int OFF_AB = OFF_XS + SZ_XS;
-  static constexpr int CFS = 12;                       // floats per point of the staged coefficients
-  static constexpr int OFF_CF = OFF_AB + SZ_AB;        // coefficients [point][CFS], FP32
-  static constexpr int OFF_SD = OFF_CF + CFS * N3 * 4;
-  static constexpr int OFF_RED = OFF_SD + (N3 * 4 + 15) / 16 * 16;   // FP16: [NW warps][8] column maxima, [8] scales
-  static constexpr int OFF_USC = OFF_RED + (NW + 1) * 8 * 4;         // FP16: [8] unscale factors
-  static constexpr int QCAP = 64;                      // staged (pair, projector) rows of Q per tile
-  static constexpr int PCAP = 16;                      // staged (pair, atom) entries of a cell
-  static constexpr int OFF_QS = OFF_USC + 8 * 4;       // [QCAP][8] Delta-scaled projections of the tile's columns
-  static constexpr int OFF_SP = OFF_QS + QCAP * 8 * 4; // [PCAP] pairs of the cell, [PCAP] their atoms
-  static constexpr int OFF_DS = OFF_SP + 2 * PCAP * 4; // [N3] D^{-1/2} of the cell's nodes
-  static constexpr int OFF_MBAR = OFF_DS + (N3 * 4 + 15) / 16 * 16;
-  static constexpr int OFF_TMEM = OFF_MBAR + 8;
+  static constexpr int SZ_AB = SZ_AB0 > (N4 / 8) * SBO4 ? SZ_AB0 : (N4 / 8) * SBO4;
+  static constexpr int P_XS = 0;
+  static constexpr int P_AB = P_XS + SZ_XS;
+  static constexpr int P_QS = P_AB + SZ_AB;            // [QCAP][VT] Delta-scaled projections of the tile
+  static constexpr int P_RED = P_QS + QCAP * VT * 4;   // FP16: [8 warps][VT] column maxima, [VT] scales
+  static constexpr int P_USC = P_RED + 9 * VT * 4;     // [VT] unscale factors
+  static constexpr int P_MBAR = (P_USC + VT * 4 + 7) / 8 * 8;
+  static constexpr int PIPE = (P_MBAR + 8 + 15) / 16 * 16;
+  static constexpr int OFF_TMEM = OFF_PIPE + 2 * PIPE;
   static constexpr int BYTES = OFF_TMEM + 8;
-  static constexpr uint32_t TM_D1 = 0, TM_D1S = 128, TM_D23 = 0, TM_D23S = 64, TM_D4 = 0;
+  // tensor-memory columns, from the pipeline's base (256 g): GEMM1 tiles at 64 T, GEMM2/3 tiles at 64 T, GEMM4 at 0
+  static constexpr uint32_t TM_D1S = 64, TM_D23S = 64;
   static_assert(N >= 2 && N <= 9, "N");
-  static_assert(NN <= 128 && MT1 <= 2 && N1 <= 128 && N2 <= 64 && MT2 * 64 <= 512, "tile shapes");
-  static_assert(SZ_CST % 16 == 0 && OFF_AB % 16 == 0 && OFF_CF % 16 == 0 && OFF_MBAR % 8 == 0, "alignment");
+  static_assert(NN <= 128 && MT1 <= 2 && N1 <= 64 && N2 <= 64 && MT2 <= 3 && N4 <= 256, "tile shapes");
+  static_assert(SZ_CST % 16 == 0 && OFF_PIPE % 16 == 0 && PIPE % 16 == 0 && P_AB % 16 == 0 && P_QS % 16 == 0,
+                "alignment");
   static_assert(BYTES <= 232448, "shared memory");
 };
 
@@ -238,33 +254,49 @@ struct Params {
   int* err;              // set to 1 when a bounded wait expires
 };
 
+// named barrier of one pipeline (256 threads); and its OR-reduction of a predicate
+__device__ __forceinline__ void gsync(int g) { asm volatile("bar.sync %0, 256;\n" ::"r"(g + 1) : "memory"); }
+__device__ __forceinline__ bool gsync_or(int g, bool c) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, %2, 256, p;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)c), "r"(g + 1)
+      : "memory");
+  return r != 0;
+}
+
 template <int N, bool F16>
 __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ Params p) {
   using G = G5<N>;
-  constexpr int NT = G::NT, NN = G::NN, N3 = G::N3;
-  constexpr int GPT = (N3 + NT - 1) / NT;   // gathered nodes per thread
+  constexpr int NT = G::NT, GT = G::GT, NN = G::NN, N3 = G::N3, VT = G::VT;
+  constexpr int GPT = (N3 + GT - 1) / GT;   // gathered nodes per thread
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int quarter = warp & 3, grp = warp >> 2;   // tensor-memory lane quarter; warp group 0..3
+  const int g = tid / GT, gt = tid % GT;               // pipeline and thread within it
+  const int quarter = warp & 3, sub = (warp >> 2) & 1; // tensor-memory lane quarter; warp half of the pipeline
   const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(smem);
-  const uint32_t sXS = s0 + G::OFF_XS, sAB = s0 + G::OFF_AB;
-  const uint32_t mbar = s0 + G::OFF_MBAR;
+  unsigned char* pb_ = smem + G::OFF_PIPE + g * G::PIPE;   // this pipeline's buffers
+  const uint32_t sP = s0 + G::OFF_PIPE + g * G::PIPE;
+  const uint32_t sXS = sP + G::P_XS, sAB = sP + G::P_AB, mbar = sP + G::P_MBAR;
   float* cf = reinterpret_cast<float*>(smem + G::OFF_CF);
   int* sd = reinterpret_cast<int*>(smem + G::OFF_SD);
-  float* red = reinterpret_cast<float*>(smem + G::OFF_RED);
-  float* usc = reinterpret_cast<float*>(smem + G::OFF_USC);
-  float* qs = reinterpret_cast<float*>(smem + G::OFF_QS);
+  float* sds = reinterpret_cast<float*>(smem + G::OFF_DS);
   int* spr = reinterpret_cast<int*>(smem + G::OFF_SP);
   int* spa = spr + G::PCAP;
-  float* sds = reinterpret_cast<float*>(smem + G::OFF_DS);
+  float* qs = reinterpret_cast<float*>(pb_ + G::P_QS);
+  float* red = reinterpret_cast<float*>(pb_ + G::P_RED);
+  float* usc = reinterpret_cast<float*>(pb_ + G::P_USC);
 
-  // (0) constants; the X tile and AB start zeroed (their padding is read by
-  //     the tensor cores, multiplied by zero operator entries, and must be finite)
+  // (0) constants; both pipelines' X tiles and operand buffers start zeroed
+  //     (their padding is read by the tensor cores, multiplied by zero operator
+  //     entries, and must be finite)
   for (int i = tid; i < G::SZ_CST / 16; i += NT) reinterpret_cast<uint4*>(smem)[i] = __ldg(p.cst + i);
-  for (int i = tid; i < (G::SZ_XS + G::SZ_AB) / 16; i += NT)
-    reinterpret_cast<uint4*>(smem + G::OFF_XS)[i] = make_uint4(0u, 0u, 0u, 0u);
-  if (tid < 8) usc[tid] = 1.f;
-  if (tid == 0) {
+  for (int i = tid; i < 2 * G::PIPE / 16; i += NT)
+    reinterpret_cast<uint4*>(smem + G::OFF_PIPE)[i] = make_uint4(0u, 0u, 0u, 0u);
+  __syncthreads();
+  if (gt < VT) usc[gt] = 1.f;
+  if (gt == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
@@ -276,31 +308,31 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
   fence_before();
   __syncthreads();
   fence_after();
-  const uint32_t tmem = *reinterpret_cast<const uint32_t*>(smem + G::OFF_TMEM);
-  const uint32_t tlane = tmem + ((uint32_t)(32 * quarter) << 16);   // this warp's lane quarter
+  const uint32_t tbase = *reinterpret_cast<const uint32_t*>(smem + G::OFF_TMEM) + 256u * (uint32_t)g;
+  const uint32_t tlane = tbase + ((uint32_t)(32 * quarter) << 16);   // this warp's lane quarter
 
   constexpr uint32_t ID1 = idesc<F16>(G::N1, 0, 1), ID2 = idesc<F16>(G::N2, 0, 0);
-  constexpr uint32_t ID3 = idesc<F16>(G::N3C, 0, 0), ID4 = idesc<F16>(128, 1, 1);
+  constexpr uint32_t ID3 = idesc<F16>(G::N3C, 0, 0), ID4 = idesc<F16>(G::N4, 1, 1);
   // descriptors of the operands' first core matrices (later ones: + byte offset / 16)
   const uint64_t dKM1 = sdesc(s0 + G::OFF_KM, G::PGS, 128), dXS = sdesc(sXS, 128, G::XSB);
   const uint64_t dA2 = sdesc(sAB, G::LBO2, G::SBO2), dB2 = sdesc(s0 + G::OFF_B2, G::N2 * 16, 128);
   const uint64_t dB3 = sdesc(s0 + G::OFF_B3, G::N3C * 16, 128);
   const uint64_t dKM4 = sdesc(s0 + G::OFF_KM, 128, G::PGS), dB4 = sdesc(sAB, 128, G::SBO4);
 
-  const int ntiles = (p.ncols + 7) / 8;
+  const int ntiles = (p.ncols + VT - 1) / VT;
   const bool vec = (p.ld % 4 == 0) && (((uintptr_t)p.X & 15) == 0) && (((uintptr_t)p.Q & 15) == 0);
   const bool vecy = (p.ld % 4 == 0) && (((uintptr_t)p.Y & 15) == 0);
   const int units = p.n_cells * p.units_per_cell;
-  // this warp group's z planes in the final step
-  const int ccnt = N / 4 + (grp < N % 4 ? 1 : 0), cbeg = grp * (N / 4) + (grp < N % 4 ? grp : N % 4);
+  // this warp half's z planes in the final step
+  const int cbeg = sub ? (N + 1) / 2 : 0, ccnt = sub ? N / 2 : (N + 1) / 2;
   uint32_t phase = 0, failed_phase = 0;
   bool failed = false;
   int staged = -1;
 
-  // all threads: bounded wait for the products just committed; uniform result
+  // the pipeline's threads: bounded wait for the products just committed; uniform result
   auto wait_products = [&]() -> bool {
     const bool ok = mbar_wait(mbar, phase);
-    if (__syncthreads_or(!ok)) {
+    if (gsync_or(g, !ok)) {
       failed = true;
       failed_phase = phase;
       return false;
@@ -309,46 +341,54 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
     fence_after();
     return true;
   };
-  // this thread's gathered nodes of column tile [cx, cx + 8) and their D^{-1/2}
+  auto pipe_sync = [&]() {   // generic-proxy shared stores -> tensor cores; tensor-memory reads done
+    fence_async_smem();
+    fence_before();
+    gsync(g);
+  };
+  // this thread's gathered nodes of column tile [cx, cx + 4) and their D^{-1/2}
   // (registers; nothing waits on the loads until the tile's gather)
-  float xn[GPT][8], xs[GPT];
+  float xn[GPT][VT], xs[GPT];
   auto load_x = [&](int cx) {
-    const bool fullx = vec && cx + 8 <= p.ncols;
+    const bool fullx = vec && cx + VT <= p.ncols;
 #pragma unroll
     for (int r = 0; r < GPT; ++r) {
-      const int node = tid + r * NT;
+      const int node = gt + r * GT;
 #pragma unroll
-      for (int c = 0; c < 8; ++c) xn[r][c] = 0.f;
+      for (int c = 0; c < VT; ++c) xn[r][c] = 0.f;
       xs[r] = 1.f;
       if (node < N3) {
         const int d = sd[node];
         const float* xr = p.X + (int64_t)d * p.ld + cx;
         if (fullx) {
           const float4 a = __ldg(reinterpret_cast<const float4*>(xr));
-          const float4 b = __ldg(reinterpret_cast<const float4*>(xr) + 1);
           xn[r][0] = a.x, xn[r][1] = a.y, xn[r][2] = a.z, xn[r][3] = a.w;
-          xn[r][4] = b.x, xn[r][5] = b.y, xn[r][6] = b.z, xn[r][7] = b.w;
         } else {
 #pragma unroll
-          for (int c = 0; c < 8; ++c) xn[r][c] = cx + c < p.ncols ? __ldg(xr + c) : 0.f;
+          for (int c = 0; c < VT; ++c) xn[r][c] = cx + c < p.ncols ? __ldg(xr + c) : 0.f;
         }
         xs[r] = sds[node];
       }
     }
   };
 
-  for (int u = blockIdx.x; u < units && !failed; u += gridDim.x) {
+  for (int u = blockIdx.x; u < units; u += gridDim.x) {
     const int ci = u / p.units_per_cell;
     const int t_begin = (u % p.units_per_cell) * p.tiles_per_unit;
     const int t_end = min(ntiles, t_begin + p.tiles_per_unit);
     if (t_begin >= t_end) continue;
     const int e = p.cells[ci];
+    __syncthreads();   // both pipelines have finished the previous unit
     if (ci != staged) {
-      __syncthreads();   // the previous cell's scatter has finished with sd and cf
       for (int w = tid; w < N3; w += NT) {
         const int d = p.cell_dofs[(int64_t)e * N3 + w];
         sd[w] = d;
         sds[w] = p.dscale ? __ldg(p.dscale + d) : 1.f;
+      }
+      const float* gc = p.coef + (int64_t)e * p.ncoef * N3;
+      for (int w = tid; w < G::NC * N3; w += NT) {
+        const int slot = w / N3, q = w - slot * N3;
+        cf[q * G::CFS + slot] = __ldg(gc + w);
       }
       if (p.cell_pair_ptr) {
         const int b0 = p.cell_pair_ptr[e], n = min(p.cell_pair_ptr[e + 1] - b0, G::PCAP);
@@ -358,30 +398,28 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
           spa[tid] = p.pair_atom[pr];
         }
       }
-      const float* gc = p.coef + (int64_t)e * p.ncoef * N3;
-      for (int w = tid; w < G::NC * N3; w += NT) {
-        const int slot = w / N3, q = w - slot * N3;
-        cf[q * G::CFS + slot] = __ldg(gc + w);
-      }
       staged = ci;
-      __syncthreads();
     }
+    __syncthreads();
     const int pb = p.cell_pair_ptr ? p.cell_pair_ptr[e] : 0;
     const int pe = p.cell_pair_ptr ? p.cell_pair_ptr[e + 1] : 0;
+    const int nqrows = (pe - pb) * p.n_proj;
+    const bool qstaged = nqrows <= G::QCAP && pe - pb <= G::PCAP;
     bool have_next = false;   // xn already holds this tile's rows (loaded during the previous tile)
 
-    for (int t = t_begin; t < t_end; ++t) {
-      const int col0 = 8 * t;
+    // this pipeline's column tiles of the unit: every other one
+    for (int t = t_begin + g; t < t_end; t += 2) {
+      const int col0 = VT * t;
       // (1) extraction Q C P X (Algorithm 1): rows of X -> the MN-major X tile
       if (!have_next) load_x(col0);
 #pragma unroll
       for (int r = 0; r < GPT; ++r)
 #pragma unroll
-        for (int c = 0; c < 8; ++c) xn[r][c] *= xs[r];
+        for (int c = 0; c < VT; ++c) xn[r][c] *= xs[r];
       if constexpr (F16) {
-        float cm[8];
+        float cm[VT];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
+        for (int c = 0; c < VT; ++c) {
           float m = 0.f;
 #pragma unroll
           for (int r = 0; r < GPT; ++r) m = fmaxf(m, fabsf(xn[r][c]));
@@ -389,117 +427,101 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
           for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
           cm[c] = m;
         }
-        if (lane < 8) {
+        if (lane < VT) {
           float v = cm[0];
 #pragma unroll
-          for (int c = 1; c < 8; ++c) v = lane == c ? cm[c] : v;
-          red[warp * 8 + lane] = v;
+          for (int c = 1; c < VT; ++c) v = lane == c ? cm[c] : v;
+          red[(gt >> 5) * VT + lane] = v;
         }
-        __syncthreads();
-        if (tid < 8) {
+        gsync(g);
+        if (gt < VT) {
           float m = 0.f;
 #pragma unroll
-          for (int w = 0; w < G::NW; ++w) m = fmaxf(m, red[w * 8 + tid]);
-          const float s = col_scale(m);
-          red[G::NW * 8 + tid] = s;
-          usc[tid] = 1.f / s;   // exact: a power of two
+          for (int w = 0; w < 8; ++w) m = fmaxf(m, red[w * VT + gt]);
+          const float sc = col_scale(m);
+          red[8 * VT + gt] = sc;
+          usc[gt] = 1.f / sc;   // exact: a power of two
         }
-        __syncthreads();
+        gsync(g);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const float s = red[G::NW * 8 + c];
+        for (int c = 0; c < VT; ++c) {
+          const float sc = red[8 * VT + c];
 #pragma unroll
-          for (int r = 0; r < GPT; ++r) xn[r][c] *= s;
+          for (int r = 0; r < GPT; ++r) xn[r][c] *= sc;
         }
       }
 #pragma unroll
       for (int r = 0; r < GPT; ++r) {
-        const int node = tid + r * NT;
-        if (node < N3)
-          st16(sXS + (node % NN) * 16 + (node / NN) * G::XSB, pack<F16>(xn[r][0], xn[r][1]),
-               pack<F16>(xn[r][2], xn[r][3]), pack<F16>(xn[r][4], xn[r][5]), pack<F16>(xn[r][6], xn[r][7]));
-      }
-      // the tile's rows of Q (one half row per thread), stored to shared memory once GEMM1 has run
-      const int nqrows = (pe - pb) * p.n_proj;
-      const bool qstaged = nqrows <= G::QCAP && pe - pb <= G::PCAP;
-      float4 qreg = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (qstaged && tid < 2 * nqrows) {
-        const int row = tid >> 1, b = row % p.n_proj, c4 = col0 + 4 * (tid & 1);
-        const int a = spa[row / p.n_proj];
-        const float* qr = p.Q + ((int64_t)a * p.n_proj + b) * p.ld + c4;
-        if (vec && c4 + 4 <= p.ncols) {
-          qreg = __ldg(reinterpret_cast<const float4*>(qr));
-        } else {
-          if (c4 < p.ncols) qreg.x = __ldg(qr);
-          if (c4 + 1 < p.ncols) qreg.y = __ldg(qr + 1);
-          if (c4 + 2 < p.ncols) qreg.z = __ldg(qr + 2);
-          if (c4 + 3 < p.ncols) qreg.w = __ldg(qr + 3);
+        const int node = gt + r * GT;
+        if (node < N3) {
+          const int pn = node % NN, c = node / NN;
+          const uint32_t a = sXS + pn * 16 + (c & 1) * 8 + (c >> 1) * G::XSB;
+          asm volatile("st.shared.v2.b32 [%0], {%1,%2};\n" ::"r"(a), "r"(pack<F16>(xn[r][0], xn[r][1])),
+                       "r"(pack<F16>(xn[r][2], xn[r][3]))
+                       : "memory");
         }
       }
-      fence_async_smem();
-      fence_before();
-      __syncthreads();
+      // the tile's rows of Q (one row per thread), stored to shared memory once GEMM1 has run
+      float4 qreg = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (qstaged && gt < nqrows) {
+        const int b = gt % p.n_proj;
+        const float* qr = p.Q + ((int64_t)spa[gt / p.n_proj] * p.n_proj + b) * p.ld + col0;
+        if (vec && col0 + 4 <= p.ncols) {
+          qreg = __ldg(reinterpret_cast<const float4*>(qr));
+        } else {
+          if (col0 < p.ncols) qreg.x = __ldg(qr);
+          if (col0 + 1 < p.ncols) qreg.y = __ldg(qr + 1);
+          if (col0 + 2 < p.ncols) qreg.z = __ldg(qr + 2);
+          if (col0 + 3 < p.ncols) qreg.w = __ldg(qr + 3);
+        }
+      }
+      pipe_sync();
       // (2) GEMM1: P_t = K_t^T X per plane
-      if (tid == 0) {
+      if (gt == 0) {
         fence_after();
 #pragma unroll
         for (int T = 0; T < G::MT1; ++T)
 #pragma unroll
           for (int ks = 0; ks < G::KP / 16; ++ks)
-            mma(tmem + G::TM_D1 + T * G::TM_D1S, dKM1 + (uint64_t)((T * 2048 + ks * 2 * G::PGS) >> 4),
+            mma(tbase + T * G::TM_D1S, dKM1 + (uint64_t)((T * 2048 + ks * 2 * G::PGS) >> 4),
                 dXS + (uint64_t)((ks * 256) >> 4), ID1, ks > 0);
         commit(mbar);
       }
       if (!wait_products()) break;
-      if (qstaged && tid < 2 * nqrows) reinterpret_cast<float4*>(qs)[tid] = qreg;
-      // (3) GEMM1 rows (t, p') -> A2 rows (v, p'), k = 16 t + c; items (tile, half of v)
-#pragma unroll 1
-      for (int it = grp; it < 2 * G::MT1; it += 4) {
-        const int T = it % G::MT1, vh = it / G::MT1;
-        const int r1 = 128 * T + 32 * quarter + lane;
-        const int tt = r1 / NN, pp = r1 - tt * NN;
-        constexpr int NLO = N < 8 ? N : 8;               // planes c of the first chunk
-        constexpr int LD0 = (8 * NLO + 15) / 16;        // 16-column loads covering them
-        float a[16 * LD0];
+      if (qstaged && gt < nqrows) reinterpret_cast<float4*>(qs)[gt] = qreg;
+      // (3) GEMM1 rows (t, p') -> A2 rows v + 4 p', k = 16 t + c; one GEMM1 tile per warp half
+      if (sub < G::MT1) {
+        const int T = sub;
+        float a[G::N1];
 #pragma unroll
-        for (int j = 0; j < LD0; ++j) ld16(tlane + G::TM_D1 + T * G::TM_D1S + 16 * j, a + 16 * j);
+        for (int j = 0; j < G::N1 / 16; ++j) ld16(tlane + T * G::TM_D1S + 16 * j, a + 16 * j);
         ld_wait();
+        const int r1 = 128 * T + 32 * quarter + lane;
         if (r1 < G::R1) {
+          const int tt = r1 / NN, pp = r1 - tt * NN;
 #pragma unroll
-          for (int vv = 0; vv < 4; ++vv) {
-            const int v = 4 * vh + vv;
+          for (int v = 0; v < VT; ++v) {
+            const int r2 = v + 4 * pp;
+            const uint32_t row = sAB + (r2 & 7) * 16 + (r2 >> 3) * G::SBO2;
             float c8[8];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) c8[c] = c < NLO ? (vh ? a[4 + vv + 8 * c] : a[vv + 8 * c]) : 0.f;
-            st16(sAB + v * 16 + pp * G::SBO2 + (2 * tt) * G::LBO2, pack<F16>(c8[0], c8[1]), pack<F16>(c8[2], c8[3]),
-                 pack<F16>(c8[4], c8[5]), pack<F16>(c8[6], c8[7]));
-          }
-        }
-        if constexpr (N > 8) {   // plane c = 8: columns 64..71
-          float b[16];
-          ld16(tlane + G::TM_D1 + T * G::TM_D1S + 64, b);
-          ld_wait();
-          if (r1 < G::R1) {
-#pragma unroll
-            for (int vv = 0; vv < 4; ++vv) {
-              const int v = 4 * vh + vv;
-              st16(sAB + v * 16 + pp * G::SBO2 + (2 * tt + 1) * G::LBO2, pack<F16>(vh ? b[4 + vv] : b[vv], 0.f), 0u,
-                   0u, 0u);
-            }
+            for (int c = 0; c < 8; ++c) c8[c] = c < N ? a[v + VT * c] : 0.f;
+            st16(row + (2 * tt) * G::LBO2, pack<F16>(c8[0], c8[1]), pack<F16>(c8[2], c8[3]), pack<F16>(c8[4], c8[5]),
+                 pack<F16>(c8[6], c8[7]));
+            if constexpr (N > 8)
+              st16(row + (2 * tt + 1) * G::LBO2, pack<F16>(a[v + VT * 8], 0.f), 0u, 0u, 0u);
           }
         }
       }
-      fence_async_smem();
-      fence_before();
-      __syncthreads();
+      pipe_sync();
       // (4) GEMM2: the z sweep
-      if (tid == 0) {
+      if (gt == 0) {
         fence_after();
 #pragma unroll
         for (int T = 0; T < G::MT2; ++T)
 #pragma unroll
           for (int ks = 0; ks < G::K2 / 16; ++ks)
-            mma(tmem + G::TM_D23 + T * G::TM_D23S, dA2 + (uint64_t)((T * 16 * G::SBO2 + ks * 2 * G::LBO2) >> 4),
+            mma(tbase + T * G::TM_D23S, dA2 + (uint64_t)((T * 16 * G::SBO2 + ks * 2 * G::LBO2) >> 4),
                 dB2 + (uint64_t)((ks * 2 * G::N2 * 16) >> 4), ID2, ks > 0);
         commit(mbar);
       }
@@ -510,17 +532,17 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
         constexpr int LO = decltype(H)::value ? G::CH0 : 0, HI = decltype(H)::value ? G::CSL : G::CH0;
         float y[48];
 #pragma unroll
-        for (int j = 0; j < 3; ++j) ld16(tlane + G::TM_D23 + T * G::TM_D23S + 16 * j, y + 16 * j);
+        for (int j = 0; j < 3; ++j) ld16(tlane + T * G::TM_D23S + 16 * j, y + 16 * j);
         ld_wait();
         const int r2 = 128 * T + 32 * quarter + lane;
         if (r2 < G::R2) {
-          const int pp = r2 >> 3;
+          const int pp = r2 >> 2;
           float o[4 * (HI - LO) + 1];
 #pragma unroll
           for (int c = LO; c < HI; ++c) {
             float z = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f;
             if (c < N) {
-              const float* cp = cf + (pp + NN * c) * G::CFS;   // the 8 vectors of a node share the address
+              const float* cp = cf + (pp + NN * c) * G::CFS;   // the vectors of a node share the address
               const float4 ca = *reinterpret_cast<const float4*>(cp);
               const float4 cb = *reinterpret_cast<const float4*>(cp + 4);
               const float G00 = ca.x, G01 = ca.y, G02 = ca.z, G11 = ca.w, G12 = cb.x, G22 = cb.y, VL = cb.z;
@@ -543,7 +565,7 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
             o[4 * (c - LO) + 2] = w1;
             o[4 * (c - LO) + 3] = w2;
           }
-          const uint32_t row = sAB + (r2 & 7) * 16 + pp * G::SBO2;
+          const uint32_t row = sAB + (r2 & 7) * 16 + (r2 >> 3) * G::SBO2;
 #pragma unroll
           for (int kc = 0; kc < (HI - LO) / 2; ++kc)
             st16(row + (LO / 2 + kc) * G::LBO2, pack<F16>(o[8 * kc], o[8 * kc + 1]),
@@ -552,42 +574,40 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
         }
       };
 #pragma unroll 1
-      for (int it = grp; it < 2 * G::MT2; it += 4) {
+      for (int it = sub; it < 2 * G::MT2; it += 2) {
         if (it & 1)
           pointwise(it >> 1, std::integral_constant<int, 1>{});
         else
           pointwise(it >> 1, std::integral_constant<int, 0>{});
       }
-      // the next column tile's rows of X, in flight during the rest of this tile
-      have_next = t + 1 < t_end;
-      if (have_next) load_x(col0 + 8);
-      fence_async_smem();
-      fence_before();
-      __syncthreads();
+      // this pipeline's next column tile's rows of X, in flight during the rest of this tile
+      have_next = t + 2 < t_end;
+      if (have_next) load_x(col0 + 2 * VT);
+      pipe_sync();
       // (6) GEMM3: the transposed z sweep
-      if (tid == 0) {
+      if (gt == 0) {
         fence_after();
 #pragma unroll
         for (int T = 0; T < G::MT2; ++T)
 #pragma unroll
           for (int ks = 0; ks < G::K3 / 16; ++ks)
-            mma(tmem + G::TM_D23 + T * G::TM_D23S, dA2 + (uint64_t)((T * 16 * G::SBO2 + ks * 2 * G::LBO2) >> 4),
+            mma(tbase + T * G::TM_D23S, dA2 + (uint64_t)((T * 16 * G::SBO2 + ks * 2 * G::LBO2) >> 4),
                 dB3 + (uint64_t)((ks * 2 * G::N3C * 16) >> 4), ID3, ks > 0);
         commit(mbar);
       }
       if (!wait_products()) break;
-      // (7) GEMM3 rows (v, p'), columns 16 t + c -> B4 [(t, p')][c + 16 v] (MN-major);
+      // (7) GEMM3 rows v + 4 p', columns 16 t + c -> B4 [(t, p')][c + 16 v] (MN-major);
       //     items (tile, half of the chunks)
 #pragma unroll 1
-      for (int it = grp; it < 2 * G::MT2; it += 4) {
+      for (int it = sub; it < 2 * G::MT2; it += 2) {
         const int T = it >> 1, h = it & 1;
         float d3[48];
 #pragma unroll
-        for (int j = 0; j < 3; ++j) ld16(tlane + G::TM_D23 + T * G::TM_D23S + 16 * j, d3 + 16 * j);
+        for (int j = 0; j < 3; ++j) ld16(tlane + T * G::TM_D23S + 16 * j, d3 + 16 * j);
         ld_wait();
         const int r2 = 128 * T + 32 * quarter + lane;
         if (r2 < G::R2) {
-          const int v = r2 & 7, pp = r2 >> 3;
+          const int v = r2 & 3, pp = r2 >> 2;
           constexpr int HCN = N > 8 ? 2 : 1;
 #pragma unroll
           for (int ch = 0; ch < G::NC3; ++ch) {
@@ -600,32 +620,29 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
           }
         }
       }
-      fence_async_smem();
-      fence_before();
-      __syncthreads();
+      pipe_sync();
       // (8) GEMM4: the transposed plane product
-      if (tid == 0) {
+      if (gt == 0) {
         fence_after();
 #pragma unroll
         for (int ks = 0; ks < G::K4 / 16; ++ks)
-          mma(tmem + G::TM_D4, dKM4 + (uint64_t)((ks * 256) >> 4), dB4 + (uint64_t)((ks * 256) >> 4), ID4, ks > 0);
+          mma(tbase, dKM4 + (uint64_t)((ks * 256) >> 4), dB4 + (uint64_t)((ks * 256) >> 4), ID4, ks > 0);
         commit(mbar);
       }
-      // (9) F Delta P (nonlocal expansion) for this thread's node column, computed
-      //     while GEMM4 runs; then Y += alpha D^{-1/2} Q^T (Y^(e) + F Delta P)
+      // (9) F Delta P (nonlocal expansion) for this thread's nodes, computed while
+      //     GEMM4 runs; then Y += alpha D^{-1/2} Q^T (Y^(e) + F Delta P)
       const int pp = 32 * quarter + lane;   // in-plane node of this lane
-      float ex[G::MAXC][8];
+      float ex[G::MAXC][VT];
 #pragma unroll
       for (int j = 0; j < G::MAXC; ++j)
 #pragma unroll
-        for (int v = 0; v < 8; ++v) ex[j][v] = 0.f;
+        for (int v = 0; v < VT; ++v) ex[j][v] = 0.f;
       if (pp < NN && pb < pe && qstaged) {
         // every F load of a pair issued before the arithmetic; Q from shared memory (broadcast)
         constexpr int BCH = 9;
         for (int pi = pb; pi < pe; ++pi) {
-          const int pr = spr[pi - pb];
-          const float* Fp = p.F + (int64_t)pr * p.n_proj * N3 + pp + NN * cbeg;
-          const float* qp = qs + (pi - pb) * p.n_proj * 8;
+          const float* Fp = p.F + (int64_t)spr[pi - pb] * p.n_proj * N3 + pp + NN * cbeg;
+          const float* qp = qs + (pi - pb) * p.n_proj * VT;
 #pragma unroll 1
           for (int b0 = 0; b0 < p.n_proj; b0 += BCH) {
             float f[BCH][G::MAXC];
@@ -634,28 +651,27 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
 #pragma unroll
               for (int j = 0; j < G::MAXC; ++j)
                 f[bb][j] = b0 + bb < p.n_proj && j < ccnt ? __ldg(Fp + (int64_t)(b0 + bb) * N3 + NN * j) : 0.f;
-            uint64_t ex2[G::MAXC][4];   // packed accumulators, vectors (2 w, 2 w + 1)
+            uint64_t ex2[G::MAXC][2];   // packed accumulators, vectors (2 w, 2 w + 1)
 #pragma unroll
             for (int j = 0; j < G::MAXC; ++j)
 #pragma unroll
-              for (int w = 0; w < 4; ++w) ex2[j][w] = pk2(ex[j][2 * w], ex[j][2 * w + 1]);
+              for (int w = 0; w < 2; ++w) ex2[j][w] = pk2(ex[j][2 * w], ex[j][2 * w + 1]);
 #pragma unroll
             for (int bb = 0; bb < BCH; ++bb) {
               if (b0 + bb >= p.n_proj) break;
-              const float4 q0 = *reinterpret_cast<const float4*>(qp + (b0 + bb) * 8);
-              const float4 q1 = *reinterpret_cast<const float4*>(qp + (b0 + bb) * 8 + 4);
-              const uint64_t q2[4] = {pk2(q0.x, q0.y), pk2(q0.z, q0.w), pk2(q1.x, q1.y), pk2(q1.z, q1.w)};
+              const float4 q0 = *reinterpret_cast<const float4*>(qp + (b0 + bb) * VT);
+              const uint64_t q2[2] = {pk2(q0.x, q0.y), pk2(q0.z, q0.w)};
 #pragma unroll
               for (int j = 0; j < G::MAXC; ++j) {
                 const uint64_t ff = pk2(f[bb][j], f[bb][j]);
-#pragma unroll
-                for (int w = 0; w < 4; ++w) fma2(ex2[j][w], ff, q2[w]);
+                fma2(ex2[j][0], ff, q2[0]);
+                fma2(ex2[j][1], ff, q2[1]);
               }
             }
 #pragma unroll
             for (int j = 0; j < G::MAXC; ++j)
 #pragma unroll
-              for (int w = 0; w < 4; ++w) {
+              for (int w = 0; w < 2; ++w) {
                 const float2 e2 = up2(ex2[j][w]);
                 ex[j][2 * w] = e2.x;
                 ex[j][2 * w + 1] = e2.y;
@@ -663,53 +679,36 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
           }
         }
       } else if (pp < NN && pb < pe) {
-        const bool fq = vec && col0 + 8 <= p.ncols;
         for (int pi = pb; pi < pe; ++pi) {
           const int pr = p.cell_pairs[pi];
           const float* Fp = p.F + (int64_t)pr * p.n_proj * N3 + pp + NN * cbeg;
           const float* Qa = p.Q + (int64_t)p.pair_atom[pr] * p.n_proj * p.ld + col0;
 #pragma unroll 1
-          for (int b0 = 0; b0 < p.n_proj; b0 += 4) {
-            float q[4][8], f[4][G::MAXC];
+          for (int b = 0; b < p.n_proj; ++b) {
+            float q[VT];
 #pragma unroll
-            for (int bb = 0; bb < 4; ++bb) {
-              const int b = b0 + bb;
-              const bool okb = b < p.n_proj;
-              const float* qr = Qa + (int64_t)(okb ? b : 0) * p.ld;
-              if (fq) {
-                const float4 q0 = okb ? __ldg(reinterpret_cast<const float4*>(qr)) : make_float4(0.f, 0.f, 0.f, 0.f);
-                const float4 q1 = okb ? __ldg(reinterpret_cast<const float4*>(qr) + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
-                q[bb][0] = q0.x, q[bb][1] = q0.y, q[bb][2] = q0.z, q[bb][3] = q0.w;
-                q[bb][4] = q1.x, q[bb][5] = q1.y, q[bb][6] = q1.z, q[bb][7] = q1.w;
-              } else {
+            for (int v = 0; v < VT; ++v) q[v] = col0 + v < p.ncols ? __ldg(Qa + (int64_t)b * p.ld + v) : 0.f;
 #pragma unroll
-                for (int v = 0; v < 8; ++v) q[bb][v] = okb && col0 + v < p.ncols ? __ldg(qr + v) : 0.f;
-              }
+            for (int j = 0; j < G::MAXC; ++j) {
+              const float f = j < ccnt ? __ldg(Fp + (int64_t)b * N3 + NN * j) : 0.f;
 #pragma unroll
-              for (int j = 0; j < G::MAXC; ++j)
-                f[bb][j] = okb && j < ccnt ? __ldg(Fp + (int64_t)b * N3 + NN * j) : 0.f;
+              for (int v = 0; v < VT; ++v) ex[j][v] = fmaf(f, q[v], ex[j][v]);
             }
-#pragma unroll
-            for (int bb = 0; bb < 4; ++bb)
-#pragma unroll
-              for (int j = 0; j < G::MAXC; ++j)
-#pragma unroll
-                for (int v = 0; v < 8; ++v) ex[j][v] = fmaf(f[bb][j], q[bb][v], ex[j][v]);
           }
         }
       }
       if (!wait_products()) break;
       {
-        float o[G::MAXC][8];
+        float o[G::MAXC][VT];
 #pragma unroll
         for (int j = 0; j < G::MAXC; ++j)
 #pragma unroll
-          for (int v = 0; v < 8; ++v) {
+          for (int v = 0; v < VT; ++v) {
             uint32_t r;
             const int c = cbeg + (j < ccnt ? j : 0);
             asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];\n"
                          : "=r"(r)
-                         : "r"(tlane + G::TM_D4 + (uint32_t)(c + 16 * v)));
+                         : "r"(tlane + (uint32_t)(c + 16 * v)));
             o[j][v] = __uint_as_float(r);
           }
         ld_wait();
@@ -721,32 +720,36 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
             const int c = cbeg + j;
             const int d = sd[pp + NN * c];
             const float s = p.alpha * sds[pp + NN * c];
-            float w[8];
+            float w[VT];
 #pragma unroll
-            for (int v = 0; v < 8; ++v) w[v] = s * fmaf(o[j][v], usc[v], ex[j][v]);
+            for (int v = 0; v < VT; ++v) w[v] = s * fmaf(o[j][v], usc[v], ex[j][v]);
             float* yp = p.Y + (int64_t)d * p.ld + col0;
-            if (vecy && col0 + 8 <= p.ncols) {
+            if (vecy && col0 + VT <= p.ncols) {
               atomicAdd(reinterpret_cast<float4*>(yp), make_float4(w[0], w[1], w[2], w[3]));
-              atomicAdd(reinterpret_cast<float4*>(yp) + 1, make_float4(w[4], w[5], w[6], w[7]));
             } else {
 #pragma unroll
-              for (int v = 0; v < 8; ++v)
+              for (int v = 0; v < VT; ++v)
                 if (col0 + v < p.ncols) atomicAdd(yp + v, w[v]);
             }
           }
         }
       }
     }
+    if (__syncthreads_or(failed)) {
+      failed = true;
+      break;
+    }
   }
   __syncthreads();
-  if (failed && tid == 0) {
+  if (failed && gt == 0) {
     atomicExch(p.err, 1);
     (void)mbar_wait(mbar, failed_phase);   // a last bounded chance for MMAs in flight to drain
   }
   fence_before();
   __syncthreads();
   fence_after();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(tmem));
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(tbase - 256u * (uint32_t)g));
 }
 
 // The constant block of one degree: the plane operators KM and the z-sweep
@@ -792,12 +795,13 @@ cudaError_t launch_n(Params p, cudaStream_t s) {
   if (sms <= 0) sms = 152;
   cudaError_t err = cudaFuncSetAttribute(fe_tc5_kernel<N, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::BYTES);
   if (err != cudaSuccess) return err;
-  const int ntiles = (p.ncols + 7) / 8;
-  // split a cell's column tiles into units so that every SM gets about 16 or more
+  const int ntiles = (p.ncols + G::VT - 1) / G::VT;
+  // split a cell's column tiles into units so that every SM gets about 16 or more;
+  // a unit's tiles alternate between the CTA's two pipelines, so keep the count even
   int upc = 1;
-  while (upc < ntiles && (int64_t)p.n_cells * upc < 16LL * sms) upc *= 2;
-  if (upc > ntiles) upc = ntiles;
+  while (2 * upc < ntiles && (int64_t)p.n_cells * upc < 16LL * sms) upc *= 2;
   p.tiles_per_unit = (ntiles + upc - 1) / upc;
+  p.tiles_per_unit += p.tiles_per_unit & 1;
   p.units_per_cell = (ntiles + p.tiles_per_unit - 1) / p.tiles_per_unit;
   const int64_t units = (int64_t)p.n_cells * p.units_per_cell;
   const int grid = (int)std::min<int64_t>(units, sms);

@@ -61,6 +61,17 @@ def _measured_hbm_gbs():
 PEAK_HBM_GBS = _measured_hbm_gbs()
 
 
+def _measured_bf16_tflops():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except (OSError, ValueError, KeyError):
+        return 1900.0   # fallback figure of an earlier GB300 measurement
+
+
+PEAK_BF16_TFLOPS = _measured_bf16_tflops()
+
+
 def parse():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -1100,6 +1111,23 @@ def detail_sections(args, wl, res, world):
                                                 / (bf["ms"] * 1e-3),
                          "mma_sync_live_probe_tflops": (res["peak_mma_live"] or 0) / 1e12},
             "clocks": bf["clocks"], "gpu_launches": bf["launches"]}
+        tcgen05 = key in ("bf16", "f16") and bf.get("tile_config") == 0 and not wl.complex and wl.nq == wl.p + 1
+        detail[name]["kernel"] = ("tcgen05 (plane and z-sweep products, tile configuration 0)" if tcgen05 else
+                                  "warp-level mma.sync (one sweep per direction)")
+        detail[name]["tile_config"] = bf.get("tile_config")
+        detail[name]["tune_ms_per_config"] = [t for t in bf.get("tune_ms", []) if t > 0]
+        if tcgen05:
+            # tcgen05 MMA work executed per application: per cell and 4-vector tile, GEMM1
+            # (plane, 2 M-tiles x K 96 x N 48), GEMM2 and GEMM3 (3 M-tiles x K 48 x N 48) and
+            # GEMM4 (K 256 x N 64), all with M = 128
+            n = wl.p + 1
+            nn = n * n
+            mt1, kp, n1 = -(-3 * nn // 128), -(-nn // 16) * 16, -(-4 * n // 16) * 16
+            mt2, n2, k4 = -(-4 * nn // 128), -(-4 * n // 16) * 16, -(-3 * nn // 16) * 16
+            per_tile = 2 * 128 * (mt1 * kp * n1 + mt2 * 48 * n2 + mt2 * n2 * 48 + k4 * 64)
+            fl = wl.n_cells * -(-wl.n_v // 4) * per_tile
+            detail[name]["roofline"]["tcgen05_tflops_executed"] = fl / (bf["ms"] * 1e-3) / 1e12
+            detail[name]["roofline"]["tcgen05_frac_of_bf16_peak"] = fl / (bf["ms"] * 1e-3) / (PEAK_BF16_TFLOPS * 1e12)
     if res["e2e"]:
         detail["e2e"] = res["e2e"]
     if res["filter"]:
@@ -1161,6 +1189,10 @@ def compact_line(detail, args, config, world):
         elif "frac_of_nominal_fp64" in d:
             q["frac"] = _r(d["frac_of_nominal_fp64"], 3)
             q["bound"] = "alu"
+        if d.get("kernel"):
+            q["kernel"] = "tcgen05" if d["kernel"].startswith("tcgen05") else "mma.sync"
+        if "roofline" in d and "tcgen05_frac_of_bf16_peak" in d["roofline"]:
+            q["tensor_frac"] = _r(d["roofline"]["tcgen05_frac_of_bf16_peak"], 3)
         prec[name] = q
     if prec:
         line["precisions"] = prec

@@ -508,8 +508,9 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
             for (int c = 0; c < 8; ++c) c8[c] = c < N ? a[v + VT * c] : 0.f;
             st16(row + (2 * tt) * G::LBO2, pack<F16>(c8[0], c8[1]), pack<F16>(c8[2], c8[3]), pack<F16>(c8[4], c8[5]),
                  pack<F16>(c8[6], c8[7]));
-            if constexpr (N > 8)
-              st16(row + (2 * tt + 1) * G::LBO2, pack<F16>(a[v + VT * 8], 0.f), 0u, 0u, 0u);
+            // second chunk (c = 8..15): the plane c = 8, or zeros (the buffer is shared with the
+            // other products; a NaN left there would survive the zero operator entries)
+            st16(row + (2 * tt + 1) * G::LBO2, N > 8 ? pack<F16>(a[v + VT * (N > 8 ? 8 : 0)], 0.f) : 0u, 0u, 0u, 0u);
           }
         }
       }
@@ -620,6 +621,10 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
           }
         }
       }
+      // the K padding of GEMM4 (rows R1..K4 of B4, multiplied by zero rows of KM) must be
+      // finite: zero it, as the buffer held other products' data
+      for (int i = gt; i < (G::K4 - G::R1) * (G::N4 / 8); i += GT)
+        st16(sAB + (G::R1 + i / (G::N4 / 8)) * 16 + (i % (G::N4 / 8)) * G::SBO4, 0u, 0u, 0u, 0u);
       pipe_sync();
       // (8) GEMM4: the transposed plane product
       if (gt == 0) {

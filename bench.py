@@ -301,8 +301,12 @@ def run_native(args, wl, rank, world):
         if args.config is None:
             best, tune_ms = fk.fe_ks_tune(ctx, X, Y, n_v, precision, reps=1)
         else:
-            fk.fe_ks_set_config(ctx, precision, args.config)
-            best, tune_ms = args.config, []
+            try:
+                fk.fe_ks_set_config(ctx, precision, args.config)
+                best = args.config
+            except fk.FeKsError:   # a precision with a single kernel (the split one)
+                best = 0
+            tune_ms = []
         for _ in range(warmup):
             fk.fe_ks_apply(ctx, X, Y, n_v, precision)
         torch.cuda.synchronize()

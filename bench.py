@@ -891,9 +891,29 @@ def run_batched(args, wls=None):
                         best = (ms, stiles, sc, occ, threads)
                         split = (t64, t32)
                     fk.fe_ks_batch_set_split(b, 0, 0)
+    # direct systems: the largest ones (by their own application time) on their own tuned
+    # kernels, on side streams beside the persistent launch of the others
+    _, tiles, cells, occ, threads = best
+    ms_each = [timed(lambda c=c, X=X, Y=Y, wl=wl, pr=pr: fk.fe_ks_apply(c, X, Y, wl.n_v, pr), 2)
+               for c, X, Y, wl, pr in zip(ctxs, Xs, Ys, wls, prec)]
+    order = sorted(range(len(wls)), key=lambda i: -ms_each[i])
+    direct = None
+    for k in sorted({1, 2, len(wls)}):
+        flags = [1 if i in order[:k] else 0 for i in range(len(wls))]
+        fk.fe_ks_batch_configure(b, tiles, cells, depth, 2.0, False, blocks_per_sm=occ, threads=threads)
+        fk.fe_ks_batch_set_split(b, *split)
+        fk.fe_ks_batch_set_direct(b, flags)
+        ms = timed(lambda: fk.fe_ks_batch_apply(b, Xs, Ys, stream.cuda_stream), 2)
+        fk.fe_ks_batch_status(b)
+        trials.append({"direct": flags, "ms": round(ms, 3)})
+        if ms < best[0]:
+            best = (ms, tiles, cells, occ, threads)
+            direct = flags
+        fk.fe_ks_batch_set_direct(b, None)
     _, tiles, cells, occ, threads = best
     fk.fe_ks_batch_configure(b, tiles, cells, depth, 2.0, False, blocks_per_sm=occ, threads=threads)
     fk.fe_ks_batch_set_split(b, *split)
+    fk.fe_ks_batch_set_direct(b, direct)
     g = torch.cuda.CUDAGraph()
     side = torch.cuda.Stream()
     side.wait_stream(stream)
@@ -916,7 +936,8 @@ def run_batched(args, wls=None):
             "one_launch_per_system": {"value": units / (ms_sep * 1e-3), "ms_per_step": ms_sep},
             "speedup_vs_separate": ms_sep / ms_graph,
             "tuned": {"tile_config": tiles, "cells_per_item": cells, "depth": depth, "blocks_per_sm": occ,
-                      "threads": threads, "split_threads": list(split)},
+                      "threads": threads, "split_threads": list(split), "direct_systems": direct},
+            "ms_each_system_alone": [round(t, 3) for t in ms_each],
             "tuning_trials": trials, "items": info["n_items"], "grid": info["grid"],
             "smem_bytes": info["smem_bytes"], "graph": True, "x_inputs": "device RNG (seed 5000), U(-1,1)",
             "l2": "flushed (256 MiB write) before each timed rep"}

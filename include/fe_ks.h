@@ -392,6 +392,22 @@ fe_ks_status fe_ks_batch_status(fe_ks_batch* b);
  * (as fe_ks_batch_configure does); the other tunables are kept.
  */
 fe_ks_status fe_ks_batch_set_split(fe_ks_batch* b, int threads_f64, int threads_f32);
+/*
+ * Direct systems: direct[s] != 0 (host array of n_sys flags; NULL clears all)
+ * takes system s out of the persistent queue.  fe_ks_batch_apply then applies
+ * it with its own context's kernels (projection and one tuned cell-kernel
+ * launch per colour, as fe_ks_apply does, in the context's current tile
+ * configuration), each direct system on a side stream of its own forked from
+ * cuda_stream with an event and joined back into it; the persistent launch of
+ * the remaining systems (if any) runs on cuda_stream concurrently.  The whole
+ * call still captures as one CUDA graph.  For a batch whose work is dominated
+ * by a few large systems, whose own tuned launches beat any routine inside a
+ * shared persistent kernel, while the small ones still gain from the queue.
+ * During fe_ks_batch_apply a direct system's context has its stream switched to
+ * the side stream and restored before the call returns.  The first call with
+ * flags creates the streams and events.  Rebuilds the queue.
+ */
+fe_ks_status fe_ks_batch_set_direct(fe_ks_batch* b, const int* direct);
 fe_ks_status fe_ks_batch_info(const fe_ks_batch* b, int* n_items, int* grid, size_t* smem_bytes);
 void fe_ks_batch_destroy(fe_ks_batch* b);
 

@@ -132,6 +132,12 @@ struct fe_ks_batch {
   int grid_cls[2] = {0, 0};
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // direct systems (fe_ks_batch_set_direct): applied by their own tuned cell kernels, each
+  // on a side stream of its own, concurrently with the persistent launch of the others
+  std::vector<int> direct;
+  std::vector<cudaStream_t> dstream;
+  std::vector<cudaEvent_t> djoin;
+  cudaEvent_t dfork = nullptr;
 };
 
 static constexpr int kStateWords = 3 + kMaxSys * kMaxPhase;
@@ -152,6 +158,7 @@ static fe_ks_status batch_build(fe_ks_batch* b) {
   size_t smem = 0;
   size_t smem_cls[2] = {0, 0};
   for (int s = 0; s < ns; ++s) {
+    if (!b->direct.empty() && b->direct[s]) continue;   // applied by its own kernels, not from the queue
     const Ctx& c = b->ctxs[s]->c;
     const int ncols = (int)b->n_v[s];
     const int vt = vt_of(c.p, b->cfg[s]);
@@ -228,9 +235,9 @@ static fe_ks_status batch_build(fe_ks_batch* b) {
     for (auto& v : per_phase) items.insert(items.end(), v.begin(), v.end());
     if (!upload_items(items, &b->d_items)) return fail(FE_KS_ERR_OOM, "batch queue");
     b->n_items = (int)items.size();
-    b->smem = smem;
+    b->smem = std::max<size_t>(smem, 16);
     int per_sm = 0;
-    if (prepare_nt(b->nt, smem, b->blocks_per_sm, &per_sm) != cudaSuccess) {
+    if (prepare_nt(b->nt, b->smem, b->blocks_per_sm, &per_sm) != cudaSuccess) {
       cudaGetLastError();
       return fail(FE_KS_ERR_CUDA, "batched kernel shared memory / occupancy");
     }
@@ -361,12 +368,41 @@ fe_ks_status fe_ks_batch_apply(fe_ks_batch* b, const void* const* X, void* const
     P.sys[i].X = X[i];
     P.sys[i].Y = Y[i];
   }
+  // direct systems first: fork one side stream per system from the caller's stream
+  bool any_direct = false;
+  for (size_t i = 0; i < b->direct.size(); ++i) any_direct = any_direct || b->direct[i];
+  if (any_direct) {
+    if (cudaEventRecord(b->dfork, s) != cudaSuccess) return fail(FE_KS_ERR_CUDA, "batch fork event");
+    for (size_t i = 0; i < b->ctxs.size(); ++i) {
+      if (!b->direct[i]) continue;
+      Ctx& c = b->ctxs[i]->c;
+      if (cudaStreamWaitEvent(b->dstream[i], b->dfork, 0) != cudaSuccess) return fail(FE_KS_ERR_CUDA, "batch fork");
+      const cudaStream_t keep = c.stream;
+      c.stream = b->dstream[i];   // the context's own kernels, launched on the system's side stream
+      const fe_ks_status st =
+          b->prec[i] == FE_KS_F64
+              ? apply_core<double>(c, static_cast<const double*>(X[i]), static_cast<double*>(Y[i]), b->n_v[i], false,
+                                   1.0, true)
+              : apply_core<float>(c, static_cast<const float*>(X[i]), static_cast<float*>(Y[i]), b->n_v[i], false,
+                                  1.f, true);
+      c.stream = keep;
+      if (st != FE_KS_OK) return st;
+      if (cudaEventRecord(b->djoin[i], b->dstream[i]) != cudaSuccess) return fail(FE_KS_ERR_CUDA, "batch join event");
+    }
+  }
+  auto join_direct = [&]() -> fe_ks_status {
+    for (size_t i = 0; i < b->direct.size(); ++i)
+      if (b->direct[i] && cudaStreamWaitEvent(s, b->djoin[i], 0) != cudaSuccess)
+        return fail(FE_KS_ERR_CUDA, "batch join");
+    return FE_KS_OK;
+  };
+  if (b->n_items == 0) return join_direct();
   if (cudaMemsetAsync(b->d_state, 0, sizeof(int) * kStateWords, s) != cudaSuccess)
     return fail(FE_KS_ERR_CUDA, "reset of the batch counters failed");
   if (!batch_split(b)) {
     cudaError_t err = launch_nt(b->nt, P, b->grid, b->smem, b->blocks_per_sm, s);
     if (err != cudaSuccess) return fail(FE_KS_ERR_CUDA, std::string("batched kernel: ") + cudaGetErrorString(err));
-    return FE_KS_OK;
+    return join_direct();
   }
   // split: FP64 object on the caller's stream, FP32 object on the side stream, joined back
   cudaError_t err = cudaEventRecord(b->ev_fork, s);
@@ -383,7 +419,7 @@ fe_ks_status fe_ks_batch_apply(fe_ks_batch* b, const void* const* X, void* const
   if (err == cudaSuccess) err = cudaEventRecord(b->ev_join, b->side);
   if (err == cudaSuccess) err = cudaStreamWaitEvent(s, b->ev_join, 0);
   if (err != cudaSuccess) return fail(FE_KS_ERR_CUDA, std::string("batched class kernels: ") + cudaGetErrorString(err));
-  return FE_KS_OK;
+  return join_direct();
 }
 
 fe_ks_status fe_ks_batch_status(fe_ks_batch* b) {
@@ -391,7 +427,7 @@ fe_ks_status fe_ks_batch_status(fe_ks_batch* b) {
   int err = 0;
   if (cudaDeviceSynchronize() != cudaSuccess || cudaMemcpy(&err, b->d_state + 2, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
     return fail(FE_KS_ERR_CUDA, "reading the batch status failed");
-  if (err) return fail(FE_KS_ERR_TIMEOUT, "a batched work item waited longer than the configured limit");
+  if (err && b->n_items > 0) return fail(FE_KS_ERR_TIMEOUT, "a batched work item waited longer than the configured limit");
   return FE_KS_OK;
 }
 
@@ -419,8 +455,31 @@ fe_ks_status fe_ks_batch_set_split(fe_ks_batch* b, int threads_f64, int threads_
   return batch_build(b);
 }
 
+fe_ks_status fe_ks_batch_set_direct(fe_ks_batch* b, const int* direct) {
+  if (!b) return fail(FE_KS_ERR_ARG, "batch is NULL");
+  const size_t ns = b->ctxs.size();
+  if (direct && b->dstream.empty()) {
+    b->dstream.assign(ns, nullptr);
+    b->djoin.assign(ns, nullptr);
+    bool ok = cudaEventCreateWithFlags(&b->dfork, cudaEventDisableTiming) == cudaSuccess;
+    for (size_t i = 0; i < ns && ok; ++i)
+      ok = cudaStreamCreateWithFlags(&b->dstream[i], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&b->djoin[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) return fail(FE_KS_ERR_CUDA, "creating the direct systems' streams and events failed");
+  }
+  b->direct.assign(ns, 0);
+  if (direct)
+    for (size_t i = 0; i < ns; ++i) b->direct[i] = direct[i] != 0;
+  return batch_build(b);
+}
+
 void fe_ks_batch_destroy(fe_ks_batch* b) {
   if (!b) return;
+  for (size_t i = 0; i < b->dstream.size(); ++i) {
+    if (b->dstream[i]) cudaStreamDestroy(b->dstream[i]);
+    if (b->djoin[i]) cudaEventDestroy(b->djoin[i]);
+  }
+  if (b->dfork) cudaEventDestroy(b->dfork);
   for (int k = 0; k < 2; ++k)
     if (b->d_items_cls[k]) cudaFree(b->d_items_cls[k]);
   if (b->ev_fork) cudaEventDestroy(b->ev_fork);

@@ -85,6 +85,7 @@ def _load():
     lib.fe_ks_batch_apply.argtypes = [vp, P(vp), P(vp), vp]
     lib.fe_ks_batch_status.argtypes = [vp]
     lib.fe_ks_batch_set_split.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    lib.fe_ks_batch_set_direct.argtypes = [vp, P(ctypes.c_int)]
     lib.fe_ks_batch_info.argtypes = [vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_size_t)]
     lib.fe_ks_batch_destroy.argtypes = [vp]
     lib.fe_ks_batch_destroy.restype = None
@@ -293,6 +294,12 @@ def fe_ks_batch_apply(batch, Xs, Ys, stream=None):
 
 def fe_ks_batch_set_split(batch, threads_f64, threads_f32):
     _check(_lib.fe_ks_batch_set_split(batch, threads_f64, threads_f32))
+
+
+def fe_ks_batch_set_direct(batch, direct=None):
+    """Systems flagged in `direct` run their own tuned kernels on side streams (None: none)."""
+    arr = None if direct is None else (ctypes.c_int * len(direct))(*[int(bool(d)) for d in direct])
+    _check(_lib.fe_ks_batch_set_direct(batch, arr))
 
 
 def fe_ks_batch_status(batch):

@@ -229,3 +229,46 @@ def test_batched_rejects_complex_and_bad_arguments():
             fk.fe_ks_batch_create([ctx], [2], [fk.FE_KS_F64])
     finally:
         fk.fe_ks_destroy(ctx)
+
+
+@pytest.mark.parametrize("direct,split", [([1, 0, 0, 0, 0, 0], (0, 0)), ([0, 1, 0, 1, 0, 0], (0, 0)),
+                                          ([1] * 6, (0, 0)), ([0, 0, 1, 0, 0, 1], (256, 384))])
+def test_direct_systems_equal_individual_applications(batch_setup, direct, split):
+    """Direct systems run their own kernels on side streams beside the persistent launch of
+    the others (also with split mode, and with no system left in the queue)."""
+    wls, hps, ctxs, Xs, Ys, refs, b = batch_setup
+    fk.fe_ks_batch_configure(b, [(s // 2) % 2 for s in range(6)], 2, 2, 2.0, False)
+    fk.fe_ks_batch_set_split(b, *split)
+    fk.fe_ks_batch_set_direct(b, direct)
+    try:
+        for Y in Ys:
+            Y.fill_(float("nan"))
+        fk.fe_ks_batch_apply(b, Xs, Ys, torch.cuda.current_stream().cuda_stream)
+        fk.fe_ks_batch_status(b)
+        _check(Ys, refs)
+    finally:
+        fk.fe_ks_batch_set_direct(b, None)
+        fk.fe_ks_batch_set_split(b, 0, 0)
+
+
+def test_direct_systems_in_cuda_graph(batch_setup):
+    """The forked per-system streams and the persistent launch capture as one graph."""
+    wls, hps, ctxs, Xs, Ys, refs, b = batch_setup
+    fk.fe_ks_batch_configure(b, [1] * 6, 2, 2, 2.0, False)
+    fk.fe_ks_batch_set_direct(b, [1, 0, 1, 0, 0, 0])
+    try:
+        stream = torch.cuda.current_stream()
+        fk.fe_ks_batch_apply(b, Xs, Ys, stream.cuda_stream)      # warm-up outside capture
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fk.fe_ks_batch_apply(b, Xs, Ys, torch.cuda.current_stream().cuda_stream)
+        for _ in range(2):
+            for Y in Ys:
+                Y.fill_(float("nan"))
+            g.replay()
+            torch.cuda.synchronize()
+            fk.fe_ks_batch_status(b)
+            _check(Ys, refs)
+    finally:
+        fk.fe_ks_batch_set_direct(b, None)

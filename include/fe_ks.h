@@ -346,15 +346,21 @@ fe_ks_status fe_ks_colour_cells(int64_t n_cells, int32_t np3, int64_t n_dofs, co
 
 /*
  * Batched application: Y_s = H_s X_s for up to 16 independent systems of
- * uneven size, degree (4..8), vector count and precision in ONE persistent
- * kernel launch.  The work queue is phase-major -- zero-fill of every Y_s and
- * the per-atom projections first, then the cells of colour 0, 1, ... of every
+ * uneven size, degree, vector count and precision in ONE call.  Real FP64 /
+ * FP32 systems of degree 4..8 with n_q = n_p go to ONE persistent kernel
+ * launch: the work queue is phase-major -- zero-fill of every Y_s and the
+ * per-atom projections first, then the cells of colour 0, 1, ... of every
  * system -- and a work item of system s waits (bounded) for the completion of
- * s's previous phase only, so systems overlap freely.  Real operators only.
+ * s's previous phase only, so systems overlap freely.  Every other system
+ * (complex operators, n_q = n_p + 2, degrees 1..3, FE_KS_F64E / FE_KS_BF16 /
+ * FE_KS_F16 / FE_KS_BF16X2) is a direct system (fe_ks_batch_set_direct below):
+ * applied by its own kernels on a side stream, concurrently.
  *
  * fe_ks_batch_create builds the queue for the given contexts (owned by the
- * caller, must outlive the batch), vector counts and precisions (FE_KS_F64 /
- * FE_KS_F32); it allocates the queue and counters (the only allocation).
+ * caller, must outlive the batch), vector counts and precisions; it allocates
+ * the queue and counters (the only allocation), and the side streams when a
+ * system is direct.  X[s] and Y[s] of a complex system hold interleaved
+ * (re, im) columns, as for fe_ks_apply.
  * fe_ks_batch_configure sets the tunables -- tile configuration per system
  * (0/1: columns per tile), cells per work item, items claimed per fetch, resident CTAs per SM (1, or
  * 2 with a tighter register budget; 672-thread blocks run one per SM),

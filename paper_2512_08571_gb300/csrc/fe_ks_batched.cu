@@ -135,6 +135,7 @@ struct fe_ks_batch {
   // direct systems (fe_ks_batch_set_direct): applied by their own tuned cell kernels, each
   // on a side stream of its own, concurrently with the persistent launch of the others
   std::vector<int> direct;
+  std::vector<int> forced;   // systems the persistent routines do not cover: always direct
   std::vector<cudaStream_t> dstream;
   std::vector<cudaEvent_t> djoin;
   cudaEvent_t dfork = nullptr;
@@ -150,7 +151,9 @@ static fe_ks_status batch_build(fe_ks_batch* b) {
   const int ns = (int)b->ctxs.size();
   const bool split = batch_split(b);
   int max_ph = 0;
-  for (int s = 0; s < ns; ++s) max_ph = std::max<int>(max_ph, (int)b->ctxs[s]->c.colour_ptr.size() - 1 + 2);
+  for (int s = 0; s < ns; ++s)
+    if (b->direct.empty() || !b->direct[s])
+      max_ph = std::max<int>(max_ph, (int)b->ctxs[s]->c.colour_ptr.size() - 1 + 2);
   if (max_ph >= kMaxPhase) return fail(FE_KS_ERR_UNSUPPORTED, "too many colours for the batched launch");
   std::vector<std::vector<int4>> per_phase(max_ph + 1);
   std::vector<std::vector<int4>> per_phase_cls[2] = {std::vector<std::vector<int4>>(max_ph + 1),
@@ -247,6 +250,7 @@ static fe_ks_status batch_build(fe_ks_batch* b) {
   BatchParams& P = b->host;
   P = BatchParams{};
   for (int s = 0; s < ns; ++s) {
+    if (!b->direct.empty() && b->direct[s]) continue;
     const Ctx& c = b->ctxs[s]->c;
     BatchSys& d = P.sys[s];
     const bool f64 = b->prec[s] == FE_KS_F64;
@@ -296,22 +300,29 @@ fe_ks_status fe_ks_batch_create(fe_ks_ctx* const* ctxs, int n_sys, const int64_t
   if (!ctxs || !n_v || !precision || !out) return fail(FE_KS_ERR_ARG, "NULL argument");
   *out = nullptr;
   if (n_sys < 1 || n_sys > kMaxSys) return fail(FE_KS_ERR_ARG, "n_sys must be in 1..16");
+  std::vector<int> forced(n_sys, 0);
   for (int s = 0; s < n_sys; ++s) {
     if (!ctxs[s]) return fail(FE_KS_ERR_ARG, "NULL context");
     const Ctx& c = ctxs[s]->c;
-    if (c.cplx) return fail(FE_KS_ERR_UNSUPPORTED, "the batched launch supports real operators");
-    if (c.p < 4 || c.p > 8) return fail(FE_KS_ERR_UNSUPPORTED, "the batched launch supports degrees 4..8");
-    if (c.nq != c.np) return fail(FE_KS_ERR_UNSUPPORTED, "the batched launch supports n_q = n_p");
     if (n_v[s] < 1 || n_v[s] > c.n_v_max) return fail(FE_KS_ERR_ARG, "n_v out of range");
-    if (precision[s] != FE_KS_F64 && precision[s] != FE_KS_F32) return fail(FE_KS_ERR_ARG, "unknown precision");
-    if (c.colour_ptr.size() - 1 > (size_t)kMaxPhase - 1) return fail(FE_KS_ERR_UNSUPPORTED, "too many colours");
-    if (c.n_proj > 16) return fail(FE_KS_ERR_UNSUPPORTED, "n_proj > 16");
+    const int pr = precision[s];
+    if (pr != FE_KS_F64 && pr != FE_KS_F32 && pr != FE_KS_F64E && pr != FE_KS_BF16 && pr != FE_KS_F16 &&
+        pr != FE_KS_BF16X2)
+      return fail(FE_KS_ERR_ARG, "unknown precision");
+    if ((pr == FE_KS_BF16 || pr == FE_KS_F16 || pr == FE_KS_BF16X2) && c.nq != c.np)
+      return fail(FE_KS_ERR_UNSUPPORTED, "the tensor-core precisions need n_q = n_p");
+    // the persistent routines cover real FP64 / FP32 systems of degree 4..8 with n_q = n_p;
+    // every other system is applied by its own kernels on a side stream
+    forced[s] = c.cplx || c.p < 4 || c.p > 8 || c.nq != c.np || (pr != FE_KS_F64 && pr != FE_KS_F32) ||
+                c.colour_ptr.size() - 1 > (size_t)kMaxPhase - 3 || c.n_proj > 16;
   }
   auto* b = new fe_ks_batch();
   b->ctxs.assign(ctxs, ctxs + n_sys);
   b->n_v.assign(n_v, n_v + n_sys);
   b->prec.assign(precision, precision + n_sys);
   b->cfg.assign(n_sys, 0);
+  b->forced = forced;
+  b->direct = forced;
   b->stream = ctxs[0]->c.stream;
   cudaGetDevice(&b->device);
   cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
@@ -320,6 +331,16 @@ fe_ks_status fe_ks_batch_create(fe_ks_ctx* const* ctxs, int n_sys, const int64_t
     if (b->d_need) cudaFree(b->d_need);
     delete b;
     return fail(FE_KS_ERR_OOM, "batch state");
+  }
+  if (std::count(forced.begin(), forced.end(), 1) > 0) {
+    fe_ks_status st = fe_ks_batch_set_direct(b, nullptr);   // creates the side streams; keeps the forced flags
+    if (st != FE_KS_OK) {
+      std::string msg = fe_ks_last_error();
+      fe_ks_batch_destroy(b);
+      return fail(st, msg);
+    }
+    *out = b;
+    return FE_KS_OK;
   }
   fe_ks_status st = batch_build(b);
   if (st != FE_KS_OK) {
@@ -379,12 +400,16 @@ fe_ks_status fe_ks_batch_apply(fe_ks_batch* b, const void* const* X, void* const
       if (cudaStreamWaitEvent(b->dstream[i], b->dfork, 0) != cudaSuccess) return fail(FE_KS_ERR_CUDA, "batch fork");
       const cudaStream_t keep = c.stream;
       c.stream = b->dstream[i];   // the context's own kernels, launched on the system's side stream
+      const int64_t ncols = b->n_v[i] * (c.cplx ? 2 : 1);
+      const int pr = b->prec[i];
       const fe_ks_status st =
-          b->prec[i] == FE_KS_F64
-              ? apply_core<double>(c, static_cast<const double*>(X[i]), static_cast<double*>(Y[i]), b->n_v[i], false,
-                                   1.0, true)
-              : apply_core<float>(c, static_cast<const float*>(X[i]), static_cast<float*>(Y[i]), b->n_v[i], false,
-                                  1.f, true);
+          pr == FE_KS_F64    ? apply_core<double>(c, static_cast<const double*>(X[i]), static_cast<double*>(Y[i]), ncols,
+                                                  false, 1.0, true)
+          : pr == FE_KS_F64E ? apply_core_emu(c, static_cast<const double*>(X[i]), static_cast<double*>(Y[i]), ncols,
+                                              false, 1.0, true)
+                             : apply_core<float>(c, static_cast<const float*>(X[i]), static_cast<float*>(Y[i]), ncols,
+                                                 false, 1.f, true,
+                                                 pr == FE_KS_BF16 ? 1 : pr == FE_KS_F16 ? 2 : pr == FE_KS_BF16X2 ? 3 : 0);
       c.stream = keep;
       if (st != FE_KS_OK) return st;
       if (cudaEventRecord(b->djoin[i], b->dstream[i]) != cudaSuccess) return fail(FE_KS_ERR_CUDA, "batch join event");
@@ -458,7 +483,9 @@ fe_ks_status fe_ks_batch_set_split(fe_ks_batch* b, int threads_f64, int threads_
 fe_ks_status fe_ks_batch_set_direct(fe_ks_batch* b, const int* direct) {
   if (!b) return fail(FE_KS_ERR_ARG, "batch is NULL");
   const size_t ns = b->ctxs.size();
-  if (direct && b->dstream.empty()) {
+  bool want = false;
+  for (size_t i = 0; i < ns; ++i) want = want || (direct && direct[i]) || b->forced[i];
+  if (want && b->dstream.empty()) {
     b->dstream.assign(ns, nullptr);
     b->djoin.assign(ns, nullptr);
     bool ok = cudaEventCreateWithFlags(&b->dfork, cudaEventDisableTiming) == cudaSuccess;
@@ -468,8 +495,7 @@ fe_ks_status fe_ks_batch_set_direct(fe_ks_batch* b, const int* direct) {
     if (!ok) return fail(FE_KS_ERR_CUDA, "creating the direct systems' streams and events failed");
   }
   b->direct.assign(ns, 0);
-  if (direct)
-    for (size_t i = 0; i < ns; ++i) b->direct[i] = direct[i] != 0;
+  for (size_t i = 0; i < ns; ++i) b->direct[i] = (direct && direct[i] != 0) || b->forced[i];
   return batch_build(b);
 }
 

@@ -220,15 +220,63 @@ def test_split_batch_in_cuda_graph_and_timeout(batch_setup):
         fk.fe_ks_batch_configure(b, [0] * 6, 1, 1, 2.0, False)
 
 
-def test_batched_rejects_complex_and_bad_arguments():
-    wl = Workload("cx", L=6.0, n=2, p=4, nq=5, n_v=2, kfrac=(0.2, 0, 0), complex=True, seed=1)
-    hp = HostProblem(wl)
-    ctx = fk.fe_ks_setup(hp.struct, fk.TERM_ALL, 2, torch.cuda.current_stream().cuda_stream)
+def test_uncovered_systems_run_direct_in_the_batch():
+    """Systems the persistent routines do not cover -- a complex (Bloch) operator, n_q = n_p + 2,
+    degree 2, the pair-of-floats and 16-bit precisions -- are accepted and applied by their
+    own kernels on side streams, next to queue systems; each equals its own fe_ks_apply,
+    bit for bit (the same kernels on the same data), also inside a captured graph."""
+    stream = torch.cuda.current_stream().cuda_stream
+    spec = [  # (workload, precision)
+        (Workload("cx", L=6.0, n=2, p=4, nq=5, n_v=3, kfrac=(0.2, 0, 0), complex=True, gga=True, n_atoms=1,
+                  seed=11), fk.FE_KS_F64),
+        (Workload("q2", L=6.0, n=2, p=5, nq=8, n_v=4, gga=True, n_atoms=1, seed=12), fk.FE_KS_F32),
+        (Workload("d2", L=6.0, n=3, p=2, nq=3, n_v=5, gga=True, seed=13), fk.FE_KS_F64),
+        (Workload("ff", L=6.0, n=2, p=6, nq=7, n_v=4, gga=True, n_atoms=2, seed=14), fk.FE_KS_F64E),
+        (Workload("bf", L=6.0, n=2, p=8, nq=9, n_v=9, gga=True, n_atoms=2, seed=15), fk.FE_KS_BF16),
+        (Workload("qq", L=6.0, n=2, p=6, nq=7, n_v=6, gga=True, n_atoms=1, seed=16), fk.FE_KS_F32),   # queue
+        (Workload("q6", L=6.0, n=2, p=4, nq=5, n_v=3, gga=True, n_atoms=1, seed=17), fk.FE_KS_F64),   # queue
+    ]
+    hps = [HostProblem(wl) for wl, _ in spec]
+    ctxs = [fk.fe_ks_setup(hp.struct, fk.TERM_ALL, wl.n_v, stream) for hp, (wl, _) in zip(hps, spec)]
+    b = None
     try:
-        with pytest.raises(fk.FeKsError, match="real"):
-            fk.fe_ks_batch_create([ctx], [2], [fk.FE_KS_F64])
+        Xs, Ys, refs = [], [], []
+        for (wl, pr), ctx in zip(spec, ctxs):
+            X = torch.from_numpy(trial_vectors(wl)).cuda().to(torch_dtype(pr, wl.complex))
+            R = torch.empty_like(X)
+            fk.fe_ks_apply(ctx, X, R, wl.n_v, pr)
+            Xs.append(X)
+            Ys.append(torch.full_like(X, float("nan")))
+            refs.append(R)
+        b = fk.fe_ks_batch_create(ctxs, [wl.n_v for wl, _ in spec], [pr for _, pr in spec])
+        fk.fe_ks_batch_apply(b, Xs, Ys, stream)
+        fk.fe_ks_batch_status(b)
+        torch.cuda.synchronize()
+        for s, (Y, R) in enumerate(zip(Ys, refs)):
+            if s < 5:
+                assert torch.equal(Y, R), s
+            else:
+                err = parity_err(Y.double().cpu().numpy(), R.double().cpu().numpy())
+                assert err <= TOL[spec[s][1]], (s, err)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fk.fe_ks_batch_apply(b, Xs, Ys, torch.cuda.current_stream().cuda_stream)
+        for Y in Ys:
+            Y.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        fk.fe_ks_batch_status(b)
+        for s in range(5):
+            assert torch.equal(Ys[s], refs[s]), s
+        with pytest.raises(fk.FeKsError, match="ERR_ARG"):
+            fk.fe_ks_batch_create(ctxs[:1], [3], [99])
+        with pytest.raises(fk.FeKsError, match="n_q = n_p"):
+            fk.fe_ks_batch_create(ctxs[1:2], [4], [fk.FE_KS_BF16])
     finally:
-        fk.fe_ks_destroy(ctx)
+        if b is not None:
+            fk.fe_ks_batch_destroy(b)
+        for c in ctxs:
+            fk.fe_ks_destroy(c)
 
 
 @pytest.mark.parametrize("direct,split", [([1, 0, 0, 0, 0, 0], (0, 0)), ([0, 1, 0, 1, 0, 0], (0, 0)),

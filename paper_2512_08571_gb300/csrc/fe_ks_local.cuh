@@ -50,11 +50,49 @@ struct Num<ff2> {
   }
 };
 
+// Two FP32 columns in one 64-bit register: the packed FP32x2 instructions of
+// this architecture (add / sub / mul / fma .f32x2) do the two columns' work in
+// one issue slot, each half rounded exactly as its scalar instruction.
+struct f2v {
+  unsigned long long v;
+};
+__device__ __forceinline__ f2v f2v_make(float lo, float hi) {
+  f2v r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 f2v_split(f2v x) {
+  float lo, hi;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(x.v));
+  return make_float2(lo, hi);
+}
+__device__ __forceinline__ f2v operator+(f2v a, f2v b) {
+  f2v r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ f2v operator-(f2v a, f2v b) {
+  f2v r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ f2v operator*(float a, f2v b) {
+  f2v r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(f2v_make(a, a).v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ f2v fma(float a, f2v b, f2v c) {
+  f2v r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(f2v_make(a, a).v), "l"(b.v), "l"(c.v));
+  return r;
+}
+
 // y = M x for an NO x NI matrix with M[NO-1-o][NI-1-i] = S M[o][i], given its
 // even-odd split (see EOMat).  All indices are compile-time constants, so the
-// table entries are read straight from the kernel parameter bank.
-template <int NI, int NO, int S, typename T>
-__device__ __forceinline__ void eo_apply(const T* x, T* y, const EOMat<T>& m) {
+// table entries are read straight from the kernel parameter bank.  T is the
+// data type (also f2v: two FP32 columns at once), TM the matrix entries' type.
+template <int NI, int NO, int S, typename T, typename TM>
+__device__ __forceinline__ void eo_apply(const T* x, T* y, const EOMat<TM>& m) {
   constexpr int HI = NI / 2, HO = NO / 2;
   T xe[HI], xo[HI];
 #pragma unroll
@@ -87,6 +125,47 @@ __device__ __forceinline__ void eo_apply(const T* x, T* y, const EOMat<T>& m) {
       for (int i = 1; i < HI; ++i) ym = fma(m.MID[i], xo[i], ym);
     }
     y[HO] = ym;
+  }
+}
+
+// eo_apply for each of a thread's VPT columns: x[VPT][NI] -> o[NO][VPT]
+// (O_COL_MAJOR false) or o[VPT][NO] (true).  FP32 columns go two at a time
+// through the packed FP32x2 instructions; the results are bit for bit those
+// of the per-column scalar form.
+template <int NI, int NO, int S, bool O_COL_MAJOR = false, typename T, int VPT, typename TO>
+__device__ __forceinline__ void eo_apply_cols(const T (&x)[VPT][NI], TO& o, const EOMat<T>& m) {
+  if constexpr (std::is_same<T, float>::value && VPT % 2 == 0) {
+#pragma unroll
+    for (int u = 0; u < VPT; u += 2) {
+      f2v xx[NI], tt[NO];
+#pragma unroll
+      for (int k = 0; k < NI; ++k) xx[k] = f2v_make(x[u][k], x[u + 1][k]);
+      eo_apply<NI, NO, S>(xx, tt, m);
+#pragma unroll
+      for (int q = 0; q < NO; ++q) {
+        const float2 r = f2v_split(tt[q]);
+        if constexpr (O_COL_MAJOR) {
+          o[u][q] = r.x;
+          o[u + 1][q] = r.y;
+        } else {
+          o[q][u] = r.x;
+          o[q][u + 1] = r.y;
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < VPT; ++u) {
+      T t[NO];
+      eo_apply<NI, NO, S>(x[u], t, m);
+#pragma unroll
+      for (int q = 0; q < NO; ++q) {
+        if constexpr (O_COL_MAJOR)
+          o[u][q] = t[q];
+        else
+          o[q][u] = t[q];
+      }
+    }
   }
 }
 
@@ -502,12 +581,7 @@ __device__ __forceinline__ void tile_body_v(const Prm& p, const EOTables<T>& tb,
       for (int u = 0; u < VPT; ++u) x[u][k] = c[u];
     }
     T o[NQ][VPT];
-#pragma unroll
-    for (int u = 0; u < VPT; ++u) {
-      eo_apply<NP, NQ, 1>(x[u], t, tb.N);
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) o[q][u] = t[q];
-    }
+    eo_apply_cols<NP, NQ, 1>(x, o, tb.N);
 #pragma unroll
     for (int q = 0; q < NQ; ++q) st_cols<T, VPT>(A + i * SX + j * SY + q * SZ + v0, o[q]);
   }
@@ -526,12 +600,7 @@ __device__ __forceinline__ void tile_body_v(const Prm& p, const EOTables<T>& tb,
 #pragma unroll
       for (int u = 0; u < VPT; ++u) x[u][jj] = c[u];
     }
-#pragma unroll
-    for (int u = 0; u < VPT; ++u) {
-      eo_apply<NP, NQ, 1>(x[u], t, tb.N);
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) o[q][u] = t[q];
-    }
+    eo_apply_cols<NP, NQ, 1>(x, o, tb.N);
 #pragma unroll
     for (int q = 0; q < NQ; ++q) st_cols<T, VPT>(A + i * SX + q * SY + qz * SZ + v0, o[q]);
   }
@@ -549,12 +618,7 @@ __device__ __forceinline__ void tile_body_v(const Prm& p, const EOTables<T>& tb,
 #pragma unroll
       for (int u = 0; u < VPT; ++u) x[u][ii] = c[u];
     }
-#pragma unroll
-    for (int u = 0; u < VPT; ++u) {
-      eo_apply<NP, NQ, 1>(x[u], t, tb.N);
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) o[q][u] = t[q];
-    }
+    eo_apply_cols<NP, NQ, 1>(x, o, tb.N);
 #pragma unroll
     for (int q = 0; q < NQ; ++q) st_cols<T, VPT>(A + q * SX + qy * SY + qz * SZ + v0, o[q]);
   }
@@ -572,12 +636,7 @@ __device__ __forceinline__ void tile_body_v(const Prm& p, const EOTables<T>& tb,
 #pragma unroll
       for (int u = 0; u < VPT; ++u) x[u][r] = c[u];
     }
-#pragma unroll
-    for (int u = 0; u < VPT; ++u) {
-      eo_apply<NQ, NQ, -1>(x[u], t, tb.D);
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) o[q][u] = t[q];
-    }
+    eo_apply_cols<NQ, NQ, -1>(x, o, tb.D);
 #pragma unroll
     for (int q = 0; q < NQ; ++q) st_cols<T, VPT>(B + q * SX + a0 * SY + qz * SZ + v0, o[q]);
 #pragma unroll
@@ -587,12 +646,7 @@ __device__ __forceinline__ void tile_body_v(const Prm& p, const EOTables<T>& tb,
 #pragma unroll
       for (int u = 0; u < VPT; ++u) x[u][r] = c[u];
     }
-#pragma unroll
-    for (int u = 0; u < VPT; ++u) {
-      eo_apply<NQ, NQ, -1>(x[u], t, tb.D);
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) o[q][u] = t[q];
-    }
+    eo_apply_cols<NQ, NQ, -1>(x, o, tb.D);
 #pragma unroll
     for (int q = 0; q < NQ; ++q) st_cols<T, VPT>(C + a0 * SX + q * SY + qz * SZ + v0, o[q]);
   }
@@ -610,8 +664,7 @@ __device__ __forceinline__ void tile_body_v(const Prm& p, const EOTables<T>& tb,
 #pragma unroll
       for (int u = 0; u < VPT; ++u) u_[u][q] = c[u];
     }
-#pragma unroll
-    for (int u = 0; u < VPT; ++u) eo_apply<NQ, NQ, -1>(u_[u], g_[u], tb.D);
+    eo_apply_cols<NQ, NQ, -1, true>(u_, g_, tb.D);
     const T* cf = cfs + qx + NQ * qy;
 #pragma unroll
     for (int qz = 0; qz < NQ; ++qz) {
@@ -661,13 +714,12 @@ __device__ __forceinline__ void tile_body_v(const Prm& p, const EOTables<T>& tb,
       st_cols<T, VPT>(B + s, w0);
       st_cols<T, VPT>(C + s, w1);
     }
-    T t[NQ], o[NQ][VPT];
+    T o[NQ][VPT];
+    eo_apply_cols<NQ, NQ, -1>(u_, o, tb.Dt);
 #pragma unroll
-    for (int u = 0; u < VPT; ++u) {
-      eo_apply<NQ, NQ, -1>(u_[u], t, tb.Dt);
+    for (int u = 0; u < VPT; ++u)
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) o[q][u] = z_[u][q] + t[q];
-    }
+      for (int q = 0; q < NQ; ++q) o[q][u] = z_[u][q] + o[q][u];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) st_cols<T, VPT>(A + qx * SX + qy * SY + q * SZ + v0, o[q]);
   }
@@ -685,12 +737,7 @@ __device__ __forceinline__ void tile_body_v(const Prm& p, const EOTables<T>& tb,
 #pragma unroll
       for (int u = 0; u < VPT; ++u) x[u][r] = c[u];
     }
-#pragma unroll
-    for (int u = 0; u < VPT; ++u) {
-      eo_apply<NQ, NQ, -1>(x[u], t, tb.Dt);
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) o[q][u] = t[q];
-    }
+    eo_apply_cols<NQ, NQ, -1>(x, o, tb.Dt);
 #pragma unroll
     for (int q = 0; q < NQ; ++q) st_cols<T, VPT>(B + q * SX + a0 * SY + qz * SZ + v0, o[q]);
 #pragma unroll
@@ -700,12 +747,7 @@ __device__ __forceinline__ void tile_body_v(const Prm& p, const EOTables<T>& tb,
 #pragma unroll
       for (int u = 0; u < VPT; ++u) x[u][r] = c[u];
     }
-#pragma unroll
-    for (int u = 0; u < VPT; ++u) {
-      eo_apply<NQ, NQ, -1>(x[u], t, tb.Dt);
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) o[q][u] = t[q];
-    }
+    eo_apply_cols<NQ, NQ, -1>(x, o, tb.Dt);
 #pragma unroll
     for (int q = 0; q < NQ; ++q) st_cols<T, VPT>(C + a0 * SX + q * SY + qz * SZ + v0, o[q]);
   }
@@ -726,12 +768,7 @@ __device__ __forceinline__ void tile_body_v(const Prm& p, const EOTables<T>& tb,
 #pragma unroll
       for (int u = 0; u < VPT; ++u) zc[u][q] = a[u] + (b[u] + c[u]);
     }
-#pragma unroll
-    for (int u = 0; u < VPT; ++u) {
-      eo_apply<NQ, NP, 1>(zc[u], t, tb.Nt);
-#pragma unroll
-      for (int k = 0; k < NP; ++k) o[k][u] = t[k];
-    }
+    eo_apply_cols<NQ, NP, 1>(zc, o, tb.Nt);
 #pragma unroll
     for (int k = 0; k < NP; ++k) st_cols<T, VPT>(A + qx * SX + qy * SY + k * SZ + v0, o[k]);
   }
@@ -749,12 +786,7 @@ __device__ __forceinline__ void tile_body_v(const Prm& p, const EOTables<T>& tb,
 #pragma unroll
       for (int u = 0; u < VPT; ++u) x[u][q] = c[u];
     }
-#pragma unroll
-    for (int u = 0; u < VPT; ++u) {
-      eo_apply<NQ, NP, 1>(x[u], t, tb.Nt);
-#pragma unroll
-      for (int jj = 0; jj < NP; ++jj) o[jj][u] = t[jj];
-    }
+    eo_apply_cols<NQ, NP, 1>(x, o, tb.Nt);
 #pragma unroll
     for (int jj = 0; jj < NP; ++jj) st_cols<T, VPT>(A + qx * SX + jj * SY + k * SZ + v0, o[jj]);
   }
@@ -772,8 +804,7 @@ __device__ __forceinline__ void tile_body_v(const Prm& p, const EOTables<T>& tb,
 #pragma unroll
       for (int u = 0; u < VPT; ++u) x[u][q] = c[u];
     }
-#pragma unroll
-    for (int u = 0; u < VPT; ++u) eo_apply<NQ, NP, 1>(x[u], y[u], tb.Nt);
+    eo_apply_cols<NQ, NP, 1, true>(x, y, tb.Nt);
     if (p.cell_pair_ptr) {
       const int pb = p.cell_pair_ptr[e], pe = p.cell_pair_ptr[e + 1];
       for (int pi = pb; pi < pe; ++pi) {

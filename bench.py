@@ -1136,8 +1136,9 @@ def detail_sections(args, wl, res, world):
                                                 / (bf["ms"] * 1e-3),
                          "mma_sync_live_probe_tflops": (res["peak_mma_live"] or 0) / 1e12},
             "clocks": bf["clocks"], "gpu_launches": bf["launches"]}
-        tcgen05 = key in ("bf16", "f16") and bf.get("tile_config") == 0 and not wl.complex and wl.nq == wl.p + 1
-        detail[name]["kernel"] = ("tcgen05 (plane and z-sweep products, tile configuration 0)" if tcgen05 else
+        tcgen05 = key in ("bf16", "f16") and bf.get("tile_config") != 1 and not wl.complex and wl.nq == wl.p + 1
+        detail[name]["kernel"] = (f"tcgen05 (plane and z-sweep products, tile configuration {bf.get('tile_config')})"
+                                  if tcgen05 else
                                   "warp-level mma.sync (one sweep per direction)")
         detail[name]["tile_config"] = bf.get("tile_config")
         detail[name]["tune_ms_per_config"] = [t for t in bf.get("tune_ms", []) if t > 0]

@@ -247,12 +247,14 @@ fe_ks_status fe_ks_cheb_filter_ghep(fe_ks_ctx* ctx, fe_ks_ctx* mass, double* X, 
 
 /*
  * Tile configuration of the fused cell kernel.  FE_KS_BF16 and FE_KS_F16 (real
- * operators, n_q = n_p): 0 = the 5th-generation tensor-core kernel (tcgen05:
- * the x-y plane products and the z sweeps of Algorithm 2 as four MMA chains
- * per cell and 4-vector tile, two pipelines per CTA, accumulators in tensor
- * memory; the default),
- * 1 = the warp-level MMA kernel (one sweep per direction); complex operators
- * and FE_KS_BF16X2 have the warp-level kernel only.  FE_KS_F64, FE_KS_F32,
+ * operators, n_q = n_p): 0, 2, 3 = the 5th-generation tensor-core kernel
+ * (tcgen05: the x-y plane products and the z sweeps of Algorithm 2 as four MMA
+ * chains per cell and 4-vector tile, two pipelines per CTA, accumulators in
+ * tensor memory), its second pipeline starting each work unit after the first
+ * one's first plane product (0, the default), at once (2) or after its first
+ * quadrature-point step (3); 1 = the warp-level MMA kernel (one sweep per
+ * direction).  Complex operators and FE_KS_BF16X2 have the warp-level kernel
+ * only.  FE_KS_F64, FE_KS_F32,
  * FE_KS_F64E:
  *   0..2  one CTA per (cell, column tile), 3 tile widths;
  *   3..4  one CTA per cell walking all column tiles, the next tile's rows of X

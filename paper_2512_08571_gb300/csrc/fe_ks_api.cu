@@ -199,11 +199,12 @@ int* config_slot(Ctx& c, int prec) {
 }
 
 // tile configurations of a precision: 10 for the CUDA-core kernels; the BF16 and
-// FP16 cell kernels have two (0 = tcgen05, 1 = warp-level MMA) where the tcgen05
-// kernel serves the context (real, n_q = n_p), else one
+// FP16 cell kernels have four (1 = warp-level MMA; 0, 2, 3 = tcgen05 with its two
+// pipelines staggered by a point of the tile) where the tcgen05 kernel serves the
+// context (real, n_q = n_p), else one
 static int n_configs(const Ctx& c, int prec) {
   if (prec == FE_KS_F64 || prec == FE_KS_F32 || prec == FE_KS_F64E) return kLocalConfigs;
-  if (prec == FE_KS_BF16 || prec == FE_KS_F16) return (!c.cplx && c.nq == c.np && c.tc5_cst) ? 2 : 1;
+  if (prec == FE_KS_BF16 || prec == FE_KS_F16) return (!c.cplx && c.nq == c.np && c.tc5_cst) ? 4 : 1;
   return 1;
 }
 
@@ -736,7 +737,7 @@ fe_ks_status apply_core(Ctx& c, const T* X, T* Y, int64_t ncols, bool scaled, T 
     cudaError_t err;
     if constexpr (std::is_same<T, float>::value)
       err = !tc ? launch_local<T, T>(c, lp, s)   // tc: n_q = n_p, checked above
-            : use_tc5(c, tc) ? launch_tc5(c, lp, s, tc == 2)
+            : use_tc5(c, tc) ? launch_tc5(c, lp, s, tc == 2, tc5_stagger(c.cfg_tc[tc - 1]))
                              : launch_tc(c, lp, s, tc);
     else
       err = launch_local<T, T>(c, lp, s);

@@ -105,7 +105,8 @@ struct Ctx {
   int cplx = 0, terms = 0, gga = 0, ncoef = 0;
   int cfg64 = 0, cfg32 = 0, cfgE = 0;   // tile configuration of the fused kernel per precision
   int rr_gram_tc = 1;                   // Rayleigh-Ritz Gram products on the tensor cores (pairs plan)
-  int cfg_tc[2] = {0, 0};               // BF16, FP16 cell kernel: 0 = tcgen05 (where supported), 1 = warp-level MMA
+  int cfg_tc[2] = {0, 0};               // BF16, FP16 cell kernel: 1 = warp-level MMA; 0, 2, 3 = tcgen05 (where
+                                        // supported) with its two pipelines staggered by a point of the tile
   bool cfg_explicit[6] = {};            // set by fe_ks_set_config / fe_ks_tune, per precision
   int64_t E = 0, m = 0, n_v_max = 0;
   int n_atoms = 0, n_proj = 0;
@@ -223,11 +224,13 @@ cudaError_t launch_proj_pairs_emu(const Ctx& c, const ProjParams<double>& prm, c
 cudaError_t launch_tc(const Ctx& c, const LocalParams<float>& lp, cudaStream_t s, int tc);
 size_t tc_smem_bytes(int n, bool cplx);
 // tcgen05 cell kernel (fe_ks_tc5.cu): real operators, n_q = n_p; f16 selects FP16 operands
-cudaError_t launch_tc5(const Ctx& c, const LocalParams<float>& lp, cudaStream_t s, bool f16);
+cudaError_t launch_tc5(const Ctx& c, const LocalParams<float>& lp, cudaStream_t s, bool f16, int stagger);
 void build_tc5_const(int p, bool f16, std::vector<uint4>& out);
+// stagger point of the tcgen05 kernel's two pipelines for a 16-bit tile configuration (0, 2, 3)
+inline int tc5_stagger(int cfg) { return cfg == 2 ? 0 : cfg == 3 ? 2 : 1; }
 // true when the tcgen05 kernel serves this context and precision (tc: 1 = BF16, 2 = FP16)
 inline bool use_tc5(const Ctx& c, int tc) {
-  return (tc == 1 || tc == 2) && c.cfg_tc[tc - 1] == 0 && !c.cplx && c.nq == c.np && c.tc5_cst && c.tc5_cst16;
+  return (tc == 1 || tc == 2) && c.cfg_tc[tc - 1] != 1 && !c.cplx && c.nq == c.np && c.tc5_cst && c.tc5_cst16;
 }
 
 }  // namespace feks

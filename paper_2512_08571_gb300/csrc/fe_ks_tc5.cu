@@ -251,6 +251,8 @@ struct Params {
   const uint4* cst;      // the constant block (KM, B2, B3) in shared-memory layout
   int units_per_cell;    // a cell's column tiles are split into this many work units
   int tiles_per_unit;
+  int stagger;           // pipeline 1 starts a unit once pipeline 0 has passed: 0 no point,
+                         // 1 its first GEMM1, 2 its first quadrature-point step
   int* err;              // set to 1 when a bounded wait expires
 };
 
@@ -265,6 +267,10 @@ __device__ __forceinline__ bool gsync_or(int g, bool c) {
       : "memory");
   return r != 0;
 }
+
+// barrier 3: pipeline 0 arrives (256 threads), pipeline 1 waits (256 threads)
+__device__ __forceinline__ void stagger_arrive() { asm volatile("bar.arrive 3, 512;\n" ::: "memory"); }
+__device__ __forceinline__ void stagger_wait() { asm volatile("bar.sync 3, 512;\n" ::: "memory"); }
 
 template <int N, bool F16>
 __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ Params p) {
@@ -406,6 +412,11 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
     const int nqrows = (pe - pb) * p.n_proj;
     const bool qstaged = nqrows <= G::QCAP && pe - pb <= G::PCAP;
     bool have_next = false;   // xn already holds this tile's rows (loaded during the previous tile)
+    // offset the two pipelines within the unit: pipeline 1 waits until pipeline 0 has passed
+    // the stagger point of its first tile (pipeline 0 always has one; it arrives exactly once,
+    // also when its wait fails, so the barrier always completes)
+    bool arrived = p.stagger == 0 || g == 1;
+    if (p.stagger != 0 && g == 1) stagger_wait();
 
     // this pipeline's column tiles of the unit: every other one
     for (int t = t_begin + g; t < t_end; t += 2) {
@@ -487,7 +498,12 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
                 dXS + (uint64_t)((ks * 256) >> 4), ID1, ks > 0);
         commit(mbar);
       }
-      if (!wait_products()) break;
+      const bool ok1 = wait_products();
+      if (!arrived && (p.stagger == 1 || !ok1)) {
+        stagger_arrive();
+        arrived = true;
+      }
+      if (!ok1) break;
       if (qstaged && gt < nqrows) reinterpret_cast<float4*>(qs)[gt] = qreg;
       // (3) GEMM1 rows (t, p') -> A2 rows v + 4 p', k = 16 t + c; one GEMM1 tile per warp half
       if (sub < G::MT1) {
@@ -580,6 +596,10 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
           pointwise(it >> 1, std::integral_constant<int, 1>{});
         else
           pointwise(it >> 1, std::integral_constant<int, 0>{});
+      }
+      if (!arrived) {   // stagger point 2: after the first quadrature-point step
+        stagger_arrive();
+        arrived = true;
       }
       // this pipeline's next column tile's rows of X, in flight during the rest of this tile
       have_next = t + 2 < t_end;
@@ -740,6 +760,7 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
         }
       }
     }
+    if (!arrived) stagger_arrive();   // pipeline 0 left the unit before its stagger point
     if (__syncthreads_or(failed)) {
       failed = true;
       break;
@@ -862,7 +883,7 @@ void build_tc5_const(int p, bool f16, std::vector<uint4>& out) {
   }
 }
 
-cudaError_t launch_tc5(const Ctx& c, const LocalParams<float>& lp, cudaStream_t s, bool f16) {
+cudaError_t launch_tc5(const Ctx& c, const LocalParams<float>& lp, cudaStream_t s, bool f16, int stagger) {
   tc5::Params p{};
   p.X = lp.X;
   p.Y = lp.Y;
@@ -883,6 +904,7 @@ cudaError_t launch_tc5(const Ctx& c, const LocalParams<float>& lp, cudaStream_t 
   p.n_proj = lp.n_proj;
   p.alpha = lp.alpha;
   p.cst = f16 ? c.tc5_cst16 : c.tc5_cst;
+  p.stagger = stagger;
   p.err = c.dev_status;
   if (!p.cst || !p.err || c.cplx || c.nq != c.np) return cudaErrorInvalidValue;
   switch (c.np) {

@@ -59,9 +59,12 @@ def apply_status(hp, X, prec, config, scaled=False, terms=fk.TERM_ALL):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("config", [0, 1])
+@pytest.mark.parametrize("config", [0, 1, 2, 3])
 @pytest.mark.parametrize("key", list(SMALL))
 def test_both_kernels_match_oracle(cases, key, config, prec):
+    """Configurations 0, 2, 3: the tcgen05 kernel with its pipelines staggered after the
+    first plane product, not at all, after the first quadrature-point step; 1: the
+    warp-level one."""
     wl, hp, P, X = cases[key]
     Xin = round_input(X, prec)
     Y, status = apply_status(hp, Xin, prec, config)
@@ -136,7 +139,7 @@ def test_tcgen05_f16_column_scaling_range(cases, scale):
 
 
 def test_configuration_interface(cases):
-    """Real n_q = n_p contexts: two BF16/FP16 configurations, tcgen05 the default,
+    """Real n_q = n_p contexts: four BF16/FP16 configurations, tcgen05 the default,
     the tuner times both; complex contexts have the warp-level kernel only."""
     wl, hp, P, X = cases["C4s"]
     n_v = X.shape[1]
@@ -145,11 +148,11 @@ def test_configuration_interface(cases):
         assert fk.fe_ks_get_config(ctx, fk.FE_KS_BF16) == 0
         assert fk.fe_ks_get_config(ctx, fk.FE_KS_F16) == 0
         with pytest.raises(fk.FeKsError):
-            fk.fe_ks_set_config(ctx, fk.FE_KS_BF16, 2)
+            fk.fe_ks_set_config(ctx, fk.FE_KS_BF16, 4)
         Xd = torch.from_numpy(round_input(X, fk.FE_KS_BF16)).to("cuda").float()
         Yd = torch.empty_like(Xd)
         best, ms = fk.fe_ks_tune(ctx, Xd, Yd, n_v, fk.FE_KS_BF16, reps=1)
-        assert best in (0, 1) and ms[0] > 0 and ms[1] > 0 and all(m == -1.0 for m in ms[2:])
+        assert best in (0, 1, 2, 3) and all(m > 0 for m in ms[:4]) and all(m == -1.0 for m in ms[4:])
         assert fk.fe_ks_get_config(ctx, fk.FE_KS_BF16) == best
     finally:
         fk.fe_ks_destroy(ctx)

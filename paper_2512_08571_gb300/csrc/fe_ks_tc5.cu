@@ -352,6 +352,25 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
     fence_before();
     gsync(g);
   };
+  // a bounded wait whose outcome is combined at the next pipe_sync_or instead of its own
+  // barrier: a thread whose wait expired only moves stale tensor-memory values into shared
+  // buffers that the failed tile never uses (the wait before the scatter keeps its own check)
+  bool expired = false;
+  auto wait_local = [&]() {
+    if (!mbar_wait(mbar, phase)) expired = true;
+    phase ^= 1u;
+    fence_after();
+  };
+  auto pipe_sync_or = [&]() -> bool {   // pipe_sync, and whether any thread's wait expired
+    fence_async_smem();
+    fence_before();
+    if (gsync_or(g, expired)) {
+      failed = true;
+      failed_phase = phase ^ 1u;
+      return false;
+    }
+    return true;
+  };
   // this thread's gathered nodes of column tile [cx, cx + 4) and their D^{-1/2}
   // (registers; nothing waits on the loads until the tile's gather)
   float xn[GPT][VT], xs[GPT];
@@ -498,12 +517,11 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
                 dXS + (uint64_t)((ks * 256) >> 4), ID1, ks > 0);
         commit(mbar);
       }
-      const bool ok1 = wait_products();
-      if (!arrived && (p.stagger == 1 || !ok1)) {
+      wait_local();
+      if (!arrived && p.stagger == 1) {
         stagger_arrive();
         arrived = true;
       }
-      if (!ok1) break;
       if (qstaged && gt < nqrows) reinterpret_cast<float4*>(qs)[gt] = qreg;
       // (3) GEMM1 rows (t, p') -> A2 rows v + 4 p', k = 16 t + c; one GEMM1 tile per warp half
       if (sub < G::MT1) {
@@ -530,7 +548,7 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
           }
         }
       }
-      pipe_sync();
+      if (!pipe_sync_or()) break;
       // (4) GEMM2: the z sweep
       if (gt == 0) {
         fence_after();
@@ -542,7 +560,7 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
                 dB2 + (uint64_t)((ks * 2 * G::N2 * 16) >> 4), ID2, ks > 0);
         commit(mbar);
       }
-      if (!wait_products()) break;
+      wait_local();
       // (5) quadrature-point step: (Y0, Y_x, Y_y, Y_z)[c'] -> (Z, W_x, W_y, W_z)[c'] (A3, k = 4 c' + q);
       //     items (tile, half of the c' range)
       auto pointwise = [&](int T, auto H) {
@@ -604,7 +622,7 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
       // this pipeline's next column tile's rows of X, in flight during the rest of this tile
       have_next = t + 2 < t_end;
       if (have_next) load_x(col0 + 2 * VT);
-      pipe_sync();
+      if (!pipe_sync_or()) break;
       // (6) GEMM3: the transposed z sweep
       if (gt == 0) {
         fence_after();
@@ -616,7 +634,7 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
                 dB3 + (uint64_t)((ks * 2 * G::N3C * 16) >> 4), ID3, ks > 0);
         commit(mbar);
       }
-      if (!wait_products()) break;
+      wait_local();
       // (7) GEMM3 rows v + 4 p', columns 16 t + c -> B4 [(t, p')][c + 16 v] (MN-major);
       //     items (tile, half of the chunks)
 #pragma unroll 1
@@ -645,7 +663,7 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
       // finite: zero it, as the buffer held other products' data
       for (int i = gt; i < (G::K4 - G::R1) * (G::N4 / 8); i += GT)
         st16(sAB + (G::R1 + i / (G::N4 / 8)) * 16 + (i % (G::N4 / 8)) * G::SBO4, 0u, 0u, 0u, 0u);
-      pipe_sync();
+      if (!pipe_sync_or()) break;
       // (8) GEMM4: the transposed plane product
       if (gt == 0) {
         fence_after();

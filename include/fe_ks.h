@@ -294,6 +294,17 @@ fe_ks_status fe_ks_get_config(const fe_ks_ctx* ctx, int precision, int* config);
 fe_ks_status fe_ks_device_status(fe_ks_ctx* ctx, int* status);
 
 /*
+ * Host-side fault injection for tests of the failure path (no GPU fault):
+ * kind = 1 makes every later launch of the tcgen05 cell kernel on ctx skip the
+ * issue and the commit of each pipeline's first plane product, with a short
+ * wait limit; the pipelines' bounded waits then expire, the CTAs stop, free
+ * their tensor memory and set the device status word (fe_ks_device_status
+ * reports 1), and the application's Y is not valid.  kind = 0 turns it off;
+ * the context stays usable.  FE_KS_ERR_ARG for another kind.
+ */
+fe_ks_status fe_ks_inject_fault(fe_ks_ctx* ctx, int kind);
+
+/*
  * Cell-matrix (CM) baseline: the method the paper's matrix-free algorithms
  * are measured against (Sec. 3, eq. HX with precomputed H^(e)).  Real
  * operators only.

@@ -976,6 +976,14 @@ fe_ks_status fe_ks_device_status(fe_ks_ctx* ctx, int* status) {
   return FE_KS_OK;
 }
 
+fe_ks_status fe_ks_inject_fault(fe_ks_ctx* ctx, int kind) {
+  g_last_error.clear();
+  if (!ctx) return fail(FE_KS_ERR_ARG, "ctx is NULL");
+  if (kind != 0 && kind != 1) return fail(FE_KS_ERR_ARG, "kind must be 0 (off) or 1");
+  ctx->c.inject_fault = kind;
+  return FE_KS_OK;
+}
+
 fe_ks_status fe_ks_apply_scaled(fe_ks_ctx* ctx, const void* X, void* Y, int64_t n_v, int precision) {
   if (precision == FE_KS_F64) return apply_impl<double>(ctx, X, Y, n_v, true);
   if (precision == FE_KS_F64E) return apply_impl<ff2>(ctx, X, Y, n_v, true);

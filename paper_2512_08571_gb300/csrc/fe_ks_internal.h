@@ -144,6 +144,7 @@ struct Ctx {
   uint4* tc5_cst = nullptr;        // tcgen05 cell kernel: plane and z-sweep operators, BF16 (real, n_q = n_p)
   uint4* tc5_cst16 = nullptr;      // the same in FP16
   int* dev_status = nullptr;       // device word: 1 after a bounded wait in a cell kernel expired
+  int inject_fault = 0;            // host-side fault injection into the tcgen05 cell kernel (tests)
   std::vector<void*> allocations;
   // host-buffer pipeline (fe_ks_apply_host): copy-in and copy-out streams and,
   // per workspace slot, events for "X copied in", "applied", "Y copied out"

@@ -129,7 +129,8 @@ struct G5 {
   static_assert(BYTES <= 232448, "shared memory");
 };
 
-constexpr long long kWaitIters = 1LL << 22;   // bound of an mbarrier wait (try_wait polls)
+constexpr int kWaitIters = 1 << 22;           // bound of an mbarrier wait (try_wait polls)
+constexpr int kWaitItersInjected = 1 << 12;   // the same under host-side fault injection
 
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = 0;
@@ -178,9 +179,9 @@ __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::aft
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
 // bounded wait for phase `parity` of the mbarrier; false on expiry
-__device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity, int iters = kWaitIters) {
   uint32_t done = 0;
-  for (long long it = 0; it < kWaitIters && !done; ++it) {
+  for (int it = 0; it < iters && !done; ++it) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(done)
@@ -253,6 +254,8 @@ struct Params {
   int tiles_per_unit;
   int stagger;           // pipeline 1 starts a unit once pipeline 0 has passed: 0 no point,
                          // 1 its first GEMM1, 2 its first quadrature-point step
+  int inject;            // host-side fault injection: each pipeline's first GEMM1 is neither
+                         // issued nor committed, so its waits (short limit) expire
   int* err;              // set to 1 when a bounded wait expires
 };
 
@@ -334,10 +337,11 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
   uint32_t phase = 0, failed_phase = 0;
   bool failed = false;
   int staged = -1;
+#define FEKS_TC5_WAIT_ITERS (p.inject ? kWaitItersInjected : kWaitIters)
 
   // the pipeline's threads: bounded wait for the products just committed; uniform result
   auto wait_products = [&]() -> bool {
-    const bool ok = mbar_wait(mbar, phase);
+    const bool ok = mbar_wait(mbar, phase, FEKS_TC5_WAIT_ITERS);
     if (gsync_or(g, !ok)) {
       failed = true;
       failed_phase = phase;
@@ -357,7 +361,7 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
   // buffers that the failed tile never uses (the wait before the scatter keeps its own check)
   bool expired = false;
   auto wait_local = [&]() {
-    if (!mbar_wait(mbar, phase)) expired = true;
+    if (!mbar_wait(mbar, phase, FEKS_TC5_WAIT_ITERS)) expired = true;
     phase ^= 1u;
     fence_after();
   };
@@ -507,7 +511,8 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
       }
       pipe_sync();
       // (2) GEMM1: P_t = K_t^T X per plane
-      if (gt == 0) {
+      // fault injection (host side): the CTA's first tile of each pipeline issues nothing
+      if (gt == 0 && !(p.inject && u == (int)blockIdx.x && t == t_begin + g)) {
         fence_after();
 #pragma unroll
         for (int T = 0; T < G::MT1; ++T)
@@ -787,13 +792,14 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
   __syncthreads();
   if (failed && gt == 0) {
     atomicExch(p.err, 1);
-    (void)mbar_wait(mbar, failed_phase);   // a last bounded chance for MMAs in flight to drain
+    (void)mbar_wait(mbar, failed_phase, FEKS_TC5_WAIT_ITERS);   // a last bounded chance for MMAs in flight to drain
   }
   fence_before();
   __syncthreads();
   fence_after();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(tbase - 256u * (uint32_t)g));
+#undef FEKS_TC5_WAIT_ITERS
 }
 
 // The constant block of one degree: the plane operators KM and the z-sweep
@@ -923,6 +929,7 @@ cudaError_t launch_tc5(const Ctx& c, const LocalParams<float>& lp, cudaStream_t 
   p.alpha = lp.alpha;
   p.cst = f16 ? c.tc5_cst16 : c.tc5_cst;
   p.stagger = stagger;
+  p.inject = c.inject_fault;
   p.err = c.dev_status;
   if (!p.cst || !p.err || c.cplx || c.nq != c.np) return cudaErrorInvalidValue;
   switch (c.np) {

@@ -73,6 +73,7 @@ def _load():
     lib.fe_ks_set_config.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     lib.fe_ks_get_config.argtypes = [vp, ctypes.c_int, P(ctypes.c_int)]
     lib.fe_ks_device_status.argtypes = [vp, P(ctypes.c_int)]
+    lib.fe_ks_inject_fault.argtypes = [vp, ctypes.c_int]
     lib.fe_ks_cm_create.argtypes = [vp, ctypes.c_int, i64, P(vp)]
     lib.fe_ks_cm_apply.argtypes = [vp, vp, vp, i64]
     lib.fe_ks_cm_info.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_size_t)]
@@ -235,6 +236,11 @@ def fe_ks_device_status(ctx):
     out = ctypes.c_int()
     _check(_lib.fe_ks_device_status(ctx, ctypes.byref(out)))
     return out.value
+
+
+def fe_ks_inject_fault(ctx, kind):
+    """Host-side fault injection into the tcgen05 cell kernel (1 = on, 0 = off); tests only."""
+    _check(_lib.fe_ks_inject_fault(ctx, kind))
 
 
 def fe_ks_cm_create(ctx, precision, n_v_max):

@@ -165,3 +165,30 @@ def test_configuration_interface(cases):
         assert fk.fe_ks_device_status(ctx) == 0
     finally:
         fk.fe_ks_destroy(ctx)
+
+
+def test_expired_wait_reports_status_and_context_recovers(cases):
+    """Failure path without a GPU fault: with the host-side injection each pipeline's first
+    plane product is never issued or committed, so its bounded waits (short limit) run
+    out; the kernel stops cleanly, fe_ks_device_status reports it, and the next
+    application on the same context is correct."""
+    wl, hp, P, X = cases["C4v"]
+    prec = fk.FE_KS_BF16
+    Xin = round_input(X, prec)
+    n_v = X.shape[1]
+    ctx = fk.fe_ks_setup(hp.struct, fk.TERM_ALL, n_v, torch.cuda.current_stream().cuda_stream)
+    try:
+        Xd = torch.from_numpy(np.ascontiguousarray(Xin)).to("cuda").float()
+        Yd = torch.empty_like(Xd)
+        fk.fe_ks_inject_fault(ctx, 1)
+        fk.fe_ks_apply(ctx, Xd, Yd, n_v, prec)
+        assert fk.fe_ks_device_status(ctx) == 1
+        fk.fe_ks_inject_fault(ctx, 0)
+        Yd.fill_(float("nan"))
+        fk.fe_ks_apply(ctx, Xd, Yd, n_v, prec)
+        assert fk.fe_ks_device_status(ctx) == 0
+        assert parity_err(Yd.cpu().numpy(), P.apply(Xin)) <= TOL[prec]
+        with pytest.raises(fk.FeKsError, match="ERR_ARG"):
+            fk.fe_ks_inject_fault(ctx, 2)
+    finally:
+        fk.fe_ks_destroy(ctx)

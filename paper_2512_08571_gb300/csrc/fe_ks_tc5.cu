@@ -570,9 +570,10 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
       //     items (tile, half of the c' range)
       auto pointwise = [&](int T, auto H) {
         constexpr int LO = decltype(H)::value ? G::CH0 : 0, HI = decltype(H)::value ? G::CSL : G::CH0;
+        constexpr int J0 = 4 * LO / 16, J1 = (4 * HI + 15) / 16 < 3 ? (4 * HI + 15) / 16 : 3;   // 16-column blocks used
         float y[48];
 #pragma unroll
-        for (int j = 0; j < 3; ++j) ld16(tlane + T * G::TM_D23S + 16 * j, y + 16 * j);
+        for (int j = J0; j < J1; ++j) ld16(tlane + T * G::TM_D23S + 16 * j, y + 16 * j);
         ld_wait();
         const int r2 = 128 * T + 32 * quarter + lane;
         if (r2 < G::R2) {
@@ -642,27 +643,33 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
       wait_local();
       // (7) GEMM3 rows v + 4 p', columns 16 t + c -> B4 [(t, p')][c + 16 v] (MN-major);
       //     items (tile, half of the chunks)
-#pragma unroll 1
-      for (int it = sub; it < 2 * G::MT2; it += 2) {
-        const int T = it >> 1, h = it & 1;
+      auto readout3 = [&](int T, auto H) {
+        constexpr int HCN = N > 8 ? 2 : 1;
+        constexpr int C0 = decltype(H)::value ? G::NC3 / 2 : 0, C1 = decltype(H)::value ? G::NC3 : G::NC3 / 2;
+        constexpr int J0 = (16 * (C0 / HCN) + 8 * (C0 % HCN)) / 16;                 // 16-column blocks used
+        constexpr int J1 = (16 * ((C1 - 1) / HCN) + 8 * ((C1 - 1) % HCN) + 8 + 15) / 16;
         float d3[48];
 #pragma unroll
-        for (int j = 0; j < 3; ++j) ld16(tlane + T * G::TM_D23S + 16 * j, d3 + 16 * j);
+        for (int j = J0; j < J1; ++j) ld16(tlane + T * G::TM_D23S + 16 * j, d3 + 16 * j);
         ld_wait();
         const int r2 = 128 * T + 32 * quarter + lane;
         if (r2 < G::R2) {
           const int v = r2 & 3, pp = r2 >> 2;
-          constexpr int HCN = N > 8 ? 2 : 1;
 #pragma unroll
-          for (int ch = 0; ch < G::NC3; ++ch) {
-            if ((ch < G::NC3 / 2) == (h == 0)) {
-              const int tt = ch / HCN, hc = ch % HCN;
-              const float* sv = d3 + 16 * tt + 8 * hc;
-              st16(sAB + (tt * NN + pp) * 16 + (hc + 2 * v) * G::SBO4, pack<F16>(sv[0], sv[1]),
-                   pack<F16>(sv[2], sv[3]), pack<F16>(sv[4], sv[5]), pack<F16>(sv[6], sv[7]));
-            }
+          for (int ch = C0; ch < C1; ++ch) {
+            const int tt = ch / HCN, hc = ch % HCN;
+            const float* sv = d3 + 16 * tt + 8 * hc;
+            st16(sAB + (tt * NN + pp) * 16 + (hc + 2 * v) * G::SBO4, pack<F16>(sv[0], sv[1]), pack<F16>(sv[2], sv[3]),
+                 pack<F16>(sv[4], sv[5]), pack<F16>(sv[6], sv[7]));
           }
         }
+      };
+#pragma unroll 1
+      for (int it = sub; it < 2 * G::MT2; it += 2) {
+        if (it & 1)
+          readout3(it >> 1, std::integral_constant<int, 1>{});
+        else
+          readout3(it >> 1, std::integral_constant<int, 0>{});
       }
       // the K padding of GEMM4 (rows R1..K4 of B4, multiplied by zero rows of KM) must be
       // finite: zero it, as the buffer held other products' data

@@ -271,6 +271,9 @@ __device__ __forceinline__ bool gsync_or(int g, bool c) {
   return r != 0;
 }
 
+// bound of the kernel's mbarrier waits (short under host-side fault injection)
+__device__ __forceinline__ int wait_limit(const Params& p) { return p.inject ? kWaitItersInjected : kWaitIters; }
+
 // barrier 3: pipeline 0 arrives (256 threads), pipeline 1 waits (256 threads)
 __device__ __forceinline__ void stagger_arrive() { asm volatile("bar.arrive 3, 512;\n" ::: "memory"); }
 __device__ __forceinline__ void stagger_wait() { asm volatile("bar.sync 3, 512;\n" ::: "memory"); }
@@ -337,11 +340,10 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
   uint32_t phase = 0, failed_phase = 0;
   bool failed = false;
   int staged = -1;
-#define FEKS_TC5_WAIT_ITERS (p.inject ? kWaitItersInjected : kWaitIters)
 
   // the pipeline's threads: bounded wait for the products just committed; uniform result
   auto wait_products = [&]() -> bool {
-    const bool ok = mbar_wait(mbar, phase, FEKS_TC5_WAIT_ITERS);
+    const bool ok = mbar_wait(mbar, phase, wait_limit(p));
     if (gsync_or(g, !ok)) {
       failed = true;
       failed_phase = phase;
@@ -361,7 +363,7 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
   // buffers that the failed tile never uses (the wait before the scatter keeps its own check)
   bool expired = false;
   auto wait_local = [&]() {
-    if (!mbar_wait(mbar, phase, FEKS_TC5_WAIT_ITERS)) expired = true;
+    if (!mbar_wait(mbar, phase, wait_limit(p))) expired = true;
     phase ^= 1u;
     fence_after();
   };
@@ -799,14 +801,13 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
   __syncthreads();
   if (failed && gt == 0) {
     atomicExch(p.err, 1);
-    (void)mbar_wait(mbar, failed_phase, FEKS_TC5_WAIT_ITERS);   // a last bounded chance for MMAs in flight to drain
+    (void)mbar_wait(mbar, failed_phase, wait_limit(p));   // a last bounded chance for MMAs in flight to drain
   }
   fence_before();
   __syncthreads();
   fence_after();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(tbase - 256u * (uint32_t)g));
-#undef FEKS_TC5_WAIT_ITERS
 }
 
 // The constant block of one degree: the plane operators KM and the z-sweep

@@ -42,13 +42,18 @@
 //        [(t,p')][c + 16 v] (MN-major).
 //   B2, B3  the 1D operators of the z sweeps, K-major.
 // Tensor memory (from the pipeline's base column 256 g): GEMM1 tiles at 0 and
-// 64, GEMM2/3 tiles at 64 T, GEMM4 at 0 (each read out before the next
-// product overwrites it).
+// 64, GEMM2/3 tiles at 64 T, GEMM4 at 192 (each read out before the next
+// product that writes there is issued).
 //
-// One thread per pipeline issues each product's MMAs and commits them to the
-// pipeline's mbarrier; every wait is bounded (on expiry the pipeline stops, the
-// CTA sets the error word after the unit, lets the MMAs in flight drain with a
-// last bounded wait, frees its tensor memory and returns).  The nonlocal
+// One thread per pipeline issues each product's MMAs and commits them to one
+// of the pipeline's two mbarriers; it sits in the lane quarter whose in-plane
+// nodes (96..127) have no expansion or scatter work.  A tile's GEMM1 is issued
+// right after the previous tile's GEMM4 (the two do not share tensor-memory
+// columns), with the tile's X tile gathered while the previous tile's GEMM3
+// ran, so a tile starts with its plane product done.  Every wait is bounded
+// (on expiry the pipeline stops, the CTA sets the error word after the unit,
+// lets the MMAs in flight drain with a last bounded wait, frees its tensor
+// memory and returns).  The nonlocal
 // expansion F Delta P (FP32: the pair's F rows and the tile's Delta-scaled
 // projections Q, staged in shared memory) is computed while GEMM4 runs and
 // added to the accumulators in registers before the scatter; colour-exclusive
@@ -115,15 +120,18 @@ struct G5 {
   static constexpr int P_AB = P_XS + SZ_XS;
   static constexpr int P_QS = P_AB + SZ_AB;            // [QCAP][VT] Delta-scaled projections of the tile
   static constexpr int P_RED = P_QS + QCAP * VT * 4;   // FP16: [8 warps][VT] column maxima, [VT] scales
-  static constexpr int P_USC = P_RED + 9 * VT * 4;     // [VT] unscale factors
-  static constexpr int P_MBAR = (P_USC + VT * 4 + 7) / 8 * 8;
-  static constexpr int PIPE = (P_MBAR + 8 + 15) / 16 * 16;
+  static constexpr int P_USC = P_RED + 9 * VT * 4;     // [2][VT] unscale factors (two tiles in flight)
+  static constexpr int P_MBAR = (P_USC + 2 * VT * 4 + 7) / 8 * 8;   // two mbarriers: GEMM2-4, GEMM1
+  static constexpr int PIPE = (P_MBAR + 16 + 15) / 16 * 16;
   static constexpr int OFF_TMEM = OFF_PIPE + 2 * PIPE;
   static constexpr int BYTES = OFF_TMEM + 8;
-  // tensor-memory columns, from the pipeline's base (256 g): GEMM1 tiles at 64 T, GEMM2/3 tiles at 64 T, GEMM4 at 0
-  static constexpr uint32_t TM_D1S = 64, TM_D23S = 64;
+  // tensor-memory columns, from the pipeline's base (256 g): GEMM1 tiles at 64 T, GEMM2/3 tiles at 64 T
+  // (T <= 2: columns 0..175), GEMM4 at 192 (so the next tile's GEMM1 can run beside it)
+  static constexpr uint32_t TM_D1S = 64, TM_D23S = 64, TM_D4 = 192;
   static_assert(N >= 2 && N <= 9, "N");
-  static_assert(NN <= 128 && MT1 <= 2 && N1 <= 64 && N2 <= 64 && MT2 <= 3 && N4 <= 256, "tile shapes");
+  static_assert(NN <= 128 && MT1 <= 2 && N1 <= 64 && N2 <= 64 && MT2 <= 3 && N4 <= 64, "tile shapes");
+  static_assert((MT2 - 1) * TM_D23S + N2 <= TM_D4 && (MT1 - 1) * TM_D1S + N1 <= TM_D4 && TM_D4 + N4 <= 256,
+                "tensor-memory columns");
   static_assert(SZ_CST % 16 == 0 && OFF_PIPE % 16 == 0 && PIPE % 16 == 0 && P_AB % 16 == 0 && P_QS % 16 == 0,
                 "alignment");
   static_assert(BYTES <= 232448, "shared memory");
@@ -290,7 +298,10 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
   const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(smem);
   unsigned char* pb_ = smem + G::OFF_PIPE + g * G::PIPE;   // this pipeline's buffers
   const uint32_t sP = s0 + G::OFF_PIPE + g * G::PIPE;
-  const uint32_t sXS = sP + G::P_XS, sAB = sP + G::P_AB, mbar = sP + G::P_MBAR;
+  const uint32_t sXS = sP + G::P_XS, sAB = sP + G::P_AB, mbar = sP + G::P_MBAR, mbar1 = mbar + 8;
+  // the MMA-issuing thread: lane 0 of the pipeline's last warp (lane quarter 3: its in-plane
+  // nodes 96..127 have no expansion or scatter work, so issuing delays no other step)
+  constexpr int ISS = GT - 32;
   float* cf = reinterpret_cast<float*>(smem + G::OFF_CF);
   int* sd = reinterpret_cast<int*>(smem + G::OFF_SD);
   float* sds = reinterpret_cast<float*>(smem + G::OFF_DS);
@@ -307,9 +318,10 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
   for (int i = tid; i < 2 * G::PIPE / 16; i += NT)
     reinterpret_cast<uint4*>(smem + G::OFF_PIPE)[i] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
-  if (gt < VT) usc[gt] = 1.f;
+  if (gt < 2 * VT) usc[gt] = 1.f;
   if (gt == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar1));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 0) {
@@ -337,8 +349,9 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
   const int units = p.n_cells * p.units_per_cell;
   // this warp half's z planes in the final step
   const int cbeg = sub ? (N + 1) / 2 : 0, ccnt = sub ? N / 2 : (N + 1) / 2;
-  uint32_t phase = 0, failed_phase = 0;
-  bool failed = false;
+  // mbarrier phases: `mbar` tracks GEMM2-4, `mbar1` GEMM1 (issued one tile ahead)
+  uint32_t phase = 0, phase1 = 0, failed_phase = 0, failed_bar = 0;
+  bool failed = false, pend1 = false;   // pend1: a committed GEMM1 not yet waited for
   int staged = -1;
 
   // the pipeline's threads: bounded wait for the products just committed; uniform result
@@ -346,6 +359,7 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
     const bool ok = mbar_wait(mbar, phase, wait_limit(p));
     if (gsync_or(g, !ok)) {
       failed = true;
+      failed_bar = mbar;
       failed_phase = phase;
       return false;
     }
@@ -362,20 +376,31 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
   // barrier: a thread whose wait expired only moves stale tensor-memory values into shared
   // buffers that the failed tile never uses (the wait before the scatter keeps its own check)
   bool expired = false;
-  auto wait_local = [&]() {
-    if (!mbar_wait(mbar, phase, wait_limit(p))) expired = true;
-    phase ^= 1u;
+  auto wait_local = [&](uint32_t bar, uint32_t& ph) {
+    if (!mbar_wait(bar, ph, wait_limit(p))) expired = true;
+    ph ^= 1u;
     fence_after();
   };
-  auto pipe_sync_or = [&]() -> bool {   // pipe_sync, and whether any thread's wait expired
+  // pipe_sync, and whether any thread's wait expired; bar / ph: the barrier of the last
+  // wait and its phase after that wait
+  auto pipe_sync_or = [&](uint32_t bar, uint32_t ph) -> bool {
     fence_async_smem();
     fence_before();
     if (gsync_or(g, expired)) {
       failed = true;
-      failed_phase = phase ^ 1u;
+      failed_bar = bar;
+      failed_phase = ph ^ 1u;
       return false;
     }
     return true;
+  };
+  auto issue_gemm1 = [&]() {   // (2) GEMM1: P_t = K_t^T X per plane
+#pragma unroll
+    for (int T = 0; T < G::MT1; ++T)
+#pragma unroll
+      for (int ks = 0; ks < G::KP / 16; ++ks)
+        mma(tbase + T * G::TM_D1S, dKM1 + (uint64_t)((T * 2048 + ks * 2 * G::PGS) >> 4),
+            dXS + (uint64_t)((ks * 256) >> 4), ID1, ks > 0);
   };
   // this thread's gathered nodes of column tile [cx, cx + 4) and their D^{-1/2}
   // (registers; nothing waits on the loads until the tile's gather)
@@ -436,18 +461,10 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
     const int pe = p.cell_pair_ptr ? p.cell_pair_ptr[e + 1] : 0;
     const int nqrows = (pe - pb) * p.n_proj;
     const bool qstaged = nqrows <= G::QCAP && pe - pb <= G::PCAP;
-    bool have_next = false;   // xn already holds this tile's rows (loaded during the previous tile)
-    // offset the two pipelines within the unit: pipeline 1 waits until pipeline 0 has passed
-    // the stagger point of its first tile (pipeline 0 always has one; it arrives exactly once,
-    // also when its wait fails, so the barrier always completes)
-    bool arrived = p.stagger == 0 || g == 1;
-    if (p.stagger != 0 && g == 1) stagger_wait();
-
-    // this pipeline's column tiles of the unit: every other one
-    for (int t = t_begin + g; t < t_end; t += 2) {
-      const int col0 = VT * t;
-      // (1) extraction Q C P X (Algorithm 1): rows of X -> the MN-major X tile
-      if (!have_next) load_x(col0);
+    // (1) extraction Q C P X (Algorithm 1) of column tile [cx, cx + 4): the prefetched rows
+    //     of X (xn) -> the MN-major X tile; FP16 scales -> unscale set ubn; the tile's rows of
+    //     Q -> q (stored to shared memory once the previous tile's expansion is done)
+    auto gather = [&](int cx, int ubn, float4& q) {
 #pragma unroll
       for (int r = 0; r < GPT; ++r)
 #pragma unroll
@@ -476,7 +493,7 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
           for (int w = 0; w < 8; ++w) m = fmaxf(m, red[w * VT + gt]);
           const float sc = col_scale(m);
           red[8 * VT + gt] = sc;
-          usc[gt] = 1.f / sc;   // exact: a power of two
+          usc[ubn * VT + gt] = 1.f / sc;   // exact: a power of two
         }
         gsync(g);
 #pragma unroll
@@ -497,34 +514,47 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
                        : "memory");
         }
       }
-      // the tile's rows of Q (one row per thread), stored to shared memory once GEMM1 has run
-      float4 qreg = make_float4(0.f, 0.f, 0.f, 0.f);
+      // the tile's rows of Q (one row per thread)
+      q = make_float4(0.f, 0.f, 0.f, 0.f);
       if (qstaged && gt < nqrows) {
         const int b = gt % p.n_proj;
-        const float* qr = p.Q + ((int64_t)spa[gt / p.n_proj] * p.n_proj + b) * p.ld + col0;
-        if (vec && col0 + 4 <= p.ncols) {
-          qreg = __ldg(reinterpret_cast<const float4*>(qr));
+        const float* qr = p.Q + ((int64_t)spa[gt / p.n_proj] * p.n_proj + b) * p.ld + cx;
+        if (vec && cx + 4 <= p.ncols) {
+          q = __ldg(reinterpret_cast<const float4*>(qr));
         } else {
-          if (col0 < p.ncols) qreg.x = __ldg(qr);
-          if (col0 + 1 < p.ncols) qreg.y = __ldg(qr + 1);
-          if (col0 + 2 < p.ncols) qreg.z = __ldg(qr + 2);
-          if (col0 + 3 < p.ncols) qreg.w = __ldg(qr + 3);
+          if (cx < p.ncols) q.x = __ldg(qr);
+          if (cx + 1 < p.ncols) q.y = __ldg(qr + 1);
+          if (cx + 2 < p.ncols) q.z = __ldg(qr + 2);
+          if (cx + 3 < p.ncols) q.w = __ldg(qr + 3);
         }
       }
+    };
+    // offset the two pipelines within the unit: pipeline 1 waits until pipeline 0 has passed
+    // the stagger point of its first tile (pipeline 0 always has one; it arrives exactly once,
+    // also when its wait fails, so the barrier always completes)
+    bool arrived = p.stagger == 0 || g == 1;
+    if (p.stagger != 0 && g == 1) stagger_wait();
+    // this pipeline's column tiles of the unit: every other one.  A tile's GEMM1 is issued
+    // during the previous tile (with its GEMM4), or here for the first.
+    int ub = 0;   // the unscale set of the current tile
+    float4 qreg = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (t_begin + g < t_end) {
+      load_x(VT * (t_begin + g));
+      gather(VT * (t_begin + g), 0, qreg);
       pipe_sync();
-      // (2) GEMM1: P_t = K_t^T X per plane
-      // fault injection (host side): the CTA's first tile of each pipeline issues nothing
-      if (gt == 0 && !(p.inject && u == (int)blockIdx.x && t == t_begin + g)) {
+      // fault injection (host side): the CTA's first GEMM1 of each pipeline is not issued
+      if (gt == ISS && !(p.inject && u == (int)blockIdx.x)) {
         fence_after();
-#pragma unroll
-        for (int T = 0; T < G::MT1; ++T)
-#pragma unroll
-          for (int ks = 0; ks < G::KP / 16; ++ks)
-            mma(tbase + T * G::TM_D1S, dKM1 + (uint64_t)((T * 2048 + ks * 2 * G::PGS) >> 4),
-                dXS + (uint64_t)((ks * 256) >> 4), ID1, ks > 0);
-        commit(mbar);
+        issue_gemm1();
+        commit(mbar1);
       }
-      wait_local();
+      pend1 = true;
+    }
+    for (int t = t_begin + g; t < t_end; t += 2) {
+      const int col0 = VT * t;
+      const bool nxt = t + 2 < t_end;   // this pipeline has another tile in the unit
+      wait_local(mbar1, phase1);
+      pend1 = false;
       if (!arrived && p.stagger == 1) {
         stagger_arrive();
         arrived = true;
@@ -555,9 +585,9 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
           }
         }
       }
-      if (!pipe_sync_or()) break;
+      if (!pipe_sync_or(mbar1, phase1)) break;
       // (4) GEMM2: the z sweep
-      if (gt == 0) {
+      if (gt == ISS) {
         fence_after();
 #pragma unroll
         for (int T = 0; T < G::MT2; ++T)
@@ -567,7 +597,7 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
                 dB2 + (uint64_t)((ks * 2 * G::N2 * 16) >> 4), ID2, ks > 0);
         commit(mbar);
       }
-      wait_local();
+      wait_local(mbar, phase);
       // (5) quadrature-point step: (Y0, Y_x, Y_y, Y_z)[c'] -> (Z, W_x, W_y, W_z)[c'] (A3, k = 4 c' + q);
       //     items (tile, half of the c' range)
       auto pointwise = [&](int T, auto H) {
@@ -616,9 +646,10 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
                  pack<F16>(o[8 * kc + 6], o[8 * kc + 7]));
         }
       };
+      // a warp half's items alternate halves of the c' range (the upper half holds more planes)
 #pragma unroll 1
       for (int it = sub; it < 2 * G::MT2; it += 2) {
-        if (it & 1)
+        if ((it ^ (it >> 1)) & 1)
           pointwise(it >> 1, std::integral_constant<int, 1>{});
         else
           pointwise(it >> 1, std::integral_constant<int, 0>{});
@@ -627,12 +658,9 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
         stagger_arrive();
         arrived = true;
       }
-      // this pipeline's next column tile's rows of X, in flight during the rest of this tile
-      have_next = t + 2 < t_end;
-      if (have_next) load_x(col0 + 2 * VT);
-      if (!pipe_sync_or()) break;
+      if (!pipe_sync_or(mbar, phase)) break;
       // (6) GEMM3: the transposed z sweep
-      if (gt == 0) {
+      if (gt == ISS) {
         fence_after();
 #pragma unroll
         for (int T = 0; T < G::MT2; ++T)
@@ -642,7 +670,9 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
                 dB3 + (uint64_t)((ks * 2 * G::N3C * 16) >> 4), ID3, ks > 0);
         commit(mbar);
       }
-      wait_local();
+      // the next tile's rows of X, in flight while GEMM3 runs and its accumulators are read out
+      if (nxt) load_x(col0 + 2 * VT);
+      wait_local(mbar, phase);
       // (7) GEMM3 rows v + 4 p', columns 16 t + c -> B4 [(t, p')][c + 16 v] (MN-major);
       //     items (tile, half of the chunks)
       auto readout3 = [&](int T, auto H) {
@@ -677,15 +707,23 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
       // finite: zero it, as the buffer held other products' data
       for (int i = gt; i < (G::K4 - G::R1) * (G::N4 / 8); i += GT)
         st16(sAB + (G::R1 + i / (G::N4 / 8)) * 16 + (i % (G::N4 / 8)) * G::SBO4, 0u, 0u, 0u, 0u);
-      if (!pipe_sync_or()) break;
-      // (8) GEMM4: the transposed plane product
-      if (gt == 0) {
+      // the next tile's X tile (free: this tile's GEMM1 is done)
+      if (nxt) gather(col0 + 2 * VT, ub ^ 1, qreg);
+      if (!pipe_sync_or(mbar, phase)) break;
+      // (8) GEMM4: the transposed plane product; then the next tile's GEMM1 (its accumulators
+      //     do not overlap GEMM4's)
+      if (gt == ISS) {
         fence_after();
 #pragma unroll
         for (int ks = 0; ks < G::K4 / 16; ++ks)
-          mma(tbase, dKM4 + (uint64_t)((ks * 256) >> 4), dB4 + (uint64_t)((ks * 256) >> 4), ID4, ks > 0);
+          mma(tbase + G::TM_D4, dKM4 + (uint64_t)((ks * 256) >> 4), dB4 + (uint64_t)((ks * 256) >> 4), ID4, ks > 0);
         commit(mbar);
+        if (nxt) {
+          issue_gemm1();
+          commit(mbar1);
+        }
       }
+      pend1 = nxt;
       // (9) F Delta P (nonlocal expansion) for this thread's nodes, computed while
       //     GEMM4 runs; then Y += alpha D^{-1/2} Q^T (Y^(e) + F Delta P)
       const int pp = 32 * quarter + lane;   // in-plane node of this lane
@@ -765,7 +803,7 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
             const int c = cbeg + (j < ccnt ? j : 0);
             asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];\n"
                          : "=r"(r)
-                         : "r"(tlane + (uint32_t)(c + 16 * v)));
+                         : "r"(tlane + G::TM_D4 + (uint32_t)(c + 16 * v)));
             o[j][v] = __uint_as_float(r);
           }
         ld_wait();
@@ -779,7 +817,7 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
             const float s = p.alpha * sds[pp + NN * c];
             float w[VT];
 #pragma unroll
-            for (int v = 0; v < VT; ++v) w[v] = s * fmaf(o[j][v], usc[v], ex[j][v]);
+            for (int v = 0; v < VT; ++v) w[v] = s * fmaf(o[j][v], usc[ub * VT + v], ex[j][v]);
             float* yp = p.Y + (int64_t)d * p.ld + col0;
             if (vecy && col0 + VT <= p.ncols) {
               atomicAdd(reinterpret_cast<float4*>(yp), make_float4(w[0], w[1], w[2], w[3]));
@@ -791,6 +829,7 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
           }
         }
       }
+      ub ^= 1;
     }
     if (!arrived) stagger_arrive();   // pipeline 0 left the unit before its stagger point
     if (__syncthreads_or(failed)) {
@@ -801,7 +840,10 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
   __syncthreads();
   if (failed && gt == 0) {
     atomicExch(p.err, 1);
-    (void)mbar_wait(mbar, failed_phase, wait_limit(p));   // a last bounded chance for MMAs in flight to drain
+    // a last bounded chance for the MMAs in flight to drain: the products of the wait that
+    // expired, and a GEMM1 committed ahead (a pipeline stopped only by the other one has none)
+    if (failed_bar) (void)mbar_wait(failed_bar, failed_phase, wait_limit(p));
+    if (pend1 && failed_bar != mbar1) (void)mbar_wait(mbar1, phase1, wait_limit(p));
   }
   fence_before();
   __syncthreads();

@@ -47,13 +47,13 @@
 //
 // One thread per pipeline issues each product's MMAs and commits them to one
 // of the pipeline's two mbarriers; it sits in the lane quarter whose in-plane
-// nodes (96..127) have no expansion or scatter work.  A tile's GEMM1 is issued
-// right after the previous tile's GEMM4 (the two do not share tensor-memory
-// columns), with the tile's X tile gathered while the previous tile's GEMM3
-// ran, so a tile starts with its plane product done.  Every wait is bounded
-// (on expiry the pipeline stops, the CTA sets the error word after the unit,
-// lets the MMAs in flight drain with a last bounded wait, frees its tensor
-// memory and returns).  The nonlocal
+// nodes (96..127) have no expansion or scatter work.  A tile's X tile is
+// gathered while the previous tile's GEMM4 runs, and its GEMM1 is issued once
+// that GEMM4 is done (the two do not share tensor-memory columns), beside the
+// previous tile's scatter: a tile starts with its plane product done.  Every
+// wait is bounded (on expiry the pipeline stops, the CTA sets the error word
+// after the unit, lets the MMAs in flight drain with a last bounded wait, frees
+// its tensor memory and returns).  The nonlocal
 // expansion F Delta P (FP32: the pair's F rows and the tile's Delta-scaled
 // projections Q, staged in shared memory) is computed while GEMM4 runs and
 // added to the accumulators in registers before the scatter; colour-exclusive
@@ -355,8 +355,10 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
   int staged = -1;
 
   // the pipeline's threads: bounded wait for the products just committed; uniform result
+  // (the barrier also hands the generic-proxy shared stores before it to the tensor cores)
   auto wait_products = [&]() -> bool {
     const bool ok = mbar_wait(mbar, phase, wait_limit(p));
+    fence_async_smem();
     if (gsync_or(g, !ok)) {
       failed = true;
       failed_bar = mbar;
@@ -670,7 +672,7 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
                 dB3 + (uint64_t)((ks * 2 * G::N3C * 16) >> 4), ID3, ks > 0);
         commit(mbar);
       }
-      // the next tile's rows of X, in flight while GEMM3 runs and its accumulators are read out
+      // the next tile's rows of X, in flight until its gather during GEMM4
       if (nxt) load_x(col0 + 2 * VT);
       wait_local(mbar, phase);
       // (7) GEMM3 rows v + 4 p', columns 16 t + c -> B4 [(t, p')][c + 16 v] (MN-major);
@@ -707,23 +709,15 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
       // finite: zero it, as the buffer held other products' data
       for (int i = gt; i < (G::K4 - G::R1) * (G::N4 / 8); i += GT)
         st16(sAB + (G::R1 + i / (G::N4 / 8)) * 16 + (i % (G::N4 / 8)) * G::SBO4, 0u, 0u, 0u, 0u);
-      // the next tile's X tile (free: this tile's GEMM1 is done)
-      if (nxt) gather(col0 + 2 * VT, ub ^ 1, qreg);
       if (!pipe_sync_or(mbar, phase)) break;
-      // (8) GEMM4: the transposed plane product; then the next tile's GEMM1 (its accumulators
-      //     do not overlap GEMM4's)
+      // (8) GEMM4: the transposed plane product
       if (gt == ISS) {
         fence_after();
 #pragma unroll
         for (int ks = 0; ks < G::K4 / 16; ++ks)
           mma(tbase + G::TM_D4, dKM4 + (uint64_t)((ks * 256) >> 4), dB4 + (uint64_t)((ks * 256) >> 4), ID4, ks > 0);
         commit(mbar);
-        if (nxt) {
-          issue_gemm1();
-          commit(mbar1);
-        }
       }
-      pend1 = nxt;
       // (9) F Delta P (nonlocal expansion) for this thread's nodes, computed while
       //     GEMM4 runs; then Y += alpha D^{-1/2} Q^T (Y^(e) + F Delta P)
       const int pp = 32 * quarter + lane;   // in-plane node of this lane
@@ -792,7 +786,15 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
           }
         }
       }
+      // the next tile's X tile (free: this tile's GEMM1 is done), while GEMM4 runs
+      if (nxt) gather(col0 + 2 * VT, ub ^ 1, qreg);
       if (!wait_products()) break;
+      // the next tile's GEMM1 (its accumulators do not overlap GEMM4's), beside this tile's scatter
+      if (gt == ISS && nxt) {
+        issue_gemm1();
+        commit(mbar1);
+      }
+      pend1 = nxt;
       {
         float o[G::MAXC][VT];
 #pragma unroll

@@ -93,6 +93,9 @@ struct G5 {
   static constexpr int CSL = K3 / 4;                   // c' slots of a row (with padding)
   static constexpr int NC3 = 3 * (N > 8 ? 2 : 1);      // 16-byte chunks of a GEMM4 operand row group
   static constexpr int MAXC = (N + 1) / 2;             // z planes per warp half in the final step
+  static constexpr int PWC = (CH0 > (CSL < N ? CSL : N) - CH0 ? CH0 : (CSL < N ? CSL : N) - CH0);
+                                                       // planes c' < N in a half of the quadrature-point step
+  static constexpr int R3C = NC3 - NC3 / 2;            // chunks in a half of the GEMM3 readout (the larger)
   static constexpr int PG = 16;                        // p groups of KM (GEMM4 M = 128)
   static constexpr int PGS = R1P * 16;                 // byte stride of a p group in KM
   static constexpr int QCAP = 64, PCAP = 16;           // staged (pair, projector) rows; staged pairs
@@ -179,6 +182,24 @@ __device__ __forceinline__ void ld16(uint32_t ta, float* v) {
       : "r"(ta));
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 8 (4) consecutive FP32 columns of this thread's tensor-memory lane
+__device__ __forceinline__ void ld8(uint32_t ta, float* v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(ta));
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void ld4(uint32_t ta, float* v) {
+  uint32_t r[4];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(ta));
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ void ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
@@ -600,15 +621,18 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
         commit(mbar);
       }
       wait_local(mbar, phase);
-      // (5) quadrature-point step: (Y0, Y_x, Y_y, Y_z)[c'] -> (Z, W_x, W_y, W_z)[c'] (A3, k = 4 c' + q);
-      //     items (tile, half of the c' range)
-      auto pointwise = [&](int T, auto H) {
+      // (5) quadrature-point step: (Y0, Y_x, Y_y, Y_z)[c'] -> (Z, W_x, W_y, W_z)[c'] (A3, k = 4 c' + q).
+      //     Items (tile T, half H of the c' range): a warp half takes (0, H), (1, !H), (2, H) (the
+      //     upper half holds more planes).  It loads the accumulator columns (4 per plane) of the
+      //     first two, waits once, and loads the third's while it computes the first.
+      auto pw_load = [&](int T, auto H, float* y) {
         constexpr int LO = decltype(H)::value ? G::CH0 : 0, HI = decltype(H)::value ? G::CSL : G::CH0;
-        constexpr int J0 = 4 * LO / 16, J1 = (4 * HI + 15) / 16 < 3 ? (4 * HI + 15) / 16 : 3;   // 16-column blocks used
-        float y[48];
+        constexpr int NV = (HI < N ? HI : N) - LO;   // planes c' < N of the half
 #pragma unroll
-        for (int j = J0; j < J1; ++j) ld16(tlane + T * G::TM_D23S + 16 * j, y + 16 * j);
-        ld_wait();
+        for (int k = 0; k < NV; ++k) ld4(tlane + T * G::TM_D23S + 4 * (LO + k), y + 4 * k);
+      };
+      auto pw_compute = [&](int T, auto H, const float* y) {
+        constexpr int LO = decltype(H)::value ? G::CH0 : 0, HI = decltype(H)::value ? G::CSL : G::CH0;
         const int r2 = 128 * T + 32 * quarter + lane;
         if (r2 < G::R2) {
           const int pp = r2 >> 2;
@@ -621,7 +645,8 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
               const float4 ca = *reinterpret_cast<const float4*>(cp);
               const float4 cb = *reinterpret_cast<const float4*>(cp + 4);
               const float G00 = ca.x, G01 = ca.y, G02 = ca.z, G11 = ca.w, G12 = cb.x, G22 = cb.y, VL = cb.z;
-              const float u = y[4 * c], gx = y[4 * c + 1], gy = y[4 * c + 2], gz = y[4 * c + 3];
+              const float* yc = y + 4 * (c - LO);
+              const float u = yc[0], gx = yc[1], gy = yc[2], gz = yc[3];
               z = VL * u;
               w0 = fmaf(G00, gx, fmaf(G01, gy, G02 * gz));
               w1 = fmaf(G01, gx, fmaf(G11, gy, G12 * gz));
@@ -648,14 +673,25 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
                  pack<F16>(o[8 * kc + 6], o[8 * kc + 7]));
         }
       };
-      // a warp half's items alternate halves of the c' range (the upper half holds more planes)
-#pragma unroll 1
-      for (int it = sub; it < 2 * G::MT2; it += 2) {
-        if ((it ^ (it >> 1)) & 1)
-          pointwise(it >> 1, std::integral_constant<int, 1>{});
-        else
-          pointwise(it >> 1, std::integral_constant<int, 0>{});
-      }
+      auto pw_items = [&](auto H) {
+        using HA = std::integral_constant<int, decltype(H)::value>;
+        using HB = std::integral_constant<int, 1 - decltype(H)::value>;
+        float y0[4 * G::PWC], y1[4 * G::PWC], y2[4 * G::PWC];
+        pw_load(0, HA{}, y0);
+        if constexpr (G::MT2 > 1) pw_load(1, HB{}, y1);
+        ld_wait();
+        pw_compute(0, HA{}, y0);
+        if constexpr (G::MT2 > 2) pw_load(2, HA{}, y2);
+        if constexpr (G::MT2 > 1) pw_compute(1, HB{}, y1);
+        if constexpr (G::MT2 > 2) {
+          ld_wait();
+          pw_compute(2, HA{}, y2);
+        }
+      };
+      if (sub)
+        pw_items(std::integral_constant<int, 1>{});
+      else
+        pw_items(std::integral_constant<int, 0>{});
       if (!arrived) {   // stagger point 2: after the first quadrature-point step
         stagger_arrive();
         arrived = true;
@@ -676,35 +712,43 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
       if (nxt) load_x(col0 + 2 * VT);
       wait_local(mbar, phase);
       // (7) GEMM3 rows v + 4 p', columns 16 t + c -> B4 [(t, p')][c + 16 v] (MN-major);
-      //     items (tile, half of the chunks)
-      auto readout3 = [&](int T, auto H) {
-        constexpr int HCN = N > 8 ? 2 : 1;
+      //     items (tile T, half H = the warp half of the 16-byte chunks (t, 8-column half)): the
+      //     chunks of all three tiles are loaded (8 columns each), then stored after one wait
+      constexpr int HCN = N > 8 ? 2 : 1;   // 8-column chunks of a 16-column group
+      auto r3_load = [&](int T, auto H, float* d) {
         constexpr int C0 = decltype(H)::value ? G::NC3 / 2 : 0, C1 = decltype(H)::value ? G::NC3 : G::NC3 / 2;
-        constexpr int J0 = (16 * (C0 / HCN) + 8 * (C0 % HCN)) / 16;                 // 16-column blocks used
-        constexpr int J1 = (16 * ((C1 - 1) / HCN) + 8 * ((C1 - 1) % HCN) + 8 + 15) / 16;
-        float d3[48];
 #pragma unroll
-        for (int j = J0; j < J1; ++j) ld16(tlane + T * G::TM_D23S + 16 * j, d3 + 16 * j);
-        ld_wait();
+        for (int ch = C0; ch < C1; ++ch)
+          ld8(tlane + T * G::TM_D23S + 16 * (ch / HCN) + 8 * (ch % HCN), d + 8 * (ch - C0));
+      };
+      auto r3_store = [&](int T, auto H, const float* d) {
+        constexpr int C0 = decltype(H)::value ? G::NC3 / 2 : 0, C1 = decltype(H)::value ? G::NC3 : G::NC3 / 2;
         const int r2 = 128 * T + 32 * quarter + lane;
         if (r2 < G::R2) {
           const int v = r2 & 3, pp = r2 >> 2;
 #pragma unroll
           for (int ch = C0; ch < C1; ++ch) {
             const int tt = ch / HCN, hc = ch % HCN;
-            const float* sv = d3 + 16 * tt + 8 * hc;
+            const float* sv = d + 8 * (ch - C0);
             st16(sAB + (tt * NN + pp) * 16 + (hc + 2 * v) * G::SBO4, pack<F16>(sv[0], sv[1]), pack<F16>(sv[2], sv[3]),
                  pack<F16>(sv[4], sv[5]), pack<F16>(sv[6], sv[7]));
           }
         }
       };
-#pragma unroll 1
-      for (int it = sub; it < 2 * G::MT2; it += 2) {
-        if (it & 1)
-          readout3(it >> 1, std::integral_constant<int, 1>{});
-        else
-          readout3(it >> 1, std::integral_constant<int, 0>{});
-      }
+      auto r3_items = [&](auto H) {
+        float d0[8 * G::R3C], d1[8 * G::R3C], d2[8 * G::R3C];
+        r3_load(0, H, d0);
+        if constexpr (G::MT2 > 1) r3_load(1, H, d1);
+        if constexpr (G::MT2 > 2) r3_load(2, H, d2);
+        ld_wait();
+        r3_store(0, H, d0);
+        if constexpr (G::MT2 > 1) r3_store(1, H, d1);
+        if constexpr (G::MT2 > 2) r3_store(2, H, d2);
+      };
+      if (sub)
+        r3_items(std::integral_constant<int, 1>{});
+      else
+        r3_items(std::integral_constant<int, 0>{});
       // the K padding of GEMM4 (rows R1..K4 of B4, multiplied by zero rows of KM) must be
       // finite: zero it, as the buffer held other products' data
       for (int i = gt; i < (G::K4 - G::R1) * (G::N4 / 8); i += GT)

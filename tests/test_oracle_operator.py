@@ -172,6 +172,25 @@ def test_volume_and_null_space_jittered(nqx):
     assert abs(P.lumped_mass().sum() - wl.L ** 3) < 1e-9 * wl.L ** 3
 
 
+@pytest.mark.parametrize("p,jitter", [(1, 0.0), (2, 0.0), (3, 0.1), (4, 0.12), (5, 0.1)])
+def test_lumped_mass_is_the_row_sum_of_the_consistent_mass(p, jitter):
+    """D_I (GLL weights times det J at the node) equals sum_J M_IJ = int N_I dV wherever the
+    GLL rule integrates N_I det J exactly: N_I has degree p per variable, det J of a trilinear
+    cell degree <= 2 (0 when the cell is affine), and the (p + 1)-point GLL rule is exact to
+    degree 2 p - 1, so affine cells for every p and jittered cells for p >= 3.  Unlike the
+    volume check, this holds node by node, so a misplaced weight or det J evaluated at the
+    wrong node (an axis swap keeps the sum) fails it."""
+    wl = _periodic(n=3, p=p, jitter=jitter)
+    P = Problem(wl, vloc=_zero, vgga=None)
+    one = np.ones(P.m)
+    M1 = np.zeros(P.m)
+    for e in range(P.E):
+        d = P.dofs[e]
+        M1[d] += P.mass_matrix(e) @ one[d]
+    D = P.lumped_mass()
+    assert np.max(np.abs(D - M1)) <= 1e-13 * np.max(M1)
+
+
 @pytest.mark.parametrize("nqx", [0, 2])
 def test_k_shift_null_space(nqx):
     """V = V^G = 0, no atoms: H(k) 1 = |k|^2/2 M 1."""

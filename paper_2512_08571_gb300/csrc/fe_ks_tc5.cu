@@ -129,7 +129,8 @@ struct G5 {
   static constexpr int OFF_TMEM = OFF_PIPE + 2 * PIPE;
   static constexpr int BYTES = OFF_TMEM + 8;
   // tensor-memory columns, from the pipeline's base (256 g): GEMM1 tiles at 64 T, GEMM2/3 tiles at 64 T
-  // (T <= 2: columns 0..175), GEMM4 at 192 (so the next tile's GEMM1 can run beside it)
+  // (T <= 2: columns 0..175), GEMM4 at 192 (so the next tile's GEMM1 can run while GEMM4's
+  // accumulators are read out)
   static constexpr uint32_t TM_D1S = 64, TM_D23S = 64, TM_D4 = 192;
   static_assert(N >= 2 && N <= 9, "N");
   static_assert(NN <= 128 && MT1 <= 2 && N1 <= 64 && N2 <= 64 && MT2 <= 3 && N4 <= 64, "tile shapes");
@@ -558,7 +559,7 @@ __global__ void __launch_bounds__(512, 1) fe_tc5_kernel(const __grid_constant__ 
     bool arrived = p.stagger == 0 || g == 1;
     if (p.stagger != 0 && g == 1) stagger_wait();
     // this pipeline's column tiles of the unit: every other one.  A tile's GEMM1 is issued
-    // during the previous tile (with its GEMM4), or here for the first.
+    // during the previous tile (once its GEMM4 is done), or here for the first.
     int ub = 0;   // the unscale set of the current tile
     float4 qreg = make_float4(0.f, 0.f, 0.f, 0.f);
     if (t_begin + g < t_end) {
